@@ -1,0 +1,570 @@
+"""Pins of the FP64 oracle against things other than itself: textbook
+routines, closed forms, identities of the paper's equations, brute-force
+quadrature of the paper's 3D formulas, and the paper's printed constants.
+
+Each test names the passage of Busuioc & Sofonea (arXiv:2503.15187) it checks.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+PV = json.load(open(GOLDEN))
+
+
+def mk(nz=64, Q=16, dz=0.25, bc=0, relax=0, dt=None, rcut=6.0):
+    if dt is None:
+        xi, _ = O.gauss_hermite(Q)
+        dt = 0.5 * dz / np.abs(xi).max()
+    return O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=dt, bc=bc, relax=relax, rcut=rcut))
+
+
+# ---------------------------------------------------------------------------
+# velocity set (Sec. III: full-range Gauss-Hermite quadrature)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("Q", [4, 8, 16, 24, 32])
+def test_gauss_hermite_against_golub_welsch(Q):
+    """Nodes/weights agree with the Golub-Welsch eigen-decomposition of the
+    Jacobi matrix of the probabilists' Hermite recurrence."""
+    xi, w = O.gauss_hermite(Q)
+    J = np.diag(np.sqrt(np.arange(1, Q)), 1)
+    J = J + J.T
+    ev, V = np.linalg.eigh(J)
+    assert np.allclose(np.sort(xi), ev, rtol=0, atol=1e-12 * max(1, np.abs(ev).max()))
+    wgw = V[0, :] ** 2
+    order = np.argsort(xi)
+    assert np.allclose(w[order], wgw, rtol=1e-9, atol=1e-16)
+    assert abs(w.sum() - 1) < 1e-14
+
+
+def test_gauss_hermite_small_closed_forms():
+    xi, w = O.gauss_hermite(2)
+    assert np.allclose(np.sort(xi), [-1, 1], atol=1e-15) and np.allclose(w, 0.5, atol=1e-15)
+    xi, w = O.gauss_hermite(3)
+    o = np.argsort(xi)
+    assert np.allclose(xi[o], [-math.sqrt(3), 0, math.sqrt(3)], atol=1e-14)
+    assert np.allclose(w[o], [1 / 6, 2 / 3, 1 / 6], atol=1e-15)
+
+
+@pytest.mark.parametrize("Q", [8, 16, 32])
+def test_gauss_hermite_moment_exactness(Q):
+    """sum_k w_k xi_k^s = E[Z^s] = (s-1)!! for even s, 0 for odd, s <= 2Q-1."""
+    xi, w = O.gauss_hermite(Q)
+    for s in range(0, 2 * Q):
+        exact = 0.0 if s % 2 else float(np.prod(np.arange(s - 1, 0, -2, dtype=float))) if s else 1.0
+        got = np.sum(w * xi ** s)
+        scale = max(1.0, float(np.sum(w * np.abs(xi) ** s)))
+        assert abs(got - exact) <= 1e-13 * scale, (s, got, exact)
+
+
+# ---------------------------------------------------------------------------
+# projected equilibria and moments (Sec. II.B moments; C4 reading)
+# ---------------------------------------------------------------------------
+def gauss_moment(s, u, T):
+    """E[(u + sqrt(T) Z)^s] by the binomial expansion and E[Z^j] = (j-1)!!."""
+    tot = 0.0
+    for j in range(0, s + 1, 2):
+        dfact = float(np.prod(np.arange(j - 1, 0, -2, dtype=float))) if j else 1.0
+        tot += math.comb(s, j) * u ** (s - j) * T ** (j / 2) * dfact
+    return tot
+
+
+@pytest.mark.parametrize("Q,u,T", [(16, 0.0, 0.6), (16, 0.3, 0.55), (24, -0.4, 0.9), (32, 0.2, 0.7)])
+def test_projected_maxwellian_moments(Q, u, T):
+    """Projected equilibrium reproduces the Gaussian moments up to order Q-1."""
+    o = mk(nz=4, Q=Q)
+    n = 0.37
+    FS, GS, JF, JG = o.equilibria_node(n, u, T)
+    for s in range(Q):
+        exact = n * gauss_moment(s, u, T)
+        # rounding scale: the synthesis w_k sum_l a_l He_l(xi_k)/l! is an orthogonal
+        # transform up to sqrt(w_k), so each F_k carries an absolute error of
+        # order eps n sqrt(w_k), which xi_k^s amplifies at the tail nodes
+        scale = float(np.sum(np.abs(FS * o.xi ** s))) + n * float(np.sum(np.sqrt(o.w) * np.abs(o.xi) ** s))
+        assert abs(np.sum(FS * o.xi ** s) - exact) <= 1e-13 * scale, s
+        assert abs(np.sum(GS * o.xi ** s) - T * exact) <= 1e-13 * T * scale, s
+    assert np.all(JF == 0) and np.all(JG == 0)
+
+
+def test_moments_recover_state():
+    o = mk(nz=5, Q=16)
+    n = np.array([0.1, 0.2, 0.3, 0.5, 0.7])
+    u = np.array([0.0, 0.1, -0.2, 0.3, -0.05])
+    T = np.array([0.5, 0.6, 0.7, 0.8, 1.1])
+    F, G = o.equilibrium(n, u, T)
+    n2, u2, T2, q2 = o.moments(F, G)
+    assert np.allclose(n2, n, rtol=1e-14) and np.allclose(u2, u, atol=1e-14)
+    assert np.allclose(T2, T, rtol=1e-13) and np.all(np.abs(q2) < 1e-14)
+
+
+def _reduced_3d_coeffs(Q, n, u, T, q, Pr, bnchi, A, B, D, nq=20):
+    """Hermite coefficients int h(xi) He_l(xi) dxi of the reduced distributions,
+    computed by integrating the paper's 3D f^S (Sec. II.B) and 3D J1 (Eq. (J1))
+    over (p_x, p_y, p_z) with a tensor Gauss-Hermite rule; reduction weights 1
+    (for F) and (p_y^2 + p_z^2)/2 (for G)."""
+    z, wz = O.gauss_hermite(nq)
+    Z1, Z2, Z3 = np.meshgrid(z, z, z, indexing="ij")
+    W = (wz[:, None, None] * wz[None, :, None] * wz[None, None, :]) * n
+    st = math.sqrt(T)
+    cx, cy, cz = st * Z1, st * Z2, st * Z3
+    c2 = cx * cx + cy * cy + cz * cz
+    Pi = n * T
+    shak = 1 + (1 - Pr) / (Pi * T) * (c2 / (5 * T) - 1) * (cx * q)
+    zeta2 = c2 / (2 * T)
+    j1 = -bnchi * (cx * (A + 0.6 * (zeta2 - 2.5) * B)
+                   + 0.4 * (2 * (cx * cx / (2 * T)) * D + (zeta2 - 2.5) * D))
+    wG = (cy * cy + cz * cz) / 2
+    xi = u + cx
+    he = [np.ones_like(xi), xi]
+    for l in range(1, Q):
+        he.append(xi * he[l] - l * he[l - 1])
+    out = {}
+    for name, fac in (("FS", shak), ("GS", shak * wG), ("JF", j1), ("JG", j1 * wG)):
+        out[name] = np.array([np.sum(W * fac * he[l]) for l in range(Q)])
+    return out
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=0.3, u=0.1, T=0.6, q=0.02, Pr=0.7, bnchi=0.8, A=0.3, B=-0.2, D=0.15),
+    dict(n=0.6, u=-0.2, T=0.75, q=-0.05, Pr=0.8, bnchi=2.1, A=-1.1, B=0.4, D=-0.3),
+])
+def test_reduced_equilibria_match_3d_integration(case):
+    """The oracle's reduced Shakhov and J1 terms (C3 reading) equal the
+    projections of the paper's 3D expressions integrated over p_y, p_z."""
+    Q = 16
+    o = mk(nz=4, Q=Q)
+    FS, GS, JF, JG = o.equilibria_node(**case)
+    co = _reduced_3d_coeffs(Q, **case)
+    fact = np.array([math.factorial(l) for l in range(Q)], dtype=float)
+    heK = [np.ones(Q), o.xi.copy()]
+    for l in range(1, Q):
+        heK.append(o.xi * heK[l] - l * heK[l - 1])
+    heK = np.array(heK[:Q])
+    for name, got in (("FS", FS), ("GS", GS), ("JF", JF), ("JG", JG)):
+        ref = o.w * ((co[name] / fact) @ heK)
+        scale = max(np.abs(ref).max(), 1e-3 * case["n"])
+        assert np.abs(got - ref).max() <= 1e-12 * scale, name
+
+
+def test_shakhov_heat_flux_identity():
+    """int c (c^2/2 F^S + G^S) = (1 - Pr) q, and F^S = F_MB when q = 0."""
+    o = mk(nz=4, Q=16)
+    n, u, T, q, Pr = 0.4, 0.15, 0.65, 0.03, 0.72
+    FS, GS, _, _ = o.equilibria_node(n, u, T, q=q, Pr=Pr)
+    c = o.xi - u
+    assert abs(np.sum(c * (0.5 * c * c * FS + GS)) - (1 - Pr) * q) < 1e-14
+    assert abs(np.sum(FS) - n) < 1e-14 and abs(np.sum(o.xi * FS) - n * u) < 1e-14
+    FM, GM, _, _ = o.equilibria_node(n, u, T)
+    F0, G0, _, _ = o.equilibria_node(n, u, T, q=0.0, Pr=Pr)
+    assert np.abs(F0 - FM).max() < 1e-16 and np.abs(G0 - GM).max() < 1e-16
+
+
+def test_J1_moments():
+    """Eq. (J1): zero mass moment; momentum moment -b n^2 chi T A; vanishes
+    without gradients."""
+    o = mk(nz=4, Q=16)
+    n, u, T, bnchi, A, B, D = 0.5, 0.1, 0.7, 1.3, 0.4, -0.3, 0.2
+    _, _, JF, JG = o.equilibria_node(n, u, T, bnchi=bnchi, A=A, B=B, D=D)
+    assert abs(np.sum(JF)) < 1e-15
+    c = o.xi - u
+    assert abs(np.sum(c * JF) - (-bnchi * n * T * A)) < 1e-14
+    _, _, J0F, J0G = o.equilibria_node(n, u, T, bnchi=bnchi)
+    assert np.abs(J0F).max() < 1e-16 and np.abs(J0G).max() < 1e-16
+
+
+# ---------------------------------------------------------------------------
+# velocity derivative (C5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("Q", [8, 16, 32])
+def test_dxi_on_hermite_modes(Q):
+    """d/dxi [omega He_l] = -omega He_{l+1}: for h_k = w_k He_l(xi_k) the
+    operator returns -w_k He_{l+1}(xi_k), l <= Q-2."""
+    o = mk(nz=4, Q=Q)
+    he = [np.ones(Q), o.xi.copy()]
+    for l in range(1, Q + 1):
+        he.append(o.xi * he[l] - l * he[l - 1])
+    for l in range(Q - 1):
+        got = o.dxi(o.w * he[l])
+        ref = -o.w * he[l + 1]
+        scale = np.abs(o.w * np.sqrt(float(math.factorial(l + 1)))).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale, l
+
+
+def test_dxi_moment_identities():
+    """sum dF = 0, sum xi dF = -n, sum xi^2 dF = -2 n u for any F."""
+    o = mk(nz=4, Q=16)
+    rng = np.random.Generator(np.random.PCG64(7))
+    F = o.w * (1 + 0.3 * rng.standard_normal(16))
+    dF = o.dxi(F)
+    n, j = F.sum(), (o.xi * F).sum()
+    assert abs(dF.sum()) < 1e-14
+    assert abs((o.xi * dF).sum() + n) < 1e-14
+    assert abs((o.xi ** 2 * dF).sum() + 2 * j) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# interaction kernels (Eqs. (sutherland), (force), (F1), (F2))
+# ---------------------------------------------------------------------------
+def phi_suth(r, sigma=1.0, phi=1.0, gamma=6.0):
+    return -phi * (r / sigma) ** (-gamma)
+
+
+def dphi_suth(r, sigma=1.0, phi=1.0, gamma=6.0):
+    return gamma * phi * sigma ** gamma * r ** (-gamma - 1)
+
+
+@pytest.mark.parametrize("z", [0.0, 0.3, 0.99, 1.0, 1.7, 3.2, 5.9])
+def test_force_kernel_is_plane_integral_of_eq_force(z):
+    """g(z) = int over the plane at offset z of phi'(rho) z/rho (rho > sigma),
+    i.e. the 1D reduction of Eq. (force) that Eq. (F1) states."""
+    o = mk()
+    r0 = math.sqrt(max(1.0 - z * z, 0.0))
+    val, _ = integrate.quad(lambda r: 2 * math.pi * r * dphi_suth(math.hypot(z, r)) * z / math.hypot(z, r),
+                            r0, np.inf, epsabs=1e-14, epsrel=1e-13, limit=200)
+    assert abs(o.force_kernel(z) - val) < 1e-11 * max(1, abs(val))
+    assert abs(o.force_kernel(-z) + val) < 1e-11 * max(1, abs(val))
+
+
+@pytest.mark.parametrize("z", [0.0, 0.5, 0.999, 1.3, 2.5, 6.0])
+def test_plane_potential_closed_form(z):
+    """North-star closed form: -phi pi sigma^2/2 inside, -phi pi sigma^6/(2 z^4)
+    beyond, equals the plane integral of the Sutherland tail over rho > sigma."""
+    o = mk()
+    r0 = math.sqrt(max(1.0 - z * z, 0.0))
+    val, _ = integrate.quad(lambda r: 2 * math.pi * r * phi_suth(math.hypot(z, r)), r0, np.inf,
+                            epsabs=1e-14, epsrel=1e-13, limit=200)
+    assert abs(o.plane_potential(z) - val) < 1e-11
+    closed = -math.pi / 2 if z < 1 else -math.pi / (2 * z ** 4)
+    assert abs(o.plane_potential(z) - closed) < 1e-14
+
+
+def test_uniform_pair_energy_of_plane_potential():
+    """(1/2) n^2 int Phi_pl dz = -a n^2 with a = 2 pi sigma^3 phi / 3."""
+    o = mk()
+    tot = 2 * integrate.quad(lambda z: o.plane_potential(z), 0, 1, epsabs=1e-14)[0] \
+        + 2 * integrate.quad(lambda z: o.plane_potential(z), 1, np.inf, epsabs=1e-14)[0]
+    assert abs(0.5 * tot - (-2 * math.pi / 3)) < 1e-10
+
+
+def test_first_moment_of_force_kernel_is_2a_of_eq_F2():
+    """int z g(z) dz = 2a with a = (2 pi sigma^3/3) phi gamma/(gamma-3) of
+    Eq. (F2): the gradient expansion of Eq. (F1) to first order."""
+    o = mk()
+    m = 2 * (integrate.quad(lambda z: z * o.force_kernel(z), 0, 1, epsabs=1e-14)[0]
+             + integrate.quad(lambda z: z * o.force_kernel(z), 1, np.inf, epsabs=1e-14)[0])
+    a = 2 * math.pi / 3 * 6 / 3
+    assert abs(m - 2 * a) < 1e-10
+
+
+def test_force_potential_is_antiderivative():
+    o = mk()
+    for z in [0.2, 0.7, 1.5, 3.0, 5.0]:
+        h = 1e-5
+        d = (o.force_potential(z + h) - o.force_potential(z - h)) / (2 * h)
+        assert abs(d - o.force_kernel(z)) < 1e-7
+        assert o.force_potential(z) == o.force_potential(-z)
+    assert abs(o.force_potential(1e6)) < 1e-20
+    assert abs(o.force_potential(1 - 1e-12) - o.force_potential(1 + 1e-12)) < 1e-10
+
+
+@pytest.mark.parametrize("dz", [0.25, 0.1])
+def test_linear_density_force_is_2ad_gradient(dz):
+    """For a linear density the Simpson force is exactly 2 a_d n' away from the
+    ends (outflow harness), a_d = (1/2) sum_j s_j (j dz) g(j dz)."""
+    nz = 200
+    o = mk(nz=nz, Q=8, dz=dz, bc=1)
+    M = int(round(6.0 / dz))
+    slope = 1e-3
+    n = 0.2 + slope * dz * np.arange(nz)
+    F, G = o.equilibrium(n, np.zeros(nz), np.full(nz, 0.7))
+    f = o.node_fields(F, G)
+    inner = slice(M, nz - M)
+    assert np.allclose(f["force"][inner], 2 * o.discrete_a() * slope, rtol=1e-12, atol=0)
+
+
+def test_discrete_a_converges_to_cut_integral():
+    """a_d -> a_cut = (1/2) int_{-6}^{6} z g(z) dz at the Simpson rate; without
+    the cut a_cut -> a = 4 pi/3 of Eq. (F2)."""
+    o = mk()
+    a_cut = (integrate.quad(lambda z: z * o.force_kernel(z), 0, 1, epsabs=1e-14)[0]
+             + integrate.quad(lambda z: z * o.force_kernel(z), 1, 6, epsabs=1e-14)[0])
+    e = [abs(mk(dz=dz).discrete_a() - a_cut) for dz in (0.25, 0.125, 0.0625)]
+    assert e[0] < 2e-2 and e[0] / e[1] > 12 and e[1] / e[2] > 12, e
+    assert abs(a_cut + 2 * math.pi / (3 * 6.0 ** 3) - 4 * math.pi / 3) < 1e-12
+
+
+def test_periodic_force_of_cosine():
+    """n = n0 + e cos(k z) on a periodic grid: F1 = -e sin(k z) int g(s) sin(k s) ds
+    over |s| <= rcut; the Simpson error falls at 4th order."""
+    errs = []
+    for dz in (0.25, 0.125):
+        nz = int(round(64 / dz))
+        L = nz * dz
+        o = mk(nz=nz, Q=8, dz=dz)
+        k = 2 * math.pi * 3 / L
+        z = dz * np.arange(nz)
+        n = 0.3 + 0.01 * np.cos(k * z)
+        F, G = o.equilibrium(n, np.zeros(nz), np.full(nz, 0.7))
+        f = o.node_fields(F, G)
+        Ik = 2 * (integrate.quad(lambda s: o.force_kernel(s) * math.sin(k * s), 0, 1, epsabs=1e-14)[0]
+                  + integrate.quad(lambda s: o.force_kernel(s) * math.sin(k * s), 1, 6, epsabs=1e-14)[0])
+        ref = -0.01 * np.sin(k * z) * Ik
+        errs.append(np.abs(f["force"] - ref).max() / np.abs(ref).max())
+    assert errs[0] < 5e-3 and errs[0] / errs[1] > 10, errs
+
+
+# ---------------------------------------------------------------------------
+# chi, Fischer-Methfessel average, EOS (Eqs. (carnstar), (EOSS); Sec. III.A)
+# ---------------------------------------------------------------------------
+def test_chi_two_forms_of_eq_carnstar():
+    """chi = (1/(n b)) (p_hs/(n T) - 1) = (2-eta)/(2(1-eta)^3)."""
+    o = mk()
+    b = 2 * math.pi / 3
+    for n in [0.01, 0.2, 0.5, 0.8]:
+        eta = math.pi * n / 6
+        Z = (1 + eta + eta ** 2 - eta ** 3) / (1 - eta) ** 3
+        assert abs(o.chi(n) - (Z - 1) / (n * b)) < 1e-13 * o.chi(n)
+
+
+def test_fm_average_polynomials():
+    """nbar of constant and linear n is exact; of a quadratic it is
+    z^2 + sigma^2/5 minus the composite-Simpson error of a quartic."""
+    nz, dz = 120, 0.25
+    o = mk(nz=nz, Q=8, dz=dz, bc=1)
+    z = dz * (np.arange(nz) - nz / 2)
+    inner = slice(10, nz - 10)
+    for n, ref in ((np.full(nz, 0.3), np.full(nz, 0.3)),
+                   (0.3 + 0.01 * z, 0.3 + 0.01 * z)):
+        F, G = o.equilibrium(n, np.zeros(nz), np.full(nz, 0.7))
+        assert np.allclose(o.node_fields(F, G)["nbar"][inner], ref[inner], rtol=1e-13)
+    n = 0.2 + 0.001 * z ** 2
+    F, G = o.equilibrium(n, np.zeros(nz), np.full(nz, 0.7))
+    simpson_err = 3 / 4 * (2 * dz ** 4 * 24 / 180)   # (b-a) h^4 f''''/180, f'''' = -24
+    ref = 0.2 + 0.001 * (z ** 2 + 1 / 5 - simpson_err)
+    assert np.allclose(o.node_fields(F, G)["nbar"][inner], ref[inner], rtol=1e-12)
+
+
+def test_gradient_exact_for_quartics():
+    """4th-order central differences are exact for polynomials of degree <= 4."""
+    nz, dz = 40, 0.25
+    o = mk(nz=nz, Q=8, dz=dz, bc=1)
+    z = dz * (np.arange(nz) - nz / 2)
+    u = 0.01 * z + 0.002 * z ** 2 - 0.0003 * z ** 3 + 1e-5 * z ** 4
+    du = 0.01 + 0.004 * z - 0.0009 * z ** 2 + 4e-5 * z ** 3
+    F, G = o.equilibrium(np.full(nz, 0.3), u, np.full(nz, 0.7))
+    f = o.node_fields(F, G)
+    inner = slice(2, nz - 2)
+    assert np.allclose(f["D"][inner], du[inner], rtol=0, atol=1e-13)
+
+
+def test_transport_dilute_limit_and_prandtl_identity():
+    """Eqs. (viscosity), (tau), (prandtl): Pr = c_P mu/lambda (1+3x/5)/(1+2x/5)
+    with lambda from its own formula; dilute limit mu -> mu0, Pr -> 2/3."""
+    nz = 16
+    o = mk(nz=nz, Q=8, bc=0)
+    for n0 in [1e-7, 0.1, 0.4, 0.7]:
+        T0 = 0.8
+        F, G = o.equilibrium(np.full(nz, n0), np.zeros(nz), np.full(nz, T0))
+        f = o.node_fields(F, G)
+        chi, b = f["chi"][0], 2 * math.pi / 3
+        x = b * n0 * chi
+        mu0 = 5 / 16 * math.sqrt(T0 / math.pi)
+        lam0 = 75 / 64 * math.sqrt(T0 / math.pi)
+        mu = mu0 * (1 / chi + 0.8 * b * n0 + 4 / 25 * (1 + 12 / math.pi) * (b * n0) ** 2 * chi)
+        lam = lam0 * (1 / chi + 1.2 * b * n0 + 9 / 25 * (1 + 32 / (9 * math.pi)) * (b * n0) ** 2 * chi)
+        assert abs(f["mu"][0] - mu) < 1e-13 * mu
+        assert abs(f["Pr"][0] - 2.5 * mu / lam * (1 + 0.6 * x) / (1 + 0.4 * x)) < 1e-13
+        assert abs(f["tau"][0] * n0 * T0 * (1 + 0.4 * x) - mu) < 1e-13 * mu
+        assert abs(f["rate"][0] * f["tau"][0] - 1) < 1e-14
+        if n0 < 1e-6:
+            assert abs(f["mu"][0] - mu0) < 1e-6 and abs(f["Pr"][0] - 2 / 3) < 1e-6
+
+
+def test_critical_temperature_matches_paper():
+    """With a = 4 pi/3 (Eq. (F2), gamma = 6) the CS + mean-field EOS gives the
+    paper's printed T_c ~ 0.754632 (Sec. III.A) to its printed digits."""
+    n_c, T_c = O.critical_point(4 * math.pi / 3)
+    assert abs(T_c - PV["T_c"]["value"]) < 5e-6 * PV["T_c"]["value"]
+    # the critical point is where dP/dn and d2P/dn2 vanish
+    h = 1e-5
+    P = lambda n: O.pressure(n, T_c, 4 * math.pi / 3)
+    assert abs((P(n_c + h) - P(n_c - h)) / (2 * h)) < 1e-8
+    assert abs((P(n_c + h) - 2 * P(n_c) + P(n_c - h)) / h ** 2) < 1e-4
+
+
+@pytest.mark.parametrize("r", [0.6, 0.7, 0.75, 0.8, 0.95])
+def test_maxwell_construction_equal_area(r):
+    """Coexistence: equal P, equal mu, and the equal-area rule
+    int_{n_v}^{n_l} (P - P_s)/n^2 dn = 0 by adaptive quadrature."""
+    a = 4 * math.pi / 3
+    T = r * O.critical_point(a)[1]
+    nv, nl = O.coexistence(T, a)
+    Pv, Pl = O.pressure(nv, T, a), O.pressure(nl, T, a)
+    assert abs(Pv - Pl) < 1e-12 * max(abs(Pv), 1e-3)
+    area, _ = integrate.quad(lambda n: (O.pressure(n, T, a) - Pv) / n ** 2, nv, nl,
+                             epsabs=1e-12, epsrel=1e-12, limit=500)
+    scale = integrate.quad(lambda n: abs(O.pressure(n, T, a) - Pv) / n ** 2, nv, nl, limit=500)[0]
+    assert abs(area) < 1e-9 * scale
+    # coexistence densities at fixed T/T_c do not depend on a (P/a scaling)
+    nv2, nl2 = O.coexistence(r * O.critical_point(4.19)[1], 4.19)
+    assert abs(nv2 - nv) < 1e-10 * nv and abs(nl2 - nl) < 1e-10
+
+
+def test_spinodal_claim_of_sec_IIIB():
+    """Sec. III.B: for (T_i, omega) = (0.7, 0.4), (0.65, 0.55), (0.6, 0.65) the
+    extrema of A[1 +- omega], A = (rho_l + rho_v)/2, lie outside the spinodal
+    interval.  For (0.55, 0.7) the minimum lies inside with this EOS (a
+    discrepancy recorded in the design notes)."""
+    a = 4 * math.pi / 3
+    res = []
+    for T, om in PV["phase_separation_pairs"]["value"]:
+        nv, nl = O.coexistence(T, a)
+        A = (nv + nl) / 2
+        lo, hi = O.spinodal(T, a)
+        res.append(A * (1 - om) < lo and A * (1 + om) > hi)
+    assert res == [True, True, True, False]
+
+
+# ---------------------------------------------------------------------------
+# WENO-5 (Jiang-Shu) advection (Sec. III)
+# ---------------------------------------------------------------------------
+def test_weno_exact_for_quadratic_flux():
+    """For f(x) = x^2 sampled at integer nodes every candidate stencil
+    reconstructs h(x) = x^2 - 1/12 exactly (h's cell averages are f), so the
+    face value at 2.5 is 6.25 - 1/12 whatever the weights."""
+    v = [float(j * j) for j in range(5)]
+    assert abs(O.Oracle.weno5(v) - (6.25 - 1 / 12)) < 1e-13
+
+
+def test_weno_upwinds_at_a_step():
+    """A step 0,0,0,1,1 seen from the upwind side gives a face value ~0."""
+    assert abs(O.Oracle.weno5([0, 0, 0, 1, 1])) < 1e-10
+    assert abs(O.Oracle.weno5([1, 1, 1, 0, 0]) - 1) < 1e-10
+
+
+def test_advection_exact_for_quadratics_and_mirror_symmetric():
+    nz, dz = 32, 0.1
+    o = mk(nz=nz, Q=8, dz=dz, bc=1)
+    z = dz * np.arange(nz)
+    h = 0.3 + 0.2 * z - 0.05 * z ** 2
+    for xi in (1.7, -2.3):
+        got = o.advect_row(xi, h)
+        assert np.allclose(got[3:-3], -xi * (0.2 - 0.1 * z[3:-3]), rtol=0, atol=1e-12)
+    rng = np.random.Generator(np.random.PCG64(3))
+    h = rng.uniform(0.1, 1.0, nz)
+    # mirrored data advected the other way is the mirror image of the result
+    a = o.advect_row(1.3, h)
+    b = o.advect_row(-1.3, h[::-1].copy())[::-1]
+    assert np.allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_advection_fifth_order():
+    errs = []
+    for nz in (256, 512):
+        L = 10.0
+        dz = L / nz
+        o = mk(nz=nz, Q=8, dz=dz, bc=0)
+        z = dz * np.arange(nz)
+        h = 1.0 + 0.5 * np.sin(2 * math.pi * z / L)
+        got = o.advect_row(1.0, h)
+        ref = -0.5 * 2 * math.pi / L * np.cos(2 * math.pi * z / L)
+        errs.append(np.abs(got - ref).max())
+    assert errs[0] / errs[1] > 24, errs
+
+
+# ---------------------------------------------------------------------------
+# full right-hand side and RK3 step
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("Q,bc", [(16, 0), (24, 1)])
+def test_uniform_state_is_stationary(Q, bc):
+    nz = 48
+    o = mk(nz=nz, Q=Q, bc=bc)
+    F, G = o.equilibrium(np.full(nz, 0.25), np.zeros(nz), np.full(nz, 0.55))
+    RF, RG, f = o.rhs(F, G, with_fields=True)
+    assert np.abs(RF).max() < 1e-14 * F.max() / o.s.dt
+    assert np.abs(RG).max() < 1e-14 * G.max() / o.s.dt
+    assert np.abs(f["force"]).max() < 1e-15 and np.abs(f["A"]).max() < 1e-13
+
+
+def test_uniform_mean_field_energy():
+    """E_mf = (L/2) n^2 sum_j s_j [Phi_F(j dz) - Phi_F(R)] ~ (L/2) n^2 x
+    int_{-R}^{R} (Phi_F - Phi_F(R)) = (L/2) n^2 (-8 pi/3 + 4 pi/(3 R^3)) = -a_cut n^2 L
+    within Simpson error."""
+    nz, dz = 64, 0.25
+    o = mk(nz=nz, Q=8, dz=dz)
+    n0 = 0.3
+    F, G = o.equilibrium(np.full(nz, n0), np.zeros(nz), np.full(nz, 0.6))
+    tot = o.totals(F, G)
+    L = nz * dz
+    R = 6.0
+    ref = 0.5 * L * n0 ** 2 * (-8 * math.pi / 3 + 4 * math.pi / (3 * R ** 3))
+    assert abs(tot[3] - ref) < 2e-3 * abs(ref)
+    assert abs(tot[3] + o.discrete_a() * n0 ** 2 * L) < 5e-3 * abs(ref)
+    assert abs(tot[0] - n0 * L) < 1e-13 and abs(tot[1]) < 1e-15
+    assert abs(tot[2] - tot[3] - 1.5 * n0 * 0.6 * L) < 1e-12
+
+
+def test_mass_and_momentum_conserved_periodic():
+    """Flux-form advection, odd force kernel with symmetric taps, projected
+    Shakhov equilibria and the telescoping J1 momentum source conserve mass
+    and momentum to rounding on a periodic grid."""
+    nz = 64
+    o = mk(nz=nz, Q=16, bc=0)
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 0.25 * (1 + 0.05 * rng.uniform(-1, 1, nz))
+    u = 0.02 * rng.uniform(-1, 1, nz)
+    T = 0.55 * (1 + 0.02 * rng.uniform(-1, 1, nz))
+    F, G = o.equilibrium(n, u, T)
+    t0 = o.totals(F, G)
+    F2, G2 = o.step(F, G, 5)
+    t1 = o.totals(F2, G2)
+    assert abs(t1[0] - t0[0]) < 1e-13 * t0[0]
+    assert abs(t1[1] - t0[1]) < 1e-14 * t0[0]
+
+
+def test_energy_drift_falls_under_refinement():
+    """Total energy (kinetic + internal + E_mf) is conserved to truncation
+    order only: over a fixed time its drift falls by > 8x per halving of dz
+    (dt proportional to dz)."""
+    L, drift = 16.0, []
+    for nz in (64, 128, 256):
+        dz = L / nz
+        xi, _ = O.gauss_hermite(16)
+        nsteps = int(round(0.2 / (0.5 * dz / np.abs(xi).max())))
+        o = mk(nz=nz, Q=16, dz=dz, dt=0.2 / nsteps)
+        z = dz * np.arange(nz)
+        n = 0.25 * (1 + 0.05 * np.cos(2 * np.pi * z / L))
+        u = 0.02 * np.sin(2 * np.pi * z / L)
+        T = 0.55 * (1 + 0.02 * np.cos(4 * np.pi * z / L))
+        F, G = o.equilibrium(n, u, T)
+        t0 = o.totals(F, G)
+        t1 = o.totals(*o.step(F, G, nsteps))
+        drift.append(abs(t1[2] - t0[2]))
+    assert drift[0] / drift[1] > 8 and drift[1] / drift[2] > 8, drift
+
+
+def test_rk3_is_shu_osher_on_linear_decay():
+    """With a uniform state perturbed only in its non-equilibrium part the RHS
+    is pure relaxation; check the RK3 combination on the local ODE by
+    comparing one step with three explicit stages built from rhs()."""
+    nz = 16
+    o = mk(nz=nz, Q=8, bc=0)
+    rng = np.random.Generator(np.random.PCG64(5))
+    F, G = o.equilibrium(np.full(nz, 0.3), np.zeros(nz), np.full(nz, 0.6))
+    F = F * (1 + 0.01 * rng.standard_normal(F.shape))
+    dt = o.s.dt
+    R = lambda f, g: o.rhs(f, g)
+    RF, RG = R(F, G)
+    F1, G1 = F + dt * RF, G + dt * RG
+    RF, RG = R(F1, G1)
+    F2, G2 = 0.75 * F + 0.25 * (F1 + dt * RF), 0.75 * G + 0.25 * (G1 + dt * RG)
+    RF, RG = R(F2, G2)
+    F3, G3 = F / 3 + 2 / 3 * (F2 + dt * RF), G / 3 + 2 / 3 * (G2 + dt * RG)
+    Fs, Gs = o.step(F, G, 1)
+    assert np.abs(Fs - F3).max() < 1e-15 and np.abs(Gs - G3).max() < 1e-15
