@@ -1,0 +1,308 @@
+"""Benchmark of the EV-FDLB time step on GB300.
+
+Workload (one "step" = one Shu-Osher RK3 time step, i.e. all of the hot path
+over the whole slab): 1D liquid-slab evaporation, Nz = 4096 nodes,
+dz = 0.1 sigma, Q = 32 Gauss-Hermite velocities, outflow ends, a centred
+liquid slab 20 sigma thick at the coexistence densities of T = 0.8 T_c with
+tanh interfaces of width 2 sigma, FP64.  Metric: GNVUPS = nodes x velocities
+x steps / s / 1e9 (F and G together count as one velocity).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank advances its own copy of the slab (replicas;
+weak scaling) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NZ, Q, DZ, T_RATIO, SLAB, WIDTH = 4096, 32, 0.1, 0.8, 20.0, 2.0
+WORKLOAD = (f"1D liquid-slab evaporation: Nz={NZ}, dz={DZ} sigma, Q={Q}, outflow ends, "
+            f"{SLAB:g}-sigma liquid slab at coexistence, T={T_RATIO} T_c, tanh width {WIDTH:g} sigma, FP64")
+METRIC = "GNVUPS (node x velocity updates/s)"
+UNIT = "GNVUPS"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def stage_flops(Q: int, M: int, m: int) -> float:
+    """Algorithmic FP64 flops of one stage-kernel launch per node (FMA = 2,
+    division = 1), from the operation counts of the method:
+      per node and distribution, per velocity: Hermite analysis 2(Q-1),
+      synthesis 2Q, one WENO-5 face 65, advective difference, relaxation and
+      RK combine 10, moment sums 6;
+      per node: two coefficient recurrences 2 * 14 Q, force taps 2(2M+1),
+      Fischer-Methfessel taps 2(2m+1), gradients, transport and heat flux 100."""
+    per_vel = 2 * (Q - 1) + 2 * Q + 65 + 10 + 6
+    per_node = 2 * 14 * Q + 2 * (2 * M + 1) + 2 * (2 * m + 1) + 100
+    return 2 * Q * per_vel + per_node
+
+
+def fp64_peak_gflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP64 FMA rate of GB300: 2 FP64 FMA per clock per SM (4 flops)."""
+    return sms * 4 * sm_mhz * 1e6 / 1e9
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons in the background."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[3 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def build_workload(ev, W):
+    p = ev.Params(nx=NZ, dx=DZ, Q=Q, bc=ev.BC_OUTFLOW)
+    T = T_RATIO * ev.critical_T(p)
+    nv, nl = ev.coexistence(p, T)
+    n0 = W.liquid_slab(NZ, DZ, nl, nv, thickness=SLAB, width=WIDTH)
+    return p, T, n0
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2503_15187_gb300 as ev
+    from paper_2503_15187_gb300 import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    p, T, n0 = build_workload(ev, W)
+    stream = torch.cuda.current_stream()
+    sim = ev.Sim(p, stream=stream)
+    sim.init(n0, np.zeros(NZ), np.full(NZ, T))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    sim.step(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))             # evict the slab from L2 (untimed)
+            starts[i].record(stream)
+            sim.step_async(1)
+            ends[i].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    sim.step(0)                               # reads the device error word
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_total = sum(ms_steps)
+
+    # end-to-end through the public API with pinned host buffers: per step the
+    # state goes host -> device, one step runs, the moments come back.
+    Fh = torch.empty(sim.NF, dtype=torch.float64, pin_memory=True).numpy()
+    Gh = torch.empty(sim.NF, dtype=torch.float64, pin_memory=True).numpy()
+    sim.get_state(Fh, Gh)
+    outs = [torch.empty(NZ, dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+    tot = torch.empty(4, dtype=torch.float64, pin_memory=True).numpy()
+    import ctypes
+    L = ev.lib()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        ev._check(L.evfdlb_set_state(sim.h, Fh.ctypes.data, Gh.ctypes.data, 0), "set_state")
+        ev._check(L.evfdlb_step(sim.h, 1), "step")
+        ev._check(L.evfdlb_moments(sim.h, *[o.ctypes.data for o in outs], tot.ctypes.data, 0), "moments")
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    h2d = 2 * sim.NF * 8
+    d2h = 4 * NZ * 8 + 4 * 8
+
+    # reduce: max time over ranks
+    def maxred(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_total = maxred(ms_total)
+    e2e_ms = maxred(e2e_ms)
+    nvu = NZ * Q * args.steps * world
+    value = nvu / (ms_total * 1e-3) / 1e9
+    e2e = nvu / (e2e_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    sd = [ev.lib()]  # keep the library loaded until here
+    del sd
+    M, m = int(round(6.0 / DZ)), int(round(1.0 / DZ))
+    launch_ms = (ms_total / args.steps) / 3.0      # three stage launches per step, back to back
+    flops = stage_flops(Q, M, m) * NZ
+    achieved = flops / (launch_ms * 1e-3) / 1e9
+    peak = fp64_peak_gflops(2070.0)
+    hbm_bytes = 128 * NZ * Q                       # 8 array passes x 2 distributions x 8 B per NVU-step
+    hbm = hbm_bytes / (ms_total / args.steps * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": NZ, "velocities": Q, "steps_timed": args.steps,
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+                   "parallelism": f"replicas x{world}", "tile_nodes": sim.tile_nodes()},
+        "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GFLOP/s", "frac": achieved / peak,
+                     "peak_note": "FP64 FMA: 152 SMs x 2 FMA/clk x 2070 MHz (derived)",
+                     "flops_per_launch": flops, "launch_ms": launch_ms, "traffic": None},
+        "hbm": {"algorithmic_GBps": hbm, "frac_of_measured": hbm / hbm_peak},
+        "clocks": clocks,
+        "gpu_launches": sim.launches_per_step() * args.steps,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms / args.steps},
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
+    sim.close()
+    return line
+
+
+def cpu_baseline(budget_s, T, n0, max_steps=10**9):
+    """Times the FP64 oracle as it stands on one host core on a bounded sample
+    of the same workload (whole slab, as many steps as fit in budget_s)."""
+    import numpy as np
+    import oracle as O
+    xi, _ = O.gauss_hermite(Q)
+    dt = 0.5 * DZ / np.abs(xi).max()
+    orc = O.Oracle(O.Setup(nz=NZ, Q=Q, dz=DZ, dt=dt, bc=1))
+    F, G = orc.equilibrium(n0, np.zeros(NZ), np.full(NZ, T))
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        F, G = orc.step(F, G, 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": NZ * Q * steps / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full time steps of the {NZ}x{Q} slab ({el:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step one full oracle time step."""
+    import numpy as np
+    import oracle as O
+    p_T = None
+    xi, _ = O.gauss_hermite(Q)
+    dt = 0.5 * DZ / np.abs(xi).max()
+    orc = O.Oracle(O.Setup(nz=NZ, Q=Q, dz=DZ, dt=dt, bc=1))
+    T = T_RATIO * orc.critical_T()
+    nv, nl = O.coexistence(T, orc.discrete_a())
+    from paper_2503_15187_gb300 import workloads as W
+    n0 = W.liquid_slab(NZ, DZ, nl, nv, thickness=SLAB, width=WIDTH)
+    F, G = orc.equilibrium(n0, np.zeros(NZ), np.full(NZ, T))
+    F, G = orc.step(F, G, args.warmup)
+    t0 = time.perf_counter()
+    F, G = orc.step(F, G, args.steps)
+    el = time.perf_counter() - t0
+    v = NZ * Q * args.steps / el / 1e9
+    del p_T
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nodes": NZ, "velocities": Q},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full time steps of the {NZ}x{Q} slab, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    from paper_2503_15187_gb300.buildlib import build
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * evfdlb.h -- C ABI of libevfdlb, a GB300 (sm_103a) implementation of the
+ * time step of the Enskog-Vlasov finite-difference lattice Boltzmann model
+ * (EV-FDLB, EV1 force) of Busuioc & Sofonea, "Thermal Enskog-Vlasov Lattice
+ * Boltzmann model with phase separation", arXiv:2503.15187.
+ *
+ * The model (paper Sec. II-III): a fluid of hard spheres of diameter sigma
+ * with a Sutherland attractive tail -phi_a (r/sigma)^-gamma, Eq. (sutherland),
+ * homogeneous across the slab, described by the reduced distributions
+ *   F(z, xi) = int f dp_y dp_z,   G(z, xi) = int f (p_y^2 + p_z^2)/2 dp_y dp_z
+ * on the full-range Gauss-Hermite velocity set xi_k (k < Q) and a uniform grid
+ * z_i = i dx (i < nx).  One time step is the third-order TVD Runge-Kutta
+ * scheme of Shu and Osher applied to
+ *   dF/dt = -xi dF/dz - F1[n] dF/dxi - nu (F - F^S) + J1_F      (Eqs. (ev1),
+ *   dG/dt = -xi dG/dz - F1[n] dG/dxi - nu (G - G^S) + J1_G       (enskog_approx))
+ * with WENO-5 advection, the Simpson-integrated self-consistent force of
+ * Eq. (F1), the Shakhov equilibrium and the simplified Enskog term J1 of
+ * Sec. II.B evaluated with chi at the Fischer-Methfessel average density,
+ * and the transport coefficients of Eqs. (viscosity), (tau), (prandtl).
+ * Units are the reduced units of Sec. III (m = k_B = 1).
+ *
+ * Conventions for every entry point
+ *  - Returns an evfdlb_status; nothing else crosses the ABI (no exceptions,
+ *    no aborts).  A device-side error (non-finite value, n <= 0, T <= 0) is
+ *    latched by the kernels and reported by the next call that synchronises
+ *    (step, moments, get_state, rhs, fields); the context then refuses to step
+ *    (EVFDLB_E_STATE) until init or set_state is called again.
+ *  - Array arguments are borrowed for the duration of the call only.  With
+ *    on_device = 0 they are host pointers (any host memory); with
+ *    on_device = 1 they are device pointers on the context's device, read or
+ *    written in order on the context's stream.  Calls that return data to
+ *    host memory synchronise the stream before returning.
+ *  - Distributions are laid out velocity-major: F[k * nx + i] (k < Q, i < nx),
+ *    float64; for a batch, slab s occupies Q_s * nx_s consecutive entries in
+ *    slab order.  Per-node arrays are [nx] per slab, concatenated.
+ *  - A context is bound to one CUDA stream and is not thread-safe.
+ */
+#ifndef EVFDLB_H
+#define EVFDLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evfdlb_ctx evfdlb_ctx;
+
+typedef enum {
+    EVFDLB_OK = 0,
+    EVFDLB_E_INVALID_ARG = -1, /* a parameter or pointer fails validation       */
+    EVFDLB_E_CUDA = -2,        /* a CUDA runtime call failed                     */
+    EVFDLB_E_OOM = -3,         /* device allocation failed                       */
+    EVFDLB_E_NONFINITE = -4,   /* a kernel met a NaN/Inf in the state            */
+    EVFDLB_E_NEGATIVE = -5,    /* a kernel met n <= 0 or T <= 0                  */
+    EVFDLB_E_TIMEOUT = -6,     /* a bounded device wait ran out                  */
+    EVFDLB_E_STATE = -7,       /* call out of order (e.g. step before init)      */
+    EVFDLB_E_UNSUPPORTED = -8  /* valid request this build does not implement    */
+} evfdlb_status;
+
+enum { EVFDLB_BC_PERIODIC = 0, EVFDLB_BC_OUTFLOW = 1 };
+enum { EVFDLB_FP64 = 0, EVFDLB_FP32 = 1 };
+enum { EVFDLB_EV1 = 0, EVFDLB_EV2 = 1 };
+/* Relaxation rate of the Shakhov term J0 (Sec. II.B).  The paper writes
+ * J0 = -(chi/tau)(f - f^S) with tau of Eq. (tau); the Chapman-Enskog
+ * argument that fixes Eq. (tau) reproduces the Enskog viscosity only with
+ * rate 1/tau.  Both readings are selectable; 1/tau is the default. */
+enum { EVFDLB_RELAX_INV_TAU = 0, EVFDLB_RELAX_CHI_OVER_TAU = 1 };
+
+/* Problem statement of one slab (paper Sec. III: sigma = phi_a = 1, gamma = 6). */
+typedef struct {
+    int32_t dim;          /* 1 (one-dimensional slab)                                  */
+    int32_t nx;           /* grid nodes, >= 8                                          */
+    int32_t ny;           /* 1                                                         */
+    double  dx;           /* grid spacing; sigma/dx and r_cut/dx must be integers and  */
+                          /* (r_cut - sigma)/dx even (Simpson panels end at +-sigma)   */
+    double  sigma;        /* hard-sphere diameter, Eq. (sutherland)                    */
+    double  phi_a;        /* depth of the attractive tail, Eq. (sutherland)            */
+    double  gamma;        /* tail exponent (> 3), Eq. (sutherland)                     */
+    double  r_cut;        /* truncation radius of the Eq. (F1) integral (>= sigma + 2dx)*/
+    int32_t Q;            /* Gauss-Hermite order, 4 <= Q <= 32                         */
+    int32_t bc;           /* EVFDLB_BC_PERIODIC or EVFDLB_BC_OUTFLOW                   */
+    int32_t precision;    /* EVFDLB_FP64 (FP32 reserved: returns E_UNSUPPORTED)        */
+    int32_t force_model;  /* EVFDLB_EV1 (EV2 reserved: returns E_UNSUPPORTED)          */
+    int32_t relax_mode;   /* EVFDLB_RELAX_INV_TAU or EVFDLB_RELAX_CHI_OVER_TAU         */
+    double  dt;           /* > 0: time step; <= 0: dt = cfl * dx / max|xi_k|           */
+    double  cfl;          /* used when dt <= 0; 0 < cfl <= 1                           */
+    int32_t ckpt_every;   /* checkpoint interval of the adjoint (reserved; 0 = none)   */
+    double  weno_eps;     /* WENO-5 smoothness regulariser (> 0), e.g. 1e-6            */
+} evfdlb_params;
+
+/* Fills p with the defaults of Sec. III: dim 1, sigma = phi_a = 1, gamma = 6,
+ * r_cut = 6, Q = 16, periodic, FP64, EV1, rate 1/tau, cfl 0.5, weno_eps 1e-6.
+ * nx and dx are left for the caller (set to 0). */
+void evfdlb_default_params(evfdlb_params* p);
+
+/* Creates a context for nbatch >= 1 independent slabs.  With nbatch == 1 the
+ * slab is *p and per_slab may be NULL; with nbatch > 1, per_slab[s] gives slab
+ * s (p may be NULL) and all slabs advance together in evfdlb_step.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream).  The
+ * context owns all device memory it uses.  On success *out is set; on failure
+ * *out is NULL and nothing is leaked.
+ * Errors: E_INVALID_ARG (validation, see evfdlb_params), E_UNSUPPORTED,
+ * E_OOM, E_CUDA. */
+evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch,
+                            const evfdlb_params* per_slab, void* cuda_stream,
+                            evfdlb_ctx** out);
+
+/* Sets the state to the Hermite-projected Maxwellian pair (F_MB, T F_MB) of
+ * the fields n0 > 0, u0, T0 > 0 ([sum nx], slab order).  Errors:
+ * E_INVALID_ARG (NULL pointer), E_NONFINITE / E_NEGATIVE (checked on the
+ * device), E_CUDA. */
+evfdlb_status evfdlb_init(evfdlb_ctx* ctx, const double* n0, const double* u0,
+                          const double* T0, int32_t on_device);
+
+/* Advances every slab by nsteps >= 0 Shu-Osher RK3 steps (3 right-hand-side
+ * evaluations each).  Work is queued on the context's stream as CUDA graphs;
+ * the call synchronises once at the end to read the device error word.
+ * Errors: E_STATE (no valid state), E_NONFINITE, E_NEGATIVE, E_CUDA. */
+evfdlb_status evfdlb_step(evfdlb_ctx* ctx, int64_t nsteps);
+
+/* Queues nsteps steps without synchronising and without reading the error
+ * word (for timing and for callers that overlap work); a later synchronising
+ * call reports any latched device error. */
+evfdlb_status evfdlb_step_async(evfdlb_ctx* ctx, int64_t nsteps);
+
+/* Macroscopic fields of the current state (Sec. II.B): n, u, T and heat flux
+ * q per node ([sum nx] each; any may be NULL) and, if totals != NULL, per
+ * slab four totals {mass, momentum, energy incl. mean-field energy, mean-field
+ * energy} ([4 * nbatch], always host memory).  Mean-field energy:
+ * (dx/2) sum_i n_i sum_j s_j [Phi(j dx) - Phi(r_cut)] n_{i+j} with Phi the even
+ * potential whose derivative is the Eq. (F1) kernel and s_j Simpson weights. */
+evfdlb_status evfdlb_moments(evfdlb_ctx* ctx, double* n, double* u, double* T,
+                             double* q, double* totals, int32_t on_device);
+
+/* Copies the state (F, G; [sum Q nx] each, layout above) out of / into the
+ * context.  set_state also clears a latched device error. */
+evfdlb_status evfdlb_get_state(evfdlb_ctx* ctx, double* F, double* G, int32_t on_device);
+evfdlb_status evfdlb_set_state(evfdlb_ctx* ctx, const double* F, const double* G,
+                               int32_t on_device);
+
+/* One evaluation of the right-hand side L(F, G) of Eq. (ev1) at the current
+ * state, written to RF, RG (layout of the state).  Diagnostic; the state is
+ * not changed. */
+evfdlb_status evfdlb_rhs(evfdlb_ctx* ctx, double* RF, double* RG, int32_t on_device);
+
+/* Node fields of one right-hand-side evaluation at the current state, as
+ * [EVFDLB_NFIELDS][sum nx]: n, u, T, q, nbar (Fischer-Methfessel average,
+ * Sec. II.A), chi (Eq. (carnstar) at nbar), F1 (Eq. (F1)), mu (Eq. (viscosity)),
+ * tau (Eq. (tau)), Pr (Eq. (prandtl)), nu (relaxation rate), A = d ln(n^2 chi T)/dz,
+ * B = d ln T/dz, D = du/dz (Eq. (J1)), X = n^2 chi T, b n chi. */
+#define EVFDLB_NFIELDS 16
+evfdlb_status evfdlb_fields(evfdlb_ctx* ctx, double* fields, int32_t on_device);
+
+/* Number of slabs, and the nodes / velocity order / time step of slab s. */
+evfdlb_status evfdlb_slab_info(const evfdlb_ctx* ctx, int32_t s, int32_t* nx,
+                               int32_t* Q, double* dt);
+
+/* Number of the library's own kernel launches queued per time step (all
+ * slabs), for launch accounting. */
+int32_t evfdlb_launches_per_step(const evfdlb_ctx* ctx);
+
+/* Node tile of the work decomposition: each CTA of a stage kernel advances
+ * all velocities of tile_nodes consecutive nodes of one slab (1..64).  The
+ * context picks one wave of CTAs over the SMs by default; evfdlb_tune
+ * re-partitions (and re-captures the step graphs), e.g. for an autotuner.
+ * Synchronises the stream.  Errors: E_INVALID_ARG, E_CUDA. */
+evfdlb_status evfdlb_tune(evfdlb_ctx* ctx, int32_t tile_nodes);
+int32_t evfdlb_tile_nodes(const evfdlb_ctx* ctx);
+
+/* Releases the context and its device memory (NULL is a no-op). */
+void evfdlb_destroy(evfdlb_ctx* ctx);
+
+/* Static description of a status code. */
+const char* evfdlb_status_string(evfdlb_status s);
+
+/* Host-side model constants (no GPU needed).
+ *  evfdlb_discrete_a: a_d = (1/2) sum_j s_j (j dx) g(j dx), the constant the
+ *    Simpson-integrated Eq. (F1) force gives for a linear density (F1 = 2 a_d dn/dz);
+ *  evfdlb_critical_T: critical temperature of Eq. (EOSS) with a = a_d
+ *    (Carnahan-Starling repulsion, mean-field attraction);
+ *  evfdlb_coexistence: Maxwell construction (Sec. III.A) at temperature T:
+ *    vapour and liquid densities with equal pressure and chemical potential.
+ * All return NaN / E_INVALID_ARG on invalid parameters. */
+double evfdlb_discrete_a(const evfdlb_params* p);
+double evfdlb_critical_T(const evfdlb_params* p);
+evfdlb_status evfdlb_coexistence(const evfdlb_params* p, double T, double* n_vapour,
+                                 double* n_liquid);
+
+/* Full-range Gauss-Hermite velocity set of order Q (4 <= Q <= 64): roots of
+ * the probabilists' He_Q and weights summing to 1, ascending. */
+evfdlb_status evfdlb_velocity_set(int32_t Q, double* xi, double* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVFDLB_H */

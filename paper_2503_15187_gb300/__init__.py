@@ -1,0 +1,264 @@
+"""GB300 (sm_103a) EV-FDLB time step: thin Python binding of libevfdlb.
+
+Every step of the model runs in the CUDA library (``csrc/``, C ABI in
+``include/evfdlb.h``); this module only marshals arguments.  There is no CPU
+fallback: if the library is not built, or no CUDA device is present, the
+calls raise.
+
+Paper: Busuioc & Sofonea, "Thermal Enskog-Vlasov Lattice Boltzmann model
+with phase separation", arXiv:2503.15187.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields as dc_fields
+
+import numpy as np
+
+from .buildlib import LIB as LIB_PATH, build  # noqa: F401
+
+EVFDLB_NFIELDS = 16
+FIELD_NAMES = ("n", "u", "T", "q", "nbar", "chi", "force", "mu", "tau", "Pr",
+               "nu", "A", "B", "D", "X", "bnchi")
+
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+FP64, FP32 = 0, 1
+EV1, EV2 = 0, 1
+RELAX_INV_TAU, RELAX_CHI_OVER_TAU = 0, 1
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "out of device memory",
+          -4: "non-finite value in the state", -5: "non-positive density or temperature",
+          -6: "bounded device wait timed out", -7: "call out of order", -8: "not supported"}
+
+
+class EvfdlbError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+
+
+class CParams(ctypes.Structure):
+    """Mirror of evfdlb_params (include/evfdlb.h)."""
+    _fields_ = [("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("sigma", ctypes.c_double), ("phi_a", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("r_cut", ctypes.c_double), ("Q", ctypes.c_int32),
+                ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("force_model", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("cfl", ctypes.c_double), ("ckpt_every", ctypes.c_int32),
+                ("weno_eps", ctypes.c_double)]
+
+
+@dataclass
+class Params:
+    """Python view of evfdlb_params with the defaults of the paper's Sec. III."""
+    nx: int
+    dx: float
+    Q: int = 16
+    bc: int = BC_PERIODIC
+    sigma: float = 1.0
+    phi_a: float = 1.0
+    gamma: float = 6.0
+    r_cut: float = 6.0
+    precision: int = FP64
+    force_model: int = EV1
+    relax_mode: int = RELAX_INV_TAU
+    dt: float = 0.0
+    cfl: float = 0.5
+    ckpt_every: int = 0
+    weno_eps: float = 1e-6
+    dim: int = 1
+    ny: int = 1
+
+    def c(self) -> CParams:
+        return CParams(**{f.name: getattr(self, f.name) for f in dc_fields(self)})
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libevfdlb (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libevfdlb is not built ({LIB_PATH}); call "
+                               "paper_2503_15187_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(CParams)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "evfdlb_default_params": (None, [P]),
+            "evfdlb_create": (i32, [P, i32, P, vp, ctypes.POINTER(vp)]),
+            "evfdlb_init": (i32, [vp, vp, vp, vp, i32]),
+            "evfdlb_step": (i32, [vp, i64]),
+            "evfdlb_step_async": (i32, [vp, i64]),
+            "evfdlb_moments": (i32, [vp, vp, vp, vp, vp, vp, i32]),
+            "evfdlb_get_state": (i32, [vp, vp, vp, i32]),
+            "evfdlb_set_state": (i32, [vp, vp, vp, i32]),
+            "evfdlb_rhs": (i32, [vp, vp, vp, i32]),
+            "evfdlb_fields": (i32, [vp, vp, i32]),
+            "evfdlb_slab_info": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(d)]),
+            "evfdlb_launches_per_step": (i32, [vp]),
+            "evfdlb_tune": (i32, [vp, i32]),
+            "evfdlb_tile_nodes": (i32, [vp]),
+            "evfdlb_destroy": (None, [vp]),
+            "evfdlb_status_string": (ctypes.c_char_p, [i32]),
+            "evfdlb_discrete_a": (d, [P]),
+            "evfdlb_critical_T": (d, [P]),
+            "evfdlb_coexistence": (i32, [P, d, ctypes.POINTER(d), ctypes.POINTER(d)]),
+            "evfdlb_velocity_set": (i32, [i32, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise EvfdlbError(code, where)
+
+
+def _host(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(x):
+    """(pointer, on_device) for a numpy array or a CUDA torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, 0
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+            raise ValueError("device arrays must be contiguous float64 tensors")
+        return x.data_ptr(), 1
+    raise TypeError("expected a numpy array or a CUDA float64 tensor")
+
+
+# ---------------------------------------------------------------------------
+# host-side model constants
+# ---------------------------------------------------------------------------
+def velocity_set(Q: int):
+    xi, w = np.empty(Q), np.empty(Q)
+    _check(lib().evfdlb_velocity_set(Q, xi.ctypes.data, w.ctypes.data), "evfdlb_velocity_set")
+    return xi, w
+
+
+def discrete_a(p: Params) -> float:
+    return lib().evfdlb_discrete_a(ctypes.byref(p.c()))
+
+
+def critical_T(p: Params) -> float:
+    return lib().evfdlb_critical_T(ctypes.byref(p.c()))
+
+
+def coexistence(p: Params, T: float):
+    nv, nl = ctypes.c_double(), ctypes.c_double()
+    _check(lib().evfdlb_coexistence(ctypes.byref(p.c()), T, ctypes.byref(nv), ctypes.byref(nl)),
+           "evfdlb_coexistence")
+    return nv.value, nl.value
+
+
+# ---------------------------------------------------------------------------
+# simulation context
+# ---------------------------------------------------------------------------
+class Sim:
+    """One evfdlb context: nbatch independent slabs advanced together.
+
+    ``stream`` is a torch.cuda.Stream (or None for torch's current stream)."""
+
+    def __init__(self, params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the EV-FDLB library runs on the GPU only")
+        plist = list(params) if isinstance(params, (list, tuple)) else [params]
+        self.params = plist
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (CParams * len(plist))(*[p.c() for p in plist])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        _check(lib().evfdlb_create(None, len(plist), arr, ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.byref(h)), "evfdlb_create")
+        self.h = h
+        self.nx = [p.nx for p in plist]
+        self.Q = [p.Q for p in plist]
+        self.NN = sum(self.nx)
+        self.NF = sum(p.nx * p.Q for p in plist)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().evfdlb_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def dt(self, s=0):
+        nx, Q, dt = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().evfdlb_slab_info(self.h, s, ctypes.byref(nx), ctypes.byref(Q), ctypes.byref(dt)),
+               "evfdlb_slab_info")
+        return dt.value
+
+    def launches_per_step(self):
+        return lib().evfdlb_launches_per_step(self.h)
+
+    def tune(self, tile_nodes):
+        _check(lib().evfdlb_tune(self.h, int(tile_nodes)), "evfdlb_tune")
+
+    def tile_nodes(self):
+        return lib().evfdlb_tile_nodes(self.h)
+
+    def init(self, n0, u0, T0):
+        if isinstance(n0, np.ndarray) or not hasattr(n0, "data_ptr"):
+            n0, u0, T0 = (_host(a, self.NN) for a in (n0, u0, T0))
+        (pn, dev), (pu, _), (pT, _) = _ptr(n0), _ptr(u0), _ptr(T0)
+        _check(lib().evfdlb_init(self.h, pn, pu, pT, dev), "evfdlb_init")
+
+    def step(self, nsteps=1):
+        _check(lib().evfdlb_step(self.h, int(nsteps)), "evfdlb_step")
+
+    def step_async(self, nsteps=1):
+        _check(lib().evfdlb_step_async(self.h, int(nsteps)), "evfdlb_step_async")
+
+    def get_state(self, F=None, G=None):
+        if F is None:
+            F, G = np.empty(self.NF), np.empty(self.NF)
+        (pF, dev), (pG, _) = _ptr(F), _ptr(G)
+        _check(lib().evfdlb_get_state(self.h, pF, pG, dev), "evfdlb_get_state")
+        return F, G
+
+    def set_state(self, F, G):
+        if isinstance(F, np.ndarray) or not hasattr(F, "data_ptr"):
+            F, G = _host(F, self.NF), _host(G, self.NF)
+        (pF, dev), (pG, _) = _ptr(F), _ptr(G)
+        _check(lib().evfdlb_set_state(self.h, pF, pG, dev), "evfdlb_set_state")
+
+    def rhs(self):
+        RF, RG = np.empty(self.NF), np.empty(self.NF)
+        _check(lib().evfdlb_rhs(self.h, RF.ctypes.data, RG.ctypes.data, 0), "evfdlb_rhs")
+        return RF, RG
+
+    def fields(self):
+        out = np.empty((EVFDLB_NFIELDS, self.NN))
+        _check(lib().evfdlb_fields(self.h, out.ctypes.data, 0), "evfdlb_fields")
+        return {k: out[i] for i, k in enumerate(FIELD_NAMES)}
+
+    def moments(self, with_totals=True):
+        n, u, T, q = (np.empty(self.NN) for _ in range(4))
+        tot = np.empty(4 * len(self.params)) if with_totals else None
+        _check(lib().evfdlb_moments(self.h, n.ctypes.data, u.ctypes.data, T.ctypes.data, q.ctypes.data,
+                                    tot.ctypes.data if tot is not None else None, 0), "evfdlb_moments")
+        return n, u, T, q, (tot.reshape(-1, 4) if tot is not None else None)
+
+    # helpers for one slab --------------------------------------------------
+    def state_2d(self, s=0):
+        """(F, G) of slab s as (Q, nx) arrays."""
+        F, G = self.get_state()
+        off = sum(self.nx[i] * self.Q[i] for i in range(s))
+        n = self.nx[s] * self.Q[s]
+        return (F[off:off + n].reshape(self.Q[s], self.nx[s]),
+                G[off:off + n].reshape(self.Q[s], self.nx[s]))

@@ -1,0 +1,490 @@
+// evfdlb_api.cu -- the C ABI of libevfdlb (see include/evfdlb.h): context
+// set-up, device buffers, CUDA-graph capture of the time step, transfers and
+// error reporting.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "evfdlb_internal.h"
+
+namespace evfdlb {
+size_t stage_smem_bytes(int Q, int Z, int M);
+cudaError_t configure_kernels(size_t smem_bytes);
+void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                  const double* tables, const double* taps, const double* src, const double* base,
+                  double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
+                  double alpha, double beta, int mode, int Z, unsigned* err);
+void launch_init(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                 const double* tables, const double* n0, const double* u0, const double* T0,
+                 double* state, double* mom, long long NF, long long NN, int Z, unsigned* err);
+void launch_sums(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                 const double* tables, const double* state, double* mom, long long NF, long long NN,
+                 unsigned* err);
+void launch_fields(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                   const double* tables, const double* taps, const double* mom, double* fields,
+                   long long NN, int Z, unsigned* err);
+void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
+                    double* q);
+void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
+                   long long NN, double* out);
+}  // namespace evfdlb
+
+using namespace evfdlb;
+
+struct evfdlb_ctx {
+    int nbatch = 0;
+    std::vector<evfdlb_params> params;
+    std::vector<SlabDesc> slabs_h;
+    std::vector<WorkItem> items_h;
+    long long NF = 0;           // elements of F (= of G) over all slabs
+    long long NN = 0;           // nodes over all slabs
+    int Z = 1;                  // node tile of the work items
+    size_t smem = 0;
+    int device = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    double* state[3] = {nullptr, nullptr, nullptr};  // each [2][NF]: F then G
+    double* mom[3] = {nullptr, nullptr, nullptr};    // each [6][NN]
+    double* tables = nullptr;
+    double* taps = nullptr;
+    double* scratch = nullptr;   // [2 NF + 16 NN + 4 nbatch]
+    SlabDesc* slabs = nullptr;
+    WorkItem* items = nullptr;
+    unsigned* err = nullptr;
+    cudaGraphExec_t g_chunk = nullptr;
+    cudaGraphExec_t g_one = nullptr;
+    int chunk = 16;
+    int Qmax = 0, Mmax = 0;
+    size_t items_cap = 0;        // capacity of the device work list
+    bool have_state = false;
+    bool poisoned = false;
+};
+
+namespace {
+
+evfdlb_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return EVFDLB_OK;
+    if (e == cudaErrorMemoryAllocation) return EVFDLB_E_OOM;
+    return EVFDLB_E_CUDA;
+}
+
+#define TRY_CUDA(x)                                  \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+void free_ctx(evfdlb_ctx* c) {
+    if (!c) return;
+    if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
+    if (c->g_one) cudaGraphExecDestroy(c->g_one);
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(c->state[i]);
+        cudaFree(c->mom[i]);
+    }
+    cudaFree(c->tables);
+    cudaFree(c->taps);
+    cudaFree(c->scratch);
+    cudaFree(c->slabs);
+    cudaFree(c->items);
+    cudaFree(c->err);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+// Queues one time step (three stages) on stream st.
+void queue_step(evfdlb_ctx* c, cudaStream_t st) {
+    const int n = (int)c->items_h.size();
+    double *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
+    double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
+    // u1 = u + dt L(u)
+    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f0, nullptr, f1, m0, m1, c->NF,
+                 c->NN, 0.0, 1.0, 0, c->Z, c->err);
+    // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
+    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f1, f0, f2, m1, m2, c->NF, c->NN,
+                 0.75, 0.25, 0, c->Z, c->err);
+    // u_new = 1/3 u + 2/3 (u2 + dt L(u2)), written over u
+    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f2, f0, f0, m2, m0, c->NF, c->NN,
+                 1.0 / 3.0, 2.0 / 3.0, 0, c->Z, c->err);
+}
+
+// Splits every slab into node tiles of Z nodes (the last tile of a slab may
+// be shorter); the device work list is sized for the finest split (Z = 1).
+void partition(evfdlb_ctx* c, int Z) {
+    c->Z = Z;
+    c->items_h.clear();
+    for (int s = 0; s < c->nbatch; ++s)
+        for (int i0 = 0; i0 < c->params[s].nx; i0 += Z)
+            c->items_h.push_back(WorkItem{s, i0, std::min(Z, c->params[s].nx - i0), 0});
+    c->smem = stage_smem_bytes(c->Qmax, Z, c->Mmax);
+    if (c->items_cap == 0) c->items_cap = (size_t)c->NN;
+}
+
+evfdlb_status capture(evfdlb_ctx* c, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    TRY_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < steps; ++s) queue_step(c, c->cap);
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+}
+
+// Reads and clears the device error word (synchronises the user stream).
+evfdlb_status check_device(evfdlb_ctx* c) {
+    unsigned h = 0;
+    TRY_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->user));
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    if (h) {
+        c->poisoned = true;
+        TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
+        return (h & ERR_NONFINITE) ? EVFDLB_E_NONFINITE : EVFDLB_E_NEGATIVE;
+    }
+    return EVFDLB_OK;
+}
+
+evfdlb_status copy_in(evfdlb_ctx* c, double* dst, const double* src, size_t bytes, int on_device) {
+    TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->user));
+    return EVFDLB_OK;
+}
+
+evfdlb_status copy_out(evfdlb_ctx* c, double* dst, const double* src, size_t bytes, int on_device) {
+    TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->user));
+    return EVFDLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void evfdlb_default_params(evfdlb_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dim = 1;
+    p->ny = 1;
+    p->sigma = 1.0;
+    p->phi_a = 1.0;
+    p->gamma = 6.0;
+    p->r_cut = 6.0;
+    p->Q = 16;
+    p->bc = EVFDLB_BC_PERIODIC;
+    p->precision = EVFDLB_FP64;
+    p->force_model = EVFDLB_EV1;
+    p->relax_mode = EVFDLB_RELAX_INV_TAU;
+    p->dt = 0.0;
+    p->cfl = 0.5;
+    p->ckpt_every = 0;
+    p->weno_eps = 1e-6;
+}
+
+const char* evfdlb_status_string(evfdlb_status s) {
+    switch (s) {
+        case EVFDLB_OK: return "ok";
+        case EVFDLB_E_INVALID_ARG: return "invalid argument";
+        case EVFDLB_E_CUDA: return "CUDA runtime error";
+        case EVFDLB_E_OOM: return "out of device memory";
+        case EVFDLB_E_NONFINITE: return "non-finite value in the state";
+        case EVFDLB_E_NEGATIVE: return "non-positive density or temperature";
+        case EVFDLB_E_TIMEOUT: return "bounded device wait timed out";
+        case EVFDLB_E_STATE: return "call out of order (no valid state)";
+        case EVFDLB_E_UNSUPPORTED: return "not supported by this build";
+    }
+    return "unknown status";
+}
+
+double evfdlb_discrete_a(const evfdlb_params* p) {
+    if (!p || !validate(*p, nullptr)) return NAN;
+    return discrete_a(*p);
+}
+
+double evfdlb_critical_T(const evfdlb_params* p) {
+    if (!p || !validate(*p, nullptr)) return NAN;
+    return critical_T_of_a(discrete_a(*p), p->sigma, nullptr);
+}
+
+evfdlb_status evfdlb_coexistence(const evfdlb_params* p, double T, double* nv, double* nl) {
+    if (!p || !nv || !nl || !validate(*p, nullptr)) return EVFDLB_E_INVALID_ARG;
+    if (!coexistence_of(discrete_a(*p), p->sigma, T, nv, nl)) return EVFDLB_E_INVALID_ARG;
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_velocity_set(int32_t Q, double* xi, double* w) {
+    if (!xi || !w || Q < 4 || Q > 64) return EVFDLB_E_INVALID_ARG;
+    return velocity_set(Q, xi, w) ? EVFDLB_OK : EVFDLB_E_INVALID_ARG;
+}
+
+evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb_params* per_slab,
+                            void* cuda_stream, evfdlb_ctx** out) {
+    if (!out) return EVFDLB_E_INVALID_ARG;
+    *out = nullptr;
+    if (nbatch < 1) return EVFDLB_E_INVALID_ARG;
+    if (nbatch == 1 && !p && !per_slab) return EVFDLB_E_INVALID_ARG;
+    if (nbatch > 1 && !per_slab) return EVFDLB_E_INVALID_ARG;
+    std::vector<evfdlb_params> ps(nbatch);
+    for (int s = 0; s < nbatch; ++s) {
+        ps[s] = (nbatch == 1) ? (p ? *p : per_slab[0]) : per_slab[s];
+        if (!validate(ps[s], nullptr)) return EVFDLB_E_INVALID_ARG;
+        if (ps[s].precision != EVFDLB_FP64 || ps[s].force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
+    }
+    evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
+    if (!c) return EVFDLB_E_OOM;
+    c->nbatch = nbatch;
+    c->params = ps;
+    c->user = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return EVFDLB_E_CUDA; }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (sms <= 0) sms = 1;
+
+    // velocity tables, one block per distinct Q
+    std::map<int, int> tab_off;
+    std::vector<double> tables;
+    for (auto& q : ps) {
+        if (tab_off.count(q.Q)) continue;
+        TableLayout L(q.Q);
+        std::vector<double> xi(q.Q), w(q.Q);
+        velocity_set(q.Q, xi.data(), w.data());
+        tab_off[q.Q] = (int)tables.size();
+        tables.resize(tables.size() + L.total);
+        build_tables(q.Q, xi.data(), w.data(), tables.data() + tab_off[q.Q]);
+    }
+    // taps, slab descriptors, work items
+    std::vector<double> taps;
+    long long NF = 0, NN = 0;
+    int Qmax = 0, Mmax = 0;
+    for (int s = 0; s < nbatch; ++s) {
+        const evfdlb_params& q = ps[s];
+        SlabDesc d;
+        memset(&d, 0, sizeof(d));
+        d.nx = q.nx;
+        d.Q = q.Q;
+        d.bc = q.bc;
+        d.relax = q.relax_mode;
+        d.M = tap_halfwidth(q.r_cut, q.dx);
+        d.m = tap_halfwidth(q.sigma, q.dx);
+        d.tab_off = tab_off[q.Q];
+        d.tap_off = (int)taps.size();
+        std::vector<double> t;
+        build_taps(q, t);
+        taps.insert(taps.end(), t.begin(), t.end());
+        d.f_off = NF;
+        d.node_off = NN;
+        d.dx = q.dx;
+        d.inv_dx = 1.0 / q.dx;
+        d.dt = resolved_dt(q);
+        d.weno_eps = q.weno_eps;
+        d.b = 2.0 * M_PI * q.sigma * q.sigma * q.sigma / 3.0;
+        d.eta_coef = M_PI * q.sigma * q.sigma * q.sigma / 6.0;
+        d.mu0_coef = 5.0 / (16.0 * q.sigma * q.sigma * sqrt(M_PI));
+        NF += (long long)q.Q * q.nx;
+        NN += q.nx;
+        Qmax = std::max(Qmax, q.Q);
+        Mmax = std::max(Mmax, d.M);
+        c->slabs_h.push_back(d);
+    }
+    c->NF = NF;
+    c->NN = NN;
+    c->Qmax = Qmax;
+    c->Mmax = Mmax;
+    // node tile: one wave of CTAs over the SMs when possible
+    long long z = (NN + sms - 1) / sms;
+    partition(c, (int)std::min<long long>(std::max<long long>(z, 1), kZMax));
+
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    for (int i = 0; i < 3; ++i) {
+        alloc((void**)&c->state[i], sizeof(double) * 2 * NF);
+        alloc((void**)&c->mom[i], sizeof(double) * kNumMoments * NN);
+    }
+    alloc((void**)&c->tables, sizeof(double) * tables.size());
+    alloc((void**)&c->taps, sizeof(double) * taps.size());
+    alloc((void**)&c->scratch, sizeof(double) * (2 * NF + EVFDLB_NFIELDS * NN + 4 * nbatch));
+    alloc((void**)&c->slabs, sizeof(SlabDesc) * nbatch);
+    alloc((void**)&c->items, sizeof(WorkItem) * c->items_cap);
+    alloc((void**)&c->err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(c->tables, tables.data(), sizeof(double) * tables.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->slabs, c->slabs_h.data(), sizeof(SlabDesc) * nbatch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = configure_kernels(stage_smem_bytes(Qmax, kZMax, Mmax));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        evfdlb_status st = cuda_status(e);
+        free_ctx(c);
+        return st;
+    }
+    evfdlb_status st = capture(c, 1, &c->g_one);
+    if (st == EVFDLB_OK) st = capture(c, c->chunk, &c->g_chunk);
+    if (st != EVFDLB_OK) {
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return EVFDLB_OK;
+}
+
+void evfdlb_destroy(evfdlb_ctx* c) {
+    if (!c) return;
+    if (c->user) cudaStreamSynchronize(c->user);
+    else cudaDeviceSynchronize();
+    free_ctx(c);
+}
+
+evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, const double* T0, int32_t on_device) {
+    if (!c || !n0 || !u0 || !T0) return EVFDLB_E_INVALID_ARG;
+    const double* dn = n0;
+    const double* du = u0;
+    const double* dT = T0;
+    size_t bytes = sizeof(double) * c->NN;
+    if (!on_device) {
+        double* buf = c->scratch;   // [3 NN] fits inside the scratch block
+        evfdlb_status s;
+        if ((s = copy_in(c, buf, n0, bytes, 0)) != EVFDLB_OK) return s;
+        if ((s = copy_in(c, buf + c->NN, u0, bytes, 0)) != EVFDLB_OK) return s;
+        if ((s = copy_in(c, buf + 2 * c->NN, T0, bytes, 0)) != EVFDLB_OK) return s;
+        dn = buf;
+        du = buf + c->NN;
+        dT = buf + 2 * c->NN;
+    }
+    TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
+    launch_init((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, dn, du, dT, c->state[0],
+                c->mom[0], c->NF, c->NN, c->Z, c->err);
+    TRY_CUDA(cudaGetLastError());
+    c->poisoned = false;
+    evfdlb_status s = check_device(c);
+    c->have_state = (s == EVFDLB_OK);
+    return s;
+}
+
+evfdlb_status evfdlb_step_async(evfdlb_ctx* c, int64_t nsteps) {
+    if (!c || nsteps < 0) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
+    int64_t full = nsteps / c->chunk, rest = nsteps % c->chunk;
+    for (int64_t i = 0; i < full; ++i) TRY_CUDA(cudaGraphLaunch(c->g_chunk, c->user));
+    for (int64_t i = 0; i < rest; ++i) TRY_CUDA(cudaGraphLaunch(c->g_one, c->user));
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_step(evfdlb_ctx* c, int64_t nsteps) {
+    evfdlb_status s = evfdlb_step_async(c, nsteps);
+    if (s != EVFDLB_OK) return s;
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_get_state(evfdlb_ctx* c, double* F, double* G, int32_t on_device) {
+    if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    size_t bytes = sizeof(double) * c->NF;
+    evfdlb_status s;
+    if ((s = copy_out(c, F, c->state[0], bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_out(c, G, c->state[0] + c->NF, bytes, on_device)) != EVFDLB_OK) return s;
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, int32_t on_device) {
+    if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
+    size_t bytes = sizeof(double) * c->NF;
+    evfdlb_status s;
+    if ((s = copy_in(c, c->state[0], F, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_in(c, c->state[0] + c->NF, G, bytes, on_device)) != EVFDLB_OK) return s;
+    TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
+    launch_sums((int)c->items_h.size(), c->user, c->slabs, c->items, c->tables, c->state[0], c->mom[0], c->NF,
+                c->NN, c->err);
+    TRY_CUDA(cudaGetLastError());
+    c->poisoned = false;
+    s = check_device(c);
+    c->have_state = (s == EVFDLB_OK);
+    return s;
+}
+
+evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_device) {
+    if (!c || !RF || !RG) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    launch_stage((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->taps, c->state[0],
+                 nullptr, c->scratch, c->mom[0], nullptr, c->NF, c->NN, 0.0, 1.0, 1, c->Z, c->err);
+    TRY_CUDA(cudaGetLastError());
+    size_t bytes = sizeof(double) * c->NF;
+    evfdlb_status s;
+    if ((s = copy_out(c, RF, c->scratch, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_out(c, RG, c->scratch + c->NF, bytes, on_device)) != EVFDLB_OK) return s;
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_fields(evfdlb_ctx* c, double* fields, int32_t on_device) {
+    if (!c || !fields) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    double* buf = c->scratch;
+    launch_fields((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->taps, c->mom[0], buf,
+                  c->NN, c->Z, c->err);
+    TRY_CUDA(cudaGetLastError());
+    evfdlb_status s = copy_out(c, fields, buf, sizeof(double) * EVFDLB_NFIELDS * c->NN, on_device);
+    if (s != EVFDLB_OK) return s;
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, double* q, double* totals,
+                             int32_t on_device) {
+    if (!c) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    double* buf = c->scratch;
+    double* outs[4] = {n, u, T, q};
+    double* dptr[4];
+    for (int i = 0; i < 4; ++i) dptr[i] = outs[i] ? (on_device ? outs[i] : buf + i * c->NN) : nullptr;
+    launch_moments(c->user, c->mom[0], c->NN, dptr[0], dptr[1], dptr[2], dptr[3]);
+    TRY_CUDA(cudaGetLastError());
+    if (!on_device)
+        for (int i = 0; i < 4; ++i)
+            if (outs[i]) {
+                evfdlb_status s = copy_out(c, outs[i], dptr[i], sizeof(double) * c->NN, 0);
+                if (s != EVFDLB_OK) return s;
+            }
+    if (totals) {
+        double* dt = buf + EVFDLB_NFIELDS * c->NN;
+        launch_totals(c->nbatch, c->user, c->slabs, c->taps, c->mom[0], c->NN, dt);
+        TRY_CUDA(cudaGetLastError());
+        evfdlb_status s = copy_out(c, totals, dt, sizeof(double) * 4 * c->nbatch, 0);
+        if (s != EVFDLB_OK) return s;
+    }
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_slab_info(const evfdlb_ctx* c, int32_t s, int32_t* nx, int32_t* Q, double* dt) {
+    if (!c || s < 0 || s >= c->nbatch) return EVFDLB_E_INVALID_ARG;
+    if (nx) *nx = c->slabs_h[s].nx;
+    if (Q) *Q = c->slabs_h[s].Q;
+    if (dt) *dt = c->slabs_h[s].dt;
+    return EVFDLB_OK;
+}
+
+int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? 3 : 0; }
+
+int32_t evfdlb_tile_nodes(const evfdlb_ctx* c) { return c ? c->Z : 0; }
+
+evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
+    if (!c || tile_nodes < 1 || tile_nodes > kZMax) return EVFDLB_E_INVALID_ARG;
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    partition(c, tile_nodes);
+    TRY_CUDA(cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice));
+    if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
+    if (c->g_one) cudaGraphExecDestroy(c->g_one);
+    c->g_chunk = c->g_one = nullptr;
+    evfdlb_status st = capture(c, 1, &c->g_one);
+    if (st == EVFDLB_OK) st = capture(c, c->chunk, &c->g_chunk);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// evfdlb_internal.h -- structures shared by the host model code, the kernels
+// and the C-ABI layer of libevfdlb.  Not part of the public interface.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "evfdlb.h"
+
+#ifdef __CUDACC__
+#define EVF_HD __host__ __device__
+#else
+#define EVF_HD
+#endif
+
+namespace evfdlb {
+
+constexpr int kQMax = 32;          // largest Gauss-Hermite order of a slab
+constexpr int kZMax = 64;          // largest node tile of one CTA
+constexpr int kThreads = 256;      // threads of the stage kernels
+constexpr int kNumMoments = 6;     // raw moment sums kept per node
+constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
+
+// Raw moment sums of a state, per node: S0 = sum F, S1 = sum xi F,
+// S2 = sum xi^2 F, S3 = sum xi^3 F, G0 = sum G, G1 = sum xi G.
+enum { MOM_S0 = 0, MOM_S1, MOM_S2, MOM_S3, MOM_G0, MOM_G1 };
+
+// Error bits latched by the kernels.
+enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u };
+
+// Offsets inside the table block of one velocity order Q (doubles).
+struct TableLayout {
+    int xi, w, P, S, rinv, rr, r1, r2, r3, total;
+    EVF_HD explicit TableLayout(int Q) {
+        xi = 0;
+        w = xi + Q;
+        P = w + Q;          // P[l*Q + j] = psi_l(xi_j)          (analysis)
+        S = P + Q * Q;      // S[k*Q + l] = w_k psi_l(xi_k)      (synthesis)
+        rinv = S + Q * Q;   // 1/sqrt(l+1)
+        rr = rinv + Q;      // sqrt(l)/sqrt(l+1)
+        r1 = rr + Q;        // sqrt(l)
+        r2 = r1 + Q;        // sqrt(l(l-1))
+        r3 = r2 + Q;        // sqrt(l(l-1)(l-2))
+        total = r3 + Q;
+    }
+};
+
+// One slab as the kernels see it.
+struct SlabDesc {
+    int nx, Q, bc, relax;
+    int M, m;            // half-widths of the force and Fischer-Methfessel taps
+    int tab_off;         // offset of this slab's velocity tables (doubles)
+    int tap_off;         // offset of this slab's taps: force[2M+1], fm[2m+1], energy[2M+1]
+    long long f_off;     // offset of this slab in the F (and G) arrays (elements)
+    long long node_off;  // offset of this slab in per-node arrays
+    double dx, inv_dx, dt, weno_eps;
+    double b;            // 2 pi sigma^3 / 3, Eq. (carnstar)
+    double eta_coef;     // pi sigma^3 / 6
+    double mu0_coef;     // 5 / (16 sigma^2 sqrt(pi)), Eq. (viscosity)
+};
+
+// One CTA's share of work: nodes [i0, i0 + nz) of slab `slab`.
+struct WorkItem {
+    int slab, i0, nz, pad;
+};
+
+// ---- host model code (host_model.cpp) ----
+bool velocity_set(int Q, double* xi, double* w);                 // ascending, sum w = 1
+void build_tables(int Q, const double* xi, const double* w, double* out);  // TableLayout(Q)
+bool validate(const evfdlb_params& p, const char** why);
+int tap_halfwidth(double len, double dx);                        // len/dx if integral, else -1
+void build_taps(const evfdlb_params& p, std::vector<double>& out);  // force, fm, energy
+double discrete_a(const evfdlb_params& p);
+double critical_T_of_a(double a, double sigma, double* n_c);
+bool coexistence_of(double a, double sigma, double T, double* nv, double* nl);
+double resolved_dt(const evfdlb_params& p);
+
+}  // namespace evfdlb

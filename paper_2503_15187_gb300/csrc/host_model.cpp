@@ -1,0 +1,264 @@
+// host_model.cpp -- host-side model constants of libevfdlb: the Gauss-Hermite
+// velocity set and its Hermite tables, the Simpson taps of the force and of
+// the Fischer-Methfessel average, parameter validation, and the equation of
+// state with its critical point and Maxwell construction.
+//
+// Paper: Busuioc & Sofonea, arXiv:2503.15187.  Equations cited by label.
+#include <math.h>
+
+#include <vector>
+
+#include "evfdlb_internal.h"
+
+namespace evfdlb {
+
+namespace {
+const long double kPiL = 3.141592653589793238462643383279502884L;
+const double kPi = 3.14159265358979323846;
+
+// Orthonormal probabilists' Hermite functions psi_l = He_l / sqrt(l!) at x,
+// l = 0..L, by psi_{l+1} = (x psi_l - sqrt(l) psi_{l-1}) / sqrt(l+1).
+template <typename R>
+void psi_all(int L, R x, R* psi) {
+    psi[0] = 1;
+    if (L >= 1) psi[1] = x;
+    for (int l = 1; l < L; ++l)
+        psi[l + 1] = (x * psi[l] - sqrtl((long double)l) * psi[l - 1]) / sqrtl((long double)(l + 1));
+}
+
+// Number of eigenvalues below x of the Jacobi matrix of the probabilists'
+// Hermite recurrence (zero diagonal, off-diagonal sqrt(k)), by the Sturm
+// count of the LDL^T pivots.
+int sturm_count(int Q, long double x) {
+    int count = 0;
+    long double d = -x;
+    if (d < 0) ++count;
+    for (int k = 1; k < Q; ++k) {
+        long double piv = (d == 0) ? 1e-300L : d;
+        d = -x - (long double)k / piv;
+        if (d < 0) ++count;
+    }
+    return count;
+}
+}  // namespace
+
+// Roots of He_Q (the velocity nodes of the full-range Gauss-Hermite rule) by
+// bisection on the Sturm count, polished by Newton on psi_Q with
+// psi_Q' = sqrt(Q) psi_{Q-1}; weights w = 1 / (Q psi_{Q-1}(x)^2), which sum to 1.
+bool velocity_set(int Q, double* xi, double* w) {
+    if (Q < 1 || Q > 64) return false;
+    std::vector<long double> psi(Q + 1);
+    long double bound = sqrtl(4.0L * Q + 2.0L) + 1.0L;
+    for (int k = 0; k < Q; ++k) {
+        long double lo = -bound, hi = bound;   // k-th smallest: count(x) >= k+1
+        for (int it = 0; it < 200 && hi - lo > 1e-18L * (1 + fabsl(lo)); ++it) {
+            long double mid = 0.5L * (lo + hi);
+            if (sturm_count(Q, mid) >= k + 1) hi = mid; else lo = mid;
+        }
+        long double x = 0.5L * (lo + hi);
+        for (int it = 0; it < 3; ++it) {
+            psi_all<long double>(Q, x, psi.data());
+            long double dpsi = sqrtl((long double)Q) * psi[Q - 1];
+            if (dpsi == 0) break;
+            x -= psi[Q] / dpsi;
+        }
+        psi_all<long double>(Q, x, psi.data());
+        xi[k] = (double)x;
+        w[k] = (double)(1.0L / ((long double)Q * psi[Q - 1] * psi[Q - 1]));
+    }
+    return true;
+}
+
+void build_tables(int Q, const double* xi, const double* w, double* out) {
+    TableLayout L(Q);
+    std::vector<long double> psi(Q + 1);
+    for (int k = 0; k < Q; ++k) {
+        out[L.xi + k] = xi[k];
+        out[L.w + k] = w[k];
+        psi_all<long double>(Q, (long double)xi[k], psi.data());
+        for (int l = 0; l < Q; ++l) {
+            out[L.P + l * Q + k] = (double)psi[l];
+            out[L.S + k * Q + l] = (double)((long double)w[k] * psi[l]);
+        }
+    }
+    for (int l = 0; l < Q; ++l) {
+        long double ll = l;
+        out[L.rinv + l] = (double)(1.0L / sqrtl(ll + 1));
+        out[L.rr + l] = (double)(sqrtl(ll) / sqrtl(ll + 1));
+        out[L.r1 + l] = (double)sqrtl(ll);
+        out[L.r2 + l] = (double)sqrtl(ll * (ll - 1 > 0 ? ll - 1 : 0));
+        out[L.r3 + l] = (double)sqrtl(ll * (ll - 1 > 0 ? ll - 1 : 0) * (ll - 2 > 0 ? ll - 2 : 0));
+    }
+}
+
+int tap_halfwidth(double len, double dx) {
+    double r = len / dx;
+    long long n = llround(r);
+    if (n < 1 || fabs(r - (double)n) > 1e-9 * (1.0 + r)) return -1;
+    return (int)n;
+}
+
+bool validate(const evfdlb_params& p, const char** why) {
+    const char* w = nullptr;
+    if (p.dim != 1) w = "dim must be 1";
+    else if (p.ny != 1) w = "ny must be 1 for a 1D slab";
+    else if (p.nx < 8) w = "nx must be >= 8";
+    else if (!(p.dx > 0)) w = "dx must be > 0";
+    else if (!(p.sigma > 0)) w = "sigma must be > 0";
+    else if (!(p.phi_a >= 0)) w = "phi_a must be >= 0";
+    else if (!(p.gamma > 3)) w = "gamma must be > 3";
+    else if (p.Q < 4 || p.Q > kQMax) w = "Q must be in [4, 32]";
+    else if (p.bc != EVFDLB_BC_PERIODIC && p.bc != EVFDLB_BC_OUTFLOW) w = "bad bc";
+    else if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) w = "bad relax_mode";
+    else if (!(p.weno_eps > 0)) w = "weno_eps must be > 0";
+    else if (!(p.dt > 0) && !(p.cfl > 0 && p.cfl <= 1)) w = "need dt > 0 or 0 < cfl <= 1";
+    else {
+        int m = tap_halfwidth(p.sigma, p.dx);
+        int M = tap_halfwidth(p.r_cut, p.dx);
+        if (m < 1) w = "sigma/dx must be a positive integer";
+        else if (M < 1) w = "r_cut/dx must be a positive integer";
+        else if (M < m + 2) w = "r_cut must be >= sigma + 2 dx";
+        else if ((M - m) % 2) w = "(r_cut - sigma)/dx must be even (Simpson panels end at +-sigma)";
+    }
+    if (why) *why = w;
+    return w == nullptr;
+}
+
+namespace {
+double simpson(int j, int M, double dx) {
+    int t = j + M;
+    double c = (t == 0 || t == 2 * M) ? 1.0 : ((t & 1) ? 4.0 : 2.0);
+    return c * dx / 3.0;
+}
+// Eq. (F1) kernel: the 3D force of Eq. (force) integrated over a plane at offset z.
+double g_kernel(double z, double s, double phi, double gam) {
+    double az = fabs(z);
+    if (az < s) return 2.0 * kPi * phi * z;
+    return 2.0 * kPi * phi * pow(s / az, gam) * z;
+}
+// Even potential whose derivative is g, vanishing at infinity.
+double g_potential(double z, double s, double phi, double gam) {
+    double az = fabs(z);
+    if (az < s) return kPi * phi * (z * z - s * s * gam / (gam - 2.0));
+    return -2.0 * kPi * phi * s * s * pow(s / az, gam - 2.0) / (gam - 2.0);
+}
+}  // namespace
+
+// Taps of one slab: [force 2M+1 | Fischer-Methfessel 2m+1 | energy 2M+1].
+//  force_j  = s_j g(j dx)                                (Eq. (F1), Simpson 1/3)
+//  fm_j     = 3/(4 sigma^3) s_j (sigma^2 - (j dx)^2)     (sphere average, Sec. II.A)
+//  energy_j = s_j [Phi(j dx) - Phi(r_cut)]               (mean-field energy)
+void build_taps(const evfdlb_params& p, std::vector<double>& out) {
+    int M = tap_halfwidth(p.r_cut, p.dx), m = tap_halfwidth(p.sigma, p.dx);
+    out.clear();
+    for (int j = -M; j <= M; ++j)
+        out.push_back(simpson(j, M, p.dx) * g_kernel(j * p.dx, p.sigma, p.phi_a, p.gamma));
+    double s3 = p.sigma * p.sigma * p.sigma;
+    for (int j = -m; j <= m; ++j) {
+        double z = j * p.dx;
+        out.push_back(3.0 / (4.0 * s3) * simpson(j, m, p.dx) * (p.sigma * p.sigma - z * z));
+    }
+    double phiR = g_potential(p.r_cut, p.sigma, p.phi_a, p.gamma);
+    for (int j = -M; j <= M; ++j)
+        out.push_back(simpson(j, M, p.dx) * (g_potential(j * p.dx, p.sigma, p.phi_a, p.gamma) - phiR));
+}
+
+double discrete_a(const evfdlb_params& p) {
+    int M = tap_halfwidth(p.r_cut, p.dx);
+    if (M < 1) return NAN;
+    long double acc = 0;
+    for (int j = -M; j <= M; ++j)
+        acc += (long double)simpson(j, M, p.dx) * (j * p.dx) * g_kernel(j * p.dx, p.sigma, p.phi_a, p.gamma);
+    return (double)(0.5L * acc);
+}
+
+double resolved_dt(const evfdlb_params& p) {
+    if (p.dt > 0) return p.dt;
+    double xi[kQMax], w[kQMax];
+    velocity_set(p.Q, xi, w);
+    return p.cfl * p.dx / fabs(xi[p.Q - 1]);
+}
+
+// ---------------------------------------------------------------------------
+// Equation of state, Eq. (EOSS): P = n T Z(eta) - a n^2 with the
+// Carnahan-Starling Z = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = pi s^3 n/6.
+// With y(eta) = eta Z(eta):
+//   y'  = (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4) / (1 - eta)^4
+//   y'' = [N'(1 - eta) + 4 N] / (1 - eta)^5,  N the numerator of y'.
+// ---------------------------------------------------------------------------
+namespace {
+struct Eos {
+    double a, s, k;  // k = 6 / (pi s^3): n = k eta
+    double eta(double n) const { return n / k; }
+    double P(double n, double T) const {
+        double e = eta(n), om = 1 - e;
+        return n * T * (1 + e + e * e - e * e * e) / (om * om * om) - a * n * n;
+    }
+    static double y1(double e) {
+        double om = 1 - e;
+        return (1 + 4 * e + 4 * e * e - 4 * e * e * e + e * e * e * e) / (om * om * om * om);
+    }
+    static double y2(double e) {
+        double om = 1 - e;
+        double N = 1 + 4 * e + 4 * e * e - 4 * e * e * e + e * e * e * e;
+        double dN = 4 + 8 * e - 12 * e * e + 4 * e * e * e;
+        return (dN * om + 4 * N) / (om * om * om * om * om);
+    }
+    double dPdn(double n, double T) const { return T * y1(eta(n)) - 2 * a * n; }
+    // chemical potential up to a function of T: n dmu/dn = dP/dn
+    double mu(double n, double T) const {
+        double e = eta(n), om = 1 - e;
+        return T * (log(n) + (8 * e - 9 * e * e + 3 * e * e * e) / (om * om * om)) - 2 * a * n;
+    }
+};
+
+template <typename Fn>
+double bisect(Fn f, double lo, double hi, int iters = 400) {
+    double flo = f(lo);
+    for (int it = 0; it < iters; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        double fm = f(mid);
+        if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    }
+    return 0.5 * (lo + hi);
+}
+}  // namespace
+
+// Critical point: dP/dn = d2P/dn2 = 0, i.e. y'(eta) = eta y''(eta) and
+// T_c = 2 a k / y''(eta_c).
+double critical_T_of_a(double a, double sigma, double* n_c) {
+    Eos E{a, sigma, 6.0 / (kPi * sigma * sigma * sigma)};
+    double ec = bisect([](double e) { return Eos::y1(e) - e * Eos::y2(e); }, 0.01, 0.4);
+    if (n_c) *n_c = E.k * ec;
+    return 2.0 * a * E.k / Eos::y2(ec);
+}
+
+// Maxwell construction at temperature T (Sec. III.A): find the saturation
+// pressure at which the vapour and liquid branches have equal chemical potential.
+bool coexistence_of(double a, double sigma, double T, double* nv, double* nl) {
+    double n_c;
+    double Tc = critical_T_of_a(a, sigma, &n_c);
+    if (!(T > 0) || !(T < Tc)) return false;
+    Eos E{a, sigma, 6.0 / (kPi * sigma * sigma * sigma)};
+    double n_max = 0.99 * E.k;
+    double s_lo = bisect([&](double n) { return E.dPdn(n, T); }, 1e-12, n_c);
+    double s_hi = bisect([&](double n) { return E.dPdn(n, T); }, n_c, n_max);
+    double p_hi = E.P(s_lo, T);
+    double p_lo = E.P(s_hi, T);
+    if (p_lo < 0) p_lo = 0;
+    auto branches = [&](double Ps, double* v, double* l) {
+        // vapour branch is increasing on (0, s_lo), liquid on (s_hi, n_max)
+        *v = bisect([&](double n) { return E.P(n, T) - Ps; }, 1e-300, s_lo);
+        *l = bisect([&](double n) { return E.P(n, T) - Ps; }, s_hi, n_max);
+    };
+    double Ps = bisect([&](double P) {
+        double v, l;
+        branches(P, &v, &l);
+        return E.mu(l, T) - E.mu(v, T);
+    }, p_lo + 1e-300, p_hi, 200);
+    branches(Ps, nv, nl);
+    return true;
+}
+
+}  // namespace evfdlb

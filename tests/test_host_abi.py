@@ -1,0 +1,87 @@
+"""CPU-side checks of libevfdlb: the library builds and loads, exports every
+entry point include/evfdlb.h declares, and its host-side model constants
+(velocity set, force constant, critical point, Maxwell construction) agree
+with the oracle's independent implementations.  No CUDA call is made."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2503_15187_gb300 as ev
+from paper_2503_15187_gb300.buildlib import build as build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_lib()
+    return ev.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "evfdlb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(evfdlb_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings(L):
+    for code in range(-8, 1):
+        assert L.evfdlb_status_string(code)
+    assert L.evfdlb_status_string(-4) == b"non-finite value in the state"
+
+
+@pytest.mark.parametrize("Q", [4, 8, 16, 24, 32, 48])
+def test_velocity_set_matches_oracle(L, Q):
+    xi, w = ev.velocity_set(Q)
+    xo, wo = O.gauss_hermite(Q)
+    o = np.argsort(xo)
+    assert np.all(np.diff(xi) > 0)
+    assert np.allclose(xi, xo[o], rtol=0, atol=2e-14 * max(1, np.abs(xo).max()))
+    assert np.allclose(w, wo[o], rtol=1e-12, atol=0)
+    assert abs(w.sum() - 1) < 1e-14
+
+
+def test_default_params_are_the_papers(L):
+    cp = ev.CParams()
+    L.evfdlb_default_params(ctypes.byref(cp))
+    assert (cp.sigma, cp.phi_a, cp.gamma, cp.r_cut, cp.Q) == (1.0, 1.0, 6.0, 6.0, 16)
+    assert cp.weno_eps == 1e-6 and cp.cfl == 0.5 and cp.dim == 1
+
+
+@pytest.mark.parametrize("dx", [0.25, 0.1, 0.125])
+def test_force_constant_and_critical_point(L, dx):
+    p = ev.Params(nx=64, dx=dx)
+    orc = O.Oracle(O.Setup(nz=64, Q=8, dz=dx, dt=0.01))
+    assert abs(ev.discrete_a(p) - orc.discrete_a()) < 1e-13 * orc.discrete_a()
+    assert abs(ev.critical_T(p) - orc.critical_T()) < 1e-12
+
+
+@pytest.mark.parametrize("r", [0.6, 0.7, 0.8, 0.95])
+def test_coexistence_matches_oracle(L, r):
+    p = ev.Params(nx=64, dx=0.25)
+    a = ev.discrete_a(p)
+    T = r * ev.critical_T(p)
+    nv, nl = ev.coexistence(p, T)
+    nvo, nlo = O.coexistence(T, a)
+    assert abs(nv - nvo) < 1e-9 * nvo and abs(nl - nlo) < 1e-9 * nlo
+
+
+def test_invalid_params_rejected(L):
+    for bad in (dict(dx=0.3), dict(dx=0.25, Q=40), dict(dx=0.25, r_cut=5.75),
+                dict(dx=0.25, gamma=3.0), dict(dx=0.25, bc=7)):
+        kw = dict(nx=64)
+        kw.update(bad)
+        p = ev.Params(**kw)
+        assert math.isnan(ev.critical_T(p)), bad
