@@ -168,6 +168,41 @@ int32_t evfdlb_launches_per_step(const evfdlb_ctx* ctx);
 evfdlb_status evfdlb_tune(evfdlb_ctx* ctx, int32_t tile_nodes);
 int32_t evfdlb_tile_nodes(const evfdlb_ctx* ctx);
 
+/* Time step without any device allocation.  The paper has no counterpart.
+ * It serves callers that cannot call cudaMalloc: a plugin whose host
+ * application owns all device memory through its own pool and hands out
+ * only pointers; a process held to a fixed device-memory budget fixed at
+ * start-up, where a later allocation may fail; and latency-bound loops, where
+ * cudaMalloc / cudaFree may synchronise the device and take unbounded time.
+ *
+ * Advances the slab described by *p (validated as for evfdlb_create; FP64,
+ * EV1) by nsteps Shu-Osher RK3 steps, in place.  state is a DEVICE pointer to
+ * 2 * Q * nx doubles: F (velocity-major, [k * nx + i]) followed by G, owned
+ * by the caller.  All working memory (the two intermediate stages, moment
+ * sums, velocity tables, taps, work list and error word) lives in one
+ * file-scope __device__ array of about 3.4 MiB that every GPU loading the
+ * library holds until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ * Limits: nx <= EVFDLB_STATIC_MAX_NODES, Q * nx <= EVFDLB_STATIC_MAX_ELEMENTS,
+ * r_cut / dx <= EVFDLB_STATIC_MAX_HALFWIDTH; larger requests return
+ * EVFDLB_E_INVALID_ARG before any CUDA call.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and raises the stage
+ * kernel's shared-memory limit; make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind
+ * (the error word is cleared at the start of each call; everything else is
+ * written before it is read), so calls that overlap on the GPU -- on
+ * different streams or host threads of one device -- race: the caller must
+ * serialise them.  Work is queued on cuda_stream (a cudaStream_t, NULL = the
+ * legacy default stream); the call synchronises that stream once at the end
+ * to read the error word.
+ * Errors: E_INVALID_ARG, E_UNSUPPORTED, E_NONFINITE, E_NEGATIVE, E_CUDA. */
+#define EVFDLB_STATIC_MAX_NODES 8192
+#define EVFDLB_STATIC_MAX_ELEMENTS 65536
+#define EVFDLB_STATIC_MAX_HALFWIDTH 500
+evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* state, int64_t nsteps,
+                                 void* cuda_stream);
+
 /* Releases the context and its device memory (NULL is a no-op). */
 void evfdlb_destroy(evfdlb_ctx* ctx);
 

@@ -108,6 +108,7 @@ def lib():
             "evfdlb_critical_T": (d, [P]),
             "evfdlb_coexistence": (i32, [P, d, ctypes.POINTER(d), ctypes.POINTER(d)]),
             "evfdlb_velocity_set": (i32, [i32, vp, vp]),
+            "evfdlb_step_static": (i32, [P, vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -162,6 +163,22 @@ def coexistence(p: Params, T: float):
     _check(lib().evfdlb_coexistence(ctypes.byref(p.c()), T, ctypes.byref(nv), ctypes.byref(nl)),
            "evfdlb_coexistence")
     return nv.value, nl.value
+
+
+def step_static(p: Params, state, nsteps: int = 1, stream=None):
+    """Advances a caller-owned device state (contiguous float64 CUDA tensor of
+    2 * Q * nx values, F then G) by nsteps steps in place, without any device
+    allocation: for callers that cannot allocate device memory (a host
+    application's own pool, a fixed memory budget).  Calls that overlap on
+    the GPU share the library's static working memory and must be serialised.
+    ``stream`` is a torch.cuda.Stream (None: torch's current stream)."""
+    import torch
+    ptr, dev = _ptr(state)
+    if not dev or state.numel() != 2 * p.Q * p.nx:
+        raise ValueError("state must be a CUDA float64 tensor of 2 * Q * nx values")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().evfdlb_step_static(ctypes.byref(p.c()), ptr, int(nsteps), ctypes.c_void_p(s.cuda_stream)),
+           "evfdlb_step_static")
 
 
 # ---------------------------------------------------------------------------

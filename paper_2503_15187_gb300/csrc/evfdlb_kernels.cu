@@ -566,6 +566,16 @@ cudaError_t configure_kernels(size_t smem_bytes) {
     return cudaFuncSetAttribute(fields_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
+// Raises (never lowers) the stage kernel's dynamic shared-memory limit on the
+// current device to at least smem_bytes.
+cudaError_t ensure_stage_smem(size_t smem_bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= smem_bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
 void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                   const double* tables, const double* taps, const double* src, const double* base,
                   double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
