@@ -215,10 +215,42 @@ def run_ours(args, rank, world):
                 "ms_per_step": e2e_ms / args.steps},
         "wall_s_timed_region": t_wall,
     }
+    n64 = sim.moments(with_totals=False)[0]
+    sim.close()
+    line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
-    sim.close()
     return line
+
+
+def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
+    """The FP32 variant on the same workload and timing protocol: FP32 state and
+    per-velocity work, FP64 chi / transport / gradients / conserved sums.  Its
+    density after the same number of steps is compared with the FP64 run."""
+    import dataclasses
+    import numpy as np
+    import torch
+    p32 = dataclasses.replace(p, precision=ev.FP32)
+    sim = ev.Sim(p32, stream=stream)
+    sim.init(n0, np.zeros(NZ), np.full(NZ, T))
+    sim.step(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        sim.step_async(1)
+        ends[i].record(stream)
+    barrier()
+    sim.step(1)          # the FP64 state compared against has W + K + 1 steps (its end-to-end leg adds one)
+    ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    n32 = sim.moments(with_totals=False)[0]
+    sim.close()
+    return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32 (f64 chi, "
+            "transport, gradients, conserved sums)", "ms_per_step": ms / args.steps,
+            "max_rel_diff_n_vs_fp64": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
+            "gpu_launches": 3 * args.steps}
 
 
 def cpu_baseline(budget_s, T, n0, max_steps=10**9):

@@ -80,7 +80,9 @@ typedef struct {
     double  r_cut;        /* truncation radius of the Eq. (F1) integral (>= sigma + 2dx)*/
     int32_t Q;            /* Gauss-Hermite order, 4 <= Q <= 32                         */
     int32_t bc;           /* EVFDLB_BC_PERIODIC or EVFDLB_BC_OUTFLOW                   */
-    int32_t precision;    /* EVFDLB_FP64 (FP32 reserved: returns E_UNSUPPORTED)        */
+    int32_t precision;    /* EVFDLB_FP64, or EVFDLB_FP32: FP32 state and per-velocity  */
+                          /* work, FP64 chi / transport / gradients / conserved sums;  */
+                          /* one precision per context (the ABI stays float64)         */
     int32_t force_model;  /* EVFDLB_EV1 (EV2 reserved: returns E_UNSUPPORTED)          */
     int32_t relax_mode;   /* EVFDLB_RELAX_INV_TAU or EVFDLB_RELAX_CHI_OVER_TAU         */
     double  dt;           /* > 0: time step; <= 0: dt = cfl * dx / max|xi_k|           */

@@ -14,21 +14,25 @@
 #include "evfdlb_internal.h"
 
 namespace evfdlb {
-size_t stage_smem_bytes(int Q, int Z, int M);
-cudaError_t configure_kernels(size_t smem_bytes);
-void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                  const double* tables, const double* taps, const double* src, const double* base,
-                  double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
-                  double alpha, double beta, int mode, int Z, unsigned* err);
-void launch_init(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                 const double* tables, const double* n0, const double* u0, const double* T0,
-                 double* state, double* mom, long long NF, long long NN, int Z, unsigned* err);
-void launch_sums(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                 const double* tables, const double* state, double* mom, long long NF, long long NN,
-                 unsigned* err);
-void launch_fields(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                   const double* tables, const double* taps, const double* mom, double* fields,
-                   long long NN, int Z, unsigned* err);
+size_t stage_smem_bytes_p(int prec, int Q, int Z, int M);
+cudaError_t configure_kernels_p(int prec, size_t smem_bytes);
+void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                    const WorkItem* items, const double* tables, const void* rtab, const double* taps,
+                    const void* rtaps, const void* src, const void* base, void* out, double* rhs_out,
+                    const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
+                    int mode, int Z, unsigned* err);
+void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                   const WorkItem* items, const double* tables, const void* rtab, const double* n0,
+                   const double* u0, const double* T0, void* state, double* mom, long long NF, long long NN, int Z,
+                   unsigned* err);
+void launch_sums_p(int prec, int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                   const double* tables, const void* rtab, const void* state, double* mom, long long NF,
+                   long long NN, unsigned* err);
+void launch_fields_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                     const WorkItem* items, const void* rtab, const double* taps, const void* rtaps,
+                     const double* mom, double* fields, long long NN, int Z, unsigned* err);
+void launch_convert_to_f32(cudaStream_t st, const double* in, float* out, long long n);
+void launch_convert_to_f64(cudaStream_t st, const float* in, double* out, long long n);
 void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
                     double* q);
 void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
@@ -49,10 +53,14 @@ struct evfdlb_ctx {
     int device = 0;
     cudaStream_t user = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
-    double* state[3] = {nullptr, nullptr, nullptr};  // each [2][NF]: F then G
+    int prec = EVFDLB_FP64;      // storage / per-velocity precision of the state
+    size_t esize = sizeof(double);
+    void* state[3] = {nullptr, nullptr, nullptr};    // each [2][NF] of esize: F then G
     double* mom[3] = {nullptr, nullptr, nullptr};    // each [6][NN]
     double* tables = nullptr;
     double* taps = nullptr;
+    void* rtables = nullptr;     // tables / taps in the state precision (aliases for FP64)
+    void* rtaps = nullptr;
     double* scratch = nullptr;   // [2 NF + 16 NN + 4 nbatch]
     SlabDesc* slabs = nullptr;
     WorkItem* items = nullptr;
@@ -88,6 +96,8 @@ void free_ctx(evfdlb_ctx* c) {
         cudaFree(c->state[i]);
         cudaFree(c->mom[i]);
     }
+    if (c->rtables != c->tables) cudaFree(c->rtables);
+    if (c->rtaps != c->taps) cudaFree(c->rtaps);
     cudaFree(c->tables);
     cudaFree(c->taps);
     cudaFree(c->scratch);
@@ -101,17 +111,16 @@ void free_ctx(evfdlb_ctx* c) {
 // Queues one time step (three stages) on stream st.
 void queue_step(evfdlb_ctx* c, cudaStream_t st) {
     const int n = (int)c->items_h.size();
-    double *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
+    void *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
     double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
-    // u1 = u + dt L(u)
-    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f0, nullptr, f1, m0, m1, c->NF,
-                 c->NN, 0.0, 1.0, 0, c->Z, c->err);
-    // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
-    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f1, f0, f2, m1, m2, c->NF, c->NN,
-                 0.75, 0.25, 0, c->Z, c->err);
-    // u_new = 1/3 u + 2/3 (u2 + dt L(u2)), written over u
-    launch_stage(n, c->smem, st, c->slabs, c->items, c->tables, c->taps, f2, f0, f0, m2, m0, c->NF, c->NN,
-                 1.0 / 3.0, 2.0 / 3.0, 0, c->Z, c->err);
+    auto stage = [&](const void* src, const void* base, void* out, const double* mi, double* mo, double a,
+                     double b) {
+        launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps, src,
+                       base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
+    };
+    stage(f0, nullptr, f1, m0, m1, 0.0, 1.0);              // u1 = u + dt L(u)
+    stage(f1, f0, f2, m1, m2, 0.75, 0.25);                 // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
+    stage(f2, f0, f0, m2, m0, 1.0 / 3.0, 2.0 / 3.0);       // u_new = 1/3 u + 2/3 (u2 + dt L(u2)), over u
 }
 
 // Splits every slab into node tiles of Z nodes (the last tile of a slab may
@@ -122,7 +131,7 @@ void partition(evfdlb_ctx* c, int Z) {
     for (int s = 0; s < c->nbatch; ++s)
         for (int i0 = 0; i0 < c->params[s].nx; i0 += Z)
             c->items_h.push_back(WorkItem{s, i0, std::min(Z, c->params[s].nx - i0), 0});
-    c->smem = stage_smem_bytes(c->Qmax, Z, c->Mmax);
+    c->smem = stage_smem_bytes_p(c->prec, c->Qmax, Z, c->Mmax);
     if (c->items_cap == 0) c->items_cap = (size_t)c->NN;
 }
 
@@ -233,13 +242,17 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     for (int s = 0; s < nbatch; ++s) {
         ps[s] = (nbatch == 1) ? (p ? *p : per_slab[0]) : per_slab[s];
         if (!validate(ps[s], nullptr)) return EVFDLB_E_INVALID_ARG;
-        if (ps[s].precision != EVFDLB_FP64 || ps[s].force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
+        if (ps[s].precision != EVFDLB_FP64 && ps[s].precision != EVFDLB_FP32) return EVFDLB_E_INVALID_ARG;
+        if (ps[s].precision != ps[0].precision) return EVFDLB_E_INVALID_ARG;   // one precision per context
+        if (ps[s].force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
     }
     evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
     if (!c) return EVFDLB_E_OOM;
     c->nbatch = nbatch;
     c->params = ps;
     c->user = (cudaStream_t)cuda_stream;
+    c->prec = ps[0].precision;
+    c->esize = (c->prec == EVFDLB_FP32) ? sizeof(float) : sizeof(double);
     if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return EVFDLB_E_CUDA; }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -304,22 +317,34 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
     };
     for (int i = 0; i < 3; ++i) {
-        alloc((void**)&c->state[i], sizeof(double) * 2 * NF);
+        alloc((void**)&c->state[i], c->esize * 2 * NF);
         alloc((void**)&c->mom[i], sizeof(double) * kNumMoments * NN);
     }
     alloc((void**)&c->tables, sizeof(double) * tables.size());
     alloc((void**)&c->taps, sizeof(double) * taps.size());
+    std::vector<float> tables_f(tables.begin(), tables.end()), taps_f(taps.begin(), taps.end());
+    if (c->prec == EVFDLB_FP32) {
+        alloc((void**)&c->rtables, sizeof(float) * tables_f.size());
+        alloc((void**)&c->rtaps, sizeof(float) * taps_f.size());
+    } else {
+        c->rtables = c->tables;
+        c->rtaps = c->taps;
+    }
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + EVFDLB_NFIELDS * NN + 4 * nbatch));
     alloc((void**)&c->slabs, sizeof(SlabDesc) * nbatch);
     alloc((void**)&c->items, sizeof(WorkItem) * c->items_cap);
     alloc((void**)&c->err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tables.data(), sizeof(double) * tables.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->prec == EVFDLB_FP32)
+        e = cudaMemcpy(c->rtables, tables_f.data(), sizeof(float) * tables_f.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->prec == EVFDLB_FP32)
+        e = cudaMemcpy(c->rtaps, taps_f.data(), sizeof(float) * taps_f.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->slabs, c->slabs_h.data(), sizeof(SlabDesc) * nbatch, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = configure_kernels(stage_smem_bytes(Qmax, kZMax, Mmax));
+    if (e == cudaSuccess) e = configure_kernels_p(c->prec, stage_smem_bytes_p(c->prec, Qmax, kZMax, Mmax));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         evfdlb_status st = cuda_status(e);
@@ -360,8 +385,8 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
         dT = buf + 2 * c->NN;
     }
     TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
-    launch_init((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, dn, du, dT, c->state[0],
-                c->mom[0], c->NF, c->NN, c->Z, c->err);
+    launch_init_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables, dn,
+                  du, dT, c->state[0], c->mom[0], c->NF, c->NN, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
     c->poisoned = false;
     evfdlb_status s = check_device(c);
@@ -388,9 +413,15 @@ evfdlb_status evfdlb_get_state(evfdlb_ctx* c, double* F, double* G, int32_t on_d
     if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
     if (!c->have_state) return EVFDLB_E_STATE;
     size_t bytes = sizeof(double) * c->NF;
+    const double* src = (const double*)c->state[0];
+    if (c->prec == EVFDLB_FP32) {   // widen into the scratch block first
+        launch_convert_to_f64(c->user, (const float*)c->state[0], c->scratch, 2 * c->NF);
+        TRY_CUDA(cudaGetLastError());
+        src = c->scratch;
+    }
     evfdlb_status s;
-    if ((s = copy_out(c, F, c->state[0], bytes, on_device)) != EVFDLB_OK) return s;
-    if ((s = copy_out(c, G, c->state[0] + c->NF, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_out(c, F, src, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_out(c, G, src + c->NF, bytes, on_device)) != EVFDLB_OK) return s;
     TRY_CUDA(cudaStreamSynchronize(c->user));
     return EVFDLB_OK;
 }
@@ -398,12 +429,17 @@ evfdlb_status evfdlb_get_state(evfdlb_ctx* c, double* F, double* G, int32_t on_d
 evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, int32_t on_device) {
     if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
     size_t bytes = sizeof(double) * c->NF;
+    double* dst = (c->prec == EVFDLB_FP32) ? c->scratch : (double*)c->state[0];
     evfdlb_status s;
-    if ((s = copy_in(c, c->state[0], F, bytes, on_device)) != EVFDLB_OK) return s;
-    if ((s = copy_in(c, c->state[0] + c->NF, G, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_in(c, dst, F, bytes, on_device)) != EVFDLB_OK) return s;
+    if ((s = copy_in(c, dst + c->NF, G, bytes, on_device)) != EVFDLB_OK) return s;
+    if (c->prec == EVFDLB_FP32) {   // round to the state precision
+        launch_convert_to_f32(c->user, c->scratch, (float*)c->state[0], 2 * c->NF);
+        TRY_CUDA(cudaGetLastError());
+    }
     TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
-    launch_sums((int)c->items_h.size(), c->user, c->slabs, c->items, c->tables, c->state[0], c->mom[0], c->NF,
-                c->NN, c->err);
+    launch_sums_p(c->prec, (int)c->items_h.size(), c->user, c->slabs, c->items, c->tables, c->rtables, c->state[0],
+                  c->mom[0], c->NF, c->NN, c->err);
     TRY_CUDA(cudaGetLastError());
     c->poisoned = false;
     s = check_device(c);
@@ -414,8 +450,9 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
 evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_device) {
     if (!c || !RF || !RG) return EVFDLB_E_INVALID_ARG;
     if (!c->have_state) return EVFDLB_E_STATE;
-    launch_stage((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->taps, c->state[0],
-                 nullptr, c->scratch, c->mom[0], nullptr, c->NF, c->NN, 0.0, 1.0, 1, c->Z, c->err);
+    launch_stage_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables,
+                   c->taps, c->rtaps, c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr, c->NF, c->NN,
+                   0.0, 1.0, 1, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
     size_t bytes = sizeof(double) * c->NF;
     evfdlb_status s;
@@ -428,8 +465,8 @@ evfdlb_status evfdlb_fields(evfdlb_ctx* c, double* fields, int32_t on_device) {
     if (!c || !fields) return EVFDLB_E_INVALID_ARG;
     if (!c->have_state) return EVFDLB_E_STATE;
     double* buf = c->scratch;
-    launch_fields((int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->taps, c->mom[0], buf,
-                  c->NN, c->Z, c->err);
+    launch_fields_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->rtables, c->taps,
+                    c->rtaps, c->mom[0], buf, c->NN, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
     evfdlb_status s = copy_out(c, fields, buf, sizeof(double) * EVFDLB_NFIELDS * c->NN, on_device);
     if (s != EVFDLB_OK) return s;

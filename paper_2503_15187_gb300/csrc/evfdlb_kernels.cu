@@ -1,4 +1,5 @@
-// evfdlb_kernels.cu -- sm_103a kernels of libevfdlb (FP64 forward path).
+// evfdlb_kernels.cu -- sm_103a kernels of libevfdlb (forward path, FP64 and
+// FP32 variants).
 //
 // One launch of `stage_kernel` evaluates the right-hand side of the EV1
 // equations (Busuioc & Sofonea, arXiv:2503.15187, Eqs. (ev1) and
@@ -24,8 +25,20 @@
 // FP64 is the GB300's scarcest pipe (about 1/60 of FP32), so the design
 // minimises FP64 instructions: one division per WENO face, per-node work
 // shared by all velocities, no re-reads of the state.
+//
+// Precision variants.  The kernels are templated on R, the type of the stored
+// distributions and of the per-velocity work (WENO faces, Hermite analysis and
+// synthesis, the force convolution, the coefficient recurrences and the RK
+// combine).  R = double is the plain FP64 form.  R = float is the FP32
+// variant; it keeps FP64 for the Fischer-Methfessel average, chi and the
+// transport coefficients (the equation-of-state part, which is sensitive near
+// liquid packing), the gradients, and the per-node sums of the conserved
+// moments (mass, momentum, energy); the heat-flux sums are FP32.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
+#include <type_traits>
 
 #include "evfdlb_internal.h"
 
@@ -40,36 +53,57 @@ __device__ __forceinline__ int gidx(int i, int nx, int bc) {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout of one CTA (doubles), sized for (Q, Z, M).
+// Shared-memory layout of one CTA, sized for (Q, Z, M): an FP64 block of node
+// fields followed by an R block of velocity-space data.
 // ---------------------------------------------------------------------------
+template <typename R>
 struct Smem {
-    double *P, *S;      // analysis / synthesis tables [Q*Q] each
     double *N;          // n on nodes [i0 - M, i0 + Z + M)
     double *U, *T;      // u, T on nodes [i0 - 2, i0 + Z + 2)
     double *X, *Chi;    // X = n^2 chi T and chi on the same nodes
     double *Sc;         // per-node scalars [kNumScalars][Z]
-    double *C;          // coefficients [2][Q][Z]
-    double *A;          // analysis [2][Q][Z]
-    double *F;          // state tile with halo [2][Q][Z+6]
-    double *Face;       // WENO face values [2][Q][Z+1]
+    R *P, *S;           // analysis / synthesis tables [Q*Q] each
+    R *Nr;              // n halo in R (the force convolution), aliases N for FP64
+    R *Scr;             // nu and F1 in R, [2][Z]
+    R *C;               // coefficients [2][Q][Z]
+    R *A;               // analysis [2][Q][Z]
+    R *F;               // state tile with halo [2][Q][Z+6]
+    R *Face;            // WENO face values [2][Q][Z+1]
 };
 
-__host__ __device__ inline size_t smem_doubles(int Q, int Z, int M) {
-    return (size_t)2 * Q * Q + (Z + 2 * M) + 4 * (Z + 4) + kNumScalars * Z + 2 * (size_t)Q * Z +
-           2 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1);
+// Length of the R copy of the density halo, rounded up to an even count so
+// that the blocks after it stay 8-byte aligned (init_kernel stores doubles in
+// the coefficient block).
+__host__ __device__ inline size_t nr_len(int Z, int M) { return ((size_t)(Z + 2 * M) + 1) & ~(size_t)1; }
+
+template <typename R>
+__host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
+    size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z;
+    size_t nr = 2 * (size_t)Q * Q + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
+                4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1);
+    return nd * sizeof(double) + nr * sizeof(R);
 }
 
-__device__ inline Smem carve(double* base, int Q, int Z, int M) {
-    Smem s;
-    s.P = base;
-    s.S = s.P + Q * Q;
-    s.N = s.S + Q * Q;
+template <typename R>
+__device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
+    Smem<R> s;
+    s.N = base;
     s.U = s.N + (Z + 2 * M);
     s.T = s.U + (Z + 4);
     s.X = s.T + (Z + 4);
     s.Chi = s.X + (Z + 4);
     s.Sc = s.Chi + (Z + 4);
-    s.C = s.Sc + kNumScalars * Z;
+    R* r = reinterpret_cast<R*>(s.Sc + kNumScalars * Z);
+    s.P = r;
+    s.S = s.P + Q * Q;
+    if constexpr (std::is_same<R, double>::value) {
+        s.Nr = s.N;
+        s.Scr = s.S + Q * Q;
+    } else {
+        s.Nr = s.S + Q * Q;
+        s.Scr = s.Nr + nr_len(Z, M);
+    }
+    s.C = s.Scr + 2 * Z;
     s.A = s.C + 2 * Q * Z;
     s.F = s.A + 2 * Q * Z;
     s.Face = s.F + 2 * Q * (Z + 6);
@@ -84,16 +118,19 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 // Phase 0: stage the tables, the density halo, u/T near the tile and the
 // state tile (+-3 nodes for WENO-5) into shared memory.
 // ---------------------------------------------------------------------------
-__device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                                 const double* __restrict__ tables, const double* __restrict__ mom,
-                                 long long NN) {
+template <typename R>
+__device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                 const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
     const int Q = sd.Q, M = sd.M, nx = sd.nx, bc = sd.bc;
     TableLayout L(Q);
-    const double* tab = tables + sd.tab_off;
+    const R* tab = rtab + sd.tab_off;
     for (int t = threadIdx.x; t < 2 * Q * Q; t += blockDim.x) s.P[t] = tab[L.P + t];  // P then S
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x)
-        s.N[t] = S0[gidx(it.i0 - M + t, nx, bc)];
+    for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {
+        double n = S0[gidx(it.i0 - M + t, nx, bc)];
+        s.N[t] = n;
+        if constexpr (!std::is_same<R, double>::value) s.Nr[t] = (R)n;
+    }
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
     const double* S2 = mom + MOM_S2 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
@@ -107,8 +144,9 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     }
 }
 
-__device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                                const double* __restrict__ src, long long NF) {
+template <typename R>
+__device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                const R* __restrict__ src, long long NF) {
     const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
     const int cols = it.nz + 6;
     for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
@@ -122,12 +160,13 @@ __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Sm
 // ---------------------------------------------------------------------------
 // Phases 1-2: node fields of the tile.
 // ---------------------------------------------------------------------------
-__device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                            const double* __restrict__ taps, const double* __restrict__ mom,
-                            long long NN, unsigned* err, double* fields_out) {
+template <typename R>
+__device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                            const double* __restrict__ taps, const R* __restrict__ rtaps,
+                            const double* __restrict__ mom, long long NN, unsigned* err, double* fields_out) {
     const int M = sd.M, m = sd.m;
-    const double* ftap = taps + sd.tap_off;          // force [2M+1]
-    const double* mtap = ftap + 2 * M + 1;           // Fischer-Methfessel [2m+1]
+    const R* ftap = rtaps + sd.tap_off;                  // force [2M+1]
+    const double* mtap = taps + sd.tap_off + 2 * M + 1;  // Fischer-Methfessel [2m+1]
     // Fischer-Methfessel average (Sec. II.A), chi (Eq. (carnstar)) and
     // X = n^2 chi T on nodes i0-2 .. i0+nz+1.  Under the outflow rule a ghost
     // node copies every node field of the nearest interior node, so the
@@ -168,9 +207,10 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem& 
         double X = s.X[c], chi = s.Chi[c];
         double A = dX / X, B = dT / T;
         // self-consistent force, Eq. (F1), Simpson taps over |j| <= M
-        const double* nn = s.N + (t + M);
-        double f1 = 0.0;
-        for (int j = -M; j <= M; ++j) f1 = fma(ftap[j + M], nn[j], f1);
+        const R* nn = s.Nr + (t + M);
+        R f1r = 0;
+        for (int j = -M; j <= M; ++j) f1r = fma(ftap[j + M], nn[j], f1r);
+        double f1 = (double)f1r;
         // heat flux from the raw sums: q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
         double q = 0.5 * (S3[i] - 3.0 * u * S2[i] + 3.0 * u * u * S1[i] - u * u * u * S0[i]) + G1[i] - u * G0[i];
         // transport, Eqs. (viscosity), (tau), (prandtl)
@@ -191,6 +231,8 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem& 
         sc[SC_A * Z + t] = A;
         sc[SC_B * Z + t] = B;
         sc[SC_D * Z + t] = dU;
+        s.Scr[t] = (R)nu;
+        s.Scr[Z + t] = f1r;
         if (!(n > 0.0) || !(T > 0.0)) {
             atomicOr(err, (finite(n) && finite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
         } else if (!finite(f1) || !finite(nu) || !finite(q) || !finite(A) || !finite(B)) {
@@ -218,12 +260,14 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem& 
 //      c2 = 3/5 K D T,        c3 = nu kq/5 + 3/10 K B T^2
 //   G: c0 = nu n T + 2/5 K T D,  c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
 //      c2 = 3/5 K T^2 D,         c3 = nu kq T/5 + 3/10 K T^3 B
+// The four constants are formed in FP64; the recurrence runs in R.
 // ---------------------------------------------------------------------------
-__device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                                         const double* __restrict__ tables) {
+template <typename R>
+__device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                         const R* __restrict__ rtab) {
     const int Q = sd.Q;
     TableLayout L(Q);
-    const double* tab = tables + sd.tab_off;
+    const R* tab = rtab + sd.tab_off;
     for (int e = threadIdx.x; e < 2 * it.nz; e += blockDim.x) {
         int t = e % it.nz, d = e / it.nz;
         const double* sc = s.Sc;
@@ -242,15 +286,16 @@ __device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it,
             c2 = 0.6 * K * T * T * D;
             c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
         }
-        double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
-        double* out = s.C + (size_t)d * Q * Z + t;
+        const R rc0 = (R)c0, rc1 = (R)c1, rc2 = (R)c2, rc3 = (R)c3, ru = (R)u, Tm1 = (R)(T - 1.0);
+        R m0 = 1, m1 = 0, m2 = 0, m3 = 0;
+        R* out = s.C + (size_t)d * Q * Z + t;
         for (int l = 0; l < Q; ++l) {
-            double c = c0 * m0;
-            c = fma(c1 * tab[L.r1 + l], m1, c);
-            c = fma(c2 * tab[L.r2 + l], m2, c);
-            c = fma(c3 * tab[L.r3 + l], m3, c);
+            R c = rc0 * m0;
+            c = fma(rc1 * tab[L.r1 + l], m1, c);
+            c = fma(rc2 * tab[L.r2 + l], m2, c);
+            c = fma(rc3 * tab[L.r3 + l], m3, c);
             out[l * Z] = c;
-            double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
+            R mn = fma(ru * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
             m3 = m2;
             m2 = m1;
             m1 = m0;
@@ -261,15 +306,16 @@ __device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it,
 
 // Phase 3b: analysis a_l = sum_j psi_l(xi_j) h_j, l <= Q-2 (the force needs
 // a_0 .. a_{Q-2}; the l = Q-1 term meets psi_Q(xi_k) = 0).
-__device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z) {
+template <typename R>
+__device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     const int per_d = (Q - 1) * nz;
     for (int e = threadIdx.x; e < 2 * per_d; e += blockDim.x) {
         int d = e / per_d, r = e % per_d;
         int l = r / nz, t = r % nz;
-        const double* Pl = s.P + l * Q;
-        const double* h = s.F + (size_t)d * Q * W + (t + 3);
-        double acc = 0.0;
+        const R* Pl = s.P + l * Q;
+        const R* h = s.F + (size_t)d * Q * W + (t + 3);
+        R acc = 0;
         for (int j = 0; j < Q; ++j) acc = fma(Pl[j], h[j * W], acc);
         s.A[((size_t)d * Q + l) * Z + t] = acc;
     }
@@ -278,56 +324,98 @@ __device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem& s, 
 // WENO-5 (Jiang & Shu) value at the face between v2 and v3, upwind side v0..v2.
 // The nonlinear weights omega_r = (d_r / e_r) / sum_s (d_s / e_s),
 // e_r = (eps + beta_r)^2, are formed with a single division.
-__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4, double eps) {
-    const double k6 = 1.0 / 6.0, k1312 = 13.0 / 12.0;
-    double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * k6;
-    double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * k6;
-    double q2 = (2.0 * v2 + 5.0 * v3 - v4) * k6;
-    double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
-    double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
-    double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
-    double e0 = eps + fma(k1312 * t0, t0, 0.25 * s0 * s0);
-    double e1 = eps + fma(k1312 * t1, t1, 0.25 * s1 * s1);
-    double e2 = eps + fma(k1312 * t2, t2, 0.25 * s2 * s2);
+template <typename R>
+__device__ __forceinline__ R weno5(R v0, R v1, R v2, R v3, R v4, R eps) {
+    const R k6 = R(1) / R(6), k1312 = R(13) / R(12), qr = R(0.25);
+    R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * k6;
+    R q1 = (-v1 + R(5) * v2 + R(2) * v3) * k6;
+    R q2 = (R(2) * v2 + R(5) * v3 - v4) * k6;
+    R t0 = v0 - R(2) * v1 + v2, s0 = v0 - R(4) * v1 + R(3) * v2;
+    R t1 = v1 - R(2) * v2 + v3, s1 = v1 - v3;
+    R t2 = v2 - R(2) * v3 + v4, s2 = R(3) * v2 - R(4) * v3 + v4;
+    R e0 = eps + fma(k1312 * t0, t0, qr * s0 * s0);
+    R e1 = eps + fma(k1312 * t1, t1, qr * s1 * s1);
+    R e2 = eps + fma(k1312 * t2, t2, qr * s2 * s2);
     e0 *= e0;
     e1 *= e1;
     e2 *= e2;
-    double a0 = 0.1 * (e1 * e2), a1 = 0.6 * (e0 * e2), a2 = 0.3 * (e0 * e1);
+    R a0 = R(0.1) * (e1 * e2), a1 = R(0.6) * (e0 * e2), a2 = R(0.3) * (e0 * e1);
     return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
 }
 
 // Phase 3c: face values h_{i-1/2} for faces f = 0..nz (face f lies between
 // tile nodes f-1 and f), upwind by the sign of xi_k.
-__device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                      const double* __restrict__ tables) {
+template <typename R>
+__device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                      const R* __restrict__ rtab) {
     const int Q = sd.Q, W = Z + 6, nf = it.nz + 1;
     TableLayout L(Q);
-    const double* xi = tables + sd.tab_off + L.xi;
+    const R* xi = rtab + sd.tab_off + L.xi;
+    const R eps = (R)sd.weno_eps;
     for (int e = threadIdx.x; e < 2 * Q * nf; e += blockDim.x) {
         int f = e % nf, r = e / nf;
         int k = r % Q, d = r / Q;
-        const double* h = s.F + (size_t)(d * Q + k) * W;
-        double x = xi[k], v;
-        if (x > 0.0) v = weno5(h[f], h[f + 1], h[f + 2], h[f + 3], h[f + 4], sd.weno_eps);
-        else if (x < 0.0) v = weno5(h[f + 5], h[f + 4], h[f + 3], h[f + 2], h[f + 1], sd.weno_eps);
-        else v = 0.0;
+        const R* h = s.F + (size_t)(d * Q + k) * W;
+        R x = xi[k], v;
+        if (x > R(0)) v = weno5<R>(h[f], h[f + 1], h[f + 2], h[f + 3], h[f + 4], eps);
+        else if (x < R(0)) v = weno5<R>(h[f + 5], h[f + 4], h[f + 3], h[f + 2], h[f + 1], eps);
+        else v = 0;
         s.Face[(size_t)(d * Q + k) * (Z + 1) + f] = v;
     }
 }
 
 // Phase 4: add the force term F1 sqrt(l) a_{l-1} to the coefficients
 // (d/dxi [omega psi_{l-1}] = -sqrt(l) omega psi_l).
-__device__ void add_force(const SlabDesc& sd, const WorkItem& it, const Smem& s, int Z,
-                          const double* __restrict__ tables) {
+template <typename R>
+__device__ void add_force(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                          const R* __restrict__ rtab) {
     const int Q = sd.Q, nz = it.nz;
     TableLayout L(Q);
-    const double* r1 = tables + sd.tab_off + L.r1;
+    const R* r1 = rtab + sd.tab_off + L.r1;
     for (int e = threadIdx.x; e < 2 * (Q - 1) * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
         int l = 1 + r % (Q - 1), d = r / (Q - 1);
-        double f1 = s.Sc[SC_FORCE * Z + t];
+        R f1 = s.Scr[Z + t];
         s.C[((size_t)d * Q + l) * Z + t] =
             fma(f1 * r1[l], s.A[((size_t)d * Q + l - 1) * Z + t], s.C[((size_t)d * Q + l) * Z + t]);
+    }
+}
+
+// One raw moment sum of one node from a column h[k * stride] (k < Q).  The
+// conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
+// (heat flux) in R.
+template <typename R>
+__device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
+                                             const double* __restrict__ xi, const R* __restrict__ rxi) {
+    const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
+    if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
+        which == MOM_G0) {
+        double acc = 0.0;
+        for (int k = 0; k < Q; ++k) {
+            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
+            acc = fma(wgt, (double)h[k * stride], acc);
+        }
+        return acc;
+    }
+    R racc = 0;
+    for (int k = 0; k < Q; ++k) {
+        R x = rxi[k], wgt = (p == 1) ? x : x * x * x;
+        racc = fma(wgt, h[k * stride], racc);
+    }
+    return (double)racc;
+}
+
+// Raw moment sums of the tile held in s.F (columns 3 .. nz+2).
+template <typename R>
+__device__ void tile_moment_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                 const double* __restrict__ xi, const R* __restrict__ rxi,
+                                 double* __restrict__ mom_out, long long NN) {
+    const int Q = sd.Q, W = Z + 6, nz = it.nz;
+    for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
+        int t = e % nz, which = e / nz;
+        int d = which >= MOM_G0 ? 1 : 0;
+        const R* h = s.F + (size_t)d * Q * W + t + 3;
+        mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xi, rxi);
     }
 }
 
@@ -335,53 +423,54 @@ __device__ void add_force(const SlabDesc& sd, const WorkItem& it, const Smem& s,
 // Kernels
 // ---------------------------------------------------------------------------
 
-// mode 0: out = alpha base + beta (src + dt R);  mode 1: out = R.
+// mode 0: out = alpha base + beta (src + dt R);  mode 1: rhs_out = R (FP64).
+template <typename R>
 __global__ void __launch_bounds__(kThreads)
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-             const double* __restrict__ tables, const double* __restrict__ taps,
-             const double* __restrict__ src, const double* base, double* out,
+             const double* __restrict__ tables, const R* __restrict__ rtab,
+             const double* __restrict__ taps, const R* __restrict__ rtaps,
+             const R* __restrict__ src, const R* base, R* out, double* rhs_out,
              const double* __restrict__ mom_in, double* __restrict__ mom_out,
              long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
     extern __shared__ double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    Smem s = carve(smem, Q, Z, sd.M);
+    Smem<R> s = carve<R>(smem, Q, Z, sd.M);
 
-    load_node_inputs(sd, it, s, Z, tables, mom_in, NN);
-    load_state_tile(sd, it, s, Z, src, NF);
+    load_node_inputs<R>(sd, it, s, Z, rtab, mom_in, NN);
+    load_state_tile<R>(sd, it, s, Z, src, NF);
     __syncthreads();
-    node_fields(sd, it, s, Z, taps, mom_in, NN, err, nullptr);
+    node_fields<R>(sd, it, s, Z, taps, rtaps, mom_in, NN, err, nullptr);
     __syncthreads();
-    equilibrium_coefficients(sd, it, s, Z, tables);
-    analysis(sd, it, s, Z);
-    faces(sd, it, s, Z, tables);
+    equilibrium_coefficients<R>(sd, it, s, Z, rtab);
+    analysis<R>(sd, it, s, Z);
+    faces<R>(sd, it, s, Z, rtab);
     __syncthreads();
-    add_force(sd, it, s, Z, tables);
+    add_force<R>(sd, it, s, Z, rtab);
     __syncthreads();
 
     // Phase 5: synthesis, advection, relaxation and the RK stage.
     TableLayout L(Q);
-    const double* xi = tables + sd.tab_off + L.xi;
-    const double dt = sd.dt;
+    const R* xi = rtab + sd.tab_off + L.xi;
+    const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
     for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
         int k = r % Q, d = r / Q;
-        const double* Sk = s.S + k * Q;
-        const double* c = s.C + (size_t)d * Q * Z + t;
-        double syn = 0.0;
+        const R* Sk = s.S + k * Q;
+        const R* c = s.C + (size_t)d * Q * Z + t;
+        R syn = 0;
         for (int l = 0; l < Q; ++l) syn = fma(Sk[l], c[l * Z], syn);
-        const double* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
-        double h = s.F[(size_t)(d * Q + k) * W + t + 3];
-        double R = fma(-xi[k] * sd.inv_dx, fc[t + 1] - fc[t], fma(-s.Sc[SC_NU * Z + t], h, syn));
+        const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
+        R h = s.F[(size_t)(d * Q + k) * W + t + 3];
+        R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
         long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
-        double o;
         if (mode == 1) {
-            o = R;
-        } else {
-            o = beta * fma(dt, R, h);
-            if (alpha != 0.0) o = fma(alpha, base[g], o);
+            rhs_out[g] = (double)Rv;
+            continue;
         }
+        R o = rbeta * fma(dt, Rv, h);
+        if (alpha != 0.0) o = fma(ralpha, base[g], o);
         out[g] = o;
         s.F[(size_t)(d * Q + k) * W + t + 3] = o;
     }
@@ -389,35 +478,28 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     __syncthreads();
 
     // Phase 6: raw moment sums of the new stage for the next stage's node fields.
-    for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
-        int t = e % nz, which = e / nz;
-        int d = which >= MOM_G0 ? 1 : 0;
-        int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
-        const double* h = s.F + (size_t)d * Q * W + t + 3;
-        double acc = 0.0;
-        for (int k = 0; k < Q; ++k) {
-            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
-            acc = fma(wgt, h[k * W], acc);
-        }
-        mom_out[which * NN + sd.node_off + it.i0 + t] = acc;
-    }
+    tile_moment_sums<R>(sd, it, s, Z, tables + sd.tab_off + L.xi, xi, mom_out, NN);
 }
 
-// Projected Maxwellian pair (F_MB, T F_MB) from node fields:
-// F_k = sum_l S_kl n m_l(u, T), G_k = T F_k; also writes the raw moment sums.
+// Projected Maxwellian pair (F_MB, T F_MB) from node fields, formed in FP64 and
+// stored as R: F_k = sum_l S_kl n m_l(u, T), G_k = T F_k; also writes the raw
+// moment sums of the stored state.
+template <typename R>
 __global__ void __launch_bounds__(kThreads)
 init_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-            const double* __restrict__ tables, const double* __restrict__ n0,
-            const double* __restrict__ u0, const double* __restrict__ T0, double* state,
+            const double* __restrict__ tables, const R* __restrict__ rtab, const double* __restrict__ n0,
+            const double* __restrict__ u0, const double* __restrict__ T0, R* state,
             double* mom, long long NF, long long NN, int Z, unsigned* err) {
     extern __shared__ double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    Smem s = carve(smem, Q, Z, sd.M);
+    Smem<R> s = carve<R>(smem, Q, Z, sd.M);
     TableLayout L(Q);
     const double* tab = tables + sd.tab_off;
-    for (int t = threadIdx.x; t < 2 * Q * Q; t += blockDim.x) s.P[t] = tab[L.P + t];
+    // FP64 coefficients [Q][Z] in the R blocks C and A (2 Q Z + 2 Q Z R values
+    // hold at least Q Z doubles for either R)
+    double* coef = reinterpret_cast<double*>(s.C);
     for (int t = threadIdx.x; t < nz; t += blockDim.x) {
         long long o = sd.node_off + it.i0 + t;
         double n = n0[o], u = u0[o], T = T0[o];
@@ -426,77 +508,65 @@ init_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ ite
         s.Sc[SC_T * Z + t] = T;
         double m0 = 1.0, m1 = 0.0, Tm1 = T - 1.0;
         for (int l = 0; l < Q; ++l) {
-            s.C[l * Z + t] = n * m0;
+            coef[l * Z + t] = n * m0;
             double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
             m1 = m0;
             m0 = mn;
         }
     }
     __syncthreads();
-    const double* xi = tab + L.xi;
     for (int e = threadIdx.x; e < Q * nz; e += blockDim.x) {
         int t = e % nz, k = e / nz;
         double acc = 0.0;
-        for (int l = 0; l < Q; ++l) acc = fma(s.S[k * Q + l], s.C[l * Z + t], acc);
+        for (int l = 0; l < Q; ++l) acc = fma(tab[L.S + k * Q + l], coef[l * Z + t], acc);
         double gval = s.Sc[SC_T * Z + t] * acc;
         long long g = sd.f_off + (long long)k * sd.nx + it.i0 + t;
-        state[g] = acc;
-        state[NF + g] = gval;
-        s.F[(size_t)k * W + t + 3] = acc;
-        s.F[(size_t)(Q + k) * W + t + 3] = gval;
+        R fa = (R)acc, ga = (R)gval;
+        state[g] = fa;
+        state[NF + g] = ga;
+        s.F[(size_t)k * W + t + 3] = fa;
+        s.F[(size_t)(Q + k) * W + t + 3] = ga;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
-        int t = e % nz, which = e / nz;
-        int d = which >= MOM_G0 ? 1 : 0;
-        int p = (which >= MOM_G0) ? which - MOM_G0 : which;
-        const double* h = s.F + (size_t)d * Q * W + t + 3;
-        double acc = 0.0;
-        for (int k = 0; k < Q; ++k) {
-            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
-            acc = fma(wgt, h[k * W], acc);
-        }
-        mom[which * NN + sd.node_off + it.i0 + t] = acc;
-    }
+    tile_moment_sums<R>(sd, it, s, Z, tab + L.xi, rtab + sd.tab_off + L.xi, mom, NN);
 }
 
-// Raw moment sums of an arbitrary state (after set_state).
+// Raw moment sums of an arbitrary state (after set_state); same precision rule
+// as the stage kernel.
+template <typename R>
 __global__ void __launch_bounds__(kThreads)
 sums_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-            const double* __restrict__ tables, const double* __restrict__ state, double* mom,
-            long long NF, long long NN, unsigned* err) {
+            const double* __restrict__ tables, const R* __restrict__ rtab, const R* __restrict__ state,
+            double* mom, long long NF, long long NN, unsigned* err) {
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q;
     TableLayout L(Q);
     const double* xi = tables + sd.tab_off + L.xi;
+    const R* rxi = rtab + sd.tab_off + L.xi;
     for (int e = threadIdx.x; e < kNumMoments * it.nz; e += blockDim.x) {
         int t = e % it.nz, which = e / it.nz;
         int d = which >= MOM_G0 ? 1 : 0;
-        int p = (which >= MOM_G0) ? which - MOM_G0 : which;
-        const double* h = state + d * NF + sd.f_off + it.i0 + t;
-        double acc = 0.0;
-        for (int k = 0; k < Q; ++k) {
-            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
-            acc = fma(wgt, h[(long long)k * sd.nx], acc);
-        }
+        const R* h = state + d * NF + sd.f_off + it.i0 + t;
+        double acc = moment_sum<R>(which, Q, h, sd.nx, xi, rxi);
         if (!finite(acc)) atomicOr(err, ERR_NONFINITE);
         mom[which * NN + sd.node_off + it.i0 + t] = acc;
     }
 }
 
 // Node fields of the current state (diagnostic).
+template <typename R>
 __global__ void __launch_bounds__(kThreads)
 fields_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-              const double* __restrict__ tables, const double* __restrict__ taps,
+              const R* __restrict__ rtab, const double* __restrict__ taps, const R* __restrict__ rtaps,
               const double* __restrict__ mom, double* fields, long long NN, int Z, unsigned* err) {
     extern __shared__ double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
-    Smem s = carve(smem, sd.Q, Z, sd.M);
-    load_node_inputs(sd, it, s, Z, tables, mom, NN);
+    Smem<R> s = carve<R>(smem, sd.Q, Z, sd.M);
+    load_node_inputs<R>(sd, it, s, Z, rtab, mom, NN);
     __syncthreads();
-    node_fields(sd, it, s, Z, taps, mom, NN, err, fields);
+    node_fields<R>(sd, it, s, Z, taps, rtaps, mom, NN, err, fields);
 }
 
 // n, u, T, q per node from the raw sums.
@@ -553,53 +623,124 @@ totals_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ tap
     }
 }
 
-// ---------------------------------------------------------------------------
-// Host-side launch helpers (called from the C-ABI layer).
-// ---------------------------------------------------------------------------
-size_t stage_smem_bytes(int Q, int Z, int M) { return smem_doubles(Q, Z, M) * sizeof(double); }
-
-cudaError_t configure_kernels(size_t smem_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fields_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+// Element-wise precision conversion (state copies in and out of FP32 contexts).
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ in, B* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
 }
 
-// Raises (never lowers) the stage kernel's dynamic shared-memory limit on the
-// current device to at least smem_bytes.
+// ---------------------------------------------------------------------------
+// Host-side launch helpers (called from the C-ABI layer).  `prec` selects the
+// instantiation: EVFDLB_FP64 (R = double) or EVFDLB_FP32 (R = float); the R
+// tables and taps are the FP64 ones for FP64 and float copies for FP32.
+// ---------------------------------------------------------------------------
+size_t stage_smem_bytes(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M); }
+
+size_t stage_smem_bytes_p(int prec, int Q, int Z, int M) {
+    return prec == EVFDLB_FP32 ? smem_bytes_t<float>(Q, Z, M) : smem_bytes_t<double>(Q, Z, M);
+}
+
+template <typename R>
+static cudaError_t configure_t(size_t smem_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(init_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fields_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+cudaError_t configure_kernels_p(int prec, size_t smem_bytes) {
+    return prec == EVFDLB_FP32 ? configure_t<float>(smem_bytes) : configure_t<double>(smem_bytes);
+}
+
+cudaError_t configure_kernels(size_t smem_bytes) { return configure_t<double>(smem_bytes); }
+
+// Raises (never lowers) the FP64 stage kernel's dynamic shared-memory limit on
+// the current device to at least smem_bytes.
 cudaError_t ensure_stage_smem(size_t smem_bytes) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, stage_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_kernel<double>);
     if (e != cudaSuccess) return e;
     if ((size_t)a.maxDynamicSharedSizeBytes >= smem_bytes) return cudaSuccess;
-    return cudaFuncSetAttribute(stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return cudaFuncSetAttribute(stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
+void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                    const WorkItem* items, const double* tables, const void* rtab, const double* taps,
+                    const void* rtaps, const void* src, const void* base, void* out, double* rhs_out,
+                    const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
+                    int mode, int Z, unsigned* err) {
+    if (prec == EVFDLB_FP32)
+        stage_kernel<float><<<nitems, kThreads, smem, st>>>(
+            slabs, items, tables, (const float*)rtab, taps, (const float*)rtaps, (const float*)src,
+            (const float*)base, (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+    else
+        stage_kernel<double><<<nitems, kThreads, smem, st>>>(
+            slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps, (const double*)src,
+            (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+}
+
+// FP64 stage (mode 0 writes out; mode 1 writes the right-hand side to out).
 void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                   const double* tables, const double* taps, const double* src, const double* base,
                   double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
                   double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, taps, src, base, out, mom_in, mom_out,
-                                                 NF, NN, alpha, beta, mode, Z, err);
+    stage_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, tables, tables, taps, taps, src, base, out,
+                                                         out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
-void launch_init(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                 const double* tables, const double* n0, const double* u0, const double* T0,
-                 double* state, double* mom, long long NF, long long NN, int Z, unsigned* err) {
-    init_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, n0, u0, T0, state, mom, NF, NN, Z, err);
+void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                   const WorkItem* items, const double* tables, const void* rtab, const double* n0,
+                   const double* u0, const double* T0, void* state, double* mom, long long NF, long long NN, int Z,
+                   unsigned* err) {
+    if (prec == EVFDLB_FP32)
+        init_kernel<float><<<nitems, kThreads, smem, st>>>(slabs, items, tables, (const float*)rtab, n0, u0, T0,
+                                                           (float*)state, mom, NF, NN, Z, err);
+    else
+        init_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, tables, (const double*)rtab, n0, u0, T0,
+                                                            (double*)state, mom, NF, NN, Z, err);
+}
+
+void launch_sums_p(int prec, int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                   const double* tables, const void* rtab, const void* state, double* mom, long long NF,
+                   long long NN, unsigned* err) {
+    if (prec == EVFDLB_FP32)
+        sums_kernel<float><<<nitems, kThreads, 0, st>>>(slabs, items, tables, (const float*)rtab,
+                                                        (const float*)state, mom, NF, NN, err);
+    else
+        sums_kernel<double><<<nitems, kThreads, 0, st>>>(slabs, items, tables, (const double*)rtab,
+                                                         (const double*)state, mom, NF, NN, err);
 }
 
 void launch_sums(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                  const double* tables, const double* state, double* mom, long long NF, long long NN,
                  unsigned* err) {
-    sums_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, tables, state, mom, NF, NN, err);
+    launch_sums_p(EVFDLB_FP64, nitems, st, slabs, items, tables, tables, state, mom, NF, NN, err);
 }
 
-void launch_fields(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                   const double* tables, const double* taps, const double* mom, double* fields,
-                   long long NN, int Z, unsigned* err) {
-    fields_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, taps, mom, fields, NN, Z, err);
+void launch_fields_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                     const WorkItem* items, const void* rtab, const double* taps, const void* rtaps,
+                     const double* mom, double* fields, long long NN, int Z, unsigned* err) {
+    if (prec == EVFDLB_FP32)
+        fields_kernel<float><<<nitems, kThreads, smem, st>>>(slabs, items, (const float*)rtab, taps,
+                                                             (const float*)rtaps, mom, fields, NN, Z, err);
+    else
+        fields_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, (const double*)rtab, taps,
+                                                              (const double*)rtaps, mom, fields, NN, Z, err);
+}
+
+void launch_convert_to_f32(cudaStream_t st, const double* in, float* out, long long n) {
+    int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    if (blocks < 1) blocks = 1;
+    convert_kernel<double, float><<<blocks, 256, 0, st>>>(in, out, n);
+}
+
+void launch_convert_to_f64(cudaStream_t st, const float* in, double* out, long long n) {
+    int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    if (blocks < 1) blocks = 1;
+    convert_kernel<float, double><<<blocks, 256, 0, st>>>(in, out, n);
 }
 
 void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
