@@ -14,10 +14,16 @@ Contents
   construction (Sec. III.A), in numpy/scipy.
 * ``Oracle``: a ctypes wrapper around the C routines (moments, node fields,
   right-hand side, Shu-Osher RK3 steps, projected equilibria, totals).
+* Tangent-linear maps (``rhs_tl``, ``step_tl``, ``equilibrium_tl``,
+  ``trajectory_tl``): the same C source compiled over double complex
+  (``evfdlb_oracle_cs.c``) and evaluated by complex step, the reference for
+  the adjoint of the time step.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, identities, brute-force quadrature, textbook routines and the
-paper's printed critical temperature).
+paper's printed critical temperature) and, for the tangent-linear maps, by
+``tests/test_oracle_tangent.py`` (finite differences of the FP64 oracle with
+their h^2 convergence, linearised mass and momentum conservation).
 """
 from __future__ import annotations
 
@@ -32,6 +38,7 @@ from numpy.polynomial.hermite_e import hermegauss
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "evfdlb_oracle.c")
+_SRC_CS = os.path.join(_HERE, "evfdlb_oracle_cs.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 NFIELDS = 16
@@ -42,12 +49,14 @@ PI = np.pi
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/_build/liborc.so (gcc, -O2, IEEE FP)."""
+    """Compile the C oracle into oracle/_build/liborc.so (gcc, -O2, IEEE FP):
+    the FP64 routines and their complex-step twins from the same source."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CS))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_CS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -82,6 +91,10 @@ def _load():
         _lib.orc_advect_row.argtypes = [P, d, vp, vp]
         _lib.orc_step.argtypes = [P, vp, vp, i]
         _lib.orc_totals.argtypes = [P, vp, vp, vp]
+        _lib.orc_cs_moments.argtypes = [P, vp, vp, vp, vp, vp, vp]
+        _lib.orc_cs_equilibrium.argtypes = [P, vp, vp, vp, vp, vp]
+        _lib.orc_cs_rhs.argtypes = [P, vp, vp, vp, vp, vp]
+        _lib.orc_cs_step.argtypes = [P, vp, vp, i]
     return _lib
 
 
@@ -92,7 +105,7 @@ class _Params(ctypes.Structure):
                 ("rcut", ctypes.c_double), ("bc", ctypes.c_int), ("relax", ctypes.c_int),
                 ("weno_eps", ctypes.c_double), ("xi", ctypes.c_void_p),
                 ("w", ctypes.c_void_p), ("nq", ctypes.c_int), ("zq", ctypes.c_void_p),
-                ("wq", ctypes.c_void_p)]
+                ("wq", ctypes.c_void_p), ("phi_tl", ctypes.c_double)]
 
 
 # --------------------------------------------------------------------------
@@ -229,7 +242,7 @@ class Oracle:
         self._p = _Params(setup.nz, setup.Q, setup.dz, setup.dt, setup.sigma, setup.phi,
                           setup.gamma, setup.rcut, setup.bc, setup.relax, setup.weno_eps,
                           self.xi.ctypes.data, self.w.ctypes.data, setup.nq,
-                          self.zq.ctypes.data, self.wq.ctypes.data)
+                          self.zq.ctypes.data, self.wq.ctypes.data, 0.0)
         self.p = ctypes.byref(self._p)
 
     # scalar kernels -------------------------------------------------------
@@ -326,6 +339,64 @@ class Oracle:
         G = self._arr(G, (Q, nz)).copy()
         self.lib.orc_step(self.p, F.ctypes.data, G.ctypes.data, int(nsteps))
         return F, G
+
+    # tangent-linear maps by complex step ---------------------------------
+    # Each routine evaluates the oracle's own arithmetic at x + i h v
+    # (double complex build) and returns (f(x), J v) = (Re, Im / h); h is
+    # tiny, so J v is exact to rounding (Squire & Trapp 1998).
+    CS_H = 1e-30
+
+    def _c(self, x, dx, shape):
+        z = np.empty(shape, dtype=np.complex128)
+        z.real = np.asarray(x, dtype=np.float64).reshape(shape)
+        z.imag = (self.CS_H * np.asarray(dx, dtype=np.float64)).reshape(shape) if dx is not None else 0.0
+        return z
+
+    def _with_phi_tangent(self, dphi):
+        self._p.phi_tl = self.CS_H * float(dphi)
+
+    def rhs_tl(self, F, G, dF, dG, dphi=0.0):
+        """(RF, RG) and the tangent (dRF, dRG) of the right-hand side along
+        (dF, dG) and a change dphi of the well depth phi."""
+        nz, Q = self.s.nz, self.s.Q
+        Fc, Gc = self._c(F, dF, (Q, nz)), self._c(G, dG, (Q, nz))
+        RF = np.empty((Q, nz), dtype=np.complex128)
+        RG = np.empty((Q, nz), dtype=np.complex128)
+        fl = np.empty((NFIELDS, nz), dtype=np.complex128)
+        self._with_phi_tangent(dphi)
+        try:
+            self.lib.orc_cs_rhs(self.p, Fc.ctypes.data, Gc.ctypes.data, RF.ctypes.data,
+                                RG.ctypes.data, fl.ctypes.data)
+        finally:
+            self._with_phi_tangent(0.0)
+        return RF.real.copy(), RG.real.copy(), RF.imag / self.CS_H, RG.imag / self.CS_H
+
+    def step_tl(self, F, G, dF, dG, nsteps=1, dphi=0.0):
+        """nsteps RK3 steps and their tangent along (dF, dG, dphi)."""
+        nz, Q = self.s.nz, self.s.Q
+        Fc, Gc = self._c(F, dF, (Q, nz)), self._c(G, dG, (Q, nz))
+        self._with_phi_tangent(dphi)
+        try:
+            self.lib.orc_cs_step(self.p, Fc.ctypes.data, Gc.ctypes.data, int(nsteps))
+        finally:
+            self._with_phi_tangent(0.0)
+        return Fc.real.copy(), Gc.real.copy(), Fc.imag / self.CS_H, Gc.imag / self.CS_H
+
+    def equilibrium_tl(self, n, u, T, dn, du, dT):
+        """Projected Maxwellian pair and its tangent along (dn, du, dT)."""
+        nz, Q = self.s.nz, self.s.Q
+        nc, uc, Tc = self._c(n, dn, (nz,)), self._c(u, du, (nz,)), self._c(T, dT, (nz,))
+        F = np.empty((Q, nz), dtype=np.complex128)
+        G = np.empty((Q, nz), dtype=np.complex128)
+        self.lib.orc_cs_equilibrium(self.p, nc.ctypes.data, uc.ctypes.data, Tc.ctypes.data,
+                                    F.ctypes.data, G.ctypes.data)
+        return F.real.copy(), G.real.copy(), F.imag / self.CS_H, G.imag / self.CS_H
+
+    def trajectory_tl(self, n0, u0, T0, dn0, du0, dT0, nsteps, dphi=0.0):
+        """State after projecting (n0, u0, T0) and nsteps RK3 steps, and the
+        tangent of that state along (dn0, du0, dT0, dphi)."""
+        F, G, dF, dG = self.equilibrium_tl(n0, u0, T0, dn0, du0, dT0)
+        return self.step_tl(F, G, dF, dG, nsteps, dphi)
 
     def totals(self, F, G):
         """[mass, momentum, energy (incl. E_mf), E_mf]"""

@@ -25,6 +25,26 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Scalar type of everything that depends on the state.  The file is compiled
+ * twice: as plain FP64 (real = double, entry points orc_*), and with
+ * ORC_COMPLEX (real = double complex, entry points orc_cs_*) for
+ * complex-step differentiation (Squire & Trapp 1998): evaluating the same
+ * arithmetic at x + i h v gives the tangent-linear map J v = Im f / h to
+ * rounding, with no subtractive cancellation.  Nothing in the arithmetic
+ * differs between the two builds. */
+#ifdef ORC_COMPLEX
+#include <complex.h>
+typedef double _Complex real;
+#define R_SQRT csqrt
+#define ORC(name) orc_cs_##name
+#define ORC_CONST static
+#else
+typedef double real;
+#define R_SQRT sqrt
+#define ORC(name) orc_##name
+#define ORC_CONST
+#endif
+
 typedef struct {
     int nz;            /* grid nodes                                        */
     int Q;             /* velocity nodes (full-range Gauss-Hermite order)   */
@@ -42,6 +62,7 @@ typedef struct {
     int nq;            /* points of the projection rule                     */
     const double *zq;  /* [nq] nodes of a normalised Gauss-Hermite rule     */
     const double *wq;  /* [nq] its weights, sum 1                           */
+    double phi_tl;     /* complex-step build only: imaginary part of phi    */
 } orc_params;
 
 /* number of per-node fields returned by orc_node_fields */
@@ -65,7 +86,7 @@ static int gidx(const orc_params *p, int i)
 
 /* probabilists' Hermite polynomials He_0..He_L at x by their three-term
  * recurrence He_{l+1} = x He_l - l He_{l-1}. */
-static void hermite_all(int L, double x, double *he)
+static void hermite_all(int L, real x, real *he)
 {
     he[0] = 1.0;
     if (L >= 1) he[1] = x;
@@ -91,7 +112,7 @@ static double simpson_w(int j, int M, double dz)
  *   F1(x) = integral g(x'-x) n(x') dx',
  *   g(z) = 2 pi phi z              for |z| <  sigma,
  *        = 2 pi phi sigma^g z/|z|^g for |z| >= sigma.            */
-double orc_force_kernel(const orc_params *p, double z)
+ORC_CONST double orc_force_kernel(const orc_params *p, double z)
 {
     double az = fabs(z);
     if (az < p->sigma) return 2.0 * PI * p->phi * z;
@@ -102,7 +123,7 @@ double orc_force_kernel(const orc_params *p, double z)
  * mean-field energy of the F1 dynamics is (1/2) sum n Phi_F n.
  * READING: energy bookkeeping is not printed in the paper; Phi_F is the
  * unique even antiderivative of the Eq. (F1) kernel that vanishes at infinity. */
-double orc_force_potential(const orc_params *p, double z)
+ORC_CONST double orc_force_potential(const orc_params *p, double z)
 {
     double az = fabs(z), s = p->sigma, g = p->gamma;
     if (az < s) return PI * p->phi * (z * z - s * s * g / (g - 2.0));
@@ -113,7 +134,7 @@ double orc_force_potential(const orc_params *p, double z)
  * rho > sigma (Eq. (sutherland)):
  *   -2 pi phi sigma^2/(g-2)                for |z| < sigma,
  *   -2 pi phi sigma^g |z|^(2-g)/(g-2)       beyond.               */
-double orc_plane_potential(const orc_params *p, double z)
+ORC_CONST double orc_plane_potential(const orc_params *p, double z)
 {
     double az = fabs(z), s = p->sigma, g = p->gamma;
     if (az < s) return -2.0 * PI * p->phi * s * s / (g - 2.0);
@@ -122,10 +143,10 @@ double orc_plane_potential(const orc_params *p, double z)
 
 /* Carnahan-Starling contact value, Eq. (carnstar): chi = (2-eta)/(2(1-eta)^3),
  * eta = pi sigma^3 n / 6. */
-double orc_chi(const orc_params *p, double n)
+real ORC(chi)(const orc_params *p, real n)
 {
-    double eta = PI * p->sigma * p->sigma * p->sigma * n / 6.0;
-    double om = 1.0 - eta;
+    real eta = PI * p->sigma * p->sigma * p->sigma * n / 6.0;
+    real om = 1.0 - eta;
     return (2.0 - eta) / (2.0 * om * om * om);
 }
 
@@ -136,21 +157,21 @@ double orc_chi(const orc_params *p, double n)
 /* n = int F; n u = int xi F; (3/2) n T = int [(xi-u)^2/2 F + G];
  * q = int (xi-u)[(xi-u)^2/2 F + G]  (moment definitions of Sec. II.B and the
  * heat flux under the Shakhov term, written for the reduced distributions). */
-void orc_moments(const orc_params *p, const double *F, const double *G,
-                 double *n, double *u, double *T, double *q)
+void ORC(moments)(const orc_params *p, const real *F, const real *G,
+                  real *n, real *u, real *T, real *q)
 {
     int nz = p->nz, Q = p->Q;
     for (int i = 0; i < nz; i++) {
-        double sn = 0.0, sj = 0.0;
+        real sn = 0.0, sj = 0.0;
         for (int k = 0; k < Q; k++) {
             sn += F[k * nz + i];
             sj += p->xi[k] * F[k * nz + i];
         }
-        double ui = sj / sn;
-        double se = 0.0, sq = 0.0;
+        real ui = sj / sn;
+        real se = 0.0, sq = 0.0;
         for (int k = 0; k < Q; k++) {
-            double c = p->xi[k] - ui;
-            double e = 0.5 * c * c * F[k * nz + i] + G[k * nz + i];
+            real c = p->xi[k] - ui;
+            real e = 0.5 * c * c * F[k * nz + i] + G[k * nz + i];
             se += e;
             sq += c * e;
         }
@@ -169,12 +190,12 @@ void orc_moments(const orc_params *p, const double *F, const double *G,
  * reduced to 1D: nbar(z) = 3/(4 sigma^3) int_{|s|<sigma} (sigma^2 - s^2) n(z+s) ds,
  * the factor pi(sigma^2 - s^2) being the area of the slice of the sphere at
  * offset s; composite Simpson 1/3 over 2m panels, m = sigma/dz. */
-static void fm_average(const orc_params *p, const double *n, double *nbar)
+static void fm_average(const orc_params *p, const real *n, real *nbar)
 {
     int m = (int)lround(p->sigma / p->dz);
     double s3 = p->sigma * p->sigma * p->sigma;
     for (int i = 0; i < p->nz; i++) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int j = -m; j <= m; j++) {
             double z = j * p->dz;
             acc += simpson_w(j, m, p->dz) * (p->sigma * p->sigma - z * z) * n[gidx(p, i + j)];
@@ -185,20 +206,24 @@ static void fm_average(const orc_params *p, const double *n, double *nbar)
 
 /* EV1 force, Eq. (F1), by the composite Simpson 1/3 rule on the grid,
  * truncated at |x'-x| <= rcut (M = rcut/dz panels each side). */
-static void ev1_force(const orc_params *p, const double *n, double *force)
+static void ev1_force(const orc_params *p, const real *n, real *force)
 {
     int M = (int)lround(p->rcut / p->dz);
     for (int i = 0; i < p->nz; i++) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int j = -M; j <= M; j++)
             acc += simpson_w(j, M, p->dz) * orc_force_kernel(p, j * p->dz) * n[gidx(p, i + j)];
+#ifdef ORC_COMPLEX
+        /* the kernel is linear in phi: a complex phi scales the integral */
+        acc = acc * (1.0 + I * (p->phi_tl / p->phi));
+#endif
         force[i] = acc;
     }
 }
 
 /* fourth-order central difference (Sec. III):
  * f'_i = (f_{i-2} - 8 f_{i-1} + 8 f_{i+1} - f_{i+2}) / (12 dz) */
-static void grad4(const orc_params *p, const double *f, double *df)
+static void grad4(const orc_params *p, const real *f, real *df)
 {
     for (int i = 0; i < p->nz; i++) {
         df[i] = (f[gidx(p, i - 2)] - 8.0 * f[gidx(p, i - 1)]
@@ -213,32 +238,32 @@ static void grad4(const orc_params *p, const double *f, double *df)
  * 14 X = n^2 chi T            15 b n chi
  * READING (gradients): A = D4(X)/X and B = D4(T)/T, the logarithmic
  * derivatives of Eq. (J1) taken as derivative over value. */
-void orc_node_fields(const orc_params *p, const double *n, const double *u,
-                     const double *T, const double *q, double *out)
+void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
+                      const real *T, const real *q, real *out)
 {
     int nz = p->nz;
-    double *nbar = out + 4 * nz, *chi = out + 5 * nz, *force = out + 6 * nz;
-    double *mu = out + 7 * nz, *tau = out + 8 * nz, *Pr = out + 9 * nz;
-    double *rate = out + 10 * nz, *A = out + 11 * nz, *B = out + 12 * nz;
-    double *D = out + 13 * nz, *X = out + 14 * nz, *bnchi = out + 15 * nz;
+    real *nbar = out + 4 * nz, *chi = out + 5 * nz, *force = out + 6 * nz;
+    real *mu = out + 7 * nz, *tau = out + 8 * nz, *Pr = out + 9 * nz;
+    real *rate = out + 10 * nz, *A = out + 11 * nz, *B = out + 12 * nz;
+    real *D = out + 13 * nz, *X = out + 14 * nz, *bnchi = out + 15 * nz;
     double b = 2.0 * PI * p->sigma * p->sigma * p->sigma / 3.0;   /* Eq. (carnstar) */
 
-    memcpy(out + 0 * nz, n, nz * sizeof(double));
-    memcpy(out + 1 * nz, u, nz * sizeof(double));
-    memcpy(out + 2 * nz, T, nz * sizeof(double));
-    memcpy(out + 3 * nz, q, nz * sizeof(double));
+    memcpy(out + 0 * nz, n, nz * sizeof(real));
+    memcpy(out + 1 * nz, u, nz * sizeof(real));
+    memcpy(out + 2 * nz, T, nz * sizeof(real));
+    memcpy(out + 3 * nz, q, nz * sizeof(real));
 
     /* chi at the Fischer-Methfessel averaged density (Sec. II.A) */
     fm_average(p, n, nbar);
-    for (int i = 0; i < nz; i++) chi[i] = orc_chi(p, nbar[i]);
+    for (int i = 0; i < nz; i++) chi[i] = ORC(chi)(p, nbar[i]);
 
     /* self-consistent force, Eq. (F1) */
     ev1_force(p, n, force);
 
     /* gradients entering J1, Eq. (J1) */
     for (int i = 0; i < nz; i++) X[i] = n[i] * n[i] * chi[i] * T[i];
-    double *dX = (double *)malloc(nz * sizeof(double));
-    double *dT = (double *)malloc(nz * sizeof(double));
+    real *dX = (real *)malloc(nz * sizeof(real));
+    real *dT = (real *)malloc(nz * sizeof(real));
     grad4(p, X, dX);
     grad4(p, T, dT);
     grad4(p, u, D);
@@ -251,11 +276,11 @@ void orc_node_fields(const orc_params *p, const double *n, const double *u,
 
     /* transport coefficients, Eqs. (viscosity), (tau), (prandtl) */
     for (int i = 0; i < nz; i++) {
-        double bn = b * n[i];
-        double x = bn * chi[i];
-        double mu0 = 5.0 / (16.0 * p->sigma * p->sigma) * sqrt(T[i] / PI);
+        real bn = b * n[i];
+        real x = bn * chi[i];
+        real mu0 = 5.0 / (16.0 * p->sigma * p->sigma) * R_SQRT(T[i] / PI);
         mu[i] = mu0 * (1.0 / chi[i] + 0.8 * bn + 4.0 / 25.0 * (1.0 + 12.0 / PI) * bn * bn * chi[i]);
-        double Pi = n[i] * T[i];
+        real Pi = n[i] * T[i];
         tau[i] = mu[i] / (Pi * (1.0 + 0.4 * x));
         Pr[i] = 2.0 / 3.0 * (1.0 + 0.6 * x) / (1.0 + 0.4 * x)
               * (1.0 + 0.8 * x + 4.0 / 25.0 * (1.0 + 12.0 / PI) * x * x)
@@ -274,13 +299,14 @@ void orc_node_fields(const orc_params *p, const double *n, const double *u,
  * For h = F_MB * poly(c), c = xi - u, a_l = n E[poly(c) He_l(u + c)],
  * c ~ N(0, T), computed with the nq-point normalised Gauss-Hermite rule at
  * c = sqrt(T) z (exact for the polynomial degrees involved). */
-static void project(const orc_params *p, const double *coef_l, double *h)
+static void project(const orc_params *p, const real *coef_l, real *h)
 {
     int Q = p->Q;
-    double *he = (double *)malloc((Q + 1) * sizeof(double));
+    real *he = (real *)malloc((Q + 1) * sizeof(real));
     for (int k = 0; k < Q; k++) {
         hermite_all(Q, p->xi[k], he);
-        double acc = 0.0, fact = 1.0;
+        real acc = 0.0;
+        double fact = 1.0;
         for (int l = 0; l < Q; l++) {
             if (l > 0) fact *= l;
             acc += coef_l[l] * he[l] / fact;
@@ -303,28 +329,28 @@ static void project(const orc_params *p, const double *coef_l, double *h)
  *   J1_F = -b n chi F_MB { c [A + 3/5 (c^2/(2T) - 3/2) B] + 2/5 (3c^2/(2T) - 3/2) D }
  *   J1_G = -b n chi F_MB { c [T A + 3/5 (c^2/2 - T/2) B] + 2/5 (3c^2/2 - T/2) D }
  * with F_MB = n (2 pi T)^(-1/2) exp(-c^2/(2T)). */
-void orc_equilibria_node(const orc_params *p, double n, double u, double T,
-                         double q, double Pr, double bnchi, double A, double B,
-                         double D, double *FS, double *GS, double *JF, double *JG)
+void ORC(equilibria_node)(const orc_params *p, real n, real u, real T,
+                          real q, real Pr, real bnchi, real A, real B,
+                          real D, real *FS, real *GS, real *JF, real *JG)
 {
     int Q = p->Q;
-    double *aS = (double *)calloc(Q, sizeof(double));
-    double *bS = (double *)calloc(Q, sizeof(double));
-    double *aJ = (double *)calloc(Q, sizeof(double));
-    double *bJ = (double *)calloc(Q, sizeof(double));
-    double *he = (double *)malloc((Q + 1) * sizeof(double));
-    double s = (1.0 - Pr) * q / (n * T * T);
-    double sqT = sqrt(T);
+    real *aS = (real *)calloc(Q, sizeof(real));
+    real *bS = (real *)calloc(Q, sizeof(real));
+    real *aJ = (real *)calloc(Q, sizeof(real));
+    real *bJ = (real *)calloc(Q, sizeof(real));
+    real *he = (real *)malloc((Q + 1) * sizeof(real));
+    real s = (1.0 - Pr) * q / (n * T * T);
+    real sqT = R_SQRT(T);
     for (int m = 0; m < p->nq; m++) {
-        double c = sqT * p->zq[m];
-        double W = p->wq[m] * n;
+        real c = sqT * p->zq[m];
+        real W = p->wq[m] * n;
         hermite_all(Q, u + c, he);
-        double pS = 1.0 + s * c * (c * c / (5.0 * T) - 0.6);
-        double pG = T * (1.0 + s * c * (c * c / (5.0 * T) - 0.2));
-        double pJF = -bnchi * (c * (A + 0.6 * (c * c / (2.0 * T) - 1.5) * B)
-                               + 0.4 * (3.0 * c * c / (2.0 * T) - 1.5) * D);
-        double pJG = -bnchi * (c * (T * A + 0.6 * (c * c / 2.0 - T / 2.0) * B)
-                               + 0.4 * (3.0 * c * c / 2.0 - T / 2.0) * D);
+        real pS = 1.0 + s * c * (c * c / (5.0 * T) - 0.6);
+        real pG = T * (1.0 + s * c * (c * c / (5.0 * T) - 0.2));
+        real pJF = -bnchi * (c * (A + 0.6 * (c * c / (2.0 * T) - 1.5) * B)
+                             + 0.4 * (3.0 * c * c / (2.0 * T) - 1.5) * D);
+        real pJG = -bnchi * (c * (T * A + 0.6 * (c * c / 2.0 - T / 2.0) * B)
+                             + 0.4 * (3.0 * c * c / 2.0 - T / 2.0) * D);
         for (int l = 0; l < Q; l++) {
             aS[l] += W * pS * he[l];
             bS[l] += W * pG * he[l];
@@ -340,16 +366,16 @@ void orc_equilibria_node(const orc_params *p, double n, double u, double T,
 }
 
 /* Projected Maxwellian pair (F_MB, T F_MB) for initial data. */
-void orc_equilibrium(const orc_params *p, const double *n, const double *u,
-                     const double *T, double *F, double *G)
+void ORC(equilibrium)(const orc_params *p, const real *n, const real *u,
+                      const real *T, real *F, real *G)
 {
     int nz = p->nz, Q = p->Q;
-    double *FS = (double *)malloc(Q * sizeof(double));
-    double *GS = (double *)malloc(Q * sizeof(double));
-    double *JF = (double *)malloc(Q * sizeof(double));
-    double *JG = (double *)malloc(Q * sizeof(double));
+    real *FS = (real *)malloc(Q * sizeof(real));
+    real *GS = (real *)malloc(Q * sizeof(real));
+    real *JF = (real *)malloc(Q * sizeof(real));
+    real *JG = (real *)malloc(Q * sizeof(real));
     for (int i = 0; i < nz; i++) {
-        orc_equilibria_node(p, n[i], u[i], T[i], 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, FS, GS, JF, JG);
+        ORC(equilibria_node)(p, n[i], u[i], T[i], 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, FS, GS, JF, JG);
         for (int k = 0; k < Q; k++) {
             F[k * nz + i] = FS[k];
             G[k * nz + i] = GS[k];
@@ -365,18 +391,19 @@ void orc_equilibrium(const orc_params *p, const double *n, const double *u,
 /* (d/dxi h)_k for a projected h: since d/dxi [omega He_l] = -omega He_{l+1},
  * (dh)_k = -w_k sum_{l=0}^{Q-2} He_{l+1}(xi_k)/l! sum_j h_j He_l(xi_j);
  * the l = Q-1 term vanishes at the nodes because He_Q(xi_k) = 0. */
-void orc_dxi(const orc_params *p, const double *h, double *dh)
+void ORC(dxi)(const orc_params *p, const real *h, real *dh)
 {
     int Q = p->Q;
-    double *a = (double *)calloc(Q, sizeof(double));
-    double *he = (double *)malloc((Q + 1) * sizeof(double));
+    real *a = (real *)calloc(Q, sizeof(real));
+    real *he = (real *)malloc((Q + 1) * sizeof(real));
     for (int j = 0; j < Q; j++) {
         hermite_all(Q, p->xi[j], he);
         for (int l = 0; l < Q; l++) a[l] += h[j] * he[l];
     }
     for (int k = 0; k < Q; k++) {
         hermite_all(Q, p->xi[k], he);
-        double acc = 0.0, fact = 1.0;
+        real acc = 0.0;
+        double fact = 1.0;
         for (int l = 0; l <= Q - 2; l++) {
             if (l > 0) fact *= l;
             acc += he[l + 1] / fact * a[l];
@@ -393,51 +420,51 @@ void orc_dxi(const orc_params *p, const double *h, double *dh)
 
 /* Value at the face between the third and fourth of five upwind-ordered
  * points v0..v4 (v2 is the upwind cell of the face). */
-double orc_weno5(double v0, double v1, double v2, double v3, double v4, double eps)
+real ORC(weno5)(real v0, real v1, real v2, real v3, real v4, double eps)
 {
-    double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) / 6.0;
-    double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) / 6.0;
-    double q2 = (2.0 * v2 + 5.0 * v3 - v4) / 6.0;
-    double b0 = 13.0 / 12.0 * (v0 - 2.0 * v1 + v2) * (v0 - 2.0 * v1 + v2)
+    real q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) / 6.0;
+    real q1 = (-v1 + 5.0 * v2 + 2.0 * v3) / 6.0;
+    real q2 = (2.0 * v2 + 5.0 * v3 - v4) / 6.0;
+    real b0 = 13.0 / 12.0 * (v0 - 2.0 * v1 + v2) * (v0 - 2.0 * v1 + v2)
               + 0.25 * (v0 - 4.0 * v1 + 3.0 * v2) * (v0 - 4.0 * v1 + 3.0 * v2);
-    double b1 = 13.0 / 12.0 * (v1 - 2.0 * v2 + v3) * (v1 - 2.0 * v2 + v3)
+    real b1 = 13.0 / 12.0 * (v1 - 2.0 * v2 + v3) * (v1 - 2.0 * v2 + v3)
               + 0.25 * (v1 - v3) * (v1 - v3);
-    double b2 = 13.0 / 12.0 * (v2 - 2.0 * v3 + v4) * (v2 - 2.0 * v3 + v4)
+    real b2 = 13.0 / 12.0 * (v2 - 2.0 * v3 + v4) * (v2 - 2.0 * v3 + v4)
               + 0.25 * (3.0 * v2 - 4.0 * v3 + v4) * (3.0 * v2 - 4.0 * v3 + v4);
-    double a0 = 0.1 / ((eps + b0) * (eps + b0));
-    double a1 = 0.6 / ((eps + b1) * (eps + b1));
-    double a2 = 0.3 / ((eps + b2) * (eps + b2));
-    double sa = a0 + a1 + a2;
+    real a0 = 0.1 / ((eps + b0) * (eps + b0));
+    real a1 = 0.6 / ((eps + b1) * (eps + b1));
+    real a2 = 0.3 / ((eps + b2) * (eps + b2));
+    real sa = a0 + a1 + a2;
     return (a0 * q0 + a1 * q1 + a2 * q2) / sa;
 }
 
 /* -xi (h_{i+1/2} - h_{i-1/2}) / dz for one velocity row h[0..nz) with the
  * boundary rule; upwind side by the sign of xi (flux xi h is linear in h).
  * READING: the reconstruction acts on the stored F_k, G_k (weights included). */
-static void advect_row(const orc_params *p, double xi, const double *h, double *out)
+static void advect_row(const orc_params *p, double xi, const real *h, real *out)
 {
     int nz = p->nz;
     double e = p->weno_eps;
     for (int i = 0; i < nz; i++) {
         if (xi == 0.0) { out[i] = 0.0; continue; }
-        double fr, fl;   /* faces i+1/2 and i-1/2 */
+        real fr, fl;   /* faces i+1/2 and i-1/2 */
         if (xi > 0.0) {
-            fr = orc_weno5(h[gidx(p, i - 2)], h[gidx(p, i - 1)], h[gidx(p, i)],
-                           h[gidx(p, i + 1)], h[gidx(p, i + 2)], e);
-            fl = orc_weno5(h[gidx(p, i - 3)], h[gidx(p, i - 2)], h[gidx(p, i - 1)],
-                           h[gidx(p, i)], h[gidx(p, i + 1)], e);
+            fr = ORC(weno5)(h[gidx(p, i - 2)], h[gidx(p, i - 1)], h[gidx(p, i)],
+                            h[gidx(p, i + 1)], h[gidx(p, i + 2)], e);
+            fl = ORC(weno5)(h[gidx(p, i - 3)], h[gidx(p, i - 2)], h[gidx(p, i - 1)],
+                            h[gidx(p, i)], h[gidx(p, i + 1)], e);
         } else {
-            fr = orc_weno5(h[gidx(p, i + 3)], h[gidx(p, i + 2)], h[gidx(p, i + 1)],
-                           h[gidx(p, i)], h[gidx(p, i - 1)], e);
-            fl = orc_weno5(h[gidx(p, i + 2)], h[gidx(p, i + 1)], h[gidx(p, i)],
-                           h[gidx(p, i - 1)], h[gidx(p, i - 2)], e);
+            fr = ORC(weno5)(h[gidx(p, i + 3)], h[gidx(p, i + 2)], h[gidx(p, i + 1)],
+                            h[gidx(p, i)], h[gidx(p, i - 1)], e);
+            fl = ORC(weno5)(h[gidx(p, i + 2)], h[gidx(p, i + 1)], h[gidx(p, i)],
+                            h[gidx(p, i - 1)], h[gidx(p, i - 2)], e);
         }
         out[i] = -xi * (fr - fl) / p->dz;
     }
 }
 
 /* exported form of the free-streaming term of one velocity row */
-void orc_advect_row(const orc_params *p, double xi, const double *h, double *out)
+void ORC(advect_row)(const orc_params *p, double xi, const real *h, real *out)
 {
     advect_row(p, xi, h, out);
 }
@@ -449,29 +476,29 @@ void orc_advect_row(const orc_params *p, double xi, const double *h, double *out
 /* dF/dt = -xi dF/dz - F1 dF/dxi - nu (F - F^S) + J1_F, and the same for G,
  * Eqs. (enskog_approx) and (ev1).  Writes RF, RG ([Q][nz]); fields (optional,
  * may be NULL) receives the node fields of orc_node_fields. */
-void orc_rhs(const orc_params *p, const double *F, const double *G,
-             double *RF, double *RG, double *fields)
+void ORC(rhs)(const orc_params *p, const real *F, const real *G,
+              real *RF, real *RG, real *fields)
 {
     int nz = p->nz, Q = p->Q;
-    double *n = (double *)malloc(nz * sizeof(double));
-    double *u = (double *)malloc(nz * sizeof(double));
-    double *T = (double *)malloc(nz * sizeof(double));
-    double *q = (double *)malloc(nz * sizeof(double));
-    double *fl = (double *)malloc((size_t)ORC_NFIELDS * nz * sizeof(double));
-    double *row = (double *)malloc(nz * sizeof(double));
-    double *hk = (double *)malloc(Q * sizeof(double));
-    double *dh = (double *)malloc(Q * sizeof(double));
-    double *FS = (double *)malloc(Q * sizeof(double));
-    double *GS = (double *)malloc(Q * sizeof(double));
-    double *JF = (double *)malloc(Q * sizeof(double));
-    double *JG = (double *)malloc(Q * sizeof(double));
+    real *n = (real *)malloc(nz * sizeof(real));
+    real *u = (real *)malloc(nz * sizeof(real));
+    real *T = (real *)malloc(nz * sizeof(real));
+    real *q = (real *)malloc(nz * sizeof(real));
+    real *fl = (real *)malloc((size_t)ORC_NFIELDS * nz * sizeof(real));
+    real *row = (real *)malloc(nz * sizeof(real));
+    real *hk = (real *)malloc(Q * sizeof(real));
+    real *dh = (real *)malloc(Q * sizeof(real));
+    real *FS = (real *)malloc(Q * sizeof(real));
+    real *GS = (real *)malloc(Q * sizeof(real));
+    real *JF = (real *)malloc(Q * sizeof(real));
+    real *JG = (real *)malloc(Q * sizeof(real));
 
     /* moments, then node fields */
-    orc_moments(p, F, G, n, u, T, q);
-    orc_node_fields(p, n, u, T, q, fl);
-    const double *force = fl + 6 * nz, *Pr = fl + 9 * nz, *rate = fl + 10 * nz;
-    const double *A = fl + 11 * nz, *B = fl + 12 * nz, *D = fl + 13 * nz;
-    const double *bnchi = fl + 15 * nz;
+    ORC(moments)(p, F, G, n, u, T, q);
+    ORC(node_fields)(p, n, u, T, q, fl);
+    const real *force = fl + 6 * nz, *Pr = fl + 9 * nz, *rate = fl + 10 * nz;
+    const real *A = fl + 11 * nz, *B = fl + 12 * nz, *D = fl + 13 * nz;
+    const real *bnchi = fl + 15 * nz;
 
     /* free streaming term */
     for (int k = 0; k < Q; k++) {
@@ -480,18 +507,18 @@ void orc_rhs(const orc_params *p, const double *F, const double *G,
     }
     /* force, collision and J1 terms, node by node */
     for (int i = 0; i < nz; i++) {
-        orc_equilibria_node(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
-                            A[i], B[i], D[i], FS, GS, JF, JG);
+        ORC(equilibria_node)(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
+                             A[i], B[i], D[i], FS, GS, JF, JG);
         for (int k = 0; k < Q; k++) hk[k] = F[k * nz + i];
-        orc_dxi(p, hk, dh);
+        ORC(dxi)(p, hk, dh);
         for (int k = 0; k < Q; k++)
             RF[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - FS[k]) + JF[k];
         for (int k = 0; k < Q; k++) hk[k] = G[k * nz + i];
-        orc_dxi(p, hk, dh);
+        ORC(dxi)(p, hk, dh);
         for (int k = 0; k < Q; k++)
             RG[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - GS[k]) + JG[k];
     }
-    if (fields) memcpy(fields, fl, (size_t)ORC_NFIELDS * nz * sizeof(double));
+    if (fields) memcpy(fields, fl, (size_t)ORC_NFIELDS * nz * sizeof(real));
     free(n); free(u); free(T); free(q); free(fl); free(row);
     free(hk); free(dh); free(FS); free(GS); free(JF); free(JG);
 }
@@ -502,28 +529,28 @@ void orc_rhs(const orc_params *p, const double *F, const double *G,
 
 /* u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
  * u_new = 1/3 u + 2/3 (u2 + dt L(u2)).  Advances (F, G) in place. */
-void orc_step(const orc_params *p, double *F, double *G, int nsteps)
+void ORC(step)(const orc_params *p, real *F, real *G, int nsteps)
 {
     size_t N = (size_t)p->Q * p->nz;
-    double *F1 = (double *)malloc(N * sizeof(double));
-    double *G1 = (double *)malloc(N * sizeof(double));
-    double *F2 = (double *)malloc(N * sizeof(double));
-    double *G2 = (double *)malloc(N * sizeof(double));
-    double *RF = (double *)malloc(N * sizeof(double));
-    double *RG = (double *)malloc(N * sizeof(double));
+    real *F1 = (real *)malloc(N * sizeof(real));
+    real *G1 = (real *)malloc(N * sizeof(real));
+    real *F2 = (real *)malloc(N * sizeof(real));
+    real *G2 = (real *)malloc(N * sizeof(real));
+    real *RF = (real *)malloc(N * sizeof(real));
+    real *RG = (real *)malloc(N * sizeof(real));
     double dt = p->dt;
     for (int s = 0; s < nsteps; s++) {
-        orc_rhs(p, F, G, RF, RG, NULL);
+        ORC(rhs)(p, F, G, RF, RG, NULL);
         for (size_t e = 0; e < N; e++) {
             F1[e] = F[e] + dt * RF[e];
             G1[e] = G[e] + dt * RG[e];
         }
-        orc_rhs(p, F1, G1, RF, RG, NULL);
+        ORC(rhs)(p, F1, G1, RF, RG, NULL);
         for (size_t e = 0; e < N; e++) {
             F2[e] = 0.75 * F[e] + 0.25 * (F1[e] + dt * RF[e]);
             G2[e] = 0.75 * G[e] + 0.25 * (G1[e] + dt * RG[e]);
         }
-        orc_rhs(p, F2, G2, RF, RG, NULL);
+        ORC(rhs)(p, F2, G2, RF, RG, NULL);
         for (size_t e = 0; e < N; e++) {
             F[e] = F[e] / 3.0 + 2.0 / 3.0 * (F2[e] + dt * RF[e]);
             G[e] = G[e] / 3.0 + 2.0 / 3.0 * (G2[e] + dt * RG[e]);
@@ -532,6 +559,7 @@ void orc_step(const orc_params *p, double *F, double *G, int nsteps)
     free(F1); free(G1); free(F2); free(G2); free(RF); free(RG);
 }
 
+#ifndef ORC_COMPLEX
 /* ------------------------------------------------------------------ */
 /* Conserved totals                                                    */
 /* ------------------------------------------------------------------ */
@@ -584,3 +612,4 @@ double orc_discrete_a(const orc_params *p)
         acc += simpson_w(j, M, p->dz) * (j * p->dz) * orc_force_kernel(p, j * p->dz);
     return 0.5 * acc;
 }
+#endif /* ORC_COMPLEX */
