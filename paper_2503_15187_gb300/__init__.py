@@ -109,6 +109,9 @@ def lib():
             "evfdlb_coexistence": (i32, [P, d, ctypes.POINTER(d), ctypes.POINTER(d)]),
             "evfdlb_velocity_set": (i32, [i32, vp, vp]),
             "evfdlb_step_static": (i32, [P, vp, i64, vp]),
+            "evfdlb_rhs_vjp": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+            "evfdlb_adjoint_state": (i32, [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+            "evfdlb_adjoint": (i32, [vp, vp, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -270,6 +273,44 @@ class Sim:
         _check(lib().evfdlb_moments(self.h, n.ctypes.data, u.ctypes.data, T.ctypes.data, q.ctypes.data,
                                     tot.ctypes.data if tot is not None else None, 0), "evfdlb_moments")
         return n, u, T, q, (tot.reshape(-1, 4) if tot is not None else None)
+
+    # adjoint ----------------------------------------------------------------
+    def rhs_vjp(self, WF, WG):
+        """(J^T W_F, J^T W_G, dphi): the transpose of the Jacobian of one
+        right-hand side at the current state applied to (W_F, W_G), and
+        sum W . dR/dphi_a per slab."""
+        WF, WG = _host(WF, self.NF), _host(WG, self.NF)
+        oF, oG = np.empty(self.NF), np.empty(self.NF)
+        dphi = np.empty(len(self.params))
+        _check(lib().evfdlb_rhs_vjp(self.h, WF.ctypes.data, WG.ctypes.data, 0, oF.ctypes.data, oG.ctypes.data,
+                                    dphi.ctypes.data), "evfdlb_rhs_vjp")
+        return oF, oG, dphi
+
+    def adjoint_state(self, barF, barG, fields=True):
+        """Reverse sweep over every step since the last init / set_state for
+        the cotangent (barF, barG) of the current state.  Returns a dict with
+        dphi [nbatch], dF0, dG0 [NF] and, if fields and the trajectory began
+        at init, dn0, du0, dT0 [NN] (gradients per node)."""
+        barF, barG = _host(barF, self.NF), _host(barG, self.NF)
+        out = {"dphi": np.empty(len(self.params)), "dF0": np.empty(self.NF), "dG0": np.empty(self.NF)}
+        ptr = {k: None for k in ("dn0", "du0", "dT0")}
+        if fields:
+            for k in ptr:
+                out[k] = np.empty(self.NN)
+                ptr[k] = out[k].ctypes.data
+        _check(lib().evfdlb_adjoint_state(self.h, barF.ctypes.data, barG.ctypes.data, 0, out["dphi"].ctypes.data,
+                                          out["dF0"].ctypes.data, out["dG0"].ctypes.data, ptr["dn0"], ptr["du0"],
+                                          ptr["dT0"]), "evfdlb_adjoint_state")
+        return out
+
+    def adjoint(self, dL_dn):
+        """Gradient of a loss L(n_end) given dL/dn_end [NN]: (dphi [nbatch],
+        dT0 [NN], dn0 [NN]) with respect to phi_a and the initial T0, n0."""
+        g = _host(dL_dn, self.NN)
+        dphi, dT0, dn0 = np.empty(len(self.params)), np.empty(self.NN), np.empty(self.NN)
+        _check(lib().evfdlb_adjoint(self.h, g.ctypes.data, 0, dphi.ctypes.data, dT0.ctypes.data, dn0.ctypes.data),
+               "evfdlb_adjoint")
+        return dphi, dT0, dn0
 
     # helpers for one slab --------------------------------------------------
     def state_2d(self, s=0):

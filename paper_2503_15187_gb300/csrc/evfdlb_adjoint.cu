@@ -1,0 +1,612 @@
+// evfdlb_adjoint.cu -- discrete adjoint of the EV1 time step (FP64, periodic
+// slabs): vector-Jacobian products of the right-hand side L of Eqs. (ev1) and
+// (enskog_approx), of the Shu-Osher RK3 stages, and of the projected initial
+// state, for the gradient of a loss of the final state with respect to the
+// initial fields (n0, u0, T0), the initial distributions and the well depth
+// phi_a of Eq. (sutherland) (through the Eq. (F1) force, which is linear in
+// phi_a).
+//
+// One stage of the reverse sweep, given the adjoint ybar of the stage output
+// and the stage input u (recomputed from a checkpoint), forms
+//   out     = ca ybar + J(u)^T v + cc acc_in,   v = cb dt ybar,
+//   acc_out = cacc acc_in + cy ybar,
+// where J(u) is the Jacobian of L at u, in three launches:
+//   adj_local_kernel  -- per node tile: the velocity-space part of J^T v
+//                        (transposed Hermite synthesis and analysis, the
+//                        transposed WENO-5 faces, relaxation) and the adjoints
+//                        of the node fields that L reads (n, u, T, q, chi, X,
+//                        the three gradients and the force F1);
+//   adj_nodes_kernel  -- per node: transposed fourth-order differences and
+//                        the chain X = n^2 chi T, chi(nbar) of Eq. (carnstar);
+//   adj_moments_kernel-- per node: transposed Fischer-Methfessel average and
+//                        transposed Eq. (F1) convolution (correlations), the
+//                        chain from (n, u, T, q) to the raw moment sums, and
+//                        their transpose onto F and G.
+// Forward quantities are recomputed from the stage input and its raw moment
+// sums with the same device code as the forward kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "evfdlb_device.cuh"
+
+namespace evfdlb {
+
+// per-node adjoints written by adj_local_kernel ([kNumNodeAdj][NN])
+enum { AD_N = 0, AD_U, AD_T, AD_Q, AD_CHI, AD_X, AD_DX, AD_DT, AD_DU, AD_F1, kNumNodeAdj };
+// per-node adjoints written by adj_nodes_kernel ([kNumNodeAdjB][NN])
+enum { AB_N = 0, AB_U, AB_T, AB_NBAR, kNumNodeAdjB };
+
+constexpr int kHaloH = 5;   // state halo of the transposed WENO-5 faces
+constexpr int kHaloV = 3;   // halo of v
+
+struct AdjSmem {
+    Smem<double> f;   // P, S, N, U, T, X, Chi, Sc, Scr of the forward layout
+    double* H;        // state tile [2][Q][Z + 2 kHaloH]
+    double* V;        // v tile [2][Q][Z + 2 kHaloV]
+    double* Cb;       // cbar_l = sum_k S_kl v_k, [2][Q][Z]
+    double* Ae;       // analysis a_l of the state, [2][Q][Z]; reused for the WENO part
+    double* Red;      // per (distribution, node) sums [2][8][Z]
+};
+
+__host__ __device__ inline size_t adj_smem_doubles(int Q, int Z, int M) {
+    return 2 * (size_t)Q * Q + (Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + 2 * (size_t)Z +
+           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 4 * (size_t)Q * Z + 16 * (size_t)Z;
+}
+
+__device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
+    AdjSmem s;
+    s.f.P = base;
+    s.f.S = s.f.P + Q * Q;
+    s.f.N = s.f.S + Q * Q;
+    s.f.Nr = s.f.N;
+    s.f.U = s.f.N + (Z + 2 * M);
+    s.f.T = s.f.U + (Z + 4);
+    s.f.X = s.f.T + (Z + 4);
+    s.f.Chi = s.f.X + (Z + 4);
+    s.f.Sc = s.f.Chi + (Z + 4);
+    s.f.Scr = s.f.Sc + kNumScalars * Z;
+    s.f.C = s.f.A = s.f.F = s.f.Face = nullptr;
+    s.H = s.f.Scr + 2 * Z;
+    s.V = s.H + 2 * Q * (Z + 2 * kHaloH);
+    s.Cb = s.V + 2 * Q * (Z + 2 * kHaloV);
+    s.Ae = s.Cb + 2 * Q * Z;
+    s.Red = s.Ae + 2 * Q * Z;
+    return s;
+}
+
+// Gradient of the WENO-5 face value Phi(v0..v4) of weno5() (upwind side
+// v0..v2), times pb: g_r = pb dPhi/dv_r.  With e_r = eps + beta_r,
+// omega_r = (d_r / e_r^2) / sum_s (d_s / e_s^2) and Phi = sum_r omega_r q_r,
+//   dPhi/dv = sum_r omega_r [dq_r/dv - 2 (q_r - Phi) / e_r * dbeta_r/dv].
+__device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, double v3, double v4, double eps,
+                                           double pb, double g[5]) {
+    const double k6 = 1.0 / 6.0, k1312 = 13.0 / 12.0, k136 = 13.0 / 6.0;
+    double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * k6;
+    double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * k6;
+    double q2 = (2.0 * v2 + 5.0 * v3 - v4) * k6;
+    double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
+    double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
+    double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
+    double e0 = eps + fma(k1312 * t0, t0, 0.25 * s0 * s0);
+    double e1 = eps + fma(k1312 * t1, t1, 0.25 * s1 * s1);
+    double e2 = eps + fma(k1312 * t2, t2, 0.25 * s2 * s2);
+    double iP = 1.0 / (e0 * e1 * e2);
+    double ie0 = e1 * e2 * iP, ie1 = e0 * e2 * iP, ie2 = e0 * e1 * iP;
+    double a0 = 0.1 * ie0 * ie0, a1 = 0.6 * ie1 * ie1, a2 = 0.3 * ie2 * ie2;
+    double iS = 1.0 / (a0 + a1 + a2);
+    double w0 = a0 * iS, w1 = a1 * iS, w2 = a2 * iS;
+    double Phi = w0 * q0 + w1 * q1 + w2 * q2;
+    double kk0 = -2.0 * w0 * (q0 - Phi) * ie0;
+    double kk1 = -2.0 * w1 * (q1 - Phi) * ie1;
+    double kk2 = -2.0 * w2 * (q2 - Phi) * ie2;
+    // dbeta_r/dv = (13/6) t_r dt_r/dv + (1/2) s_r ds_r/dv
+    double bt0 = k136 * t0 * kk0, bs0 = 0.5 * s0 * kk0;
+    double bt1 = k136 * t1 * kk1, bs1 = 0.5 * s1 * kk1;
+    double bt2 = k136 * t2 * kk2, bs2 = 0.5 * s2 * kk2;
+    g[0] = pb * (w0 * 2.0 * k6 + bt0 + bs0);
+    g[1] = pb * (-w0 * 7.0 * k6 - w1 * k6 - 2.0 * bt0 - 4.0 * bs0 + bt1 + bs1);
+    g[2] = pb * (w0 * 11.0 * k6 + w1 * 5.0 * k6 + w2 * 2.0 * k6 + bt0 + 3.0 * bs0 - 2.0 * bt1 + bt2 + 3.0 * bs2);
+    g[3] = pb * (w1 * 2.0 * k6 + w2 * 5.0 * k6 + bt1 - bs1 - 2.0 * bt2 - 4.0 * bs2);
+    g[4] = pb * (-w2 * k6 + bt2 + bs2);
+}
+
+__global__ void __launch_bounds__(kThreads)
+adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                 const double* __restrict__ tables, const double* __restrict__ taps,
+                 const double* __restrict__ src, const double* __restrict__ mom, const double* __restrict__ ybar,
+                 const double* acc_in, double* acc_out, double* out, double* __restrict__ nadj,
+                 double* __restrict__ phis, long long NF, long long NN, double ca, double cb, int use_dt,
+                 double cc, double cacc, double cy, int Z, unsigned* err) {
+    extern __shared__ double smem[];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    const int Q = sd.Q, nz = it.nz, nx = sd.nx, bc = sd.bc;
+    const int WH = Z + 2 * kHaloH, WV = Z + 2 * kHaloV;
+    AdjSmem s = adj_carve(smem, Q, Z, sd.M);
+    TableLayout L(Q);
+    const double* tab = tables + sd.tab_off;
+    const double* xi = tab + L.xi;
+    const double* r1 = tab + L.r1;
+    const double* r2 = tab + L.r2;
+    const double* r3 = tab + L.r3;
+
+    // phase 0: tables and node inputs, the state tile (+-5) and v (+-3)
+    load_node_inputs<double>(sd, it, s.f, Z, tables, mom, NN);
+    for (int e = threadIdx.x; e < 2 * Q * (nz + 2 * kHaloH); e += blockDim.x) {
+        int c = e % (nz + 2 * kHaloH), r = e / (nz + 2 * kHaloH);
+        int k = r % Q, d = r / Q;
+        s.H[r * WH + c] = src[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloH + c, nx, bc)];
+    }
+    const double vscale = cb * (use_dt ? sd.dt : 1.0);
+    for (int e = threadIdx.x; e < 2 * Q * (nz + 2 * kHaloV); e += blockDim.x) {
+        int c = e % (nz + 2 * kHaloV), r = e / (nz + 2 * kHaloV);
+        int k = r % Q, d = r / Q;
+        s.V[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloV + c, nx, bc)];
+    }
+    __syncthreads();
+    node_fields<double>(sd, it, s.f, Z, taps, taps, mom, NN, err, nullptr);
+    __syncthreads();
+
+    // phase 1: analysis a_l (l <= Q-2) and transposed synthesis cbar_l
+    for (int e = threadIdx.x; e < 2 * (Q - 1) * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int l = r % (Q - 1), d = r / (Q - 1);
+        const double* Pl = s.f.P + l * Q;
+        const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
+        double acc = 0.0;
+        for (int j = 0; j < Q; ++j) acc = fma(Pl[j], h[j * WH], acc);
+        s.Ae[((size_t)d * Q + l) * Z + t] = acc;
+    }
+    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int l = r % Q, d = r / Q;
+        const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
+        double acc = 0.0;
+        for (int k = 0; k < Q; ++k) acc = fma(s.f.S[k * Q + l], v[k * WV], acc);
+        s.Cb[((size_t)d * Q + l) * Z + t] = acc;
+    }
+    __syncthreads();
+
+    // phase 2: per (distribution, node): adjoints of the coefficient
+    // constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!) m_{l-r}), of u and T
+    // through m_l (dm_l/du = sqrt(l) m_{l-1}, dm_l/dT = sqrt(l(l-1)) m_{l-2}/2,
+    // so dc_l/du = sqrt(l) c_{l-1}, dc_l/dT = sqrt(l(l-1)) c_{l-2}/2), of F1
+    // (c_l += F1 sqrt(l) a_{l-1}) and of nu (the -nu h term).
+    for (int e = threadIdx.x; e < 2 * nz; e += blockDim.x) {
+        int t = e % nz, d = e / nz;
+        const double* sc = s.f.Sc;
+        double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
+        double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
+        double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
+        double c0, c1, c2, c3;
+        if (d == 0) {
+            c0 = nu * n;
+            c1 = K * A * T;
+            c2 = 0.6 * K * D * T;
+            c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
+        } else {
+            c0 = nu * n * T + 0.4 * K * T * D;
+            c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
+            c2 = 0.6 * K * T * T * D;
+            c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
+        }
+        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
+        const double* a = s.Ae + (size_t)d * Q * Z + t;
+        double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
+        double cm1 = 0.0, cm2 = 0.0;      // c_{l-1}, c_{l-2}
+        double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, fb = 0;
+        for (int l = 0; l < Q; ++l) {
+            double cl = cbar[l * Z];
+            double w1 = r1[l] * m1, w2 = r2[l] * m2, w3 = r3[l] * m3;
+            b0 = fma(cl, m0, b0);
+            b1 = fma(cl, w1, b1);
+            b2 = fma(cl, w2, b2);
+            b3 = fma(cl, w3, b3);
+            ub = fma(cl * r1[l], cm1, ub);
+            Tb = fma(cl * 0.5 * r2[l], cm2, Tb);
+            if (l >= 1) fb = fma(cl * r1[l], a[(l - 1) * Z], fb);
+            double c = c0 * m0 + c1 * w1 + c2 * w2 + c3 * w3;
+            cm2 = cm1;
+            cm1 = c;
+            double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
+            m3 = m2;
+            m2 = m1;
+            m1 = m0;
+            m0 = mn;
+        }
+        double nb = 0.0;
+        const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
+        const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
+        for (int k = 0; k < Q; ++k) nb = fma(-h[k * WH], v[k * WV], nb);
+        double* red = s.Red + (size_t)d * 8 * Z + t;
+        red[0] = b0;
+        red[Z] = b1;
+        red[2 * Z] = b2;
+        red[3 * Z] = b3;
+        red[4 * Z] = ub;
+        red[5 * Z] = Tb;
+        red[6 * Z] = fb;
+        red[7 * Z] = nb;
+    }
+    __syncthreads();
+
+    // phase 3a: per node, the chain through the coefficient constants, the
+    // transport coefficients of Eqs. (viscosity), (tau), (prandtl), and the
+    // gradients A = dX/X, B = dT/T, D = du.
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) {
+        const double* sc = s.f.Sc;
+        double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
+        double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
+        double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
+        double F1 = sc[SC_FORCE * Z + t];
+        const double* rF = s.Red + t;
+        const double* rG = s.Red + 8 * Z + t;
+        double cF0 = rF[0], cF1 = rF[Z], cF2 = rF[2 * Z], cF3 = rF[3 * Z];
+        double cG0 = rG[0], cG1 = rG[Z], cG2 = rG[2 * Z], cG3 = rG[3 * Z];
+        double ub = rF[4 * Z] + rG[4 * Z];
+        double Tb = rF[5 * Z] + rG[5 * Z];
+        double F1b = rF[6 * Z] + rG[6 * Z];
+        double nub = rF[7 * Z] + rG[7 * Z];
+        double nb = 0, Kb = 0, kqb = 0, Ab = 0, Bb = 0, Db = 0, chib = 0, xb = 0, qb = 0;
+        // F: c0 = nu n, c1 = K A T, c2 = 3/5 K D T, c3 = nu kq/5 + 3/10 K B T^2
+        nub += cF0 * n;
+        nb += cF0 * nu;
+        Kb += cF1 * A * T;
+        Ab += cF1 * K * T;
+        Tb += cF1 * K * A;
+        Kb += 0.6 * cF2 * D * T;
+        Db += 0.6 * cF2 * K * T;
+        Tb += 0.6 * cF2 * K * D;
+        nub += 0.2 * cF3 * kq;
+        kqb += 0.2 * cF3 * nu;
+        Kb += 0.3 * cF3 * B * T * T;
+        Bb += 0.3 * cF3 * K * T * T;
+        Tb += 0.6 * cF3 * K * B * T;
+        // G: c0 = nu n T + 2/5 K T D, c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
+        //    c2 = 3/5 K T^2 D, c3 = nu kq T/5 + 3/10 K T^3 B
+        nub += cG0 * n * T;
+        nb += cG0 * nu * T;
+        Tb += cG0 * (nu * n + 0.4 * K * D);
+        Kb += 0.4 * cG0 * T * D;
+        Db += 0.4 * cG0 * K * T;
+        nub += 0.4 * cG1 * kq;
+        kqb += 0.4 * cG1 * nu;
+        Kb += cG1 * T * T * (A + 0.6 * B);
+        Tb += 2.0 * cG1 * K * T * (A + 0.6 * B);
+        Ab += cG1 * K * T * T;
+        Bb += 0.6 * cG1 * K * T * T;
+        Kb += 0.6 * cG2 * T * T * D;
+        Tb += 1.2 * cG2 * K * T * D;
+        Db += 0.6 * cG2 * K * T * T;
+        nub += 0.2 * cG3 * kq * T;
+        kqb += 0.2 * cG3 * nu * T;
+        Tb += cG3 * (0.2 * nu * kq + 0.9 * K * T * T * B);
+        Kb += 0.3 * cG3 * T * T * T * B;
+        Bb += 0.3 * cG3 * K * T * T * T;
+        // transport (recomputed as in node_fields)
+        double chi = s.f.Chi[t + 2], X = s.f.X[t + 2];
+        double bn = sd.b * n, x = bn * chi;
+        const double k1 = (4.0 / 25.0) * (1.0 + 12.0 / M_PI), k2 = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI));
+        double sqT = sqrt(T);
+        double gmu = 1.0 / chi + 0.8 * bn + k1 * bn * bn * chi;
+        double mu = sd.mu0_coef * sqT * gmu;
+        double den = 1.0 + 0.4 * x;
+        double tau = mu / (n * T * den);
+        double N1 = 1.0 + 0.6 * x, N2 = 1.0 + 0.8 * x + k1 * x * x, D1 = den, D2 = 1.0 + 1.2 * x + k2 * x * x;
+        double Pr = (2.0 / 3.0) * N1 * N2 / (D1 * D2);
+        // q from the raw sums (as node_fields forms it)
+        long long o = sd.node_off + it.i0 + t;
+        double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
+        double S3 = mom[MOM_S3 * NN + o], G0 = mom[MOM_G0 * NN + o], G1 = mom[MOM_G1 * NN + o];
+        double q = 0.5 * (S3 - 3.0 * u * S2 + 3.0 * u * u * S1 - u * u * u * S0) + G1 - u * G0;
+        // K = -b n^2 chi
+        nb += -2.0 * x * Kb;
+        chib += -bn * n * Kb;
+        // kq = (1 - Pr) q
+        qb += kqb * (1.0 - Pr);
+        double Prb = -kqb * q;
+        // nu = 1/tau or chi/tau
+        double taub;
+        if (sd.relax == EVFDLB_RELAX_INV_TAU) {
+            taub = -nub / (tau * tau);
+        } else {
+            chib += nub / tau;
+            taub = -nub * chi / (tau * tau);
+        }
+        // tau = mu / (n T (1 + 2x/5))
+        double mub = taub / (n * T * den);
+        nb += -taub * tau / n;
+        Tb += -taub * tau / T;
+        xb += -taub * tau * 0.4 / den;
+        // Pr(x)
+        xb += Prb * Pr * (0.6 / N1 + (0.8 + 2.0 * k1 * x) / N2 - 0.4 / D1 - (1.2 + 2.0 * k2 * x) / D2);
+        // mu = mu0 sqrt(T) (1/chi + 4/5 b n + k1 b^2 n^2 chi)
+        Tb += mub * mu / (2.0 * T);
+        nb += mub * sd.mu0_coef * sqT * (0.8 * sd.b + 2.0 * k1 * sd.b * bn * chi);
+        chib += mub * sd.mu0_coef * sqT * (-1.0 / (chi * chi) + k1 * bn * bn);
+        // x = b n chi
+        nb += xb * sd.b * chi;
+        chib += xb * bn;
+        // gradients
+        double dXb = Ab / X;
+        double Xb = -Ab * A / X;
+        double dTb = Bb / T;
+        Tb += -Bb * B / T;
+        double* na = nadj + sd.node_off + it.i0 + t;
+        na[AD_N * NN] = nb;
+        na[AD_U * NN] = ub;
+        na[AD_T * NN] = Tb;
+        na[AD_Q * NN] = qb;
+        na[AD_CHI * NN] = chib;
+        na[AD_X * NN] = Xb;
+        na[AD_DX * NN] = dXb;
+        na[AD_DT * NN] = dTb;
+        na[AD_DU * NN] = Db;
+        na[AD_F1 * NN] = F1b;
+        phis[o] += F1b * F1;
+    }
+
+    // phase 3b: transposed WENO-5 faces, one warp per velocity row.  For a
+    // chunk of up to 28 tile nodes, lane L owns one face; the node at lane L'
+    // collects the five faces that read it from lanes L'..L'+4.
+    {
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+        const double rdz = sd.inv_dx, eps = sd.weno_eps;
+        double* HB = s.Ae;    // the analysis is no longer needed: [2][Q][Z]
+        __syncthreads();      // all phase-2 reads of Ae are done
+        for (int row = warp; row < 2 * Q; row += nwarps) {
+            const int k = row % Q;
+            const double x = xi[k];
+            const double* h = s.H + (size_t)row * WH + kHaloH;   // h[i], i tile-relative
+            const double* v = s.V + (size_t)row * WV + kHaloV;
+            for (int c0 = 0; c0 < nz; c0 += 28) {
+                const int cn = min(28, nz - c0);
+                double g[5] = {0, 0, 0, 0, 0};
+                if (x != 0.0 && lane < cn + 4) {
+                    if (x > 0.0) {
+                        int f = c0 - 1 + lane;            // face between nodes f-1 and f
+                        double pb = x * rdz * (v[f] - v[f - 1]);
+                        weno5_grad(h[f - 3], h[f - 2], h[f - 1], h[f], h[f + 1], eps, pb, g);
+                    } else {
+                        int f = c0 - 2 + lane;
+                        double pb = x * rdz * (v[f] - v[f - 1]);
+                        weno5_grad(h[f + 2], h[f + 1], h[f], h[f - 1], h[f - 2], eps, pb, g);
+                    }
+                }
+                double acc;
+                const int src0 = min(lane, 27);
+                if (x > 0.0) {
+                    acc = __shfl_sync(0xffffffffu, g[4], src0);
+                    acc += __shfl_sync(0xffffffffu, g[3], src0 + 1);
+                    acc += __shfl_sync(0xffffffffu, g[2], src0 + 2);
+                    acc += __shfl_sync(0xffffffffu, g[1], src0 + 3);
+                    acc += __shfl_sync(0xffffffffu, g[0], src0 + 4);
+                } else {
+                    acc = __shfl_sync(0xffffffffu, g[0], src0);
+                    acc += __shfl_sync(0xffffffffu, g[1], src0 + 1);
+                    acc += __shfl_sync(0xffffffffu, g[2], src0 + 2);
+                    acc += __shfl_sync(0xffffffffu, g[3], src0 + 3);
+                    acc += __shfl_sync(0xffffffffu, g[4], src0 + 4);
+                }
+                if (lane < cn) HB[(size_t)row * Z + c0 + lane] = (x != 0.0) ? acc : 0.0;
+            }
+        }
+    }
+    __syncthreads();
+
+    // phase 4: the distribution-local adjoint and the RK-stage combination
+    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int j = r % Q, d = r / Q;
+        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
+        double hb = 0.0;   // analysis^T of abar_{l-1} = F1 sqrt(l) cbar_l
+        for (int l = 1; l < Q; ++l) hb = fma(s.f.P[(l - 1) * Q + j] * r1[l], cbar[l * Z], hb);
+        double F1 = s.f.Sc[SC_FORCE * Z + t], nu = s.f.Sc[SC_NU * Z + t];
+        double vv = s.V[(size_t)r * WV + t + kHaloV];
+        double val = F1 * hb - nu * vv + s.Ae[(size_t)r * Z + t];
+        long long g = d * NF + sd.f_off + (long long)j * nx + it.i0 + t;
+        double yb = ybar[g];
+        double o = fma(ca, yb, val);
+        if (cc != 0.0) o = fma(cc, acc_in[g], o);
+        if (acc_out) acc_out[g] = (cacc != 0.0 ? cacc * acc_in[g] : 0.0) + cy * yb;
+        out[g] = o;
+    }
+}
+
+// Per node: transposed fourth-order differences of X, T, u and the chain
+// X = n^2 chi T, chi = chi(eta), eta = pi sigma^3 nbar / 6 (Eq. (carnstar)).
+__global__ void __launch_bounds__(kThreads)
+adj_nodes_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                 const double* __restrict__ taps, const double* __restrict__ mom,
+                 const double* __restrict__ nadj, double* __restrict__ nbo, long long NN) {
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    const int nx = sd.nx, bc = sd.bc, m = sd.m;
+    const double* mtap = taps + sd.tap_off + 2 * sd.M + 1;
+    const double inv12 = sd.inv_dx / 12.0;
+    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
+    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
+    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
+    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
+    for (int t = threadIdx.x; t < it.nz; t += blockDim.x) {
+        const int i = it.i0 + t;
+        double n = S0[i], u = S1[i] / n;
+        double T = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) / n - 0.5 * u * u);
+        double nbF = 0.0;
+        for (int j = -m; j <= m; ++j) nbF = fma(mtap[j + m], S0[gidx(i + j, nx, bc)], nbF);
+        double eta = sd.eta_coef * nbF, om = 1.0 - eta;
+        double chi = (2.0 - eta) / (2.0 * om * om * om);
+        auto d4t = [&](int which) {
+            const double* g = nadj + which * NN + sd.node_off;
+            return (g[gidx(i + 2, nx, bc)] - 8.0 * g[gidx(i + 1, nx, bc)] + 8.0 * g[gidx(i - 1, nx, bc)] -
+                    g[gidx(i - 2, nx, bc)]) * inv12;
+        };
+        long long o = sd.node_off + i;
+        double Xb = nadj[AD_X * NN + o] + d4t(AD_DX);
+        double Tb = nadj[AD_T * NN + o] + d4t(AD_DT) + Xb * n * n * chi;
+        double ub = nadj[AD_U * NN + o] + d4t(AD_DU);
+        double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
+        double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
+        double dchi = (5.0 - 2.0 * eta) / (2.0 * om * om * om * om);
+        nbo[AB_N * NN + o] = nb;
+        nbo[AB_U * NN + o] = ub;
+        nbo[AB_T * NN + o] = Tb;
+        nbo[AB_NBAR * NN + o] = chib * dchi * sd.eta_coef;
+    }
+}
+
+// Per node: transposed Fischer-Methfessel average and Eq. (F1) convolution
+// (correlations with the same taps), the chain (n, u, T, q) <- raw sums, and
+// out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
+__global__ void __launch_bounds__(kThreads)
+adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                   const double* __restrict__ tables, const double* __restrict__ taps,
+                   const double* __restrict__ mom, const double* __restrict__ nadj,
+                   const double* __restrict__ nbo, double* out, long long NF, long long NN) {
+    __shared__ double sb[kNumMoments][kZMax];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    const int nx = sd.nx, bc = sd.bc, M = sd.M, m = sd.m, Q = sd.Q, nz = it.nz;
+    const double* ftap = taps + sd.tap_off;
+    const double* mtap = ftap + 2 * M + 1;
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) {
+        const int i = it.i0 + t;
+        long long o = sd.node_off + i;
+        const double* nbar = nbo + AB_NBAR * NN + sd.node_off;
+        const double* f1b = nadj + AD_F1 * NN + sd.node_off;
+        double nb = nbo[AB_N * NN + o];
+        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], nbar[gidx(i - j, nx, bc)], nb);
+        for (int j = -M; j <= M; ++j) nb = fma(ftap[j + M], f1b[gidx(i - j, nx, bc)], nb);
+        double ub = nbo[AB_U * NN + o], Tb = nbo[AB_T * NN + o], qb = nadj[AD_Q * NN + o];
+        double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
+        double G0 = mom[MOM_G0 * NN + o];
+        double n = S0, u = S1 / n;
+        double E = (0.5 * S2 + G0) / n;
+        // q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
+        double S3b = 0.5 * qb, S2b = -1.5 * u * qb, S1b = 1.5 * u * u * qb, S0b = -0.5 * u * u * u * qb;
+        double G1b = qb, G0b = -u * qb;
+        ub += qb * (-1.5 * S2 + 3.0 * u * S1 - 1.5 * u * u * S0 - G0);
+        // T = (2/3)(E - u^2/2), E = (S2/2 + G0)/n
+        double Eb = (2.0 / 3.0) * Tb;
+        ub += -(2.0 / 3.0) * u * Tb;
+        S2b += Eb / (2.0 * n);
+        G0b += Eb / n;
+        nb += -Eb * E / n;
+        // u = S1/n
+        S1b += ub / n;
+        nb += -ub * u / n;
+        S0b += nb;
+        sb[MOM_S0][t] = S0b;
+        sb[MOM_S1][t] = S1b;
+        sb[MOM_S2][t] = S2b;
+        sb[MOM_S3][t] = S3b;
+        sb[MOM_G0][t] = G0b;
+        sb[MOM_G1][t] = G1b;
+    }
+    __syncthreads();
+    TableLayout L(Q);
+    const double* xi = tables + sd.tab_off + L.xi;
+    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int k = r % Q, d = r / Q;
+        double x = xi[k];
+        double add = (d == 0) ? sb[MOM_S0][t] + x * (sb[MOM_S1][t] + x * (sb[MOM_S2][t] + x * sb[MOM_S3][t]))
+                              : sb[MOM_G0][t] + x * sb[MOM_G1][t];
+        out[d * NF + sd.f_off + (long long)k * nx + it.i0 + t] += add;
+    }
+}
+
+// Adjoint of the projected initial state F_k = sum_l S_kl n m_l(u, T),
+// G_k = T F_k: per node, with W_k = Fb_k + T Gb_k,
+//   nb = sum_k W_k F_k / n,  ub = n sum_l (S^T W)_l sqrt(l) m_{l-1},
+//   Tb = sum_k Gb_k F_k + n sum_l (S^T W)_l sqrt(l(l-1)) m_{l-2} / 2.
+__global__ void __launch_bounds__(kThreads)
+adj_init_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                const double* __restrict__ tables, const double* __restrict__ init_fields,
+                const double* __restrict__ lam, double* dn0, double* du0, double* dT0, long long NF, long long NN) {
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    const int Q = sd.Q, nx = sd.nx;
+    TableLayout L(Q);
+    const double* tab = tables + sd.tab_off;
+    for (int t = threadIdx.x; t < it.nz; t += blockDim.x) {
+        const int i = it.i0 + t;
+        long long o = sd.node_off + i;
+        double n = init_fields[o], u = init_fields[NN + o], T = init_fields[2 * NN + o];
+        double m0 = 1.0, m1 = 0.0, m2 = 0.0, Tm1 = T - 1.0;
+        double nb = 0.0, ub = 0.0, Tb1 = 0.0, Tb2 = 0.0;
+        for (int l = 0; l < Q; ++l) {
+            double wl = 0.0, gl = 0.0;
+            for (int k = 0; k < Q; ++k) {
+                long long g = sd.f_off + (long long)k * nx + i;
+                double Fb = lam[g], Gb = lam[NF + g];
+                double Skl = tab[L.S + k * Q + l];
+                wl = fma(Skl, fma(T, Gb, Fb), wl);
+                gl = fma(Skl, Gb, gl);
+            }
+            nb = fma(wl, m0, nb);
+            ub = fma(wl * tab[L.r1 + l], m1, ub);
+            Tb1 = fma(gl, m0, Tb1);
+            Tb2 = fma(wl * 0.5 * tab[L.r2 + l], m2, Tb2);
+            double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
+            m2 = m1;
+            m1 = m0;
+            m0 = mn;
+        }
+        if (dn0) dn0[o] = nb;
+        if (du0) du0[o] = n * ub;
+        if (dT0) dT0[o] = n * (Tb1 + Tb2);
+    }
+}
+
+// Per slab: sum of the per-node phi contributions (fixed-order tree), / phi_a.
+__global__ void __launch_bounds__(kThreads)
+adj_phi_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ phis, const double* __restrict__ phi_a,
+               double* out) {
+    __shared__ double red[kThreads];
+    const SlabDesc sd = slabs[blockIdx.x];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < sd.nx; i += blockDim.x) a += phis[sd.node_off + i];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0] / phi_a[blockIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers.
+// ---------------------------------------------------------------------------
+size_t adj_smem_bytes(int Q, int Z, int M) { return adj_smem_doubles(Q, Z, M) * sizeof(double); }
+
+cudaError_t configure_adjoint(size_t smem_bytes) {
+    return cudaFuncSetAttribute(adj_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+// One stage of the reverse sweep (see the file comment); nadj [10][NN] and
+// nbo [4][NN] are work arrays, phis [NN] accumulates F1b * F1.
+void launch_adj_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                      const double* tables, const double* taps, const double* src, const double* mom,
+                      const double* ybar, const double* acc_in, double* acc_out, double* out, double* nadj,
+                      double* nbo, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
+                      double cc, double cacc, double cy, int Z, unsigned* err) {
+    adj_local_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, taps, src, mom, ybar, acc_in, acc_out,
+                                                     out, nadj, phis, NF, NN, ca, cb, use_dt, cc, cacc, cy, Z, err);
+    adj_nodes_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, taps, mom, nadj, nbo, NN);
+    adj_moments_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, tables, taps, mom, nadj, nbo, out, NF, NN);
+}
+
+void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                     const double* tables, const double* init_fields, const double* lam, double* dn0, double* du0,
+                     double* dT0, long long NF, long long NN) {
+    adj_init_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, tables, init_fields, lam, dn0, du0, dT0, NF, NN);
+}
+
+void launch_adj_phi(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* phis, const double* phi_a,
+                    double* out) {
+    adj_phi_kernel<<<nslabs, kThreads, 0, st>>>(slabs, phis, phi_a, out);
+}
+
+}  // namespace evfdlb

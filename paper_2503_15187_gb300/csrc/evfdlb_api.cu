@@ -37,6 +37,18 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
                     double* q);
 void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
                    long long NN, double* out);
+size_t adj_smem_bytes(int Q, int Z, int M);
+cudaError_t configure_adjoint(size_t smem_bytes);
+void launch_adj_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                      const double* tables, const double* taps, const double* src, const double* mom,
+                      const double* ybar, const double* acc_in, double* acc_out, double* out, double* nadj,
+                      double* nbo, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
+                      double cc, double cacc, double cy, int Z, unsigned* err);
+void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                     const double* tables, const double* init_fields, const double* lam, double* dn0, double* du0,
+                     double* dT0, long long NF, long long NN);
+void launch_adj_phi(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* phis, const double* phi_a,
+                    double* out);
 }  // namespace evfdlb
 
 using namespace evfdlb;
@@ -72,6 +84,14 @@ struct evfdlb_ctx {
     size_t items_cap = 0;        // capacity of the device work list
     bool have_state = false;
     bool poisoned = false;
+    // adjoint: checkpoints of the trajectory since the last init / set_state
+    int ckpt_every = 0;          // 0: no tracking (no adjoint)
+    int64_t steps = 0;           // steps since the trajectory origin
+    bool origin_init = false;    // origin set by evfdlb_init (fields known)
+    double* init_fields = nullptr;           // [3][NN]: n0, u0, T0
+    std::vector<double*> ckpts;              // state at steps 0, K, 2K, ...
+    double* seg = nullptr;       // recomputed segment: (3K+1) states [2 NF] then (3K+1) moment sets [6 NN]
+    double* adj = nullptr;       // lam, y1, y2, acc [4][2 NF]; nadj [10 NN]; nbo [4 NN]; phis [NN]; phi [2 nbatch]
 };
 
 namespace {
@@ -101,6 +121,10 @@ void free_ctx(evfdlb_ctx* c) {
     cudaFree(c->tables);
     cudaFree(c->taps);
     cudaFree(c->scratch);
+    cudaFree(c->init_fields);
+    for (double* p : c->ckpts) cudaFree(p);
+    cudaFree(c->seg);
+    cudaFree(c->adj);
     cudaFree(c->slabs);
     cudaFree(c->items);
     cudaFree(c->err);
@@ -169,6 +193,44 @@ evfdlb_status copy_out(evfdlb_ctx* c, double* dst, const double* src, size_t byt
     TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->user));
     return EVFDLB_OK;
+}
+
+// Work buffers of the adjoint, allocated on first use.
+evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
+    if (!c->adj) {
+        size_t n = 4 * 2 * (size_t)c->NF + (10 + 4 + 1) * (size_t)c->NN + 2 * (size_t)c->nbatch;
+        TRY_CUDA(cudaMalloc((void**)&c->adj, sizeof(double) * n));
+        std::vector<double> phi(c->nbatch);
+        for (int s = 0; s < c->nbatch; ++s) phi[s] = c->params[s].phi_a;
+        double* dphi = c->adj + 4 * 2 * c->NF + 15 * c->NN;
+        TRY_CUDA(cudaMemcpy(dphi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
+        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax)));
+    }
+    if (!c->seg && c->ckpt_every > 0) {
+        size_t nst = 3 * (size_t)c->ckpt_every + 1;
+        TRY_CUDA(cudaMalloc((void**)&c->seg, sizeof(double) * nst * (2 * (size_t)c->NF + kNumMoments * (size_t)c->NN)));
+    }
+    return EVFDLB_OK;
+}
+
+evfdlb_status adjoint_supported(evfdlb_ctx* c) {
+    if (c->prec != EVFDLB_FP64) return EVFDLB_E_UNSUPPORTED;
+    for (auto& q : c->params) {
+        if (q.bc != EVFDLB_BC_PERIODIC) return EVFDLB_E_UNSUPPORTED;
+        if (!(q.phi_a != 0.0)) return EVFDLB_E_UNSUPPORTED;   // the phi gradient divides by phi_a
+    }
+    return EVFDLB_OK;
+}
+
+// One stage of the reverse sweep on the context's stream.
+void adj_stage(evfdlb_ctx* c, const double* src, const double* mom, const double* ybar, const double* acc_in,
+               double* acc_out, double* out, double ca, double cb, int use_dt, double cc, double cacc, double cy) {
+    double* nadj = c->adj + 4 * 2 * c->NF;
+    double* nbo = nadj + 10 * c->NN;
+    double* phis = nbo + 4 * c->NN;
+    launch_adj_stage((int)c->items_h.size(), adj_smem_bytes(c->Qmax, c->Z, c->Mmax), c->user, c->slabs, c->items, c->tables, c->taps, src, mom,
+                     ybar, acc_in, acc_out, out, nadj, nbo, phis, c->NF, c->NN, ca, cb, use_dt, cc, cacc, cy, c->Z,
+                     c->err);
 }
 
 }  // namespace
@@ -252,6 +314,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     c->params = ps;
     c->user = (cudaStream_t)cuda_stream;
     c->prec = ps[0].precision;
+    c->ckpt_every = ps[0].ckpt_every > 0 ? ps[0].ckpt_every : 0;
     c->esize = (c->prec == EVFDLB_FP32) ? sizeof(float) : sizeof(double);
     if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return EVFDLB_E_CUDA; }
     int sms = 0;
@@ -334,6 +397,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     alloc((void**)&c->slabs, sizeof(SlabDesc) * nbatch);
     alloc((void**)&c->items, sizeof(WorkItem) * c->items_cap);
     alloc((void**)&c->err, sizeof(unsigned));
+    if (c->ckpt_every > 0) alloc((void**)&c->init_fields, sizeof(double) * 3 * NN);
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tables.data(), sizeof(double) * tables.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
@@ -388,6 +452,13 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
     launch_init_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables, dn,
                   du, dT, c->state[0], c->mom[0], c->NF, c->NN, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
+    if (c->ckpt_every > 0) {   // trajectory origin for the adjoint
+        TRY_CUDA(cudaMemcpyAsync(c->init_fields, dn, bytes, cudaMemcpyDeviceToDevice, c->user));
+        TRY_CUDA(cudaMemcpyAsync(c->init_fields + c->NN, du, bytes, cudaMemcpyDeviceToDevice, c->user));
+        TRY_CUDA(cudaMemcpyAsync(c->init_fields + 2 * c->NN, dT, bytes, cudaMemcpyDeviceToDevice, c->user));
+    }
+    c->steps = 0;
+    c->origin_init = true;
     c->poisoned = false;
     evfdlb_status s = check_device(c);
     c->have_state = (s == EVFDLB_OK);
@@ -397,9 +468,29 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
 evfdlb_status evfdlb_step_async(evfdlb_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return EVFDLB_E_INVALID_ARG;
     if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
-    int64_t full = nsteps / c->chunk, rest = nsteps % c->chunk;
-    for (int64_t i = 0; i < full; ++i) TRY_CUDA(cudaGraphLaunch(c->g_chunk, c->user));
-    for (int64_t i = 0; i < rest; ++i) TRY_CUDA(cudaGraphLaunch(c->g_one, c->user));
+    while (nsteps > 0) {
+        int64_t n = nsteps;
+        if (c->ckpt_every > 0) {
+            // the state at every multiple of ckpt_every steps is kept for the adjoint
+            const int64_t K = c->ckpt_every;
+            if (c->steps % K == 0) {
+                size_t idx = (size_t)(c->steps / K);
+                while (c->ckpts.size() <= idx) {
+                    double* p = nullptr;
+                    TRY_CUDA(cudaMalloc((void**)&p, sizeof(double) * 2 * c->NF));
+                    c->ckpts.push_back(p);
+                }
+                TRY_CUDA(cudaMemcpyAsync(c->ckpts[idx], c->state[0], sizeof(double) * 2 * c->NF,
+                                         cudaMemcpyDeviceToDevice, c->user));
+            }
+            n = std::min<int64_t>(nsteps, K - c->steps % K);
+        }
+        int64_t full = n / c->chunk, rest = n % c->chunk;
+        for (int64_t i = 0; i < full; ++i) TRY_CUDA(cudaGraphLaunch(c->g_chunk, c->user));
+        for (int64_t i = 0; i < rest; ++i) TRY_CUDA(cudaGraphLaunch(c->g_one, c->user));
+        c->steps += n;
+        nsteps -= n;
+    }
     return EVFDLB_OK;
 }
 
@@ -441,6 +532,8 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
     launch_sums_p(c->prec, (int)c->items_h.size(), c->user, c->slabs, c->items, c->tables, c->rtables, c->state[0],
                   c->mom[0], c->NF, c->NN, c->err);
     TRY_CUDA(cudaGetLastError());
+    c->steps = 0;
+    c->origin_init = false;
     c->poisoned = false;
     s = check_device(c);
     c->have_state = (s == EVFDLB_OK);
@@ -522,6 +615,136 @@ evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
     evfdlb_status st = capture(c, 1, &c->g_one);
     if (st == EVFDLB_OK) st = capture(c, c->chunk, &c->g_chunk);
     return st;
+}
+
+evfdlb_status evfdlb_rhs_vjp(evfdlb_ctx* c, const double* WF, const double* WG, int32_t on_device, double* outF,
+                             double* outG, double* dphi) {
+    if (!c || !WF || !WG || !outF || !outG) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    evfdlb_status st = adjoint_supported(c);
+    if (st != EVFDLB_OK) return st;
+    if ((st = ensure_adjoint_buffers(c)) != EVFDLB_OK) return st;
+    size_t bytes = sizeof(double) * c->NF;
+    double* w = c->adj + 2 * c->NF;        // y1 slot
+    double* o = c->adj;                    // lam slot
+    double* phis = c->adj + 4 * 2 * c->NF + 14 * c->NN;
+    double* dph = phis + c->NN + c->nbatch;
+    if ((st = copy_in(c, w, WF, bytes, on_device)) != EVFDLB_OK) return st;
+    if ((st = copy_in(c, w + c->NF, WG, bytes, on_device)) != EVFDLB_OK) return st;
+    TRY_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * c->NN, c->user));
+    adj_stage(c, (const double*)c->state[0], c->mom[0], w, nullptr, nullptr, o, 0.0, 1.0, 0, 0.0, 0.0, 0.0);
+    launch_adj_phi(c->nbatch, c->user, c->slabs, phis, phis + c->NN, dph);
+    TRY_CUDA(cudaGetLastError());
+    if ((st = copy_out(c, outF, o, bytes, on_device)) != EVFDLB_OK) return st;
+    if ((st = copy_out(c, outG, o + c->NF, bytes, on_device)) != EVFDLB_OK) return st;
+    if (dphi) TRY_CUDA(cudaMemcpyAsync(dphi, dph, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const double* barG, int32_t on_device,
+                                   double* dL_dphi_a, double* dL_dF0, double* dL_dG0, double* dL_dn0,
+                                   double* dL_du0, double* dL_dT0) {
+    if (!c || !barF || !barG) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state || c->poisoned || c->ckpt_every <= 0) return EVFDLB_E_STATE;
+    if ((dL_dn0 || dL_du0 || dL_dT0) && !c->origin_init) return EVFDLB_E_STATE;
+    evfdlb_status st = adjoint_supported(c);
+    if (st != EVFDLB_OK) return st;
+    if ((st = ensure_adjoint_buffers(c)) != EVFDLB_OK) return st;
+    const long long NF = c->NF, NN = c->NN;
+    const size_t sbytes = sizeof(double) * NF;
+    double* lam = c->adj;
+    double* y1 = lam + 2 * NF;
+    double* y2 = y1 + 2 * NF;
+    double* acc = y2 + 2 * NF;
+    double* phis = c->adj + 4 * 2 * NF + 14 * NN;
+    double* phi_dev = phis + NN;
+    double* dph = phi_dev + c->nbatch;
+    if ((st = copy_in(c, lam, barF, sbytes, on_device)) != EVFDLB_OK) return st;
+    if ((st = copy_in(c, lam + NF, barG, sbytes, on_device)) != EVFDLB_OK) return st;
+    TRY_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * NN, c->user));
+    const int K = c->ckpt_every;
+    const size_t nst = 3 * (size_t)K + 1;
+    auto sstate = [&](size_t j) { return c->seg + j * 2 * NF; };
+    auto smom = [&](size_t j) { return c->seg + nst * 2 * NF + j * kNumMoments * NN; };
+    const int n = (int)c->items_h.size();
+    const int64_t nseg = (c->steps + K - 1) / K;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t s0 = sg * K;
+        const int ns = (int)std::min<int64_t>(K, c->steps - s0);
+        // recompute the segment from its checkpoint, keeping every stage input
+        TRY_CUDA(cudaMemcpyAsync(sstate(0), c->ckpts[sg], sizeof(double) * 2 * NF, cudaMemcpyDeviceToDevice, c->user));
+        launch_sums_p(EVFDLB_FP64, n, c->user, c->slabs, c->items, c->tables, c->tables, sstate(0), smom(0), NF, NN,
+                      c->err);
+        for (int t = 0; t < ns; ++t) {
+            size_t b = 3 * (size_t)t;
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sstate(b), nullptr, sstate(b + 1), nullptr, smom(b), smom(b + 1), NF, NN, 0.0,
+                           1.0, 0, c->Z, c->err);
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sstate(b + 1), sstate(b), sstate(b + 2), nullptr, smom(b + 1), smom(b + 2), NF,
+                           NN, 0.75, 0.25, 0, c->Z, c->err);
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sstate(b + 2), sstate(b), sstate(b + 3), nullptr, smom(b + 2), smom(b + 3), NF,
+                           NN, 1.0 / 3.0, 2.0 / 3.0, 0, c->Z, c->err);
+        }
+        // reverse sweep of the segment (Shu-Osher stages in reverse order):
+        //   y2  = 2/3 lam + J(u2)^T (2/3 dt lam),   acc = 1/3 lam
+        //   y1  = 1/4 y2  + J(u1)^T (1/4 dt y2),    acc += 3/4 y2
+        //   lam = y1 + J(u)^T (dt y1) + acc
+        for (int t = ns - 1; t >= 0; --t) {
+            size_t b = 3 * (size_t)t;
+            adj_stage(c, sstate(b + 2), smom(b + 2), lam, nullptr, acc, y2, 2.0 / 3.0, 2.0 / 3.0, 1, 0.0, 0.0,
+                      1.0 / 3.0);
+            adj_stage(c, sstate(b + 1), smom(b + 1), y2, acc, acc, y1, 0.25, 0.25, 1, 0.0, 1.0, 0.75);
+            adj_stage(c, sstate(b), smom(b), y1, acc, nullptr, lam, 1.0, 1.0, 1, 1.0, 0.0, 0.0);
+        }
+        TRY_CUDA(cudaGetLastError());
+    }
+    evfdlb_status s2;
+    if (dL_dF0 && (s2 = copy_out(c, dL_dF0, lam, sbytes, on_device)) != EVFDLB_OK) return s2;
+    if (dL_dG0 && (s2 = copy_out(c, dL_dG0, lam + NF, sbytes, on_device)) != EVFDLB_OK) return s2;
+    if (dL_dn0 || dL_du0 || dL_dT0) {
+        double* f = y1;   // [3][NN] fits in the y1 slot (2 NF >= 3 NN for Q >= 2)
+        launch_adj_init(n, c->user, c->slabs, c->items, c->tables, c->init_fields, lam, f, f + NN, f + 2 * NN, NF, NN);
+        TRY_CUDA(cudaGetLastError());
+        size_t nb = sizeof(double) * NN;
+        if (dL_dn0 && (s2 = copy_out(c, dL_dn0, f, nb, on_device)) != EVFDLB_OK) return s2;
+        if (dL_du0 && (s2 = copy_out(c, dL_du0, f + NN, nb, on_device)) != EVFDLB_OK) return s2;
+        if (dL_dT0 && (s2 = copy_out(c, dL_dT0, f + 2 * NN, nb, on_device)) != EVFDLB_OK) return s2;
+    }
+    if (dL_dphi_a) {
+        launch_adj_phi(c->nbatch, c->user, c->slabs, phis, phi_dev, dph);
+        TRY_CUDA(cudaGetLastError());
+        TRY_CUDA(cudaMemcpyAsync(dL_dphi_a, dph, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
+    }
+    return check_device(c);
+}
+
+evfdlb_status evfdlb_adjoint(evfdlb_ctx* c, const double* dL_dn_end, int32_t on_device, double* dL_dphi_a,
+                             double* dL_dT0, double* dL_dn0) {
+    if (!c || !dL_dn_end) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state) return EVFDLB_E_STATE;
+    // n = sum_k F_k, so dL/dF_k = dL/dn for every k and dL/dG = 0
+    std::vector<double> hF((size_t)c->NF), hG((size_t)c->NF, 0.0), hn((size_t)c->NN);
+    if (on_device) {
+        TRY_CUDA(cudaMemcpyAsync(hn.data(), dL_dn_end, sizeof(double) * c->NN, cudaMemcpyDeviceToHost, c->user));
+        TRY_CUDA(cudaStreamSynchronize(c->user));
+    } else {
+        std::copy(dL_dn_end, dL_dn_end + c->NN, hn.begin());
+    }
+    for (int s = 0; s < c->nbatch; ++s) {
+        const SlabDesc& d = c->slabs_h[s];
+        for (int k = 0; k < d.Q; ++k)
+            for (int i = 0; i < d.nx; ++i) hF[(size_t)d.f_off + (size_t)k * d.nx + i] = hn[(size_t)d.node_off + i];
+    }
+    if (!on_device)
+        return evfdlb_adjoint_state(c, hF.data(), hG.data(), 0, dL_dphi_a, nullptr, nullptr, dL_dn0, nullptr, dL_dT0);
+    // device outputs: the cotangent goes through the scratch block
+    TRY_CUDA(cudaMemcpyAsync(c->scratch, hF.data(), sizeof(double) * c->NF, cudaMemcpyHostToDevice, c->user));
+    TRY_CUDA(cudaMemcpyAsync(c->scratch + c->NF, hG.data(), sizeof(double) * c->NF, cudaMemcpyHostToDevice, c->user));
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    return evfdlb_adjoint_state(c, c->scratch, c->scratch + c->NF, 1, dL_dphi_a, nullptr, nullptr, dL_dn0, nullptr,
+                                dL_dT0);
 }
 
 }  // extern "C"

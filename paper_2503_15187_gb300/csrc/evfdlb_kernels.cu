@@ -40,384 +40,9 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "evfdlb_internal.h"
+#include "evfdlb_device.cuh"
 
 namespace evfdlb {
-
-__device__ __forceinline__ int gidx(int i, int nx, int bc) {
-    if (bc == EVFDLB_BC_PERIODIC) {
-        int r = i % nx;
-        return r < 0 ? r + nx : r;
-    }
-    return i < 0 ? 0 : (i >= nx ? nx - 1 : i);
-}
-
-// ---------------------------------------------------------------------------
-// Shared-memory layout of one CTA, sized for (Q, Z, M): an FP64 block of node
-// fields followed by an R block of velocity-space data.
-// ---------------------------------------------------------------------------
-template <typename R>
-struct Smem {
-    double *N;          // n on nodes [i0 - M, i0 + Z + M)
-    double *U, *T;      // u, T on nodes [i0 - 2, i0 + Z + 2)
-    double *X, *Chi;    // X = n^2 chi T and chi on the same nodes
-    double *Sc;         // per-node scalars [kNumScalars][Z]
-    R *P, *S;           // analysis / synthesis tables [Q*Q] each
-    R *Nr;              // n halo in R (the force convolution), aliases N for FP64
-    R *Scr;             // nu and F1 in R, [2][Z]
-    R *C;               // coefficients [2][Q][Z]
-    R *A;               // analysis [2][Q][Z]
-    R *F;               // state tile with halo [2][Q][Z+6]
-    R *Face;            // WENO face values [2][Q][Z+1]
-};
-
-// Length of the R copy of the density halo, rounded up to an even count so
-// that the blocks after it stay 8-byte aligned (init_kernel stores doubles in
-// the coefficient block).
-__host__ __device__ inline size_t nr_len(int Z, int M) { return ((size_t)(Z + 2 * M) + 1) & ~(size_t)1; }
-
-template <typename R>
-__host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
-    size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z;
-    size_t nr = 2 * (size_t)Q * Q + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
-                4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1);
-    return nd * sizeof(double) + nr * sizeof(R);
-}
-
-template <typename R>
-__device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
-    Smem<R> s;
-    s.N = base;
-    s.U = s.N + (Z + 2 * M);
-    s.T = s.U + (Z + 4);
-    s.X = s.T + (Z + 4);
-    s.Chi = s.X + (Z + 4);
-    s.Sc = s.Chi + (Z + 4);
-    R* r = reinterpret_cast<R*>(s.Sc + kNumScalars * Z);
-    s.P = r;
-    s.S = s.P + Q * Q;
-    if constexpr (std::is_same<R, double>::value) {
-        s.Nr = s.N;
-        s.Scr = s.S + Q * Q;
-    } else {
-        s.Nr = s.S + Q * Q;
-        s.Scr = s.Nr + nr_len(Z, M);
-    }
-    s.C = s.Scr + 2 * Z;
-    s.A = s.C + 2 * Q * Z;
-    s.F = s.A + 2 * Q * Z;
-    s.Face = s.F + 2 * Q * (Z + 6);
-    return s;
-}
-
-enum { SC_N = 0, SC_U, SC_T, SC_NU, SC_FORCE, SC_KQ, SC_K, SC_A, SC_B, SC_D };
-
-__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
-
-// ---------------------------------------------------------------------------
-// Phase 0: stage the tables, the density halo, u/T near the tile and the
-// state tile (+-3 nodes for WENO-5) into shared memory.
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                 const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
-    const int Q = sd.Q, M = sd.M, nx = sd.nx, bc = sd.bc;
-    TableLayout L(Q);
-    const R* tab = rtab + sd.tab_off;
-    for (int t = threadIdx.x; t < 2 * Q * Q; t += blockDim.x) s.P[t] = tab[L.P + t];  // P then S
-    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {
-        double n = S0[gidx(it.i0 - M + t, nx, bc)];
-        s.N[t] = n;
-        if constexpr (!std::is_same<R, double>::value) s.Nr[t] = (R)n;
-    }
-    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
-    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
-    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
-        int i = gidx(it.i0 - 2 + t, nx, bc);
-        double n = S0[i], inv_n = 1.0 / n;
-        double u = S1[i] * inv_n;
-        // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2
-        s.U[t] = u;
-        s.T[t] = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) * inv_n - 0.5 * u * u);
-    }
-}
-
-template <typename R>
-__device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                const R* __restrict__ src, long long NF) {
-    const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
-    const int cols = it.nz + 6;
-    for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
-        int c = e % cols, r = e / cols;
-        int k = r % Q, d = r / Q;
-        int i = gidx(it.i0 - 3 + c, nx, bc);
-        s.F[(d * Q + k) * W + c] = src[d * NF + sd.f_off + (long long)k * nx + i];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Phases 1-2: node fields of the tile.
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                            const double* __restrict__ taps, const R* __restrict__ rtaps,
-                            const double* __restrict__ mom, long long NN, unsigned* err, double* fields_out) {
-    const int M = sd.M, m = sd.m;
-    const R* ftap = rtaps + sd.tap_off;                  // force [2M+1]
-    const double* mtap = taps + sd.tap_off + 2 * M + 1;  // Fischer-Methfessel [2m+1]
-    // Fischer-Methfessel average (Sec. II.A), chi (Eq. (carnstar)) and
-    // X = n^2 chi T on nodes i0-2 .. i0+nz+1.  Under the outflow rule a ghost
-    // node copies every node field of the nearest interior node, so the
-    // average is centred on the clamped node; under the periodic rule the
-    // window around the ghost position is the wrapped node's window.
-    for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
-        int pos = it.i0 - 2 + t;
-        int shift = (sd.bc == EVFDLB_BC_OUTFLOW) ? gidx(pos, sd.nx, sd.bc) - pos : 0;
-        const double* nn = s.N + (t - 2 + M + shift);
-        double nb = 0.0;
-        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], nn[j], nb);
-        double eta = sd.eta_coef * nb, om = 1.0 - eta;
-        double chi = (2.0 - eta) / (2.0 * om * om * om);
-        double n = nn[0];
-        s.Chi[t] = chi;
-        s.X[t] = n * n * chi * s.T[t];
-        if (fields_out && t >= 2 && t < it.nz + 2) {
-            long long NNf = NN;
-            fields_out[4 * NNf + sd.node_off + it.i0 + t - 2] = nb;
-        }
-    }
-    __syncthreads();
-    const double inv12 = sd.inv_dx / 12.0;
-    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
-    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
-    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
-    const double* S3 = mom + MOM_S3 * NN + sd.node_off;
-    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    const double* G1 = mom + MOM_G1 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz; t += blockDim.x) {
-        const int c = t + 2;                         // index in the +-2 arrays
-        const int i = it.i0 + t;
-        double n = s.N[t + M], u = s.U[c], T = s.T[c];
-        // fourth-order central differences (Sec. III)
-        double dX = (s.X[c - 2] - 8.0 * s.X[c - 1] + 8.0 * s.X[c + 1] - s.X[c + 2]) * inv12;
-        double dT = (s.T[c - 2] - 8.0 * s.T[c - 1] + 8.0 * s.T[c + 1] - s.T[c + 2]) * inv12;
-        double dU = (s.U[c - 2] - 8.0 * s.U[c - 1] + 8.0 * s.U[c + 1] - s.U[c + 2]) * inv12;
-        double X = s.X[c], chi = s.Chi[c];
-        double A = dX / X, B = dT / T;
-        // self-consistent force, Eq. (F1), Simpson taps over |j| <= M
-        const R* nn = s.Nr + (t + M);
-        R f1r = 0;
-        for (int j = -M; j <= M; ++j) f1r = fma(ftap[j + M], nn[j], f1r);
-        double f1 = (double)f1r;
-        // heat flux from the raw sums: q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
-        double q = 0.5 * (S3[i] - 3.0 * u * S2[i] + 3.0 * u * u * S1[i] - u * u * u * S0[i]) + G1[i] - u * G0[i];
-        // transport, Eqs. (viscosity), (tau), (prandtl)
-        double bn = sd.b * n, x = bn * chi;
-        double mu = sd.mu0_coef * sqrt(T) * (1.0 / chi + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
-        double tau = mu / (n * T * (1.0 + 0.4 * x));
-        double Pr = (2.0 / 3.0) * (1.0 + 0.6 * x) * (1.0 + 0.8 * x + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * x * x) /
-                    ((1.0 + 0.4 * x) * (1.0 + 1.2 * x + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * x * x));
-        double nu = (sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 / tau : chi / tau;
-        double* sc = s.Sc;
-        sc[SC_N * Z + t] = n;
-        sc[SC_U * Z + t] = u;
-        sc[SC_T * Z + t] = T;
-        sc[SC_NU * Z + t] = nu;
-        sc[SC_FORCE * Z + t] = f1;
-        sc[SC_KQ * Z + t] = (1.0 - Pr) * q;
-        sc[SC_K * Z + t] = -x * n;        // -b n^2 chi, the prefactor of J1
-        sc[SC_A * Z + t] = A;
-        sc[SC_B * Z + t] = B;
-        sc[SC_D * Z + t] = dU;
-        s.Scr[t] = (R)nu;
-        s.Scr[Z + t] = f1r;
-        if (!(n > 0.0) || !(T > 0.0)) {
-            atomicOr(err, (finite(n) && finite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
-        } else if (!finite(f1) || !finite(nu) || !finite(q) || !finite(A) || !finite(B)) {
-            atomicOr(err, ERR_NONFINITE);
-        }
-        if (fields_out) {
-            long long o = sd.node_off + i;
-            double vals[EVFDLB_NFIELDS] = {n, u, T, q, 0.0, chi, f1, mu, tau, Pr, nu, A, B, dU, X, x};
-            for (int f = 0; f < EVFDLB_NFIELDS; ++f)
-                if (f != 4) fields_out[f * NN + o] = vals[f];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Phase 3a: Hermite coefficients of nu F^S + J1_F and nu G^S + J1_G.
-// With m_l = E[psi_l(u + c)], c ~ N(0, T) (m_0 = 1,
-// m_{l+1} = u m_l / sqrt(l+1) + (T-1) sqrt(l/(l+1)) m_{l-1}) and Stein's
-// identity E[c h(c)] = T E[h'(c)], the projections of the reduced Shakhov
-// equilibria and of the reduced J1 of Sec. II.B are
-//   c_l = c0 m_l + c1 sqrt(l) m_{l-1} + c2 sqrt(l(l-1)) m_{l-2}
-//         + c3 sqrt(l(l-1)(l-2)) m_{l-3}
-// with per-node constants (K = -b n^2 chi, kq = (1-Pr) q):
-//   F: c0 = nu n,             c1 = K A T,
-//      c2 = 3/5 K D T,        c3 = nu kq/5 + 3/10 K B T^2
-//   G: c0 = nu n T + 2/5 K T D,  c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
-//      c2 = 3/5 K T^2 D,         c3 = nu kq T/5 + 3/10 K T^3 B
-// The four constants are formed in FP64; the recurrence runs in R.
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                         const R* __restrict__ rtab) {
-    const int Q = sd.Q;
-    TableLayout L(Q);
-    const R* tab = rtab + sd.tab_off;
-    for (int e = threadIdx.x; e < 2 * it.nz; e += blockDim.x) {
-        int t = e % it.nz, d = e / it.nz;
-        const double* sc = s.Sc;
-        double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
-        double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
-        double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-        double c0, c1, c2, c3;
-        if (d == 0) {
-            c0 = nu * n;
-            c1 = K * A * T;
-            c2 = 0.6 * K * D * T;
-            c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
-        } else {
-            c0 = nu * n * T + 0.4 * K * T * D;
-            c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
-            c2 = 0.6 * K * T * T * D;
-            c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
-        }
-        const R rc0 = (R)c0, rc1 = (R)c1, rc2 = (R)c2, rc3 = (R)c3, ru = (R)u, Tm1 = (R)(T - 1.0);
-        R m0 = 1, m1 = 0, m2 = 0, m3 = 0;
-        R* out = s.C + (size_t)d * Q * Z + t;
-        for (int l = 0; l < Q; ++l) {
-            R c = rc0 * m0;
-            c = fma(rc1 * tab[L.r1 + l], m1, c);
-            c = fma(rc2 * tab[L.r2 + l], m2, c);
-            c = fma(rc3 * tab[L.r3 + l], m3, c);
-            out[l * Z] = c;
-            R mn = fma(ru * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
-            m3 = m2;
-            m2 = m1;
-            m1 = m0;
-            m0 = mn;
-        }
-    }
-}
-
-// Phase 3b: analysis a_l = sum_j psi_l(xi_j) h_j, l <= Q-2 (the force needs
-// a_0 .. a_{Q-2}; the l = Q-1 term meets psi_Q(xi_k) = 0).
-template <typename R>
-__device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z) {
-    const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    const int per_d = (Q - 1) * nz;
-    for (int e = threadIdx.x; e < 2 * per_d; e += blockDim.x) {
-        int d = e / per_d, r = e % per_d;
-        int l = r / nz, t = r % nz;
-        const R* Pl = s.P + l * Q;
-        const R* h = s.F + (size_t)d * Q * W + (t + 3);
-        R acc = 0;
-        for (int j = 0; j < Q; ++j) acc = fma(Pl[j], h[j * W], acc);
-        s.A[((size_t)d * Q + l) * Z + t] = acc;
-    }
-}
-
-// WENO-5 (Jiang & Shu) value at the face between v2 and v3, upwind side v0..v2.
-// The nonlinear weights omega_r = (d_r / e_r) / sum_s (d_s / e_s),
-// e_r = (eps + beta_r)^2, are formed with a single division.
-template <typename R>
-__device__ __forceinline__ R weno5(R v0, R v1, R v2, R v3, R v4, R eps) {
-    const R k6 = R(1) / R(6), k1312 = R(13) / R(12), qr = R(0.25);
-    R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * k6;
-    R q1 = (-v1 + R(5) * v2 + R(2) * v3) * k6;
-    R q2 = (R(2) * v2 + R(5) * v3 - v4) * k6;
-    R t0 = v0 - R(2) * v1 + v2, s0 = v0 - R(4) * v1 + R(3) * v2;
-    R t1 = v1 - R(2) * v2 + v3, s1 = v1 - v3;
-    R t2 = v2 - R(2) * v3 + v4, s2 = R(3) * v2 - R(4) * v3 + v4;
-    R e0 = eps + fma(k1312 * t0, t0, qr * s0 * s0);
-    R e1 = eps + fma(k1312 * t1, t1, qr * s1 * s1);
-    R e2 = eps + fma(k1312 * t2, t2, qr * s2 * s2);
-    e0 *= e0;
-    e1 *= e1;
-    e2 *= e2;
-    R a0 = R(0.1) * (e1 * e2), a1 = R(0.6) * (e0 * e2), a2 = R(0.3) * (e0 * e1);
-    return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
-}
-
-// Phase 3c: face values h_{i-1/2} for faces f = 0..nz (face f lies between
-// tile nodes f-1 and f), upwind by the sign of xi_k.
-template <typename R>
-__device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                      const R* __restrict__ rtab) {
-    const int Q = sd.Q, W = Z + 6, nf = it.nz + 1;
-    TableLayout L(Q);
-    const R* xi = rtab + sd.tab_off + L.xi;
-    const R eps = (R)sd.weno_eps;
-    for (int e = threadIdx.x; e < 2 * Q * nf; e += blockDim.x) {
-        int f = e % nf, r = e / nf;
-        int k = r % Q, d = r / Q;
-        const R* h = s.F + (size_t)(d * Q + k) * W;
-        R x = xi[k], v;
-        if (x > R(0)) v = weno5<R>(h[f], h[f + 1], h[f + 2], h[f + 3], h[f + 4], eps);
-        else if (x < R(0)) v = weno5<R>(h[f + 5], h[f + 4], h[f + 3], h[f + 2], h[f + 1], eps);
-        else v = 0;
-        s.Face[(size_t)(d * Q + k) * (Z + 1) + f] = v;
-    }
-}
-
-// Phase 4: add the force term F1 sqrt(l) a_{l-1} to the coefficients
-// (d/dxi [omega psi_{l-1}] = -sqrt(l) omega psi_l).
-template <typename R>
-__device__ void add_force(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                          const R* __restrict__ rtab) {
-    const int Q = sd.Q, nz = it.nz;
-    TableLayout L(Q);
-    const R* r1 = rtab + sd.tab_off + L.r1;
-    for (int e = threadIdx.x; e < 2 * (Q - 1) * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int l = 1 + r % (Q - 1), d = r / (Q - 1);
-        R f1 = s.Scr[Z + t];
-        s.C[((size_t)d * Q + l) * Z + t] =
-            fma(f1 * r1[l], s.A[((size_t)d * Q + l - 1) * Z + t], s.C[((size_t)d * Q + l) * Z + t]);
-    }
-}
-
-// One raw moment sum of one node from a column h[k * stride] (k < Q).  The
-// conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
-// (heat flux) in R.
-template <typename R>
-__device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
-                                             const double* __restrict__ xi, const R* __restrict__ rxi) {
-    const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
-    if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
-        which == MOM_G0) {
-        double acc = 0.0;
-        for (int k = 0; k < Q; ++k) {
-            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
-            acc = fma(wgt, (double)h[k * stride], acc);
-        }
-        return acc;
-    }
-    R racc = 0;
-    for (int k = 0; k < Q; ++k) {
-        R x = rxi[k], wgt = (p == 1) ? x : x * x * x;
-        racc = fma(wgt, h[k * stride], racc);
-    }
-    return (double)racc;
-}
-
-// Raw moment sums of the tile held in s.F (columns 3 .. nz+2).
-template <typename R>
-__device__ void tile_moment_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                 const double* __restrict__ xi, const R* __restrict__ rxi,
-                                 double* __restrict__ mom_out, long long NN) {
-    const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
-        int t = e % nz, which = e / nz;
-        int d = which >= MOM_G0 ? 1 : 0;
-        const R* h = s.F + (size_t)d * Q * W + t + 3;
-        mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xi, rxi);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Kernels

@@ -1,0 +1,149 @@
+"""GPU parity of the discrete adjoint against the oracle's tangent-linear maps.
+
+The adjoint of the time step (evfdlb_rhs_vjp, evfdlb_adjoint_state,
+evfdlb_adjoint) is checked against the complex-step tangent of the FP64
+oracle (pinned in test_oracle_tangent.py):
+  * the full transposed Jacobian of one right-hand side on a tiny slab, built
+    column by column from the oracle tangent, element by element;
+  * dot-product identities <w, J v> = <J^T w, v> on larger slabs with ragged
+    node tiles, both relaxation readings, Q = 8..32;
+  * the gradient of a loss of the final density after many steps with
+    checkpoints (ragged last segment) against oracle directional derivatives
+    along seeded directions in n0, a uniform change of T0, phi_a and F0.
+Bars: elementwise 1e-12 of the largest entry for the explicit transpose;
+dot products to 1e-11 of the Cauchy-Schwarz scale |w| |J v| (FP64 rounding
+of O(Q^2) sums); whole-trajectory directional derivatives to 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2503_15187_gb300 as ev
+from paper_2503_15187_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def nonequilibrium(orc, seed=4, steps=2):
+    rng = np.random.default_rng(seed)
+    nz = orc.s.nz
+    z = np.arange(nz)
+    n0 = 0.25 * (1 + 0.3 * np.sin(2 * np.pi * z / nz) + 0.02 * rng.uniform(-1, 1, nz))
+    u0 = 0.04 * np.cos(2 * np.pi * z / nz)
+    T0 = 0.6 * (1 + 0.05 * np.sin(4 * np.pi * z / nz))
+    F, G = orc.equilibrium(n0, u0, T0)
+    return orc.step(F, G, steps)
+
+
+def make(nz, Q, dz, relax=0, tile=None, ckpt=0):
+    sim = ev.Sim(ev.Params(nx=nz, dx=dz, Q=Q, relax_mode=relax, ckpt_every=ckpt))
+    if tile:
+        sim.tune(tile)
+    orc = O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=sim.dt(), relax=relax))
+    return sim, orc
+
+
+def test_rhs_transpose_jacobian_elementwise():
+    nz, Q = 16, 8
+    sim, orc = make(nz, Q, 0.25, tile=5)
+    F, G = nonequilibrium(orc)
+    sim.set_state(F.ravel(), G.ravel())
+    N = Q * nz
+    J = np.empty((2 * N, 2 * N))           # J[:, c] = d R / d x_c
+    for c in range(2 * N):
+        e = np.zeros(2 * N)
+        e[c] = 1.0
+        _, _, dF, dG = orc.rhs_tl(F, G, e[:N].reshape(Q, nz), e[N:].reshape(Q, nz))
+        J[:, c] = np.concatenate([dF.ravel(), dG.ravel()])
+    rng = np.random.default_rng(7)
+    for trial in range(2):
+        w = rng.uniform(-1, 1, 2 * N)
+        oF, oG, dphi = sim.rhs_vjp(w[:N], w[N:])
+        ref = J.T @ w
+        got = np.concatenate([oF, oG])
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        print(f"J^T w elementwise: {err:.2e}")
+        assert err < 1e-12
+        _, _, pF, pG = orc.rhs_tl(F, G, np.zeros((Q, nz)), np.zeros((Q, nz)), dphi=1.0)
+        ref_phi = w @ np.concatenate([pF.ravel(), pG.ravel()])
+        assert abs(dphi[0] - ref_phi) < 1e-12 * np.abs(w).sum() * np.abs(np.concatenate([pF.ravel(), pG.ravel()])).max()
+
+
+@pytest.mark.parametrize("case", [(64, 16, 0.25, 0, 7), (97, 24, 0.25, 0, 13), (50, 8, 0.25, 1, 64),
+                                  (150, 32, 0.1, 0, 27)])
+def test_rhs_dot_product_identity(case):
+    nz, Q, dz, relax, tile = case
+    sim, orc = make(nz, Q, dz, relax=relax, tile=tile)
+    F, G = nonequilibrium(orc)
+    sim.set_state(F.ravel(), G.ravel())
+    rng = np.random.default_rng(nz)
+    for trial in range(3):
+        vF, vG = F * rng.uniform(-1, 1, F.shape), G * rng.uniform(-1, 1, G.shape)
+        wF, wG = rng.uniform(-1, 1, F.shape), rng.uniform(-1, 1, G.shape)
+        dphi_dir = rng.uniform(-1, 1)
+        _, _, jF, jG = orc.rhs_tl(F, G, vF, vG, dphi=dphi_dir)
+        lhs = (wF * jF).sum() + (wG * jG).sum()
+        oF, oG, dphi = sim.rhs_vjp(wF.ravel(), wG.ravel())
+        rhs = (oF.reshape(Q, nz) * vF).sum() + (oG.reshape(Q, nz) * vG).sum() + dphi[0] * dphi_dir
+        scale = np.sqrt((wF ** 2).sum() + (wG ** 2).sum()) * np.sqrt((jF ** 2).sum() + (jG ** 2).sum())
+        print(f"{case}: <w,Jv> {lhs:.6e} <J^T w,v> {rhs:.6e} rel {abs(lhs - rhs) / scale:.2e}")
+        assert abs(lhs - rhs) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("case", [(32, 12, 0.25, 20, 6, 5), (40, 16, 0.25, 9, 9, 64)])
+def test_trajectory_gradient_against_oracle_tangent(case):
+    """Loss L = sum_z (n_end - n_target)^2 after `steps` steps from the
+    projected (n0, u0 = 0, T0), checkpoints every `ckpt` steps."""
+    nz, Q, dz, steps, ckpt, tile = case
+    sim, orc = make(nz, Q, dz, tile=tile, ckpt=ckpt)
+    rng = np.random.default_rng(2025)
+    z = np.arange(nz)
+    n0 = 0.25 * (1 + 0.05 * rng.uniform(-1, 1, nz))
+    u0 = np.zeros(nz)
+    T0 = np.full(nz, 0.55)
+    target = 0.25 * (1 + 0.02 * np.cos(2 * np.pi * z / nz + 0.3))
+    sim.init(n0, u0, T0)
+    sim.step(steps)
+    n_end = sim.moments(with_totals=False)[0]
+    dL_dn = 2.0 * (n_end - target)
+    g = sim.adjoint_state(np.repeat(dL_dn[None, :], Q, axis=0).ravel(), np.zeros(Q * nz))
+    dphi, dT, dn = sim.adjoint(dL_dn)
+    assert np.allclose(dphi, g["dphi"], rtol=1e-14, atol=0) and np.allclose(dn, g["dn0"], rtol=1e-14, atol=0)
+
+    def dL(dn0=None, dT0=None, dphi_dir=0.0):
+        dn0 = np.zeros(nz) if dn0 is None else dn0
+        dT0 = np.zeros(nz) if dT0 is None else dT0
+        F, G, tF, tG = orc.trajectory_tl(n0, u0, T0, dn0, np.zeros(nz), dT0, steps, dphi=dphi_dir)
+        n = F.sum(axis=0)
+        return (2.0 * (n - target) * tF.sum(axis=0)).sum()
+
+    d = rng.uniform(-1, 1, nz)
+    checks = [("n0 direction", dL(dn0=d), (g["dn0"] * d).sum()),
+              ("uniform T0", dL(dT0=np.ones(nz)), g["dT0"].sum()),
+              ("phi_a", dL(dphi_dir=1.0), g["dphi"][0])]
+    for name, ref, got in checks:
+        print(f"{case} {name}: oracle {ref:.10e} gpu {got:.10e}")
+        assert abs(got - ref) < 1e-9 * abs(ref), name
+    # the cotangent of the initial distributions
+    F0, G0 = orc.equilibrium(n0, u0, T0)
+    vF, vG = F0 * rng.uniform(-1, 1, F0.shape), G0 * rng.uniform(-1, 1, G0.shape)
+    F, G, tF, tG = orc.step_tl(F0, G0, vF, vG, steps)
+    ref = (2.0 * (F.sum(axis=0) - target) * tF.sum(axis=0)).sum()
+    got = (g["dF0"].reshape(Q, nz) * vF).sum() + (g["dG0"].reshape(Q, nz) * vG).sum()
+    print(f"{case} F0 direction: oracle {ref:.10e} gpu {got:.10e}")
+    assert abs(got - ref) < 1e-9 * abs(ref)
+
+
+def test_adjoint_requires_tracking_and_periodic():
+    sim = ev.Sim(ev.Params(nx=32, dx=0.25, Q=8))                 # ckpt_every = 0
+    sim.init(np.full(32, 0.25), np.zeros(32), np.full(32, 0.6))
+    sim.step(2)
+    with pytest.raises(ev.EvfdlbError) as e:
+        sim.adjoint(np.ones(32))
+    assert e.value.code == -7
+    sim = ev.Sim(ev.Params(nx=32, dx=0.25, Q=8, bc=ev.BC_OUTFLOW, ckpt_every=4))
+    sim.init(np.full(32, 0.25), np.zeros(32), np.full(32, 0.6))
+    sim.step(2)
+    with pytest.raises(ev.EvfdlbError) as e:
+        sim.adjoint(np.ones(32))
+    assert e.value.code == -8
