@@ -217,7 +217,8 @@ def run_ours(args, rank, world):
     }
     n64 = sim.moments(with_totals=False)[0]
     sim.close()
-    line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)}
+    line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
+                        "adjoint": adjoint_leg(ev, W, stream)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
     return line
@@ -251,6 +252,38 @@ def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)
             "transport, gradients, conserved sums)", "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
             "gpu_launches": 3 * args.steps}
+
+
+def adjoint_leg(ev, W, stream, steps=200):
+    """Cost of the discrete adjoint against the forward run on the adjoint
+    calibration workload (periodic slab Nz = 1024, dz = 0.25, Q = 24,
+    T = 0.7 T_c, mean n = 0.25 with +-1% noise, checkpoint every 100 steps),
+    over `steps` steps: backward (segment recompute + reverse sweep + initial
+    projection) / forward (steps with checkpoint copies)."""
+    import numpy as np
+    import torch
+    nz, Q, dz = 1024, 24, 0.25
+    p = ev.Params(nx=nz, dx=dz, Q=Q, ckpt_every=100)
+    T = 0.7 * ev.critical_T(p)
+    n0 = W.noisy_uniform(nz, 0.25, 0.01)
+    sim = ev.Sim(p, stream=stream)
+    times = []
+    for rep in range(2):                  # the first pass allocates the work buffers
+        sim.init(n0, np.zeros(nz), np.full(nz, T))
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        sim.step(steps)
+        e[1].record(stream)
+        n = sim.moments(with_totals=False)[0]
+        sim.adjoint(2.0 * (n - 0.25))
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        times.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+    sim.close()
+    fwd, bwd = times[-1]
+    return {"workload": f"periodic Nz={nz}, dz={dz}, Q={Q}, {steps} steps, checkpoint every 100", "forward_ms": fwd,
+            "backward_ms": bwd, "backward_over_forward": bwd / fwd}
 
 
 def cpu_baseline(budget_s, T, n0, max_steps=10**9):

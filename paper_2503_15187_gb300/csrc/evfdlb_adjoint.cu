@@ -10,18 +10,19 @@
 // and the stage input u (recomputed from a checkpoint), forms
 //   out     = ca ybar + J(u)^T v + cc acc_in,   v = cb dt ybar,
 //   acc_out = cacc acc_in + cy ybar,
-// where J(u) is the Jacobian of L at u, in three launches:
+// where J(u) is the Jacobian of L at u, in two launches:
 //   adj_local_kernel  -- per node tile: the velocity-space part of J^T v
 //                        (transposed Hermite synthesis and analysis, the
 //                        transposed WENO-5 faces, relaxation) and the adjoints
 //                        of the node fields that L reads (n, u, T, q, chi, X,
 //                        the three gradients and the force F1);
-//   adj_nodes_kernel  -- per node: transposed fourth-order differences and
-//                        the chain X = n^2 chi T, chi(nbar) of Eq. (carnstar);
-//   adj_moments_kernel-- per node: transposed Fischer-Methfessel average and
-//                        transposed Eq. (F1) convolution (correlations), the
-//                        chain from (n, u, T, q) to the raw moment sums, and
-//                        their transpose onto F and G.
+//   adj_moments_kernel-- per node tile: transposed fourth-order differences,
+//                        the chain X = n^2 chi T, chi(nbar) of Eq. (carnstar)
+//                        (on the tile and a Fischer-Methfessel halo), the
+//                        transposed Fischer-Methfessel average and Eq. (F1)
+//                        convolution (correlations), the chain from
+//                        (n, u, T, q) to the raw moment sums, and their
+//                        transpose onto F and G.
 // Forward quantities are recomputed from the stage input and its raw moment
 // sums with the same device code as the forward kernels.
 #include <cuda_runtime.h>
@@ -33,24 +34,24 @@ namespace evfdlb {
 
 // per-node adjoints written by adj_local_kernel ([kNumNodeAdj][NN])
 enum { AD_N = 0, AD_U, AD_T, AD_Q, AD_CHI, AD_X, AD_DX, AD_DT, AD_DU, AD_F1, kNumNodeAdj };
-// per-node adjoints written by adj_nodes_kernel ([kNumNodeAdjB][NN])
-enum { AB_N = 0, AB_U, AB_T, AB_NBAR, kNumNodeAdjB };
 
 constexpr int kHaloH = 5;   // state halo of the transposed WENO-5 faces
 constexpr int kHaloV = 3;   // halo of v
 
 struct AdjSmem {
-    Smem<double> f;   // P, S, N, U, T, X, Chi, Sc, Scr of the forward layout
+    Smem<double> f;   // S, N, U, T, X, Chi, Sc, Scr of the forward layout; f.P holds
+                      // the scaled transposed analysis table PT[l][j] = sqrt(l) psi_{l-1}(xi_j)
     double* H;        // state tile [2][Q][Z + 2 kHaloH]
     double* V;        // v tile [2][Q][Z + 2 kHaloV]
     double* Cb;       // cbar_l = sum_k S_kl v_k, [2][Q][Z]
-    double* Ae;       // analysis a_l of the state, [2][Q][Z]; reused for the WENO part
+    double* Ha;       // sum_l PT[l][j] cbar_l, [2][Q][Z]
+    double* Hw;       // transposed WENO-5 part, [2][Q][Z]
     double* Red;      // per (distribution, node) sums [2][8][Z]
 };
 
 __host__ __device__ inline size_t adj_smem_doubles(int Q, int Z, int M) {
     return 2 * (size_t)Q * Q + (Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + 2 * (size_t)Z +
-           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 4 * (size_t)Q * Z + 16 * (size_t)Z;
+           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 6 * (size_t)Q * Z + 16 * (size_t)Z;
 }
 
 __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
@@ -69,8 +70,9 @@ __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
     s.H = s.f.Scr + 2 * Z;
     s.V = s.H + 2 * Q * (Z + 2 * kHaloH);
     s.Cb = s.V + 2 * Q * (Z + 2 * kHaloV);
-    s.Ae = s.Cb + 2 * Q * Z;
-    s.Red = s.Ae + 2 * Q * Z;
+    s.Ha = s.Cb + 2 * Q * Z;
+    s.Hw = s.Ha + 2 * Q * Z;
+    s.Red = s.Hw + 2 * Q * Z;
     return s;
 }
 
@@ -145,18 +147,15 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     }
     __syncthreads();
     node_fields<double>(sd, it, s.f, Z, taps, taps, mom, NN, err, nullptr);
+    // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
+    // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term
+    for (int e = threadIdx.x; e < Q * Q; e += blockDim.x) {
+        int l = e / Q, j = e % Q;
+        s.f.P[e] = (l == 0) ? 0.0 : r1[l] * tab[L.P + (l - 1) * Q + j];
+    }
     __syncthreads();
 
-    // phase 1: analysis a_l (l <= Q-2) and transposed synthesis cbar_l
-    for (int e = threadIdx.x; e < 2 * (Q - 1) * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int l = r % (Q - 1), d = r / (Q - 1);
-        const double* Pl = s.f.P + l * Q;
-        const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
-        double acc = 0.0;
-        for (int j = 0; j < Q; ++j) acc = fma(Pl[j], h[j * WH], acc);
-        s.Ae[((size_t)d * Q + l) * Z + t] = acc;
-    }
+    // phase 1: transposed synthesis cbar_l = sum_k S_kl v_k
     for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
         int l = r % Q, d = r / Q;
@@ -164,6 +163,18 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         double acc = 0.0;
         for (int k = 0; k < Q; ++k) acc = fma(s.f.S[k * Q + l], v[k * WV], acc);
         s.Cb[((size_t)d * Q + l) * Z + t] = acc;
+    }
+    __syncthreads();
+    // phase 1b: Ha_j = sum_l sqrt(l) psi_{l-1}(xi_j) cbar_l, the transposed analysis
+    // of the force term c_l += F1 sqrt(l) a_{l-1} (times F1 in phase 4); with
+    // a_{l-1} = sum_j psi_{l-1}(xi_j) h_j it also gives F1b = sum_j h_j Ha_j.
+    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int j = r % Q, d = r / Q;
+        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
+        double acc = 0.0;
+        for (int l = 1; l < Q; ++l) acc = fma(s.f.P[l * Q + j], cbar[l * Z], acc);
+        s.Ha[(size_t)r * Z + t] = acc;
     }
     __syncthreads();
 
@@ -191,7 +202,6 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
             c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
         }
         const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-        const double* a = s.Ae + (size_t)d * Q * Z + t;
         double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
         double cm1 = 0.0, cm2 = 0.0;      // c_{l-1}, c_{l-2}
         double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, fb = 0;
@@ -204,7 +214,6 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
             b3 = fma(cl, w3, b3);
             ub = fma(cl * r1[l], cm1, ub);
             Tb = fma(cl * 0.5 * r2[l], cm2, Tb);
-            if (l >= 1) fb = fma(cl * r1[l], a[(l - 1) * Z], fb);
             double c = c0 * m0 + c1 * w1 + c2 * w2 + c3 * w3;
             cm2 = cm1;
             cm1 = c;
@@ -217,7 +226,11 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         double nb = 0.0;
         const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
         const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
-        for (int k = 0; k < Q; ++k) nb = fma(-h[k * WH], v[k * WV], nb);
+        const double* ha = s.Ha + (size_t)d * Q * Z + t;
+        for (int k = 0; k < Q; ++k) {
+            nb = fma(-h[k * WH], v[k * WV], nb);
+            fb = fma(h[k * WH], ha[k * Z], fb);
+        }
         double* red = s.Red + (size_t)d * 8 * Z + t;
         red[0] = b0;
         red[Z] = b1;
@@ -346,50 +359,56 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         phis[o] += F1b * F1;
     }
 
-    // phase 3b: transposed WENO-5 faces, one warp per velocity row.  For a
-    // chunk of up to 28 tile nodes, lane L owns one face; the node at lane L'
-    // collects the five faces that read it from lanes L'..L'+4.
+    // phase 3b: transposed WENO-5 faces.  A velocity row is cut into chunks of
+    // up to 28 tile nodes; a chunk's cn + 4 faces occupy a segment of cn + 4
+    // consecutive lanes (one face per lane), and a warp carries as many
+    // segments (rows) as fit in 32 lanes.  Each lane forms the five
+    // derivatives of its face value times the face adjoint, ordered so that
+    // the node at segment lane L' collects g'[s] from segment lane L' + s,
+    // s = 0..4 (the five faces that read it).
     {
         const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
         const double rdz = sd.inv_dx, eps = sd.weno_eps;
-        double* HB = s.Ae;    // the analysis is no longer needed: [2][Q][Z]
-        __syncthreads();      // all phase-2 reads of Ae are done
-        for (int row = warp; row < 2 * Q; row += nwarps) {
-            const int k = row % Q;
-            const double x = xi[k];
-            const double* h = s.H + (size_t)row * WH + kHaloH;   // h[i], i tile-relative
-            const double* v = s.V + (size_t)row * WV + kHaloV;
-            for (int c0 = 0; c0 < nz; c0 += 28) {
-                const int cn = min(28, nz - c0);
-                double g[5] = {0, 0, 0, 0, 0};
-                if (x != 0.0 && lane < cn + 4) {
+        const int nchunk = (nz + 27) / 28;
+        const int cmax = min(28, nz), seg = cmax + 4;
+        const int per_warp = 32 / seg;                 // segments per warp
+        const int nseg = 2 * Q * nchunk;               // (row, chunk) pairs
+        const int sub = lane / seg, sl = lane % seg;
+        for (int base = warp * per_warp; base < nseg; base += nwarps * per_warp) {
+            const int sid = base + sub;
+            const bool active = (sub < per_warp) && (sid < nseg);
+            double g[5] = {0, 0, 0, 0, 0};
+            int row = 0, c0 = 0, cn = 0;
+            double x = 0.0;
+            if (active) {
+                row = sid / nchunk;
+                c0 = (sid % nchunk) * 28;
+                cn = min(28, nz - c0);
+                x = xi[row % Q];
+                const double* h = s.H + (size_t)row * WH + kHaloH;   // h[i], i tile-relative
+                const double* v = s.V + (size_t)row * WV + kHaloV;
+                if (x != 0.0 && sl < cn + 4) {
+                    double gg[5];
                     if (x > 0.0) {
-                        int f = c0 - 1 + lane;            // face between nodes f-1 and f
+                        int f = c0 - 1 + sl;                     // face between nodes f-1 and f
                         double pb = x * rdz * (v[f] - v[f - 1]);
-                        weno5_grad(h[f - 3], h[f - 2], h[f - 1], h[f], h[f + 1], eps, pb, g);
+                        weno5_grad(h[f - 3], h[f - 2], h[f - 1], h[f], h[f + 1], eps, pb, gg);
+                        g[0] = gg[4]; g[1] = gg[3]; g[2] = gg[2]; g[3] = gg[1]; g[4] = gg[0];
                     } else {
-                        int f = c0 - 2 + lane;
+                        int f = c0 - 2 + sl;
                         double pb = x * rdz * (v[f] - v[f - 1]);
-                        weno5_grad(h[f + 2], h[f + 1], h[f], h[f - 1], h[f - 2], eps, pb, g);
+                        weno5_grad(h[f + 2], h[f + 1], h[f], h[f - 1], h[f - 2], eps, pb, gg);
+                        g[0] = gg[0]; g[1] = gg[1]; g[2] = gg[2]; g[3] = gg[3]; g[4] = gg[4];
                     }
                 }
-                double acc;
-                const int src0 = min(lane, 27);
-                if (x > 0.0) {
-                    acc = __shfl_sync(0xffffffffu, g[4], src0);
-                    acc += __shfl_sync(0xffffffffu, g[3], src0 + 1);
-                    acc += __shfl_sync(0xffffffffu, g[2], src0 + 2);
-                    acc += __shfl_sync(0xffffffffu, g[1], src0 + 3);
-                    acc += __shfl_sync(0xffffffffu, g[0], src0 + 4);
-                } else {
-                    acc = __shfl_sync(0xffffffffu, g[0], src0);
-                    acc += __shfl_sync(0xffffffffu, g[1], src0 + 1);
-                    acc += __shfl_sync(0xffffffffu, g[2], src0 + 2);
-                    acc += __shfl_sync(0xffffffffu, g[3], src0 + 3);
-                    acc += __shfl_sync(0xffffffffu, g[4], src0 + 4);
-                }
-                if (lane < cn) HB[(size_t)row * Z + c0 + lane] = (x != 0.0) ? acc : 0.0;
             }
+            const int src = min(lane, 27);               // keeps src + 4 <= 31
+            double acc = __shfl_sync(0xffffffffu, g[0], src);
+            acc += __shfl_sync(0xffffffffu, g[1], src + 1);
+            acc += __shfl_sync(0xffffffffu, g[2], src + 2);
+            acc += __shfl_sync(0xffffffffu, g[3], src + 3);
+            acc += __shfl_sync(0xffffffffu, g[4], src + 4);
+            if (active && sl < cn) s.Hw[(size_t)row * Z + c0 + sl] = (x != 0.0) ? acc : 0.0;
         }
     }
     __syncthreads();
@@ -398,12 +417,9 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
         int j = r % Q, d = r / Q;
-        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-        double hb = 0.0;   // analysis^T of abar_{l-1} = F1 sqrt(l) cbar_l
-        for (int l = 1; l < Q; ++l) hb = fma(s.f.P[(l - 1) * Q + j] * r1[l], cbar[l * Z], hb);
         double F1 = s.f.Sc[SC_FORCE * Z + t], nu = s.f.Sc[SC_NU * Z + t];
         double vv = s.V[(size_t)r * WV + t + kHaloV];
-        double val = F1 * hb - nu * vv + s.Ae[(size_t)r * Z + t];
+        double val = fma(F1, s.Ha[(size_t)r * Z + t], fma(-nu, vv, s.Hw[(size_t)r * Z + t]));
         long long g = d * NF + sd.f_off + (long long)j * nx + it.i0 + t;
         double yb = ybar[g];
         double o = fma(ca, yb, val);
@@ -413,79 +429,81 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     }
 }
 
-// Per node: transposed fourth-order differences of X, T, u and the chain
-// X = n^2 chi T, chi = chi(eta), eta = pi sigma^3 nbar / 6 (Eq. (carnstar)).
+// Per node tile: transposed fourth-order differences of X, T, u, the chain
+// X = n^2 chi T, chi = chi(eta), eta = pi sigma^3 nbar / 6 (Eq. (carnstar)) on
+// the tile and its Fischer-Methfessel halo, the transposed Fischer-Methfessel
+// average and Eq. (F1) convolution (correlations with the same taps), the
+// chain (n, u, T, q) <- raw sums, and
+// out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
+__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m) {
+    return 5 * (size_t)(Z + 2 * m) + (size_t)kNumMoments * Z;
+}
+
 __global__ void __launch_bounds__(kThreads)
-adj_nodes_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-                 const double* __restrict__ taps, const double* __restrict__ mom,
-                 const double* __restrict__ nadj, double* __restrict__ nbo, long long NN) {
+adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                   const double* __restrict__ tables, const double* __restrict__ taps,
+                   const double* __restrict__ mom, const double* __restrict__ nadj, double* out, long long NF,
+                   long long NN, int Z) {
+    extern __shared__ double sm[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
-    const int nx = sd.nx, bc = sd.bc, m = sd.m;
-    const double* mtap = taps + sd.tap_off + 2 * sd.M + 1;
+    const int nx = sd.nx, bc = sd.bc, M = sd.M, m = sd.m, Q = sd.Q, nz = it.nz;
+    const int HW = Z + 2 * m;
+    double* sXb = sm;              // X adjoint on [i0 - m, i0 + nz + m)
+    double* sNb = sXb + HW;        // nbar adjoint (source of the FM correlation)
+    double* sn = sNb + HW;         // n, T, chi on the same nodes
+    double* sT = sn + HW;
+    double* schi = sT + HW;
+    double* sb = schi + HW;        // [kNumMoments][Z] raw-sum adjoints of the tile
+    const double* ftap = taps + sd.tap_off;
+    const double* mtap = ftap + 2 * M + 1;
     const double inv12 = sd.inv_dx / 12.0;
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
     const double* S2 = mom + MOM_S2 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz; t += blockDim.x) {
-        const int i = it.i0 + t;
+    auto d4t = [&](int which, int i) {
+        const double* g = nadj + which * NN + sd.node_off;
+        return (g[gidx(i + 2, nx, bc)] - 8.0 * g[gidx(i + 1, nx, bc)] + 8.0 * g[gidx(i - 1, nx, bc)] -
+                g[gidx(i - 2, nx, bc)]) * inv12;
+    };
+    for (int c = threadIdx.x; c < nz + 2 * m; c += blockDim.x) {
+        const int i = gidx(it.i0 - m + c, nx, bc);
         double n = S0[i], u = S1[i] / n;
         double T = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) / n - 0.5 * u * u);
         double nbF = 0.0;
         for (int j = -m; j <= m; ++j) nbF = fma(mtap[j + m], S0[gidx(i + j, nx, bc)], nbF);
         double eta = sd.eta_coef * nbF, om = 1.0 - eta;
         double chi = (2.0 - eta) / (2.0 * om * om * om);
-        auto d4t = [&](int which) {
-            const double* g = nadj + which * NN + sd.node_off;
-            return (g[gidx(i + 2, nx, bc)] - 8.0 * g[gidx(i + 1, nx, bc)] + 8.0 * g[gidx(i - 1, nx, bc)] -
-                    g[gidx(i - 2, nx, bc)]) * inv12;
-        };
         long long o = sd.node_off + i;
-        double Xb = nadj[AD_X * NN + o] + d4t(AD_DX);
-        double Tb = nadj[AD_T * NN + o] + d4t(AD_DT) + Xb * n * n * chi;
-        double ub = nadj[AD_U * NN + o] + d4t(AD_DU);
-        double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
+        double Xb = nadj[AD_X * NN + o] + d4t(AD_DX, i);
         double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
         double dchi = (5.0 - 2.0 * eta) / (2.0 * om * om * om * om);
-        nbo[AB_N * NN + o] = nb;
-        nbo[AB_U * NN + o] = ub;
-        nbo[AB_T * NN + o] = Tb;
-        nbo[AB_NBAR * NN + o] = chib * dchi * sd.eta_coef;
+        sXb[c] = Xb;
+        sNb[c] = chib * dchi * sd.eta_coef;
+        sn[c] = n;
+        sT[c] = T;
+        schi[c] = chi;
     }
-}
-
-// Per node: transposed Fischer-Methfessel average and Eq. (F1) convolution
-// (correlations with the same taps), the chain (n, u, T, q) <- raw sums, and
-// out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
-__global__ void __launch_bounds__(kThreads)
-adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-                   const double* __restrict__ tables, const double* __restrict__ taps,
-                   const double* __restrict__ mom, const double* __restrict__ nadj,
-                   const double* __restrict__ nbo, double* out, long long NF, long long NN) {
-    __shared__ double sb[kNumMoments][kZMax];
-    const WorkItem it = items[blockIdx.x];
-    const SlabDesc sd = slabs[it.slab];
-    const int nx = sd.nx, bc = sd.bc, M = sd.M, m = sd.m, Q = sd.Q, nz = it.nz;
-    const double* ftap = taps + sd.tap_off;
-    const double* mtap = ftap + 2 * M + 1;
+    __syncthreads();
     for (int t = threadIdx.x; t < nz; t += blockDim.x) {
-        const int i = it.i0 + t;
+        const int i = it.i0 + t, c = t + m;
         long long o = sd.node_off + i;
-        const double* nbar = nbo + AB_NBAR * NN + sd.node_off;
         const double* f1b = nadj + AD_F1 * NN + sd.node_off;
-        double nb = nbo[AB_N * NN + o];
-        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], nbar[gidx(i - j, nx, bc)], nb);
+        double n = sn[c], T = sT[c], chi = schi[c], Xb = sXb[c];
+        double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
+        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], sNb[c - j], nb);
         for (int j = -M; j <= M; ++j) nb = fma(ftap[j + M], f1b[gidx(i - j, nx, bc)], nb);
-        double ub = nbo[AB_U * NN + o], Tb = nbo[AB_T * NN + o], qb = nadj[AD_Q * NN + o];
-        double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
-        double G0 = mom[MOM_G0 * NN + o];
-        double n = S0, u = S1 / n;
-        double E = (0.5 * S2 + G0) / n;
+        double ub = nadj[AD_U * NN + o] + d4t(AD_DU, i);
+        double Tb = nadj[AD_T * NN + o] + d4t(AD_DT, i) + Xb * n * n * chi;
+        double qb = nadj[AD_Q * NN + o];
+        double S0v = S0[i], S1v = S1[i], S2v = S2[i], G0v = G0[i];
+        double u = S1v / n;
+        double E = (0.5 * S2v + G0v) / n;
         // q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
         double S3b = 0.5 * qb, S2b = -1.5 * u * qb, S1b = 1.5 * u * u * qb, S0b = -0.5 * u * u * u * qb;
         double G1b = qb, G0b = -u * qb;
-        ub += qb * (-1.5 * S2 + 3.0 * u * S1 - 1.5 * u * u * S0 - G0);
+        ub += qb * (-1.5 * S2v + 3.0 * u * S1v - 1.5 * u * u * S0v - G0v);
         // T = (2/3)(E - u^2/2), E = (S2/2 + G0)/n
         double Eb = (2.0 / 3.0) * Tb;
         ub += -(2.0 / 3.0) * u * Tb;
@@ -496,12 +514,12 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         S1b += ub / n;
         nb += -ub * u / n;
         S0b += nb;
-        sb[MOM_S0][t] = S0b;
-        sb[MOM_S1][t] = S1b;
-        sb[MOM_S2][t] = S2b;
-        sb[MOM_S3][t] = S3b;
-        sb[MOM_G0][t] = G0b;
-        sb[MOM_G1][t] = G1b;
+        sb[MOM_S0 * Z + t] = S0b;
+        sb[MOM_S1 * Z + t] = S1b;
+        sb[MOM_S2 * Z + t] = S2b;
+        sb[MOM_S3 * Z + t] = S3b;
+        sb[MOM_G0 * Z + t] = G0b;
+        sb[MOM_G1 * Z + t] = G1b;
     }
     __syncthreads();
     TableLayout L(Q);
@@ -510,8 +528,8 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         int t = e % nz, r = e / nz;
         int k = r % Q, d = r / Q;
         double x = xi[k];
-        double add = (d == 0) ? sb[MOM_S0][t] + x * (sb[MOM_S1][t] + x * (sb[MOM_S2][t] + x * sb[MOM_S3][t]))
-                              : sb[MOM_G0][t] + x * sb[MOM_G1][t];
+        double add = (d == 0) ? sb[MOM_S0 * Z + t] + x * (sb[MOM_S1 * Z + t] + x * (sb[MOM_S2 * Z + t] + x * sb[MOM_S3 * Z + t]))
+                              : sb[MOM_G0 * Z + t] + x * sb[MOM_G1 * Z + t];
         out[d * NF + sd.f_off + (long long)k * nx + it.i0 + t] += add;
     }
 }
@@ -581,21 +599,24 @@ adj_phi_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ ph
 // ---------------------------------------------------------------------------
 size_t adj_smem_bytes(int Q, int Z, int M) { return adj_smem_doubles(Q, Z, M) * sizeof(double); }
 
-cudaError_t configure_adjoint(size_t smem_bytes) {
-    return cudaFuncSetAttribute(adj_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+size_t adj_moments_smem_bytes(int Z, int m) { return adj_moments_smem_doubles(Z, m) * sizeof(double); }
+
+cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(adj_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(adj_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_bytes);
 }
 
-// One stage of the reverse sweep (see the file comment); nadj [10][NN] and
-// nbo [4][NN] are work arrays, phis [NN] accumulates F1b * F1.
-void launch_adj_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                      const double* tables, const double* taps, const double* src, const double* mom,
-                      const double* ybar, const double* acc_in, double* acc_out, double* out, double* nadj,
-                      double* nbo, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
+// One stage of the reverse sweep (see the file comment); nadj [10][NN] is a
+// work array, phis [NN] accumulates F1b * F1.
+void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
+                      const WorkItem* items, const double* tables, const double* taps, const double* src,
+                      const double* mom, const double* ybar, const double* acc_in, double* acc_out, double* out,
+                      double* nadj, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
                       double cc, double cacc, double cy, int Z, unsigned* err) {
     adj_local_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, taps, src, mom, ybar, acc_in, acc_out,
                                                      out, nadj, phis, NF, NN, ca, cb, use_dt, cc, cacc, cy, Z, err);
-    adj_nodes_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, taps, mom, nadj, nbo, NN);
-    adj_moments_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, tables, taps, mom, nadj, nbo, out, NF, NN);
+    adj_moments_kernel<<<nitems, kThreads, smem2, st>>>(slabs, items, tables, taps, mom, nadj, out, NF, NN, Z);
 }
 
 void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,

@@ -38,11 +38,12 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
 void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
                    long long NN, double* out);
 size_t adj_smem_bytes(int Q, int Z, int M);
-cudaError_t configure_adjoint(size_t smem_bytes);
-void launch_adj_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
-                      const double* tables, const double* taps, const double* src, const double* mom,
-                      const double* ybar, const double* acc_in, double* acc_out, double* out, double* nadj,
-                      double* nbo, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
+size_t adj_moments_smem_bytes(int Z, int m);
+cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
+void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
+                      const WorkItem* items, const double* tables, const double* taps, const double* src,
+                      const double* mom, const double* ybar, const double* acc_in, double* acc_out, double* out,
+                      double* nadj, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
                       double cc, double cacc, double cy, int Z, unsigned* err);
 void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                      const double* tables, const double* init_fields, const double* lam, double* dn0, double* du0,
@@ -80,7 +81,7 @@ struct evfdlb_ctx {
     cudaGraphExec_t g_chunk = nullptr;
     cudaGraphExec_t g_one = nullptr;
     int chunk = 16;
-    int Qmax = 0, Mmax = 0;
+    int Qmax = 0, Mmax = 0, mmax = 0;
     size_t items_cap = 0;        // capacity of the device work list
     bool have_state = false;
     bool poisoned = false;
@@ -204,7 +205,7 @@ evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
         for (int s = 0; s < c->nbatch; ++s) phi[s] = c->params[s].phi_a;
         double* dphi = c->adj + 4 * 2 * c->NF + 15 * c->NN;
         TRY_CUDA(cudaMemcpy(dphi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
-        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax)));
+        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax), adj_moments_smem_bytes(kZMax, c->mmax)));
     }
     if (!c->seg && c->ckpt_every > 0) {
         size_t nst = 3 * (size_t)c->ckpt_every + 1;
@@ -226,10 +227,10 @@ evfdlb_status adjoint_supported(evfdlb_ctx* c) {
 void adj_stage(evfdlb_ctx* c, const double* src, const double* mom, const double* ybar, const double* acc_in,
                double* acc_out, double* out, double ca, double cb, int use_dt, double cc, double cacc, double cy) {
     double* nadj = c->adj + 4 * 2 * c->NF;
-    double* nbo = nadj + 10 * c->NN;
-    double* phis = nbo + 4 * c->NN;
-    launch_adj_stage((int)c->items_h.size(), adj_smem_bytes(c->Qmax, c->Z, c->Mmax), c->user, c->slabs, c->items, c->tables, c->taps, src, mom,
-                     ybar, acc_in, acc_out, out, nadj, nbo, phis, c->NF, c->NN, ca, cb, use_dt, cc, cacc, cy, c->Z,
+    double* phis = nadj + 14 * c->NN;
+    launch_adj_stage((int)c->items_h.size(), adj_smem_bytes(c->Qmax, c->Z, c->Mmax),
+                     adj_moments_smem_bytes(c->Z, c->mmax), c->user, c->slabs, c->items, c->tables, c->taps, src,
+                     mom, ybar, acc_in, acc_out, out, nadj, phis, c->NF, c->NN, ca, cb, use_dt, cc, cacc, cy, c->Z,
                      c->err);
 }
 
@@ -336,7 +337,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     // taps, slab descriptors, work items
     std::vector<double> taps;
     long long NF = 0, NN = 0;
-    int Qmax = 0, Mmax = 0;
+    int Qmax = 0, Mmax = 0, mmax = 0;
     for (int s = 0; s < nbatch; ++s) {
         const evfdlb_params& q = ps[s];
         SlabDesc d;
@@ -365,12 +366,14 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         NN += q.nx;
         Qmax = std::max(Qmax, q.Q);
         Mmax = std::max(Mmax, d.M);
+        mmax = std::max(mmax, d.m);
         c->slabs_h.push_back(d);
     }
     c->NF = NF;
     c->NN = NN;
     c->Qmax = Qmax;
     c->Mmax = Mmax;
+    c->mmax = mmax;
     // node tile: one wave of CTAs over the SMs when possible
     long long z = (NN + sms - 1) / sms;
     partition(c, (int)std::min<long long>(std::max<long long>(z, 1), kZMax));

@@ -147,3 +147,85 @@ def test_adjoint_requires_tracking_and_periodic():
     with pytest.raises(ev.EvfdlbError) as e:
         sim.adjoint(np.ones(32))
     assert e.value.code == -8
+
+
+def test_autograd_function_small_against_oracle():
+    """EVRun (torch.autograd.Function) on a small periodic slab: phi_a.grad,
+    T0.grad and n0.grad of L = sum (n_end - target)^2 against the oracle's
+    complex-step directional derivatives."""
+    import torch
+    from paper_2503_15187_gb300.autograd import EVRun
+    nz, Q, dz, steps = 32, 12, 0.25, 15
+    p = ev.Params(nx=nz, dx=dz, Q=Q, ckpt_every=4)
+    rng = np.random.default_rng(99)
+    n0h = 0.25 * (1 + 0.05 * rng.uniform(-1, 1, nz))
+    target = torch.full((nz,), 0.25, dtype=torch.float64, device="cuda")
+    phi = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    T0 = torch.tensor(0.55, dtype=torch.float64, requires_grad=True)
+    n0 = torch.tensor(n0h, dtype=torch.float64, device="cuda", requires_grad=True)
+    n_end = EVRun.apply(phi, T0, n0, p, steps)
+    loss = ((n_end - target) ** 2).sum()
+    loss.backward()
+    xi, _ = O.gauss_hermite(Q)
+    orc = O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=0.5 * dz / np.abs(xi).max()))
+    tgt = target.cpu().numpy()
+
+    def dL(dn0, dT0, dphi):
+        F, G, tF, tG = orc.trajectory_tl(n0h, np.zeros(nz), np.full(nz, 0.55), dn0, np.zeros(nz), dT0, steps,
+                                         dphi=dphi)
+        return (2.0 * (F.sum(axis=0) - tgt) * tF.sum(axis=0)).sum()
+
+    d = rng.uniform(-1, 1, nz)
+    for name, ref, got in [("phi_a", dL(np.zeros(nz), np.zeros(nz), 1.0), float(phi.grad)),
+                           ("T0", dL(np.zeros(nz), np.ones(nz), 0.0), float(T0.grad)),
+                           ("n0", dL(d, np.zeros(nz), 0.0), float((n0.grad.cpu().numpy() * d).sum()))]:
+        print(f"autograd {name}: oracle {ref:.10e} gpu {got:.10e}")
+        assert abs(got - ref) < 1e-9 * abs(ref), name
+
+
+def test_adjoint_calibration_full_size_against_central_differences():
+    """Adjoint calibration workload: periodic slab Nz = 1024, dz = 0.25, Q = 24,
+    2000 steps at CFL 0.5, T = 0.7 T_c, mean n = 0.25 with +-1% seeded noise,
+    checkpoint every 100 steps; loss = sum_z (n(z, t_end) - n_target(z))^2
+    with n_target from a seeded forward run at perturbed phi_a and T.
+    Gradients through the autograd function against central differences
+    (h = 1e-6) of forward runs, for phi_a, T and four seeded directions in n0:
+    agreement to 1e-6 relative."""
+    import torch
+    from paper_2503_15187_gb300.autograd import EVRun
+    nz, Q, dz, steps = 1024, 24, 0.25, 2000
+    p = ev.Params(nx=nz, dx=dz, Q=Q, ckpt_every=100)
+    T = 0.7 * ev.critical_T(p)
+    n0h = W.noisy_uniform(nz, 0.25, 0.01)
+    rng = np.random.default_rng(15187)
+    phi_t, T_t = 1.0 + 0.05 * rng.uniform(-1, 1), T * (1 + 0.02 * rng.uniform(-1, 1))
+
+    def forward(phi, Tv, n0):
+        sim = ev.Sim(ev.Params(nx=nz, dx=dz, Q=Q, phi_a=phi))
+        sim.init(n0, np.zeros(nz), np.full(nz, Tv))
+        sim.step(steps)
+        n = sim.moments(with_totals=False)[0]
+        sim.close()
+        return n
+
+    target = forward(phi_t, T_t, n0h)
+    loss_of = lambda n: float(((n - target) ** 2).sum())
+    phi = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    Tt = torch.tensor(T, dtype=torch.float64, requires_grad=True)
+    n0 = torch.tensor(n0h, dtype=torch.float64, device="cuda", requires_grad=True)
+    n_end = EVRun.apply(phi, Tt, n0, p, steps)
+    loss = ((n_end - torch.from_numpy(target).cuda()) ** 2).sum()
+    loss.backward()
+    h = 1e-6
+    checks = [("phi_a", (loss_of(forward(1 + h, T, n0h)) - loss_of(forward(1 - h, T, n0h))) / (2 * h),
+               float(phi.grad)),
+              ("T", (loss_of(forward(1.0, T + h, n0h)) - loss_of(forward(1.0, T - h, n0h))) / (2 * h),
+               float(Tt.grad))]
+    g = n0.grad.cpu().numpy()
+    for j in range(4):
+        d = np.random.default_rng(100 + j).uniform(-1, 1, nz)
+        fd = (loss_of(forward(1.0, T, n0h + h * d)) - loss_of(forward(1.0, T, n0h - h * d))) / (2 * h)
+        checks.append((f"n0 direction {j}", fd, float((g * d).sum())))
+    for name, fd, got in checks:
+        print(f"calibration {name}: central difference {fd:.9e} adjoint {got:.9e} rel {abs(got - fd) / abs(fd):.2e}")
+        assert abs(got - fd) < 1e-6 * abs(fd), name
