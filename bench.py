@@ -218,7 +218,8 @@ def run_ours(args, rank, world):
     n64 = sim.moments(with_totals=False)[0]
     sim.close()
     line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
-                        "adjoint": adjoint_leg(ev, W, stream)}
+                        "adjoint": adjoint_leg(ev, W, stream),
+                        "batched": batched_leg(ev, W, stream)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
     return line
@@ -284,6 +285,60 @@ def adjoint_leg(ev, W, stream, steps=200):
     fwd, bwd = times[-1]
     return {"workload": f"periodic Nz={nz}, dz={dz}, Q={Q}, {steps} steps, checkpoint every 100", "forward_ms": fwd,
             "backward_ms": bwd, "backward_over_forward": bwd / fwd}
+
+
+def batched_leg(ev, W, stream, steps=4):
+    """Batched against per-instance launches on the phase-separation batch:
+    256 independent periodic slabs, Nz log-uniform in [128, 8192],
+    Q in {16, 24, 32}, T/T_c in [0.6, 0.95], mean n in [0.15, 0.35], +-1%
+    noise, dz = 0.25, FP64.  Batched: one context, one launch per RK stage for
+    all slabs, node tile from the autotuner.  Per-instance: one context per
+    slab, each with its own (one-wave) tile, launched back to back on the
+    same stream.  Both are timed over `steps` steps from the same state."""
+    import numpy as np
+    import torch
+    from paper_2503_15187_gb300 import autotune as AT
+    slabs = W.batch_slabs(nslab=256)
+    DZb = 0.25
+    params = [ev.Params(nx=s["nz"], dx=DZb, Q=s["Q"]) for s in slabs]
+    n0 = np.concatenate([s["n0"] for s in slabs])
+    T0 = np.concatenate([np.full(s["nz"], s["T_ratio"] * ev.critical_T(p)) for s, p in zip(slabs, params)])
+    u0 = np.zeros_like(n0)
+    nvu = sum(p.nx * p.Q for p in params) * steps
+    best, tune_ms = AT.autotune(params, n0, u0, T0, stream=stream)
+    sim = ev.Sim(params, stream=stream)
+    sim.tune(best)
+    sim.init(n0, u0, T0)
+    sim.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step_async(steps)
+    e1.record(stream)
+    sim.step(0)
+    ms_b = e0.elapsed_time(e1)
+    sim.close()
+    sims, off = [], 0
+    for p, s in zip(params, slabs):
+        one = ev.Sim(p, stream=stream)
+        one.init(s["n0"], np.zeros(p.nx), T0[off:off + p.nx])
+        off += p.nx
+        one.step(2)
+        sims.append(one)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for one in sims:
+        one.step_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    for one in sims:
+        one.step(0)
+        one.close()
+    vb, vp = nvu / (ms_b * 1e-3) / 1e9, nvu / (ms_p * 1e-3) / 1e9
+    return {"workload": "256 periodic slabs, Nz log-uniform [128, 8192], Q in {16,24,32}, dz 0.25, FP64",
+            "nvu_per_step": nvu // steps, "steps": steps, "batched_GNVUPS": vb, "per_instance_GNVUPS": vp,
+            "batched_over_per_instance": vb / vp, "tile_nodes": best,
+            "autotune_ms_per_step": {str(k): round(v, 3) for k, v in tune_ms.items()}}
 
 
 def cpu_baseline(budget_s, T, n0, max_steps=10**9):
