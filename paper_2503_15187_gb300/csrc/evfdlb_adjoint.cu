@@ -146,228 +146,239 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         s.V[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloV + c, nx, bc)];
     }
     __syncthreads();
-    node_fields<double>(sd, it, s.f, Z, taps, taps, mom, NN, err, nullptr);
-    // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
-    // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term
-    for (int e = threadIdx.x; e < Q * Q; e += blockDim.x) {
-        int l = e / Q, j = e % Q;
-        s.f.P[e] = (l == 0) ? 0.0 : r1[l] * tab[L.P + (l - 1) * Q + j];
+    // Warp 0 recomputes the node fields while warps 1-7 run phases 1 and 1b,
+    // which need only v and the tables (named barrier 1 joins warps 1-7).
+    const bool node_warp = threadIdx.x < 32;
+    const int tid7 = threadIdx.x - 32, nth7 = blockDim.x - 32;
+    if (node_warp) {
+        node_fields_pass1<double>(sd, it, s.f, taps, NN, nullptr, threadIdx.x, 32);
+        __syncwarp();
+        node_fields_pass2<double>(sd, it, s.f, Z, taps, mom, NN, err, nullptr, threadIdx.x, 32);
+    } else {
+        // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
+        // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term
+        for (int e = tid7; e < Q * Q; e += nth7) {
+            int l = e / Q, j = e % Q;
+            s.f.P[e] = (l == 0) ? 0.0 : r1[l] * tab[L.P + (l - 1) * Q + j];
+        }
+
+        // phase 1: transposed synthesis cbar_l = sum_k S_kl v_k
+        for (int e = tid7; e < 2 * Q * nz; e += nth7) {
+            int t = e % nz, r = e / nz;
+            int l = r % Q, d = r / Q;
+            const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
+            double acc = 0.0;
+            for (int k = 0; k < Q; ++k) acc = fma(s.f.S[k * Q + l], v[k * WV], acc);
+            s.Cb[((size_t)d * Q + l) * Z + t] = acc;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nth7) : "memory");
+        // phase 1b: Ha_j = sum_l sqrt(l) psi_{l-1}(xi_j) cbar_l, the transposed analysis
+        // of the force term c_l += F1 sqrt(l) a_{l-1} (times F1 in phase 4); with
+        // a_{l-1} = sum_j psi_{l-1}(xi_j) h_j it also gives F1b = sum_j h_j Ha_j.
+        for (int e = tid7; e < 2 * Q * nz; e += nth7) {
+            int t = e % nz, r = e / nz;
+            int j = r % Q, d = r / Q;
+            const double* cbar = s.Cb + (size_t)d * Q * Z + t;
+            double acc = 0.0;
+            for (int l = 1; l < Q; ++l) acc = fma(s.f.P[l * Q + j], cbar[l * Z], acc);
+            s.Ha[(size_t)r * Z + t] = acc;
+        }
     }
     __syncthreads();
 
-    // phase 1: transposed synthesis cbar_l = sum_k S_kl v_k
-    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int l = r % Q, d = r / Q;
-        const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
-        double acc = 0.0;
-        for (int k = 0; k < Q; ++k) acc = fma(s.f.S[k * Q + l], v[k * WV], acc);
-        s.Cb[((size_t)d * Q + l) * Z + t] = acc;
-    }
-    __syncthreads();
-    // phase 1b: Ha_j = sum_l sqrt(l) psi_{l-1}(xi_j) cbar_l, the transposed analysis
-    // of the force term c_l += F1 sqrt(l) a_{l-1} (times F1 in phase 4); with
-    // a_{l-1} = sum_j psi_{l-1}(xi_j) h_j it also gives F1b = sum_j h_j Ha_j.
-    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int j = r % Q, d = r / Q;
-        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-        double acc = 0.0;
-        for (int l = 1; l < Q; ++l) acc = fma(s.f.P[l * Q + j], cbar[l * Z], acc);
-        s.Ha[(size_t)r * Z + t] = acc;
-    }
-    __syncthreads();
+    // Warp 0 runs phases 2 and 3a (per node) while warps 1-7 run phase 3b.
+    if (node_warp) {
 
-    // phase 2: per (distribution, node): adjoints of the coefficient
-    // constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!) m_{l-r}), of u and T
-    // through m_l (dm_l/du = sqrt(l) m_{l-1}, dm_l/dT = sqrt(l(l-1)) m_{l-2}/2,
-    // so dc_l/du = sqrt(l) c_{l-1}, dc_l/dT = sqrt(l(l-1)) c_{l-2}/2), of F1
-    // (c_l += F1 sqrt(l) a_{l-1}) and of nu (the -nu h term).
-    for (int e = threadIdx.x; e < 2 * nz; e += blockDim.x) {
-        int t = e % nz, d = e / nz;
-        const double* sc = s.f.Sc;
-        double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
-        double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
-        double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-        double c0, c1, c2, c3;
-        if (d == 0) {
-            c0 = nu * n;
-            c1 = K * A * T;
-            c2 = 0.6 * K * D * T;
-            c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
-        } else {
-            c0 = nu * n * T + 0.4 * K * T * D;
-            c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
-            c2 = 0.6 * K * T * T * D;
-            c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
+        // phase 2: per (distribution, node): adjoints of the coefficient
+        // constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!) m_{l-r}), of u and T
+        // through m_l (dm_l/du = sqrt(l) m_{l-1}, dm_l/dT = sqrt(l(l-1)) m_{l-2}/2,
+        // so dc_l/du = sqrt(l) c_{l-1}, dc_l/dT = sqrt(l(l-1)) c_{l-2}/2), of F1
+        // (c_l += F1 sqrt(l) a_{l-1}) and of nu (the -nu h term).
+        for (int e = threadIdx.x; e < 2 * nz; e += 32) {
+            int t = e % nz, d = e / nz;
+            const double* sc = s.f.Sc;
+            double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
+            double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
+            double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
+            double c0, c1, c2, c3;
+            if (d == 0) {
+                c0 = nu * n;
+                c1 = K * A * T;
+                c2 = 0.6 * K * D * T;
+                c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
+            } else {
+                c0 = nu * n * T + 0.4 * K * T * D;
+                c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
+                c2 = 0.6 * K * T * T * D;
+                c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
+            }
+            const double* cbar = s.Cb + (size_t)d * Q * Z + t;
+            double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
+            double cm1 = 0.0, cm2 = 0.0;      // c_{l-1}, c_{l-2}
+            double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, fb = 0;
+            for (int l = 0; l < Q; ++l) {
+                double cl = cbar[l * Z];
+                double w1 = r1[l] * m1, w2 = r2[l] * m2, w3 = r3[l] * m3;
+                b0 = fma(cl, m0, b0);
+                b1 = fma(cl, w1, b1);
+                b2 = fma(cl, w2, b2);
+                b3 = fma(cl, w3, b3);
+                ub = fma(cl * r1[l], cm1, ub);
+                Tb = fma(cl * 0.5 * r2[l], cm2, Tb);
+                double c = c0 * m0 + c1 * w1 + c2 * w2 + c3 * w3;
+                cm2 = cm1;
+                cm1 = c;
+                double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
+                m3 = m2;
+                m2 = m1;
+                m1 = m0;
+                m0 = mn;
+            }
+            double nb = 0.0;
+            const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
+            const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
+            const double* ha = s.Ha + (size_t)d * Q * Z + t;
+            for (int k = 0; k < Q; ++k) {
+                nb = fma(-h[k * WH], v[k * WV], nb);
+                fb = fma(h[k * WH], ha[k * Z], fb);
+            }
+            double* red = s.Red + (size_t)d * 8 * Z + t;
+            red[0] = b0;
+            red[Z] = b1;
+            red[2 * Z] = b2;
+            red[3 * Z] = b3;
+            red[4 * Z] = ub;
+            red[5 * Z] = Tb;
+            red[6 * Z] = fb;
+            red[7 * Z] = nb;
         }
-        const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-        double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
-        double cm1 = 0.0, cm2 = 0.0;      // c_{l-1}, c_{l-2}
-        double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, fb = 0;
-        for (int l = 0; l < Q; ++l) {
-            double cl = cbar[l * Z];
-            double w1 = r1[l] * m1, w2 = r2[l] * m2, w3 = r3[l] * m3;
-            b0 = fma(cl, m0, b0);
-            b1 = fma(cl, w1, b1);
-            b2 = fma(cl, w2, b2);
-            b3 = fma(cl, w3, b3);
-            ub = fma(cl * r1[l], cm1, ub);
-            Tb = fma(cl * 0.5 * r2[l], cm2, Tb);
-            double c = c0 * m0 + c1 * w1 + c2 * w2 + c3 * w3;
-            cm2 = cm1;
-            cm1 = c;
-            double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
-            m3 = m2;
-            m2 = m1;
-            m1 = m0;
-            m0 = mn;
-        }
-        double nb = 0.0;
-        const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
-        const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
-        const double* ha = s.Ha + (size_t)d * Q * Z + t;
-        for (int k = 0; k < Q; ++k) {
-            nb = fma(-h[k * WH], v[k * WV], nb);
-            fb = fma(h[k * WH], ha[k * Z], fb);
-        }
-        double* red = s.Red + (size_t)d * 8 * Z + t;
-        red[0] = b0;
-        red[Z] = b1;
-        red[2 * Z] = b2;
-        red[3 * Z] = b3;
-        red[4 * Z] = ub;
-        red[5 * Z] = Tb;
-        red[6 * Z] = fb;
-        red[7 * Z] = nb;
-    }
-    __syncthreads();
+        __syncwarp();
 
-    // phase 3a: per node, the chain through the coefficient constants, the
-    // transport coefficients of Eqs. (viscosity), (tau), (prandtl), and the
-    // gradients A = dX/X, B = dT/T, D = du.
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) {
-        const double* sc = s.f.Sc;
-        double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
-        double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
-        double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-        double F1 = sc[SC_FORCE * Z + t];
-        const double* rF = s.Red + t;
-        const double* rG = s.Red + 8 * Z + t;
-        double cF0 = rF[0], cF1 = rF[Z], cF2 = rF[2 * Z], cF3 = rF[3 * Z];
-        double cG0 = rG[0], cG1 = rG[Z], cG2 = rG[2 * Z], cG3 = rG[3 * Z];
-        double ub = rF[4 * Z] + rG[4 * Z];
-        double Tb = rF[5 * Z] + rG[5 * Z];
-        double F1b = rF[6 * Z] + rG[6 * Z];
-        double nub = rF[7 * Z] + rG[7 * Z];
-        double nb = 0, Kb = 0, kqb = 0, Ab = 0, Bb = 0, Db = 0, chib = 0, xb = 0, qb = 0;
-        // F: c0 = nu n, c1 = K A T, c2 = 3/5 K D T, c3 = nu kq/5 + 3/10 K B T^2
-        nub += cF0 * n;
-        nb += cF0 * nu;
-        Kb += cF1 * A * T;
-        Ab += cF1 * K * T;
-        Tb += cF1 * K * A;
-        Kb += 0.6 * cF2 * D * T;
-        Db += 0.6 * cF2 * K * T;
-        Tb += 0.6 * cF2 * K * D;
-        nub += 0.2 * cF3 * kq;
-        kqb += 0.2 * cF3 * nu;
-        Kb += 0.3 * cF3 * B * T * T;
-        Bb += 0.3 * cF3 * K * T * T;
-        Tb += 0.6 * cF3 * K * B * T;
-        // G: c0 = nu n T + 2/5 K T D, c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
-        //    c2 = 3/5 K T^2 D, c3 = nu kq T/5 + 3/10 K T^3 B
-        nub += cG0 * n * T;
-        nb += cG0 * nu * T;
-        Tb += cG0 * (nu * n + 0.4 * K * D);
-        Kb += 0.4 * cG0 * T * D;
-        Db += 0.4 * cG0 * K * T;
-        nub += 0.4 * cG1 * kq;
-        kqb += 0.4 * cG1 * nu;
-        Kb += cG1 * T * T * (A + 0.6 * B);
-        Tb += 2.0 * cG1 * K * T * (A + 0.6 * B);
-        Ab += cG1 * K * T * T;
-        Bb += 0.6 * cG1 * K * T * T;
-        Kb += 0.6 * cG2 * T * T * D;
-        Tb += 1.2 * cG2 * K * T * D;
-        Db += 0.6 * cG2 * K * T * T;
-        nub += 0.2 * cG3 * kq * T;
-        kqb += 0.2 * cG3 * nu * T;
-        Tb += cG3 * (0.2 * nu * kq + 0.9 * K * T * T * B);
-        Kb += 0.3 * cG3 * T * T * T * B;
-        Bb += 0.3 * cG3 * K * T * T * T;
-        // transport (recomputed as in node_fields)
-        double chi = s.f.Chi[t + 2], X = s.f.X[t + 2];
-        double bn = sd.b * n, x = bn * chi;
-        const double k1 = (4.0 / 25.0) * (1.0 + 12.0 / M_PI), k2 = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI));
-        double sqT = sqrt(T);
-        double gmu = 1.0 / chi + 0.8 * bn + k1 * bn * bn * chi;
-        double mu = sd.mu0_coef * sqT * gmu;
-        double den = 1.0 + 0.4 * x;
-        double tau = mu / (n * T * den);
-        double N1 = 1.0 + 0.6 * x, N2 = 1.0 + 0.8 * x + k1 * x * x, D1 = den, D2 = 1.0 + 1.2 * x + k2 * x * x;
-        double Pr = (2.0 / 3.0) * N1 * N2 / (D1 * D2);
-        // q from the raw sums (as node_fields forms it)
-        long long o = sd.node_off + it.i0 + t;
-        double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
-        double S3 = mom[MOM_S3 * NN + o], G0 = mom[MOM_G0 * NN + o], G1 = mom[MOM_G1 * NN + o];
-        double q = 0.5 * (S3 - 3.0 * u * S2 + 3.0 * u * u * S1 - u * u * u * S0) + G1 - u * G0;
-        // K = -b n^2 chi
-        nb += -2.0 * x * Kb;
-        chib += -bn * n * Kb;
-        // kq = (1 - Pr) q
-        qb += kqb * (1.0 - Pr);
-        double Prb = -kqb * q;
-        // nu = 1/tau or chi/tau
-        double taub;
-        if (sd.relax == EVFDLB_RELAX_INV_TAU) {
-            taub = -nub / (tau * tau);
-        } else {
-            chib += nub / tau;
-            taub = -nub * chi / (tau * tau);
+        // phase 3a: per node, the chain through the coefficient constants, the
+        // transport coefficients of Eqs. (viscosity), (tau), (prandtl), and the
+        // gradients A = dX/X, B = dT/T, D = du.
+        for (int t = threadIdx.x; t < nz; t += 32) {
+            const double* sc = s.f.Sc;
+            double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
+            double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
+            double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
+            double F1 = sc[SC_FORCE * Z + t];
+            const double* rF = s.Red + t;
+            const double* rG = s.Red + 8 * Z + t;
+            double cF0 = rF[0], cF1 = rF[Z], cF2 = rF[2 * Z], cF3 = rF[3 * Z];
+            double cG0 = rG[0], cG1 = rG[Z], cG2 = rG[2 * Z], cG3 = rG[3 * Z];
+            double ub = rF[4 * Z] + rG[4 * Z];
+            double Tb = rF[5 * Z] + rG[5 * Z];
+            double F1b = rF[6 * Z] + rG[6 * Z];
+            double nub = rF[7 * Z] + rG[7 * Z];
+            double nb = 0, Kb = 0, kqb = 0, Ab = 0, Bb = 0, Db = 0, chib = 0, xb = 0, qb = 0;
+            // F: c0 = nu n, c1 = K A T, c2 = 3/5 K D T, c3 = nu kq/5 + 3/10 K B T^2
+            nub += cF0 * n;
+            nb += cF0 * nu;
+            Kb += cF1 * A * T;
+            Ab += cF1 * K * T;
+            Tb += cF1 * K * A;
+            Kb += 0.6 * cF2 * D * T;
+            Db += 0.6 * cF2 * K * T;
+            Tb += 0.6 * cF2 * K * D;
+            nub += 0.2 * cF3 * kq;
+            kqb += 0.2 * cF3 * nu;
+            Kb += 0.3 * cF3 * B * T * T;
+            Bb += 0.3 * cF3 * K * T * T;
+            Tb += 0.6 * cF3 * K * B * T;
+            // G: c0 = nu n T + 2/5 K T D, c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
+            //    c2 = 3/5 K T^2 D, c3 = nu kq T/5 + 3/10 K T^3 B
+            nub += cG0 * n * T;
+            nb += cG0 * nu * T;
+            Tb += cG0 * (nu * n + 0.4 * K * D);
+            Kb += 0.4 * cG0 * T * D;
+            Db += 0.4 * cG0 * K * T;
+            nub += 0.4 * cG1 * kq;
+            kqb += 0.4 * cG1 * nu;
+            Kb += cG1 * T * T * (A + 0.6 * B);
+            Tb += 2.0 * cG1 * K * T * (A + 0.6 * B);
+            Ab += cG1 * K * T * T;
+            Bb += 0.6 * cG1 * K * T * T;
+            Kb += 0.6 * cG2 * T * T * D;
+            Tb += 1.2 * cG2 * K * T * D;
+            Db += 0.6 * cG2 * K * T * T;
+            nub += 0.2 * cG3 * kq * T;
+            kqb += 0.2 * cG3 * nu * T;
+            Tb += cG3 * (0.2 * nu * kq + 0.9 * K * T * T * B);
+            Kb += 0.3 * cG3 * T * T * T * B;
+            Bb += 0.3 * cG3 * K * T * T * T;
+            // transport (recomputed as in node_fields)
+            double chi = s.f.Chi[t + 2], X = s.f.X[t + 2];
+            double bn = sd.b * n, x = bn * chi;
+            const double k1 = (4.0 / 25.0) * (1.0 + 12.0 / M_PI), k2 = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI));
+            double sqT = sqrt(T);
+            double gmu = 1.0 / chi + 0.8 * bn + k1 * bn * bn * chi;
+            double mu = sd.mu0_coef * sqT * gmu;
+            double den = 1.0 + 0.4 * x;
+            double tau = mu / (n * T * den);
+            double N1 = 1.0 + 0.6 * x, N2 = 1.0 + 0.8 * x + k1 * x * x, D1 = den, D2 = 1.0 + 1.2 * x + k2 * x * x;
+            double Pr = (2.0 / 3.0) * N1 * N2 / (D1 * D2);
+            // q from the raw sums (as node_fields forms it)
+            long long o = sd.node_off + it.i0 + t;
+            double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
+            double S3 = mom[MOM_S3 * NN + o], G0 = mom[MOM_G0 * NN + o], G1 = mom[MOM_G1 * NN + o];
+            double q = 0.5 * (S3 - 3.0 * u * S2 + 3.0 * u * u * S1 - u * u * u * S0) + G1 - u * G0;
+            // K = -b n^2 chi
+            nb += -2.0 * x * Kb;
+            chib += -bn * n * Kb;
+            // kq = (1 - Pr) q
+            qb += kqb * (1.0 - Pr);
+            double Prb = -kqb * q;
+            // nu = 1/tau or chi/tau
+            double taub;
+            if (sd.relax == EVFDLB_RELAX_INV_TAU) {
+                taub = -nub / (tau * tau);
+            } else {
+                chib += nub / tau;
+                taub = -nub * chi / (tau * tau);
+            }
+            // tau = mu / (n T (1 + 2x/5))
+            double mub = taub / (n * T * den);
+            nb += -taub * tau / n;
+            Tb += -taub * tau / T;
+            xb += -taub * tau * 0.4 / den;
+            // Pr(x)
+            xb += Prb * Pr * (0.6 / N1 + (0.8 + 2.0 * k1 * x) / N2 - 0.4 / D1 - (1.2 + 2.0 * k2 * x) / D2);
+            // mu = mu0 sqrt(T) (1/chi + 4/5 b n + k1 b^2 n^2 chi)
+            Tb += mub * mu / (2.0 * T);
+            nb += mub * sd.mu0_coef * sqT * (0.8 * sd.b + 2.0 * k1 * sd.b * bn * chi);
+            chib += mub * sd.mu0_coef * sqT * (-1.0 / (chi * chi) + k1 * bn * bn);
+            // x = b n chi
+            nb += xb * sd.b * chi;
+            chib += xb * bn;
+            // gradients
+            double dXb = Ab / X;
+            double Xb = -Ab * A / X;
+            double dTb = Bb / T;
+            Tb += -Bb * B / T;
+            double* na = nadj + sd.node_off + it.i0 + t;
+            na[AD_N * NN] = nb;
+            na[AD_U * NN] = ub;
+            na[AD_T * NN] = Tb;
+            na[AD_Q * NN] = qb;
+            na[AD_CHI * NN] = chib;
+            na[AD_X * NN] = Xb;
+            na[AD_DX * NN] = dXb;
+            na[AD_DT * NN] = dTb;
+            na[AD_DU * NN] = Db;
+            na[AD_F1 * NN] = F1b;
+            phis[o] += F1b * F1;
         }
-        // tau = mu / (n T (1 + 2x/5))
-        double mub = taub / (n * T * den);
-        nb += -taub * tau / n;
-        Tb += -taub * tau / T;
-        xb += -taub * tau * 0.4 / den;
-        // Pr(x)
-        xb += Prb * Pr * (0.6 / N1 + (0.8 + 2.0 * k1 * x) / N2 - 0.4 / D1 - (1.2 + 2.0 * k2 * x) / D2);
-        // mu = mu0 sqrt(T) (1/chi + 4/5 b n + k1 b^2 n^2 chi)
-        Tb += mub * mu / (2.0 * T);
-        nb += mub * sd.mu0_coef * sqT * (0.8 * sd.b + 2.0 * k1 * sd.b * bn * chi);
-        chib += mub * sd.mu0_coef * sqT * (-1.0 / (chi * chi) + k1 * bn * bn);
-        // x = b n chi
-        nb += xb * sd.b * chi;
-        chib += xb * bn;
-        // gradients
-        double dXb = Ab / X;
-        double Xb = -Ab * A / X;
-        double dTb = Bb / T;
-        Tb += -Bb * B / T;
-        double* na = nadj + sd.node_off + it.i0 + t;
-        na[AD_N * NN] = nb;
-        na[AD_U * NN] = ub;
-        na[AD_T * NN] = Tb;
-        na[AD_Q * NN] = qb;
-        na[AD_CHI * NN] = chib;
-        na[AD_X * NN] = Xb;
-        na[AD_DX * NN] = dXb;
-        na[AD_DT * NN] = dTb;
-        na[AD_DU * NN] = Db;
-        na[AD_F1 * NN] = F1b;
-        phis[o] += F1b * F1;
-    }
 
-    // phase 3b: transposed WENO-5 faces.  A velocity row is cut into chunks of
-    // up to 28 tile nodes; a chunk's cn + 4 faces occupy a segment of cn + 4
-    // consecutive lanes (one face per lane), and a warp carries as many
-    // segments (rows) as fit in 32 lanes.  Each lane forms the five
-    // derivatives of its face value times the face adjoint, ordered so that
-    // the node at segment lane L' collects g'[s] from segment lane L' + s,
-    // s = 0..4 (the five faces that read it).
-    {
-        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+        // phase 3b: transposed WENO-5 faces.  A velocity row is cut into chunks of
+        // up to 28 tile nodes; a chunk's cn + 4 faces occupy a segment of cn + 4
+        // consecutive lanes (one face per lane), and a warp carries as many
+        // segments (rows) as fit in 32 lanes.  Each lane forms the five
+        // derivatives of its face value times the face adjoint, ordered so that
+        // the node at segment lane L' collects g'[s] from segment lane L' + s,
+        // s = 0..4 (the five faces that read it).
+    } else {
+        const int warp = threadIdx.x / 32 - 1, lane = threadIdx.x % 32, nwarps = blockDim.x / 32 - 1;
         const double rdz = sd.inv_dx, eps = sd.weno_eps;
         const int nchunk = (nz + 27) / 28;
         const int cmax = min(28, nz), seg = cmax + 4;

@@ -42,6 +42,8 @@ struct Smem {
     R *A;               // analysis [2][Q][Z]
     R *F;               // state tile with halo [2][Q][Z+6]
     R *Face;            // WENO face values [2][Q][Z+1]
+    R *Cc;              // per-node coefficient constants c0..c3 [2][4][Z]
+    R *Mm;              // Hermite moments m_l of N(u, T) per node [Q][Z]
 };
 
 // Length of the R copy of the density halo, rounded up to an even count so
@@ -53,7 +55,8 @@ template <typename R>
 __host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
     size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z;
     size_t nr = 2 * (size_t)Q * Q + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
-                4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1);
+                4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z +
+                (size_t)Q * Z;
     return nd * sizeof(double) + nr * sizeof(R);
 }
 
@@ -80,6 +83,8 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     s.A = s.C + 2 * Q * Z;
     s.F = s.A + 2 * Q * Z;
     s.Face = s.F + 2 * Q * (Z + 6);
+    s.Cc = s.Face + 2 * Q * (Z + 1);
+    s.Mm = s.Cc + 8 * Z;
     return s;
 }
 
@@ -133,19 +138,21 @@ __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Sm
 // ---------------------------------------------------------------------------
 // Phases 1-2: node fields of the tile.
 // ---------------------------------------------------------------------------
+// Pass 1 (threads tid, tid + nth, ...): Fischer-Methfessel average, chi and X
+// on nodes i0-2 .. i0+nz+1.  Pass 2 reads the +-2 neighbours of pass 1, so
+// the caller separates the passes with a barrier of the participating threads.
 template <typename R>
-__device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                            const double* __restrict__ taps, const R* __restrict__ rtaps,
-                            const double* __restrict__ mom, long long NN, unsigned* err, double* fields_out) {
+__device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s,
+                                  const double* __restrict__ taps, long long NN, double* fields_out, int tid,
+                                  int nth) {
     const int M = sd.M, m = sd.m;
-    const R* ftap = rtaps + sd.tap_off;                  // force [2M+1]
     const double* mtap = taps + sd.tap_off + 2 * M + 1;  // Fischer-Methfessel [2m+1]
     // Fischer-Methfessel average (Sec. II.A), chi (Eq. (carnstar)) and
     // X = n^2 chi T on nodes i0-2 .. i0+nz+1.  Under the outflow rule a ghost
     // node copies every node field of the nearest interior node, so the
     // average is centred on the clamped node; under the periodic rule the
     // window around the ghost position is the wrapped node's window.
-    for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
+    for (int t = tid; t < it.nz + 4; t += nth) {
         int pos = it.i0 - 2 + t;
         int shift = (sd.bc == EVFDLB_BC_OUTFLOW) ? gidx(pos, sd.nx, sd.bc) - pos : 0;
         const double* nn = s.N + (t - 2 + M + shift);
@@ -161,7 +168,16 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R
             fields_out[4 * NNf + sd.node_off + it.i0 + t - 2] = nb;
         }
     }
-    __syncthreads();
+}
+
+// Pass 2: per tile node, the gradients, the Eq. (F1) force (in R), the heat
+// flux, the transport coefficients and the scalars of Sc and Scr.
+template <typename R>
+__device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                  const R* __restrict__ rtaps, const double* __restrict__ mom, long long NN,
+                                  unsigned* err, double* fields_out, int tid, int nth) {
+    const int M = sd.M;
+    const R* ftap = rtaps + sd.tap_off;                  // force [2M+1]
     const double inv12 = sd.inv_dx / 12.0;
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
@@ -169,7 +185,7 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R
     const double* S3 = mom + MOM_S3 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
     const double* G1 = mom + MOM_G1 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz; t += blockDim.x) {
+    for (int t = tid; t < it.nz; t += nth) {
         const int c = t + 2;                         // index in the +-2 arrays
         const int i = it.i0 + t;
         double n = s.N[t + M], u = s.U[c], T = s.T[c];
@@ -220,8 +236,18 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R
     }
 }
 
+// Both passes with all threads of the CTA.
+template <typename R>
+__device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                            const double* __restrict__ taps, const R* __restrict__ rtaps,
+                            const double* __restrict__ mom, long long NN, unsigned* err, double* fields_out) {
+    node_fields_pass1<R>(sd, it, s, taps, NN, fields_out, threadIdx.x, blockDim.x);
+    __syncthreads();
+    node_fields_pass2<R>(sd, it, s, Z, rtaps, mom, NN, err, fields_out, threadIdx.x, blockDim.x);
+}
+
 // ---------------------------------------------------------------------------
-// Phase 3a: Hermite coefficients of nu F^S + J1_F and nu G^S + J1_G.
+// Hermite coefficients of nu F^S + J1_F and nu G^S + J1_G.
 // With m_l = E[psi_l(u + c)], c ~ N(0, T) (m_0 = 1,
 // m_{l+1} = u m_l / sqrt(l+1) + (T-1) sqrt(l/(l+1)) m_{l-1}) and Stein's
 // identity E[c h(c)] = T E[h'(c)], the projections of the reduced Shakhov
@@ -233,64 +259,85 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R
 //      c2 = 3/5 K D T,        c3 = nu kq/5 + 3/10 K B T^2
 //   G: c0 = nu n T + 2/5 K T D,  c1 = 2/5 nu kq + K T^2 (A + 3/5 B),
 //      c2 = 3/5 K T^2 D,         c3 = nu kq T/5 + 3/10 K T^3 B
-// The four constants are formed in FP64; the recurrence runs in R.
+// node_coefficients forms the constants (FP64, stored in R) and the moments
+// m_l (recurrence in R) per node; coefficients() then forms every c_l in
+// parallel and adds the force term F1 sqrt(l) a_{l-1}
+// (d/dxi [omega psi_{l-1}] = -sqrt(l) omega psi_l).
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ void equilibrium_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                         const R* __restrict__ rtab) {
+__device__ void node_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                  const R* __restrict__ tab, int tid, int nth) {
     const int Q = sd.Q;
     TableLayout L(Q);
-    const R* tab = rtab + sd.tab_off;
-    for (int e = threadIdx.x; e < 2 * it.nz; e += blockDim.x) {
-        int t = e % it.nz, d = e / it.nz;
+    for (int t = tid; t < it.nz; t += nth) {
         const double* sc = s.Sc;
         double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
         double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
         double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-        double c0, c1, c2, c3;
-        if (d == 0) {
-            c0 = nu * n;
-            c1 = K * A * T;
-            c2 = 0.6 * K * D * T;
-            c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
-        } else {
-            c0 = nu * n * T + 0.4 * K * T * D;
-            c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
-            c2 = 0.6 * K * T * T * D;
-            c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
-        }
-        const R rc0 = (R)c0, rc1 = (R)c1, rc2 = (R)c2, rc3 = (R)c3, ru = (R)u, Tm1 = (R)(T - 1.0);
-        R m0 = 1, m1 = 0, m2 = 0, m3 = 0;
-        R* out = s.C + (size_t)d * Q * Z + t;
+        R* cF = s.Cc + t;
+        R* cG = s.Cc + 4 * Z + t;
+        cF[0] = (R)(nu * n);
+        cF[Z] = (R)(K * A * T);
+        cF[2 * Z] = (R)(0.6 * K * D * T);
+        cF[3 * Z] = (R)(0.2 * nu * kq + 0.3 * K * B * T * T);
+        cG[0] = (R)(nu * n * T + 0.4 * K * T * D);
+        cG[Z] = (R)(0.4 * nu * kq + K * T * T * (A + 0.6 * B));
+        cG[2 * Z] = (R)(0.6 * K * T * T * D);
+        cG[3 * Z] = (R)(0.2 * nu * kq * T + 0.3 * K * T * T * T * B);
+        const R ru = (R)u, Tm1 = (R)(T - 1.0);
+        R m0 = 1, m1 = 0;
         for (int l = 0; l < Q; ++l) {
-            R c = rc0 * m0;
-            c = fma(rc1 * tab[L.r1 + l], m1, c);
-            c = fma(rc2 * tab[L.r2 + l], m2, c);
-            c = fma(rc3 * tab[L.r3 + l], m3, c);
-            out[l * Z] = c;
+            s.Mm[l * Z + t] = m0;
             R mn = fma(ru * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
-            m3 = m2;
-            m2 = m1;
             m1 = m0;
             m0 = mn;
         }
     }
 }
 
-// Phase 3b: analysis a_l = sum_j psi_l(xi_j) h_j, l <= Q-2 (the force needs
-// a_0 .. a_{Q-2}; the l = Q-1 term meets psi_Q(xi_k) = 0).
 template <typename R>
-__device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z) {
+__device__ void coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                             const R* __restrict__ tab, int tid, int nth) {
+    const int Q = sd.Q, nz = it.nz;
+    TableLayout L(Q);
+    for (int e = tid; e < 2 * Q * nz; e += nth) {
+        int t = e % nz, r = e / nz;
+        int l = r % Q, d = r / Q;
+        const R* cc = s.Cc + d * 4 * Z + t;
+        const R* mm = s.Mm + t;
+        // the sqrt factors vanish where the moment index would be negative
+        R c = cc[0] * mm[l * Z];
+        c = fma(cc[Z] * tab[L.r1 + l], mm[max(l - 1, 0) * Z], c);
+        c = fma(cc[2 * Z] * tab[L.r2 + l], mm[max(l - 2, 0) * Z], c);
+        c = fma(cc[3 * Z] * tab[L.r3 + l], mm[max(l - 3, 0) * Z], c);
+        if (l >= 1) c = fma(s.Scr[Z + t] * tab[L.r1 + l], s.A[((size_t)d * Q + l - 1) * Z + t], c);
+        s.C[((size_t)d * Q + l) * Z + t] = c;
+    }
+}
+
+// Analysis a_l = sum_j psi_l(xi_j) h_j, l <= Q-2 (the force needs
+// a_0 .. a_{Q-2}; the l = Q-1 term meets psi_Q(xi_k) = 0), two orders per
+// thread so that each state value loaded feeds two FMAs.
+template <typename R>
+__device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z, int tid, int nth) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    const int per_d = (Q - 1) * nz;
-    for (int e = threadIdx.x; e < 2 * per_d; e += blockDim.x) {
+    const int np = Q / 2;                          // pairs (l, l+1) covering l <= Q-2
+    const int per_d = np * nz;
+    for (int e = tid; e < 2 * per_d; e += nth) {
         int d = e / per_d, r = e % per_d;
-        int l = r / nz, t = r % nz;
-        const R* Pl = s.P + l * Q;
+        int l0 = 2 * (r / nz), t = r % nz;
+        const bool two = (l0 + 1 <= Q - 2);
+        const R* P0 = s.P + l0 * Q;
+        const R* P1 = s.P + (two ? l0 + 1 : l0) * Q;
         const R* h = s.F + (size_t)d * Q * W + (t + 3);
-        R acc = 0;
-        for (int j = 0; j < Q; ++j) acc = fma(Pl[j], h[j * W], acc);
-        s.A[((size_t)d * Q + l) * Z + t] = acc;
+        R a0 = 0, a1 = 0;
+        for (int j = 0; j < Q; ++j) {
+            R hv = h[j * W];
+            a0 = fma(P0[j], hv, a0);
+            a1 = fma(P1[j], hv, a1);
+        }
+        s.A[((size_t)d * Q + l0) * Z + t] = a0;
+        if (two) s.A[((size_t)d * Q + l0 + 1) * Z + t] = a1;
     }
 }
 
@@ -320,12 +367,12 @@ __device__ __forceinline__ R weno5(R v0, R v1, R v2, R v3, R v4, R eps) {
 // tile nodes f-1 and f), upwind by the sign of xi_k.
 template <typename R>
 __device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                      const R* __restrict__ rtab) {
+                      const R* __restrict__ rtab, int tid, int nth) {
     const int Q = sd.Q, W = Z + 6, nf = it.nz + 1;
     TableLayout L(Q);
     const R* xi = rtab + sd.tab_off + L.xi;
     const R eps = (R)sd.weno_eps;
-    for (int e = threadIdx.x; e < 2 * Q * nf; e += blockDim.x) {
+    for (int e = tid; e < 2 * Q * nf; e += nth) {
         int f = e % nf, r = e / nf;
         int k = r % Q, d = r / Q;
         const R* h = s.F + (size_t)(d * Q + k) * W;
@@ -334,23 +381,6 @@ __device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, 
         else if (x < R(0)) v = weno5<R>(h[f + 5], h[f + 4], h[f + 3], h[f + 2], h[f + 1], eps);
         else v = 0;
         s.Face[(size_t)(d * Q + k) * (Z + 1) + f] = v;
-    }
-}
-
-// Phase 4: add the force term F1 sqrt(l) a_{l-1} to the coefficients
-// (d/dxi [omega psi_{l-1}] = -sqrt(l) omega psi_l).
-template <typename R>
-__device__ void add_force(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                          const R* __restrict__ rtab) {
-    const int Q = sd.Q, nz = it.nz;
-    TableLayout L(Q);
-    const R* r1 = rtab + sd.tab_off + L.r1;
-    for (int e = threadIdx.x; e < 2 * (Q - 1) * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int l = 1 + r % (Q - 1), d = r / (Q - 1);
-        R f1 = s.Scr[Z + t];
-        s.C[((size_t)d * Q + l) * Z + t] =
-            fma(f1 * r1[l], s.A[((size_t)d * Q + l - 1) * Z + t], s.C[((size_t)d * Q + l) * Z + t]);
     }
 }
 

@@ -66,38 +66,60 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     load_node_inputs<R>(sd, it, s, Z, rtab, mom_in, NN);
     load_state_tile<R>(sd, it, s, Z, src, NF);
     __syncthreads();
-    node_fields<R>(sd, it, s, Z, taps, rtaps, mom_in, NN, err, nullptr);
+    // Warp 0 forms the node-level quantities of the tile (node fields,
+    // coefficient constants, Hermite moments of the local Gaussian) while the
+    // other warps do the velocity-space work that needs only the state tile
+    // (Hermite analysis, WENO-5 faces), so the serial node work overlaps it.
+    const R* rt = rtab + sd.tab_off;
+    if (threadIdx.x < 32) {
+        node_fields_pass1<R>(sd, it, s, taps, NN, nullptr, threadIdx.x, 32);
+        __syncwarp();
+        node_fields_pass2<R>(sd, it, s, Z, rtaps, mom_in, NN, err, nullptr, threadIdx.x, 32);
+        __syncwarp();
+        node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32);
+    } else {
+        analysis<R>(sd, it, s, Z, threadIdx.x - 32, blockDim.x - 32);
+        faces<R>(sd, it, s, Z, rtab, threadIdx.x - 32, blockDim.x - 32);
+    }
     __syncthreads();
-    equilibrium_coefficients<R>(sd, it, s, Z, rtab);
-    analysis<R>(sd, it, s, Z);
-    faces<R>(sd, it, s, Z, rtab);
-    __syncthreads();
-    add_force<R>(sd, it, s, Z, rtab);
+    coefficients<R>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
     __syncthreads();
 
-    // Phase 5: synthesis, advection, relaxation and the RK stage.
+    // Phase 5: synthesis, advection, relaxation and the RK stage; two
+    // velocities per thread share every coefficient loaded.
     TableLayout L(Q);
     const R* xi = rtab + sd.tab_off + L.xi;
     const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
-    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+    const int nkp = (Q + 1) / 2;
+    for (int e = threadIdx.x; e < 2 * nkp * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
-        int k = r % Q, d = r / Q;
-        const R* Sk = s.S + k * Q;
+        int k0 = 2 * (r % nkp), d = r / nkp;
+        const int nk = (k0 + 1 < Q) ? 2 : 1;
+        const R* S0 = s.S + k0 * Q;
+        const R* S1 = s.S + (k0 + nk - 1) * Q;
         const R* c = s.C + (size_t)d * Q * Z + t;
-        R syn = 0;
-        for (int l = 0; l < Q; ++l) syn = fma(Sk[l], c[l * Z], syn);
-        const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
-        R h = s.F[(size_t)(d * Q + k) * W + t + 3];
-        R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
-        long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
-        if (mode == 1) {
-            rhs_out[g] = (double)Rv;
-            continue;
+        R syn0 = 0, syn1 = 0;
+        for (int l = 0; l < Q; ++l) {
+            R cl = c[l * Z];
+            syn0 = fma(S0[l], cl, syn0);
+            syn1 = fma(S1[l], cl, syn1);
         }
-        R o = rbeta * fma(dt, Rv, h);
-        if (alpha != 0.0) o = fma(ralpha, base[g], o);
-        out[g] = o;
-        s.F[(size_t)(d * Q + k) * W + t + 3] = o;
+        for (int q = 0; q < nk; ++q) {
+            const int k = k0 + q;
+            const R syn = q ? syn1 : syn0;
+            const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
+            R h = s.F[(size_t)(d * Q + k) * W + t + 3];
+            R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
+            long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
+            if (mode == 1) {
+                rhs_out[g] = (double)Rv;
+                continue;
+            }
+            R o = rbeta * fma(dt, Rv, h);
+            if (alpha != 0.0) o = fma(ralpha, base[g], o);
+            out[g] = o;
+            s.F[(size_t)(d * Q + k) * W + t + 3] = o;
+        }
     }
     if (mode == 1) return;
     __syncthreads();
