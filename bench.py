@@ -217,9 +217,10 @@ def run_ours(args, rank, world):
     }
     n64 = sim.moments(with_totals=False)[0]
     sim.close()
-    line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
-                        "adjoint": adjoint_leg(ev, W, stream),
-                        "batched": batched_leg(ev, W, stream)}
+    if not args.no_variants:
+        line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
+                            "adjoint": adjoint_leg(ev, W, stream),
+                            "batched": batched_leg(ev, W, stream)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
     return line
@@ -397,6 +398,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="report the headline FP64 leg only (no FP32 / adjoint / batched legs), e.g. for ncu")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
