@@ -220,7 +220,7 @@ def run_ours(args, rank, world):
     if not args.no_variants:
         line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
                             "adjoint": adjoint_leg(ev, W, stream),
-                            "batched": batched_leg(ev, W, stream)}
+                            "batched": batched_leg(ev, W, stream, rank, world, maxred)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
     return line
@@ -288,24 +288,31 @@ def adjoint_leg(ev, W, stream, steps=200):
             "backward_ms": bwd, "backward_over_forward": bwd / fwd}
 
 
-def batched_leg(ev, W, stream, steps=4):
+def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=4):
     """Batched against per-instance launches on the phase-separation batch:
     256 independent periodic slabs, Nz log-uniform in [128, 8192],
     Q in {16, 24, 32}, T/T_c in [0.6, 0.95], mean n in [0.15, 0.35], +-1%
     noise, dz = 0.25, FP64.  Batched: one context, one launch per RK stage for
     all slabs, node tile from the autotuner.  Per-instance: one context per
     slab, each with its own (one-wave) tile, launched back to back on the
-    same stream.  Both are timed over `steps` steps from the same state."""
+    same stream.  Both are timed over `steps` steps from the same state.
+    Under N ranks each rank advances its longest-processing-time share of the
+    slabs (no exchange while stepping; weak in slab count), the rates are
+    whole-job (all slabs / slowest rank), and the per-slab masses are gathered
+    at the end."""
     import numpy as np
     import torch
     from paper_2503_15187_gb300 import autotune as AT
-    slabs = W.batch_slabs(nslab=256)
+    from paper_2503_15187_gb300 import shard
+    all_slabs = W.batch_slabs(nslab=256)
+    mine = shard.my_share(all_slabs, rank, world) if world > 1 else list(range(len(all_slabs)))
+    slabs = [all_slabs[i] for i in mine]
     DZb = 0.25
     params = [ev.Params(nx=s["nz"], dx=DZb, Q=s["Q"]) for s in slabs]
     n0 = np.concatenate([s["n0"] for s in slabs])
     T0 = np.concatenate([np.full(s["nz"], s["T_ratio"] * ev.critical_T(p)) for s, p in zip(slabs, params)])
     u0 = np.zeros_like(n0)
-    nvu = sum(p.nx * p.Q for p in params) * steps
+    nvu = sum(s["nz"] * s["Q"] for s in all_slabs) * steps
     best, tune_ms = AT.autotune(params, n0, u0, T0, stream=stream)
     sim = ev.Sim(params, stream=stream)
     sim.tune(best)
@@ -316,8 +323,12 @@ def batched_leg(ev, W, stream, steps=4):
     sim.step_async(steps)
     e1.record(stream)
     sim.step(0)
-    ms_b = e0.elapsed_time(e1)
+    ms_b = maxred(e0.elapsed_time(e1))
+    mass = sim.moments()[4][:, 0]
     sim.close()
+    if world > 1:
+        masses = shard.gather_by_slab({i: float(m) for i, m in zip(mine, mass)}, len(all_slabs))
+        assert len(masses) == len(all_slabs)
     sims, off = [], 0
     for p, s in zip(params, slabs):
         one = ev.Sim(p, stream=stream)
@@ -331,12 +342,13 @@ def batched_leg(ev, W, stream, steps=4):
         one.step_async(steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1)
+    ms_p = maxred(e0.elapsed_time(e1))
     for one in sims:
         one.step(0)
         one.close()
     vb, vp = nvu / (ms_b * 1e-3) / 1e9, nvu / (ms_p * 1e-3) / 1e9
     return {"workload": "256 periodic slabs, Nz log-uniform [128, 8192], Q in {16,24,32}, dz 0.25, FP64",
+            "sharding": f"LPT over {world} rank(s), {len(mine)} slabs on rank {rank}",
             "nvu_per_step": nvu // steps, "steps": steps, "batched_GNVUPS": vb, "per_instance_GNVUPS": vp,
             "batched_over_per_instance": vb / vp, "tile_nodes": best,
             "autotune_ms_per_step": {str(k): round(v, 3) for k, v in tune_ms.items()}}
