@@ -39,6 +39,7 @@ from numpy.polynomial.hermite_e import hermegauss
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "evfdlb_oracle.c")
 _SRC_CS = os.path.join(_HERE, "evfdlb_oracle_cs.c")
+_SRC_2D = os.path.join(_HERE, "evfdlb_oracle2d.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 NFIELDS = 16
@@ -52,11 +53,11 @@ def build(force: bool = False) -> str:
     """Compile the C oracle into oracle/_build/liborc.so (gcc, -O2, IEEE FP):
     the FP64 routines and their complex-step twins from the same source."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CS))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_CS, _SRC_2D))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_CS, "-lm"])
+                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_CS, _SRC_2D, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -95,6 +96,18 @@ def _load():
         _lib.orc_cs_equilibrium.argtypes = [P, vp, vp, vp, vp, vp]
         _lib.orc_cs_rhs.argtypes = [P, vp, vp, vp, vp, vp]
         _lib.orc_cs_step.argtypes = [P, vp, vp, i]
+        P2 = ctypes.POINTER(_Params2)
+        _lib.orc2_force_kernel.argtypes = [P2, d, d, vp]
+        _lib.orc2_discrete_a.restype = d
+        _lib.orc2_discrete_a.argtypes = [P2]
+        _lib.orc2_moments.argtypes = [P2, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.orc2_node_fields.argtypes = [P2, vp, vp, vp, vp, vp, vp, vp]
+        _lib.orc2_equilibria_node.argtypes = [P2, vp, vp, vp, vp, vp]
+        _lib.orc2_equilibrium.argtypes = [P2, vp, vp, vp, vp, vp, vp]
+        _lib.orc2_dxi.argtypes = [P2, vp, vp, vp]
+        _lib.orc2_rhs.argtypes = [P2, vp, vp, vp, vp, vp]
+        _lib.orc2_step.argtypes = [P2, vp, vp, i]
+        _lib.orc2_totals.argtypes = [P2, vp, vp, vp]
     return _lib
 
 
@@ -106,6 +119,15 @@ class _Params(ctypes.Structure):
                 ("weno_eps", ctypes.c_double), ("xi", ctypes.c_void_p),
                 ("w", ctypes.c_void_p), ("nq", ctypes.c_int), ("zq", ctypes.c_void_p),
                 ("wq", ctypes.c_void_p), ("phi_tl", ctypes.c_double)]
+
+
+class _Params2(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("Q", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("phi", ctypes.c_double), ("gamma", ctypes.c_double), ("rcut", ctypes.c_double),
+                ("weno_eps", ctypes.c_double), ("relax", ctypes.c_int), ("xi", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("nq", ctypes.c_int), ("zq", ctypes.c_void_p),
+                ("wq", ctypes.c_void_p)]
 
 
 # --------------------------------------------------------------------------
@@ -405,4 +427,121 @@ class Oracle:
         G = self._arr(G, (Q, nz))
         out = np.empty(4)
         self.lib.orc_totals(self.p, F.ctypes.data, G.ctypes.data, out.ctypes.data)
+        return out
+
+
+# --------------------------------------------------------------------------
+# Two-dimensional extension (evfdlb_oracle2d.c)
+# --------------------------------------------------------------------------
+NFIELDS2 = 22
+FIELD_NAMES2 = ("n", "ux", "uy", "T", "qx", "qy", "nbar", "chi", "Fx", "Fy", "mu", "tau", "Pr", "nu",
+                "Ax", "Ay", "Bx", "By", "Dxx", "Dxy", "Dyx", "Dyy")
+
+
+@dataclass
+class Setup2:
+    nx: int
+    ny: int
+    Q: int
+    dx: float
+    dt: float
+    sigma: float = 1.0
+    phi: float = 1.0
+    gamma: float = 6.0
+    rcut: float = 6.0
+    weno_eps: float = 1e-6
+    relax: int = 0
+    nq: int = 32
+
+
+class Oracle2D:
+    """FP64 CPU reference of the 2D tensor-product model.  Distributions are
+    arrays of shape (Q, Q, ny, nx) (index [kx, ky, y, x]), float64."""
+
+    def __init__(self, setup: Setup2):
+        self.s = setup
+        self.lib = _load()
+        self.xi, self.w = gauss_hermite(setup.Q)
+        self.zq, self.wq = gauss_hermite(setup.nq)
+        self._p = _Params2(setup.nx, setup.ny, setup.Q, setup.dx, setup.dt, setup.sigma, setup.phi,
+                           setup.gamma, setup.rcut, setup.weno_eps, setup.relax, self.xi.ctypes.data,
+                           self.w.ctypes.data, setup.nq, self.zq.ctypes.data, self.wq.ctypes.data)
+        self.p = ctypes.byref(self._p)
+        self.shape = (setup.Q, setup.Q, setup.ny, setup.nx)
+
+    def _a(self, x, shape):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        assert a.shape == shape, (a.shape, shape)
+        return a
+
+    def force_kernel(self, rx, ry):
+        out = np.empty(2)
+        self.lib.orc2_force_kernel(self.p, float(rx), float(ry), out.ctypes.data)
+        return out
+
+    def discrete_a(self):
+        return self.lib.orc2_discrete_a(self.p)
+
+    def critical_T(self):
+        return critical_point(self.discrete_a(), self.s.sigma)[1]
+
+    def moments(self, F, G):
+        F, G = self._a(F, self.shape), self._a(G, self.shape)
+        grid = (self.s.ny, self.s.nx)
+        out = [np.empty(grid) for _ in range(6)]
+        self.lib.orc2_moments(self.p, F.ctypes.data, G.ctypes.data, *[o.ctypes.data for o in out])
+        return tuple(out)
+
+    def node_fields(self, F, G):
+        mom = self.moments(F, G)
+        out = np.empty((NFIELDS2, self.s.ny, self.s.nx))
+        self.lib.orc2_node_fields(self.p, *[m.ctypes.data for m in mom], out.ctypes.data)
+        return {k: out[i] for i, k in enumerate(FIELD_NAMES2)}
+
+    def equilibria_node(self, fields: dict):
+        """(F^S, G^S, J1_F, J1_G), each (Q, Q), for one node's fields (missing
+        entries 0; chi and Pr default to 1)."""
+        fl = np.zeros(NFIELDS2)
+        fl[FIELD_NAMES2.index("chi")] = 1.0
+        fl[FIELD_NAMES2.index("Pr")] = 1.0
+        for k, v in fields.items():
+            fl[FIELD_NAMES2.index(k)] = v
+        Q = self.s.Q
+        outs = [np.empty((Q, Q)) for _ in range(4)]
+        self.lib.orc2_equilibria_node(self.p, fl.ctypes.data, *[o.ctypes.data for o in outs])
+        return tuple(outs)
+
+    def equilibrium(self, n, ux, uy, T):
+        grid = (self.s.ny, self.s.nx)
+        args = [self._a(np.broadcast_to(a, grid), grid) for a in (n, ux, uy, T)]
+        F, G = np.empty(self.shape), np.empty(self.shape)
+        self.lib.orc2_equilibrium(self.p, *[a.ctypes.data for a in args], F.ctypes.data, G.ctypes.data)
+        return F, G
+
+    def dxi(self, h):
+        Q = self.s.Q
+        h = self._a(h, (Q, Q))
+        ox, oy = np.empty((Q, Q)), np.empty((Q, Q))
+        self.lib.orc2_dxi(self.p, h.ctypes.data, ox.ctypes.data, oy.ctypes.data)
+        return ox, oy
+
+    def rhs(self, F, G, with_fields=False):
+        F, G = self._a(F, self.shape), self._a(G, self.shape)
+        RF, RG = np.empty(self.shape), np.empty(self.shape)
+        fl = np.empty((NFIELDS2, self.s.ny, self.s.nx))
+        self.lib.orc2_rhs(self.p, F.ctypes.data, G.ctypes.data, RF.ctypes.data, RG.ctypes.data, fl.ctypes.data)
+        if with_fields:
+            return RF, RG, {k: fl[i] for i, k in enumerate(FIELD_NAMES2)}
+        return RF, RG
+
+    def step(self, F, G, nsteps=1):
+        F, G = self._a(F, self.shape).copy(), self._a(G, self.shape).copy()
+        self.lib.orc2_step(self.p, F.ctypes.data, G.ctypes.data, int(nsteps))
+        return F, G
+
+    def totals(self, F, G):
+        """[mass, momentum x, momentum y, kinetic + internal energy]"""
+        F, G = self._a(F, self.shape), self._a(G, self.shape)
+        out = np.empty(4)
+        self.lib.orc2_totals(self.p, F.ctypes.data, G.ctypes.data, out.ctypes.data)
         return out
