@@ -205,10 +205,16 @@ class Sim:
         _check(lib().evfdlb_create(None, len(plist), arr, ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h)), "evfdlb_create")
         self.h = h
+        self.dim = plist[0].dim
         self.nx = [p.nx for p in plist]
         self.Q = [p.Q for p in plist]
-        self.NN = sum(self.nx)
-        self.NF = sum(p.nx * p.Q for p in plist)
+        if self.dim == 2:        # one plane periodic domain: nodes nx * ny, velocities Q * Q
+            p0 = plist[0]
+            self.NN = p0.nx * p0.ny
+            self.NF = p0.Q * p0.Q * self.NN
+        else:
+            self.NN = sum(self.nx)
+            self.NF = sum(p.nx * p.Q for p in plist)
 
     def close(self):
         if getattr(self, "h", None):
@@ -233,8 +239,11 @@ class Sim:
         return lib().evfdlb_tile_nodes(self.h)
 
     def init(self, n0, u0, T0):
+        """Projected Maxwellian state of (n0, u0, T0); in 2D u0 holds ux then
+        uy ([2, nx * ny])."""
+        nu = self.NN * (2 if self.dim == 2 else 1)
         if isinstance(n0, np.ndarray) or not hasattr(n0, "data_ptr"):
-            n0, u0, T0 = (_host(a, self.NN) for a in (n0, u0, T0))
+            n0, u0, T0 = _host(n0, self.NN), _host(u0, nu), _host(T0, self.NN)
         (pn, dev), (pu, _), (pT, _) = _ptr(n0), _ptr(u0), _ptr(T0)
         _check(lib().evfdlb_init(self.h, pn, pu, pT, dev), "evfdlb_init")
 
@@ -258,6 +267,7 @@ class Sim:
         _check(lib().evfdlb_set_state(self.h, pF, pG, dev), "evfdlb_set_state")
 
     def rhs(self):
+        """One right-hand side at the current state (state layout)."""
         RF, RG = np.empty(self.NF), np.empty(self.NF)
         _check(lib().evfdlb_rhs(self.h, RF.ctypes.data, RG.ctypes.data, 0), "evfdlb_rhs")
         return RF, RG
@@ -268,10 +278,16 @@ class Sim:
         return {k: out[i] for i, k in enumerate(FIELD_NAMES)}
 
     def moments(self, with_totals=True):
-        n, u, T, q = (np.empty(self.NN) for _ in range(4))
+        """(n, u, T, q, totals): per node; in 2D u and q are [2, nx * ny] and
+        totals are {mass, momentum x, momentum y, kinetic + internal energy}."""
+        vec = 2 if self.dim == 2 else 1
+        n, T = np.empty(self.NN), np.empty(self.NN)
+        u, q = np.empty(vec * self.NN), np.empty(vec * self.NN)
         tot = np.empty(4 * len(self.params)) if with_totals else None
         _check(lib().evfdlb_moments(self.h, n.ctypes.data, u.ctypes.data, T.ctypes.data, q.ctypes.data,
                                     tot.ctypes.data if tot is not None else None, 0), "evfdlb_moments")
+        if vec == 2:
+            u, q = u.reshape(2, self.NN), q.reshape(2, self.NN)
         return n, u, T, q, (tot.reshape(-1, 4) if tot is not None else None)
 
     # adjoint ----------------------------------------------------------------
@@ -314,8 +330,13 @@ class Sim:
 
     # helpers for one slab --------------------------------------------------
     def state_2d(self, s=0):
-        """(F, G) of slab s as (Q, nx) arrays."""
+        """(F, G) of slab s as (Q, nx) arrays; for a 2D context as
+        (Q, Q, ny, nx) arrays (index [kx, ky, y, x])."""
         F, G = self.get_state()
+        if self.dim == 2:
+            p = self.params[0]
+            shp = (p.Q, p.Q, p.ny, p.nx)
+            return F.reshape(shp), G.reshape(shp)
         off = sum(self.nx[i] * self.Q[i] for i in range(s))
         n = self.nx[s] * self.Q[s]
         return (F[off:off + n].reshape(self.Q[s], self.nx[s]),

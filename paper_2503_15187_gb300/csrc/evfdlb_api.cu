@@ -50,11 +50,28 @@ void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const W
                      double* dT0, long long NF, long long NN);
 void launch_adj_phi(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* phis, const double* phi_a,
                     double* out);
+// two-dimensional model (evfdlb_2d.cu)
+struct Ctx2;
+evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out);
+void destroy_2d(Ctx2* c);
+evfdlb_status init_2d(Ctx2* c, const double* n0, const double* u0, const double* T0, int on_device);
+evfdlb_status step_async_2d(Ctx2* c, int64_t nsteps);
+evfdlb_status check_2d(Ctx2* c);
+evfdlb_status get_state_2d(Ctx2* c, double* F, double* G, int on_device);
+evfdlb_status set_state_2d(Ctx2* c, const double* F, const double* G, int on_device);
+evfdlb_status rhs_2d(Ctx2* c, double* RF, double* RG, int on_device);
+evfdlb_status moments_2d(Ctx2* c, double* n, double* u, double* T, double* q, double* totals, int on_device);
+long long nodes_2d(const Ctx2* c);
+double dt_2d(const Ctx2* c);
+double discrete_a_2d(const evfdlb_params& p);
+bool validate_2d(const evfdlb_params& p);
 }  // namespace evfdlb
 
 using namespace evfdlb;
 
 struct evfdlb_ctx {
+    Ctx2* c2 = nullptr;          // set for a two-dimensional context (the rest unused)
+    bool c2_state = false;
     int nbatch = 0;
     std::vector<evfdlb_params> params;
     std::vector<SlabDesc> slabs_h;
@@ -111,6 +128,7 @@ evfdlb_status cuda_status(cudaError_t e) {
 
 void free_ctx(evfdlb_ctx* c) {
     if (!c) return;
+    if (c->c2) destroy_2d(c->c2);
     if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
     if (c->g_one) cudaGraphExecDestroy(c->g_one);
     for (int i = 0; i < 3; ++i) {
@@ -274,18 +292,22 @@ const char* evfdlb_status_string(evfdlb_status s) {
 }
 
 double evfdlb_discrete_a(const evfdlb_params* p) {
+    if (p && p->dim == 2) return validate_2d(*p) ? discrete_a_2d(*p) : NAN;
     if (!p || !validate(*p, nullptr)) return NAN;
     return discrete_a(*p);
 }
 
 double evfdlb_critical_T(const evfdlb_params* p) {
+    if (p && p->dim == 2) return validate_2d(*p) ? critical_T_of_a(discrete_a_2d(*p), p->sigma, nullptr) : NAN;
     if (!p || !validate(*p, nullptr)) return NAN;
     return critical_T_of_a(discrete_a(*p), p->sigma, nullptr);
 }
 
 evfdlb_status evfdlb_coexistence(const evfdlb_params* p, double T, double* nv, double* nl) {
-    if (!p || !nv || !nl || !validate(*p, nullptr)) return EVFDLB_E_INVALID_ARG;
-    if (!coexistence_of(discrete_a(*p), p->sigma, T, nv, nl)) return EVFDLB_E_INVALID_ARG;
+    if (!p || !nv || !nl) return EVFDLB_E_INVALID_ARG;
+    const bool two = (p->dim == 2);
+    if (two ? !validate_2d(*p) : !validate(*p, nullptr)) return EVFDLB_E_INVALID_ARG;
+    if (!coexistence_of(two ? discrete_a_2d(*p) : discrete_a(*p), p->sigma, T, nv, nl)) return EVFDLB_E_INVALID_ARG;
     return EVFDLB_OK;
 }
 
@@ -299,6 +321,24 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     if (!out) return EVFDLB_E_INVALID_ARG;
     *out = nullptr;
     if (nbatch < 1) return EVFDLB_E_INVALID_ARG;
+    {
+        const evfdlb_params* q0 = p ? p : per_slab;
+        if (q0 && q0->dim == 2) {     // one plane periodic domain per context
+            if (nbatch != 1) return EVFDLB_E_UNSUPPORTED;
+            evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
+            if (!c) return EVFDLB_E_OOM;
+            evfdlb_status st = create_2d(*q0, cuda_stream, &c->c2);
+            if (st != EVFDLB_OK) {
+                delete c;
+                return st;
+            }
+            c->nbatch = 1;
+            c->params.push_back(*q0);
+            c->user = (cudaStream_t)cuda_stream;
+            *out = c;
+            return EVFDLB_OK;
+        }
+    }
     if (nbatch == 1 && !p && !per_slab) return EVFDLB_E_INVALID_ARG;
     if (nbatch > 1 && !per_slab) return EVFDLB_E_INVALID_ARG;
     std::vector<evfdlb_params> ps(nbatch);
@@ -437,6 +477,12 @@ void evfdlb_destroy(evfdlb_ctx* c) {
 
 evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, const double* T0, int32_t on_device) {
     if (!c || !n0 || !u0 || !T0) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) {
+        evfdlb_status s = init_2d(c->c2, n0, u0, T0, on_device);
+        c->c2_state = (s == EVFDLB_OK);
+        c->poisoned = false;
+        return s;
+    }
     const double* dn = n0;
     const double* du = u0;
     const double* dT = T0;
@@ -470,6 +516,10 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
 
 evfdlb_status evfdlb_step_async(evfdlb_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) {
+        if (!c->c2_state || c->poisoned) return EVFDLB_E_STATE;
+        return step_async_2d(c->c2, nsteps);
+    }
     if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
     while (nsteps > 0) {
         int64_t n = nsteps;
@@ -500,11 +550,17 @@ evfdlb_status evfdlb_step_async(evfdlb_ctx* c, int64_t nsteps) {
 evfdlb_status evfdlb_step(evfdlb_ctx* c, int64_t nsteps) {
     evfdlb_status s = evfdlb_step_async(c, nsteps);
     if (s != EVFDLB_OK) return s;
+    if (c->c2) {
+        s = check_2d(c->c2);
+        if (s != EVFDLB_OK) c->poisoned = true;
+        return s;
+    }
     return check_device(c);
 }
 
 evfdlb_status evfdlb_get_state(evfdlb_ctx* c, double* F, double* G, int32_t on_device) {
     if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return c->c2_state ? get_state_2d(c->c2, F, G, on_device) : EVFDLB_E_STATE;
     if (!c->have_state) return EVFDLB_E_STATE;
     size_t bytes = sizeof(double) * c->NF;
     const double* src = (const double*)c->state[0];
@@ -522,6 +578,12 @@ evfdlb_status evfdlb_get_state(evfdlb_ctx* c, double* F, double* G, int32_t on_d
 
 evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, int32_t on_device) {
     if (!c || !F || !G) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) {
+        evfdlb_status s = set_state_2d(c->c2, F, G, on_device);
+        c->c2_state = (s == EVFDLB_OK);
+        c->poisoned = false;
+        return s;
+    }
     size_t bytes = sizeof(double) * c->NF;
     double* dst = (c->prec == EVFDLB_FP32) ? c->scratch : (double*)c->state[0];
     evfdlb_status s;
@@ -545,6 +607,7 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
 
 evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_device) {
     if (!c || !RF || !RG) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return c->c2_state ? rhs_2d(c->c2, RF, RG, on_device) : EVFDLB_E_STATE;
     if (!c->have_state) return EVFDLB_E_STATE;
     launch_stage_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables,
                    c->taps, c->rtaps, c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr, c->NF, c->NN,
@@ -559,6 +622,7 @@ evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_devic
 
 evfdlb_status evfdlb_fields(evfdlb_ctx* c, double* fields, int32_t on_device) {
     if (!c || !fields) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
     if (!c->have_state) return EVFDLB_E_STATE;
     double* buf = c->scratch;
     launch_fields_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->rtables, c->taps,
@@ -572,6 +636,7 @@ evfdlb_status evfdlb_fields(evfdlb_ctx* c, double* fields, int32_t on_device) {
 evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, double* q, double* totals,
                              int32_t on_device) {
     if (!c) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return c->c2_state ? moments_2d(c->c2, n, u, T, q, totals, on_device) : EVFDLB_E_STATE;
     if (!c->have_state) return EVFDLB_E_STATE;
     double* buf = c->scratch;
     double* outs[4] = {n, u, T, q};
@@ -597,18 +662,25 @@ evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, dou
 
 evfdlb_status evfdlb_slab_info(const evfdlb_ctx* c, int32_t s, int32_t* nx, int32_t* Q, double* dt) {
     if (!c || s < 0 || s >= c->nbatch) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) {
+        if (nx) *nx = c->params[0].nx;
+        if (Q) *Q = c->params[0].Q;
+        if (dt) *dt = dt_2d(c->c2);
+        return EVFDLB_OK;
+    }
     if (nx) *nx = c->slabs_h[s].nx;
     if (Q) *Q = c->slabs_h[s].Q;
     if (dt) *dt = c->slabs_h[s].dt;
     return EVFDLB_OK;
 }
 
-int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? 3 : 0; }
+int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? (c->c2 ? 12 : 3) : 0; }
 
-int32_t evfdlb_tile_nodes(const evfdlb_ctx* c) { return c ? c->Z : 0; }
+int32_t evfdlb_tile_nodes(const evfdlb_ctx* c) { return c ? (c->c2 ? 0 : c->Z) : 0; }
 
 evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
     if (!c || tile_nodes < 1 || tile_nodes > kZMax) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
     TRY_CUDA(cudaStreamSynchronize(c->user));
     partition(c, tile_nodes);
     TRY_CUDA(cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice));
@@ -623,6 +695,7 @@ evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
 evfdlb_status evfdlb_rhs_vjp(evfdlb_ctx* c, const double* WF, const double* WG, int32_t on_device, double* outF,
                              double* outG, double* dphi) {
     if (!c || !WF || !WG || !outF || !outG) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
     if (!c->have_state) return EVFDLB_E_STATE;
     evfdlb_status st = adjoint_supported(c);
     if (st != EVFDLB_OK) return st;
@@ -648,6 +721,7 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
                                    double* dL_dphi_a, double* dL_dF0, double* dL_dG0, double* dL_dn0,
                                    double* dL_du0, double* dL_dT0) {
     if (!c || !barF || !barG) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
     if (!c->have_state || c->poisoned || c->ckpt_every <= 0) return EVFDLB_E_STATE;
     if ((dL_dn0 || dL_du0 || dL_dT0) && !c->origin_init) return EVFDLB_E_STATE;
     evfdlb_status st = adjoint_supported(c);
@@ -726,6 +800,7 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
 evfdlb_status evfdlb_adjoint(evfdlb_ctx* c, const double* dL_dn_end, int32_t on_device, double* dL_dphi_a,
                              double* dL_dT0, double* dL_dn0) {
     if (!c || !dL_dn_end) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
     if (!c->have_state) return EVFDLB_E_STATE;
     // n = sum_k F_k, so dL/dF_k = dL/dn for every k and dL/dG = 0
     std::vector<double> hF((size_t)c->NF), hG((size_t)c->NF, 0.0), hn((size_t)c->NN);
