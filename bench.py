@@ -218,9 +218,12 @@ def run_ours(args, rank, world):
     n64 = sim.moments(with_totals=False)[0]
     sim.close()
     if not args.no_variants:
-        line["variants"] = {"fp32": fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
-                            "adjoint": adjoint_leg(ev, W, stream),
-                            "batched": batched_leg(ev, W, stream, rank, world, maxred)}
+        legs = {"fp32": lambda: fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
+                "adjoint": lambda: adjoint_leg(ev, W, stream),
+                "batched": lambda: batched_leg(ev, W, stream, rank, world, maxred),
+                "two_d": lambda: two_d_leg(ev, stream, flush, maxred, world)}
+        want = args.variants.split(",") if args.variants else list(legs)
+        line["variants"] = {k: legs[k]() for k in want}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, T, n0)
     return line
@@ -354,6 +357,41 @@ def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=4):
             "autotune_ms_per_step": {str(k): round(v, 3) for k, v in tune_ms.items()}}
 
 
+def two_d_leg(ev, stream, flush, maxred, world, steps=3):
+    """2D phase separation: 1024 x 1024 periodic grid, dx = 0.25 sigma,
+    tensor-product Gauss-Hermite 16 x 16 velocities, FP32 bulk with FP64
+    conserved sums, T = 0.75 T_c, mean n = 0.25 with +-1% seeded noise.
+    State 2 GiB per copy (larger than L2); timed over `steps` steps with CUDA
+    events.  Algorithmic HBM bytes per node-velocity-step: the four launches
+    of a stage move the state 7 times (moments 1, collision 2, advection 4:
+    source, local RHS, base, output), 2 distributions x 4 B, 3 stages: 168 B."""
+    import numpy as np
+    import torch
+    nx = ny = 1024
+    Q = 16
+    p = ev.Params(nx=nx, dx=0.25, Q=Q, dim=2, ny=ny, precision=ev.FP32)
+    T = 0.75 * ev.critical_T(p)
+    sim = ev.Sim(p, stream=stream)
+    rng = np.random.default_rng(15187)
+    n0 = 0.25 * (1 + 0.01 * rng.uniform(-1, 1, nx * ny))
+    sim.init(n0, np.zeros(2 * nx * ny), np.full(nx * ny, T))
+    sim.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step_async(steps)
+    e1.record(stream)
+    sim.step(0)
+    ms = maxred(e0.elapsed_time(e1)) / steps
+    mass = sim.moments()[4][0][0]
+    sim.close()
+    nvu = nx * ny * Q * Q
+    gbs = 168.0 * nvu / (ms * 1e-3) / 1e9
+    return {"workload": "2D phase separation 1024x1024, dx 0.25, 16x16 velocities, FP32 (FP64 conserved sums)",
+            "value": nvu * world / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "algorithmic_GBps": gbs,
+            "mass": mass, "gpu_launches_per_step": 12}
+
+
 def cpu_baseline(budget_s, T, n0, max_steps=10**9):
     """Times the FP64 oracle as it stands on one host core on a bounded sample
     of the same workload (whole slab, as many steps as fit in budget_s)."""
@@ -411,7 +449,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
-                    help="report the headline FP64 leg only (no FP32 / adjoint / batched legs), e.g. for ncu")
+                    help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")
+    ap.add_argument("--variants", default="", help="comma-separated subset of fp32,adjoint,batched,two_d")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

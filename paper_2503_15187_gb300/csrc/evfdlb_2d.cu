@@ -17,15 +17,15 @@
 //     normalised; fourth-order gradients and WENO-5 along each axis.
 // One RK stage is four launches:
 //   k2_moments  raw moment sums of the stage input per node (the conserved
-//               ones -- mass, momentum, energy -- in FP64);
+//               ones -- mass, momentum, energy -- to FP64 accuracy);
 //   k2_fields   node fields per 16x16 node tile (force disc, FM average, chi,
 //               gradients, transport) and the polynomial coefficients of the
 //               equilibria;
 //   k2_coll     per group of 8 nodes, all Q^2 velocities: separable Hermite
 //               analysis, coefficients (equilibria + force), separable
 //               synthesis; writes the local part -nu h + sum S c;
-//   k2_adv      per velocity plane and 32x8 node tile: WENO-5 faces along x
-//               and y, the full right-hand side and the Shu-Osher combine.
+//   k2_adv      per 32x16 node tile and 8 velocity planes: WENO-5 faces along
+//               x and y, the full right-hand side and the Shu-Osher combine.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -56,7 +56,8 @@ enum { F2_N = 0, F2_UX, F2_UY, F2_T, F2_NU, F2_FX, F2_FY, F2_PF = 7, F2_PG = 17,
 
 constexpr int kTile2 = 16;     // k2_fields tile edge
 constexpr int kNB = 8;         // nodes per k2_coll CTA
-constexpr int kAdvX = 32, kAdvY = 8;
+constexpr int kAdvX = 32, kAdvY = 16, kAdvPlanes = 8;
+static_assert(kAdvX == 32 && kAdvY % 8 == 0, "k2_adv maps a warp (256 threads per CTA) to tile rows");
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     int r = i % n;
@@ -65,9 +66,29 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 
 // ---------------------------------------------------------------------------
 // k2_moments: per node, raw sums over the Q^2 velocities.  Conserved sums
-// (S0, S1, S2xx, S2yy, G0) are accumulated in FP64 through row and column
-// sums of the velocity grid; the heat-flux sums in R.
+// (S0, S1, S2xx, S2yy, G0) are formed from the row and column sums of the
+// velocity grid, combined in FP64; for an FP32 state each 16-term row or
+// column sum is a compensated (Neumaier) FP32 sum kept as an unevaluated
+// pair, accurate to O(Q u^2) of the sum of magnitudes, i.e. FP64 quality at
+// FP32-pipe cost.  The heat-flux sums are plain R sums.
 // ---------------------------------------------------------------------------
+template <typename R>
+struct CompSum {                       // R = double: plain accumulation
+    double s = 0.0;
+    __device__ __forceinline__ void add(R x) { s += (double)x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct CompSum<float> {                // Neumaier's compensated sum
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 k2_moments(Slab2 s, const double* __restrict__ tab, const R* __restrict__ st, double* __restrict__ mom,
@@ -77,40 +98,41 @@ k2_moments(Slab2 s, const double* __restrict__ tab, const R* __restrict__ st, do
     TableLayout L(Q);
     const double* xi = tab + L.xi;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        double col[16];
-        for (int k = 0; k < Q; ++k) col[k] = 0.0;
+        CompSum<R> col[16];
         double s0 = 0, s1x = 0, s2xx = 0, g0 = 0;
         R s2xy = 0, s3x = 0, s3y = 0, g1x = 0, g1y = 0;
         for (int kx = 0; kx < Q; ++kx) {
             const double x = xi[kx];
-            double rowF = 0.0, rowG = 0.0;
+            CompSum<R> rowF, rowG;
             R ps2xy = 0, ps3x = 0, ps3y = 0, pg1y = 0;
             for (int ky = 0; ky < Q; ++ky) {
                 const long long g = (long long)(kx * Q + ky) * N + i;
                 R f = st[g], gg = st[NF + g];
-                rowF += (double)f;
-                rowG += (double)gg;
-                col[ky] += (double)f;
+                rowF.add(f);
+                rowG.add(gg);
+                col[ky].add(f);
                 const R y = (R)xi[ky], xr = (R)x, v2 = xr * xr + y * y;
                 ps2xy = fma(y, f, ps2xy);
                 ps3x = fma(v2, f, ps3x);
                 ps3y = fma(y * v2, f, ps3y);
                 pg1y = fma(y, gg, pg1y);
             }
-            s0 += rowF;
-            s1x = fma(x, rowF, s1x);
-            s2xx = fma(x * x, rowF, s2xx);
-            g0 += rowG;
+            const double rf = rowF.value(), rg = rowG.value();
+            s0 += rf;
+            s1x = fma(x, rf, s1x);
+            s2xx = fma(x * x, rf, s2xx);
+            g0 += rg;
             s2xy = fma((R)x, ps2xy, s2xy);
             s3x = fma((R)x, ps3x, s3x);
             s3y += ps3y;
-            g1x = fma((R)x, (R)rowG, g1x);
+            g1x = fma((R)x, (R)rg, g1x);
             g1y += pg1y;
         }
         double s1y = 0, s2yy = 0;
         for (int ky = 0; ky < Q; ++ky) {
-            s1y = fma(xi[ky], col[ky], s1y);
-            s2yy = fma(xi[ky] * xi[ky], col[ky], s2yy);
+            const double cv = col[ky].value();
+            s1y = fma(xi[ky], cv, s1y);
+            s2yy = fma(xi[ky] * xi[ky], cv, s2yy);
         }
         if (!isfinite(s0) || !isfinite(s2xx + s2yy + g0)) atomicOr(err, ERR_NONFINITE);
         mom[M2_S0 * N + i] = s0;
@@ -273,45 +295,92 @@ k2_fields(Slab2 s, const double* __restrict__ mom, const int* __restrict__ ft_of
 // the coefficient of psi_l(xi_x) psi_m(xi_y) of F_MB sum_ab P_ab c_x^a c_y^b is
 // n sum_ab P_ab mu^a_l(u_x) mu^b_m(u_y).
 // ---------------------------------------------------------------------------
-template <typename R>
-__host__ __device__ inline size_t coll_smem_bytes(int Q) {
-    size_t K = (size_t)Q * Q;
-    return sizeof(R) * (2 * K + 3 * Q + 3 * 2 * K * kNB + kNumFld2 * kNB + 4 * Q * kNB + 2 * 4 * Q * kNB);
-}
+// Shared layout of k2_coll: per distribution and node a Q x Q matrix with
+// rows padded to kRow (a multiple of 4 elements, so that a row is float4 /
+// double2 aligned), node stride padded by 4 so that the eight nodes of a
+// group fall in different banks.
+constexpr int kRow = 16;
+__host__ __device__ constexpr int padded_q(int Q) { return (Q + 3) & ~3; }
+__host__ __device__ constexpr int node_stride(int Q) { return padded_q(Q) * kRow + 4; }
 
 template <typename R>
+__host__ __device__ inline size_t coll_smem_bytes(int Q) {
+    size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
+    return sizeof(R) * (2 * (size_t)Q * kRow + 3 * (size_t)Q + 3 * X + kNumFld2 * kNB + 4 * (size_t)Q * kNB +
+                        2 * 4 * (size_t)Q * kNB);
+}
+
+// Out[i][j] = sum_k Lt[k][i] In[k][j]  (left contraction, Lt = transposed left matrix)
+// or         sum_k In[i][k] Rt[k][j]  (right contraction, Rt = transposed right matrix)
+// for the matrices of one (distribution, node); each thread forms a 4 x 4
+// block from four-wide loads of a row of Lt (or Rt) and of In.
+template <typename R, bool LEFT, int Q>
+__device__ __forceinline__ void block_transform(const R* __restrict__ M, const R* __restrict__ In, R* __restrict__ Out,
+                                                int i0, int j0) {
+    R acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        R m[4], x[4];
+        if (LEFT) {
+            for (int a = 0; a < 4; ++a) m[a] = M[k * kRow + i0 + a];       // Lt[k][i0 + a]
+            for (int b = 0; b < 4; ++b) x[b] = In[k * kRow + j0 + b];      // In[k][j0 + b]
+        } else {
+            for (int a = 0; a < 4; ++a) m[a] = In[(i0 + a) * kRow + k];    // In[i0 + a][k]
+            for (int b = 0; b < 4; ++b) x[b] = M[k * kRow + j0 + b];       // Rt[k][j0 + b]
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a], x[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) Out[(i0 + a) * kRow + j0 + b] = acc[a][b];
+}
+
+template <typename R, int Q>
 __global__ void __launch_bounds__(256)
-k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* __restrict__ fld, R* __restrict__ RL,
-        double* __restrict__ rhs_scratch_unused) {
+k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* __restrict__ fld, R* __restrict__ RL) {
     extern __shared__ double smc[];
-    const int Q = s.Q, K = Q * Q;
+    constexpr int K = Q * Q, NS = node_stride(Q), Qp = padded_q(Q);
     const long long N = s.N, NF = (long long)K * N;
     const long long i0 = (long long)blockIdx.x * kNB;
     const int nb = (int)min((long long)kNB, N - i0);
     TableLayout L(Q);
-    R* P = reinterpret_cast<R*>(smc);      // P[l][j] = psi_l(xi_j)
-    R* S = P + K;                          // S[k][l] = w_k psi_l(xi_k)
-    R* r1 = S + K;
+    R* Pt = reinterpret_cast<R*>(smc);     // Pt[j][l] = psi_l(xi_j)       (transposed analysis table)
+    R* St = Pt + Q * kRow;                 // St[l][k] = w_k psi_l(xi_k)   (transposed synthesis table)
+    R* r1 = St + Q * kRow;
     R* r2 = r1 + Q;
     R* r3 = r2 + Q;
-    R* Hh = r3 + Q;                        // [2][K][kNB]
-    R* T1 = Hh + 2 * K * kNB;
-    R* A = T1 + 2 * K * kNB;
-    R* sc = A + 2 * K * kNB;               // [kNumFld2][kNB]
+    R* X0 = r3 + Q;                        // [2][kNB] matrices, node stride NS
+    R* X1 = X0 + 2 * kNB * NS;
+    R* X2 = X1 + 2 * kNB * NS;
+    R* sc = X2 + 2 * kNB * NS;             // [kNumFld2][kNB]
     R* mux = sc + kNumFld2 * kNB;          // [4][Q][kNB]
     R* Vy = mux + 4 * Q * kNB;             // [2][4][Q][kNB]
-    for (int e = threadIdx.x; e < K; e += blockDim.x) {
-        P[e] = rtab[L.P + e];
-        S[e] = rtab[L.S + e];
+    auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
+    for (int e = threadIdx.x; e < Q * kRow; e += blockDim.x) {
+        int r = e / kRow, c = e % kRow;
+        Pt[e] = (c < Q) ? rtab[L.P + c * Q + r] : R(0);
+        St[e] = (c < Q) ? rtab[L.S + c * Q + r] : R(0);
     }
     for (int e = threadIdx.x; e < Q; e += blockDim.x) {
         r1[e] = rtab[L.r1 + e];
         r2[e] = rtab[L.r2 + e];
         r3[e] = rtab[L.r3 + e];
     }
+    // state of the group as [d][node][kx][ky] (ky contiguous, rows of kRow);
+    // rows and columns Q .. Qp-1 of every matrix stay zero
+    for (int e = threadIdx.x; e < 3 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
+    __syncthreads();
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
         int t = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
-        Hh[e] = (t < nb) ? st[d * NF + (long long)k * N + i0 + t] : R(0);
+        mat(X0, d, t)[(k / Q) * kRow + k % Q] = (t < nb) ? st[d * NF + (long long)k * N + i0 + t] : R(0);
     }
     for (int e = threadIdx.x; e < kNumFld2 * kNB; e += blockDim.x) {
         int t = e % kNB, f = e / kNB;
@@ -367,60 +436,56 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             m0 = mn;
         }
     }
-    // analysis, first axis: T1[d][l][ky] = sum_kx P[l][kx] h[d][kx][ky]
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, ky = (e / kNB) % Q, l = (e / (kNB * Q)) % Q, d = e / (kNB * K);
-        const R* h = Hh + (size_t)d * K * kNB + ky * kNB + t;
-        R acc = 0;
-        for (int kx = 0; kx < Q; ++kx) acc = fma(P[l * Q + kx], h[kx * Q * kNB], acc);
-        T1[e] = acc;
+    // the four tensor transforms: one (distribution, node, 4x4 block) per thread
+    const int nblk = (Qp / 4) * (Qp / 4);
+    const int item = threadIdx.x / nblk, blk = threadIdx.x % nblk;   // item = d * kNB + node
+    const bool active = item < 2 * kNB;
+    const int d = item / kNB, t = item % kNB;
+    const int bi = 4 * (blk / (Qp / 4)), bj = 4 * (blk % (Qp / 4));
+    // analysis along xi_x: X1[l][ky] = sum_kx psi_l(xi_kx) X0[kx][ky]
+    if (active) block_transform<R, true, Q>(Pt, mat(X0, d, t), mat(X1, d, t), bi, bj);
+    __syncthreads();
+    // analysis along xi_y: X2[l][m] = sum_ky X1[l][ky] psi_m(xi_ky)
+    if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X2, d, t), bi, bj);
+    __syncthreads();
+    // coefficients (equilibria, J1, force terms) into X1
+    for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
+        const int l = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
+        const R* A = mat(X2, dd, tt);
+        R* C = mat(X1, dd, tt) + l * kRow;
+        R mx[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) mx[a] = mux[(a * Q + l) * kNB + tt];
+        const R fx = sc[F2_FX * kNB + tt] * r1[l], fy = sc[F2_FY * kNB + tt];
+#pragma unroll
+        for (int mm = 0; mm < Q; ++mm) {
+            R c = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) c = fma(mx[a], Vy[((dd * 4 + a) * Q + mm) * kNB + tt], c);
+            if (l >= 1) c = fma(fx, A[(l - 1) * kRow + mm], c);
+            if (mm >= 1) c = fma(fy * r1[mm], A[l * kRow + mm - 1], c);
+            C[mm] = c;
+        }
     }
     __syncthreads();
-    // analysis, second axis: A[d][l][m] = sum_ky P[m][ky] T1[d][l][ky]
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, m = (e / kNB) % Q, l = (e / (kNB * Q)) % Q, d = e / (kNB * K);
-        const R* tl = T1 + ((size_t)d * K + l * Q) * kNB + t;
-        R acc = 0;
-        for (int ky = 0; ky < Q; ++ky) acc = fma(P[m * Q + ky], tl[ky * kNB], acc);
-        A[e] = acc;
-    }
+    // synthesis along xi_x: X2[kx][m] = sum_l w_kx psi_l(xi_kx) X1[l][m]
+    if (active) block_transform<R, true, Q>(St, mat(X1, d, t), mat(X2, d, t), bi, bj);
     __syncthreads();
-    // coefficients: equilibria and J1, plus the force terms
-    // Fx sqrt(l) a_{l-1,m} + Fy sqrt(m) a_{l,m-1}; written over T1
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, m = (e / kNB) % Q, l = (e / (kNB * Q)) % Q, d = e / (kNB * K);
-        R c = 0;
-        for (int a = 0; a < 4; ++a) c = fma(mux[(a * Q + l) * kNB + t], Vy[((d * 4 + a) * Q + m) * kNB + t], c);
-        const R* Ad = A + (size_t)d * K * kNB + t;
-        if (l >= 1) c = fma(sc[F2_FX * kNB + t] * r1[l], Ad[((l - 1) * Q + m) * kNB], c);
-        if (m >= 1) c = fma(sc[F2_FY * kNB + t] * r1[m], Ad[(l * Q + m - 1) * kNB], c);
-        T1[e] = c;
-    }
+    // synthesis along xi_y: X1[kx][ky] = sum_m X2[kx][m] w_ky psi_m(xi_ky)
+    if (active) block_transform<R, false, Q>(St, mat(X2, d, t), mat(X1, d, t), bi, bj);
     __syncthreads();
-    // synthesis, first axis: A[d][kx][m] = sum_l S[kx][l] C[d][l][m]
+    // the local right-hand side -nu h + sum S S c
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, m = (e / kNB) % Q, kx = (e / (kNB * Q)) % Q, d = e / (kNB * K);
-        const R* cm = T1 + (size_t)d * K * kNB + m * kNB + t;
-        R acc = 0;
-        for (int l = 0; l < Q; ++l) acc = fma(S[kx * Q + l], cm[l * Q * kNB], acc);
-        A[e] = acc;
-    }
-    __syncthreads();
-    // synthesis, second axis, and the local right-hand side -nu h + sum S S c
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, ky = (e / kNB) % Q, kx = (e / (kNB * Q)) % Q, d = e / (kNB * K);
-        if (t >= nb) continue;
-        const R* um = A + ((size_t)d * K + kx * Q) * kNB + t;
-        R acc = 0;
-        for (int m = 0; m < Q; ++m) acc = fma(S[ky * Q + m], um[m * kNB], acc);
-        const int k = kx * Q + ky;
-        RL[d * NF + (long long)k * N + i0 + t] = fma(-sc[F2_NU * kNB + t], Hh[e], acc);
+        int tt = e % kNB, k = (e / kNB) % K, dd = e / (kNB * K);
+        if (tt >= nb) continue;
+        const int off = (k / Q) * kRow + k % Q;
+        RL[dd * NF + (long long)k * N + i0 + tt] = fma(-sc[F2_NU * kNB + tt], mat(X0, dd, tt)[off], mat(X1, dd, tt)[off]);
     }
 }
 
 // ---------------------------------------------------------------------------
-// k2_adv: one velocity plane, one 32x8 node tile: WENO-5 faces along x and
-// y, the right-hand side and the Shu-Osher combine
+// k2_adv: a 32x16 node tile and a run of velocity planes: WENO-5 faces along
+// x and y, the right-hand side and the Shu-Osher combine
 //   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -439,70 +504,93 @@ __device__ __forceinline__ R weno5_2(R v0, R v1, R v2, R v3, R v4, R eps) {
     e1 *= e1;
     e2 *= e2;
     R a0 = R(0.1) * (e1 * e2), a1 = R(0.6) * (e0 * e2), a2 = R(0.3) * (e0 * e1);
-    return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+    R num = fma(a0, q0, fma(a1, q1, a2 * q2)), den = a0 + a1 + a2;
+    // FP32: the fast reciprocal-based quotient (2 ulp) is far inside the FP32
+    // variant's error budget; FP64 keeps the IEEE quotient
+    if constexpr (std::is_same<R, float>::value) return __fdividef(num, den);
+    else return num / den;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256)
 k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* base, R* out,
        const R* __restrict__ RL, double* rhs_out, double alpha, double beta, int mode) {
-    __shared__ R Hs[(kAdvY + 6) * (kAdvX + 6)];
+    constexpr int WX = kAdvX + 6, WY = kAdvY + 6;
+    __shared__ R Hs[WY * WX];
     __shared__ R FX[kAdvY * (kAdvX + 1)];
     __shared__ R FY[(kAdvY + 1) * kAdvX];
+    __shared__ long long rowoff[WY];
+    __shared__ int coloff[WX];
     const int Q = s.Q, K = Q * Q, nx = s.nx, ny = s.ny;
     const long long N = s.N, NF = (long long)K * N;
     const int tilesx = (nx + kAdvX - 1) / kAdvX;
     const int x0 = (blockIdx.x % tilesx) * kAdvX, y0 = (blockIdx.x / tilesx) * kAdvY;
-    const int plane = blockIdx.y, d = plane / K, k = plane % K;
     TableLayout L(Q);
-    const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
-    const R* h = src + d * NF + (long long)k * N;
-    constexpr int WX = kAdvX + 6;
-    for (int e = threadIdx.x; e < (kAdvY + 6) * WX; e += blockDim.x) {
-        int cy = e / WX, cx = e % WX;
-        Hs[e] = h[(long long)wrapi(y0 - 3 + cy, ny) * nx + wrapi(x0 - 3 + cx, nx)];
+    // wrapped halo coordinates, shared by every plane of this tile
+    for (int e = threadIdx.x; e < WY + WX; e += blockDim.x) {
+        if (e < WY) rowoff[e] = (long long)wrapi(y0 - 3 + e, ny) * nx;
+        else coloff[e - WY] = wrapi(x0 - 3 + (e - WY), nx);
     }
-    __syncthreads();
-    const R eps = (R)s.weno_eps;
-    // x faces: face f of row r lies between tile columns f-1 and f
-    for (int e = threadIdx.x; e < kAdvY * (kAdvX + 1); e += blockDim.x) {
-        int r = e / (kAdvX + 1), f = e % (kAdvX + 1);
-        const R* row = Hs + (r + 3) * WX;
-        R v;
-        if (vx > R(0)) v = weno5_2<R>(row[f], row[f + 1], row[f + 2], row[f + 3], row[f + 4], eps);
-        else if (vx < R(0)) v = weno5_2<R>(row[f + 5], row[f + 4], row[f + 3], row[f + 2], row[f + 1], eps);
-        else v = 0;
-        FX[e] = v;
+    const R eps = (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
+    const bool with_base = (alpha != 0.0);
+    const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
+    for (int plane = p0; plane < p1; ++plane) {
+        const int d = plane / K, k = plane % K;
+        const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
+        const R* h = src + d * NF + (long long)k * N;
+        __syncthreads();   // previous plane's faces consumed; halo offsets written
+        for (int e = threadIdx.x; e < WY * WX; e += blockDim.x) {
+            int cy = e / WX, cx = e % WX;
+            Hs[e] = h[rowoff[cy] + coloff[cx]];
+        }
+        __syncthreads();
+        // x faces: face f of row r lies between tile columns f-1 and f; warp w
+        // owns rows 2w and 2w+1 (lane = face, lane 0 also face 32)
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int rr = 0; rr < kAdvY / 8; ++rr) {
+            const int r = warp * (kAdvY / 8) + rr;
+            const R* row = Hs + (r + 3) * WX;
+            for (int f = lane; f <= kAdvX; f += 32) {
+                R v;
+                if (vx > R(0)) v = weno5_2<R>(row[f], row[f + 1], row[f + 2], row[f + 3], row[f + 4], eps);
+                else if (vx < R(0)) v = weno5_2<R>(row[f + 5], row[f + 4], row[f + 3], row[f + 2], row[f + 1], eps);
+                else v = 0;
+                FX[r * (kAdvX + 1) + f] = v;
+            }
+        }
+        // y faces: face f of column c lies between tile rows f-1 and f; warp w
+        // owns face rows w, w + 8, ... (lane = column)
+        for (int f = warp; f <= kAdvY; f += 8) {
+            const R* col = Hs + lane + 3;
+            R v;
+            if (vy > R(0))
+                v = weno5_2<R>(col[f * WX], col[(f + 1) * WX], col[(f + 2) * WX], col[(f + 3) * WX],
+                               col[(f + 4) * WX], eps);
+            else if (vy < R(0))
+                v = weno5_2<R>(col[(f + 5) * WX], col[(f + 4) * WX], col[(f + 3) * WX], col[(f + 2) * WX],
+                               col[(f + 1) * WX], eps);
+            else v = 0;
+            FY[f * kAdvX + lane] = v;
+        }
+        __syncthreads();
+        const int x = x0 + lane;
+        for (int rr = 0; rr < kAdvY / 8; ++rr) {
+            const int ty = warp * (kAdvY / 8) + rr, y = y0 + ty;
+            if (x >= nx || y >= ny) continue;
+            const long long g = d * NF + (long long)k * N + (long long)y * nx + x;
+            R Rv = RL[g];
+            Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
+            Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
+            if (mode == 1) {
+                rhs_out[g] = (double)Rv;
+                continue;
+            }
+            const R hv = Hs[(ty + 3) * WX + lane + 3];
+            R o = rbeta * fma(dt, Rv, hv);
+            if (with_base) o = fma(ralpha, base[g], o);
+            out[g] = o;
+        }
     }
-    // y faces: face f of column c lies between tile rows f-1 and f
-    for (int e = threadIdx.x; e < (kAdvY + 1) * kAdvX; e += blockDim.x) {
-        int f = e / kAdvX, cc = e % kAdvX;
-        const R* col = Hs + cc + 3;
-        R v;
-        if (vy > R(0))
-            v = weno5_2<R>(col[f * WX], col[(f + 1) * WX], col[(f + 2) * WX], col[(f + 3) * WX], col[(f + 4) * WX], eps);
-        else if (vy < R(0))
-            v = weno5_2<R>(col[(f + 5) * WX], col[(f + 4) * WX], col[(f + 3) * WX], col[(f + 2) * WX], col[(f + 1) * WX], eps);
-        else v = 0;
-        FY[e] = v;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x % kAdvX, ty = threadIdx.x / kAdvX;
-    const int x = x0 + tx, y = y0 + ty;
-    if (ty >= kAdvY || x >= nx || y >= ny) return;
-    const long long g = d * NF + (long long)k * N + (long long)y * nx + x;
-    const R idx = (R)s.inv_dx;
-    R Rv = RL[g];
-    Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + tx + 1] - FX[ty * (kAdvX + 1) + tx], Rv);
-    Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + tx] - FY[ty * kAdvX + tx], Rv);
-    if (mode == 1) {
-        rhs_out[g] = (double)Rv;
-        return;
-    }
-    const R hv = Hs[(ty + 3) * WX + tx + 3];
-    R o = (R)beta * fma((R)s.dt, Rv, hv);
-    if (alpha != 0.0) o = fma((R)alpha, base[g], o);
-    out[g] = o;
 }
 
 // ---------------------------------------------------------------------------
@@ -697,7 +785,7 @@ Taps2 taps_2d(const evfdlb_params& p) {
 
 bool validate_2d(const evfdlb_params& p) {
     if (p.dim != 2 || p.nx < 8 || p.ny < 8 || !(p.dx > 0) || !(p.sigma > 0) || !(p.phi_a >= 0)) return false;
-    if (p.Q < 4 || p.Q > 16 || p.bc != EVFDLB_BC_PERIODIC) return false;
+    if (p.Q < 4 || p.Q > 16 || (p.Q & 1) || p.bc != EVFDLB_BC_PERIODIC) return false;
     if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) return false;
     if (!(p.weno_eps > 0) || (!(p.dt > 0) && !(p.cfl > 0 && p.cfl <= 1))) return false;
     double g2 = (p.gamma + 2.0) / 2.0;
@@ -745,6 +833,35 @@ struct Ctx2 {
 };
 
 namespace {
+// k2_coll is compiled for each even Q of the 2D model (4 .. 16)
+template <typename R>
+void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, const R* rtab, const R* src,
+                 const R* fld, R* RL) {
+    switch (Q) {
+        case 4: k2_coll<R, 4><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 6: k2_coll<R, 6><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 8: k2_coll<R, 8><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 10: k2_coll<R, 10><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 12: k2_coll<R, 12><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 14: k2_coll<R, 14><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        default: k2_coll<R, 16><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+    }
+}
+
+template <typename R>
+cudaError_t coll_attr(int Q, size_t smem) {
+    const int v = (int)smem;
+    switch (Q) {
+        case 4: return cudaFuncSetAttribute(k2_coll<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        case 6: return cudaFuncSetAttribute(k2_coll<R, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        case 8: return cudaFuncSetAttribute(k2_coll<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        case 10: return cudaFuncSetAttribute(k2_coll<R, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        case 12: return cudaFuncSetAttribute(k2_coll<R, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        case 14: return cudaFuncSetAttribute(k2_coll<R, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        default: return cudaFuncSetAttribute(k2_coll<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    }
+}
+
 template <typename R>
 void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, void* out, double* rhs_out,
                    double alpha, double beta, int mode) {
@@ -756,9 +873,8 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
     k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->ft_off, (const R*)c->ft_g, c->fm_off, c->fm_w,
                                                    (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
-    k2_coll<R><<<nc, 256, c->smem_coll, st>>>(s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL,
-                                               nullptr);
-    dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), 2 * Q * Q);
+    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
+    dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
     k2_adv<R><<<ga, 256, 0, st>>>(s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL,
                                    rhs_out, alpha, beta, mode);
 }
@@ -868,12 +984,10 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     if (e == cudaSuccess) {
         if (c->prec == EVFDLB_FP32) {
             e = cudaFuncSetAttribute(k2_fields<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k2_coll<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_coll);
+            if (e == cudaSuccess) e = coll_attr<float>(p.Q, c->smem_coll);
         } else {
             e = cudaFuncSetAttribute(k2_fields<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k2_coll<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_coll);
+            if (e == cudaSuccess) e = coll_attr<double>(p.Q, c->smem_coll);
         }
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
