@@ -67,11 +67,21 @@ enum { EVFDLB_EV1 = 0, EVFDLB_EV2 = 1 };
  * rate 1/tau.  Both readings are selectable; 1/tau is the default. */
 enum { EVFDLB_RELAX_INV_TAU = 0, EVFDLB_RELAX_CHI_OVER_TAU = 1 };
 
-/* Problem statement of one slab (paper Sec. III: sigma = phi_a = 1, gamma = 6). */
+/* Problem statement of one slab (paper Sec. III: sigma = phi_a = 1, gamma = 6),
+ * or, with dim = 2, of one plane periodic domain of the two-dimensional
+ * tensor-product extension (the paper names 2D as future work, Sec. IV):
+ * reduced distributions over p_z on the tensor product of the order-Q
+ * Gauss-Hermite set per axis (Q even, 4..16), the Eq. (force) integral over
+ * z as the in-plane kernel summed over the grid offsets inside the r_cut
+ * disc, the Fischer-Methfessel average with chord weights, WENO-5 and
+ * fourth-order gradients along each axis; periodic only, EV1, FP32 or FP64,
+ * gamma an even integer, dt = cfl dx / (2 max|xi|) when dt <= 0.  A 2D
+ * context has nbatch = 1; evfdlb_fields, evfdlb_tune, evfdlb_rhs_vjp and the
+ * adjoint return E_UNSUPPORTED for it. */
 typedef struct {
-    int32_t dim;          /* 1 (one-dimensional slab)                                  */
-    int32_t nx;           /* grid nodes, >= 8                                          */
-    int32_t ny;           /* 1                                                         */
+    int32_t dim;          /* 1 (slab) or 2 (plane, see above)                          */
+    int32_t nx;           /* grid nodes along x, >= 8                                  */
+    int32_t ny;           /* 1 for a slab; nodes along y (>= 8) for dim = 2            */
     double  dx;           /* grid spacing; sigma/dx and r_cut/dx must be integers and  */
                           /* (r_cut - sigma)/dx even (Simpson panels end at +-sigma)   */
     double  sigma;        /* hard-sphere diameter, Eq. (sutherland)                    */
@@ -109,9 +119,10 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch,
                             evfdlb_ctx** out);
 
 /* Sets the state to the Hermite-projected Maxwellian pair (F_MB, T F_MB) of
- * the fields n0 > 0, u0, T0 > 0 ([sum nx], slab order).  Errors:
- * E_INVALID_ARG (NULL pointer), E_NONFINITE / E_NEGATIVE (checked on the
- * device), E_CUDA. */
+ * the fields n0 > 0, u0, T0 > 0 ([sum nx], slab order).  For dim = 2 the
+ * arrays are [nx * ny] (index y * nx + x), u0 is [2][nx * ny] (u_x then
+ * u_y) and the pair is (F_MB, T/2 F_MB).  Errors: E_INVALID_ARG (NULL
+ * pointer), E_NONFINITE / E_NEGATIVE (checked on the device), E_CUDA. */
 evfdlb_status evfdlb_init(evfdlb_ctx* ctx, const double* n0, const double* u0,
                           const double* T0, int32_t on_device);
 
@@ -129,14 +140,17 @@ evfdlb_status evfdlb_step_async(evfdlb_ctx* ctx, int64_t nsteps);
 /* Macroscopic fields of the current state (Sec. II.B): n, u, T and heat flux
  * q per node ([sum nx] each; any may be NULL) and, if totals != NULL, per
  * slab four totals {mass, momentum, energy incl. mean-field energy, mean-field
- * energy} ([4 * nbatch], always host memory).  Mean-field energy:
+ * energy} ([4 * nbatch], always host memory).  For dim = 2: u and q are
+ * [2][nx * ny] and the totals are {mass, momentum x, momentum y, kinetic +
+ * internal energy} (the 2D mean-field energy is not formed).  Mean-field energy:
  * (dx/2) sum_i n_i sum_j s_j [Phi(j dx) - Phi(r_cut)] n_{i+j} with Phi the even
  * potential whose derivative is the Eq. (F1) kernel and s_j Simpson weights. */
 evfdlb_status evfdlb_moments(evfdlb_ctx* ctx, double* n, double* u, double* T,
                              double* q, double* totals, int32_t on_device);
 
 /* Copies the state (F, G; [sum Q nx] each, layout above) out of / into the
- * context.  set_state also clears a latched device error. */
+ * context.  set_state also clears a latched device error.  For dim = 2 the
+ * state is [Q * Q][ny][nx] per distribution, velocity index kx * Q + ky. */
 evfdlb_status evfdlb_get_state(evfdlb_ctx* ctx, double* F, double* G, int32_t on_device);
 evfdlb_status evfdlb_set_state(evfdlb_ctx* ctx, const double* F, const double* G,
                                int32_t on_device);
