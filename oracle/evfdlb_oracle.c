@@ -63,6 +63,7 @@ typedef struct {
     const double *zq;  /* [nq] nodes of a normalised Gauss-Hermite rule     */
     const double *wq;  /* [nq] its weights, sum 1                           */
     double phi_tl;     /* complex-step build only: imaginary part of phi    */
+    int force_model;   /* 0: EV1, Eq. (F1); 1: EV2, Eq. (F2)                */
 } orc_params;
 
 /* number of per-node fields returned by orc_node_fields */
@@ -221,6 +222,41 @@ static void ev1_force(const orc_params *p, const real *n, real *force)
     }
 }
 
+static void grad4(const orc_params *p, const real *f, real *df);
+static void d3_5pt(const orc_params *p, const real *f, real *d3);
+
+/* EV2 force, Eq. (F2): F2 = 2a dn/dz + kappa d^3n/dz^3 with
+ * a = (2 pi sigma^3/3) phi gamma/(gamma-3), kappa = (2 pi sigma^5/15) phi gamma/(gamma-5);
+ * dn/dz by the fourth-order central difference and d^3n/dz^3 by the five-point
+ * stencil (Sec. III). */
+static void ev2_force(const orc_params *p, const real *n, real *force)
+{
+    double s = p->sigma, g = p->gamma;
+    double a = 2.0 * PI * s * s * s / 3.0 * p->phi * g / (g - 3.0);
+    double kappa = 2.0 * PI * pow(s, 5.0) / 15.0 * p->phi * g / (g - 5.0);
+    real *dn = (real *)malloc(p->nz * sizeof(real));
+    real *d3 = (real *)malloc(p->nz * sizeof(real));
+    grad4(p, n, dn);
+    d3_5pt(p, n, d3);
+    for (int i = 0; i < p->nz; i++) {
+        real f = 2.0 * a * dn[i] + kappa * d3[i];
+#ifdef ORC_COMPLEX
+        f = f * (1.0 + I * (p->phi_tl / p->phi));
+#endif
+        force[i] = f;
+    }
+    free(dn);
+    free(d3);
+}
+
+/* five-point third derivative: (f_{i+2} - 2 f_{i+1} + 2 f_{i-1} - f_{i-2}) / (2 dz^3) */
+static void d3_5pt(const orc_params *p, const real *f, real *d3)
+{
+    double h3 = p->dz * p->dz * p->dz;
+    for (int i = 0; i < p->nz; i++)
+        d3[i] = (f[gidx(p, i + 2)] - 2.0 * f[gidx(p, i + 1)] + 2.0 * f[gidx(p, i - 1)] - f[gidx(p, i - 2)]) / (2.0 * h3);
+}
+
 /* fourth-order central difference (Sec. III):
  * f'_i = (f_{i-2} - 8 f_{i-1} + 8 f_{i+1} - f_{i+2}) / (12 dz) */
 static void grad4(const orc_params *p, const real *f, real *df)
@@ -257,8 +293,9 @@ void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
     fm_average(p, n, nbar);
     for (int i = 0; i < nz; i++) chi[i] = ORC(chi)(p, nbar[i]);
 
-    /* self-consistent force, Eq. (F1) */
-    ev1_force(p, n, force);
+    /* self-consistent force, Eq. (F1) or Eq. (F2) */
+    if (p->force_model == 1) ev2_force(p, n, force);
+    else ev1_force(p, n, force);
 
     /* gradients entering J1, Eq. (J1) */
     for (int i = 0; i < nz; i++) X[i] = n[i] * n[i] * chi[i] * T[i];
@@ -589,11 +626,24 @@ void orc_totals(const orc_params *p, const double *F, const double *G, double *o
         }
         mass += n[i];
     }
-    for (int i = 0; i < nz; i++) {
-        double acc = 0.0;
-        for (int j = -M; j <= M; j++)
-            acc += simpson_w(j, M, p->dz) * (orc_force_potential(p, j * p->dz) - phiR) * n[gidx(p, i + j)];
-        emf += 0.5 * n[i] * acc;
+    if (p->force_model == 1) {
+        /* EV2: the field psi = -2a n - kappa d2n/dz2 has -dpsi/dz = F2 of Eq. (F2);
+         * E_mf = sum dz (1/2) n psi with the fourth-order second difference */
+        double s = p->sigma, g = p->gamma;
+        double a = 2.0 * PI * s * s * s / 3.0 * p->phi * g / (g - 3.0);
+        double kappa = 2.0 * PI * pow(s, 5.0) / 15.0 * p->phi * g / (g - 5.0);
+        for (int i = 0; i < nz; i++) {
+            double d2 = (-n[gidx(p, i - 2)] + 16.0 * n[gidx(p, i - 1)] - 30.0 * n[i] + 16.0 * n[gidx(p, i + 1)]
+                         - n[gidx(p, i + 2)]) / (12.0 * p->dz * p->dz);
+            emf += 0.5 * n[i] * (-2.0 * a * n[i] - kappa * d2);
+        }
+    } else {
+        for (int i = 0; i < nz; i++) {
+            double acc = 0.0;
+            for (int j = -M; j <= M; j++)
+                acc += simpson_w(j, M, p->dz) * (orc_force_potential(p, j * p->dz) - phiR) * n[gidx(p, i + j)];
+            emf += 0.5 * n[i] * acc;
+        }
     }
     out[0] = mass * p->dz;
     out[1] = mom * p->dz;
@@ -606,6 +656,8 @@ void orc_totals(const orc_params *p, const double *F, const double *G, double *o
  * density the Simpson force of Eq. (F1) is exactly 2 a_d dn/dz. */
 double orc_discrete_a(const orc_params *p)
 {
+    if (p->force_model == 1)   /* EV2: the printed a of Eq. (F2) */
+        return 2.0 * PI * p->sigma * p->sigma * p->sigma / 3.0 * p->phi * p->gamma / (p->gamma - 3.0);
     int M = (int)lround(p->rcut / p->dz);
     double acc = 0.0;
     for (int j = -M; j <= M; j++)
