@@ -60,6 +60,13 @@ typedef enum {
 
 enum { EVFDLB_BC_PERIODIC = 0, EVFDLB_BC_OUTFLOW = 1 };
 enum { EVFDLB_FP64 = 0, EVFDLB_FP32 = 1 };
+/* Force model (Sec. II.A).  EV1: the convolution of Eq. (F1), Simpson taps
+ * over |z| <= r_cut.  EV2: its gradient expansion, Eq. (F2),
+ * F2 = 2a dn/dz + kappa d3n/dz3 with a = (2 pi sigma^3/3) phi_a gamma/(gamma-3)
+ * and kappa = (2 pi sigma^5/15) phi_a gamma/(gamma-5); dn/dz by the
+ * fourth-order central difference and d3n/dz3 by the five-point stencil
+ * (-1, 2, 0, -2, 1)/(2 dx^3) (Sec. III).  EV2 ignores r_cut and needs
+ * gamma > 5; dim = 2 is EV1 only. */
 enum { EVFDLB_EV1 = 0, EVFDLB_EV2 = 1 };
 /* Relaxation rate of the Shakhov term J0 (Sec. II.B).  The paper writes
  * J0 = -(chi/tau)(f - f^S) with tau of Eq. (tau); the Chapman-Enskog
@@ -82,18 +89,18 @@ typedef struct {
     int32_t dim;          /* 1 (slab) or 2 (plane, see above)                          */
     int32_t nx;           /* grid nodes along x, >= 8                                  */
     int32_t ny;           /* 1 for a slab; nodes along y (>= 8) for dim = 2            */
-    double  dx;           /* grid spacing; sigma/dx and r_cut/dx must be integers and  */
-                          /* (r_cut - sigma)/dx even (Simpson panels end at +-sigma)   */
+    double  dx;           /* grid spacing; sigma/dx and (EV1) r_cut/dx must be integers*/
+                          /* and (r_cut - sigma)/dx even (Simpson panels end at sigma) */
     double  sigma;        /* hard-sphere diameter, Eq. (sutherland)                    */
     double  phi_a;        /* depth of the attractive tail, Eq. (sutherland)            */
     double  gamma;        /* tail exponent (> 3), Eq. (sutherland)                     */
-    double  r_cut;        /* truncation radius of the Eq. (F1) integral (>= sigma + 2dx)*/
+    double  r_cut;        /* EV1: cut of the Eq. (F1) integral (>= sigma + 2dx)        */
     int32_t Q;            /* Gauss-Hermite order, 4 <= Q <= 32                         */
     int32_t bc;           /* EVFDLB_BC_PERIODIC or EVFDLB_BC_OUTFLOW                   */
     int32_t precision;    /* EVFDLB_FP64, or EVFDLB_FP32: FP32 state and per-velocity  */
                           /* work, FP64 chi / transport / gradients / conserved sums;  */
                           /* one precision per context (the ABI stays float64)         */
-    int32_t force_model;  /* EVFDLB_EV1 (EV2 reserved: returns E_UNSUPPORTED)          */
+    int32_t force_model;  /* EVFDLB_EV1 or EVFDLB_EV2 (see above)                      */
     int32_t relax_mode;   /* EVFDLB_RELAX_INV_TAU or EVFDLB_RELAX_CHI_OVER_TAU         */
     double  dt;           /* > 0: time step; <= 0: dt = cfl * dx / max|xi_k|           */
     double  cfl;          /* used when dt <= 0; 0 < cfl <= 1                           */
@@ -143,8 +150,10 @@ evfdlb_status evfdlb_step_async(evfdlb_ctx* ctx, int64_t nsteps);
  * energy} ([4 * nbatch], always host memory).  For dim = 2: u and q are
  * [2][nx * ny] and the totals are {mass, momentum x, momentum y, kinetic +
  * internal energy} (the 2D mean-field energy is not formed).  Mean-field energy:
- * (dx/2) sum_i n_i sum_j s_j [Phi(j dx) - Phi(r_cut)] n_{i+j} with Phi the even
- * potential whose derivative is the Eq. (F1) kernel and s_j Simpson weights. */
+ * EV1: (dx/2) sum_i n_i sum_j s_j [Phi(j dx) - Phi(r_cut)] n_{i+j} with Phi the
+ * even potential whose derivative is the Eq. (F1) kernel and s_j Simpson
+ * weights; EV2: (dx/2) sum_i n_i psi_i with psi = -2a n - kappa d2n/dz2 (the
+ * fourth-order second difference), whose -dpsi/dz is F2. */
 evfdlb_status evfdlb_moments(evfdlb_ctx* ctx, double* n, double* u, double* T,
                              double* q, double* totals, int32_t on_device);
 
@@ -192,7 +201,7 @@ int32_t evfdlb_tile_nodes(const evfdlb_ctx* ctx);
  * cudaMalloc / cudaFree may synchronise the device and take unbounded time.
  *
  * Advances the slab described by *p (validated as for evfdlb_create; FP64,
- * EV1) by nsteps Shu-Osher RK3 steps, in place.  state is a DEVICE pointer to
+ * EV1 or EV2) by nsteps Shu-Osher RK3 steps, in place.  state is a DEVICE pointer to
  * 2 * Q * nx doubles: F (velocity-major, [k * nx + i]) followed by G, owned
  * by the caller.  All working memory (the two intermediate stages, moment
  * sums, velocity tables, taps, work list and error word) lives in one
@@ -200,7 +209,8 @@ int32_t evfdlb_tile_nodes(const evfdlb_ctx* ctx);
  * library holds until the process exits; no cudaMalloc, cudaFree or other
  * allocating routine is called.
  * Limits: nx <= EVFDLB_STATIC_MAX_NODES, Q * nx <= EVFDLB_STATIC_MAX_ELEMENTS,
- * r_cut / dx <= EVFDLB_STATIC_MAX_HALFWIDTH; larger requests return
+ * force tap half-width (EV1: r_cut / dx; EV2: sigma / dx + 2)
+ * <= EVFDLB_STATIC_MAX_HALFWIDTH; larger requests return
  * EVFDLB_E_INVALID_ARG before any CUDA call.
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and raises the stage
@@ -228,6 +238,7 @@ const char* evfdlb_status_string(evfdlb_status s);
 /* Host-side model constants (no GPU needed).
  *  evfdlb_discrete_a: a_d = (1/2) sum_j s_j (j dx) g(j dx), the constant the
  *    Simpson-integrated Eq. (F1) force gives for a linear density (F1 = 2 a_d dn/dz);
+ *    for EV2 the a of Eq. (F2), which its stencils reproduce on a linear density;
  *  evfdlb_critical_T: critical temperature of Eq. (EOSS) with a = a_d
  *    (Carnahan-Starling repulsion, mean-field attraction);
  *  evfdlb_coexistence: Maxwell construction (Sec. III.A) at temperature T:

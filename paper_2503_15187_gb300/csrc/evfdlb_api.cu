@@ -347,7 +347,6 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         if (!validate(ps[s], nullptr)) return EVFDLB_E_INVALID_ARG;
         if (ps[s].precision != EVFDLB_FP64 && ps[s].precision != EVFDLB_FP32) return EVFDLB_E_INVALID_ARG;
         if (ps[s].precision != ps[0].precision) return EVFDLB_E_INVALID_ARG;   // one precision per context
-        if (ps[s].force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
     }
     evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
     if (!c) return EVFDLB_E_OOM;
@@ -386,7 +385,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         d.Q = q.Q;
         d.bc = q.bc;
         d.relax = q.relax_mode;
-        d.M = tap_halfwidth(q.r_cut, q.dx);
+        d.M = force_halfwidth(q);
         d.m = tap_halfwidth(q.sigma, q.dx);
         d.tab_off = tab_off[q.Q];
         d.tap_off = (int)taps.size();

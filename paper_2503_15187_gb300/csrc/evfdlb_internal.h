@@ -70,7 +70,11 @@ bool velocity_set(int Q, double* xi, double* w);                 // ascending, s
 void build_tables(int Q, const double* xi, const double* w, double* out);  // TableLayout(Q)
 bool validate(const evfdlb_params& p, const char** why);
 int tap_halfwidth(double len, double dx);                        // len/dx if integral, else -1
+int force_halfwidth(const evfdlb_params& p);                     // force/energy taps and density halo
+int fill_taps(const evfdlb_params& p, double* out, int cap);     // force, fm, energy; no heap
 void build_taps(const evfdlb_params& p, std::vector<double>& out);  // force, fm, energy
+double ev2_a(const evfdlb_params& p);                            // Eq. (F2) a
+double ev2_kappa(const evfdlb_params& p);                        // Eq. (F2) kappa
 double discrete_a(const evfdlb_params& p);
 double critical_T_of_a(double a, double sigma, double* n_c);
 bool coexistence_of(double a, double sigma, double T, double* nv, double* nl);

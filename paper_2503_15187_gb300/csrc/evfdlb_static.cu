@@ -41,7 +41,7 @@ namespace {
 // Limits of the static working memory.
 constexpr long long kMaxElems = EVFDLB_STATIC_MAX_ELEMENTS;  // Q * nx
 constexpr int kMaxNodes = EVFDLB_STATIC_MAX_NODES;           // nx
-constexpr int kMaxHalfWidth = EVFDLB_STATIC_MAX_HALFWIDTH;   // r_cut / dx
+constexpr int kMaxHalfWidth = EVFDLB_STATIC_MAX_HALFWIDTH;   // force tap half-width
 constexpr int kMaxTaps = 3 * (2 * kMaxHalfWidth + 1);         // force, FM (m <= M), energy
 constexpr int kTableDoubles = 7 * kQMax + 2 * kQMax * kQMax; // TableLayout(32).total
 constexpr int kDescDoubles = (sizeof(SlabDesc) + 7) / 8;
@@ -73,39 +73,6 @@ WorkItem h_items[kMaxNodes];
 
 evfdlb_status st_of(cudaError_t e) {
     return e == cudaSuccess ? EVFDLB_OK : (e == cudaErrorMemoryAllocation ? EVFDLB_E_OOM : EVFDLB_E_CUDA);
-}
-
-double simpson_weight(int j, int M, double dx) {
-    int t = j + M;
-    double c = (t == 0 || t == 2 * M) ? 1.0 : ((t & 1) ? 4.0 : 2.0);
-    return c * dx / 3.0;
-}
-
-// Taps of one slab without heap use: force 2M+1, Fischer-Methfessel 2m+1,
-// energy 2M+1 (the same quantities the context path uploads).
-int fill_taps(const evfdlb_params& p, double* out, int cap) {
-    int M = tap_halfwidth(p.r_cut, p.dx), m = tap_halfwidth(p.sigma, p.dx);
-    int need = 2 * (2 * M + 1) + 2 * m + 1;
-    if (need > cap) return -1;
-    const double pi = M_PI, s = p.sigma, g = p.gamma, phi = p.phi_a;
-    auto kern = [&](double z) {
-        double az = fabs(z);
-        return az < s ? 2.0 * pi * phi * z : 2.0 * pi * phi * pow(s / az, g) * z;
-    };
-    auto pot = [&](double z) {
-        double az = fabs(z);
-        return az < s ? pi * phi * (z * z - s * s * g / (g - 2.0))
-                      : -2.0 * pi * phi * s * s * pow(s / az, g - 2.0) / (g - 2.0);
-    };
-    int o = 0;
-    for (int j = -M; j <= M; ++j) out[o++] = simpson_weight(j, M, p.dx) * kern(j * p.dx);
-    for (int j = -m; j <= m; ++j) {
-        double z = j * p.dx;
-        out[o++] = 3.0 / (4.0 * s * s * s) * simpson_weight(j, m, p.dx) * (s * s - z * z);
-    }
-    double phiR = pot(p.r_cut);
-    for (int j = -M; j <= M; ++j) out[o++] = simpson_weight(j, M, p.dx) * (pot(j * p.dx) - phiR);
-    return o;
 }
 
 // Velocity set of order Q <= 32 with fixed-size storage: Sturm-count
@@ -153,9 +120,9 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
                                             void* cuda_stream) {
     if (!p || !state || nsteps < 0) return EVFDLB_E_INVALID_ARG;
     if (!validate(*p, nullptr)) return EVFDLB_E_INVALID_ARG;
-    if (p->precision != EVFDLB_FP64 || p->force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
+    if (p->precision != EVFDLB_FP64) return EVFDLB_E_UNSUPPORTED;
     if (p->nx > kMaxNodes || (long long)p->Q * p->nx > kMaxElems) return EVFDLB_E_INVALID_ARG;
-    const int M = tap_halfwidth(p->r_cut, p->dx);
+    const int M = force_halfwidth(*p);
     if (M > kMaxHalfWidth) return EVFDLB_E_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)cuda_stream;
 

@@ -112,10 +112,13 @@ bool validate(const evfdlb_params& p, const char** why) {
     else if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) w = "bad relax_mode";
     else if (!(p.weno_eps > 0)) w = "weno_eps must be > 0";
     else if (!(p.dt > 0) && !(p.cfl > 0 && p.cfl <= 1)) w = "need dt > 0 or 0 < cfl <= 1";
+    else if (p.force_model != EVFDLB_EV1 && p.force_model != EVFDLB_EV2) w = "bad force_model";
+    else if (p.force_model == EVFDLB_EV2 && !(p.gamma > 5)) w = "EV2 needs gamma > 5 (kappa of Eq. (F2))";
     else {
         int m = tap_halfwidth(p.sigma, p.dx);
         int M = tap_halfwidth(p.r_cut, p.dx);
         if (m < 1) w = "sigma/dx must be a positive integer";
+        else if (p.force_model == EVFDLB_EV2) w = nullptr;      // r_cut unused
         else if (M < 1) w = "r_cut/dx must be a positive integer";
         else if (M < m + 2) w = "r_cut must be >= sigma + 2 dx";
         else if ((M - m) % 2) w = "(r_cut - sigma)/dx must be even (Simpson panels end at +-sigma)";
@@ -144,26 +147,87 @@ double g_potential(double z, double s, double phi, double gam) {
 }
 }  // namespace
 
-// Taps of one slab: [force 2M+1 | Fischer-Methfessel 2m+1 | energy 2M+1].
-//  force_j  = s_j g(j dx)                                (Eq. (F1), Simpson 1/3)
+// Half-width of the force and energy tap blocks, which is also the density
+// halo a node tile stages.  EV1: r_cut/dx (the Simpson range of Eq. (F1)).
+// EV2: sigma/dx + 2, the halo the Fischer-Methfessel average of the +-2
+// gradient neighbours needs; the EV2 stencils reach +-2 and the taps beyond
+// are zero.
+int force_halfwidth(const evfdlb_params& p) {
+    int m = tap_halfwidth(p.sigma, p.dx);
+    if (p.force_model == EVFDLB_EV2) return m < 1 ? -1 : m + 2;
+    return tap_halfwidth(p.r_cut, p.dx);
+}
+
+// Taps of one slab: [force 2M+1 | Fischer-Methfessel 2m+1 | energy 2M+1],
+// M = force_halfwidth.  Without heap use; returns the count, or -1 when it
+// exceeds cap.
 //  fm_j     = 3/(4 sigma^3) s_j (sigma^2 - (j dx)^2)     (sphere average, Sec. II.A)
+// EV1, Eq. (F1) with Simpson 1/3 weights s_j:
+//  force_j  = s_j g(j dx)
 //  energy_j = s_j [Phi(j dx) - Phi(r_cut)]               (mean-field energy)
-void build_taps(const evfdlb_params& p, std::vector<double>& out) {
-    int M = tap_halfwidth(p.r_cut, p.dx), m = tap_halfwidth(p.sigma, p.dx);
-    out.clear();
-    for (int j = -M; j <= M; ++j)
-        out.push_back(simpson(j, M, p.dx) * g_kernel(j * p.dx, p.sigma, p.phi_a, p.gamma));
+// EV2, Eq. (F2): F2 = 2a dn/dz + kappa d3n/dz3 with the fourth-order first
+// difference (1, -8, 0, 8, -1)/(12 dx) and the five-point third difference
+// (-1, 2, 0, -2, 1)/(2 dx^3), merged into one antisymmetric stencil:
+//  force_{+-1} = +-(16a/(12 dx) - kappa/dx^3),  force_{+-2} = +-(-2a/(12 dx) + kappa/(2 dx^3))
+// and the energy field psi = -2a n - kappa d2n/dz2 (fourth-order second
+// difference (-1, 16, -30, 16, -1)/(12 dx^2)), whose -dpsi/dz is F2:
+//  energy_0 = -2a + 30 kappa/(12 dx^2), energy_{+-1} = -16 kappa/(12 dx^2),
+//  energy_{+-2} = kappa/(12 dx^2)
+int fill_taps(const evfdlb_params& p, double* out, int cap) {
+    int M = force_halfwidth(p), m = tap_halfwidth(p.sigma, p.dx);
+    if (M < 1 || m < 1) return -1;
+    int need = 2 * (2 * M + 1) + 2 * m + 1;
+    if (need > cap) return -1;
+    double* force = out;
+    double* fm = out + 2 * M + 1;
+    double* energy = fm + 2 * m + 1;
     double s3 = p.sigma * p.sigma * p.sigma;
     for (int j = -m; j <= m; ++j) {
         double z = j * p.dx;
-        out.push_back(3.0 / (4.0 * s3) * simpson(j, m, p.dx) * (p.sigma * p.sigma - z * z));
+        fm[j + m] = 3.0 / (4.0 * s3) * simpson(j, m, p.dx) * (p.sigma * p.sigma - z * z);
     }
+    if (p.force_model == EVFDLB_EV2) {
+        double a = ev2_a(p), kappa = ev2_kappa(p), h = p.dx;
+        for (int j = 0; j < 2 * M + 1; ++j) force[j] = energy[j] = 0.0;
+        double t1 = 16.0 * a / (12.0 * h) - kappa / (h * h * h);
+        double t2 = -2.0 * a / (12.0 * h) + kappa / (2.0 * h * h * h);
+        force[M + 1] = t1;
+        force[M - 1] = -t1;
+        force[M + 2] = t2;
+        force[M - 2] = -t2;
+        double k12 = kappa / (12.0 * h * h);
+        energy[M] = -2.0 * a + 30.0 * k12;
+        energy[M + 1] = energy[M - 1] = -16.0 * k12;
+        energy[M + 2] = energy[M - 2] = k12;
+        return need;
+    }
+    for (int j = -M; j <= M; ++j) force[j + M] = simpson(j, M, p.dx) * g_kernel(j * p.dx, p.sigma, p.phi_a, p.gamma);
     double phiR = g_potential(p.r_cut, p.sigma, p.phi_a, p.gamma);
     for (int j = -M; j <= M; ++j)
-        out.push_back(simpson(j, M, p.dx) * (g_potential(j * p.dx, p.sigma, p.phi_a, p.gamma) - phiR));
+        energy[j + M] = simpson(j, M, p.dx) * (g_potential(j * p.dx, p.sigma, p.phi_a, p.gamma) - phiR);
+    return need;
+}
+
+void build_taps(const evfdlb_params& p, std::vector<double>& out) {
+    int M = force_halfwidth(p), m = tap_halfwidth(p.sigma, p.dx);
+    out.assign(M < 1 || m < 1 ? 0 : 2 * (2 * M + 1) + 2 * m + 1, 0.0);
+    if (!out.empty()) fill_taps(p, out.data(), (int)out.size());
+}
+
+// Eq. (F2) constants: a = (2 pi sigma^3/3) phi gamma/(gamma-3) and
+// kappa = (2 pi sigma^5/15) phi gamma/(gamma-5), the first and third moments
+// (2a = int s g, 6 kappa = int s^3 g) of the Eq. (F1) plane kernel g.
+double ev2_a(const evfdlb_params& p) {
+    double s = p.sigma;
+    return 2.0 * kPi * s * s * s / 3.0 * p.phi_a * p.gamma / (p.gamma - 3.0);
+}
+double ev2_kappa(const evfdlb_params& p) {
+    double s = p.sigma;
+    return 2.0 * kPi * s * s * s * s * s / 15.0 * p.phi_a * p.gamma / (p.gamma - 5.0);
 }
 
 double discrete_a(const evfdlb_params& p) {
+    if (p.force_model == EVFDLB_EV2) return ev2_a(p);
     int M = tap_halfwidth(p.r_cut, p.dx);
     if (M < 1) return NAN;
     long double acc = 0;

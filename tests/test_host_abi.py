@@ -85,3 +85,24 @@ def test_invalid_params_rejected(L):
         kw.update(bad)
         p = ev.Params(**kw)
         assert math.isnan(ev.critical_T(p)), bad
+
+
+@pytest.mark.parametrize("dx", [0.25, 0.1])
+def test_ev2_constants_match_oracle(L, dx):
+    """EV2 reports the printed a of Eq. (F2); the critical point and the
+    coexistence densities follow from it."""
+    p = ev.Params(nx=64, dx=dx, force_model=ev.EV2, r_cut=5.3)   # r_cut is not used by EV2
+    orc = O.Oracle(O.Setup(nz=64, Q=8, dz=dx, dt=0.01, force_model=1))
+    assert abs(ev.discrete_a(p) - orc.discrete_a()) < 1e-15 * orc.discrete_a()
+    assert abs(ev.critical_T(p) - orc.critical_T()) < 1e-12
+    T = 0.8 * ev.critical_T(p)
+    nv, nl = ev.coexistence(p, T)
+    nvo, nlo = O.coexistence(T, orc.discrete_a())
+    assert abs(nv - nvo) < 1e-9 * nvo and abs(nl - nlo) < 1e-9 * nlo
+
+
+def test_ev2_invalid_params_rejected(L):
+    for bad in (dict(gamma=5.0), dict(gamma=4.5), dict(dx=0.3), dict(force_model=2)):
+        kw = dict(nx=64, dx=0.25, force_model=ev.EV2)
+        kw.update(bad)
+        assert math.isnan(ev.critical_T(ev.Params(**kw))), bad

@@ -32,7 +32,8 @@ def test_oversize_requests_rejected_before_any_cuda_call():
     dummy = ctypes.c_void_p(16)          # never dereferenced: the call returns first
     for kw in (dict(nx=8193, dx=0.25, Q=4),              # nx > EVFDLB_STATIC_MAX_NODES
                dict(nx=4096, dx=0.25, Q=17),             # Q * nx > EVFDLB_STATIC_MAX_ELEMENTS
-               dict(nx=4096, dx=0.01, Q=8, r_cut=6.0)):  # r_cut / dx > EVFDLB_STATIC_MAX_HALFWIDTH
+               dict(nx=4096, dx=0.01, Q=8, r_cut=6.0),   # r_cut / dx > EVFDLB_STATIC_MAX_HALFWIDTH
+               dict(nx=4096, dx=0.001, Q=8, force_model=ev.EV2)):  # sigma / dx + 2 > the same limit
         p = ev.Params(**kw)
         assert L.evfdlb_step_static(ctypes.byref(p.c()), dummy, 1, None) == -1, kw
     p = ev.Params(nx=64, dx=0.25)
@@ -41,14 +42,15 @@ def test_oversize_requests_rejected_before_any_cuda_call():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", [(97, 24, 0.25, ev.BC_OUTFLOW), (150, 32, 0.1, ev.BC_PERIODIC)])
+@pytest.mark.parametrize("case", [(97, 24, 0.25, ev.BC_OUTFLOW, ev.EV1), (150, 32, 0.1, ev.BC_PERIODIC, ev.EV1),
+                                  (97, 24, 0.25, ev.BC_OUTFLOW, ev.EV2)])
 def test_static_step_matches_context_step_twice(case):
     import torch
-    nz, Q, dz, bc = case
+    nz, Q, dz, bc, fm = case
     torch.cuda.set_device(0)
-    p = ev.Params(nx=nz, dx=dz, Q=Q, bc=bc)
+    p = ev.Params(nx=nz, dx=dz, Q=Q, bc=bc, force_model=fm)
     sim = ev.Sim(p)
-    orc = O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=sim.dt(), bc=bc))
+    orc = O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=sim.dt(), bc=bc, force_model=fm))
     T = 0.8 * orc.critical_T()
     nv, nl = O.coexistence(T, orc.discrete_a())
     n0 = W.liquid_slab(nz, dz, nl, nv, thickness=0.35 * nz * dz, width=2.0)
