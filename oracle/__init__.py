@@ -118,7 +118,8 @@ class _Params(ctypes.Structure):
                 ("rcut", ctypes.c_double), ("bc", ctypes.c_int), ("relax", ctypes.c_int),
                 ("weno_eps", ctypes.c_double), ("xi", ctypes.c_void_p),
                 ("w", ctypes.c_void_p), ("nq", ctypes.c_int), ("zq", ctypes.c_void_p),
-                ("wq", ctypes.c_void_p), ("phi_tl", ctypes.c_double), ("force_model", ctypes.c_int)]
+                ("wq", ctypes.c_void_p), ("phi_tl", ctypes.c_double), ("force_model", ctypes.c_int),
+                ("T_iso", ctypes.c_double)]
 
 
 class _Params2(ctypes.Structure):
@@ -251,6 +252,7 @@ class Setup:
     weno_eps: float = 1e-6
     nq: int = 64           # points of the projection rule
     force_model: int = 0   # 0: EV1, Eq. (F1); 1: EV2, Eq. (F2)
+    T_iso: float = 0.0     # > 0: isothermal mode at this temperature
 
 
 class Oracle:
@@ -265,7 +267,8 @@ class Oracle:
         self._p = _Params(setup.nz, setup.Q, setup.dz, setup.dt, setup.sigma, setup.phi,
                           setup.gamma, setup.rcut, setup.bc, setup.relax, setup.weno_eps,
                           self.xi.ctypes.data, self.w.ctypes.data, setup.nq,
-                          self.zq.ctypes.data, self.wq.ctypes.data, 0.0, setup.force_model)
+                          self.zq.ctypes.data, self.wq.ctypes.data, 0.0, setup.force_model,
+                          setup.T_iso)
         self.p = ctypes.byref(self._p)
 
     # scalar kernels -------------------------------------------------------

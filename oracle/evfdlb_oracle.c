@@ -64,6 +64,7 @@ typedef struct {
     const double *wq;  /* [nq] its weights, sum 1                           */
     double phi_tl;     /* complex-step build only: imaginary part of phi    */
     int force_model;   /* 0: EV1, Eq. (F1); 1: EV2, Eq. (F2)                */
+    double T_iso;      /* > 0: isothermal mode at this temperature; 0: off  */
 } orc_params;
 
 /* number of per-node fields returned by orc_node_fields */
@@ -273,11 +274,22 @@ static void grad4(const orc_params *p, const real *f, real *df)
  * 11 A = d ln(n^2 chi T)/dz   12 B = d ln T/dz   13 D = du/dz
  * 14 X = n^2 chi T            15 b n chi
  * READING (gradients): A = D4(X)/X and B = D4(T)/T, the logarithmic
- * derivatives of Eq. (J1) taken as derivative over value. */
+ * derivatives of Eq. (J1) taken as derivative over value.
+ * READING (isothermal mode, Sec. III.A keeps T constant without saying how):
+ * with T_iso > 0 every node field is formed at T = T_iso instead of the
+ * kinetic temperature of the state, so the Shakhov equilibrium, J1 and the
+ * transport coefficients hold the fluid at T_iso through the collisions
+ * (B = 0, A = d ln(n^2 chi)/dz). */
 void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
                       const real *T, const real *q, real *out)
 {
     int nz = p->nz;
+    real *Tiso = NULL;
+    if (p->T_iso > 0.0) {
+        Tiso = (real *)malloc(nz * sizeof(real));
+        for (int i = 0; i < nz; i++) Tiso[i] = p->T_iso;
+        T = Tiso;
+    }
     real *nbar = out + 4 * nz, *chi = out + 5 * nz, *force = out + 6 * nz;
     real *mu = out + 7 * nz, *tau = out + 8 * nz, *Pr = out + 9 * nz;
     real *rate = out + 10 * nz, *A = out + 11 * nz, *B = out + 12 * nz;
@@ -325,6 +337,7 @@ void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
         rate[i] = (p->relax == 0) ? 1.0 / tau[i] : chi[i] / tau[i];
         bnchi[i] = x;
     }
+    free(Tiso);
 }
 
 /* ------------------------------------------------------------------ */
@@ -536,6 +549,7 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     const real *force = fl + 6 * nz, *Pr = fl + 9 * nz, *rate = fl + 10 * nz;
     const real *A = fl + 11 * nz, *B = fl + 12 * nz, *D = fl + 13 * nz;
     const real *bnchi = fl + 15 * nz;
+    const real *Tf = fl + 2 * nz;   /* the temperature the node fields were formed at */
 
     /* free streaming term */
     for (int k = 0; k < Q; k++) {
@@ -544,7 +558,7 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     }
     /* force, collision and J1 terms, node by node */
     for (int i = 0; i < nz; i++) {
-        ORC(equilibria_node)(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
+        ORC(equilibria_node)(p, n[i], u[i], Tf[i], q[i], Pr[i], bnchi[i],
                              A[i], B[i], D[i], FS, GS, JF, JG);
         for (int k = 0; k < Q; k++) hk[k] = F[k * nz + i];
         ORC(dxi)(p, hk, dh);
