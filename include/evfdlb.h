@@ -106,10 +106,17 @@ typedef struct {
     double  cfl;          /* used when dt <= 0; 0 < cfl <= 1                           */
     int32_t ckpt_every;   /* checkpoint interval of the adjoint (reserved; 0 = none)   */
     double  weno_eps;     /* WENO-5 smoothness regulariser (> 0), e.g. 1e-6            */
+    double  T_iso;        /* 0: thermal (default).  > 0: isothermal mode -- every node */
+                          /* field (Shakhov equilibrium, J1, transport) is formed at   */
+                          /* T = T_iso instead of the state's kinetic temperature, so  */
+                          /* the collisions hold the fluid at T_iso (Sec. III.A keeps  */
+                          /* T constant; the mechanism is this library's reading).     */
+                          /* dim = 1 only; the adjoint returns E_UNSUPPORTED for it.   */
 } evfdlb_params;
 
 /* Fills p with the defaults of Sec. III: dim 1, sigma = phi_a = 1, gamma = 6,
- * r_cut = 6, Q = 16, periodic, FP64, EV1, rate 1/tau, cfl 0.5, weno_eps 1e-6.
+ * r_cut = 6, Q = 16, periodic, FP64, EV1, rate 1/tau, cfl 0.5, weno_eps 1e-6,
+ * thermal (T_iso = 0).
  * nx and dx are left for the caller (set to 0). */
 void evfdlb_default_params(evfdlb_params* p);
 

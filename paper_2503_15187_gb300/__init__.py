@@ -46,7 +46,7 @@ class CParams(ctypes.Structure):
                 ("bc", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("force_model", ctypes.c_int32), ("relax_mode", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("cfl", ctypes.c_double), ("ckpt_every", ctypes.c_int32),
-                ("weno_eps", ctypes.c_double)]
+                ("weno_eps", ctypes.c_double), ("T_iso", ctypes.c_double)]
 
 
 @dataclass
@@ -69,6 +69,7 @@ class Params:
     weno_eps: float = 1e-6
     dim: int = 1
     ny: int = 1
+    T_iso: float = 0.0     # > 0: isothermal mode at this temperature
 
     def c(self) -> CParams:
         return CParams(**{f.name: getattr(self, f.name) for f in dc_fields(self)})

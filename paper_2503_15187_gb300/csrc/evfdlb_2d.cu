@@ -918,7 +918,7 @@ void destroy_2d(Ctx2* c) {
 evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     *out = nullptr;
     if (!validate_2d(p)) return EVFDLB_E_INVALID_ARG;
-    if (p.force_model != EVFDLB_EV1) return EVFDLB_E_UNSUPPORTED;
+    if (p.force_model != EVFDLB_EV1 || p.T_iso != 0.0) return EVFDLB_E_UNSUPPORTED;
     Ctx2* c = new (std::nothrow) Ctx2();
     if (!c) return EVFDLB_E_OOM;
     c->p = p;

@@ -236,6 +236,7 @@ evfdlb_status adjoint_supported(evfdlb_ctx* c) {
     if (c->prec != EVFDLB_FP64) return EVFDLB_E_UNSUPPORTED;
     for (auto& q : c->params) {
         if (q.bc != EVFDLB_BC_PERIODIC) return EVFDLB_E_UNSUPPORTED;
+        if (q.T_iso > 0.0) return EVFDLB_E_UNSUPPORTED;       // T does not follow the state
         if (!(q.phi_a != 0.0)) return EVFDLB_E_UNSUPPORTED;   // the phi gradient divides by phi_a
     }
     return EVFDLB_OK;
@@ -401,6 +402,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         d.b = 2.0 * M_PI * q.sigma * q.sigma * q.sigma / 3.0;
         d.eta_coef = M_PI * q.sigma * q.sigma * q.sigma / 6.0;
         d.mu0_coef = 5.0 / (16.0 * q.sigma * q.sigma * sqrt(M_PI));
+        d.T_iso = q.T_iso;
         NF += (long long)q.Q * q.nx;
         NN += q.nx;
         Qmax = std::max(Qmax, q.Q);

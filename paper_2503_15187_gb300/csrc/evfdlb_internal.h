@@ -58,6 +58,7 @@ struct SlabDesc {
     double b;            // 2 pi sigma^3 / 3, Eq. (carnstar)
     double eta_coef;     // pi sigma^3 / 6
     double mu0_coef;     // 5 / (16 sigma^2 sqrt(pi)), Eq. (viscosity)
+    double T_iso;        // > 0: node fields formed at this temperature (isothermal mode)
 };
 
 // One CTA's share of work: nodes [i0, i0 + nz) of slab `slab`.

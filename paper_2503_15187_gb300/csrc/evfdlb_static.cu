@@ -175,6 +175,7 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
     h_desc.weno_eps = p->weno_eps;
     h_desc.b = 2.0 * M_PI * p->sigma * p->sigma * p->sigma / 3.0;
     h_desc.eta_coef = M_PI * p->sigma * p->sigma * p->sigma / 6.0;
+    h_desc.T_iso = p->T_iso;
     h_desc.mu0_coef = 5.0 / (16.0 * p->sigma * p->sigma * sqrt(M_PI));
     int nitems = 0;
     for (int i0 = 0; i0 < p->nx; i0 += Z) h_items[nitems++] = WorkItem{0, i0, (p->nx - i0) < Z ? p->nx - i0 : Z, 0};

@@ -111,6 +111,7 @@ bool validate(const evfdlb_params& p, const char** why) {
     else if (p.bc != EVFDLB_BC_PERIODIC && p.bc != EVFDLB_BC_OUTFLOW) w = "bad bc";
     else if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) w = "bad relax_mode";
     else if (!(p.weno_eps > 0)) w = "weno_eps must be > 0";
+    else if (!(p.T_iso >= 0) || !isfinite(p.T_iso)) w = "T_iso must be 0 (thermal) or > 0";
     else if (!(p.dt > 0) && !(p.cfl > 0 && p.cfl <= 1)) w = "need dt > 0 or 0 < cfl <= 1";
     else if (p.force_model != EVFDLB_EV1 && p.force_model != EVFDLB_EV2) w = "bad force_model";
     else if (p.force_model == EVFDLB_EV2 && !(p.gamma > 5)) w = "EV2 needs gamma > 5 (kappa of Eq. (F2))";

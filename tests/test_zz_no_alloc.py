@@ -42,13 +42,17 @@ def test_oversize_requests_rejected_before_any_cuda_call():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", [(97, 24, 0.25, ev.BC_OUTFLOW, ev.EV1), (150, 32, 0.1, ev.BC_PERIODIC, ev.EV1),
-                                  (97, 24, 0.25, ev.BC_OUTFLOW, ev.EV2)])
+@pytest.mark.parametrize("case", [(97, 24, 0.25, ev.BC_OUTFLOW, ev.EV1, False),
+                                  (150, 32, 0.1, ev.BC_PERIODIC, ev.EV1, False),
+                                  (97, 24, 0.25, ev.BC_OUTFLOW, ev.EV2, False),
+                                  (64, 16, 0.25, ev.BC_PERIODIC, ev.EV1, True)])   # isothermal mode
 def test_static_step_matches_context_step_twice(case):
     import torch
-    nz, Q, dz, bc, fm = case
+    nz, Q, dz, bc, fm, iso = case
     torch.cuda.set_device(0)
     p = ev.Params(nx=nz, dx=dz, Q=Q, bc=bc, force_model=fm)
+    if iso:
+        p.T_iso = 0.75 * ev.critical_T(p)
     sim = ev.Sim(p)
     orc = O.Oracle(O.Setup(nz=nz, Q=Q, dz=dz, dt=sim.dt(), bc=bc, force_model=fm))
     T = 0.8 * orc.critical_T()
