@@ -64,7 +64,7 @@ typedef struct {
     const double *wq;  /* [nq] its weights, sum 1                           */
     double phi_tl;     /* complex-step build only: imaginary part of phi    */
     int force_model;   /* 0: EV1, Eq. (F1); 1: EV2, Eq. (F2)                */
-    double T_iso;      /* > 0: isothermal mode at this temperature; 0: off  */
+    double T_iso;      /* > 0: temperature reset to T_iso after every step  */
 } orc_params;
 
 /* number of per-node fields returned by orc_node_fields */
@@ -274,22 +274,11 @@ static void grad4(const orc_params *p, const real *f, real *df)
  * 11 A = d ln(n^2 chi T)/dz   12 B = d ln T/dz   13 D = du/dz
  * 14 X = n^2 chi T            15 b n chi
  * READING (gradients): A = D4(X)/X and B = D4(T)/T, the logarithmic
- * derivatives of Eq. (J1) taken as derivative over value.
- * READING (isothermal mode, Sec. III.A keeps T constant without saying how):
- * with T_iso > 0 every node field is formed at T = T_iso instead of the
- * kinetic temperature of the state, so the Shakhov equilibrium, J1 and the
- * transport coefficients hold the fluid at T_iso through the collisions
- * (B = 0, A = d ln(n^2 chi)/dz). */
+ * derivatives of Eq. (J1) taken as derivative over value. */
 void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
                       const real *T, const real *q, real *out)
 {
     int nz = p->nz;
-    real *Tiso = NULL;
-    if (p->T_iso > 0.0) {
-        Tiso = (real *)malloc(nz * sizeof(real));
-        for (int i = 0; i < nz; i++) Tiso[i] = p->T_iso;
-        T = Tiso;
-    }
     real *nbar = out + 4 * nz, *chi = out + 5 * nz, *force = out + 6 * nz;
     real *mu = out + 7 * nz, *tau = out + 8 * nz, *Pr = out + 9 * nz;
     real *rate = out + 10 * nz, *A = out + 11 * nz, *B = out + 12 * nz;
@@ -337,7 +326,6 @@ void ORC(node_fields)(const orc_params *p, const real *n, const real *u,
         rate[i] = (p->relax == 0) ? 1.0 / tau[i] : chi[i] / tau[i];
         bnchi[i] = x;
     }
-    free(Tiso);
 }
 
 /* ------------------------------------------------------------------ */
@@ -549,7 +537,6 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     const real *force = fl + 6 * nz, *Pr = fl + 9 * nz, *rate = fl + 10 * nz;
     const real *A = fl + 11 * nz, *B = fl + 12 * nz, *D = fl + 13 * nz;
     const real *bnchi = fl + 15 * nz;
-    const real *Tf = fl + 2 * nz;   /* the temperature the node fields were formed at */
 
     /* free streaming term */
     for (int k = 0; k < Q; k++) {
@@ -558,7 +545,7 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     }
     /* force, collision and J1 terms, node by node */
     for (int i = 0; i < nz; i++) {
-        ORC(equilibria_node)(p, n[i], u[i], Tf[i], q[i], Pr[i], bnchi[i],
+        ORC(equilibria_node)(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
                              A[i], B[i], D[i], FS, GS, JF, JG);
         for (int k = 0; k < Q; k++) hk[k] = F[k * nz + i];
         ORC(dxi)(p, hk, dh);
@@ -572,6 +559,39 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     if (fields) memcpy(fields, fl, (size_t)ORC_NFIELDS * nz * sizeof(real));
     free(n); free(u); free(T); free(q); free(fl); free(row);
     free(hk); free(dh); free(FS); free(GS); free(JF); free(JG);
+}
+
+/* ------------------------------------------------------------------ */
+/* Isothermal mode (Sec. III.A)                                        */
+/* ------------------------------------------------------------------ */
+
+/* READING: Sec. III.A keeps the fluid temperature constant without saying
+ * how.  Here, after every time step, each node's temperature is set back to
+ * T_iso while its density, velocity and non-equilibrium part are kept:
+ *   F <- F + F_MB(n, u, T_iso) - F_MB(n, u, T),
+ *   G <- G + T_iso F_MB(n, u, T_iso) - T F_MB(n, u, T),
+ * with n, u, T the moments of the state and F_MB the Hermite-projected
+ * Maxwellian (the pair the initial state uses). */
+static void isothermal_reset(const orc_params *p, real *F, real *G)
+{
+    int nz = p->nz, Q = p->Q;
+    size_t N = (size_t)Q * nz;
+    real *n = (real *)malloc(nz * sizeof(real));
+    real *u = (real *)malloc(nz * sizeof(real));
+    real *T = (real *)malloc(nz * sizeof(real));
+    real *q = (real *)malloc(nz * sizeof(real));
+    real *Ti = (real *)malloc(nz * sizeof(real));
+    real *Fa = (real *)malloc(N * sizeof(real)), *Ga = (real *)malloc(N * sizeof(real));
+    real *Fb = (real *)malloc(N * sizeof(real)), *Gb = (real *)malloc(N * sizeof(real));
+    ORC(moments)(p, F, G, n, u, T, q);
+    for (int i = 0; i < nz; i++) Ti[i] = p->T_iso;
+    ORC(equilibrium)(p, n, u, Ti, Fa, Ga);
+    ORC(equilibrium)(p, n, u, T, Fb, Gb);
+    for (size_t e = 0; e < N; e++) {
+        F[e] += Fa[e] - Fb[e];
+        G[e] += Ga[e] - Gb[e];
+    }
+    free(n); free(u); free(T); free(q); free(Ti); free(Fa); free(Ga); free(Fb); free(Gb);
 }
 
 /* ------------------------------------------------------------------ */
@@ -606,6 +626,7 @@ void ORC(step)(const orc_params *p, real *F, real *G, int nsteps)
             F[e] = F[e] / 3.0 + 2.0 / 3.0 * (F2[e] + dt * RF[e]);
             G[e] = G[e] / 3.0 + 2.0 / 3.0 * (G2[e] + dt * RG[e]);
         }
+        if (p->T_iso > 0.0) isothermal_reset(p, F, G);
     }
     free(F1); free(G1); free(F2); free(G2); free(RF); free(RG);
 }
