@@ -219,6 +219,7 @@ def run_ours(args, rank, world):
     sim.close()
     if not args.no_variants:
         legs = {"fp32": lambda: fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
+                "ev2": lambda: ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
                 "adjoint": lambda: adjoint_leg(ev, W, stream),
                 "batched": lambda: batched_leg(ev, W, stream, rank, world, maxred),
                 "two_d": lambda: two_d_leg(ev, stream, flush, maxred, world)}
@@ -256,6 +257,37 @@ def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32 (f64 chi, "
             "transport, gradients, conserved sums)", "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
+            "gpu_launches": 3 * args.steps}
+
+
+def ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
+    """The EV2 force model (Eq. (F2)) on the same slab and timing protocol, FP64:
+    the 5-point force stencil replaces the 2 r_cut/dx + 1 Simpson taps.  The
+    slab starts at the same profile and temperature and its density after the
+    same number of steps is compared with the EV1 run."""
+    import dataclasses
+    import numpy as np
+    import torch
+    p2 = dataclasses.replace(p, force_model=ev.EV2)
+    sim = ev.Sim(p2, stream=stream)
+    sim.init(n0, np.zeros(NZ), np.full(NZ, T))
+    sim.step(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        sim.step_async(1)
+        ends[i].record(stream)
+    barrier()
+    sim.step(1)
+    ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    n2 = sim.moments(with_totals=False)[0]
+    sim.close()
+    return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f64",
+            "ms_per_step": ms / args.steps, "force": "Eq. (F2), 5-point stencils",
+            "max_rel_diff_n_vs_ev1": float(np.abs(n2 - n64).max() / np.abs(n64).max()),
             "gpu_launches": 3 * args.steps}
 
 
@@ -450,7 +482,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")
-    ap.add_argument("--variants", default="", help="comma-separated subset of fp32,adjoint,batched,two_d")
+    ap.add_argument("--variants", default="", help="comma-separated subset of fp32,ev2,adjoint,batched,two_d")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -106,12 +106,14 @@ typedef struct {
     double  cfl;          /* used when dt <= 0; 0 < cfl <= 1                           */
     int32_t ckpt_every;   /* checkpoint interval of the adjoint (reserved; 0 = none)   */
     double  weno_eps;     /* WENO-5 smoothness regulariser (> 0), e.g. 1e-6            */
-    double  T_iso;        /* 0: thermal (default).  > 0: isothermal mode -- every node */
-                          /* field (Shakhov equilibrium, J1, transport) is formed at   */
-                          /* T = T_iso instead of the state's kinetic temperature, so  */
-                          /* the collisions hold the fluid at T_iso (Sec. III.A keeps  */
-                          /* T constant; the mechanism is this library's reading).     */
-                          /* dim = 1 only; the adjoint returns E_UNSUPPORTED for it.   */
+    double  T_iso;        /* 0: thermal (default).  > 0: isothermal mode -- after every */
+                          /* step each node's temperature is set back to T_iso, its    */
+                          /* density, velocity and non-equilibrium part kept:          */
+                          /* F += F_MB(n,u,T_iso) - F_MB(n,u,T), G likewise with the   */
+                          /* pair (F_MB, T F_MB) (Sec. III.A keeps T constant; the     */
+                          /* mechanism is this library's reading).  evfdlb_rhs is the  */
+                          /* thermal right-hand side.  dim = 1 only; the adjoint       */
+                          /* returns E_UNSUPPORTED for it.                             */
 } evfdlb_params;
 
 /* Fills p with the defaults of Sec. III: dim 1, sigma = phi_a = 1, gamma = 6,

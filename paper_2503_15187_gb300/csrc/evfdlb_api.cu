@@ -28,6 +28,9 @@ void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sla
 void launch_sums_p(int prec, int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                    const double* tables, const void* rtab, const void* state, double* mom, long long NF,
                    long long NN, unsigned* err);
+void launch_iso_reset_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                        const WorkItem* items, const double* tables, const void* rtab, void* state, double* mom,
+                        long long NF, long long NN, int Z);
 void launch_fields_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                      const WorkItem* items, const void* rtab, const double* taps, const void* rtaps,
                      const double* mom, double* fields, long long NN, int Z, unsigned* err);
@@ -102,6 +105,7 @@ struct evfdlb_ctx {
     size_t items_cap = 0;        // capacity of the device work list
     bool have_state = false;
     bool poisoned = false;
+    bool iso = false;            // some slab has T_iso > 0 (reset after every step)
     // adjoint: checkpoints of the trajectory since the last init / set_state
     int ckpt_every = 0;          // 0: no tracking (no adjoint)
     int64_t steps = 0;           // steps since the trajectory origin
@@ -164,6 +168,9 @@ void queue_step(evfdlb_ctx* c, cudaStream_t st) {
     stage(f0, nullptr, f1, m0, m1, 0.0, 1.0);              // u1 = u + dt L(u)
     stage(f1, f0, f2, m1, m2, 0.75, 0.25);                 // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
     stage(f2, f0, f0, m2, m0, 1.0 / 3.0, 2.0 / 3.0);       // u_new = 1/3 u + 2/3 (u2 + dt L(u2)), over u
+    if (c->iso)                                            // isothermal slabs: T back to T_iso
+        launch_iso_reset_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, f0, m0, c->NF,
+                           c->NN, c->Z);
 }
 
 // Splits every slab into node tiles of Z nodes (the last tile of a slab may
@@ -403,6 +410,7 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         d.eta_coef = M_PI * q.sigma * q.sigma * q.sigma / 6.0;
         d.mu0_coef = 5.0 / (16.0 * q.sigma * q.sigma * sqrt(M_PI));
         d.T_iso = q.T_iso;
+        if (q.T_iso > 0.0) c->iso = true;
         NF += (long long)q.Q * q.nx;
         NN += q.nx;
         Qmax = std::max(Qmax, q.Q);
@@ -675,7 +683,7 @@ evfdlb_status evfdlb_slab_info(const evfdlb_ctx* c, int32_t s, int32_t* nx, int3
     return EVFDLB_OK;
 }
 
-int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? (c->c2 ? 12 : 3) : 0; }
+int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? (c->c2 ? 12 : (c->iso ? 4 : 3)) : 0; }
 
 int32_t evfdlb_tile_nodes(const evfdlb_ctx* c) { return c ? (c->c2 ? 0 : c->Z) : 0; }
 

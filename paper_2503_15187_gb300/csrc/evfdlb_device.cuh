@@ -116,10 +116,9 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
         int i = gidx(it.i0 - 2 + t, nx, bc);
         double n = S0[i], inv_n = 1.0 / n;
         double u = S1[i] * inv_n;
-        // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2; in the
-        // isothermal mode every node field is formed at T_iso instead
+        // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2
         s.U[t] = u;
-        s.T[t] = sd.T_iso > 0.0 ? sd.T_iso : (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) * inv_n - 0.5 * u * u);
+        s.T[t] = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) * inv_n - 0.5 * u * u);
     }
 }
 

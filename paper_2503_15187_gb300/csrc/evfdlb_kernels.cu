@@ -178,6 +178,66 @@ init_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ ite
     tile_moment_sums<R>(sd, it, s, Z, tab + L.xi, rtab + sd.tab_off + L.xi, mom, NN);
 }
 
+// Isothermal mode, applied after every step to the slabs with T_iso > 0:
+// each node's temperature is set back to T_iso with its density, velocity
+// and non-equilibrium part kept,
+//   F += F_MB(n, u, T_iso) - F_MB(n, u, T),  G += T_iso F_MB(n, u, T_iso) - T F_MB(n, u, T),
+// n, u, T from the step's moment sums; F_MB is the projected Maxwellian of
+// init_kernel (Hermite coefficients n m_l).  The tile's moment sums are
+// rewritten from the updated state.  Blocks of other slabs return at once.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+iso_reset_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                 const double* __restrict__ tables, const R* __restrict__ rtab, R* state, double* mom, long long NF,
+                 long long NN, int Z) {
+    extern __shared__ double smem[];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    if (!(sd.T_iso > 0.0)) return;
+    const int Q = sd.Q, W = Z + 6, nz = it.nz;
+    Smem<R> s = carve<R>(smem, Q, Z, sd.M);
+    TableLayout L(Q);
+    const double* tab = tables + sd.tab_off;
+    // FP64 coefficient differences [2][Q][Z] in the R blocks C and A
+    double* dcoef = reinterpret_cast<double*>(s.C);
+    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
+    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
+    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
+    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
+    const double Ti = sd.T_iso;
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) {
+        int i = it.i0 + t;
+        double n = S0[i], inv_n = 1.0 / n, u = S1[i] * inv_n;
+        double T = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) * inv_n - 0.5 * u * u);
+        // m_l of N(u, T) and N(u, T_iso) by the recurrence of init_kernel
+        double a0 = 1.0, a1 = 0.0, b0 = 1.0, b1 = 0.0, Ta = Ti - 1.0, Tb = T - 1.0;
+        for (int l = 0; l < Q; ++l) {
+            dcoef[l * Z + t] = n * (a0 - b0);
+            dcoef[(Q + l) * Z + t] = n * (Ti * a0 - T * b0);
+            double an = fma(u * tab[L.rinv + l], a0, Ta * tab[L.rr + l] * a1);
+            double bn = fma(u * tab[L.rinv + l], b0, Tb * tab[L.rr + l] * b1);
+            a1 = a0;
+            a0 = an;
+            b1 = b0;
+            b0 = bn;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
+        int t = e % nz, r = e / nz;
+        int k = r % Q, d = r / Q;
+        const double* c = dcoef + (size_t)d * Q * Z;
+        double acc = 0.0;
+        for (int l = 0; l < Q; ++l) acc = fma(tab[L.S + k * Q + l], c[l * Z + t], acc);
+        long long g = (long long)d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
+        R v = (R)((double)state[g] + acc);
+        state[g] = v;
+        s.F[(size_t)(d * Q + k) * W + t + 3] = v;
+    }
+    __syncthreads();
+    tile_moment_sums<R>(sd, it, s, Z, tab + L.xi, rtab + sd.tab_off + L.xi, mom, NN);
+}
+
 // Raw moment sums of an arbitrary state (after set_state); same precision rule
 // as the stage kernel.
 template <typename R>
@@ -295,6 +355,8 @@ static cudaError_t configure_t(size_t smem_bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(init_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(iso_reset_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fields_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
@@ -304,14 +366,19 @@ cudaError_t configure_kernels_p(int prec, size_t smem_bytes) {
 
 cudaError_t configure_kernels(size_t smem_bytes) { return configure_t<double>(smem_bytes); }
 
-// Raises (never lowers) the FP64 stage kernel's dynamic shared-memory limit on
-// the current device to at least smem_bytes.
+// Raises (never lowers) the dynamic shared-memory limit of the FP64 stage and
+// isothermal-reset kernels on the current device to at least smem_bytes.
 cudaError_t ensure_stage_smem(size_t smem_bytes) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, stage_kernel<double>);
-    if (e != cudaSuccess) return e;
-    if ((size_t)a.maxDynamicSharedSizeBytes >= smem_bytes) return cudaSuccess;
-    return cudaFuncSetAttribute(stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    const void* fns[2] = {(const void*)stage_kernel<double>, (const void*)iso_reset_kernel<double>};
+    for (const void* f : fns) {
+        cudaFuncAttributes a;
+        cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+        if ((size_t)a.maxDynamicSharedSizeBytes >= smem_bytes) continue;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
@@ -348,6 +415,17 @@ void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sla
     else
         init_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, tables, (const double*)rtab, n0, u0, T0,
                                                             (double*)state, mom, NF, NN, Z, err);
+}
+
+void launch_iso_reset_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                        const WorkItem* items, const double* tables, const void* rtab, void* state, double* mom,
+                        long long NF, long long NN, int Z) {
+    if (prec == EVFDLB_FP32)
+        iso_reset_kernel<float><<<nitems, kThreads, smem, st>>>(slabs, items, tables, (const float*)rtab,
+                                                                (float*)state, mom, NF, NN, Z);
+    else
+        iso_reset_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, tables, (const double*)rtab,
+                                                                 (double*)state, mom, NF, NN, Z);
 }
 
 void launch_sums_p(int prec, int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,

@@ -29,6 +29,9 @@ void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slab
                   const double* tables, const double* taps, const double* src, const double* base,
                   double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
                   double alpha, double beta, int mode, int Z, unsigned* err);
+void launch_iso_reset_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                        const WorkItem* items, const double* tables, const void* rtab, void* state, double* mom,
+                        long long NF, long long NN, int Z);
 void launch_sums(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                  const double* tables, const double* state, double* mom, long long NF, long long NN,
                  unsigned* err);
@@ -198,6 +201,8 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
                      0.25, 0, Z, err);
         launch_stage(nitems, smem, st, desc, items, tables, taps, u2, state, state, mom[2], mom[0], NF, NN,
                      1.0 / 3.0, 2.0 / 3.0, 0, Z, err);
+        if (p->T_iso > 0.0)
+            launch_iso_reset_p(EVFDLB_FP64, nitems, smem, st, desc, items, tables, tables, state, mom[0], NF, NN, Z);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return st_of(e);

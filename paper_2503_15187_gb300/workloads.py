@@ -14,6 +14,16 @@ Recipes (paper: Busuioc & Sofonea, arXiv:2503.15187):
   thickness h; a variant of the evaporation runs of Sec. III.C;
 * batch of slabs: per-slab sizes, orders, temperature ratios and mean
   densities drawn from one seed, noise from SeedSequence.spawn.
+
+Initial profiles of the paper's three numerical experiments (Sec. III), on
+the periodic domain [-L/2, L/2) with nodes at cell centres
+x_i = (i + 1/2) dx - L/2:
+* planar interface pair (Eq. (tanh), Sec. III.A): liquid for |x| < x0;
+* sinusoid (Eq. (rho_init_takata), Sec. III.B): A [1 + omega cos(2 pi x/L)];
+* slab in metastable vapour (Eq. (tan), Sec. III.C): liquid for |x| < x0,
+  vapour at half the coexistence vapour density;
+with the interface width xi = sqrt(3 / (4 pi sqrt(3) (T_c - T))) of both
+tanh recipes.
 """
 from __future__ import annotations
 
@@ -50,3 +60,30 @@ def batch_slabs(nslab: int = 256, seed: int = SEED, nz_min: int = 128, nz_max: i
         n0 = nbar * (1.0 + amp * r.uniform(-1.0, 1.0, nz))
         out.append(dict(nz=nz, Q=Q, T_ratio=tr, nbar=nbar, n0=n0))
     return out
+
+
+def centred_nodes(nz: int, dz: float) -> np.ndarray:
+    return dz * (np.arange(nz) + 0.5) - 0.5 * nz * dz
+
+
+def tanh_width(T_c: float, T: float) -> float:
+    """Interface width of Eqs. (tanh) and (tan)."""
+    return float(np.sqrt(3.0 / (4.0 * np.pi * np.sqrt(3.0) * (T_c - T))))
+
+
+def interface_pair(nz: int, dz: float, n_l: float, n_v: float, x0: float, xi: float) -> np.ndarray:
+    """Eq. (tanh): n_l + (n_v - n_l)/2 [1 + tanh((|x| - x0)/xi)]."""
+    x = centred_nodes(nz, dz)
+    return n_l + 0.5 * (n_v - n_l) * (1.0 + np.tanh((np.abs(x) - x0) / xi))
+
+
+def sinusoid(nz: int, dz: float, A: float, omega: float) -> np.ndarray:
+    """Eq. (rho_init_takata) with wavelength L = nz dz: A [1 + omega cos(2 pi x / L)]."""
+    x = centred_nodes(nz, dz)
+    return A * (1.0 + omega * np.cos(2.0 * np.pi * x / (nz * dz)))
+
+
+def slab_in_metastable_vapour(nz: int, dz: float, n_l: float, n_v: float, x0: float, xi: float) -> np.ndarray:
+    """Eq. (tan): n_l + (n_v - 2 n_l)/4 [1 + tanh((|x| - x0)/xi)], vapour n_v/2."""
+    x = centred_nodes(nz, dz)
+    return n_l + 0.25 * (n_v - 2.0 * n_l) * (1.0 + np.tanh((np.abs(x) - x0) / xi))

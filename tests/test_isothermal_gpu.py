@@ -1,11 +1,11 @@
-"""GPU parity of the isothermal mode (T_iso > 0: every node field formed at
-T_iso) against the oracle's isothermal path (pinned in
+"""GPU parity of the isothermal mode (T_iso > 0: after every step each
+node's temperature is set back to T_iso, density, velocity and
+non-equilibrium part kept) against the oracle's isothermal path (pinned in
 test_oracle_isothermal_pins.py) on the same seeded inputs.
 
-Bars are those of the thermal parity tests: 1e-11 for one right-hand side,
-1e-12 per step, 1e-11 after 20 steps; FP32 at 1e-5 per step.  The uniform
-relaxation case has a closed form (the RK3 stability polynomial), checked on
-the GPU elementwise as well.
+Bars are those of the thermal parity tests: 1e-12 per step, 1e-11 after 20
+steps; FP32 at 1e-5 per step.  A uniform Maxwellian at another temperature
+becomes the projected Maxwellian at T_iso after one step.
 """
 import numpy as np
 import pytest
@@ -49,9 +49,7 @@ def test_isothermal_rhs_and_step(name):
     sim, orc, n0, u0, T0 = make(name)
     F, G = orc.step(*orc.equilibrium(n0, u0, T0), 2)
     sim.set_state(F.ravel(), G.ravel())
-    fg = sim.fields()
-    assert np.all(fg["T"] == orc.s.T_iso)
-    RF, RG = sim.rhs()
+    RF, RG = sim.rhs()                             # the thermal right-hand side
     RFo, RGo = orc.rhs(F, G)
     Q, nz = F.shape
     assert rel(RF.reshape(Q, nz), RFo) < 1e-11 and rel(RG.reshape(Q, nz), RGo) < 1e-11
@@ -70,8 +68,7 @@ def test_isothermal_twenty_steps(name):
     Fg, Gg = sim.state_2d()
     assert rel(Fg, Fo) < 1e-11 and rel(Gg, Go) < 1e-11
     n, u, T, q, tot = sim.moments()
-    no, uo, To, qo = orc.moments(Fo, Go)
-    assert rel(T, To) < 1e-11                      # moments report the kinetic temperature
+    assert np.abs(T - orc.s.T_iso).max() < 1e-13 * orc.s.T_iso
 
 
 def test_isothermal_fp32_step():
@@ -84,22 +81,18 @@ def test_isothermal_fp32_step():
     assert rel(Fg, Fo) < 1e-5 and rel(Gg, Go) < 1e-5
 
 
-def test_uniform_relaxation_closed_form_on_gpu():
-    nz, Q, k = 40, 16, 9
+def test_uniform_maxwellian_reset_on_gpu():
+    nz, Q = 40, 16
     p = ev.Params(nx=nz, dx=0.25, Q=Q, T_iso=0.55)
     sim = ev.Sim(p)
     th = O.Oracle(O.Setup(nz=nz, Q=Q, dz=0.25, dt=sim.dt()))
     n0 = np.full(nz, 0.3)
-    F0, G0 = th.equilibrium(n0, np.zeros(nz), np.full(nz, 0.72))
     Fe, Ge = th.equilibrium(n0, np.zeros(nz), np.full(nz, 0.55))
-    nu = th.node_fields(Fe, Ge)["rate"][0]
-    z = -nu * sim.dt()
-    R = 1 + z + z * z / 2 + z ** 3 / 6
     sim.init(n0, np.zeros(nz), np.full(nz, 0.72))
-    sim.step(k)
+    sim.step(1)
     Fg, Gg = sim.state_2d()
-    assert np.abs(Fg - (Fe + R ** k * (F0 - Fe))).max() < 2e-14 * F0.max()
-    assert np.abs(Gg - (Ge + R ** k * (G0 - Ge))).max() < 2e-14 * G0.max()
+    assert np.abs(Fg - Fe).max() < 1e-14 * Fe.max() and np.abs(Gg - Ge).max() < 1e-14 * Ge.max()
+    assert sim.launches_per_step() == 4
 
 
 def test_isothermal_adjoint_unsupported():
