@@ -220,6 +220,7 @@ def run_ours(args, rank, world):
     if not args.no_variants:
         legs = {"fp32": lambda: fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
                 "ev2": lambda: ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
+                "fp64_df": lambda: df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
                 "adjoint": lambda: adjoint_leg(ev, W, stream),
                 "batched": lambda: batched_leg(ev, W, stream, rank, world, maxred),
                 "two_d": lambda: two_d_leg(ev, stream, flush, maxred, world)}
@@ -288,6 +289,38 @@ def ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f64",
             "ms_per_step": ms / args.steps, "force": "Eq. (F2), 5-point stencils",
             "max_rel_diff_n_vs_ev1": float(np.abs(n2 - n64).max() / np.abs(n64).max()),
+            "gpu_launches": 3 * args.steps}
+
+
+def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
+    """The FP64_DF variant on the same slab and timing protocol: FP64 state and
+    arithmetic except the stage's Hermite analysis and synthesis, which run as
+    double-float (Dot2) sums on the FP32 pipe.  Its density after the same
+    number of steps is compared with the FP64 run."""
+    import dataclasses
+    import numpy as np
+    import torch
+    pdf = dataclasses.replace(p, precision=ev.FP64_DF)
+    sim = ev.Sim(pdf, stream=stream)
+    sim.init(n0, np.zeros(NZ), np.full(NZ, T))
+    sim.step(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        sim.step_async(1)
+        ends[i].record(stream)
+    barrier()
+    sim.step(1)
+    ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    nd = sim.moments(with_totals=False)[0]
+    sim.close()
+    return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "dtype": "f64 (Hermite transforms as double-float pairs on the FP32 pipe)",
+            "ms_per_step": ms / args.steps,
+            "max_rel_diff_n_vs_fp64": float(np.abs(nd - n64).max() / np.abs(n64).max()),
             "gpu_launches": 3 * args.steps}
 
 
@@ -482,7 +515,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")
-    ap.add_argument("--variants", default="", help="comma-separated subset of fp32,ev2,adjoint,batched,two_d")
+    ap.add_argument("--variants", default="", help="comma-separated subset of fp32,ev2,fp64_df,adjoint,batched,two_d")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -59,7 +59,13 @@ typedef enum {
 } evfdlb_status;
 
 enum { EVFDLB_BC_PERIODIC = 0, EVFDLB_BC_OUTFLOW = 1 };
-enum { EVFDLB_FP64 = 0, EVFDLB_FP32 = 1 };
+/* Precision.  FP64: every step in FP64.  FP32: FP32 state and per-velocity
+ * work, FP64 chi / transport / gradients / conserved sums.  FP64_DF: FP64
+ * state and FP64 arithmetic except the Hermite analysis and synthesis of the
+ * stage, which run as double-float pairs (hi, lo floats, ~48 bits) on the
+ * FP32 pipe with the compensated dot product Dot2 of Ogita, Rump & Oishi
+ * (2005); the adjoint returns E_UNSUPPORTED for it. */
+enum { EVFDLB_FP64 = 0, EVFDLB_FP32 = 1, EVFDLB_FP64_DF = 2 };
 /* Force model (Sec. II.A).  EV1: the convolution of Eq. (F1), Simpson taps
  * over |z| <= r_cut.  EV2: its gradient expansion, Eq. (F2),
  * F2 = 2a dn/dz + kappa d3n/dz3 with a = (2 pi sigma^3/3) phi_a gamma/(gamma-3)
@@ -97,8 +103,7 @@ typedef struct {
     double  r_cut;        /* EV1: cut of the Eq. (F1) integral (>= sigma + 2dx)        */
     int32_t Q;            /* Gauss-Hermite order, 4 <= Q <= 32                         */
     int32_t bc;           /* EVFDLB_BC_PERIODIC or EVFDLB_BC_OUTFLOW                   */
-    int32_t precision;    /* EVFDLB_FP64, or EVFDLB_FP32: FP32 state and per-velocity  */
-                          /* work, FP64 chi / transport / gradients / conserved sums;  */
+    int32_t precision;    /* EVFDLB_FP64, EVFDLB_FP32 or EVFDLB_FP64_DF (see above);   */
                           /* one precision per context (the ABI stays float64)         */
     int32_t force_model;  /* EVFDLB_EV1 or EVFDLB_EV2 (see above)                      */
     int32_t relax_mode;   /* EVFDLB_RELAX_INV_TAU or EVFDLB_RELAX_CHI_OVER_TAU         */

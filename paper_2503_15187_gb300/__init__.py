@@ -23,7 +23,7 @@ FIELD_NAMES = ("n", "u", "T", "q", "nbar", "chi", "force", "mu", "tau", "Pr",
                "nu", "A", "B", "D", "X", "bnchi")
 
 BC_PERIODIC, BC_OUTFLOW = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP64_DF = 0, 1, 2
 EV1, EV2 = 0, 1
 RELAX_INV_TAU, RELAX_CHI_OVER_TAU = 0, 1
 

@@ -28,6 +28,12 @@ void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sla
 void launch_sums_p(int prec, int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                    const double* tables, const void* rtab, const void* state, double* mom, long long NF,
                    long long NN, unsigned* err);
+size_t stage_smem_bytes_df(int Q, int Z, int M);
+cudaError_t configure_df(size_t smem_bytes);
+void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                     const double* tables, const double* dftab, const double* taps, const double* src,
+                     const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
+                     long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err);
 void launch_iso_reset_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                         const WorkItem* items, const double* tables, const void* rtab, void* state, double* mom,
                         long long NF, long long NN, int Z);
@@ -106,6 +112,9 @@ struct evfdlb_ctx {
     bool have_state = false;
     bool poisoned = false;
     bool iso = false;            // some slab has T_iso > 0 (reset after every step)
+    bool df = false;             // FP64_DF: FP64 context whose stages use double-float transforms
+    double* dftables = nullptr;  // analysis / synthesis tables as float pairs (FP64_DF)
+    size_t smem_df = 0;          // stage shared memory of the FP64_DF kernel
     // adjoint: checkpoints of the trajectory since the last init / set_state
     int ckpt_every = 0;          // 0: no tracking (no adjoint)
     int64_t steps = 0;           // steps since the trajectory origin
@@ -140,6 +149,7 @@ void free_ctx(evfdlb_ctx* c) {
         cudaFree(c->mom[i]);
     }
     if (c->rtables != c->tables) cudaFree(c->rtables);
+    cudaFree(c->dftables);
     if (c->rtaps != c->taps) cudaFree(c->rtaps);
     cudaFree(c->tables);
     cudaFree(c->taps);
@@ -162,8 +172,13 @@ void queue_step(evfdlb_ctx* c, cudaStream_t st) {
     double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
     auto stage = [&](const void* src, const void* base, void* out, const double* mi, double* mo, double a,
                      double b) {
-        launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps, src,
-                       base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
+        if (c->df)
+            launch_stage_df(n, c->smem_df, st, c->slabs, c->items, c->tables, c->dftables, c->taps,
+                            (const double*)src, (const double*)base, (double*)out, nullptr, mi, mo, c->NF, c->NN, a,
+                            b, 0, c->Z, c->err);
+        else
+            launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps,
+                           src, base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
     };
     stage(f0, nullptr, f1, m0, m1, 0.0, 1.0);              // u1 = u + dt L(u)
     stage(f1, f0, f2, m1, m2, 0.75, 0.25);                 // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
@@ -182,6 +197,7 @@ void partition(evfdlb_ctx* c, int Z) {
         for (int i0 = 0; i0 < c->params[s].nx; i0 += Z)
             c->items_h.push_back(WorkItem{s, i0, std::min(Z, c->params[s].nx - i0), 0});
     c->smem = stage_smem_bytes_p(c->prec, c->Qmax, Z, c->Mmax);
+    c->smem_df = stage_smem_bytes_df(c->Qmax, Z, c->Mmax);
     if (c->items_cap == 0) c->items_cap = (size_t)c->NN;
 }
 
@@ -240,7 +256,7 @@ evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
 }
 
 evfdlb_status adjoint_supported(evfdlb_ctx* c) {
-    if (c->prec != EVFDLB_FP64) return EVFDLB_E_UNSUPPORTED;
+    if (c->prec != EVFDLB_FP64 || c->df) return EVFDLB_E_UNSUPPORTED;
     for (auto& q : c->params) {
         if (q.bc != EVFDLB_BC_PERIODIC) return EVFDLB_E_UNSUPPORTED;
         if (q.T_iso > 0.0) return EVFDLB_E_UNSUPPORTED;       // T does not follow the state
@@ -353,7 +369,8 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     for (int s = 0; s < nbatch; ++s) {
         ps[s] = (nbatch == 1) ? (p ? *p : per_slab[0]) : per_slab[s];
         if (!validate(ps[s], nullptr)) return EVFDLB_E_INVALID_ARG;
-        if (ps[s].precision != EVFDLB_FP64 && ps[s].precision != EVFDLB_FP32) return EVFDLB_E_INVALID_ARG;
+        if (ps[s].precision != EVFDLB_FP64 && ps[s].precision != EVFDLB_FP32 && ps[s].precision != EVFDLB_FP64_DF)
+            return EVFDLB_E_INVALID_ARG;
         if (ps[s].precision != ps[0].precision) return EVFDLB_E_INVALID_ARG;   // one precision per context
     }
     evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
@@ -361,7 +378,8 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     c->nbatch = nbatch;
     c->params = ps;
     c->user = (cudaStream_t)cuda_stream;
-    c->prec = ps[0].precision;
+    c->df = (ps[0].precision == EVFDLB_FP64_DF);
+    c->prec = c->df ? EVFDLB_FP64 : ps[0].precision;   // FP64_DF is an FP64 context but for its stages
     c->ckpt_every = ps[0].ckpt_every > 0 ? ps[0].ckpt_every : 0;
     c->esize = (c->prec == EVFDLB_FP32) ? sizeof(float) : sizeof(double);
     if (cudaGetDevice(&c->device) != cudaSuccess) { free_ctx(c); return EVFDLB_E_CUDA; }
@@ -461,6 +479,20 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         e = cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = configure_kernels_p(c->prec, stage_smem_bytes_p(c->prec, Qmax, kZMax, Mmax));
+    if (e == cudaSuccess && c->df) {
+        // analysis and synthesis tables as (hi, lo) float pairs in 8-byte slots
+        std::vector<double> dft(tables.size());
+        for (size_t i = 0; i < tables.size(); ++i) {
+            float pr[2];
+            pr[0] = (float)tables[i];
+            pr[1] = (float)(tables[i] - (double)pr[0]);
+            memcpy(&dft[i], pr, sizeof(pr));
+        }
+        alloc((void**)&c->dftables, sizeof(double) * dft.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->dftables, dft.data(), sizeof(double) * dft.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = configure_df(stage_smem_bytes_df(Qmax, kZMax, Mmax));
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         evfdlb_status st = cuda_status(e);
@@ -618,9 +650,14 @@ evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_devic
     if (!c || !RF || !RG) return EVFDLB_E_INVALID_ARG;
     if (c->c2) return c->c2_state ? rhs_2d(c->c2, RF, RG, on_device) : EVFDLB_E_STATE;
     if (!c->have_state) return EVFDLB_E_STATE;
-    launch_stage_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables,
-                   c->taps, c->rtaps, c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr, c->NF, c->NN,
-                   0.0, 1.0, 1, c->Z, c->err);
+    if (c->df)
+        launch_stage_df((int)c->items_h.size(), c->smem_df, c->user, c->slabs, c->items, c->tables, c->dftables,
+                        c->taps, (const double*)c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr, c->NF,
+                        c->NN, 0.0, 1.0, 1, c->Z, c->err);
+    else
+        launch_stage_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables,
+                       c->rtables, c->taps, c->rtaps, c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr,
+                       c->NF, c->NN, 0.0, 1.0, 1, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
     size_t bytes = sizeof(double) * c->NF;
     evfdlb_status s;

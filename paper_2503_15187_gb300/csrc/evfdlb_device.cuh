@@ -93,6 +93,37 @@ enum { SC_N = 0, SC_U, SC_T, SC_NU, SC_FORCE, SC_KQ, SC_K, SC_A, SC_B, SC_D };
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic for the FP64_DF variant: a value is an unevaluated
+// pair of floats (hi, lo), hi = fl32(x), lo = fl32(x - hi), about 48
+// significant bits.  Sums of products use the compensated dot product Dot2
+// of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005): the error-free TwoProduct (by FMA) and TwoSum (Knuth)
+// of every term, errors collected in a second float; the cross terms
+// hi*lo of pair operands join the error float.  The result carries about
+// twice the float precision.  __fadd_rn / __fmul_rn keep the compiler from
+// contracting the error-free transformations into FMAs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_join(float s, float e) { return (double)s + (double)e; }
+
+// (s, e) += a * b for pairs a, b.
+__device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float pe = fmaf(a.x, b.x, -p);            // exact: a.x b.x = p + pe
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // exact: s + p = t + te
+    e = __fadd_rn(e, __fadd_rn(te, pe));
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    s = t;
+}
+
+
+// ---------------------------------------------------------------------------
 // Phase 0: stage the tables, the density halo, u/T near the tile and the
 // state tile (+-3 nodes for WENO-5) into shared memory.
 // ---------------------------------------------------------------------------
@@ -122,16 +153,20 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     }
 }
 
+// With Fd (FP64_DF), the tile's interior columns are also stored as
+// double-float pairs, Fd[(d Q + k) Z + t].
 template <typename R>
 __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                const R* __restrict__ src, long long NF) {
+                                const R* __restrict__ src, long long NF, float2* Fd = nullptr) {
     const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
     const int cols = it.nz + 6;
     for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
         int c = e % cols, r = e / cols;
         int k = r % Q, d = r / Q;
         int i = gidx(it.i0 - 3 + c, nx, bc);
-        s.F[(d * Q + k) * W + c] = src[d * NF + sd.f_off + (long long)k * nx + i];
+        R v = src[d * NF + sd.f_off + (long long)k * nx + i];
+        s.F[(d * Q + k) * W + c] = v;
+        if (Fd && c >= 3 && c < it.nz + 3) Fd[(size_t)r * Z + c - 3] = df_split((double)v);
     }
 }
 
@@ -295,7 +330,9 @@ __device__ void node_coefficients(const SlabDesc& sd, const WorkItem& it, const 
     }
 }
 
-template <typename R>
+// With DF the coefficients are stored as double-float pairs (float2) in the
+// same block, for the double-float synthesis.
+template <typename R, bool DF = false>
 __device__ void coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                              const R* __restrict__ tab, int tid, int nth) {
     const int Q = sd.Q, nz = it.nz;
@@ -311,7 +348,8 @@ __device__ void coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<
         c = fma(cc[2 * Z] * tab[L.r2 + l], mm[max(l - 2, 0) * Z], c);
         c = fma(cc[3 * Z] * tab[L.r3 + l], mm[max(l - 3, 0) * Z], c);
         if (l >= 1) c = fma(s.Scr[Z + t] * tab[L.r1 + l], s.A[((size_t)d * Q + l - 1) * Z + t], c);
-        s.C[((size_t)d * Q + l) * Z + t] = c;
+        if constexpr (DF) reinterpret_cast<float2*>(s.C)[((size_t)d * Q + l) * Z + t] = df_split((double)c);
+        else s.C[((size_t)d * Q + l) * Z + t] = c;
     }
 }
 
@@ -338,6 +376,40 @@ __device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& 
         }
         s.A[((size_t)d * Q + l0) * Z + t] = a0;
         if (two) s.A[((size_t)d * Q + l0 + 1) * Z + t] = a1;
+    }
+}
+
+// Analysis in double-float: the state tile is split into pairs when it is
+// staged (Fd[(d Q + j) Z + t]); a_l = sum_j psi_l(xi_j) h_j by Dot2, four
+// orders per thread (four independent accumulator chains, each pair loaded
+// feeding four terms), joined to FP64 for the coefficients.
+__device__ inline void analysis_df(const SlabDesc& sd, const WorkItem& it, const Smem<double>& s, const float2* Fd,
+                                   const float2* P, int Z, int tid, int nth) {
+    const int Q = sd.Q, nz = it.nz;
+    const int nq = Q / 4;                          // quads of orders covering l <= Q-2 (Q even)
+    const int per_d = nq * nz;
+    for (int e = tid; e < 2 * per_d; e += nth) {
+        int d = e / per_d, r = e % per_d;
+        int l0 = 4 * (r / nz), t = r % nz;
+        const int nl = min(4, Q - 1 - l0);         // orders l0 .. l0+nl-1 (<= Q-2)
+        const float2* P0 = P + l0 * Q;
+        const float2* P1 = P + min(l0 + 1, Q - 1) * Q;
+        const float2* P2 = P + min(l0 + 2, Q - 1) * Q;
+        const float2* P3 = P + min(l0 + 3, Q - 1) * Q;
+        const float2* h = Fd + (size_t)d * Q * Z + t;
+        float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f, s3 = 0.f, e3 = 0.f;
+        for (int j = 0; j < Q; ++j) {
+            const float2 hv = h[j * Z];
+            dot2_acc(s0, e0, P0[j], hv);
+            dot2_acc(s1, e1, P1[j], hv);
+            dot2_acc(s2, e2, P2[j], hv);
+            dot2_acc(s3, e3, P3[j], hv);
+        }
+        double* A = s.A + ((size_t)d * Q + l0) * Z + t;
+        A[0] = df_join(s0, e0);
+        if (nl > 1) A[Z] = df_join(s1, e1);
+        if (nl > 2) A[2 * Z] = df_join(s2, e2);
+        if (nl > 3) A[3 * Z] = df_join(s3, e3);
     }
 }
 

@@ -49,7 +49,12 @@ namespace evfdlb {
 // ---------------------------------------------------------------------------
 
 // mode 0: out = alpha base + beta (src + dt R);  mode 1: rhs_out = R (FP64).
-template <typename R>
+// DF (R = double only): the FP64_DF variant -- rtab holds the analysis and
+// synthesis tables as double-float pairs, every other table value comes from
+// the FP64 `tables`; the Hermite analysis and synthesis run as Dot2 sums of
+// pairs on the FP32 pipe (state tile split into pairs once per stage in a
+// block after the Hermite moments), everything else as in the FP64 kernel.
+template <typename R, bool DF = false>
 __global__ void __launch_bounds__(kThreads)
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
@@ -63,14 +68,18 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     Smem<R> s = carve<R>(smem, Q, Z, sd.M);
 
+    float2* Fd = DF ? reinterpret_cast<float2*>(s.Mm + (size_t)Q * Z) : nullptr;
     load_node_inputs<R>(sd, it, s, Z, rtab, mom_in, NN);
-    load_state_tile<R>(sd, it, s, Z, src, NF);
+    load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
     __syncthreads();
     // Warp 0 forms the node-level quantities of the tile (node fields,
     // coefficient constants, Hermite moments of the local Gaussian) while the
     // other warps do the velocity-space work that needs only the state tile
     // (Hermite analysis, WENO-5 faces), so the serial node work overlaps it.
-    const R* rt = rtab + sd.tab_off;
+    // the tables of everything but the DF transforms
+    const R* vtab = DF ? reinterpret_cast<const R*>(tables) : rtab;
+    const R* rt = vtab + sd.tab_off;
+    TableLayout L(Q);
     if (threadIdx.x < 32) {
         node_fields_pass1<R>(sd, it, s, taps, NN, nullptr, threadIdx.x, 32);
         __syncwarp();
@@ -78,38 +87,62 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         __syncwarp();
         node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32);
     } else {
-        analysis<R>(sd, it, s, Z, threadIdx.x - 32, blockDim.x - 32);
-        faces<R>(sd, it, s, Z, rtab, threadIdx.x - 32, blockDim.x - 32);
+        const int tid = threadIdx.x - 32, nth = blockDim.x - 32;
+        if constexpr (DF) {
+            analysis_df(sd, it, s, Fd, reinterpret_cast<const float2*>(s.P), Z, tid, nth);
+        } else {
+            analysis<R>(sd, it, s, Z, tid, nth);
+        }
+        faces<R>(sd, it, s, Z, vtab, tid, nth);
     }
     __syncthreads();
-    coefficients<R>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
+    coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
     __syncthreads();
 
-    // Phase 5: synthesis, advection, relaxation and the RK stage; two
-    // velocities per thread share every coefficient loaded.
-    TableLayout L(Q);
-    const R* xi = rtab + sd.tab_off + L.xi;
+    // Phase 5: synthesis, advection, relaxation and the RK stage; the VK
+    // velocities of a thread share every coefficient loaded.
+    const R* xi = rt + L.xi;
     const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
-    const int nkp = (Q + 1) / 2;
-    for (int e = threadIdx.x; e < 2 * nkp * nz; e += blockDim.x) {
+    // velocities per thread: two in FP64/FP32, four in DF (four independent
+    // Dot2 chains hide the FP32 latency)
+    constexpr int VK = DF ? 4 : 2;
+    const int nkg = (Q + VK - 1) / VK;
+    for (int e = threadIdx.x; e < 2 * nkg * nz; e += blockDim.x) {
         int t = e % nz, r = e / nz;
-        int k0 = 2 * (r % nkp), d = r / nkp;
-        const int nk = (k0 + 1 < Q) ? 2 : 1;
-        const R* S0 = s.S + k0 * Q;
-        const R* S1 = s.S + (k0 + nk - 1) * Q;
-        const R* c = s.C + (size_t)d * Q * Z + t;
-        R syn0 = 0, syn1 = 0;
-        for (int l = 0; l < Q; ++l) {
-            R cl = c[l * Z];
-            syn0 = fma(S0[l], cl, syn0);
-            syn1 = fma(S1[l], cl, syn1);
+        int k0 = VK * (r % nkg), d = r / nkg;
+        const int nk = min(VK, Q - k0);
+        R syn[VK];
+        if constexpr (DF) {
+            const float2* Sd = reinterpret_cast<const float2*>(s.S);
+            const float2* c = reinterpret_cast<const float2*>(s.C) + (size_t)d * Q * Z + t;
+            float a[VK], b[VK];
+#pragma unroll
+            for (int q = 0; q < VK; ++q) a[q] = b[q] = 0.f;
+            for (int l = 0; l < Q; ++l) {
+                const float2 cl = c[l * Z];
+#pragma unroll
+                for (int q = 0; q < VK; ++q) dot2_acc(a[q], b[q], Sd[min(k0 + q, Q - 1) * Q + l], cl);
+            }
+#pragma unroll
+            for (int q = 0; q < VK; ++q) syn[q] = df_join(a[q], b[q]);
+        } else {
+            const R* c = s.C + (size_t)d * Q * Z + t;
+#pragma unroll
+            for (int q = 0; q < VK; ++q) syn[q] = 0;
+            for (int l = 0; l < Q; ++l) {
+                R cl = c[l * Z];
+#pragma unroll
+                for (int q = 0; q < VK; ++q) syn[q] = fma(s.S[min(k0 + q, Q - 1) * Q + l], cl, syn[q]);
+            }
         }
-        for (int q = 0; q < nk; ++q) {
+#pragma unroll
+        for (int q = 0; q < VK; ++q) {
+            if (q >= nk) break;
             const int k = k0 + q;
-            const R syn = q ? syn1 : syn0;
+            const R sq = syn[q];
             const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
             R h = s.F[(size_t)(d * Q + k) * W + t + 3];
-            R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
+            R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, sq));
             long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
             if (mode == 1) {
                 rhs_out[g] = (double)Rv;
@@ -347,6 +380,24 @@ size_t stage_smem_bytes(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z,
 
 size_t stage_smem_bytes_p(int prec, int Q, int Z, int M) {
     return prec == EVFDLB_FP32 ? smem_bytes_t<float>(Q, Z, M) : smem_bytes_t<double>(Q, Z, M);
+}
+
+// The FP64_DF stage adds the split state tile, 2 Q Z pairs.
+size_t stage_smem_bytes_df(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M) + 16 * (size_t)Q * Z; }
+
+cudaError_t configure_df(size_t smem_bytes) {
+    return cudaFuncSetAttribute(stage_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes);
+}
+
+// FP64_DF stage: dftab holds the analysis and synthesis tables as pairs.
+void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                     const double* tables, const double* dftab, const double* taps, const double* src,
+                     const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
+                     long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
+    stage_kernel<double, true><<<nitems, kThreads, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
+                                                               out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
+                                                               mode, Z, err);
 }
 
 template <typename R>
