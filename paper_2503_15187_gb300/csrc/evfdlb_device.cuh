@@ -413,46 +413,103 @@ __device__ inline void analysis_df(const SlabDesc& sd, const WorkItem& it, const
     }
 }
 
-// WENO-5 (Jiang & Shu) value at the face between v2 and v3, upwind side v0..v2.
-// The nonlinear weights omega_r = (d_r / e_r) / sum_s (d_s / e_s),
-// e_r = (eps + beta_r)^2, are formed with a single division.
+// WENO-5 (Jiang & Shu) faces in difference form, along a run of faces.
+// With the upwind stencil v0..v4 (face between v2 and v3) and first
+// differences d_i = v_{i+1} - v_i:
+//   q0 - v2 = (5 d1 - 2 d0)/6,  q1 - v2 = (d1 + 2 d2)/6,  q2 - v2 = (4 d2 - d3)/6,
+//   4 beta_r = 13/3 t_r^2 + s_r^2 with second differences t_0 = d1 - d0,
+//   t_1 = d2 - d1, t_2 = d3 - d2 and s_0 = 3 d1 - d0, s_1 = -(d1 + d2),
+//   s_2 = d3 - 3 d2,
+// and the face value v2 + sum_r w_r (q_r - v2), w_r = a_r / sum a with
+// a_r = d_r prod_{s != r} e_s^2, e_s = 4 (eps + beta_s) (the common factor 4
+// cancels; one division per face).  Along a run the differences and the
+// t-terms of each cell are formed once and shared by the faces that use
+// them.  For xi_k < 0 the stencil is mirrored and the run is walked from its
+// last face down, so that the new value always enters at v4.
 template <typename R>
-__device__ __forceinline__ R weno5(R v0, R v1, R v2, R v3, R v4, R eps) {
-    const R k6 = R(1) / R(6), k1312 = R(13) / R(12), qr = R(0.25);
-    R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * k6;
-    R q1 = (-v1 + R(5) * v2 + R(2) * v3) * k6;
-    R q2 = (R(2) * v2 + R(5) * v3 - v4) * k6;
-    R t0 = v0 - R(2) * v1 + v2, s0 = v0 - R(4) * v1 + R(3) * v2;
-    R t1 = v1 - R(2) * v2 + v3, s1 = v1 - v3;
-    R t2 = v2 - R(2) * v3 + v4, s2 = R(3) * v2 - R(4) * v3 + v4;
-    R e0 = eps + fma(k1312 * t0, t0, qr * s0 * s0);
-    R e1 = eps + fma(k1312 * t1, t1, qr * s1 * s1);
-    R e2 = eps + fma(k1312 * t2, t2, qr * s2 * s2);
-    e0 *= e0;
-    e1 *= e1;
-    e2 *= e2;
-    R a0 = R(0.1) * (e1 * e2), a1 = R(0.6) * (e0 * e2), a2 = R(0.3) * (e0 * e1);
-    return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
-}
+struct Weno5Run {
+    R v2, v3, v4, d0, d1, d2, d3, u0, u1, u2;   // u_r = 13/3 t_r^2 + 4 eps
+    R eps4;
+    __device__ __forceinline__ R tterm(R t) const { return fma(R(13.0 / 3.0) * t, t, eps4); }
+    __device__ __forceinline__ void start(R w0, R w1, R w2, R w3, R w4, R eps) {
+        eps4 = R(4) * eps;
+        v2 = w2;
+        v3 = w3;
+        v4 = w4;
+        d0 = w1 - w0;
+        d1 = w2 - w1;
+        d2 = w3 - w2;
+        d3 = w4 - w3;
+        u0 = tterm(d1 - d0);
+        u1 = tterm(d2 - d1);
+        u2 = tterm(d3 - d2);
+    }
+    __device__ __forceinline__ R face() const {
+        const R s0 = fma(R(3), d1, -d0), s1 = d1 + d2, s2 = fma(R(-3), d2, d3);
+        const R e0 = fma(s0, s0, u0), e1 = fma(s1, s1, u1), e2 = fma(s2, s2, u2);
+        const R E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+        const R a0 = E1 * E2, a1 = E0 * E2, a2 = E0 * E1;
+        // linear weights 0.1, 0.6, 0.3 folded into the candidate corrections
+        const R c0 = fma(R(5.0 / 60.0), d1, R(-2.0 / 60.0) * d0);
+        const R c1 = fma(R(0.2), d2, R(0.1) * d1);
+        const R c2 = fma(R(0.2), d2, R(-0.05) * d3);
+        const R num = fma(a0, c0, fma(a1, c1, a2 * c2));
+        const R den = fma(R(0.1), a0, fma(R(0.6), a1, R(0.3) * a2));
+        R q;
+        // FP32: the fast reciprocal-based quotient (2 ulp) is far inside the
+        // FP32 variant's error budget; FP64 keeps the IEEE quotient
+        if constexpr (std::is_same<R, float>::value) q = __fdividef(num, den);
+        else q = num / den;
+        return v2 + q;
+    }
+    __device__ __forceinline__ void shift(R w5) {
+        const R d4 = w5 - v4;
+        u0 = u1;
+        u1 = u2;
+        u2 = tterm(d4 - d3);
+        d0 = d1;
+        d1 = d2;
+        d2 = d3;
+        d3 = d4;
+        v2 = v3;
+        v3 = v4;
+        v4 = w5;
+    }
+};
 
 // Phase 3c: face values h_{i-1/2} for faces f = 0..nz (face f lies between
-// tile nodes f-1 and f), upwind by the sign of xi_k.
+// tile nodes f-1 and f), upwind by the sign of xi_k; runs of kRun faces per
+// thread, consecutive threads on consecutive velocity rows (the row stride
+// Z + 6 keeps their shared-memory reads apart), the walk direction chosen by
+// index arithmetic so that threads of both signs run the same instructions.
+// At xi_k = 0 the face values are formed as for xi_k > 0 and then multiplied
+// by xi_k = 0 in the flux difference.
+constexpr int kRun = 4;
 template <typename R>
 __device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                       const R* __restrict__ rtab, int tid, int nth) {
-    const int Q = sd.Q, W = Z + 6, nf = it.nz + 1;
+    const int Q = sd.Q, W = Z + 6, nf = it.nz + 1, rows = 2 * Q;
+    const int nruns = (nf + kRun - 1) / kRun;
     TableLayout L(Q);
     const R* xi = rtab + sd.tab_off + L.xi;
     const R eps = (R)sd.weno_eps;
-    for (int e = tid; e < 2 * Q * nf; e += nth) {
-        int f = e % nf, r = e / nf;
-        int k = r % Q, d = r / Q;
-        const R* h = s.F + (size_t)(d * Q + k) * W;
-        R x = xi[k], v;
-        if (x > R(0)) v = weno5<R>(h[f], h[f + 1], h[f + 2], h[f + 3], h[f + 4], eps);
-        else if (x < R(0)) v = weno5<R>(h[f + 5], h[f + 4], h[f + 3], h[f + 2], h[f + 1], eps);
-        else v = 0;
-        s.Face[(size_t)(d * Q + k) * (Z + 1) + f] = v;
+    for (int e = tid; e < rows * nruns; e += nth) {
+        const int r = e % rows, run = e / rows;
+        const int k = r % Q;
+        const int fa = run * kRun, n = min(kRun, nf - fa), fl = fa + n - 1;
+        const bool pos = xi[k] >= R(0);
+        const int dir = pos ? 1 : -1, f0 = pos ? fa : fl;
+        // x > 0: face f uses h[f .. f+4], walked up; x < 0: h[f+5 .. f+1], walked down
+        const R* hb = s.F + (size_t)r * W + (pos ? fa : fl + 5);
+        R* out = s.Face + (size_t)r * (Z + 1);
+        Weno5Run<R> w;
+        w.start(hb[0], hb[dir], hb[2 * dir], hb[3 * dir], hb[4 * dir], eps);
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            if (q >= n) break;
+            out[f0 + dir * q] = w.face();
+            if (q + 1 < n) w.shift(hb[dir * (q + 5)]);
+        }
     }
 }
 
