@@ -94,8 +94,7 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic for the FP64_DF variant: a value is an unevaluated
-// pair of floats (hi, lo), hi = fl32(x), lo = fl32(x - hi), about 48
-// significant bits.  Sums of products use the compensated dot product Dot2
+// pair of floats (hi, lo) with x = hi + lo to about 48 significant bits.  Sums of products use the compensated dot product Dot2
 // of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
 // Comput. 26, 2005): the error-free TwoProduct (by FMA) and TwoSum (Knuth)
 // of every term, errors collected in a second float; the cross terms
@@ -103,9 +102,30 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 // twice the float precision.  __fadd_rn / __fmul_rn keep the compiler from
 // contracting the error-free transformations into FMAs.
 // ---------------------------------------------------------------------------
+// The split is exact bit surgery, no FP64 instruction: hi is x with its
+// significand cut to 24 bits (the top 23 stored bits), lo the remaining 29
+// bits rounded to a float (x = hi + lo to 2^-48 relative).  |x| < 2^-126
+// gives (0, 0) and |x| < 2^-74 drops lo (absolute error below 2^-98); a
+// double-to-float conversion instruction costs several FP64-pipe slots on
+// this GPU, the integer path none.
 __device__ __forceinline__ float2 df_split(double x) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32);
+    const int ed = (int)((hw >> 20) & 0x7ffu);          // biased double exponent
+    const unsigned sgn = hw & 0x80000000u;
+    float h, l;
+    if (ed >= 897 && ed <= 1150) {                       // normal float range
+        h = __uint_as_float(sgn | ((unsigned)(ed - 896) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    } else {
+        h = (ed > 1150) ? __uint_as_float(sgn | 0x7f800000u) : 0.f;   // overflow -> inf, flagged downstream
+    }
+    if (ed >= 949 && ed <= 1150) {                       // 2^(ed - 1075) is a normal float
+        const float m = __uint2float_rn((unsigned)(b & 0x1fffffff));
+        l = __uint_as_float(__float_as_uint(m * __uint_as_float((unsigned)(ed - 948) << 23)) | sgn);
+    } else {
+        l = 0.f;
+    }
+    return make_float2(h, l);
 }
 __device__ __forceinline__ double df_join(float s, float e) { return (double)s + (double)e; }
 
@@ -337,19 +357,28 @@ __device__ void coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<
                              const R* __restrict__ tab, int tid, int nth) {
     const int Q = sd.Q, nz = it.nz;
     TableLayout L(Q);
-    for (int e = tid; e < 2 * Q * nz; e += nth) {
-        int t = e % nz, r = e / nz;
-        int l = r % Q, d = r / Q;
-        const R* cc = s.Cc + d * 4 * Z + t;
+    // one (l, node) per item, both distributions: the scaled moments
+    // sqrt(l(l-1)..) m_{l-j} and the force factor F1 sqrt(l) are shared
+    for (int e = tid; e < Q * nz; e += nth) {
+        const int t = e % nz, l = e / nz;
         const R* mm = s.Mm + t;
         // the sqrt factors vanish where the moment index would be negative
-        R c = cc[0] * mm[l * Z];
-        c = fma(cc[Z] * tab[L.r1 + l], mm[max(l - 1, 0) * Z], c);
-        c = fma(cc[2 * Z] * tab[L.r2 + l], mm[max(l - 2, 0) * Z], c);
-        c = fma(cc[3 * Z] * tab[L.r3 + l], mm[max(l - 3, 0) * Z], c);
-        if (l >= 1) c = fma(s.Scr[Z + t] * tab[L.r1 + l], s.A[((size_t)d * Q + l - 1) * Z + t], c);
-        if constexpr (DF) reinterpret_cast<float2*>(s.C)[((size_t)d * Q + l) * Z + t] = df_split((double)c);
-        else s.C[((size_t)d * Q + l) * Z + t] = c;
+        const R m0 = mm[l * Z];
+        const R M1 = tab[L.r1 + l] * mm[max(l - 1, 0) * Z];
+        const R M2 = tab[L.r2 + l] * mm[max(l - 2, 0) * Z];
+        const R M3 = tab[L.r3 + l] * mm[max(l - 3, 0) * Z];
+        const R f = s.Scr[Z + t] * tab[L.r1 + l];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const R* cc = s.Cc + d * 4 * Z + t;
+            R c = cc[0] * m0;
+            c = fma(cc[Z], M1, c);
+            c = fma(cc[2 * Z], M2, c);
+            c = fma(cc[3 * Z], M3, c);
+            if (l >= 1) c = fma(f, s.A[((size_t)d * Q + l - 1) * Z + t], c);
+            if constexpr (DF) reinterpret_cast<float2*>(s.C)[((size_t)d * Q + l) * Z + t] = df_split((double)c);
+            else s.C[((size_t)d * Q + l) * Z + t] = c;
+        }
     }
 }
 
