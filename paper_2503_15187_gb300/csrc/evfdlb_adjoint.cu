@@ -76,40 +76,51 @@ __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
     return s;
 }
 
-// Gradient of the WENO-5 face value Phi(v0..v4) of weno5() (upwind side
-// v0..v2), times pb: g_r = pb dPhi/dv_r.  With e_r = eps + beta_r,
-// omega_r = (d_r / e_r^2) / sum_s (d_s / e_s^2) and Phi = sum_r omega_r q_r,
-//   dPhi/dv = sum_r omega_r [dq_r/dv - 2 (q_r - Phi) / e_r * dbeta_r/dv].
+// Gradient of the WENO-5 face value Phi(v0..v4) (upwind side v0..v2), times
+// pb: g_r = pb dPhi/dv_r.  Phi is taken in the difference form of the forward
+// faces: with d_i = v_{i+1} - v_i, t_0 = d1 - d0, t_1 = d2 - d1, t_2 = d3 - d2,
+// s_0 = 3 d1 - d0, s_1 = d1 + d2, s_2 = d3 - 3 d2,
+//   e_r = s_r^2 + 13/3 t_r^2 + 4 eps   (= 4 (eps + beta_r)),
+//   a_0 = e_1^2 e_2^2, a_1 = e_0^2 e_2^2, a_2 = e_0^2 e_1^2,
+//   c_0 = (5 d1 - 2 d0)/60, c_1 = (d1 + 2 d2)/10, c_2 = (4 d2 - d3)/20,
+//   Phi = v2 + (sum a_r c_r) / (0.1 a_0 + 0.6 a_1 + 0.3 a_2),
+// differentiated in reverse order (one division per face).
 __device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, double v3, double v4, double eps,
                                            double pb, double g[5]) {
-    const double k6 = 1.0 / 6.0, k1312 = 13.0 / 12.0, k136 = 13.0 / 6.0;
-    double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * k6;
-    double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * k6;
-    double q2 = (2.0 * v2 + 5.0 * v3 - v4) * k6;
-    double t0 = v0 - 2.0 * v1 + v2, s0 = v0 - 4.0 * v1 + 3.0 * v2;
-    double t1 = v1 - 2.0 * v2 + v3, s1 = v1 - v3;
-    double t2 = v2 - 2.0 * v3 + v4, s2 = 3.0 * v2 - 4.0 * v3 + v4;
-    double e0 = eps + fma(k1312 * t0, t0, 0.25 * s0 * s0);
-    double e1 = eps + fma(k1312 * t1, t1, 0.25 * s1 * s1);
-    double e2 = eps + fma(k1312 * t2, t2, 0.25 * s2 * s2);
-    double iP = 1.0 / (e0 * e1 * e2);
-    double ie0 = e1 * e2 * iP, ie1 = e0 * e2 * iP, ie2 = e0 * e1 * iP;
-    double a0 = 0.1 * ie0 * ie0, a1 = 0.6 * ie1 * ie1, a2 = 0.3 * ie2 * ie2;
-    double iS = 1.0 / (a0 + a1 + a2);
-    double w0 = a0 * iS, w1 = a1 * iS, w2 = a2 * iS;
-    double Phi = w0 * q0 + w1 * q1 + w2 * q2;
-    double kk0 = -2.0 * w0 * (q0 - Phi) * ie0;
-    double kk1 = -2.0 * w1 * (q1 - Phi) * ie1;
-    double kk2 = -2.0 * w2 * (q2 - Phi) * ie2;
-    // dbeta_r/dv = (13/6) t_r dt_r/dv + (1/2) s_r ds_r/dv
-    double bt0 = k136 * t0 * kk0, bs0 = 0.5 * s0 * kk0;
-    double bt1 = k136 * t1 * kk1, bs1 = 0.5 * s1 * kk1;
-    double bt2 = k136 * t2 * kk2, bs2 = 0.5 * s2 * kk2;
-    g[0] = pb * (w0 * 2.0 * k6 + bt0 + bs0);
-    g[1] = pb * (-w0 * 7.0 * k6 - w1 * k6 - 2.0 * bt0 - 4.0 * bs0 + bt1 + bs1);
-    g[2] = pb * (w0 * 11.0 * k6 + w1 * 5.0 * k6 + w2 * 2.0 * k6 + bt0 + 3.0 * bs0 - 2.0 * bt1 + bt2 + 3.0 * bs2);
-    g[3] = pb * (w1 * 2.0 * k6 + w2 * 5.0 * k6 + bt1 - bs1 - 2.0 * bt2 - 4.0 * bs2);
-    g[4] = pb * (-w2 * k6 + bt2 + bs2);
+    const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3;
+    const double t0 = d1 - d0, t1 = d2 - d1, t2 = d3 - d2;
+    const double s0 = fma(3.0, d1, -d0), s1 = d1 + d2, s2 = fma(-3.0, d2, d3);
+    const double e4 = 4.0 * eps, k133 = 13.0 / 3.0;
+    const double e0 = fma(s0, s0, fma(k133 * t0, t0, e4));
+    const double e1 = fma(s1, s1, fma(k133 * t1, t1, e4));
+    const double e2 = fma(s2, s2, fma(k133 * t2, t2, e4));
+    const double E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+    const double a0 = E1 * E2, a1 = E0 * E2, a2 = E0 * E1;
+    const double c0 = fma(5.0 / 60.0, d1, (-2.0 / 60.0) * d0);
+    const double c1 = fma(0.2, d2, 0.1 * d1);
+    const double c2 = fma(0.2, d2, -0.05 * d3);
+    const double num = fma(a0, c0, fma(a1, c1, a2 * c2));
+    const double den = fma(0.1, a0, fma(0.6, a1, 0.3 * a2));
+    const double iden = 1.0 / den;
+    const double R = pb * iden;
+    const double psi = num * iden;             // Phi - v2
+    // adjoints (all times pb)
+    const double gc0 = a0 * R, gc1 = a1 * R, gc2 = a2 * R;
+    const double gA0 = R * fma(-0.1, psi, c0), gA1 = R * fma(-0.6, psi, c1), gA2 = R * fma(-0.3, psi, c2);
+    const double gE0 = fma(gA1, E2, gA2 * E1), gE1 = fma(gA0, E2, gA2 * E0), gE2 = fma(gA0, E1, gA1 * E0);
+    const double ge0 = 2.0 * e0 * gE0, ge1 = 2.0 * e1 * gE1, ge2 = 2.0 * e2 * gE2;
+    const double gs0 = 2.0 * s0 * ge0, gs1 = 2.0 * s1 * ge1, gs2 = 2.0 * s2 * ge2;
+    const double k263 = 26.0 / 3.0;
+    const double gt0 = k263 * t0 * ge0, gt1 = k263 * t1 * ge1, gt2 = k263 * t2 * ge2;
+    const double gd0 = -gs0 - gt0 + (-2.0 / 60.0) * gc0;
+    const double gd1 = fma(3.0, gs0, gs1) + gt0 - gt1 + fma(5.0 / 60.0, gc0, 0.1 * gc1);
+    const double gd2 = fma(-3.0, gs2, gs1) + gt1 - gt2 + fma(0.2, gc1, 0.2 * gc2);
+    const double gd3 = gs2 + gt2 - 0.05 * gc2;
+    g[0] = -gd0;
+    g[1] = gd0 - gd1;
+    g[2] = pb + gd1 - gd2;
+    g[3] = gd2 - gd3;
+    g[4] = gd3;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -446,8 +457,9 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
 // average and Eq. (F1) convolution (correlations with the same taps), the
 // chain (n, u, T, q) <- raw sums, and
 // out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
-__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m) {
-    return 5 * (size_t)(Z + 2 * m) + (size_t)kNumMoments * Z;
+__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m, int M) {
+    return 5 * (size_t)(Z + 2 * m) + (size_t)kNumMoments * Z + (size_t)(Z + 4 * m) + (size_t)(Z + 2 * M) +
+           (size_t)(Z + 2 * m + 4) + 2 * (size_t)(Z + 4);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -466,6 +478,12 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     double* sT = sn + HW;
     double* schi = sT + HW;
     double* sb = schi + HW;        // [kNumMoments][Z] raw-sum adjoints of the tile
+    // inputs read by the tap loops, staged once (all threads, coalesced):
+    double* sS0 = sb + kNumMoments * Z;    // S0 on [i0 - 2m, i0 + nz + 2m)
+    double* sF1 = sS0 + (Z + 4 * m);       // force adjoint on [i0 - M, i0 + nz + M)
+    double* sDX = sF1 + (Z + 2 * M);       // X-gradient adjoint on [i0 - m - 2, i0 + nz + m + 2)
+    double* sDU = sDX + (Z + 2 * m + 4);   // u- and T-gradient adjoints on [i0 - 2, i0 + nz + 2)
+    double* sDT = sDU + (Z + 4);
     const double* ftap = taps + sd.tap_off;
     const double* mtap = ftap + 2 * M + 1;
     const double inv12 = sd.inv_dx / 12.0;
@@ -473,21 +491,32 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
     const double* S2 = mom + MOM_S2 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    auto d4t = [&](int which, int i) {
-        const double* g = nadj + which * NN + sd.node_off;
-        return (g[gidx(i + 2, nx, bc)] - 8.0 * g[gidx(i + 1, nx, bc)] + 8.0 * g[gidx(i - 1, nx, bc)] -
-                g[gidx(i - 2, nx, bc)]) * inv12;
-    };
+    const double* gF1 = nadj + AD_F1 * NN + sd.node_off;
+    const double* gDX = nadj + AD_DX * NN + sd.node_off;
+    const double* gDU = nadj + AD_DU * NN + sd.node_off;
+    const double* gDT = nadj + AD_DT * NN + sd.node_off;
+    for (int c = threadIdx.x; c < nz + 4 * m; c += blockDim.x) sS0[c] = S0[gidx(it.i0 - 2 * m + c, nx, bc)];
+    for (int c = threadIdx.x; c < nz + 2 * M; c += blockDim.x) sF1[c] = gF1[gidx(it.i0 - M + c, nx, bc)];
+    for (int c = threadIdx.x; c < nz + 2 * m + 4; c += blockDim.x) sDX[c] = gDX[gidx(it.i0 - m - 2 + c, nx, bc)];
+    for (int c = threadIdx.x; c < nz + 4; c += blockDim.x) {
+        const int i = gidx(it.i0 - 2 + c, nx, bc);
+        sDU[c] = gDU[i];
+        sDT[c] = gDT[i];
+    }
+    __syncthreads();
+    // transposed fourth-order difference at staged position p (value at p)
+    auto d4t = [&](const double* g, int p) { return (g[p + 2] - 8.0 * g[p + 1] + 8.0 * g[p - 1] - g[p - 2]) * inv12; };
     for (int c = threadIdx.x; c < nz + 2 * m; c += blockDim.x) {
         const int i = gidx(it.i0 - m + c, nx, bc);
         double n = S0[i], u = S1[i] / n;
         double T = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) / n - 0.5 * u * u);
         double nbF = 0.0;
-        for (int j = -m; j <= m; ++j) nbF = fma(mtap[j + m], S0[gidx(i + j, nx, bc)], nbF);
+        const double* s0c = sS0 + c + m;               // S0 at node i0 - m + c
+        for (int j = -m; j <= m; ++j) nbF = fma(mtap[j + m], s0c[j], nbF);
         double eta = sd.eta_coef * nbF, om = 1.0 - eta;
         double chi = (2.0 - eta) / (2.0 * om * om * om);
         long long o = sd.node_off + i;
-        double Xb = nadj[AD_X * NN + o] + d4t(AD_DX, i);
+        double Xb = nadj[AD_X * NN + o] + d4t(sDX, c + 2);
         double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
         double dchi = (5.0 - 2.0 * eta) / (2.0 * om * om * om * om);
         sXb[c] = Xb;
@@ -500,13 +529,13 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     for (int t = threadIdx.x; t < nz; t += blockDim.x) {
         const int i = it.i0 + t, c = t + m;
         long long o = sd.node_off + i;
-        const double* f1b = nadj + AD_F1 * NN + sd.node_off;
         double n = sn[c], T = sT[c], chi = schi[c], Xb = sXb[c];
         double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
         for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], sNb[c - j], nb);
-        for (int j = -M; j <= M; ++j) nb = fma(ftap[j + M], f1b[gidx(i - j, nx, bc)], nb);
-        double ub = nadj[AD_U * NN + o] + d4t(AD_DU, i);
-        double Tb = nadj[AD_T * NN + o] + d4t(AD_DT, i) + Xb * n * n * chi;
+        const double* f1c = sF1 + t + M;               // force adjoint at node i
+        for (int j = -M; j <= M; ++j) nb = fma(ftap[j + M], f1c[-j], nb);
+        double ub = nadj[AD_U * NN + o] + d4t(sDU, t + 2);
+        double Tb = nadj[AD_T * NN + o] + d4t(sDT, t + 2) + Xb * n * n * chi;
         double qb = nadj[AD_Q * NN + o];
         double S0v = S0[i], S1v = S1[i], S2v = S2[i], G0v = G0[i];
         double u = S1v / n;
@@ -610,7 +639,7 @@ adj_phi_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ ph
 // ---------------------------------------------------------------------------
 size_t adj_smem_bytes(int Q, int Z, int M) { return adj_smem_doubles(Q, Z, M) * sizeof(double); }
 
-size_t adj_moments_smem_bytes(int Z, int m) { return adj_moments_smem_doubles(Z, m) * sizeof(double); }
+size_t adj_moments_smem_bytes(int Z, int m, int M) { return adj_moments_smem_doubles(Z, m, M) * sizeof(double); }
 
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes) {
     cudaError_t e = cudaFuncSetAttribute(adj_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

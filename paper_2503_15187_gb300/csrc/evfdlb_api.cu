@@ -47,7 +47,7 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
 void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
                    long long NN, double* out);
 size_t adj_smem_bytes(int Q, int Z, int M);
-size_t adj_moments_smem_bytes(int Z, int m);
+size_t adj_moments_smem_bytes(int Z, int m, int M);
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
 void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
                       const WorkItem* items, const double* tables, const double* taps, const double* src,
@@ -246,7 +246,7 @@ evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
         for (int s = 0; s < c->nbatch; ++s) phi[s] = c->params[s].phi_a;
         double* dphi = c->adj + 4 * 2 * c->NF + 15 * c->NN;
         TRY_CUDA(cudaMemcpy(dphi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
-        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax), adj_moments_smem_bytes(kZMax, c->mmax)));
+        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax), adj_moments_smem_bytes(kZMax, c->mmax, c->Mmax)));
     }
     if (!c->seg && c->ckpt_every > 0) {
         size_t nst = 3 * (size_t)c->ckpt_every + 1;
@@ -271,7 +271,7 @@ void adj_stage(evfdlb_ctx* c, const double* src, const double* mom, const double
     double* nadj = c->adj + 4 * 2 * c->NF;
     double* phis = nadj + 14 * c->NN;
     launch_adj_stage((int)c->items_h.size(), adj_smem_bytes(c->Qmax, c->Z, c->Mmax),
-                     adj_moments_smem_bytes(c->Z, c->mmax), c->user, c->slabs, c->items, c->tables, c->taps, src,
+                     adj_moments_smem_bytes(c->Z, c->mmax, c->Mmax), c->user, c->slabs, c->items, c->tables, c->taps, src,
                      mom, ybar, acc_in, acc_out, out, nadj, phis, c->NF, c->NN, ca, cb, use_dt, cc, cacc, cy, c->Z,
                      c->err);
 }
