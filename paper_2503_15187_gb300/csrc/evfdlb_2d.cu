@@ -484,39 +484,51 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 }
 
 // ---------------------------------------------------------------------------
-// k2_adv: a 32x16 node tile and a run of velocity planes: WENO-5 faces along
-// x and y, the right-hand side and the Shu-Osher combine
-//   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
+// k2_adv: WENO-5 faces along x and y, the right-hand side and the RK combine.
 // ---------------------------------------------------------------------------
+// One WENO-5 face in difference form (the algebra of the 1D kernels): with
+// d_i = v_{i+1} - v_i, the candidates are v2 plus corrections in d, the
+// smoothness indicators 4 (eps + beta_r) = s_r^2 + 13/3 t_r^2 + 4 eps from
+// first and second differences, and the linear weights are folded into the
+// corrections; eps4 = 4 eps.
 template <typename R>
-__device__ __forceinline__ R weno5_2(R v0, R v1, R v2, R v3, R v4, R eps) {
-    const R k6 = R(1) / R(6), k1312 = R(13) / R(12), qr = R(0.25);
-    R q0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * k6;
-    R q1 = (-v1 + R(5) * v2 + R(2) * v3) * k6;
-    R q2 = (R(2) * v2 + R(5) * v3 - v4) * k6;
-    R t0 = v0 - R(2) * v1 + v2, s0 = v0 - R(4) * v1 + R(3) * v2;
-    R t1 = v1 - R(2) * v2 + v3, s1 = v1 - v3;
-    R t2 = v2 - R(2) * v3 + v4, s2 = R(3) * v2 - R(4) * v3 + v4;
-    R e0 = eps + fma(k1312 * t0, t0, qr * s0 * s0);
-    R e1 = eps + fma(k1312 * t1, t1, qr * s1 * s1);
-    R e2 = eps + fma(k1312 * t2, t2, qr * s2 * s2);
-    e0 *= e0;
-    e1 *= e1;
-    e2 *= e2;
-    R a0 = R(0.1) * (e1 * e2), a1 = R(0.6) * (e0 * e2), a2 = R(0.3) * (e0 * e1);
-    R num = fma(a0, q0, fma(a1, q1, a2 * q2)), den = a0 + a1 + a2;
+__device__ __forceinline__ R weno5_2(R v0, R v1, R v2, R v3, R v4, R eps4) {
+    const R d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3;
+    const R t0 = d1 - d0, t1 = d2 - d1, t2 = d3 - d2;
+    const R s0 = fma(R(3), d1, -d0), s1 = d1 + d2, s2 = fma(R(-3), d2, d3);
+    const R k133 = R(13.0 / 3.0);
+    const R e0 = fma(s0, s0, fma(k133 * t0, t0, eps4));
+    const R e1 = fma(s1, s1, fma(k133 * t1, t1, eps4));
+    const R e2 = fma(s2, s2, fma(k133 * t2, t2, eps4));
+    const R E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+    const R a0 = E1 * E2, a1 = E0 * E2, a2 = E0 * E1;
+    const R c0 = fma(R(5.0 / 60.0), d1, R(-2.0 / 60.0) * d0);
+    const R c1 = fma(R(0.2), d2, R(0.1) * d1);
+    const R c2 = fma(R(0.2), d2, R(-0.05) * d3);
+    const R num = fma(a0, c0, fma(a1, c1, a2 * c2));
+    const R den = fma(R(0.1), a0, fma(R(0.6), a1, R(0.3) * a2));
     // FP32: the fast reciprocal-based quotient (2 ulp) is far inside the FP32
     // variant's error budget; FP64 keeps the IEEE quotient
-    if constexpr (std::is_same<R, float>::value) return __fdividef(num, den);
-    else return num / den;
+    if constexpr (std::is_same<R, float>::value) return v2 + __fdividef(num, den);
+    else return v2 + num / den;
 }
 
+// k2_adv: a 32x16 node tile and a run of velocity planes.  Per plane the
+// halo (tile +-3) is staged in shared memory (its global offsets computed
+// once per CTA), then 16 x 33 x-faces and 17 x 32 y-faces are formed as one
+// list of 1072 faces over the 256 threads, the same instructions for both
+// directions and both upwind signs (a face is a base pointer, a stride and a
+// walk direction), then the right-hand side and the Shu-Osher combine
+//   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
 template <typename R>
 __global__ void __launch_bounds__(256)
 k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* base, R* out,
        const R* __restrict__ RL, double* rhs_out, double alpha, double beta, int mode) {
-    constexpr int WX = kAdvX + 6, WY = kAdvY + 6;
-    __shared__ R Hs[WY * WX];
+    constexpr int WX = kAdvX + 6, WY = kAdvY + 6, NH = WX * WY;
+    constexpr int NHR = (NH + 255) / 256;                   // halo loads per thread
+    constexpr int NXF = kAdvY * kAdvX, NYF = kAdvY * kAdvX;  // regular x and y faces
+    constexpr int NF_ALL = NXF + NYF + kAdvY + kAdvX;        // + face 32 of each row, + face row 16
+    __shared__ R Hs[NH];
     __shared__ R FX[kAdvY * (kAdvX + 1)];
     __shared__ R FY[(kAdvY + 1) * kAdvX];
     __shared__ long long rowoff[WY];
@@ -531,46 +543,46 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
         if (e < WY) rowoff[e] = (long long)wrapi(y0 - 3 + e, ny) * nx;
         else coloff[e - WY] = wrapi(x0 - 3 + (e - WY), nx);
     }
-    const R eps = (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
+    __syncthreads();
+    long long hoff[NHR];
+#pragma unroll
+    for (int j = 0; j < NHR; ++j) {
+        const int e = threadIdx.x + 256 * j;
+        hoff[j] = (e < NH) ? rowoff[e / WX] + coloff[e % WX] : 0;
+    }
+    const R eps4 = R(4) * (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
     const bool with_base = (alpha != 0.0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
     for (int plane = p0; plane < p1; ++plane) {
         const int d = plane / K, k = plane % K;
         const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
         const R* h = src + d * NF + (long long)k * N;
-        __syncthreads();   // previous plane's faces consumed; halo offsets written
-        for (int e = threadIdx.x; e < WY * WX; e += blockDim.x) {
-            int cy = e / WX, cx = e % WX;
-            Hs[e] = h[rowoff[cy] + coloff[cx]];
+        __syncthreads();   // previous plane's faces and halo consumed
+#pragma unroll
+        for (int j = 0; j < NHR; ++j) {
+            const int e = threadIdx.x + 256 * j;
+            if (e < NH) Hs[e] = h[hoff[j]];
         }
         __syncthreads();
-        // x faces: face f of row r lies between tile columns f-1 and f; warp w
-        // owns rows 2w and 2w+1 (lane = face, lane 0 also face 32)
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int rr = 0; rr < kAdvY / 8; ++rr) {
-            const int r = warp * (kAdvY / 8) + rr;
-            const R* row = Hs + (r + 3) * WX;
-            for (int f = lane; f <= kAdvX; f += 32) {
-                R v;
-                if (vx > R(0)) v = weno5_2<R>(row[f], row[f + 1], row[f + 2], row[f + 3], row[f + 4], eps);
-                else if (vx < R(0)) v = weno5_2<R>(row[f + 5], row[f + 4], row[f + 3], row[f + 2], row[f + 1], eps);
-                else v = 0;
-                FX[r * (kAdvX + 1) + f] = v;
-            }
-        }
-        // y faces: face f of column c lies between tile rows f-1 and f; warp w
-        // owns face rows w, w + 8, ... (lane = column)
-        for (int f = warp; f <= kAdvY; f += 8) {
-            const R* col = Hs + lane + 3;
-            R v;
-            if (vy > R(0))
-                v = weno5_2<R>(col[f * WX], col[(f + 1) * WX], col[(f + 2) * WX], col[(f + 3) * WX],
-                               col[(f + 4) * WX], eps);
-            else if (vy < R(0))
-                v = weno5_2<R>(col[(f + 5) * WX], col[(f + 4) * WX], col[(f + 3) * WX], col[(f + 2) * WX],
-                               col[(f + 1) * WX], eps);
-            else v = 0;
-            FY[f * kAdvX + lane] = v;
+        for (int e = threadIdx.x; e < NF_ALL; e += blockDim.x) {
+            // face e: x face f of row r lies between tile columns f-1 and f,
+            // y face f of column c between tile rows f-1 and f
+            int r, f, c;
+            bool xf;
+            if (e < NXF) { xf = true; r = e >> 5; f = e & 31; c = 0; }
+            else if (e < NXF + NYF) { xf = false; f = (e - NXF) >> 5; c = e & 31; r = 0; }
+            else if (e < NXF + NYF + kAdvY) { xf = true; r = e - NXF - NYF; f = kAdvX; c = 0; }
+            else { xf = false; f = kAdvY; c = e - NXF - NYF - kAdvY; r = 0; }
+            const R v = xf ? vx : vy;
+            const int stride = xf ? 1 : WX;
+            const R* b = xf ? Hs + (r + 3) * WX + f : Hs + f * WX + c + 3;   // upwind v0 for v > 0
+            const bool pos = v >= R(0);
+            const R* p = pos ? b : b + 5 * stride;
+            const int st = pos ? stride : -stride;
+            const R fv = weno5_2<R>(p[0], p[st], p[2 * st], p[3 * st], p[4 * st], eps4);
+            if (xf) FX[r * (kAdvX + 1) + f] = fv;
+            else FY[f * kAdvX + c] = fv;
         }
         __syncthreads();
         const int x = x0 + lane;
