@@ -296,24 +296,40 @@ k2_fields(Slab2 s, const double* __restrict__ mom, const int* __restrict__ ft_of
 // n sum_ab P_ab mu^a_l(u_x) mu^b_m(u_y).
 // ---------------------------------------------------------------------------
 // Shared layout of k2_coll: per distribution and node a Q x Q matrix with
-// rows padded to kRow (a multiple of 4 elements, so that a row is float4 /
-// double2 aligned), node stride padded by 4 so that the eight nodes of a
-// group fall in different banks.
-constexpr int kRow = 16;
+// rows padded to kRow = 20 elements (a multiple of 4, so that rows are
+// 16-byte aligned for four-wide loads, and 80 bytes apart, so that rows 4
+// apart fall 16 banks apart: the eight threads of a quarter warp then read
+// distinct banks in both transform directions), node stride padded by 4 so
+// that the eight nodes of a group fall in different banks for the scalar
+// state loads.
+constexpr int kRow = 20;
 __host__ __device__ constexpr int padded_q(int Q) { return (Q + 3) & ~3; }
 __host__ __device__ constexpr int node_stride(int Q) { return padded_q(Q) * kRow + 4; }
 
 template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
     size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
-    return sizeof(R) * (2 * (size_t)Q * kRow + 3 * (size_t)Q + 3 * X + kNumFld2 * kNB + 4 * (size_t)Q * kNB +
+    return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 3 * X + kNumFld2 * kNB +
+                        4 * (size_t)Q * kNB +
                         2 * 4 * (size_t)Q * kNB);
+}
+
+// Four consecutive elements of a 16-byte aligned shared row.
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
 // Out[i][j] = sum_k Lt[k][i] In[k][j]  (left contraction, Lt = transposed left matrix)
 // or         sum_k In[i][k] Rt[k][j]  (right contraction, Rt = transposed right matrix)
 // for the matrices of one (distribution, node); each thread forms a 4 x 4
-// block from four-wide loads of a row of Lt (or Rt) and of In.
+// block from four-wide row loads: the left form walks k one row of Lt and
+// In at a time, the right form four k at a time (four rows of In, four rows
+// of Rt; the padded rows and columns Q .. Qp-1 are zero).
 template <typename R, bool LEFT, int Q>
 __device__ __forceinline__ void block_transform(const R* __restrict__ M, const R* __restrict__ In, R* __restrict__ Out,
                                                 int i0, int j0) {
@@ -322,20 +338,33 @@ __device__ __forceinline__ void block_transform(const R* __restrict__ M, const R
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    if constexpr (LEFT) {
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        R m[4], x[4];
-        if (LEFT) {
-            for (int a = 0; a < 4; ++a) m[a] = M[k * kRow + i0 + a];       // Lt[k][i0 + a]
-            for (int b = 0; b < 4; ++b) x[b] = In[k * kRow + j0 + b];      // In[k][j0 + b]
-        } else {
-            for (int a = 0; a < 4; ++a) m[a] = In[(i0 + a) * kRow + k];    // In[i0 + a][k]
-            for (int b = 0; b < 4; ++b) x[b] = M[k * kRow + j0 + b];       // Rt[k][j0 + b]
+        for (int k = 0; k < Q; ++k) {
+            R m[4], x[4];
+            load4(M + k * kRow + i0, m);       // Lt[k][i0 .. i0+3]
+            load4(In + k * kRow + j0, x);      // In[k][j0 .. j0+3]
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a], x[b], acc[a][b]);
         }
+    } else {
+        constexpr int Qp = padded_q(Q);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int k = 0; k < Qp; k += 4) {
+            R m[4][4], x[4][4];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a], x[b], acc[a][b]);
+            for (int a = 0; a < 4; ++a) load4(In + (i0 + a) * kRow + k, m[a]);   // In[i0 + a][k .. k+3]
+#pragma unroll
+            for (int q = 0; q < 4; ++q) load4(M + (k + q) * kRow + j0, x[q]);    // Rt[k + q][j0 .. j0+3]
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a][q], x[q][b], acc[a][b]);
+        }
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -346,28 +375,28 @@ __device__ __forceinline__ void block_transform(const R* __restrict__ M, const R
 template <typename R, int Q>
 __global__ void __launch_bounds__(256)
 k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* __restrict__ fld, R* __restrict__ RL) {
-    extern __shared__ double smc[];
+    extern __shared__ __align__(16) double smc[];
     constexpr int K = Q * Q, NS = node_stride(Q), Qp = padded_q(Q);
     const long long N = s.N, NF = (long long)K * N;
     const long long i0 = (long long)blockIdx.x * kNB;
     const int nb = (int)min((long long)kNB, N - i0);
     TableLayout L(Q);
     R* Pt = reinterpret_cast<R*>(smc);     // Pt[j][l] = psi_l(xi_j)       (transposed analysis table)
-    R* St = Pt + Q * kRow;                 // St[l][k] = w_k psi_l(xi_k)   (transposed synthesis table)
-    R* r1 = St + Q * kRow;
-    R* r2 = r1 + Q;
-    R* r3 = r2 + Q;
-    R* X0 = r3 + Q;                        // [2][kNB] matrices, node stride NS
+    R* St = Pt + Qp * kRow;                // St[l][k] = w_k psi_l(xi_k)   (transposed synthesis table)
+    R* r1 = St + Qp * kRow;
+    R* r2 = r1 + Qp;
+    R* r3 = r2 + Qp;
+    R* X0 = r3 + Qp;                       // [2][kNB] matrices, node stride NS (16-byte aligned)
     R* X1 = X0 + 2 * kNB * NS;
     R* X2 = X1 + 2 * kNB * NS;
     R* sc = X2 + 2 * kNB * NS;             // [kNumFld2][kNB]
     R* mux = sc + kNumFld2 * kNB;          // [4][Q][kNB]
     R* Vy = mux + 4 * Q * kNB;             // [2][4][Q][kNB]
     auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
-    for (int e = threadIdx.x; e < Q * kRow; e += blockDim.x) {
+    for (int e = threadIdx.x; e < Qp * kRow; e += blockDim.x) {
         int r = e / kRow, c = e % kRow;
-        Pt[e] = (c < Q) ? rtab[L.P + c * Q + r] : R(0);
-        St[e] = (c < Q) ? rtab[L.S + c * Q + r] : R(0);
+        Pt[e] = (c < Q && r < Q) ? rtab[L.P + c * Q + r] : R(0);
+        St[e] = (c < Q && r < Q) ? rtab[L.S + c * Q + r] : R(0);
     }
     for (int e = threadIdx.x; e < Q; e += blockDim.x) {
         r1[e] = rtab[L.r1 + e];
