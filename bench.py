@@ -99,6 +99,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def tuned_tile(p, n0, T, stream):
+    """Node tile of the stage kernels picked by the project's autotuner
+    (autotune.py: every candidate timed with CUDA events on a scratch context
+    of the same slab); results do not depend on the tile."""
+    import numpy as np
+    from paper_2503_15187_gb300 import autotune as AT
+    best, _ = AT.autotune(p, n0, np.zeros(NZ), np.full(NZ, T), cache=None, stream=stream)
+    return best
+
+
 def build_workload(ev, W):
     p = ev.Params(nx=NZ, dx=DZ, Q=Q, bc=ev.BC_OUTFLOW)
     T = T_RATIO * ev.critical_T(p)
@@ -118,6 +128,7 @@ def run_ours(args, rank, world):
     p, T, n0 = build_workload(ev, W)
     stream = torch.cuda.current_stream()
     sim = ev.Sim(p, stream=stream)
+    sim.tune(tuned_tile(p, n0, T, stream))
     sim.init(n0, np.zeros(NZ), np.full(NZ, T))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -240,6 +251,7 @@ def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)
     import torch
     p32 = dataclasses.replace(p, precision=ev.FP32)
     sim = ev.Sim(p32, stream=stream)
+    sim.tune(tuned_tile(p32, n0, T, stream))
     sim.init(n0, np.zeros(NZ), np.full(NZ, T))
     sim.step(args.warmup)
     barrier()
@@ -254,11 +266,12 @@ def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)
     sim.step(1)          # the FP64 state compared against has W + K + 1 steps (its end-to-end leg adds one)
     ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
     n32 = sim.moments(with_totals=False)[0]
+    tile = sim.tile_nodes()
     sim.close()
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32 (f64 chi, "
             "transport, gradients, conserved sums)", "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
-            "gpu_launches": 3 * args.steps}
+            "gpu_launches": 3 * args.steps, "tile_nodes": tile}
 
 
 def ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
@@ -271,6 +284,7 @@ def ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     import torch
     p2 = dataclasses.replace(p, force_model=ev.EV2)
     sim = ev.Sim(p2, stream=stream)
+    sim.tune(tuned_tile(p2, n0, T, stream))
     sim.init(n0, np.zeros(NZ), np.full(NZ, T))
     sim.step(args.warmup)
     barrier()
@@ -285,11 +299,12 @@ def ev2_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     sim.step(1)
     ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
     n2 = sim.moments(with_totals=False)[0]
+    tile = sim.tile_nodes()
     sim.close()
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f64",
             "ms_per_step": ms / args.steps, "force": "Eq. (F2), 5-point stencils",
             "max_rel_diff_n_vs_ev1": float(np.abs(n2 - n64).max() / np.abs(n64).max()),
-            "gpu_launches": 3 * args.steps}
+            "gpu_launches": 3 * args.steps, "tile_nodes": tile}
 
 
 def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
@@ -302,6 +317,7 @@ def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     import torch
     pdf = dataclasses.replace(p, precision=ev.FP64_DF)
     sim = ev.Sim(pdf, stream=stream)
+    sim.tune(tuned_tile(pdf, n0, T, stream))
     sim.init(n0, np.zeros(NZ), np.full(NZ, T))
     sim.step(args.warmup)
     barrier()
@@ -316,12 +332,13 @@ def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     sim.step(1)
     ms = maxred(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
     nd = sim.moments(with_totals=False)[0]
+    tile = sim.tile_nodes()
     sim.close()
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT,
             "dtype": "f64 (Hermite transforms as double-float pairs on the FP32 pipe)",
             "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(nd - n64).max() / np.abs(n64).max()),
-            "gpu_launches": 3 * args.steps}
+            "gpu_launches": 3 * args.steps, "tile_nodes": tile}
 
 
 def adjoint_leg(ev, W, stream, steps=200):
