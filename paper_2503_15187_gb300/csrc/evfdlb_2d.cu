@@ -542,21 +542,30 @@ __device__ __forceinline__ R weno5_2(R v0, R v1, R v2, R v3, R v4, R eps4) {
     else return v2 + num / den;
 }
 
+// The five stencil values of a face from a shared-memory pointer and a
+// compile-time stride: upwind for v >= 0 (q[0] .. q[4S]), mirrored for v < 0
+// (q[5S] .. q[S]).  The sign is uniform over a plane, so the branch is too.
+template <typename R, int S>
+__device__ __forceinline__ R face_at(const R* q, bool pos, R eps4) {
+    return pos ? weno5_2<R>(q[0], q[S], q[2 * S], q[3 * S], q[4 * S], eps4)
+               : weno5_2<R>(q[5 * S], q[4 * S], q[3 * S], q[2 * S], q[S], eps4);
+}
+
 // k2_adv: a 32x16 node tile and a run of velocity planes.  Per plane the
 // halo (tile +-3) is staged in shared memory (its global offsets computed
-// once per CTA), then 16 x 33 x-faces and 17 x 32 y-faces are formed as one
-// list of 1072 faces over the 256 threads, the same instructions for both
-// directions and both upwind signs (a face is a base pointer, a stride and a
-// walk direction), then the right-hand side and the Shu-Osher combine
+// once per CTA); warp w forms the x faces of rows 2w, 2w+1 and the y faces
+// of face rows 2w, 2w+1 (lane = face or column); the last x face of each
+// row and the last y-face row go to warps 0 and 1.  Stencil offsets are
+// compile-time constants and the upwind branch is uniform per plane.  Then
+// the right-hand side and the Shu-Osher combine
 //   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
 k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* base, R* out,
        const R* __restrict__ RL, double* rhs_out, double alpha, double beta, int mode) {
     constexpr int WX = kAdvX + 6, WY = kAdvY + 6, NH = WX * WY;
     constexpr int NHR = (NH + 255) / 256;                   // halo loads per thread
-    constexpr int NXF = kAdvY * kAdvX, NYF = kAdvY * kAdvX;  // regular x and y faces
-    constexpr int NF_ALL = NXF + NYF + kAdvY + kAdvX;        // + face 32 of each row, + face row 16
+    constexpr int RPW = kAdvY / 8;                          // rows per warp
     __shared__ R Hs[NH];
     __shared__ R FX[kAdvY * (kAdvX + 1)];
     __shared__ R FY[(kAdvY + 1) * kAdvX];
@@ -582,11 +591,23 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
     const R eps4 = R(4) * (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
     const bool with_base = (alpha != 0.0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // output nodes of this thread (rows warp*RPW + rr, column lane) and
+    // their offsets in a velocity plane
+    const int x = x0 + lane;
+    long long ooff[RPW];
+    bool oval[RPW];
+#pragma unroll
+    for (int rr = 0; rr < RPW; ++rr) {
+        const int y = y0 + warp * RPW + rr;
+        oval[rr] = (x < nx && y < ny);
+        ooff[rr] = (long long)y * nx + x;
+    }
     const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
     for (int plane = p0; plane < p1; ++plane) {
         const int d = plane / K, k = plane % K;
         const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
-        const R* h = src + d * NF + (long long)k * N;
+        const long long pbase = d * NF + (long long)k * N;
+        const R* h = src + pbase;
         __syncthreads();   // previous plane's faces and halo consumed
 #pragma unroll
         for (int j = 0; j < NHR; ++j) {
@@ -594,31 +615,28 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             if (e < NH) Hs[e] = h[hoff[j]];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < NF_ALL; e += blockDim.x) {
-            // face e: x face f of row r lies between tile columns f-1 and f,
-            // y face f of column c between tile rows f-1 and f
-            int r, f, c;
-            bool xf;
-            if (e < NXF) { xf = true; r = e >> 5; f = e & 31; c = 0; }
-            else if (e < NXF + NYF) { xf = false; f = (e - NXF) >> 5; c = e & 31; r = 0; }
-            else if (e < NXF + NYF + kAdvY) { xf = true; r = e - NXF - NYF; f = kAdvX; c = 0; }
-            else { xf = false; f = kAdvY; c = e - NXF - NYF - kAdvY; r = 0; }
-            const R v = xf ? vx : vy;
-            const int stride = xf ? 1 : WX;
-            const R* b = xf ? Hs + (r + 3) * WX + f : Hs + f * WX + c + 3;   // upwind v0 for v > 0
-            const bool pos = v >= R(0);
-            const R* p = pos ? b : b + 5 * stride;
-            const int st = pos ? stride : -stride;
-            const R fv = weno5_2<R>(p[0], p[st], p[2 * st], p[3 * st], p[4 * st], eps4);
-            if (xf) FX[r * (kAdvX + 1) + f] = fv;
-            else FY[f * kAdvX + c] = fv;
+        const bool px = vx >= R(0), py = vy >= R(0);
+#pragma unroll
+        for (int rr = 0; rr < RPW; ++rr) {
+            const int r = warp * RPW + rr;
+            // x face `lane` of row r: stencil starts at halo column lane
+            FX[r * (kAdvX + 1) + lane] = face_at<R, 1>(Hs + (r + 3) * WX + lane, px, eps4);
+            // y face row r, column lane: stencil starts at halo row r
+            FY[r * kAdvX + lane] = face_at<R, WX>(Hs + r * WX + lane + 3, py, eps4);
+        }
+        if (threadIdx.x < kAdvY) {                      // x face kAdvX of row threadIdx.x
+            const int r = threadIdx.x;
+            FX[r * (kAdvX + 1) + kAdvX] = face_at<R, 1>(Hs + (r + 3) * WX + kAdvX, px, eps4);
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kAdvX) {   // y face row kAdvY
+            const int c = threadIdx.x - 32;
+            FY[kAdvY * kAdvX + c] = face_at<R, WX>(Hs + kAdvY * WX + c + 3, py, eps4);
         }
         __syncthreads();
-        const int x = x0 + lane;
-        for (int rr = 0; rr < kAdvY / 8; ++rr) {
-            const int ty = warp * (kAdvY / 8) + rr, y = y0 + ty;
-            if (x >= nx || y >= ny) continue;
-            const long long g = d * NF + (long long)k * N + (long long)y * nx + x;
+#pragma unroll
+        for (int rr = 0; rr < RPW; ++rr) {
+            if (!oval[rr]) continue;
+            const int ty = warp * RPW + rr;
+            const long long g = pbase + ooff[rr];
             R Rv = RL[g];
             Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
             Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
