@@ -391,7 +391,7 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     R* X2 = X1 + 2 * kNB * NS;
     R* sc = X2 + 2 * kNB * NS;             // [kNumFld2][kNB]
     R* mux = sc + kNumFld2 * kNB;          // [4][Q][kNB]
-    R* Vy = mux + 4 * Q * kNB;             // [2][4][Q][kNB]
+    R* Vy = mux + 4 * Q * kNB;             // [2][4][kNB][Q]
     auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
     for (int e = threadIdx.x; e < Qp * kRow; e += blockDim.x) {
         int r = e / kRow, c = e % kRow;
@@ -456,8 +456,8 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
                         vf = fma(PF[a][b], mb[b], vf);
                         vg = fma(PG[a][b], mb[b], vg);
                     }
-                    Vy[((0 * 4 + a) * Q + l) * kNB + t] = vf;
-                    Vy[((1 * 4 + a) * Q + l) * kNB + t] = vg;
+                    Vy[((0 * 4 + a) * kNB + t) * Q + l] = vf;
+                    Vy[((1 * 4 + a) * kNB + t) * Q + l] = vg;
                 }
             }
             R mn = fma(u * rtab[L.rinv + l], m0, Tm1 * rtab[L.rr + l] * m1);
@@ -477,23 +477,25 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     // analysis along xi_y: X2[l][m] = sum_ky X1[l][ky] psi_m(xi_ky)
     if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X2, d, t), bi, bj);
     __syncthreads();
-    // coefficients (equilibria, J1, force terms) into X1
+    // coefficients (equilibria, J1, force terms) into X1: one y-order mm per
+    // thread (lanes on consecutive mm: conflict-free rows), looping over the
+    // x-order l; the y-moment factors of the thread are loop-invariant
     for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
-        const int l = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
+        const int mm = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
         const R* A = mat(X2, dd, tt);
-        R* C = mat(X1, dd, tt) + l * kRow;
-        R mx[4];
+        R* C = mat(X1, dd, tt);
+        R vy[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) mx[a] = mux[(a * Q + l) * kNB + tt];
-        const R fx = sc[F2_FX * kNB + tt] * r1[l], fy = sc[F2_FY * kNB + tt];
+        for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * Q + mm];
+        const R fx = sc[F2_FX * kNB + tt], fyr = sc[F2_FY * kNB + tt] * r1[mm];
 #pragma unroll
-        for (int mm = 0; mm < Q; ++mm) {
+        for (int l = 0; l < Q; ++l) {
             R c = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) c = fma(mx[a], Vy[((dd * 4 + a) * Q + mm) * kNB + tt], c);
-            if (l >= 1) c = fma(fx, A[(l - 1) * kRow + mm], c);
-            if (mm >= 1) c = fma(fy * r1[mm], A[l * kRow + mm - 1], c);
-            C[mm] = c;
+            for (int a = 0; a < 4; ++a) c = fma(mux[(a * Q + l) * kNB + tt], vy[a], c);
+            if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
+            if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
+            C[l * kRow + mm] = c;
         }
     }
     __syncthreads();
