@@ -309,7 +309,7 @@ __host__ __device__ constexpr int node_stride(int Q) { return padded_q(Q) * kRow
 template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
     size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
-    return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 3 * X + kNumFld2 * kNB +
+    return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 2 * X + kNumFld2 * kNB +
                         4 * (size_t)Q * kNB +
                         2 * 4 * (size_t)Q * kNB);
 }
@@ -388,8 +388,7 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     R* r3 = r2 + Qp;
     R* X0 = r3 + Qp;                       // [2][kNB] matrices, node stride NS (16-byte aligned)
     R* X1 = X0 + 2 * kNB * NS;
-    R* X2 = X1 + 2 * kNB * NS;
-    R* sc = X2 + 2 * kNB * NS;             // [kNumFld2][kNB]
+    R* sc = X1 + 2 * kNB * NS;             // [kNumFld2][kNB]
     R* mux = sc + kNumFld2 * kNB;          // [4][Q][kNB]
     R* Vy = mux + 4 * Q * kNB;             // [2][4][kNB][Q]
     auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
@@ -405,7 +404,7 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     }
     // state of the group as [d][node][kx][ky] (ky contiguous, rows of kRow);
     // rows and columns Q .. Qp-1 of every matrix stay zero
-    for (int e = threadIdx.x; e < 3 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
+    for (int e = threadIdx.x; e < 2 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
         int t = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
@@ -471,19 +470,23 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     const bool active = item < 2 * kNB;
     const int d = item / kNB, t = item % kNB;
     const int bi = 4 * (blk / (Qp / 4)), bj = 4 * (blk % (Qp / 4));
+    // Two buffers: the state is needed only by the first transform, since
+    // -nu h is synthesised from -nu times its own analysis (the tensor
+    // Gauss-Hermite transform of order Q per axis is invertible).
     // analysis along xi_x: X1[l][ky] = sum_kx psi_l(xi_kx) X0[kx][ky]
     if (active) block_transform<R, true, Q>(Pt, mat(X0, d, t), mat(X1, d, t), bi, bj);
     __syncthreads();
-    // analysis along xi_y: X2[l][m] = sum_ky X1[l][ky] psi_m(xi_ky)
-    if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X2, d, t), bi, bj);
+    // analysis along xi_y: X0[l][m] = sum_ky X1[l][ky] psi_m(xi_ky)
+    if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X0, d, t), bi, bj);
     __syncthreads();
-    // coefficients (equilibria, J1, force terms) into X1: one y-order mm per
+    // coefficients (relaxation -nu a, equilibria, J1, force terms) into X1: one y-order mm per
     // thread (lanes on consecutive mm: conflict-free rows), looping over the
     // x-order l; the y-moment factors of the thread are loop-invariant
     for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
         const int mm = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
-        const R* A = mat(X2, dd, tt);
+        const R* A = mat(X0, dd, tt);
         R* C = mat(X1, dd, tt);
+        const R mnu = -sc[F2_NU * kNB + tt];
         R vy[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * Q + mm];
@@ -495,22 +498,23 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             for (int a = 0; a < 4; ++a) c = fma(mux[(a * Q + l) * kNB + tt], vy[a], c);
             if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
             if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
+            c = fma(mnu, A[l * kRow + mm], c);
             C[l * kRow + mm] = c;
         }
     }
     __syncthreads();
-    // synthesis along xi_x: X2[kx][m] = sum_l w_kx psi_l(xi_kx) X1[l][m]
-    if (active) block_transform<R, true, Q>(St, mat(X1, d, t), mat(X2, d, t), bi, bj);
+    // synthesis along xi_x: X0[kx][m] = sum_l w_kx psi_l(xi_kx) X1[l][m]
+    if (active) block_transform<R, true, Q>(St, mat(X1, d, t), mat(X0, d, t), bi, bj);
     __syncthreads();
-    // synthesis along xi_y: X1[kx][ky] = sum_m X2[kx][m] w_ky psi_m(xi_ky)
-    if (active) block_transform<R, false, Q>(St, mat(X2, d, t), mat(X1, d, t), bi, bj);
+    // synthesis along xi_y: X1[kx][ky] = sum_m X0[kx][m] w_ky psi_m(xi_ky)
+    if (active) block_transform<R, false, Q>(St, mat(X0, d, t), mat(X1, d, t), bi, bj);
     __syncthreads();
-    // the local right-hand side -nu h + sum S S c
+    // the local right-hand side -nu h + sum S S c (both in X1)
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
         int tt = e % kNB, k = (e / kNB) % K, dd = e / (kNB * K);
         if (tt >= nb) continue;
         const int off = (k / Q) * kRow + k % Q;
-        RL[dd * NF + (long long)k * N + i0 + tt] = fma(-sc[F2_NU * kNB + tt], mat(X0, dd, tt)[off], mat(X1, dd, tt)[off]);
+        RL[dd * NF + (long long)k * N + i0 + tt] = mat(X1, dd, tt)[off];
     }
 }
 
