@@ -18,7 +18,12 @@ namespace evfdlb {
 
 constexpr int kQMax = 32;          // largest Gauss-Hermite order of a slab
 constexpr int kZMax = 64;          // largest node tile of one CTA
-constexpr int kThreads = 256;      // threads of the stage kernels
+constexpr int kThreads = 256;      // threads of the per-tile kernels
+// Threads of the RK-stage kernel (warp 0 forms the node work): the FP32
+// variant's per-velocity work is cheap and latency-bound, so it runs 16
+// warps per tile; the FP64 forms are FP64-pipe-bound and run 8.
+template <typename R> struct StageThreads { static constexpr int value = 256; };
+template <> struct StageThreads<float> { static constexpr int value = 512; };
 constexpr int kNumMoments = 6;     // raw moment sums kept per node
 constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
 

@@ -55,7 +55,7 @@ namespace evfdlb {
 // pairs on the FP32 pipe (state tile split into pairs once per stage in a
 // block after the Hermite moments), everything else as in the FP64 kernel.
 template <typename R, bool DF = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(StageThreads<R>::value, 1)
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
@@ -395,7 +395,7 @@ void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* s
                      const double* tables, const double* dftab, const double* taps, const double* src,
                      const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
                      long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<double, true><<<nitems, kThreads, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
+    stage_kernel<double, true><<<nitems, StageThreads<double>::value, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
                                                                out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
                                                                mode, Z, err);
 }
@@ -438,11 +438,11 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err) {
     if (prec == EVFDLB_FP32)
-        stage_kernel<float><<<nitems, kThreads, smem, st>>>(
+        stage_kernel<float><<<nitems, StageThreads<float>::value, smem, st>>>(
             slabs, items, tables, (const float*)rtab, taps, (const float*)rtaps, (const float*)src,
             (const float*)base, (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
     else
-        stage_kernel<double><<<nitems, kThreads, smem, st>>>(
+        stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
             slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps, (const double*)src,
             (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
@@ -452,7 +452,7 @@ void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slab
                   const double* tables, const double* taps, const double* src, const double* base,
                   double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
                   double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<double><<<nitems, kThreads, smem, st>>>(slabs, items, tables, tables, taps, taps, src, base, out,
+    stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(slabs, items, tables, tables, taps, taps, src, base, out,
                                                          out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
