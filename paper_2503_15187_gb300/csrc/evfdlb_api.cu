@@ -44,8 +44,9 @@ void launch_convert_to_f32(cudaStream_t st, const double* in, float* out, long l
 void launch_convert_to_f64(cudaStream_t st, const float* in, double* out, long long n);
 void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
                     double* q);
-void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
-                   long long NN, double* out);
+void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                   const WorkItem* items, const double* taps, const double* mom, long long NN, double* part,
+                   double* out);
 size_t adj_smem_bytes(int Q, int Z, int M);
 size_t adj_moments_smem_bytes(int Z, int m, int M);
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
@@ -698,7 +699,9 @@ evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, dou
             }
     if (totals) {
         double* dt = buf + EVFDLB_NFIELDS * c->NN;
-        launch_totals(c->nbatch, c->user, c->slabs, c->taps, c->mom[0], c->NN, dt);
+        double* part = dt + 4 * c->nbatch;   // 4 per work item (<= 4 NN <= 2 NF)
+        launch_totals(c->nbatch, (int)c->items_h.size(), sizeof(double) * (c->Z + 2 * c->Mmax), c->user, c->slabs,
+                      c->items, c->taps, c->mom[0], c->NN, part, dt);
         TRY_CUDA(cudaGetLastError());
         evfdlb_status s = copy_out(c, totals, dt, sizeof(double) * 4 * c->nbatch, 0);
         if (s != EVFDLB_OK) return s;

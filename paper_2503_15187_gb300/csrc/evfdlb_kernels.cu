@@ -324,31 +324,70 @@ __global__ void moments_kernel(const double* __restrict__ mom, long long NN, dou
     }
 }
 
-// Per-slab totals {mass, momentum, energy, mean-field energy}; one CTA per
-// slab, fixed-order tree reduction (deterministic).
+// Conserved totals, first pass: per work item (node tile) the sums of S0,
+// S1, S2/2 + G0 and of the mean-field energy density (1/2) n_i sum_j e_j
+// n_{i+j} (energy taps over a staged density halo), fixed-order tree.
 __global__ void __launch_bounds__(kThreads)
-totals_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ taps,
-              const double* __restrict__ mom, long long NN, double* out) {
+totals_part_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                   const double* __restrict__ taps, const double* __restrict__ mom, long long NN,
+                   double* __restrict__ part) {
+    extern __shared__ double sn[];          // S0 on [i0 - M, i0 + nz + M)
     __shared__ double red[4][kThreads];
-    const SlabDesc sd = slabs[blockIdx.x];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    const int M = sd.M, nz = it.nz;
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
     const double* S2 = mom + MOM_S2 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
     const double* etap = taps + sd.tap_off + 2 * sd.M + 1 + 2 * sd.m + 1;
+    for (int c = threadIdx.x; c < nz + 2 * M; c += blockDim.x) sn[c] = S0[gidx(it.i0 - M + c, sd.nx, sd.bc)];
+    __syncthreads();
+    // eight lanes per node split its 2M+1 energy taps (xor-shuffle sum)
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int i = threadIdx.x; i < sd.nx; i += blockDim.x) {
-        a0 += S0[i];
-        a1 += S1[i];
-        a2 += 0.5 * S2[i] + G0[i];
+    const int sub = threadIdx.x & 7;
+    for (int b = 0; b < nz; b += kThreads / 8) {
+        const int t = b + threadIdx.x / 8;
         double acc = 0.0;
-        for (int j = -sd.M; j <= sd.M; ++j) acc = fma(etap[j + sd.M], S0[gidx(i + j, sd.nx, sd.bc)], acc);
-        a3 += 0.5 * S0[i] * acc;
+        if (t < nz)
+            for (int j = -M + sub; j <= M; j += 8) acc = fma(etap[j + M], sn[t + M + j], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (t < nz && sub == 0) {
+            const int i = it.i0 + t;
+            a0 += S0[i];
+            a1 += S1[i];
+            a2 += 0.5 * S2[i] + G0[i];
+            a3 += 0.5 * sn[t + M] * acc;
+        }
     }
     red[0][threadIdx.x] = a0;
     red[1][threadIdx.x] = a1;
     red[2][threadIdx.x] = a2;
     red[3][threadIdx.x] = a3;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[4 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Per slab: its tiles' partial sums in work-list order (fixed assignment of
+// tiles to threads and a fixed tree: deterministic), times dx:
+// {mass, momentum, kinetic + internal + mean-field energy, mean-field energy}.
+__global__ void __launch_bounds__(kThreads)
+totals_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items, int nitems,
+              const double* __restrict__ part, double* out) {
+    __shared__ double red[4][kThreads];
+    const SlabDesc sd = slabs[blockIdx.x];
+    double a[4] = {0, 0, 0, 0};
+    for (int j = threadIdx.x; j < nitems; j += blockDim.x)
+        if (items[j].slab == (int)blockIdx.x)
+            for (int c = 0; c < 4; ++c) a[c] += part[4 * j + c];
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = a[c];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
@@ -526,9 +565,13 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
     moments_kernel<<<blocks, 256, 0, st>>>(mom, NN, n, u, T, q);
 }
 
-void launch_totals(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* taps, const double* mom,
-                   long long NN, double* out) {
-    totals_kernel<<<nslabs, kThreads, 0, st>>>(slabs, taps, mom, NN, out);
+// Conserved totals: per-tile partial sums (part: 4 per work item), then per
+// slab in work-list order.  smem: (Z + 2 Mmax) doubles.
+void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                   const WorkItem* items, const double* taps, const double* mom, long long NN, double* part,
+                   double* out) {
+    totals_part_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, taps, mom, NN, part);
+    totals_kernel<<<nslabs, kThreads, 0, st>>>(slabs, items, nitems, part, out);
 }
 
 }  // namespace evfdlb
