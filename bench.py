@@ -99,12 +99,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+TILE = 0   # --tile: fixed node tile for every leg (0: the autotuner's choice per leg)
+# DRAM bytes (read + write) of one stage_kernel<double> launch of this
+# workload at the one-wave 27-node tile, from `ncu --set full` of the current
+# kernel (4.49 MB read, 0 written: the outputs stay in the 129 MB L2); to be
+# re-measured whenever the stage kernel changes.
+STAGE_TRAFFIC_BYTES = 4.493824e6
+
+
 def tuned_tile(p, n0, T, stream):
-    """Node tile of the stage kernels picked by the project's autotuner
-    (autotune.py: every candidate timed with CUDA events on a scratch context
-    of the same slab); results do not depend on the tile."""
+    """Node tile of the stage kernels: --tile if given, else the one the
+    project's autotuner picks (autotune.py: every candidate timed with CUDA
+    events on a scratch context of the same slab).  Results do not depend on
+    the tile; a fixed --tile makes profiling runs reproduce the timed
+    configuration (the autotuner's timings shift under a profiler)."""
     import numpy as np
     from paper_2503_15187_gb300 import autotune as AT
+    if TILE > 0:
+        return TILE
     best, _ = AT.autotune(p, n0, np.zeros(NZ), np.full(NZ, T), cache=None, stream=stream)
     return best
 
@@ -218,7 +230,10 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": achieved, "peak": peak,
                      "unit": "GFLOP/s", "frac": achieved / peak,
                      "peak_note": "FP64 FMA: 152 SMs x 2 FMA/clk x 2070 MHz (derived)",
-                     "flops_per_launch": flops, "launch_ms": launch_ms, "traffic": None},
+                     "flops_per_launch": flops, "launch_ms": launch_ms, "traffic": STAGE_TRAFFIC_BYTES,
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one stage_kernel<double> "
+                                     "launch at the 27-node tile (ncu, profiles/stage_kernel_liquid_slab_"
+                                     "4096x32_fp64_full.md)"},
         "hbm": {"algorithmic_GBps": hbm, "frac_of_measured": hbm / hbm_peak},
         "clocks": clocks,
         "gpu_launches": sim.launches_per_step() * args.steps,
@@ -533,7 +548,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")
     ap.add_argument("--variants", default="", help="comma-separated subset of fp32,ev2,fp64_df,adjoint,batched,two_d")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="node tile for the 1D legs (default 0: each leg's autotuned tile), e.g. for ncu")
     args = ap.parse_args()
+    global TILE
+    TILE = args.tile
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.warmup < 3:
