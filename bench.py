@@ -249,7 +249,7 @@ def run_ours(args, rank, world):
                 "fp64_df": lambda: df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64),
                 "adjoint": lambda: adjoint_leg(ev, W, stream),
                 "batched": lambda: batched_leg(ev, W, stream, rank, world, maxred),
-                "two_d": lambda: two_d_leg(ev, stream, flush, maxred, world)}
+                "two_d": lambda: two_d_leg(ev, stream, flush, maxred, world, size=args.two_d_size)}
         want = args.variants.split(",") if args.variants else list(legs)
         line["variants"] = {k: legs[k]() for k in want}
     if rank == 0 and not args.no_cpu_baseline:
@@ -454,7 +454,7 @@ def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=4):
             "autotune_ms_per_step": {str(k): round(v, 3) for k, v in tune_ms.items()}}
 
 
-def two_d_leg(ev, stream, flush, maxred, world, steps=3):
+def two_d_leg(ev, stream, flush, maxred, world, steps=3, size=1024):
     """2D phase separation: 1024 x 1024 periodic grid, dx = 0.25 sigma,
     tensor-product Gauss-Hermite 16 x 16 velocities, FP32 bulk with FP64
     conserved sums, T = 0.75 T_c, mean n = 0.25 with +-1% seeded noise.
@@ -464,7 +464,7 @@ def two_d_leg(ev, stream, flush, maxred, world, steps=3):
     source, local RHS, base, output), 2 distributions x 4 B, 3 stages: 168 B."""
     import numpy as np
     import torch
-    nx = ny = 1024
+    nx = ny = size           # --two-d-size: a smaller grid for ncu captures only
     Q = 16
     p = ev.Params(nx=nx, dx=0.25, Q=Q, dim=2, ny=ny, precision=ev.FP32)
     T = 0.75 * ev.critical_T(p)
@@ -484,7 +484,7 @@ def two_d_leg(ev, stream, flush, maxred, world, steps=3):
     sim.close()
     nvu = nx * ny * Q * Q
     gbs = 168.0 * nvu / (ms * 1e-3) / 1e9
-    return {"workload": "2D phase separation 1024x1024, dx 0.25, 16x16 velocities, FP32 (FP64 conserved sums)",
+    return {"workload": f"2D phase separation {nx}x{ny}, dx 0.25, 16x16 velocities, FP32 (FP64 conserved sums)",
             "value": nvu * world / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "algorithmic_GBps": gbs,
             "mass": mass, "gpu_launches_per_step": 12}
 
@@ -548,6 +548,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")
     ap.add_argument("--variants", default="", help="comma-separated subset of fp32,ev2,fp64_df,adjoint,batched,two_d")
+    ap.add_argument("--two-d-size", type=int, default=1024,
+                    help="grid edge of the two_d leg (default 1024, the workload; smaller only for ncu captures)")
     ap.add_argument("--tile", type=int, default=0,
                     help="node tile for the 1D legs (default 0: each leg's autotuned tile), e.g. for ncu")
     args = ap.parse_args()
