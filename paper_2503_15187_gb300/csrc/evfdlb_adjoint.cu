@@ -67,6 +67,8 @@ __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
     s.f.Sc = s.f.Chi + (Z + 4);
     s.f.Scr = s.f.Sc + kNumScalars * Z;
     s.f.C = s.f.A = s.f.F = s.f.Face = nullptr;
+    s.f.Mtap = nullptr;            // the adjoint passes global tap pointers
+    s.f.Ftap = nullptr;
     s.H = s.f.Scr + 2 * Z;
     s.V = s.H + 2 * Q * (Z + 2 * kHaloH);
     s.Cb = s.V + 2 * Q * (Z + 2 * kHaloV);
@@ -162,9 +164,9 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     const bool node_warp = threadIdx.x < 32;
     const int tid7 = threadIdx.x - 32, nth7 = blockDim.x - 32;
     if (node_warp) {
-        node_fields_pass1<double>(sd, it, s.f, taps, NN, nullptr, threadIdx.x, 32);
+        node_fields_pass1<double>(sd, it, s.f, taps + sd.tap_off + 2 * sd.M + 1, NN, nullptr, threadIdx.x, 32);
         __syncwarp();
-        node_fields_pass2<double>(sd, it, s.f, Z, taps, mom, NN, err, nullptr, threadIdx.x, 32);
+        node_fields_pass2<double>(sd, it, s.f, Z, taps + sd.tap_off, mom, NN, err, nullptr, threadIdx.x, 32);
     } else {
         // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
         // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term

@@ -35,6 +35,7 @@ struct Smem {
     double *U, *T;      // u, T on nodes [i0 - 2, i0 + Z + 2)
     double *X, *Chi;    // X = n^2 chi T and chi on the same nodes
     double *Sc;         // per-node scalars [kNumScalars][Z]
+    double *Mtap;       // staged Fischer-Methfessel taps (2m+1 <= 2M+1)
     R *P, *S;           // analysis / synthesis tables [Q*Q] each
     R *Nr;              // n halo in R (the force convolution), aliases N for FP64
     R *Scr;             // nu and F1 in R, [2][Z]
@@ -43,6 +44,7 @@ struct Smem {
     R *F;               // state tile with halo [2][Q][Z+6]
     R *Face;            // WENO face values [2][Q][Z+1]
     R *Cc;              // per-node coefficient constants c0..c3 [2][4][Z]
+    R *Ftap;            // staged force taps [2M+1] (padded to an even count)
     R *Mm;              // Hermite moments m_l of N(u, T) per node [Q][Z]
 };
 
@@ -51,12 +53,14 @@ struct Smem {
 // the coefficient block).
 __host__ __device__ inline size_t nr_len(int Z, int M) { return ((size_t)(Z + 2 * M) + 1) & ~(size_t)1; }
 
+__host__ __device__ inline size_t ftap_len(int M) { return ((size_t)(2 * M + 1) + 1) & ~(size_t)1; }
+
 template <typename R>
 __host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
-    size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z;
+    size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + (size_t)(2 * M + 1);
     size_t nr = 2 * (size_t)Q * Q + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
                 4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z +
-                (size_t)Q * Z;
+                ftap_len(M) + (size_t)Q * Z;
     return nd * sizeof(double) + nr * sizeof(R);
 }
 
@@ -69,7 +73,8 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     s.X = s.T + (Z + 4);
     s.Chi = s.X + (Z + 4);
     s.Sc = s.Chi + (Z + 4);
-    R* r = reinterpret_cast<R*>(s.Sc + kNumScalars * Z);
+    s.Mtap = s.Sc + kNumScalars * Z;
+    R* r = reinterpret_cast<R*>(s.Mtap + (2 * M + 1));
     s.P = r;
     s.S = s.P + Q * Q;
     if constexpr (std::is_same<R, double>::value) {
@@ -84,7 +89,8 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     s.F = s.A + 2 * Q * Z;
     s.Face = s.F + 2 * Q * (Z + 6);
     s.Cc = s.Face + 2 * Q * (Z + 1);
-    s.Mm = s.Cc + 8 * Z;
+    s.Ftap = s.Cc + 8 * Z;
+    s.Mm = s.Ftap + ftap_len(M);
     return s;
 }
 
@@ -196,12 +202,12 @@ __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Sm
 // Pass 1 (threads tid, tid + nth, ...): Fischer-Methfessel average, chi and X
 // on nodes i0-2 .. i0+nz+1.  Pass 2 reads the +-2 neighbours of pass 1, so
 // the caller separates the passes with a barrier of the participating threads.
+// mtap: the slab's Fischer-Methfessel taps [2m+1] (global or staged).
 template <typename R>
 __device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s,
-                                  const double* __restrict__ taps, long long NN, double* fields_out, int tid,
+                                  const double* __restrict__ mtap, long long NN, double* fields_out, int tid,
                                   int nth) {
     const int M = sd.M, m = sd.m;
-    const double* mtap = taps + sd.tap_off + 2 * M + 1;  // Fischer-Methfessel [2m+1]
     // Fischer-Methfessel average (Sec. II.A), chi (Eq. (carnstar)) and
     // X = n^2 chi T on nodes i0-2 .. i0+nz+1.  Under the outflow rule a ghost
     // node copies every node field of the nearest interior node, so the
@@ -227,12 +233,12 @@ __device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const 
 
 // Pass 2: per tile node, the gradients, the Eq. (F1) force (in R), the heat
 // flux, the transport coefficients and the scalars of Sc and Scr.
+// ftap: the slab's force taps [2M+1] (global or staged).
 template <typename R>
 __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                  const R* __restrict__ rtaps, const double* __restrict__ mom, long long NN,
+                                  const R* __restrict__ ftap, const double* __restrict__ mom, long long NN,
                                   unsigned* err, double* fields_out, int tid, int nth) {
     const int M = sd.M;
-    const R* ftap = rtaps + sd.tap_off;                  // force [2M+1]
     const double inv12 = sd.inv_dx / 12.0;
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
@@ -296,9 +302,9 @@ template <typename R>
 __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                             const double* __restrict__ taps, const R* __restrict__ rtaps,
                             const double* __restrict__ mom, long long NN, unsigned* err, double* fields_out) {
-    node_fields_pass1<R>(sd, it, s, taps, NN, fields_out, threadIdx.x, blockDim.x);
+    node_fields_pass1<R>(sd, it, s, taps + sd.tap_off + 2 * sd.M + 1, NN, fields_out, threadIdx.x, blockDim.x);
     __syncthreads();
-    node_fields_pass2<R>(sd, it, s, Z, rtaps, mom, NN, err, fields_out, threadIdx.x, blockDim.x);
+    node_fields_pass2<R>(sd, it, s, Z, rtaps + sd.tap_off, mom, NN, err, fields_out, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------------------

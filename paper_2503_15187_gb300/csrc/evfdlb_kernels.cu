@@ -71,6 +71,10 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     float2* Fd = DF ? reinterpret_cast<float2*>(s.Mm + (size_t)Q * Z) : nullptr;
     load_node_inputs<R>(sd, it, s, Z, rtab, mom_in, NN);
     load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
+    // the slab's force and Fischer-Methfessel taps, read in warp 0's serial
+    // tap loops, staged once into shared memory
+    for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.Ftap[j] = rtaps[sd.tap_off + j];
+    for (int j = threadIdx.x; j < 2 * sd.m + 1; j += blockDim.x) s.Mtap[j] = taps[sd.tap_off + 2 * sd.M + 1 + j];
     __syncthreads();
     // Warp 0 forms the node-level quantities of the tile (node fields,
     // coefficient constants, Hermite moments of the local Gaussian) while the
@@ -81,9 +85,9 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     const R* rt = vtab + sd.tab_off;
     TableLayout L(Q);
     if (threadIdx.x < 32) {
-        node_fields_pass1<R>(sd, it, s, taps, NN, nullptr, threadIdx.x, 32);
+        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32);
         __syncwarp();
-        node_fields_pass2<R>(sd, it, s, Z, rtaps, mom_in, NN, err, nullptr, threadIdx.x, 32);
+        node_fields_pass2<R>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32);
         __syncwarp();
         node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32);
     } else {
