@@ -550,39 +550,61 @@ __device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, 
 
 // One raw moment sum of one node from a column h[k * stride] (k < Q).  The
 // conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
-// (heat flux) in R.
+// (heat flux) in R.  The velocity powers come from xp = [xi, xi^2, xi^3]
+// (FP64) and xr = [xi, xi^3] (R).
 template <typename R>
 __device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
-                                             const double* __restrict__ xi, const R* __restrict__ rxi) {
+                                             const double* __restrict__ xp, const R* __restrict__ xr) {
     const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
     if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
         which == MOM_G0) {
         double acc = 0.0;
-        for (int k = 0; k < Q; ++k) {
-            double x = xi[k], wgt = (p == 0) ? 1.0 : (p == 1 ? x : (p == 2 ? x * x : x * x * x));
-            acc = fma(wgt, (double)h[k * stride], acc);
+        if (p == 0) {
+            for (int k = 0; k < Q; ++k) acc += (double)h[k * stride];
+        } else {
+            const double* w = xp + (p - 1) * Q;
+            for (int k = 0; k < Q; ++k) acc = fma(w[k], (double)h[k * stride], acc);
         }
         return acc;
     }
+    const R* w = xr + (p == 1 ? 0 : Q);
     R racc = 0;
-    for (int k = 0; k < Q; ++k) {
-        R x = rxi[k], wgt = (p == 1) ? x : x * x * x;
-        racc = fma(wgt, h[k * stride], racc);
-    }
+    for (int k = 0; k < Q; ++k) racc = fma(w[k], h[k * stride], racc);
     return (double)racc;
 }
 
-// Raw moment sums of the tile held in s.F (columns 3 .. nz+2).
+// Velocity powers of moment_sum from the tables xi (FP64) and rxi (R).
+template <typename R>
+__device__ __forceinline__ void velocity_powers(int Q, const double* __restrict__ xi, const R* __restrict__ rxi,
+                                                double* xp, R* xr, int tid, int nth) {
+    for (int k = tid; k < Q; k += nth) {
+        const double x = xi[k];
+        xp[k] = x;
+        xp[Q + k] = x * x;
+        xp[2 * Q + k] = x * x * x;
+        const R y = rxi[k];
+        xr[k] = y;
+        xr[Q + k] = y * y * y;
+    }
+}
+
+// Raw moment sums of the tile held in s.F (columns 3 .. nz+2).  Called by
+// all threads once the tile's velocity work is done: the velocity powers
+// are staged in the (then free) table block s.P / s.S (5 Q values).
 template <typename R>
 __device__ void tile_moment_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                  const double* __restrict__ xi, const R* __restrict__ rxi,
                                  double* __restrict__ mom_out, long long NN) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
+    double* xp = reinterpret_cast<double*>(s.P);
+    R* xr = reinterpret_cast<R*>(xp + 3 * Q);
+    velocity_powers<R>(Q, xi, rxi, xp, xr, threadIdx.x, blockDim.x);
+    __syncthreads();
     for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
         int t = e % nz, which = e / nz;
         int d = which >= MOM_G0 ? 1 : 0;
         const R* h = s.F + (size_t)d * Q * W + t + 3;
-        mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xi, rxi);
+        mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xp, xr);
     }
 }
 

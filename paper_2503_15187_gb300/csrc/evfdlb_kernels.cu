@@ -286,13 +286,15 @@ sums_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ ite
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q;
     TableLayout L(Q);
-    const double* xi = tables + sd.tab_off + L.xi;
-    const R* rxi = rtab + sd.tab_off + L.xi;
+    __shared__ double xp[3 * kQMax];
+    __shared__ R xr[2 * kQMax];
+    velocity_powers<R>(Q, tables + sd.tab_off + L.xi, rtab + sd.tab_off + L.xi, xp, xr, threadIdx.x, blockDim.x);
+    __syncthreads();
     for (int e = threadIdx.x; e < kNumMoments * it.nz; e += blockDim.x) {
         int t = e % it.nz, which = e / it.nz;
         int d = which >= MOM_G0 ? 1 : 0;
         const R* h = state + d * NF + sd.f_off + it.i0 + t;
-        double acc = moment_sum<R>(which, Q, h, sd.nx, xi, rxi);
+        double acc = moment_sum<R>(which, Q, h, sd.nx, xp, xr);
         if (!finite(acc)) atomicOr(err, ERR_NONFINITE);
         mom[which * NN + sd.node_off + it.i0 + t] = acc;
     }
