@@ -35,6 +35,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "evfdlb_device.cuh"
 #include "evfdlb_internal.h"
 
 namespace evfdlb {
@@ -67,85 +68,252 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 // ---------------------------------------------------------------------------
 // k2_moments: per node, raw sums over the Q^2 velocities.  Conserved sums
 // (S0, S1, S2xx, S2yy, G0) are formed from the row and column sums of the
-// velocity grid, combined in FP64; for an FP32 state each 16-term row or
-// column sum is a compensated (Neumaier) FP32 sum kept as an unevaluated
-// pair, accurate to O(Q u^2) of the sum of magnitudes, i.e. FP64 quality at
-// FP32-pipe cost.  The heat-flux sums are plain R sums.
+// velocity grid.  For an FP32 state each 16-term row or column sum is a
+// compensated FP32 sum kept as an unevaluated pair (TwoSum, Knuth), and the
+// rows and columns are combined in float-float arithmetic (TwoSum and the
+// FMA TwoProduct against the velocity powers split into float pairs,
+// Ogita-Rump-Oishi): about 2^-44 of the sum of magnitudes, FP64 quality on
+// the FP32 pipe (the FP64 pipe of this GPU runs at 1/64 of the FP32 rate).
+// The heat-flux sums are plain R sums.  Outputs: the FP64 raw sums (when
+// `mom` is given) and, for an FP32 state, the node primitives n, u, T, q in
+// FP32 (when `prf` is given: what the stage's field kernel reads).
 // ---------------------------------------------------------------------------
+enum { P2_N = 0, P2_UX, P2_UY, P2_T, P2_QX, P2_QY, kNumPrf2 };
+
+// velocity powers of the velocity set, passed by value (kernel parameter
+// space, read as constant operands once the loops are unrolled)
+template <typename R>
+struct Pow2 {
+    R v[16], v2[16], v3[16];            // xi, xi^2, xi^3 in R
+    float h[16], l[16], h2[16], l2[16];  // xi and xi^2 (FP64) as float pairs
+};
+
 template <typename R>
 struct CompSum {                       // R = double: plain accumulation
     double s = 0.0;
     __device__ __forceinline__ void add(R x) { s += (double)x; }
-    __device__ __forceinline__ double value() const { return s; }
 };
 template <>
-struct CompSum<float> {                // Neumaier's compensated sum
+struct CompSum<float> {                // TwoSum: s + c carries the exact sum to O(n u^2)
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float x) {
-        float t = s + x;
-        c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+        const float t = __fadd_rn(s, x), z = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// float-float accumulator (hi, lo)
+struct FF {
+    float h = 0.0f, l = 0.0f;
+    // += (a + b), a pair
+    __device__ __forceinline__ void add(float a, float b) {
+        const float t = __fadd_rn(h, a), z = __fsub_rn(t, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, z)), __fsub_rn(a, z));
+        l = __fadd_rn(l, __fadd_rn(e, b));
+        h = t;
+    }
+    // += (xh + xl)(a + b); the xl b term is below the pair's precision
+    __device__ __forceinline__ void fma2(float xh, float xl, float a, float b) {
+        const float p = __fmul_rn(xh, a), pe = fmaf(xh, a, -p);
+        const float t = __fadd_rn(h, p), z = __fsub_rn(t, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, z)), __fsub_rn(p, z));
+        l = __fadd_rn(l, __fadd_rn(e, pe));
+        l = fmaf(xh, b, l);
+        l = fmaf(xl, a, l);
+        h = t;
+    }
+    __device__ __forceinline__ float value() const { return h + l; }
+    __device__ __forceinline__ double value64() const { return (double)h + (double)l; }
+};
+
+// Partial raw sums of one node over half of the y velocities (ky = K0 ..
+// K0 + Q/2 - 1) and all x velocities.  Conserved sums: float-float pairs for
+// an FP32 state (`a*`, `b*`), plain FP64 for an FP64 state (`d*`); heat-flux
+// sums in R.  Every sum is linear in the state, so the two halves add.
 template <typename R>
-__global__ void __launch_bounds__(256)
-k2_moments(Slab2 s, const double* __restrict__ tab, const R* __restrict__ st, double* __restrict__ mom,
+struct MomPart {
+    FF a0, a1, a2, a3, b1, b2;               // S0, S1x, S2xx, G0, S1y, S2yy (FP32 state)
+    double d0 = 0, d1x = 0, d2xx = 0, dg0 = 0, d1y = 0, d2yy = 0;   // (FP64 state)
+    R s2xy = 0, s3x = 0, s3y = 0, g1x = 0, g1y = 0;
+};
+constexpr int kMomX = 17;                    // values exchanged between the halves
+
+template <typename R, int Q, int K0>
+__device__ __forceinline__ void moments_half(const R* __restrict__ f, long long N, long long NF, const Pow2<R>& pw,
+                                             const R (*sv)[Q], const float (*sh)[Q], MomPart<R>& P) {
+    constexpr bool F32 = std::is_same<R, float>::value;
+    constexpr int QH = Q / 2;
+    CompSum<R> col[QH];
+    for (int kx = 0; kx < Q; ++kx) {
+        CompSum<R> rowF, rowG;
+        R p1 = 0, p2 = 0, p3 = 0, pg = 0;          // sum y f, y^2 f, y^3 f, y g over the half row
+#pragma unroll
+        for (int j = 0; j < QH; ++j) {
+            const long long o = (long long)(kx * Q + K0 + j) * N;
+            const R fv = f[o], gv = f[NF + o];
+            rowF.add(fv);
+            rowG.add(gv);
+            col[j].add(fv);
+            p1 = fma(pw.v[K0 + j], fv, p1);
+            p2 = fma(pw.v2[K0 + j], fv, p2);
+            p3 = fma(pw.v3[K0 + j], fv, p3);
+            pg = fma(pw.v[K0 + j], gv, pg);
+        }
+        const R xr = sv[0][kx], x2r = sv[1][kx];
+        R rfr, rgr;                                 // half-row sums in R
+        if constexpr (F32) {
+            P.a0.add(rowF.s, rowF.c);
+            P.a1.fma2(sh[0][kx], sh[1][kx], rowF.s, rowF.c);
+            P.a2.fma2(sh[2][kx], sh[3][kx], rowF.s, rowF.c);
+            P.a3.add(rowG.s, rowG.c);
+            rfr = rowF.s + rowF.c;
+            rgr = rowG.s + rowG.c;
+        } else {
+            P.d0 += rowF.s;
+            P.d1x = fma((double)xr, rowF.s, P.d1x);
+            P.d2xx = fma((double)x2r, rowF.s, P.d2xx);
+            P.dg0 += rowG.s;
+            rfr = (R)rowF.s;
+            rgr = (R)rowG.s;
+        }
+        // sum (x^2 + y^2) f = x^2 rowF + p2;  sum y (x^2 + y^2) f = x^2 p1 + p3
+        P.s2xy = fma(xr, p1, P.s2xy);
+        P.s3x = fma(xr, fma(x2r, rfr, p2), P.s3x);
+        P.s3y += fma(x2r, p1, p3);
+        P.g1x = fma(xr, rgr, P.g1x);
+        P.g1y += pg;
+    }
+#pragma unroll
+    for (int j = 0; j < QH; ++j) {
+        if constexpr (F32) {
+            P.b1.fma2(pw.h[K0 + j], pw.l[K0 + j], col[j].s, col[j].c);
+            P.b2.fma2(pw.h2[K0 + j], pw.l2[K0 + j], col[j].s, col[j].c);
+        } else {
+            P.d1y = fma((double)pw.v[K0 + j], col[j].s, P.d1y);
+            P.d2yy = fma((double)pw.v2[K0 + j], col[j].s, P.d2yy);
+        }
+    }
+}
+
+// FP32: four CTAs per SM keep more loads in flight; the FP64 build (parity
+// checks) keeps its registers
+template <typename R>
+constexpr int moments_min_blocks() { return std::is_same<R, float>::value ? 4 : 1; }
+
+// Per CTA pass 128 nodes: warp pair (2p, 2p+1) takes nodes 32p .. 32p+31,
+// the even warp the y velocities of the first half, the odd warp the second
+// half (each load instruction reads 32 consecutive nodes of one plane); the
+// odd warp hands its partial sums to the even one through shared memory.
+template <typename R, int Q>
+__global__ void __launch_bounds__(256, moments_min_blocks<R>())
+k2_moments(Slab2 s, const Pow2<R> pw, const R* __restrict__ st, double* __restrict__ mom, float* __restrict__ prf,
            unsigned* err) {
-    const int Q = s.Q;
+    constexpr bool F32 = std::is_same<R, float>::value;
+    constexpr int kNodes = 128;
+    static_assert(Q % 2 == 0, "the y velocities split in two halves");
     const long long N = s.N, NF = (long long)Q * Q * N;
-    TableLayout L(Q);
-    const double* xi = tab + L.xi;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        CompSum<R> col[16];
-        double s0 = 0, s1x = 0, s2xx = 0, g0 = 0;
-        R s2xy = 0, s3x = 0, s3y = 0, g1x = 0, g1y = 0;
-        for (int kx = 0; kx < Q; ++kx) {
-            const double x = xi[kx];
-            CompSum<R> rowF, rowG;
-            R ps2xy = 0, ps3x = 0, ps3y = 0, pg1y = 0;
-            for (int ky = 0; ky < Q; ++ky) {
-                const long long g = (long long)(kx * Q + ky) * N + i;
-                R f = st[g], gg = st[NF + g];
-                rowF.add(f);
-                rowG.add(gg);
-                col[ky].add(f);
-                const R y = (R)xi[ky], xr = (R)x, v2 = xr * xr + y * y;
-                ps2xy = fma(y, f, ps2xy);
-                ps3x = fma(v2, f, ps3x);
-                ps3y = fma(y * v2, f, ps3y);
-                pg1y = fma(y, gg, pg1y);
+    // the row loop indexes the powers at run time: from shared memory
+    __shared__ R sv[2][Q];
+    __shared__ float sh[4][Q];
+    __shared__ R xch[kMomX][kNodes];
+    if (threadIdx.x < Q) {
+        const int k = threadIdx.x;
+        sv[0][k] = pw.v[k];
+        sv[1][k] = pw.v2[k];
+        sh[0][k] = pw.h[k];
+        sh[1][k] = pw.l[k];
+        sh[2][k] = pw.h2[k];
+        sh[3][k] = pw.l2[k];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = warp & 1;
+    const int slot = (warp >> 1) * 32 + lane;
+    for (long long b0 = (long long)blockIdx.x * kNodes; b0 < N; b0 += (long long)gridDim.x * kNodes) {
+        const long long i = b0 + slot;
+        MomPart<R> P;
+        if (i < N) {
+            if (half == 0) moments_half<R, Q, 0>(st + i, N, NF, pw, sv, sh, P);
+            else moments_half<R, Q, Q / 2>(st + i, N, NF, pw, sv, sh, P);
+        }
+        if (half == 1) {
+            R v[kMomX];
+            if constexpr (F32) {
+                const float w[12] = {P.a0.h, P.a0.l, P.a1.h, P.a1.l, P.a2.h, P.a2.l,
+                                     P.a3.h, P.a3.l, P.b1.h, P.b1.l, P.b2.h, P.b2.l};
+#pragma unroll
+                for (int q = 0; q < 12; ++q) v[q] = w[q];
+            } else {
+                const double w[12] = {P.d0, P.d1x, P.d2xx, P.dg0, P.d1y, P.d2yy, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int q = 0; q < 12; ++q) v[q] = w[q];
             }
-            const double rf = rowF.value(), rg = rowG.value();
-            s0 += rf;
-            s1x = fma(x, rf, s1x);
-            s2xx = fma(x * x, rf, s2xx);
-            g0 += rg;
-            s2xy = fma((R)x, ps2xy, s2xy);
-            s3x = fma((R)x, ps3x, s3x);
-            s3y += ps3y;
-            g1x = fma((R)x, (R)rg, g1x);
-            g1y += pg1y;
+            v[12] = P.s2xy;
+            v[13] = P.s3x;
+            v[14] = P.s3y;
+            v[15] = P.g1x;
+            v[16] = P.g1y;
+#pragma unroll
+            for (int q = 0; q < kMomX; ++q) xch[q][slot] = v[q];
         }
-        double s1y = 0, s2yy = 0;
-        for (int ky = 0; ky < Q; ++ky) {
-            const double cv = col[ky].value();
-            s1y = fma(xi[ky], cv, s1y);
-            s2yy = fma(xi[ky] * xi[ky], cv, s2yy);
+        __syncthreads();
+        if (half == 0 && i < N) {
+            const R s2xy = P.s2xy + xch[12][slot], s3x = P.s3x + xch[13][slot], s3y = P.s3y + xch[14][slot];
+            const R g1x = P.g1x + xch[15][slot], g1y = P.g1y + xch[16][slot];
+            double S0, S1x, S1y, S2xx, S2yy, G0;
+            float n32 = 0, S1x32 = 0, S1y32 = 0, S2xx32 = 0, S2yy32 = 0, G032 = 0;
+            if constexpr (F32) {
+                P.a0.add(xch[0][slot], xch[1][slot]);
+                P.a1.add(xch[2][slot], xch[3][slot]);
+                P.a2.add(xch[4][slot], xch[5][slot]);
+                P.a3.add(xch[6][slot], xch[7][slot]);
+                P.b1.add(xch[8][slot], xch[9][slot]);
+                P.b2.add(xch[10][slot], xch[11][slot]);
+                n32 = P.a0.value(); S1x32 = P.a1.value(); S1y32 = P.b1.value();
+                S2xx32 = P.a2.value(); S2yy32 = P.b2.value(); G032 = P.a3.value();
+                if (!isfinite(n32) || !isfinite(S2xx32 + S2yy32 + G032)) atomicOr(err, ERR_NONFINITE);
+                S0 = P.a0.value64(); S1x = P.a1.value64(); S1y = P.b1.value64();
+                S2xx = P.a2.value64(); S2yy = P.b2.value64(); G0 = P.a3.value64();
+            } else {
+                S0 = P.d0 + xch[0][slot]; S1x = P.d1x + xch[1][slot]; S2xx = P.d2xx + xch[2][slot];
+                G0 = P.dg0 + xch[3][slot]; S1y = P.d1y + xch[4][slot]; S2yy = P.d2yy + xch[5][slot];
+                if (!isfinite(S0) || !isfinite(S2xx + S2yy + G0)) atomicOr(err, ERR_NONFINITE);
+            }
+            if (mom) {
+                mom[M2_S0 * N + i] = S0;
+                mom[M2_S1X * N + i] = S1x;
+                mom[M2_S1Y * N + i] = S1y;
+                mom[M2_S2XX * N + i] = S2xx;
+                mom[M2_S2YY * N + i] = S2yy;
+                mom[M2_G0 * N + i] = G0;
+                mom[M2_S2XY * N + i] = (double)s2xy;
+                mom[M2_S3X * N + i] = (double)s3x;
+                mom[M2_S3Y * N + i] = (double)s3y;
+                mom[M2_G1X * N + i] = (double)g1x;
+                mom[M2_G1Y * N + i] = (double)g1y;
+            }
+            if constexpr (F32) {
+                if (prf) {
+                    // primitives in FP32: u = S1/n, (3/2) n T = (S2xx + S2yy)/2 + G0 - n u^2/2,
+                    // q_i = sum c_i (c^2/2 F + G) expanded in the raw sums
+                    const float n = n32, ux = S1x32 / n, uy = S1y32 / n;
+                    const float u2 = ux * ux + uy * uy, S2 = S2xx32 + S2yy32;
+                    const float T = (2.0f / 3.0f) * ((0.5f * S2 + G032) / n - 0.5f * u2);
+                    const float uS1 = ux * S1x32 + uy * S1y32;
+                    const float qx = 0.5f * (s3x - 2.0f * (ux * S2xx32 + uy * s2xy) + u2 * S1x32 - ux * S2 +
+                                             2.0f * ux * uS1 - ux * u2 * n) + g1x - ux * G032;
+                    const float qy = 0.5f * (s3y - 2.0f * (ux * s2xy + uy * S2yy32) + u2 * S1y32 - uy * S2 +
+                                             2.0f * uy * uS1 - uy * u2 * n) + g1y - uy * G032;
+                    prf[P2_N * N + i] = n;
+                    prf[P2_UX * N + i] = ux;
+                    prf[P2_UY * N + i] = uy;
+                    prf[P2_T * N + i] = T;
+                    prf[P2_QX * N + i] = qx;
+                    prf[P2_QY * N + i] = qy;
+                }
+            }
         }
-        if (!isfinite(s0) || !isfinite(s2xx + s2yy + g0)) atomicOr(err, ERR_NONFINITE);
-        mom[M2_S0 * N + i] = s0;
-        mom[M2_S1X * N + i] = s1x;
-        mom[M2_S1Y * N + i] = s1y;
-        mom[M2_S2XX * N + i] = s2xx;
-        mom[M2_S2YY * N + i] = s2yy;
-        mom[M2_G0 * N + i] = g0;
-        mom[M2_S2XY * N + i] = (double)s2xy;
-        mom[M2_S3X * N + i] = (double)s3x;
-        mom[M2_S3Y * N + i] = (double)s3y;
-        mom[M2_G1X * N + i] = (double)g1x;
-        mom[M2_G1Y * N + i] = (double)g1y;
+        __syncthreads();                               // xch is reused by the next pass
     }
 }
 
@@ -161,129 +329,221 @@ __device__ __forceinline__ void prim2(const double* __restrict__ mom, long long 
 }
 
 // ---------------------------------------------------------------------------
-// k2_fields: node fields of a 16x16 tile.
+// k2_fields: node fields of a 16x16 tile, computed in the state precision R
+// (the FP32 build reads the FP32 primitives of k2_moments; the FP64 build
+// derives them from the FP64 raw sums).
+//
+// Force disc (rectangle rule over the grid offsets inside r_cut; the taps
+// carry dx^2 g2): g2 is radial, so g2x(-a, b) = -g2x(a, b) and
+// g2y(-a, b) = g2y(a, b) exactly, and one pass over the offset column pair
+// (a, -a) adds g2x (n_+ - n_-) and g2y (n_+ + n_-) (column a = 0 with halved
+// g2y).  Each warp takes a host-balanced list of column pairs over the whole
+// tile: lane = (column, block of 8 rows); the pass walks the rows of the
+// column once and keeps the last 8 weight pairs in a register ring, so each
+// staged density pair feeds 16 FMAs (8 rows x 2 components).  The per-warp
+// partial forces are summed in warp order (deterministic).
 // ---------------------------------------------------------------------------
+constexpr int kFWarps = 8;           // warps of k2_fields (256 threads)
+constexpr int kFRows = 8;            // rows of a force register block (= ring length)
+constexpr int kFPlanHead = 12;       // plan header: kFWarps + 1 prefix offsets, padded to 16 bytes
+static_assert(kTile2 == 16 && 2 * kFRows == kTile2 && kFWarps * 32 == 256, "force mapping: 16 x 2 lanes x 8 rows");
+
+// pitch of the staged density row: >= W and = 2 (mod 4), so that rows 8
+// apart (the two row blocks of a warp) fall 16 banks apart
+__host__ __device__ inline int fields_pitch(int W) { return W + ((6 - W % 4) % 4); }
+
+template <typename R>
+__host__ __device__ inline size_t fields_smem_bytes(int Mf, int mfm) {
+    const int H = Mf > mfm + 2 ? Mf : mfm + 2, W = kTile2 + 2 * H, E = kTile2 + 4, Wr = fields_pitch(W);
+    const size_t nr = (size_t)(W + kFRows) * Wr, pf = 2 * (size_t)kFWarps * kTile2 * kTile2;
+    return sizeof(R) * ((nr > pf ? nr : pf) + 5 * (size_t)E * E);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256)
-k2_fields(Slab2 s, const double* __restrict__ mom, const int* __restrict__ ft_off, const R* __restrict__ ft_g,
-          const int* __restrict__ fm_off, const double* __restrict__ fm_w, R* __restrict__ fld, unsigned* err) {
-    extern __shared__ double sm2[];
-    const int H = max(s.Mf, s.mfm + 2), W = kTile2 + 2 * H, E = kTile2 + 4;
-    double* Nh = sm2;                 // n on the tile + H halo, [W][W]
-    double* U = Nh + W * W;           // ux, uy, T, X, chi on the tile + 2, [E][E] each
-    double* V = U + E * E;
-    double* Tt = V + E * E;
-    double* Xt = Tt + E * E;
-    double* Ct = Xt + E * E;
-    R* Nr = reinterpret_cast<R*>(Ct + E * E);   // n in R for the force (FP32)
+k2_fields(Slab2 s, const double* __restrict__ mom, const float* __restrict__ prf, const R* __restrict__ ftw,
+          const int* __restrict__ fplan, const int* __restrict__ fm_off, const R* __restrict__ fm_w,
+          R* __restrict__ fld, unsigned* err) {
+    constexpr bool F32 = std::is_same<R, float>::value;
+    using R2 = typename std::conditional<F32, float2, double2>::type;
+    extern __shared__ __align__(16) unsigned char sm2raw[];
+    R* sm2 = reinterpret_cast<R*>(sm2raw);
+    const int H = max(s.Mf, s.mfm + 2), W = kTile2 + 2 * H, E = kTile2 + 4, Wr = fields_pitch(W);
+    R* Nr = sm2;                      // n on the tile + H halo, [W + 8][Wr]; rows W.. are zero
+    R* U = sm2 + max((W + kFRows) * Wr, 2 * kFWarps * kTile2 * kTile2);
+    R* V = U + E * E;                 // ux, uy, T, X, chi on the tile + 2, [E][E] each
+    R* Tt = V + E * E;
+    R* Xt = Tt + E * E;
+    R* Ct = Xt + E * E;
     const int nx = s.nx, ny = s.ny;
     const long long N = s.N;
     const int x0 = blockIdx.x * kTile2, y0 = blockIdx.y * kTile2;
-    for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
-        int cy = e / W, cx = e % W;
-        long long i = (long long)wrapi(y0 - H + cy, ny) * nx + wrapi(x0 - H + cx, nx);
-        double n = mom[M2_S0 * N + i];
-        Nh[e] = n;
-        Nr[e] = (R)n;
+    for (int e = threadIdx.x; e < (W + kFRows) * W; e += blockDim.x) {
+        const int cy = e / W, cx = e % W;
+        R n = R(0);
+        if (cy < W) {
+            const long long i = (long long)wrapi(y0 - H + cy, ny) * nx + wrapi(x0 - H + cx, nx);
+            if constexpr (F32) n = prf[P2_N * N + i];
+            else n = mom[M2_S0 * N + i];
+        }
+        Nr[cy * Wr + cx] = n;
     }
     for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
-        int cy = e / E, cx = e % E;
-        long long i = (long long)wrapi(y0 - 2 + cy, ny) * nx + wrapi(x0 - 2 + cx, nx);
-        double n, ux, uy, T;
-        prim2(mom, N, i, n, ux, uy, T);
-        U[e] = ux;
-        V[e] = uy;
-        Tt[e] = T;
+        const int cy = e / E, cx = e % E;
+        const long long i = (long long)wrapi(y0 - 2 + cy, ny) * nx + wrapi(x0 - 2 + cx, nx);
+        if constexpr (F32) {
+            U[e] = prf[P2_UX * N + i];
+            V[e] = prf[P2_UY * N + i];
+            Tt[e] = prf[P2_T * N + i];
+        } else {
+            double n, ux, uy, T;
+            prim2(mom, N, i, n, ux, uy, T);
+            U[e] = ux;
+            V[e] = uy;
+            Tt[e] = T;
+        }
     }
     __syncthreads();
     // Fischer-Methfessel average, chi (Eq. (carnstar)) and X = n^2 chi T on the tile + 2
     for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
-        int cy = e / E, cx = e % E;
-        int hy = cy - 2 + H, hx = cx - 2 + H;   // position in the halo array
-        double nb = 0.0;
-        for (int t = 0; t < s.nfm; ++t) nb = fma(fm_w[t], Nh[(hy + fm_off[2 * t + 1]) * W + hx + fm_off[2 * t]], nb);
-        double eta = s.eta_coef * nb, om = 1.0 - eta;
-        double chi = (2.0 - eta) / (2.0 * om * om * om);
-        double n = Nh[hy * W + hx];
+        const int cy = e / E, cx = e % E;
+        const int hy = cy - 2 + H, hx = cx - 2 + H;   // position in the halo array
+        R nb = R(0);
+        for (int t = 0; t < s.nfm; ++t) nb = fma(fm_w[t], Nr[(hy + fm_off[2 * t + 1]) * Wr + hx + fm_off[2 * t]], nb);
+        const R eta = (R)s.eta_coef * nb, om = R(1) - eta;
+        const R chi = (R(2) - eta) / (R(2) * om * om * om);
+        const R n = Nr[hy * Wr + hx];
         Ct[e] = chi;
         Xt[e] = n * n * chi * Tt[e];
     }
-    __syncthreads();
+    // force over the disc
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int fxl = lane & 15, yb = lane >> 4;
+    R ax[kFRows], ay[kFRows];
+#pragma unroll
+    for (int k = 0; k < kFRows; ++k) ax[k] = ay[k] = R(0);
+    {
+        const int4* ent = reinterpret_cast<const int4*>(fplan + kFPlanHead);
+        const int e1 = fplan[warp + 1];
+        for (int e = fplan[warp]; e < e1; ++e) {
+            const int4 en = ent[e];          // column a, weight offset, steps (multiple of 8), half height w
+            const int a = en.x, steps = en.z, w = en.w;
+            const R* pp = Nr + (yb * kFRows - w + H) * Wr + fxl + H + a;   // n(x + a, row of step 0)
+            const R* pm = pp - 2 * a;                                       // n(x - a, ...)
+            const R2* g = reinterpret_cast<const R2*>(ftw) + en.y;
+            // ring: slot (j & 7) holds the weights of step j, i.e. of offset b = j - w
+            R gx[kFRows], gy[kFRows];
+#pragma unroll
+            for (int k = 0; k < kFRows; ++k) gx[k] = gy[k] = R(0);
+            for (int j0 = 0; j0 < steps; j0 += kFRows) {
+#pragma unroll
+                for (int P = 0; P < kFRows; ++P) {
+                    const R vp = pp[(j0 + P) * Wr], vm = pm[(j0 + P) * Wr];
+                    const R2 gg = __ldg(g + j0 + P);
+                    gx[P] = gg.x;
+                    gy[P] = gg.y;
+                    const R dd = vp - vm, ss = vp + vm;
+                    // row k of the block takes offset b = (j - k) - w: the weights of step j - k
+#pragma unroll
+                    for (int k = 0; k < kFRows; ++k) {
+                        ax[k] = fma(gx[(P - k) & (kFRows - 1)], dd, ax[k]);
+                        ay[k] = fma(gy[(P - k) & (kFRows - 1)], ss, ay[k]);
+                    }
+                }
+            }
+        }
+    }
     const int tx = threadIdx.x % kTile2, ty = threadIdx.x / kTile2;
+    const R n = Nr[(ty + H) * Wr + tx + H];
+    __syncthreads();                  // density reads done: its space takes the partial forces
+    R* Pf = sm2;                      // [kFWarps][2][256]
+#pragma unroll
+    for (int k = 0; k < kFRows; ++k) {
+        const int node = (yb * kFRows + k) * kTile2 + fxl;
+        Pf[(2 * warp) * 256 + node] = ax[k];
+        Pf[(2 * warp + 1) * 256 + node] = ay[k];
+    }
+    __syncthreads();
+    R fx = R(0), fy = R(0);
+#pragma unroll
+    for (int w = 0; w < kFWarps; ++w) {
+        fx += Pf[(2 * w) * 256 + threadIdx.x];
+        fy += Pf[(2 * w + 1) * 256 + threadIdx.x];
+    }
     const int x = x0 + tx, y = y0 + ty;
     if (x >= nx || y >= ny) return;
     const long long i = (long long)y * nx + x;
     const int c = (ty + 2) * E + (tx + 2);
-    const double k12 = s.inv_dx / 12.0;
-    auto d4x = [&](const double* f) { return (f[c - 2] - 8.0 * f[c - 1] + 8.0 * f[c + 1] - f[c + 2]) * k12; };
-    auto d4y = [&](const double* f) { return (f[c - 2 * E] - 8.0 * f[c - E] + 8.0 * f[c + E] - f[c + 2 * E]) * k12; };
-    const double n = Nh[(ty + H) * W + tx + H], ux = U[c], uy = V[c], T = Tt[c], X = Xt[c], chi = Ct[c];
-    const double Ax = d4x(Xt) / X, Ay = d4y(Xt) / X, Bx = d4x(Tt) / T, By = d4y(Tt) / T;
-    const double Dxx = d4x(U), Dxy = d4x(V), Dyx = d4y(U), Dyy = d4y(V);
-    // force over the disc, rectangle rule (taps carry dx^2 g2)
-    R fx = 0, fy = 0;
-    const R* nc = Nr + (ty + H) * W + tx + H;
-    for (int t = 0; t < s.nft; ++t) {
-        R nn = nc[ft_off[2 * t + 1] * W + ft_off[2 * t]];
-        fx = fma(ft_g[2 * t], nn, fx);
-        fy = fma(ft_g[2 * t + 1], nn, fy);
-    }
+    const R k12 = (R)(s.inv_dx / 12.0);
+    auto d4x = [&](const R* f) { return (f[c - 2] - R(8) * f[c - 1] + R(8) * f[c + 1] - f[c + 2]) * k12; };
+    auto d4y = [&](const R* f) { return (f[c - 2 * E] - R(8) * f[c - E] + R(8) * f[c + E] - f[c + 2 * E]) * k12; };
+    const R ux = U[c], uy = V[c], T = Tt[c], X = Xt[c], chi = Ct[c];
+    const R Ax = d4x(Xt) / X, Ay = d4y(Xt) / X, Bx = d4x(Tt) / T, By = d4y(Tt) / T;
+    const R Dxx = d4x(U), Dxy = d4x(V), Dyx = d4y(U), Dyy = d4y(V);
     // heat flux q_i = sum c_i (c^2/2 F + G)
-    const double S0 = mom[M2_S0 * N + i], S1x = mom[M2_S1X * N + i], S1y = mom[M2_S1Y * N + i];
-    const double S2xx = mom[M2_S2XX * N + i], S2yy = mom[M2_S2YY * N + i], S2xy = mom[M2_S2XY * N + i];
-    const double S3x = mom[M2_S3X * N + i], S3y = mom[M2_S3Y * N + i], G0 = mom[M2_G0 * N + i];
-    const double G1x = mom[M2_G1X * N + i], G1y = mom[M2_G1Y * N + i];
-    const double u2 = ux * ux + uy * uy, S2 = S2xx + S2yy;
-    const double uS1 = ux * S1x + uy * S1y;
-    const double qx = 0.5 * (S3x - 2.0 * (ux * S2xx + uy * S2xy) + u2 * S1x - ux * S2 + 2.0 * ux * uS1 - ux * u2 * S0) +
-                      G1x - ux * G0;
-    const double qy = 0.5 * (S3y - 2.0 * (ux * S2xy + uy * S2yy) + u2 * S1y - uy * S2 + 2.0 * uy * uS1 - uy * u2 * S0) +
-                      G1y - uy * G0;
+    R qx, qy;
+    if constexpr (F32) {
+        qx = prf[P2_QX * N + i];
+        qy = prf[P2_QY * N + i];
+    } else {
+        const double S0 = mom[M2_S0 * N + i], S1x = mom[M2_S1X * N + i], S1y = mom[M2_S1Y * N + i];
+        const double S2xx = mom[M2_S2XX * N + i], S2yy = mom[M2_S2YY * N + i], S2xy = mom[M2_S2XY * N + i];
+        const double S3x = mom[M2_S3X * N + i], S3y = mom[M2_S3Y * N + i], G0 = mom[M2_G0 * N + i];
+        const double G1x = mom[M2_G1X * N + i], G1y = mom[M2_G1Y * N + i];
+        const double u2 = ux * ux + uy * uy, S2 = S2xx + S2yy;
+        const double uS1 = ux * S1x + uy * S1y;
+        qx = 0.5 * (S3x - 2.0 * (ux * S2xx + uy * S2xy) + u2 * S1x - ux * S2 + 2.0 * ux * uS1 - ux * u2 * S0) +
+             G1x - ux * G0;
+        qy = 0.5 * (S3y - 2.0 * (ux * S2xy + uy * S2yy) + u2 * S1y - uy * S2 + 2.0 * uy * uS1 - uy * u2 * S0) +
+             G1y - uy * G0;
+    }
     // transport, Eqs. (viscosity), (tau), (prandtl)
-    const double bn = s.b * n, xx = bn * chi;
-    const double mu = s.mu0_coef * sqrt(T) * (1.0 / chi + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
-    const double tau = mu / (n * T * (1.0 + 0.4 * xx));
-    const double Pr = (2.0 / 3.0) * (1.0 + 0.6 * xx) * (1.0 + 0.8 * xx + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * xx * xx) /
-                      ((1.0 + 0.4 * xx) * (1.0 + 1.2 * xx + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * xx * xx));
-    const double nu = (s.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 / tau : chi / tau;
-    if (!(n > 0.0) || !(T > 0.0)) atomicOr(err, (isfinite(n) && isfinite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
-    else if (!isfinite((double)fx + (double)fy) || !isfinite(nu) || !isfinite(qx + qy) || !isfinite(Ax + Ay))
+    const R c16 = R((4.0 / 25.0) * (1.0 + 12.0 / M_PI)), c9 = R((9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)));
+    const R bn = (R)s.b * n, xx = bn * chi;
+    const R mu = (R)s.mu0_coef * sqrt(T) * (R(1) / chi + R(0.8) * bn + c16 * bn * bn * chi);
+    const R tau = mu / (n * T * (R(1) + R(0.4) * xx));
+    const R Pr = R(2.0 / 3.0) * (R(1) + R(0.6) * xx) * (R(1) + R(0.8) * xx + c16 * xx * xx) /
+                 ((R(1) + R(0.4) * xx) * (R(1) + R(1.2) * xx + c9 * xx * xx));
+    const R nu = (s.relax == EVFDLB_RELAX_INV_TAU) ? R(1) / tau : chi / tau;
+    if (!(n > R(0)) || !(T > R(0))) atomicOr(err, (isfinite(n) && isfinite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
+    else if (!isfinite(fx + fy) || !isfinite(nu) || !isfinite(qx + qy) || !isfinite(Ax + Ay))
         atomicOr(err, ERR_NONFINITE);
     // polynomial coefficients of nu F^S + J1_F and nu G^S + J1_G over F_MB
     // (K = b n chi, sq = nu s with s = (1 - Pr)/(n T^2), div u = Dxx + Dyy)
-    const double K = xx, sq = nu * (1.0 - Pr) / (n * T * T), dv = Dxx + Dyy, iT = 1.0 / T;
-    double pf[10], pg[10];
-    pf[0] = nu + 0.8 * K * dv;
-    pf[1] = -0.8 * sq * qx - K * (Ax - 1.2 * Bx);
-    pf[2] = -0.8 * sq * qy - K * (Ay - 1.2 * By);
-    pf[3] = -0.4 * K * (Dxx + 0.5 * dv) * iT;
-    pf[4] = -0.4 * K * (Dxy + Dyx) * iT;
-    pf[5] = -0.4 * K * (Dyy + 0.5 * dv) * iT;
-    pf[6] = 0.2 * sq * qx * iT - 0.3 * K * Bx * iT;
-    pf[7] = 0.2 * sq * qy * iT - 0.3 * K * By * iT;
-    pf[8] = 0.2 * sq * qx * iT - 0.3 * K * Bx * iT;
-    pf[9] = 0.2 * sq * qy * iT - 0.3 * K * By * iT;
-    pg[0] = 0.5 * nu * T + 0.2 * T * K * dv;
-    pg[1] = -0.2 * T * sq * qx - 0.5 * T * K * (Ax - 0.6 * Bx);
-    pg[2] = -0.2 * T * sq * qy - 0.5 * T * K * (Ay - 0.6 * By);
-    pg[3] = -0.2 * K * (Dxx + 0.5 * dv);
-    pg[4] = -0.2 * K * (Dxy + Dyx);
-    pg[5] = -0.2 * K * (Dyy + 0.5 * dv);
-    pg[6] = 0.1 * sq * qx - 0.15 * K * Bx;
-    pg[7] = 0.1 * sq * qy - 0.15 * K * By;
-    pg[8] = 0.1 * sq * qx - 0.15 * K * Bx;
-    pg[9] = 0.1 * sq * qy - 0.15 * K * By;
+    const R K = xx, sq = nu * (R(1) - Pr) / (n * T * T), dv = Dxx + Dyy, iT = R(1) / T;
+    R pf[10], pg[10];
+    pf[0] = nu + R(0.8) * K * dv;
+    pf[1] = R(-0.8) * sq * qx - K * (Ax - R(1.2) * Bx);
+    pf[2] = R(-0.8) * sq * qy - K * (Ay - R(1.2) * By);
+    pf[3] = R(-0.4) * K * (Dxx + R(0.5) * dv) * iT;
+    pf[4] = R(-0.4) * K * (Dxy + Dyx) * iT;
+    pf[5] = R(-0.4) * K * (Dyy + R(0.5) * dv) * iT;
+    pf[6] = R(0.2) * sq * qx * iT - R(0.3) * K * Bx * iT;
+    pf[7] = R(0.2) * sq * qy * iT - R(0.3) * K * By * iT;
+    pf[8] = R(0.2) * sq * qx * iT - R(0.3) * K * Bx * iT;
+    pf[9] = R(0.2) * sq * qy * iT - R(0.3) * K * By * iT;
+    pg[0] = R(0.5) * nu * T + R(0.2) * T * K * dv;
+    pg[1] = R(-0.2) * T * sq * qx - R(0.5) * T * K * (Ax - R(0.6) * Bx);
+    pg[2] = R(-0.2) * T * sq * qy - R(0.5) * T * K * (Ay - R(0.6) * By);
+    pg[3] = R(-0.2) * K * (Dxx + R(0.5) * dv);
+    pg[4] = R(-0.2) * K * (Dxy + Dyx);
+    pg[5] = R(-0.2) * K * (Dyy + R(0.5) * dv);
+    pg[6] = R(0.1) * sq * qx - R(0.15) * K * Bx;
+    pg[7] = R(0.1) * sq * qy - R(0.15) * K * By;
+    pg[8] = R(0.1) * sq * qx - R(0.15) * K * Bx;
+    pg[9] = R(0.1) * sq * qy - R(0.15) * K * By;
     R* o = fld + i;
-    o[F2_N * N] = (R)n;
-    o[F2_UX * N] = (R)ux;
-    o[F2_UY * N] = (R)uy;
-    o[F2_T * N] = (R)T;
-    o[F2_NU * N] = (R)nu;
+    o[F2_N * N] = n;
+    o[F2_UX * N] = ux;
+    o[F2_UY * N] = uy;
+    o[F2_T * N] = T;
+    o[F2_NU * N] = nu;
     o[F2_FX * N] = fx;
     o[F2_FY * N] = fy;
+#pragma unroll
     for (int j = 0; j < 10; ++j) {
-        o[(F2_PF + j) * N] = (R)(n * pf[j]);
-        o[(F2_PG + j) * N] = (R)(n * pg[j]);
+        o[(F2_PF + j) * N] = n * pf[j];
+        o[(F2_PG + j) * N] = n * pg[j];
     }
 }
 
@@ -521,63 +781,35 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 // ---------------------------------------------------------------------------
 // k2_adv: WENO-5 faces along x and y, the right-hand side and the RK combine.
 // ---------------------------------------------------------------------------
-// One WENO-5 face in difference form (the algebra of the 1D kernels): with
-// d_i = v_{i+1} - v_i, the candidates are v2 plus corrections in d, the
-// smoothness indicators 4 (eps + beta_r) = s_r^2 + 13/3 t_r^2 + 4 eps from
-// first and second differences, and the linear weights are folded into the
-// corrections; eps4 = 4 eps.
-template <typename R>
-__device__ __forceinline__ R weno5_2(R v0, R v1, R v2, R v3, R v4, R eps4) {
-    const R d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3;
-    const R t0 = d1 - d0, t1 = d2 - d1, t2 = d3 - d2;
-    const R s0 = fma(R(3), d1, -d0), s1 = d1 + d2, s2 = fma(R(-3), d2, d3);
-    const R k133 = R(13.0 / 3.0);
-    const R e0 = fma(s0, s0, fma(k133 * t0, t0, eps4));
-    const R e1 = fma(s1, s1, fma(k133 * t1, t1, eps4));
-    const R e2 = fma(s2, s2, fma(k133 * t2, t2, eps4));
-    const R E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-    const R a0 = E1 * E2, a1 = E0 * E2, a2 = E0 * E1;
-    const R c0 = fma(R(5.0 / 60.0), d1, R(-2.0 / 60.0) * d0);
-    const R c1 = fma(R(0.2), d2, R(0.1) * d1);
-    const R c2 = fma(R(0.2), d2, R(-0.05) * d3);
-    const R num = fma(a0, c0, fma(a1, c1, a2 * c2));
-    const R den = fma(R(0.1), a0, fma(R(0.6), a1, R(0.3) * a2));
-    // FP32: the fast reciprocal-based quotient (2 ulp) is far inside the FP32
-    // variant's error budget; FP64 keeps the IEEE quotient
-    if constexpr (std::is_same<R, float>::value) return v2 + __fdividef(num, den);
-    else return v2 + num / den;
-}
-
-// The five stencil values of a face from a shared-memory pointer and a
-// compile-time stride: upwind for v >= 0 (q[0] .. q[4S]), mirrored for v < 0
-// (q[5S] .. q[S]).  The sign is uniform over a plane, so the branch is too.
-template <typename R, int S>
-__device__ __forceinline__ R face_at(const R* q, bool pos, R eps4) {
-    return pos ? weno5_2<R>(q[0], q[S], q[2 * S], q[3 * S], q[4 * S], eps4)
-               : weno5_2<R>(q[5 * S], q[4 * S], q[3 * S], q[2 * S], q[S], eps4);
-}
-
-// k2_adv: a 32x16 node tile and a run of velocity planes.  Per plane the
-// halo (tile +-3) is staged in shared memory (its global offsets computed
-// once per CTA); warp w forms the x faces of rows 2w, 2w+1 and the y faces
-// of face rows 2w, 2w+1 (lane = face or column); the last x face of each
-// row and the last y-face row go to warps 0 and 1.  Stencil offsets are
-// compile-time constants and the upwind branch is uniform per plane.  Then
-// the right-hand side and the Shu-Osher combine
+// A 32x16 node tile and a run of velocity planes.  Per plane the halo (tile
+// +-3) is staged in shared memory (its global offsets computed once per CTA),
+// then every thread forms one run of consecutive faces with the difference-
+// form WENO-5 of the 1D kernels (Weno5Run: the differences and the t-terms of
+// each cell formed once and shared by the run's faces): threads 0-127 the x
+// faces (16 rows x runs 5+4+4+4+4+4+4+4 of the 33 faces of a row), threads
+// 128-255 the y faces (32 columns x runs 5+4+4+4 of the 17 faces of a
+// column); for a negative velocity the stencil is mirrored and the run walked
+// down.  Then the right-hand side and the Shu-Osher combine
 //   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
+// Q is a compile-time parameter: the plane index splits by constants.
 template <typename R>
-__global__ void __launch_bounds__(256, 5)
+constexpr int adv_min_blocks() { return std::is_same<R, float>::value ? 4 : 3; }
+
+template <typename R, int Q>
+__global__ void __launch_bounds__(256, adv_min_blocks<R>())
 k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* base, R* out,
        const R* __restrict__ RL, double* rhs_out, double alpha, double beta, int mode) {
     constexpr int WX = kAdvX + 6, WY = kAdvY + 6, NH = WX * WY;
     constexpr int NHR = (NH + 255) / 256;                   // halo loads per thread
-    constexpr int RPW = kAdvY / 8;                          // rows per warp
+    constexpr int RPW = kAdvY / 8;                          // output rows per warp
+    constexpr int K = Q * Q;
+    static_assert(kAdvX == 32 && kAdvY == 16, "run split: 33 = 5 + 7 x 4 x-faces, 17 = 5 + 3 x 4 y-faces");
     __shared__ R Hs[NH];
     __shared__ R FX[kAdvY * (kAdvX + 1)];
     __shared__ R FY[(kAdvY + 1) * kAdvX];
     __shared__ long long rowoff[WY];
     __shared__ int coloff[WX];
-    const int Q = s.Q, K = Q * Q, nx = s.nx, ny = s.ny;
+    const int nx = s.nx, ny = s.ny;
     const long long N = s.N, NF = (long long)K * N;
     const int tilesx = (nx + kAdvX - 1) / kAdvX;
     const int x0 = (blockIdx.x % tilesx) * kAdvX, y0 = (blockIdx.x / tilesx) * kAdvY;
@@ -594,9 +826,19 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
         const int e = threadIdx.x + 256 * j;
         hoff[j] = (e < NH) ? rowoff[e / WX] + coloff[e % WX] : 0;
     }
-    const R eps4 = R(4) * (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
+    const R eps = (R)s.weno_eps, idx = (R)s.inv_dx, dt = (R)s.dt, ralpha = (R)alpha, rbeta = (R)beta;
     const bool with_base = (alpha != 0.0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this thread's run of faces: along x (threads 0-127) or y (128-255)
+    const bool xrun = threadIdx.x < 128;
+    const int rj = xrun ? (threadIdx.x >> 4) : ((threadIdx.x - 128) >> 5);   // run index
+    const int rl = xrun ? (threadIdx.x & 15) : (threadIdx.x & 31);           // row (x) or column (y)
+    const int fa = rj == 0 ? 0 : 4 * rj + 1, nrun = rj == 0 ? 5 : 4, fl = fa + nrun - 1;
+    const int hst = xrun ? 1 : WX;                        // halo stride along the run
+    // x face f of row r: stencil from halo (r + 3, f); y face f of column c: from halo (f, c + 3)
+    const R* hrow = xrun ? Hs + (rl + 3) * WX : Hs + rl + 3;
+    R* frow = xrun ? FX + rl * (kAdvX + 1) : FY + rl;
+    const int fst = xrun ? 1 : kAdvX;                     // face stride along the run
     // output nodes of this thread (rows warp*RPW + rr, column lane) and
     // their offsets in a velocity plane
     const int x = x0 + lane;
@@ -609,33 +851,50 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
         ooff[rr] = (long long)y * nx + x;
     }
     const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
+    auto plane_base = [&](int plane) { return (long long)(plane / K) * NF + (long long)(plane % K) * N; };
+    // the halo of the next plane is loaded into registers while this plane's
+    // faces are formed, and this plane's RL / base values before them
+    R hn[NHR];
+    {
+        const R* h = src + plane_base(p0);
+#pragma unroll
+        for (int j = 0; j < NHR; ++j) hn[j] = (threadIdx.x + 256 * j < NH) ? h[hoff[j]] : R(0);
+    }
     for (int plane = p0; plane < p1; ++plane) {
-        const int d = plane / K, k = plane % K;
+        const int k = plane % K;
         const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
-        const long long pbase = d * NF + (long long)k * N;
-        const R* h = src + pbase;
+        const long long pbase = plane_base(plane);
         __syncthreads();   // previous plane's faces and halo consumed
 #pragma unroll
-        for (int j = 0; j < NHR; ++j) {
-            const int e = threadIdx.x + 256 * j;
-            if (e < NH) Hs[e] = h[hoff[j]];
+        for (int j = 0; j < NHR; ++j)
+            if (threadIdx.x + 256 * j < NH) Hs[threadIdx.x + 256 * j] = hn[j];
+        if (plane + 1 < p1) {
+            const R* h = src + plane_base(plane + 1);
+#pragma unroll
+            for (int j = 0; j < NHR; ++j)
+                if (threadIdx.x + 256 * j < NH) hn[j] = h[hoff[j]];
         }
-        __syncthreads();
-        const bool px = vx >= R(0), py = vy >= R(0);
+        R rl[RPW], bs[RPW];
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
-            const int r = warp * RPW + rr;
-            // x face `lane` of row r: stencil starts at halo column lane
-            FX[r * (kAdvX + 1) + lane] = face_at<R, 1>(Hs + (r + 3) * WX + lane, px, eps4);
-            // y face row r, column lane: stencil starts at halo row r
-            FY[r * kAdvX + lane] = face_at<R, WX>(Hs + r * WX + lane + 3, py, eps4);
+            rl[rr] = oval[rr] ? RL[pbase + ooff[rr]] : R(0);
+            bs[rr] = (oval[rr] && with_base && mode == 0) ? base[pbase + ooff[rr]] : R(0);
         }
-        if (threadIdx.x < kAdvY) {                      // x face kAdvX of row threadIdx.x
-            const int r = threadIdx.x;
-            FX[r * (kAdvX + 1) + kAdvX] = face_at<R, 1>(Hs + (r + 3) * WX + kAdvX, px, eps4);
-        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kAdvX) {   // y face row kAdvY
-            const int c = threadIdx.x - 32;
-            FY[kAdvY * kAdvX + c] = face_at<R, WX>(Hs + kAdvY * WX + c + 3, py, eps4);
+        __syncthreads();
+        {
+            const bool pos = (xrun ? vx : vy) >= R(0);      // uniform per warp
+            const int dir = pos ? 1 : -1, f0 = pos ? fa : fl;
+            // v >= 0: face f uses halo f .. f+4, walked up; v < 0: f+5 .. f+1, walked down
+            const R* hb = hrow + (pos ? fa : fl + 5) * hst;
+            const int hs = dir * hst;
+            Weno5Run<R> w;
+            w.start(hb[0], hb[hs], hb[2 * hs], hb[3 * hs], hb[4 * hs], eps);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (q >= nrun) break;
+                frow[(f0 + dir * q) * fst] = w.face();
+                if (q + 1 < nrun) w.shift(hb[(q + 5) * hs]);
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -643,7 +902,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             if (!oval[rr]) continue;
             const int ty = warp * RPW + rr;
             const long long g = pbase + ooff[rr];
-            R Rv = RL[g];
+            R Rv = rl[rr];
             Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
             Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
             if (mode == 1) {
@@ -652,7 +911,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             }
             const R hv = Hs[(ty + 3) * WX + lane + 3];
             R o = rbeta * fma(dt, Rv, hv);
-            if (with_base) o = fma(ralpha, base[g], o);
+            if (with_base) o = fma(ralpha, bs[rr], o);
             out[g] = o;
         }
     }
@@ -846,6 +1105,96 @@ Taps2 taps_2d(const evfdlb_params& p) {
     for (long double v : w) t.mw.push_back((double)(v / wsum));
     return t;
 }
+
+// Force plan of k2_fields: the disc's offset columns a = 0 .. Mf, each as a
+// run of `steps` weight pairs (a multiple of 8: offsets b = -w .. w, then
+// zeros), column 0 with halved g2y (its pass adds n(x) twice); the columns
+// are dealt to the kFWarps warps longest first, each to the least loaded
+// warp (deterministic).  Layout of `plan`: kFWarps + 1 prefix offsets
+// (padded to kFPlanHead ints), then per entry {a, weight offset, steps, w}.
+struct ForcePlan {
+    std::vector<int> plan;
+    std::vector<double> w;     // (g2x, g2y) pairs
+    bool ok = true;
+};
+
+ForcePlan force_plan(const Taps2& t) {
+    ForcePlan fp;
+    const int Mf = t.Mf, D = 2 * Mf + 1;
+    std::vector<double> gx((size_t)D * D, 0.0), gy((size_t)D * D, 0.0);
+    std::vector<char> in((size_t)D * D, 0);
+    for (size_t j = 0; j < t.fg.size() / 2; ++j) {
+        const size_t k = (size_t)(t.foff[2 * j] + Mf) * D + (t.foff[2 * j + 1] + Mf);
+        gx[k] = t.fg[2 * j];
+        gy[k] = t.fg[2 * j + 1];
+        in[k] = 1;
+    }
+    auto at = [&](int a, int b) { return (size_t)(a + Mf) * D + (b + Mf); };
+    struct Col { int a, w, steps, off; };
+    std::vector<Col> cols;
+    for (int a = 0; a <= Mf; ++a) {
+        int w = -1;
+        for (int b = -Mf; b <= Mf; ++b)
+            if (in[at(a, b)] || in[at(-a, b)]) w = std::max(w, std::abs(b));
+        if (w < 0) continue;
+        for (int b = -w; b <= w; ++b)   // the pairing needs the disc's mirror symmetry, exactly
+            if (in[at(a, b)] != in[at(-a, b)] || gx[at(a, b)] != -gx[at(-a, b)] || gy[at(a, b)] != gy[at(-a, b)])
+                fp.ok = false;
+        const int steps = (2 * w + 8 + 7) & ~7;
+        cols.push_back({a, w, steps, (int)(fp.w.size() / 2)});
+        for (int j = 0; j < steps; ++j) {
+            const int b = j - w;
+            double x = 0.0, y = 0.0;
+            if (b <= w) {
+                x = (a == 0) ? 0.0 : gx[at(a, b)];
+                y = (a == 0) ? 0.5 * gy[at(a, b)] : gy[at(a, b)];
+            }
+            fp.w.push_back(x);
+            fp.w.push_back(y);
+        }
+    }
+    std::vector<int> order(cols.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cols[p].steps > cols[q].steps; });
+    std::vector<std::vector<int>> bins(kFWarps);
+    std::vector<long long> load(kFWarps, 0);
+    for (int ci : order) {
+        int best = 0;
+        for (int k = 1; k < kFWarps; ++k)
+            if (load[k] < load[best]) best = k;
+        bins[best].push_back(ci);
+        load[best] += cols[ci].steps;
+    }
+    fp.plan.assign(kFPlanHead, 0);
+    int n = 0;
+    for (int k = 0; k < kFWarps; ++k) {
+        fp.plan[k] = n;
+        n += (int)bins[k].size();
+    }
+    fp.plan[kFWarps] = n;
+    for (int k = 0; k < kFWarps; ++k)
+        for (int ci : bins[k]) {
+            const Col& c = cols[ci];
+            fp.plan.insert(fp.plan.end(), {c.a, c.off, c.steps, c.w});
+        }
+    return fp;
+}
+
+template <typename R>
+Pow2<R> make_pow2(int Q, const double* xi) {
+    Pow2<R> p{};
+    for (int k = 0; k < Q && k < 16; ++k) {
+        const double x = xi[k], x2 = x * x;
+        p.v[k] = (R)x;
+        p.v2[k] = (R)x2;
+        p.v3[k] = (R)(x2 * x);
+        p.h[k] = (float)x;
+        p.l[k] = (float)(x - (double)p.h[k]);
+        p.h2[k] = (float)x2;
+        p.l2[k] = (float)(x2 - (double)p.h2[k]);
+    }
+    return p;
+}
 }  // namespace
 
 bool validate_2d(const evfdlb_params& p) {
@@ -887,10 +1236,13 @@ struct Ctx2 {
     double* mom = nullptr;
     double* tables = nullptr;
     void* rtab = nullptr;
-    int* ft_off = nullptr;
-    void* ft_g = nullptr;
+    int* fplan = nullptr;        // force plan: per-warp column lists (k2_fields)
+    void* ftw = nullptr;         // force weight pairs per column step, precision R
     int* fm_off = nullptr;
-    double* fm_w = nullptr;
+    void* fm_w = nullptr;        // Fischer-Methfessel weights, precision R
+    float* prf = nullptr;        // FP32 build: node primitives [kNumPrf2][N] of the stage input
+    Pow2<float> pwf{};
+    Pow2<double> pwd{};
     double* scratch = nullptr;   // [2 Q^2 N + 8] doubles
     unsigned* err = nullptr;
     cudaGraphExec_t g_one = nullptr;
@@ -913,6 +1265,39 @@ void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, co
     }
 }
 
+// k2_adv is compiled for each even Q of the 2D model (4 .. 16)
+template <typename R>
+void launch_adv(int Q, dim3 g, cudaStream_t st, const Slab2& s, const R* rtab, const R* src, const R* base, R* out,
+                const R* RL, double* rhs_out, double alpha, double beta, int mode) {
+    switch (Q) {
+        case 4: k2_adv<R, 4><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        case 6: k2_adv<R, 6><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        case 8: k2_adv<R, 8><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        case 10: k2_adv<R, 10><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        case 12: k2_adv<R, 12><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        case 14: k2_adv<R, 14><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+        default: k2_adv<R, 16><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
+    }
+}
+
+// k2_moments: 128 nodes per CTA pass (grid-stride beyond 8192 CTAs)
+int moments_grid(long long N) { return (int)std::min<long long>((N + 127) / 128, 8192); }
+
+// k2_moments is compiled for each even Q of the 2D model (4 .. 16)
+template <typename R>
+void launch_moments(int Q, int nb, cudaStream_t st, const Slab2& s, const Pow2<R>& pw, const R* src, double* mom,
+                    float* prf, unsigned* err) {
+    switch (Q) {
+        case 4: k2_moments<R, 4><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        case 6: k2_moments<R, 6><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        case 8: k2_moments<R, 8><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        case 10: k2_moments<R, 10><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        case 12: k2_moments<R, 12><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        case 14: k2_moments<R, 14><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+        default: k2_moments<R, 16><<<nb, 256, 0, st>>>(s, pw, src, mom, prf, err); break;
+    }
+}
+
 template <typename R>
 cudaError_t coll_attr(int Q, size_t smem) {
     const int v = (int)smem;
@@ -932,16 +1317,20 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
                    double alpha, double beta, int mode) {
     const Slab2& s = c->s;
     const int Q = s.Q;
-    int nb = (int)std::min<long long>((s.N + 255) / 256, 4096);
-    k2_moments<R><<<nb, 256, 0, st>>>(s, c->tables, (const R*)src, c->mom, c->err);
+    constexpr bool F32 = std::is_same<R, float>::value;
+    // FP32: the field kernel reads the FP32 primitives; the FP64 raw sums are
+    // only needed by the FP64 build and by the diagnostics
+    const int nbm = moments_grid(s.N);
+    if constexpr (F32) launch_moments<float>(Q, nbm, st, s, c->pwf, (const float*)src, nullptr, c->prf, c->err);
+    else launch_moments<double>(Q, nbm, st, s, c->pwd, (const double*)src, c->mom, nullptr, c->err);
     dim3 gf((s.nx + kTile2 - 1) / kTile2, (s.ny + kTile2 - 1) / kTile2);
-    k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->ft_off, (const R*)c->ft_g, c->fm_off, c->fm_w,
-                                                   (R*)c->fld, c->err);
+    k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->prf, (const R*)c->ftw, c->fplan, c->fm_off,
+                                                   (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
     launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
     dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
-    k2_adv<R><<<ga, 256, 0, st>>>(s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL,
-                                   rhs_out, alpha, beta, mode);
+    launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
+                  alpha, beta, mode);
 }
 
 void queue_stage(Ctx2* c, cudaStream_t st, const void* src, const void* base, void* out, double* rhs_out,
@@ -970,10 +1359,11 @@ void destroy_2d(Ctx2* c) {
     cudaFree(c->mom);
     cudaFree(c->tables);
     if (c->rtab != c->tables) cudaFree(c->rtab);
-    cudaFree(c->ft_off);
-    cudaFree(c->ft_g);
+    cudaFree(c->fplan);
+    cudaFree(c->ftw);
     cudaFree(c->fm_off);
     cudaFree(c->fm_w);
+    cudaFree(c->prf);
     cudaFree(c->scratch);
     cudaFree(c->err);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -1022,28 +1412,34 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     alloc(&c->fld, c->esize * kNumFld2 * s.N);
     alloc((void**)&c->mom, sizeof(double) * kNumMom2 * s.N);
     alloc((void**)&c->tables, sizeof(double) * tab.size());
-    alloc((void**)&c->ft_off, sizeof(int) * t.foff.size());
-    alloc(&c->ft_g, c->esize * t.fg.size());
+    const ForcePlan fp = force_plan(t);
+    if (!fp.ok) e = cudaErrorInvalidValue;      // the tap set lost its mirror symmetry
+    const bool f32 = (c->prec == EVFDLB_FP32);
+    alloc((void**)&c->fplan, sizeof(int) * fp.plan.size());
+    alloc(&c->ftw, c->esize * fp.w.size());
     alloc((void**)&c->fm_off, sizeof(int) * t.moff.size());
-    alloc((void**)&c->fm_w, sizeof(double) * t.mw.size());
+    alloc(&c->fm_w, c->esize * t.mw.size());
+    if (f32) alloc((void**)&c->prf, sizeof(float) * kNumPrf2 * s.N);
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + 8));
     alloc((void**)&c->err, sizeof(unsigned));
-    std::vector<float> tabf(tab.begin(), tab.end()), fgf(t.fg.begin(), t.fg.end());
-    if (c->prec == EVFDLB_FP32) alloc(&c->rtab, sizeof(float) * tab.size());
+    std::vector<float> tabf(tab.begin(), tab.end()), ftwf(fp.w.begin(), fp.w.end()), mwf(t.mw.begin(), t.mw.end());
+    if (f32) alloc(&c->rtab, sizeof(float) * tab.size());
     else c->rtab = c->tables;
+    c->pwf = make_pow2<float>(p.Q, xi.data());
+    c->pwd = make_pow2<double>(p.Q, xi.data());
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
         e = cudaMemcpy(c->rtab, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->ft_off, t.foff.data(), sizeof(int) * t.foff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->fplan, fp.plan.data(), sizeof(int) * fp.plan.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = (c->prec == EVFDLB_FP32)
-                ? cudaMemcpy(c->ft_g, fgf.data(), sizeof(float) * fgf.size(), cudaMemcpyHostToDevice)
-                : cudaMemcpy(c->ft_g, t.fg.data(), sizeof(double) * t.fg.size(), cudaMemcpyHostToDevice);
+        e = f32 ? cudaMemcpy(c->ftw, ftwf.data(), sizeof(float) * ftwf.size(), cudaMemcpyHostToDevice)
+                : cudaMemcpy(c->ftw, fp.w.data(), sizeof(double) * fp.w.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->fm_off, t.moff.data(), sizeof(int) * t.moff.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->fm_w, t.mw.data(), sizeof(double) * t.mw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = f32 ? cudaMemcpy(c->fm_w, mwf.data(), sizeof(float) * mwf.size(), cudaMemcpyHostToDevice)
+                : cudaMemcpy(c->fm_w, t.mw.data(), sizeof(double) * t.mw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
-    const int H = std::max(s.Mf, s.mfm + 2), Wd = kTile2 + 2 * H, Ed = kTile2 + 4;
-    c->smem_fields = sizeof(double) * ((size_t)Wd * Wd + 5 * (size_t)Ed * Ed) + c->esize * (size_t)Wd * Wd;
+    c->smem_fields = f32 ? fields_smem_bytes<float>(s.Mf, s.mfm) : fields_smem_bytes<double>(s.Mf, s.mfm);
     c->smem_coll = (c->prec == EVFDLB_FP32) ? coll_smem_bytes<float>(p.Q) : coll_smem_bytes<double>(p.Q);
     if (c->smem_fields > 227 * 1024) e = cudaErrorInvalidValue;   // force disc too wide for a tile
     if (e == cudaSuccess) {
@@ -1167,8 +1563,11 @@ evfdlb_status rhs_2d(Ctx2* c, double* RF, double* RG, int on_device) {
 evfdlb_status moments_2d(Ctx2* c, double* n, double* u, double* T, double* q, double* totals, int on_device) {
     const long long N = c->s.N;
     int nb = (int)std::min<long long>((N + 255) / 256, 4096);
-    if (c->prec == EVFDLB_FP32) k2_moments<float><<<nb, 256, 0, c->user>>>(c->s, c->tables, (const float*)c->state[0], c->mom, c->err);
-    else k2_moments<double><<<nb, 256, 0, c->user>>>(c->s, c->tables, (const double*)c->state[0], c->mom, c->err);
+    const int nbm = moments_grid(N);
+    if (c->prec == EVFDLB_FP32)
+        launch_moments<float>(c->s.Q, nbm, c->user, c->s, c->pwf, (const float*)c->state[0], c->mom, nullptr, c->err);
+    else
+        launch_moments<double>(c->s.Q, nbm, c->user, c->s, c->pwd, (const double*)c->state[0], c->mom, nullptr, c->err);
     double* b = c->scratch;   // n [N], u [2N], T [N], q [2N], totals [4]
     double* dn = n ? (on_device ? n : b) : nullptr;
     double* du = u ? (on_device ? u : b + N) : nullptr;

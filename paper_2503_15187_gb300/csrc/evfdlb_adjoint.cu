@@ -47,11 +47,14 @@ struct AdjSmem {
     double* Ha;       // sum_l PT[l][j] cbar_l, [2][Q][Z]
     double* Hw;       // transposed WENO-5 part, [2][Q][Z]
     double* Red;      // per (distribution, node) sums [2][8][Z]
+    // f.Mtap [2M+1] (the 2m+1 Fischer-Methfessel taps) and f.Ftap [2M+1]
+    // (the Eq. (F1) taps) follow Red, staged once per CTA
 };
 
 __host__ __device__ inline size_t adj_smem_doubles(int Q, int Z, int M) {
     return 2 * (size_t)Q * Q + (Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + 2 * (size_t)Z +
-           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 6 * (size_t)Q * Z + 16 * (size_t)Z;
+           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 6 * (size_t)Q * Z + 16 * (size_t)Z +
+           2 * (size_t)(2 * M + 1);
 }
 
 __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
@@ -67,14 +70,14 @@ __device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
     s.f.Sc = s.f.Chi + (Z + 4);
     s.f.Scr = s.f.Sc + kNumScalars * Z;
     s.f.C = s.f.A = s.f.F = s.f.Face = nullptr;
-    s.f.Mtap = nullptr;            // the adjoint passes global tap pointers
-    s.f.Ftap = nullptr;
     s.H = s.f.Scr + 2 * Z;
     s.V = s.H + 2 * Q * (Z + 2 * kHaloH);
     s.Cb = s.V + 2 * Q * (Z + 2 * kHaloV);
     s.Ha = s.Cb + 2 * Q * Z;
     s.Hw = s.Ha + 2 * Q * Z;
     s.Red = s.Hw + 2 * Q * Z;
+    s.f.Mtap = s.Red + 16 * Z;
+    s.f.Ftap = s.f.Mtap + (2 * M + 1);
     return s;
 }
 
@@ -158,15 +161,17 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         int k = r % Q, d = r / Q;
         s.V[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloV + c, nx, bc)];
     }
+    for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.f.Ftap[j] = taps[sd.tap_off + j];
+    for (int j = threadIdx.x; j < 2 * sd.m + 1; j += blockDim.x) s.f.Mtap[j] = taps[sd.tap_off + 2 * sd.M + 1 + j];
     __syncthreads();
     // Warp 0 recomputes the node fields while warps 1-7 run phases 1 and 1b,
     // which need only v and the tables (named barrier 1 joins warps 1-7).
     const bool node_warp = threadIdx.x < 32;
     const int tid7 = threadIdx.x - 32, nth7 = blockDim.x - 32;
     if (node_warp) {
-        node_fields_pass1<double>(sd, it, s.f, taps + sd.tap_off + 2 * sd.M + 1, NN, nullptr, threadIdx.x, 32);
+        node_fields_pass1<double>(sd, it, s.f, s.f.Mtap, NN, nullptr, threadIdx.x, 32);
         __syncwarp();
-        node_fields_pass2<double>(sd, it, s.f, Z, taps + sd.tap_off, mom, NN, err, nullptr, threadIdx.x, 32);
+        node_fields_pass2<double>(sd, it, s.f, Z, s.f.Ftap, mom, NN, err, nullptr, threadIdx.x, 32);
     } else {
         // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
         // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term
@@ -461,7 +466,7 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
 // out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
 __host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m, int M) {
     return 5 * (size_t)(Z + 2 * m) + (size_t)kNumMoments * Z + (size_t)(Z + 4 * m) + (size_t)(Z + 2 * M) +
-           (size_t)(Z + 2 * m + 4) + 2 * (size_t)(Z + 4);
+           (size_t)(Z + 2 * m + 4) + 2 * (size_t)(Z + 4) + (size_t)(2 * M + 1) + (size_t)(2 * m + 1);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -486,8 +491,8 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     double* sDX = sF1 + (Z + 2 * M);       // X-gradient adjoint on [i0 - m - 2, i0 + nz + m + 2)
     double* sDU = sDX + (Z + 2 * m + 4);   // u- and T-gradient adjoints on [i0 - 2, i0 + nz + 2)
     double* sDT = sDU + (Z + 4);
-    const double* ftap = taps + sd.tap_off;
-    const double* mtap = ftap + 2 * M + 1;
+    double* ftap = sDT + (Z + 4);          // Eq. (F1) taps [2M+1] and FM taps [2m+1]
+    double* mtap = ftap + (2 * M + 1);
     const double inv12 = sd.inv_dx / 12.0;
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
@@ -505,6 +510,8 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         sDU[c] = gDU[i];
         sDT[c] = gDT[i];
     }
+    for (int j = threadIdx.x; j < 2 * M + 1; j += blockDim.x) ftap[j] = taps[sd.tap_off + j];
+    for (int j = threadIdx.x; j < 2 * m + 1; j += blockDim.x) mtap[j] = taps[sd.tap_off + 2 * M + 1 + j];
     __syncthreads();
     // transposed fourth-order difference at staged position p (value at p)
     auto d4t = [&](const double* g, int p) { return (g[p + 2] - 8.0 * g[p + 1] + 8.0 * g[p - 1] - g[p - 2]) * inv12; };

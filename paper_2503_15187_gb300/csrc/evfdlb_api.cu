@@ -122,7 +122,11 @@ struct evfdlb_ctx {
     bool origin_init = false;    // origin set by evfdlb_init (fields known)
     double* init_fields = nullptr;           // [3][NN]: n0, u0, T0
     std::vector<double*> ckpts;              // state at steps 0, K, 2K, ...
-    double* seg = nullptr;       // recomputed segment: (3K+1) states [2 NF] then (3K+1) moment sets [6 NN]
+    double* seg[2] = {nullptr, nullptr};   // recomputed segments (two: the recompute of one overlaps
+                                           // the reverse sweep of the other); each (3K+1) states [2 NF]
+                                           // then (3K+1) moment sets [6 NN]
+    cudaStream_t aux = nullptr;            // the adjoint's recompute stream
+    cudaEvent_t ev_fork = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_sweep[2] = {nullptr, nullptr};
     double* adj = nullptr;       // lam, y1, y2, acc [4][2 NF]; nadj [10 NN]; nbo [4 NN]; phis [NN]; phi [2 nbatch]
 };
 
@@ -157,7 +161,13 @@ void free_ctx(evfdlb_ctx* c) {
     cudaFree(c->scratch);
     cudaFree(c->init_fields);
     for (double* p : c->ckpts) cudaFree(p);
-    cudaFree(c->seg);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->seg[i]);
+        if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
+        if (c->ev_sweep[i]) cudaEventDestroy(c->ev_sweep[i]);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->aux) cudaStreamDestroy(c->aux);
     cudaFree(c->adj);
     cudaFree(c->slabs);
     cudaFree(c->items);
@@ -249,9 +259,20 @@ evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
         TRY_CUDA(cudaMemcpy(dphi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
         TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax), adj_moments_smem_bytes(kZMax, c->mmax, c->Mmax)));
     }
-    if (!c->seg && c->ckpt_every > 0) {
+    if (!c->seg[1] && c->ckpt_every > 0) {
         size_t nst = 3 * (size_t)c->ckpt_every + 1;
-        TRY_CUDA(cudaMalloc((void**)&c->seg, sizeof(double) * nst * (2 * (size_t)c->NF + kNumMoments * (size_t)c->NN)));
+        for (int i = 0; i < 2; ++i)
+            if (!c->seg[i])
+                TRY_CUDA(cudaMalloc((void**)&c->seg[i],
+                                    sizeof(double) * nst * (2 * (size_t)c->NF + kNumMoments * (size_t)c->NN)));
+    }
+    if (!c->aux) {
+        TRY_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        TRY_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        for (int i = 0; i < 2; ++i) {
+            TRY_CUDA(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
+            TRY_CUDA(cudaEventCreateWithFlags(&c->ev_sweep[i], cudaEventDisableTiming));
+        }
     }
     return EVFDLB_OK;
 }
@@ -790,29 +811,51 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     TRY_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * NN, c->user));
     const int K = c->ckpt_every;
     const size_t nst = 3 * (size_t)K + 1;
-    auto sstate = [&](size_t j) { return c->seg + j * 2 * NF; };
-    auto smom = [&](size_t j) { return c->seg + nst * 2 * NF + j * kNumMoments * NN; };
     const int n = (int)c->items_h.size();
     const int64_t nseg = (c->steps + K - 1) / K;
-    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
-        const int64_t s0 = sg * K;
-        const int ns = (int)std::min<int64_t>(K, c->steps - s0);
-        // recompute the segment from its checkpoint, keeping every stage input
-        TRY_CUDA(cudaMemcpyAsync(sstate(0), c->ckpts[sg], sizeof(double) * 2 * NF, cudaMemcpyDeviceToDevice, c->user));
-        launch_sums_p(EVFDLB_FP64, n, c->user, c->slabs, c->items, c->tables, c->tables, sstate(0), smom(0), NF, NN,
-                      c->err);
+    // Segments are swept last to first.  The recompute of segment sg - 1
+    // (from its checkpoint, on the aux stream, into the other segment buffer)
+    // runs while the user stream sweeps segment sg; the buffer is reused once
+    // the sweep of segment sg + 1 has finished with it.  Every kernel computes
+    // the same values as in a serial order: the overlap changes no result.
+    auto segp = [&](int64_t sg) { return c->seg[sg & 1]; };
+    auto recompute = [&](int64_t sg) -> cudaError_t {
+        double* base = segp(sg);
+        auto sst = [&](size_t j) { return base + j * 2 * NF; };
+        auto smo = [&](size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
+        const int ns = (int)std::min<int64_t>(K, c->steps - sg * K);
+        cudaError_t e = cudaMemcpyAsync(sst(0), c->ckpts[sg], sizeof(double) * 2 * NF, cudaMemcpyDeviceToDevice, c->aux);
+        if (e != cudaSuccess) return e;
+        launch_sums_p(EVFDLB_FP64, n, c->aux, c->slabs, c->items, c->tables, c->tables, sst(0), smo(0), NF, NN, c->err);
         for (int t = 0; t < ns; ++t) {
             size_t b = 3 * (size_t)t;
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sstate(b), nullptr, sstate(b + 1), nullptr, smom(b), smom(b + 1), NF, NN, 0.0,
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sst(b), nullptr, sst(b + 1), nullptr, smo(b), smo(b + 1), NF, NN, 0.0,
                            1.0, 0, c->Z, c->err);
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sstate(b + 1), sstate(b), sstate(b + 2), nullptr, smom(b + 1), smom(b + 2), NF,
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sst(b + 1), sst(b), sst(b + 2), nullptr, smo(b + 1), smo(b + 2), NF,
                            NN, 0.75, 0.25, 0, c->Z, c->err);
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->user, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sstate(b + 2), sstate(b), sstate(b + 3), nullptr, smom(b + 2), smom(b + 3), NF,
+            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
+                           c->taps, sst(b + 2), sst(b), sst(b + 3), nullptr, smo(b + 2), smo(b + 3), NF,
                            NN, 1.0 / 3.0, 2.0 / 3.0, 0, c->Z, c->err);
         }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_rec[sg & 1], c->aux);
+        return e;
+    };
+    TRY_CUDA(cudaEventRecord(c->ev_fork, c->user));      // the checkpoints and lam are ready
+    TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    TRY_CUDA(recompute(nseg - 1));
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        if (sg >= 1) {
+            if (sg + 1 <= nseg - 1) TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_sweep[(sg + 1) & 1], 0));
+            TRY_CUDA(recompute(sg - 1));
+        }
+        TRY_CUDA(cudaStreamWaitEvent(c->user, c->ev_rec[sg & 1], 0));
+        double* base = segp(sg);
+        auto sstate = [&](size_t j) { return base + j * 2 * NF; };
+        auto smom = [&](size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
+        const int ns = (int)std::min<int64_t>(K, c->steps - sg * K);
         // reverse sweep of the segment (Shu-Osher stages in reverse order):
         //   y2  = 2/3 lam + J(u2)^T (2/3 dt lam),   acc = 1/3 lam
         //   y1  = 1/4 y2  + J(u1)^T (1/4 dt y2),    acc += 3/4 y2
@@ -825,6 +868,7 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
             adj_stage(c, sstate(b), smom(b), y1, acc, nullptr, lam, 1.0, 1.0, 1, 1.0, 0.0, 0.0);
         }
         TRY_CUDA(cudaGetLastError());
+        TRY_CUDA(cudaEventRecord(c->ev_sweep[sg & 1], c->user));
     }
     evfdlb_status s2;
     if (dL_dF0 && (s2 = copy_out(c, dL_dF0, lam, sbytes, on_device)) != EVFDLB_OK) return s2;
