@@ -570,8 +570,8 @@ template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
     size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
     return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 2 * X + kNumFld2 * kNB +
-                        4 * (size_t)Q * kNB +
-                        2 * 4 * (size_t)Q * kNB);
+                        4 * (size_t)padded_q(Q) * kNB +
+                        2 * 4 * (size_t)padded_q(Q) * kNB);
 }
 
 // Four consecutive elements of a 16-byte aligned shared row.
@@ -591,9 +591,8 @@ __device__ __forceinline__ void load4(const double* p, double v[4]) {
 // In at a time, the right form four k at a time (four rows of In, four rows
 // of Rt; the padded rows and columns Q .. Qp-1 are zero).
 template <typename R, bool LEFT, int Q>
-__device__ __forceinline__ void block_transform(const R* __restrict__ M, const R* __restrict__ In, R* __restrict__ Out,
-                                                int i0, int j0) {
-    R acc[4][4];
+__device__ __forceinline__ void block_acc(const R* __restrict__ M, const R* __restrict__ In, R (&acc)[4][4], int i0,
+                                          int j0) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -626,6 +625,13 @@ __device__ __forceinline__ void block_transform(const R* __restrict__ M, const R
                     for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a][q], x[q][b], acc[a][b]);
         }
     }
+}
+
+template <typename R, bool LEFT, int Q>
+__device__ __forceinline__ void block_transform(const R* __restrict__ M, const R* __restrict__ In, R* __restrict__ Out,
+                                                int i0, int j0) {
+    R acc[4][4];
+    block_acc<R, LEFT, Q>(M, In, acc, i0, j0);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -649,8 +655,8 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     R* X0 = r3 + Qp;                       // [2][kNB] matrices, node stride NS (16-byte aligned)
     R* X1 = X0 + 2 * kNB * NS;
     R* sc = X1 + 2 * kNB * NS;             // [kNumFld2][kNB]
-    R* mux = sc + kNumFld2 * kNB;          // [4][Q][kNB]
-    R* Vy = mux + 4 * Q * kNB;             // [2][4][kNB][Q]
+    R* mux = sc + kNumFld2 * kNB;          // [kNB][4][Qp]
+    R* Vy = mux + 4 * Qp * kNB;            // [2][4][kNB][Qp]
     auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
     for (int e = threadIdx.x; e < Qp * kRow; e += blockDim.x) {
         int r = e / kRow, c = e % kRow;
@@ -663,9 +669,13 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
         r3[e] = rtab[L.r3 + e];
     }
     // state of the group as [d][node][kx][ky] (ky contiguous, rows of kRow);
-    // rows and columns Q .. Qp-1 of every matrix stay zero
-    for (int e = threadIdx.x; e < 2 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
-    __syncthreads();
+    // rows and columns Q .. Qp-1 of every matrix, and the padding of the
+    // moment rows, stay zero (nothing outside Q x Q is read when Qp = Q)
+    if constexpr (Qp != Q) {
+        for (int e = threadIdx.x; e < 2 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
+        for (int e = threadIdx.x; e < 4 * Qp * kNB * 3; e += blockDim.x) mux[e] = R(0);
+        __syncthreads();
+    }
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
         int t = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
         mat(X0, d, t)[(k / Q) * kRow + k % Q] = (t < nb) ? st[d * NF + (long long)k * N + i0 + t] : R(0);
@@ -703,10 +713,10 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             R mu2 = T * m[0] + T * T * r2[l] * m[2];
             R mu3 = R(3) * T * T * r1[l] * m[1] + T * T * T * r3[l] * m[3];
             if (!axis) {
-                mux[(0 * Q + l) * kNB + t] = mu0;
-                mux[(1 * Q + l) * kNB + t] = mu1;
-                mux[(2 * Q + l) * kNB + t] = mu2;
-                mux[(3 * Q + l) * kNB + t] = mu3;
+                mux[(t * 4 + 0) * Qp + l] = mu0;
+                mux[(t * 4 + 1) * Qp + l] = mu1;
+                mux[(t * 4 + 2) * Qp + l] = mu2;
+                mux[(t * 4 + 3) * Qp + l] = mu3;
             } else {
                 const R mb[4] = {mu0, mu1, mu2, mu3};
                 for (int a = 0; a < 4; ++a) {
@@ -715,8 +725,8 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
                         vf = fma(PF[a][b], mb[b], vf);
                         vg = fma(PG[a][b], mb[b], vg);
                     }
-                    Vy[((0 * 4 + a) * kNB + t) * Q + l] = vf;
-                    Vy[((1 * 4 + a) * kNB + t) * Q + l] = vg;
+                    Vy[((0 * 4 + a) * kNB + t) * Qp + l] = vf;
+                    Vy[((1 * 4 + a) * kNB + t) * Qp + l] = vg;
                 }
             }
             R mn = fma(u * rtab[L.rinv + l], m0, Tm1 * rtab[L.rr + l] * m1);
@@ -736,45 +746,89 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     // analysis along xi_x: X1[l][ky] = sum_kx psi_l(xi_kx) X0[kx][ky]
     if (active) block_transform<R, true, Q>(Pt, mat(X0, d, t), mat(X1, d, t), bi, bj);
     __syncthreads();
-    // analysis along xi_y: X0[l][m] = sum_ky X1[l][ky] psi_m(xi_ky)
-    if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X0, d, t), bi, bj);
-    __syncthreads();
-    // coefficients (relaxation -nu a, equilibria, J1, force terms) into X1: one y-order mm per
-    // thread (lanes on consecutive mm: conflict-free rows), looping over the
-    // x-order l; the y-moment factors of the thread are loop-invariant
-    for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
-        const int mm = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
-        const R* A = mat(X0, dd, tt);
-        R* C = mat(X1, dd, tt);
-        const R mnu = -sc[F2_NU * kNB + tt];
-        R vy[4];
+    // analysis along xi_y, Z[l][m] = sum_ky X1[l][ky] psi_m(xi_ky), and the
+    // coefficients (relaxation -nu a, equilibria, J1, force terms)
+    //   C[l][m] = sum_a mu^a_l V^a_m + F_x r1_l Z[l-1][m] + F_y r1_m Z[l][m-1] - nu Z[l][m]
+    // into CB.  When an item's blocks lie in one warp (32 % nblk == 0) they
+    // are formed in the transform's epilogue: Z[l-1][.] of a block's top row
+    // and Z[.][m-1] of its left column come from the blocks above and to the
+    // left by warp shuffles.  Otherwise a separate pass over Z.
+    constexpr bool kFuse = (32 % ((Qp / 4) * (Qp / 4)) == 0);
+    R* CB = kFuse ? X0 : X1;
+    R* OB = kFuse ? X1 : X0;
+    if constexpr (kFuse) {
+        R acc[4][4];
+        if (active) block_acc<R, false, Q>(Pt, mat(X1, d, t), acc, bi, bj);
+        R up[4], left[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * Q + mm];
-        const R fx = sc[F2_FX * kNB + tt], fyr = sc[F2_FY * kNB + tt] * r1[mm];
+        for (int b = 0; b < 4; ++b) up[b] = __shfl_up_sync(0xffffffffu, acc[3][b], Qp / 4);
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-            R c = 0;
+        for (int a = 0; a < 4; ++a) left[a] = __shfl_up_sync(0xffffffffu, acc[a][3], 1);
+        if (active) {
+            const R mnu = -sc[F2_NU * kNB + t], fx = sc[F2_FX * kNB + t], fy = sc[F2_FY * kNB + t];
+            R mx[4][4], vv[4][4], rl[4], rm[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) c = fma(mux[(a * Q + l) * kNB + tt], vy[a], c);
-            if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
-            if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
-            c = fma(mnu, A[l * kRow + mm], c);
-            C[l * kRow + mm] = c;
+            for (int a = 0; a < 4; ++a) {
+                load4(mux + (t * 4 + a) * Qp + bi, mx[a]);
+                load4(Vy + ((d * 4 + a) * kNB + t) * Qp + bj, vv[a]);
+            }
+            load4(r1 + bi, rl);
+            load4(r1 + bj, rm);
+            R* C = mat(CB, d, t);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int l = bi + a, m = bj + b;
+                    R c = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) c = fma(mx[q][a], vv[q][b], c);
+                    if (l >= 1) c = fma(fx * rl[a], a == 0 ? up[b] : acc[a - 1][b], c);
+                    if (m >= 1) c = fma(fy * rm[b], b == 0 ? left[a] : acc[a][b - 1], c);
+                    c = fma(mnu, acc[a][b], c);
+                    C[l * kRow + m] = (l < Q && m < Q) ? c : R(0);
+                }
         }
+        __syncthreads();
+    } else {
+        if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X0, d, t), bi, bj);
+        __syncthreads();
+        // one y-order mm per thread (lanes on consecutive mm: conflict-free
+        // rows), looping over the x-order l; its y-moment factors are loop-invariant
+        for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
+            const int mm = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
+            const R* A = mat(X0, dd, tt);
+            R* C = mat(X1, dd, tt);
+            const R mnu = -sc[F2_NU * kNB + tt];
+            R vy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * Qp + mm];
+            const R fx = sc[F2_FX * kNB + tt], fyr = sc[F2_FY * kNB + tt] * r1[mm];
+#pragma unroll
+            for (int l = 0; l < Q; ++l) {
+                R c = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) c = fma(mux[(tt * 4 + a) * Qp + l], vy[a], c);
+                if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
+                if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
+                c = fma(mnu, A[l * kRow + mm], c);
+                C[l * kRow + mm] = c;
+            }
+        }
+        __syncthreads();
     }
+    // synthesis along xi_x: OB[kx][m] = sum_l w_kx psi_l(xi_kx) CB[l][m]
+    if (active) block_transform<R, true, Q>(St, mat(CB, d, t), mat(OB, d, t), bi, bj);
     __syncthreads();
-    // synthesis along xi_x: X0[kx][m] = sum_l w_kx psi_l(xi_kx) X1[l][m]
-    if (active) block_transform<R, true, Q>(St, mat(X1, d, t), mat(X0, d, t), bi, bj);
+    // synthesis along xi_y: CB[kx][ky] = sum_m OB[kx][m] w_ky psi_m(xi_ky)
+    if (active) block_transform<R, false, Q>(St, mat(OB, d, t), mat(CB, d, t), bi, bj);
     __syncthreads();
-    // synthesis along xi_y: X1[kx][ky] = sum_m X0[kx][m] w_ky psi_m(xi_ky)
-    if (active) block_transform<R, false, Q>(St, mat(X0, d, t), mat(X1, d, t), bi, bj);
-    __syncthreads();
-    // the local right-hand side -nu h + sum S S c (both in X1)
+    // the local right-hand side -nu h + sum S S c (both in CB)
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
         int tt = e % kNB, k = (e / kNB) % K, dd = e / (kNB * K);
         if (tt >= nb) continue;
         const int off = (k / Q) * kRow + k % Q;
-        RL[dd * NF + (long long)k * N + i0 + tt] = mat(X1, dd, tt)[off];
+        RL[dd * NF + (long long)k * N + i0 + tt] = mat(CB, dd, tt)[off];
     }
 }
 
