@@ -88,7 +88,8 @@ enum { EVFDLB_RELAX_INV_TAU = 0, EVFDLB_RELAX_CHI_OVER_TAU = 1 };
  * z as the in-plane kernel summed over the grid offsets inside the r_cut
  * disc, the Fischer-Methfessel average with chord weights, WENO-5 and
  * fourth-order gradients along each axis; periodic only, EV1, FP32 or FP64,
- * gamma an even integer, dt = cfl dx / (2 max|xi|) when dt <= 0.  A 2D
+ * gamma an even integer, nx * ny < 2^31, dt = cfl dx / (2 max|xi|) when
+ * dt <= 0 (otherwise E_INVALID_ARG).  A 2D
  * context has nbatch = 1; evfdlb_fields, evfdlb_tune, evfdlb_rhs_vjp and the
  * adjoint return E_UNSUPPORTED for it. */
 typedef struct {

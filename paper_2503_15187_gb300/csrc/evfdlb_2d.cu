@@ -570,8 +570,8 @@ template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
     size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
     return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 2 * X + kNumFld2 * kNB +
-                        4 * (size_t)padded_q(Q) * kNB +
-                        2 * 4 * (size_t)padded_q(Q) * kNB);
+                        (4 * (size_t)padded_q(Q) + 4) * kNB +
+                        2 * 4 * (size_t)(padded_q(Q) + 4) * kNB);
 }
 
 // Four consecutive elements of a 16-byte aligned shared row.
@@ -582,6 +582,15 @@ __device__ __forceinline__ void load4(const float* p, float v[4]) {
 __device__ __forceinline__ void load4(const double* p, double v[4]) {
     const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// Four consecutive elements to a 16-byte aligned shared row.
+__device__ __forceinline__ void store4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
 // Out[i][j] = sum_k Lt[k][i] In[k][j]  (left contraction, Lt = transposed left matrix)
@@ -632,10 +641,9 @@ __device__ __forceinline__ void block_transform(const R* __restrict__ M, const R
                                                 int i0, int j0) {
     R acc[4][4];
     block_acc<R, LEFT, Q>(M, In, acc, i0, j0);
+    // one 16-byte store per row: the 32 rows of a warp fill the banks 4 wavefronts deep
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) Out[(i0 + a) * kRow + j0 + b] = acc[a][b];
+    for (int a = 0; a < 4; ++a) store4(Out + (i0 + a) * kRow + j0, acc[a]);
 }
 
 template <typename R, int Q>
@@ -655,8 +663,11 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     R* X0 = r3 + Qp;                       // [2][kNB] matrices, node stride NS (16-byte aligned)
     R* X1 = X0 + 2 * kNB * NS;
     R* sc = X1 + 2 * kNB * NS;             // [kNumFld2][kNB]
-    R* mux = sc + kNumFld2 * kNB;          // [kNB][4][Qp]
-    R* Vy = mux + 4 * Qp * kNB;            // [2][4][kNB][Qp]
+    // node strides padded by 4 so that the eight nodes' writes fall in
+    // different banks; rows stay 16-byte aligned for the epilogue's loads
+    constexpr int MXS = 4 * Qp + 4, VYS = Qp + 4;
+    R* mux = sc + kNumFld2 * kNB;          // [kNB][4][Qp], node stride MXS
+    R* Vy = mux + MXS * kNB;               // [2][4][kNB][Qp], node stride VYS
     auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
     for (int e = threadIdx.x; e < Qp * kRow; e += blockDim.x) {
         int r = e / kRow, c = e % kRow;
@@ -673,7 +684,7 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
     // moment rows, stay zero (nothing outside Q x Q is read when Qp = Q)
     if constexpr (Qp != Q) {
         for (int e = threadIdx.x; e < 2 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
-        for (int e = threadIdx.x; e < 4 * Qp * kNB * 3; e += blockDim.x) mux[e] = R(0);
+        for (int e = threadIdx.x; e < MXS * kNB + 8 * VYS * kNB; e += blockDim.x) mux[e] = R(0);
         __syncthreads();
     }
     for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
@@ -685,10 +696,11 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
         sc[e] = (t < nb) ? fld[f * N + i0 + t] : (f == F2_N || f == F2_T ? R(1) : R(0));
     }
     __syncthreads();
-    // one-axis Gaussian moments: x for thread t < kNB, y (folded with the
-    // polynomial coefficients) for kNB <= t < 2 kNB
-    if (threadIdx.x < 2 * kNB) {
-        const int t = threadIdx.x % kNB, axis = threadIdx.x / kNB;
+    // one-axis Gaussian moments: x on lanes 0 .. kNB-1 of warp 0, y (folded
+    // with the polynomial coefficients) on lanes 0 .. kNB-1 of warp 1, so
+    // that the two recurrences run side by side instead of diverging
+    if (threadIdx.x < 64 && (threadIdx.x & 31) < kNB) {
+        const int t = threadIdx.x & 31, axis = threadIdx.x >> 5;
         const R u = sc[(axis ? F2_UY : F2_UX) * kNB + t], T = sc[F2_T * kNB + t], Tm1 = T - R(1);
         R m[4] = {0, 0, 0, 0};   // m_{l}, m_{l-1}, m_{l-2}, m_{l-3}
         R m0 = 1, m1 = 0;
@@ -713,10 +725,10 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             R mu2 = T * m[0] + T * T * r2[l] * m[2];
             R mu3 = R(3) * T * T * r1[l] * m[1] + T * T * T * r3[l] * m[3];
             if (!axis) {
-                mux[(t * 4 + 0) * Qp + l] = mu0;
-                mux[(t * 4 + 1) * Qp + l] = mu1;
-                mux[(t * 4 + 2) * Qp + l] = mu2;
-                mux[(t * 4 + 3) * Qp + l] = mu3;
+                mux[t * MXS + 0 * Qp + l] = mu0;
+                mux[t * MXS + 1 * Qp + l] = mu1;
+                mux[t * MXS + 2 * Qp + l] = mu2;
+                mux[t * MXS + 3 * Qp + l] = mu3;
             } else {
                 const R mb[4] = {mu0, mu1, mu2, mu3};
                 for (int a = 0; a < 4; ++a) {
@@ -725,8 +737,8 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
                         vf = fma(PF[a][b], mb[b], vf);
                         vg = fma(PG[a][b], mb[b], vg);
                     }
-                    Vy[((0 * 4 + a) * kNB + t) * Qp + l] = vf;
-                    Vy[((1 * 4 + a) * kNB + t) * Qp + l] = vg;
+                    Vy[((0 * 4 + a) * kNB + t) * VYS + l] = vf;
+                    Vy[((1 * 4 + a) * kNB + t) * VYS + l] = vg;
                 }
             }
             R mn = fma(u * rtab[L.rinv + l], m0, Tm1 * rtab[L.rr + l] * m1);
@@ -769,14 +781,15 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             R mx[4][4], vv[4][4], rl[4], rm[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                load4(mux + (t * 4 + a) * Qp + bi, mx[a]);
-                load4(Vy + ((d * 4 + a) * kNB + t) * Qp + bj, vv[a]);
+                load4(mux + t * MXS + a * Qp + bi, mx[a]);
+                load4(Vy + ((d * 4 + a) * kNB + t) * VYS + bj, vv[a]);
             }
             load4(r1 + bi, rl);
             load4(r1 + bj, rm);
             R* C = mat(CB, d, t);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a) {
+                R cr[4];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const int l = bi + a, m = bj + b;
@@ -786,8 +799,10 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
                     if (l >= 1) c = fma(fx * rl[a], a == 0 ? up[b] : acc[a - 1][b], c);
                     if (m >= 1) c = fma(fy * rm[b], b == 0 ? left[a] : acc[a][b - 1], c);
                     c = fma(mnu, acc[a][b], c);
-                    C[l * kRow + m] = (l < Q && m < Q) ? c : R(0);
+                    cr[b] = (l < Q && m < Q) ? c : R(0);
                 }
+                store4(C + (bi + a) * kRow + bj, cr);
+            }
         }
         __syncthreads();
     } else {
@@ -802,13 +817,13 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
             const R mnu = -sc[F2_NU * kNB + tt];
             R vy[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * Qp + mm];
+            for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * VYS + mm];
             const R fx = sc[F2_FX * kNB + tt], fyr = sc[F2_FY * kNB + tt] * r1[mm];
 #pragma unroll
             for (int l = 0; l < Q; ++l) {
                 R c = 0;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) c = fma(mux[(tt * 4 + a) * Qp + l], vy[a], c);
+                for (int a = 0; a < 4; ++a) c = fma(mux[tt * MXS + a * Qp + l], vy[a], c);
                 if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
                 if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
                 c = fma(mnu, A[l * kRow + mm], c);
@@ -847,7 +862,7 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 //   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
 // Q is a compile-time parameter: the plane index splits by constants.
 template <typename R>
-constexpr int adv_min_blocks() { return std::is_same<R, float>::value ? 4 : 3; }
+constexpr int adv_min_blocks() { return std::is_same<R, float>::value ? 4 : 2; }
 
 template <typename R, int Q>
 __global__ void __launch_bounds__(256, adv_min_blocks<R>())
@@ -861,20 +876,21 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
     __shared__ R Hs[NH];
     __shared__ R FX[kAdvY * (kAdvX + 1)];
     __shared__ R FY[(kAdvY + 1) * kAdvX];
-    __shared__ long long rowoff[WY];
+    __shared__ int rowoff[WY];
     __shared__ int coloff[WX];
     const int nx = s.nx, ny = s.ny;
     const long long N = s.N, NF = (long long)K * N;
     const int tilesx = (nx + kAdvX - 1) / kAdvX;
     const int x0 = (blockIdx.x % tilesx) * kAdvX, y0 = (blockIdx.x / tilesx) * kAdvY;
     TableLayout L(Q);
-    // wrapped halo coordinates, shared by every plane of this tile
+    // wrapped halo coordinates, shared by every plane of this tile (node
+    // offsets fit 32 bits: the 2D context holds fewer than 2^31 nodes)
     for (int e = threadIdx.x; e < WY + WX; e += blockDim.x) {
-        if (e < WY) rowoff[e] = (long long)wrapi(y0 - 3 + e, ny) * nx;
+        if (e < WY) rowoff[e] = wrapi(y0 - 3 + e, ny) * nx;
         else coloff[e - WY] = wrapi(x0 - 3 + (e - WY), nx);
     }
     __syncthreads();
-    long long hoff[NHR];
+    int hoff[NHR];
 #pragma unroll
     for (int j = 0; j < NHR; ++j) {
         const int e = threadIdx.x + 256 * j;
@@ -896,13 +912,13 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
     // output nodes of this thread (rows warp*RPW + rr, column lane) and
     // their offsets in a velocity plane
     const int x = x0 + lane;
-    long long ooff[RPW];
+    int ooff[RPW];
     bool oval[RPW];
 #pragma unroll
     for (int rr = 0; rr < RPW; ++rr) {
         const int y = y0 + warp * RPW + rr;
         oval[rr] = (x < nx && y < ny);
-        ooff[rr] = (long long)y * nx + x;
+        ooff[rr] = oval[rr] ? y * nx + x : 0;
     }
     const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
     auto plane_base = [&](int plane) { return (long long)(plane / K) * NF + (long long)(plane % K) * N; };
@@ -928,11 +944,13 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             for (int j = 0; j < NHR; ++j)
                 if (threadIdx.x + 256 * j < NH) hn[j] = h[hoff[j]];
         }
+        const R* rlp = RL + pbase;
+        const R* bsp = base + pbase;
         R rl[RPW], bs[RPW];
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
-            rl[rr] = oval[rr] ? RL[pbase + ooff[rr]] : R(0);
-            bs[rr] = (oval[rr] && with_base && mode == 0) ? base[pbase + ooff[rr]] : R(0);
+            rl[rr] = oval[rr] ? rlp[ooff[rr]] : R(0);
+            bs[rr] = (oval[rr] && with_base && mode == 0) ? bsp[ooff[rr]] : R(0);
         }
         __syncthreads();
         {
@@ -951,22 +969,22 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             }
         }
         __syncthreads();
+        R* op = out + pbase;
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
             if (!oval[rr]) continue;
             const int ty = warp * RPW + rr;
-            const long long g = pbase + ooff[rr];
             R Rv = rl[rr];
             Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
             Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
             if (mode == 1) {
-                rhs_out[g] = (double)Rv;
+                rhs_out[pbase + ooff[rr]] = (double)Rv;
                 continue;
             }
             const R hv = Hs[(ty + 3) * WX + lane + 3];
             R o = rbeta * fma(dt, Rv, hv);
             if (with_base) o = fma(ralpha, bs[rr], o);
-            out[g] = o;
+            op[ooff[rr]] = o;
         }
     }
 }
@@ -1253,6 +1271,7 @@ Pow2<R> make_pow2(int Q, const double* xi) {
 
 bool validate_2d(const evfdlb_params& p) {
     if (p.dim != 2 || p.nx < 8 || p.ny < 8 || !(p.dx > 0) || !(p.sigma > 0) || !(p.phi_a >= 0)) return false;
+    if ((long long)p.nx * p.ny >= (1LL << 31)) return false;   // node offsets are 32-bit in k2_adv
     if (p.Q < 4 || p.Q > 16 || (p.Q & 1) || p.bc != EVFDLB_BC_PERIODIC) return false;
     if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) return false;
     if (!(p.weno_eps > 0) || (!(p.dt > 0) && !(p.cfl > 0 && p.cfl <= 1))) return false;

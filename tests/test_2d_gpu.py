@@ -6,7 +6,7 @@ RK step 1e-12 (the 1D bars).  FP32 build (the phase-separation variant:
 FP32 bulk, FP64 conserved sums): 2e-7 for the projected state (one FP32
 rounding), 1e-5 per step (Q^2-term Hermite transforms and WENO in FP32,
 u = 2^-24).  Grids are not multiples of the 16x16 field tiles, the 8-node
-collision groups or the 32x8 advection tiles.  At the full 1024 x 1024,
+collision groups or the 32x16 advection tiles.  At the full 1024 x 1024,
 16 x 16-velocity size the checks are properties that hold at any size: a
 uniform state is stationary, mass and momentum are conserved.
 """
