@@ -40,7 +40,10 @@ def make(nx, ny, Q, prec, dx=0.25):
     return sim, orc
 
 
-CASES = [(24, 20, 6), (19, 33, 8)]
+# (19, 17, 16): the velocity count of the 2D workload, where the FP32 build
+# runs its collision transforms on the tensor cores (3xTF32); 323 nodes leave
+# a ragged last group of 3 nodes
+CASES = [(24, 20, 6), (19, 33, 8), (19, 17, 16)]
 
 
 @pytest.mark.parametrize("nx,ny,Q", CASES)
