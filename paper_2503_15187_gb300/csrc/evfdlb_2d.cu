@@ -857,304 +857,6 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 }
 
 // ---------------------------------------------------------------------------
-// k2_coll_tc: k2_coll for an FP32 state with Q = 16 on the tensor cores
-// (tcgen05.mma, kind::tf32).  A group of kNB = 8 nodes: per distribution the
-// sixteen 16x16 velocity matrices of the group form one M = 128 operand
-// tile; the four one-axis transforms are D[128][16] = A[128][16] Bt[16][16]^T
-// with the analysis table psi_l(xi_j) or the synthesis table w_k psi_l(xi_k)
-// as Bt.  FP32 accuracy from three TF32 products (3xTF32): a = a_hi + a_lo
-// with a_hi the 10-bit-mantissa head, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
-// (relative error about 1e-6 per transform against 6e-8 for SIMT FP32, far
-// inside the FP32 variant's error budget).  Operands are K-major in the
-// canonical no-swizzle layout (8-row x 16-byte core matrices, K-adjacent
-// ones 128 bytes apart, 8-row groups 512 bytes apart); tile rows are ordered
-// (free index, node), so that the state scatter and every epilogue transpose
-// (TMEM row -> next operand column) write 32 distinct banks per warp.
-// Accumulators live in TMEM (32 columns: distribution d in columns 16d ..);
-// warp w reads lanes 32 (w % 4) .. of distribution w / 4.  One thread issues
-// the MMAs; completion is tracked by an mbarrier with a bounded wait (on
-// timeout the CTA records ERR_TIMEOUT, skips the rest and frees its TMEM).
-// The collision coefficients are formed in the epilogue of the second
-// analysis transform as in k2_coll (same operations, same order).
-// ---------------------------------------------------------------------------
-namespace tc {
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// byte offset of element (r, k) of a K = 16 operand tile
-__device__ __forceinline__ uint32_t koff(int r, int k) {
-    return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
-// shared-memory matrix descriptor: start address, leading byte offset 128
-// (K direction), stride byte offset 512 (8-row groups), descriptor version 1,
-// no swizzle
-__device__ __forceinline__ uint64_t desc(uint32_t a) {
-    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
-           ((uint64_t)1 << 46);
-}
-// instruction descriptor: D F32, A and B TF32, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-// element (r, k) split into its TF32 head (hi tile) and FP32 remainder (lo
-// tile, `lo` bytes after the hi tile)
-__device__ __forceinline__ void put(unsigned char* hi, uint32_t lo, int r, int k, float x) {
-    const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    const uint32_t o = koff(r, k);
-    *reinterpret_cast<float*>(hi + o) = h;
-    *reinterpret_cast<float*>(hi + lo + o) = x - h;
-}
-constexpr uint32_t kLoA = 8192, kLoB = 1024;   // operand tile 128 x 16, table 16 x 16
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
-}
-__device__ __forceinline__ void commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 20) && !done; ++it)
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-    return done != 0;
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-}  // namespace tc
-
-constexpr int kTcMXS = 4 * 16 + 4, kTcVYS = 16 + 4, kTcXB = 17, kTcWarps = 4;
-// byte offsets of the analysis (P) and synthesis (S) tables in the 4 KB
-// image of TF32-split transform tables, each [hi 1 KB | lo 1 KB]
-constexpr int kTcImgP = 0, kTcImgS = 2048, kTcImgBytes = 4096;
-__host__ __device__ constexpr size_t coll_tc_smem_bytes() {
-    return 16384 + kTcImgBytes +
-           sizeof(float) * (kNumFld2 * kNB + kTcMXS * kNB + 8 * kTcVYS * kNB + 3 * 16 + kTcWarps * kNB * kTcXB) + 16;
-}
-// the image on the host: Bt[n][k] = P[n][k] = psi_n(xi_k) and S[n][k] =
-// w_n psi_k(xi_n), split into TF32 head and FP32 remainder, in the operand
-// layout of the kernel
-inline void coll_tc_image(const float* rtab, const TableLayout& L, unsigned char* img) {
-    auto koff = [](int r, int k) { return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4; };
-    auto put = [&](int base, int r, int k, float x) {
-        uint32_t b;
-        memcpy(&b, &x, 4);
-        b &= 0xFFFFE000u;
-        float h;
-        memcpy(&h, &b, 4);
-        const float l = x - h;
-        memcpy(img + base + koff(r, k), &h, 4);
-        memcpy(img + base + 1024 + koff(r, k), &l, 4);
-    };
-    for (int n = 0; n < 16; ++n)
-        for (int k = 0; k < 16; ++k) {
-            put(kTcImgP, n, k, rtab[L.P + n * 16 + k]);
-            put(kTcImgS, n, k, rtab[L.S + n * 16 + k]);
-        }
-}
-
-// One CTA = one distribution of one group of kNB nodes (128 threads), so
-// that several independent MMA -> epilogue chains share an SM.
-template <int Q>
-__global__ void __launch_bounds__(128, 7)
-k2_coll_tc(Slab2 s, const float* __restrict__ rtab, const uint4* __restrict__ img, const float* __restrict__ st,
-           const float* __restrict__ fld, float* __restrict__ RL, unsigned* err) {
-    static_assert(Q == 16 && kNB == 8, "tensor tiles: 8 nodes x 16 rows = M 128, K = N = 16");
-    constexpr int K2 = Q * Q, MXS = kTcMXS, VYS = kTcVYS, XB = kTcXB;
-    extern __shared__ __align__(1024) unsigned char smt[];
-    unsigned char* A = smt;                                   // operand tile [hi 8 KB | lo 8 KB]
-    unsigned char* B = smt + 16384;                           // the table image
-    float* sc = reinterpret_cast<float*>(B + kTcImgBytes);    // [kNumFld2][kNB]
-    float* mux = sc + kNumFld2 * kNB;                         // [kNB][4][16], node stride MXS
-    float* Vy = mux + MXS * kNB;                              // [2][4][kNB] rows of VYS
-    float* r1 = Vy + 8 * VYS * kNB;
-    float* r2 = r1 + 16;
-    float* r3 = r2 + 16;
-    float* xb = r3 + 16;                                      // [warp][node][XB]: last Z rows of each warp
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(xb + kTcWarps * kNB * XB);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-    const long long N = s.N, NF = (long long)K2 * N;
-    const int dd = blockIdx.x & 1;
-    const long long i0 = (long long)(blockIdx.x >> 1) * kNB;
-    const int nb = (int)min((long long)kNB, N - i0);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const float* src = st + dd * NF;
-    TableLayout L(Q);
-    // ---- phase 0: tables, node fields, the state as the first operand
-    for (int e = tid; e < kTcImgBytes / 16; e += blockDim.x) reinterpret_cast<uint4*>(B)[e] = img[e];
-    if (tid < Q) {
-        r1[tid] = rtab[L.r1 + tid];
-        r2[tid] = rtab[L.r2 + tid];
-        r3[tid] = rtab[L.r3 + tid];
-    }
-    for (int e = tid; e < kNumFld2 * kNB; e += blockDim.x) {
-        const int t = e % kNB, f = e / kNB;
-        sc[e] = (t < nb) ? fld[f * N + i0 + t] : (f == F2_N || f == F2_T ? 1.0f : 0.0f);
-    }
-    // first operand: row (ky, node), K = kx; a warp reads four planes kx .. kx+3 of one ky
-    for (int e = tid; e < K2 * kNB; e += blockDim.x) {
-        const int node = e % kNB, j = e / kNB;
-        const int kx = j % Q, ky = j / Q;
-        const float v = (node < nb) ? src[(long long)(kx * Q + ky) * N + i0 + node] : 0.0f;
-        tc::put(A, tc::kLoA, ky * 8 + node, kx, v);
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::saddr(mbar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(tslot)),
-                     "r"(32));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc::fence_async();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tslot, mb = tc::saddr(mbar);
-    const int idx = 4 * warp + (lane >> 3), node = lane & 7;   // this thread's tile row (idx, node)
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    // the next operand's column is this thread's free index: row (i, node) of
-    // it lies at obase + 512 i
-    const uint32_t obase = node * 16 + (idx >> 2) * 128 + (idx & 3) * 4;
-    auto put_row = [&](int i, float x) {
-        const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-        *reinterpret_cast<float*>(A + obase + 512 * i) = h;
-        *reinterpret_cast<float*>(A + tc::kLoA + obase + 512 * i) = x - h;
-    };
-    auto issue = [&](int tb) {
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t bh = tc::saddr(B + tb), bl = bh + 1024, ah = tc::saddr(A), al = ah + tc::kLoA;
-            for (int ks = 0; ks < 2; ++ks) {                 // K = 8 per instruction
-                const uint32_t o = 256u * ks;
-                tc::mma(tmem, tc::desc(ah + o), tc::desc(bh + o), ks);
-                tc::mma(tmem, tc::desc(ah + o), tc::desc(bl + o), 1u);
-                tc::mma(tmem, tc::desc(al + o), tc::desc(bh + o), 1u);
-            }
-            tc::commit(mb);
-        }
-    };
-    bool ok = true;
-    uint32_t parity = 0;
-    auto wait_all = [&]() {
-        const bool done = tc::wait(mb, parity);
-        parity ^= 1u;
-        ok = __syncthreads_and(done ? 1 : 0) && ok;
-        tc::fence_after();
-    };
-    auto hand_over = [&]() {                           // operand writes visible to the next MMAs
-        tc::fence_async();
-        tc::fence_before();
-        __syncthreads();
-    };
-    // ---- T1: analysis along xi_x, D[(ky, node)][l] = Y[l][ky]
-    issue(kTcImgP);
-    coll_moments<float, Q>(rtab, L, sc, r1, r2, r3, mux, Vy);   // overlaps the MMAs
-    wait_all();
-    if (ok) {
-        float y[16];
-        tc::ld16(trow, y);
-#pragma unroll
-        for (int l = 0; l < 16; ++l) put_row(l, y[l]);                 // row (l, node), K = ky
-    }
-    hand_over();
-    // ---- T2: analysis along xi_y, D[(l, node)][m] = Z[l][m]; coefficients C[l][m]
-    if (ok) issue(kTcImgP);
-    wait_all();
-    float z[16];
-    if (ok) tc::ld16(trow, z);
-    float zup[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) zup[m] = __shfl_up_sync(0xffffffffu, ok ? z[m] : 0.0f, 8);   // Z[l-1][m]
-    if (ok && lane >= 24) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) xb[(warp * kNB + node) * XB + m] = z[m];
-    }
-    __syncthreads();
-    if (ok) {
-        const int l = idx;
-        if (lane < 8) {
-#pragma unroll
-            for (int m = 0; m < 16; ++m) zup[m] = (warp > 0) ? xb[((warp - 1) * kNB + node) * XB + m] : 0.0f;
-        }
-        const float mnu = -sc[F2_NU * kNB + node], fx = sc[F2_FX * kNB + node], fy = sc[F2_FY * kNB + node];
-        float mx[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) mx[a] = mux[node * MXS + a * 16 + l];
-        const float fxr = fx * r1[l];
-#pragma unroll
-        for (int m0 = 0; m0 < 16; m0 += 4) {
-            float vv[4][4], rm[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) load4(Vy + ((dd * 4 + a) * kNB + node) * VYS + m0, vv[a]);
-            load4(r1 + m0, rm);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int m = m0 + b;
-                float c = 0.0f;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) c = fmaf(mx[a], vv[a][b], c);
-                if (l >= 1) c = fmaf(fxr, zup[m], c);
-                if (m >= 1) c = fmaf(fy * rm[b], z[m - 1], c);
-                c = fmaf(mnu, z[m], c);
-                put_row(m, c);                                         // row (m, node), K = l
-            }
-        }
-    }
-    hand_over();
-    // ---- T3: synthesis along xi_x, D[(m, node)][kx] = U[kx][m]
-    if (ok) issue(kTcImgS);
-    wait_all();
-    if (ok) {
-        float u[16];
-        tc::ld16(trow, u);
-#pragma unroll
-        for (int kx = 0; kx < 16; ++kx) put_row(kx, u[kx]);            // row (kx, node), K = m
-    }
-    hand_over();
-    // ---- T4: synthesis along xi_y, D[(kx, node)][ky] = the local right-hand side
-    if (ok) issue(kTcImgS);
-    wait_all();
-    float* stg = reinterpret_cast<float*>(A);          // [kx] rows of 136: [ky][node]
-    if (ok) {
-        float v[16];
-        tc::ld16(trow, v);
-#pragma unroll
-        for (int ky = 0; ky < 16; ++ky) stg[idx * 136 + ky * 8 + node] = v[ky];
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (ok) {
-        float* dst = RL + dd * NF;
-        for (int e = tid; e < K2 * kNB; e += blockDim.x) {
-            const int t = e % kNB, j = e / kNB;
-            if (t < nb) dst[(long long)j * N + i0 + t] = stg[(j / 16) * 136 + (j % 16) * 8 + t];
-        }
-    } else {
-        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
-        tc::wait(mb, parity);                           // a last bounded wait for MMAs still in flight
-    }
-    tc::fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
-}
-
-// ---------------------------------------------------------------------------
 // k2_adv: WENO-5 faces along x and y, the right-hand side and the RK combine.
 // ---------------------------------------------------------------------------
 // A 32x16 node tile and a run of velocity planes.  Per plane the halo (tile
@@ -1621,7 +1323,6 @@ struct Ctx2 {
     int* fm_off = nullptr;
     void* fm_w = nullptr;        // Fischer-Methfessel weights, precision R
     float* prf = nullptr;        // FP32 build: node primitives [kNumPrf2][N] of the stage input
-    void* tcimg = nullptr;       // FP32, Q = 16: TF32-split transform tables of k2_coll_tc
     Pow2<float> pwf{};
     Pow2<double> pwd{};
     double* scratch = nullptr;   // [2 Q^2 N + 8] doubles
@@ -1708,12 +1409,7 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
     k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->prf, (const R*)c->ftw, c->fplan, c->fm_off,
                                                    (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
-    if (F32 && Q == 16)   // the FP32 workload shape: tensor-core transforms
-        k2_coll_tc<16><<<2 * nc, 128, coll_tc_smem_bytes(), st>>>(s, (const float*)c->rtab, (const uint4*)c->tcimg,
-                                                                   (const float*)src, (const float*)c->fld,
-                                                                   (float*)c->RL, c->err);
-    else
-        launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
+    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
     dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
     launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
                   alpha, beta, mode);
@@ -1750,7 +1446,6 @@ void destroy_2d(Ctx2* c) {
     cudaFree(c->fm_off);
     cudaFree(c->fm_w);
     cudaFree(c->prf);
-    cudaFree(c->tcimg);
     cudaFree(c->scratch);
     cudaFree(c->err);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -1807,7 +1502,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     alloc((void**)&c->fm_off, sizeof(int) * t.moff.size());
     alloc(&c->fm_w, c->esize * t.mw.size());
     if (f32) alloc((void**)&c->prf, sizeof(float) * kNumPrf2 * s.N);
-    if (f32 && p.Q == 16) alloc(&c->tcimg, kTcImgBytes);
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + 8));
     alloc((void**)&c->err, sizeof(unsigned));
     std::vector<float> tabf(tab.begin(), tab.end()), ftwf(fp.w.begin(), fp.w.end()), mwf(t.mw.begin(), t.mw.end());
@@ -1818,11 +1512,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
         e = cudaMemcpy(c->rtab, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && c->tcimg) {
-        std::vector<unsigned char> img(kTcImgBytes, 0);
-        coll_tc_image(tabf.data(), L, img.data());
-        e = cudaMemcpy(c->tcimg, img.data(), kTcImgBytes, cudaMemcpyHostToDevice);
-    }
     if (e == cudaSuccess) e = cudaMemcpy(c->fplan, fp.plan.data(), sizeof(int) * fp.plan.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = f32 ? cudaMemcpy(c->ftw, ftwf.data(), sizeof(float) * ftwf.size(), cudaMemcpyHostToDevice)
@@ -1839,9 +1528,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
         if (c->prec == EVFDLB_FP32) {
             e = cudaFuncSetAttribute(k2_fields<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
             if (e == cudaSuccess) e = coll_attr<float>(p.Q, c->smem_coll);
-            if (e == cudaSuccess && p.Q == 16)
-                e = cudaFuncSetAttribute(k2_coll_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)coll_tc_smem_bytes());
         } else {
             e = cudaFuncSetAttribute(k2_fields<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
             if (e == cudaSuccess) e = coll_attr<double>(p.Q, c->smem_coll);
@@ -1875,7 +1561,6 @@ evfdlb_status check_2d(Ctx2* c) {
     if (e != cudaSuccess) return st2(e);
     if (h) {
         cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user);
-        if (h & ERR_TIMEOUT) return EVFDLB_E_TIMEOUT;
         return (h & ERR_NONFINITE) ? EVFDLB_E_NONFINITE : EVFDLB_E_NEGATIVE;
     }
     return EVFDLB_OK;

@@ -40,9 +40,8 @@ def make(nx, ny, Q, prec, dx=0.25):
     return sim, orc
 
 
-# (19, 17, 16): the velocity count of the 2D workload, where the FP32 build
-# runs its collision transforms on the tensor cores (3xTF32); 323 nodes leave
-# a ragged last group of 3 nodes
+# (19, 17, 16): the velocity count of the 2D workload; 323 nodes leave a
+# ragged last collision group of 3 nodes
 CASES = [(24, 20, 6), (19, 33, 8), (19, 17, 16)]
 
 
