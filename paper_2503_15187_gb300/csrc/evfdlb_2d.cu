@@ -888,7 +888,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
     __shared__ int rowoff[WY];
     __shared__ int coloff[WX];
     const int nx = s.nx, ny = s.ny;
-    const long long N = s.N, NF = (long long)K * N;
+    const long long N = s.N;
     const int tilesx = (nx + kAdvX - 1) / kAdvX;
     const int x0 = (blockIdx.x % tilesx) * kAdvX, y0 = (blockIdx.x / tilesx) * kAdvY;
     TableLayout L(Q);
@@ -930,31 +930,32 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
         ooff[rr] = oval[rr] ? y * nx + x : 0;
     }
     const int p0 = blockIdx.y * kAdvPlanes, p1 = min(p0 + kAdvPlanes, 2 * K);
-    auto plane_base = [&](int plane) { return (long long)(plane / K) * NF + (long long)(plane % K) * N; };
+    // plane p (distribution p / K, velocity p % K) starts at p N: the plane
+    // pointers advance by N (no 64-bit products in the loop)
+    const long long off0 = (long long)p0 * N;
+    const R* hp = src + off0;
+    const R* rlp = RL + off0;
+    const R* bsp = base + off0;
+    R* op = out + off0;
+    double* rp = rhs_out ? rhs_out + off0 : nullptr;
     // the halo of the next plane is loaded into registers while this plane's
     // faces are formed, and this plane's RL / base values before them
     R hn[NHR];
-    {
-        const R* h = src + plane_base(p0);
 #pragma unroll
-        for (int j = 0; j < NHR; ++j) hn[j] = (threadIdx.x + 256 * j < NH) ? h[hoff[j]] : R(0);
-    }
-    for (int plane = p0; plane < p1; ++plane) {
+    for (int j = 0; j < NHR; ++j) hn[j] = (threadIdx.x + 256 * j < NH) ? hp[hoff[j]] : R(0);
+    for (int plane = p0; plane < p1; ++plane, hp += N, rlp += N, bsp += N, op += N) {
         const int k = plane % K;
         const R vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
-        const long long pbase = plane_base(plane);
         __syncthreads();   // previous plane's faces and halo consumed
 #pragma unroll
         for (int j = 0; j < NHR; ++j)
             if (threadIdx.x + 256 * j < NH) Hs[threadIdx.x + 256 * j] = hn[j];
         if (plane + 1 < p1) {
-            const R* h = src + plane_base(plane + 1);
+            const R* hq = hp + N;
 #pragma unroll
             for (int j = 0; j < NHR; ++j)
-                if (threadIdx.x + 256 * j < NH) hn[j] = h[hoff[j]];
+                if (threadIdx.x + 256 * j < NH) hn[j] = hq[hoff[j]];
         }
-        const R* rlp = RL + pbase;
-        const R* bsp = base + pbase;
         R rl[RPW], bs[RPW];
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
@@ -978,7 +979,6 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             }
         }
         __syncthreads();
-        R* op = out + pbase;
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
             if (!oval[rr]) continue;
@@ -987,7 +987,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
             Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
             if (mode == 1) {
-                rhs_out[pbase + ooff[rr]] = (double)Rv;
+                rp[(plane - p0) * N + ooff[rr]] = (double)Rv;
                 continue;
             }
             const R hv = Hs[(ty + 3) * WX + lane + 3];
