@@ -169,7 +169,9 @@ def run_ours(args, rank, world):
     ms_total = sum(ms_steps)
 
     # end-to-end through the public API with pinned host buffers: per step the
-    # state goes host -> device, one step runs, the moments come back.
+    # state goes host -> device, one step runs, the moments come back (the
+    # step is queued with evfdlb_step_async; evfdlb_moments synchronises and
+    # reports any device error of the step).
     Fh = torch.empty(sim.NF, dtype=torch.float64, pin_memory=True).numpy()
     Gh = torch.empty(sim.NF, dtype=torch.float64, pin_memory=True).numpy()
     sim.get_state(Fh, Gh)
@@ -183,7 +185,7 @@ def run_ours(args, rank, world):
     e0.record(stream)
     for i in range(args.steps):
         ev._check(L.evfdlb_set_state(sim.h, Fh.ctypes.data, Gh.ctypes.data, 0), "set_state")
-        ev._check(L.evfdlb_step(sim.h, 1), "step")
+        ev._check(L.evfdlb_step_async(sim.h, 1), "step_async")
         ev._check(L.evfdlb_moments(sim.h, *[o.ctypes.data for o in outs], tot.ctypes.data, 0), "moments")
     e1.record(stream)
     barrier()
