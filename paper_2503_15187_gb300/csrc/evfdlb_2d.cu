@@ -857,349 +857,6 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 }
 
 // ---------------------------------------------------------------------------
-// k2_coll_tc: k2_coll for an FP32 state with Q = 16 on the tensor cores
-// (tcgen05.mma, kind::tf32), software-pipelined.  A node group (kNB = 8
-// nodes): per distribution its sixteen 16x16 velocity matrices form one
-// M = 128 operand tile; the four one-axis transforms are
-// D[128][16] = A[128][16] Bt[16][16]^T with the analysis table psi_l(xi_j) or
-// the synthesis table w_k psi_l(xi_k) as Bt.  FP32 accuracy from three TF32
-// products (3xTF32): a = a_hi + a_lo with a_hi the 10-bit-mantissa head,
-// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (about 1e-6 relative per
-// transform, far inside the FP32 variant's budget).  Operands are K-major in
-// the canonical no-swizzle layout (8-row x 16-byte core matrices, K-adjacent
-// ones 128 bytes apart, 8-row groups 512 bytes apart); tile rows are ordered
-// (free index, node), so that the state scatter and every epilogue
-// transpose (TMEM row -> next operand column) write 32 distinct banks per
-// warp.  Accumulators live in TMEM; warp w reads lanes 32 (w % 4) .. of
-// distribution w / 4.  One thread issues the MMAs and commits them to an
-// mbarrier (bounded wait; on timeout the CTA records ERR_TIMEOUT, stops and
-// frees its TMEM).
-// Persistent CTAs (two per SM) hold two groups in flight, each in its own
-// slot (operand tiles, node fields, 32 TMEM columns, mbarrier), and
-// alternate between them: while the tensor core runs one slot's transform,
-// the CTA runs the other slot's epilogue (or its store and the next load).
-// The collision coefficients are formed in the epilogue of the second
-// analysis transform with the operations of k2_coll, in the same order.
-// ---------------------------------------------------------------------------
-namespace tc {
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// byte offset of element (r, k) of a K = 16 operand tile
-__device__ __forceinline__ uint32_t koff(int r, int k) {
-    return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
-// shared-memory matrix descriptor: start address, leading byte offset 128
-// (K direction), stride byte offset 512 (8-row groups), descriptor version 1,
-// no swizzle
-__device__ __forceinline__ uint64_t desc(uint32_t a) {
-    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
-           ((uint64_t)1 << 46);
-}
-// instruction descriptor: D F32, A and B TF32, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-// element (r, k) split into its TF32 head (hi tile) and FP32 remainder (lo
-// tile, `lo` bytes after the hi tile)
-__device__ __forceinline__ void put(unsigned char* hi, uint32_t lo, int r, int k, float x) {
-    const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    const uint32_t o = koff(r, k);
-    *reinterpret_cast<float*>(hi + o) = h;
-    *reinterpret_cast<float*>(hi + lo + o) = x - h;
-}
-constexpr uint32_t kLoA = 8192, kLoB = 1024;   // operand tile 128 x 16, table 16 x 16
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
-}
-__device__ __forceinline__ void commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 20) && !done; ++it)
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-    return done != 0;
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-}  // namespace tc
-constexpr int kTcMXS = 4 * 16 + 4, kTcVYS = 16 + 4, kTcXB = 17;
-// byte offsets of the analysis (P) and synthesis (S) tables in the 4 KB
-// image of TF32-split transform tables, each [hi 1 KB | lo 1 KB]
-constexpr int kTcImgP = 0, kTcImgS = 2048, kTcImgBytes = 4096;
-// one slot: operand tiles [d][hi 8 KB | lo 8 KB], then sc, mux, Vy, xb
-constexpr int kTcSlotFloats = kNumFld2 * kNB + kTcMXS * kNB + 8 * kTcVYS * kNB + 8 * kNB * kTcXB;
-constexpr int kTcSlotBytes = ((32768 + 4 * kTcSlotFloats) + 1023) / 1024 * 1024;
-__host__ __device__ constexpr size_t coll_tc_smem_bytes() {
-    return kTcImgBytes + 2 * (size_t)kTcSlotBytes + sizeof(float) * 48 + 2 * 8 + 16;
-}
-// the table image on the host: Bt[n][k] = P[n][k] = psi_n(xi_k) and
-// S[n][k] = w_n psi_k(xi_n), split into TF32 head and FP32 remainder, in the
-// operand layout of the kernel
-inline void coll_tc_image(const float* rtab, const TableLayout& L, unsigned char* img) {
-    auto koff = [](int r, int k) { return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4; };
-    auto put = [&](int base, int r, int k, float x) {
-        uint32_t b;
-        memcpy(&b, &x, 4);
-        b &= 0xFFFFE000u;
-        float h;
-        memcpy(&h, &b, 4);
-        const float l = x - h;
-        memcpy(img + base + koff(r, k), &h, 4);
-        memcpy(img + base + 1024 + koff(r, k), &l, 4);
-    };
-    for (int n = 0; n < 16; ++n)
-        for (int k = 0; k < 16; ++k) {
-            put(kTcImgP, n, k, rtab[L.P + n * 16 + k]);
-            put(kTcImgS, n, k, rtab[L.S + n * 16 + k]);
-        }
-}
-
-template <int Q>
-__global__ void __launch_bounds__(256, 2)
-k2_coll_tc(Slab2 s, const float* __restrict__ rtab, const uint4* __restrict__ img, const float* __restrict__ st,
-           const float* __restrict__ fld, float* __restrict__ RL, unsigned* err) {
-    static_assert(Q == 16 && kNB == 8, "tensor tiles: 8 nodes x 16 rows = M 128, K = N = 16");
-    constexpr int K2 = Q * Q, MXS = kTcMXS, VYS = kTcVYS, XB = kTcXB;
-    extern __shared__ __align__(1024) unsigned char smt[];
-    unsigned char* B = smt;
-    auto Aof = [&](int sl) { return smt + kTcImgBytes + sl * kTcSlotBytes; };
-    auto scof = [&](int sl) { return reinterpret_cast<float*>(Aof(sl) + 32768); };
-    float* r1 = reinterpret_cast<float*>(smt + kTcImgBytes + 2 * kTcSlotBytes);
-    float* r2 = r1 + 16;
-    float* r3 = r2 + 16;
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(r3 + 16);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-    const long long N = s.N, NF = (long long)K2 * N;
-    const long long ngroups = (N + kNB - 1) / kNB;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    TableLayout L(Q);
-    for (int e = tid; e < kTcImgBytes / 16; e += blockDim.x) reinterpret_cast<uint4*>(B)[e] = img[e];
-    if (tid < Q) {
-        r1[tid] = rtab[L.r1 + tid];
-        r2[tid] = rtab[L.r2 + tid];
-        r3[tid] = rtab[L.r3 + tid];
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::saddr(mbar)), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::saddr(mbar + 1)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(tslot)),
-                     "r"(64));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc::fence_async();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tslot;
-    const int dd = warp >> 2, q = warp & 3;                // distribution and lane quarter of this warp
-    const int idx = 4 * q + (lane >> 3), node = lane & 7;  // this thread's tile row (idx, node)
-    // the next operand's column is this thread's free index: row (i, node) of
-    // it lies at obase + 512 i in the distribution's tile
-    const uint32_t obase = node * 16 + (idx >> 2) * 128 + (idx & 3) * 4;
-    auto put_row = [&](unsigned char* Ad, int i, float x) {
-        const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-        *reinterpret_cast<float*>(Ad + obase + 512 * i) = h;
-        *reinterpret_cast<float*>(Ad + tc::kLoA + obase + 512 * i) = x - h;
-    };
-    auto hand_over = [&]() {                               // operand writes visible to the next MMAs
-        tc::fence_async();
-        tc::fence_before();
-        __syncthreads();
-    };
-    // group g into slot sl: node fields, moments, the state as the first operand
-    auto load = [&](int sl, long long g) {
-        unsigned char* A = Aof(sl);
-        float* sc = scof(sl);
-        float* mux = sc + kNumFld2 * kNB;
-        float* Vy = mux + MXS * kNB;
-        const long long i0 = g * kNB;
-        const int nb = (int)min((long long)kNB, N - i0);
-        for (int e = tid; e < kNumFld2 * kNB; e += blockDim.x) {
-            const int t = e % kNB, f = e / kNB;
-            sc[e] = (t < nb) ? fld[f * N + i0 + t] : (f == F2_N || f == F2_T ? 1.0f : 0.0f);
-        }
-        // row (ky, node), K = kx; a warp reads four planes kx .. kx+3 of one ky
-        for (int e = tid; e < 2 * K2 * kNB; e += blockDim.x) {
-            const int nd = e % kNB, j = (e / kNB) % K2, d = e / (kNB * K2);
-            const int kx = j % Q, ky = j / Q;
-            const float v = (nd < nb) ? st[d * NF + (long long)(kx * Q + ky) * N + i0 + nd] : 0.0f;
-            tc::put(A + d * 16384, tc::kLoA, ky * 8 + nd, kx, v);
-        }
-        __syncthreads();                                   // sc complete for the moments
-        coll_moments<float, Q>(rtab, L, sc, r1, r2, r3, mux, Vy);
-    };
-    auto issue = [&](int sl, int tb) {
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t bh = tc::saddr(B + tb), bl = bh + 1024;
-            for (int d = 0; d < 2; ++d) {
-                const uint32_t ah = tc::saddr(Aof(sl) + d * 16384), al = ah + tc::kLoA;
-                const uint32_t dcol = tmem + 32 * sl + 16 * d;
-                for (int ks = 0; ks < 2; ++ks) {                 // K = 8 per instruction
-                    const uint32_t o = 256u * ks;
-                    tc::mma(dcol, tc::desc(ah + o), tc::desc(bh + o), ks);
-                    tc::mma(dcol, tc::desc(ah + o), tc::desc(bl + o), 1u);
-                    tc::mma(dcol, tc::desc(al + o), tc::desc(bh + o), 1u);
-                }
-            }
-            tc::commit(tc::saddr(mbar + sl));
-        }
-    };
-    uint32_t par[2] = {0u, 0u};                            // parity of each slot's next commit
-    bool ok = true;
-    auto wait_slot = [&](int sl) {
-        const bool done = tc::wait(tc::saddr(mbar + sl), par[sl]);
-        ok = __syncthreads_and(done ? 1 : 0) && ok;
-        if (ok) par[sl] ^= 1u;
-        tc::fence_after();
-    };
-    long long grp[2];
-    int ph[2];                                             // transform awaited (1..4), 0: slot idle
-    for (int sl = 0; sl < 2; ++sl) {
-        grp[sl] = blockIdx.x + (long long)sl * gridDim.x;
-        if (grp[sl] < ngroups) load(sl, grp[sl]);
-    }
-    hand_over();
-    for (int sl = 0; sl < 2; ++sl) {
-        ph[sl] = grp[sl] < ngroups ? 1 : 0;
-        if (ph[sl]) issue(sl, kTcImgP);
-    }
-    while (ok && (ph[0] || ph[1])) {
-        for (int sl = 0; sl < 2 && ok; ++sl) {
-            if (!ph[sl]) continue;
-            wait_slot(sl);
-            if (!ok) break;
-            unsigned char* A = Aof(sl);
-            unsigned char* Ad = A + dd * 16384;
-            float* sc = scof(sl);
-            float* mux = sc + kNumFld2 * kNB;
-            float* Vy = mux + MXS * kNB;
-            float* xb = Vy + 8 * VYS * kNB;
-            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + 32 * sl + 16 * dd;
-            if (ph[sl] == 1) {
-                // T1 gave D[(ky, node)][l] = Y[l][ky]: rows (l, node), K = ky
-                float y[16];
-                tc::ld16(trow, y);
-#pragma unroll
-                for (int l = 0; l < 16; ++l) put_row(Ad, l, y[l]);
-                hand_over();
-                issue(sl, kTcImgP);
-                ph[sl] = 2;
-            } else if (ph[sl] == 2) {
-                // T2 gave D[(l, node)][m] = Z[l][m]: coefficients C[l][m], rows (m, node), K = l
-                float z[16];
-                tc::ld16(trow, z);
-                float zup[16];
-#pragma unroll
-                for (int m = 0; m < 16; ++m) zup[m] = __shfl_up_sync(0xffffffffu, z[m], 8);   // Z[l-1][m]
-                if (lane >= 24) {
-#pragma unroll
-                    for (int m = 0; m < 16; ++m) xb[(warp * kNB + node) * XB + m] = z[m];
-                }
-                __syncthreads();
-                const int l = idx;
-                if (lane < 8) {
-#pragma unroll
-                    for (int m = 0; m < 16; ++m) zup[m] = (q > 0) ? xb[((warp - 1) * kNB + node) * XB + m] : 0.0f;
-                }
-                const float mnu = -sc[F2_NU * kNB + node], fx = sc[F2_FX * kNB + node], fy = sc[F2_FY * kNB + node];
-                float mx[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) mx[a] = mux[node * MXS + a * 16 + l];
-                const float fxr = fx * r1[l];
-#pragma unroll
-                for (int m0 = 0; m0 < 16; m0 += 4) {
-                    float vv[4][4], rm[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) load4(Vy + ((dd * 4 + a) * kNB + node) * VYS + m0, vv[a]);
-                    load4(r1 + m0, rm);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int m = m0 + b;
-                        float c = 0.0f;
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) c = fmaf(mx[a], vv[a][b], c);
-                        if (l >= 1) c = fmaf(fxr, zup[m], c);
-                        if (m >= 1) c = fmaf(fy * rm[b], z[m - 1], c);
-                        c = fmaf(mnu, z[m], c);
-                        put_row(Ad, m, c);
-                    }
-                }
-                hand_over();
-                issue(sl, kTcImgS);
-                ph[sl] = 3;
-            } else if (ph[sl] == 3) {
-                // T3 gave D[(m, node)][kx] = U[kx][m]: rows (kx, node), K = m
-                float u[16];
-                tc::ld16(trow, u);
-#pragma unroll
-                for (int kx = 0; kx < 16; ++kx) put_row(Ad, kx, u[kx]);
-                hand_over();
-                issue(sl, kTcImgS);
-                ph[sl] = 4;
-            } else {
-                // T4 gave D[(kx, node)][ky], the local right-hand side: staged, stored coalesced
-                float v[16];
-                tc::ld16(trow, v);
-                float* stg = reinterpret_cast<float*>(A);     // [d][kx] rows of 136: [ky][node]
-#pragma unroll
-                for (int ky = 0; ky < 16; ++ky) stg[dd * 16 * 136 + idx * 136 + ky * 8 + node] = v[ky];
-                tc::fence_before();
-                __syncthreads();
-                const long long i0 = grp[sl] * kNB;
-                const int nb = (int)min((long long)kNB, N - i0);
-                for (int e = tid; e < 2 * K2 * kNB; e += blockDim.x) {
-                    const int t = e % kNB, j = (e / kNB) % K2, d = e / (kNB * K2);
-                    if (t < nb)
-                        RL[d * NF + (long long)j * N + i0 + t] = stg[d * 16 * 136 + (j / 16) * 136 + (j % 16) * 8 + t];
-                }
-                __syncthreads();                               // the slot's tiles are free again
-                grp[sl] += 2LL * gridDim.x;
-                if (grp[sl] < ngroups) {
-                    load(sl, grp[sl]);
-                    hand_over();
-                    issue(sl, kTcImgP);
-                    ph[sl] = 1;
-                } else {
-                    ph[sl] = 0;
-                }
-            }
-        }
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
-        for (int sl = 0; sl < 2; ++sl)                         // last bounded waits for MMAs in flight
-            if (ph[sl]) tc::wait(tc::saddr(mbar + sl), par[sl]);
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
-}
-
-// ---------------------------------------------------------------------------
 // k2_adv: WENO-5 faces along x and y, the right-hand side and the RK combine.
 // ---------------------------------------------------------------------------
 // A 32x16 node tile and a run of velocity planes.  Per plane the halo (tile
@@ -1666,8 +1323,6 @@ struct Ctx2 {
     int* fm_off = nullptr;
     void* fm_w = nullptr;        // Fischer-Methfessel weights, precision R
     float* prf = nullptr;        // FP32 build: node primitives [kNumPrf2][N] of the stage input
-    void* tcimg = nullptr;       // FP32, Q = 16: TF32-split transform tables of k2_coll_tc
-    int nsm = 1;                 // SMs of the device (persistent grid of k2_coll_tc)
     Pow2<float> pwf{};
     Pow2<double> pwd{};
     double* scratch = nullptr;   // [2 Q^2 N + 8] doubles
@@ -1754,12 +1409,7 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
     k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->prf, (const R*)c->ftw, c->fplan, c->fm_off,
                                                    (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
-    if (F32 && Q == 16)   // the FP32 workload shape: tensor-core transforms, two persistent CTAs per SM
-        k2_coll_tc<16><<<std::min(nc, 2 * c->nsm), 256, coll_tc_smem_bytes(), st>>>(
-            s, (const float*)c->rtab, (const uint4*)c->tcimg, (const float*)src, (const float*)c->fld, (float*)c->RL,
-            c->err);
-    else
-        launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
+    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
     dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
     launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
                   alpha, beta, mode);
@@ -1796,7 +1446,6 @@ void destroy_2d(Ctx2* c) {
     cudaFree(c->fm_off);
     cudaFree(c->fm_w);
     cudaFree(c->prf);
-    cudaFree(c->tcimg);
     cudaFree(c->scratch);
     cudaFree(c->err);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -1853,12 +1502,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     alloc((void**)&c->fm_off, sizeof(int) * t.moff.size());
     alloc(&c->fm_w, c->esize * t.mw.size());
     if (f32) alloc((void**)&c->prf, sizeof(float) * kNumPrf2 * s.N);
-    if (f32 && p.Q == 16) alloc(&c->tcimg, kTcImgBytes);
-    if (e == cudaSuccess) {
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + 8));
     alloc((void**)&c->err, sizeof(unsigned));
     std::vector<float> tabf(tab.begin(), tab.end()), ftwf(fp.w.begin(), fp.w.end()), mwf(t.mw.begin(), t.mw.end());
@@ -1869,11 +1512,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
         e = cudaMemcpy(c->rtab, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && c->tcimg) {
-        std::vector<unsigned char> img(kTcImgBytes, 0);
-        coll_tc_image(tabf.data(), L, img.data());
-        e = cudaMemcpy(c->tcimg, img.data(), kTcImgBytes, cudaMemcpyHostToDevice);
-    }
     if (e == cudaSuccess) e = cudaMemcpy(c->fplan, fp.plan.data(), sizeof(int) * fp.plan.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = f32 ? cudaMemcpy(c->ftw, ftwf.data(), sizeof(float) * ftwf.size(), cudaMemcpyHostToDevice)
@@ -1890,9 +1528,6 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
         if (c->prec == EVFDLB_FP32) {
             e = cudaFuncSetAttribute(k2_fields<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
             if (e == cudaSuccess) e = coll_attr<float>(p.Q, c->smem_coll);
-            if (e == cudaSuccess && p.Q == 16)
-                e = cudaFuncSetAttribute(k2_coll_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)coll_tc_smem_bytes());
         } else {
             e = cudaFuncSetAttribute(k2_fields<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_fields);
             if (e == cudaSuccess) e = coll_attr<double>(p.Q, c->smem_coll);
@@ -1926,7 +1561,6 @@ evfdlb_status check_2d(Ctx2* c) {
     if (e != cudaSuccess) return st2(e);
     if (h) {
         cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user);
-        if (h & ERR_TIMEOUT) return EVFDLB_E_TIMEOUT;
         return (h & ERR_NONFINITE) ? EVFDLB_E_NONFINITE : EVFDLB_E_NEGATIVE;
     }
     return EVFDLB_OK;

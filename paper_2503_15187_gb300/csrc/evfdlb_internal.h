@@ -32,7 +32,7 @@ constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
 enum { MOM_S0 = 0, MOM_S1, MOM_S2, MOM_S3, MOM_G0, MOM_G1 };
 
 // Error bits latched by the kernels.
-enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u, ERR_TIMEOUT = 4u };
+enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u };
 
 // Offsets inside the table block of one velocity order Q (doubles).
 struct TableLayout {
