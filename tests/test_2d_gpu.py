@@ -133,3 +133,25 @@ def test_2d_phase_separation_full_size_properties():
     n, u, Tg, q, _ = sim.moments()
     assert np.abs(n - 0.25).max() < 1e-6 and np.abs(u).max() < 1e-6 and np.abs(Tg - T).max() < 1e-6 * T
     sim.close()
+
+
+@pytest.mark.parametrize("prec,bar", [(ev.FP64, 1e-12), (ev.FP32, 1e-5)])
+@pytest.mark.parametrize("dx,rcut", [(0.5, 4.5), (0.5, 6.0)])
+def test_2d_other_disc_shapes(prec, bar, dx, rcut):
+    """The force disc as column plans other than the workload's: dx = 0.5
+    with r_cut = 4.5 (9 offset columns each side) and 6 (12), odd and
+    ragged grids; one step against the oracle in each precision."""
+    nx, ny, Q = 23, 17, 8
+    p = ev.Params(nx=nx, dx=dx, Q=Q, dim=2, ny=ny, precision=prec, r_cut=rcut)
+    sim = ev.Sim(p)
+    orc = O.Oracle2D(O.Setup2(nx=nx, ny=ny, Q=Q, dx=dx, dt=sim.dt(), rcut=rcut))
+    n, ux, uy, T = fields(nx, ny, seed=11)
+    F, G = orc.equilibrium(n, ux, uy, T)
+    F, G = orc.step(F, G, 1)
+    sim.set_state(F.ravel(), G.ravel())
+    sim.step(1)
+    Fg, Gg = sim.state_2d()
+    Fo, Go = orc.step(F, G, 1)
+    eF, eG = rel(Fg, Fo), rel(Gg, Go)
+    print(f"2D dx={dx} r_cut={rcut} prec={prec}: step F {eF:.1e} G {eG:.1e}")
+    assert eF < bar and eG < bar
