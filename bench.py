@@ -352,7 +352,7 @@ def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
     tile = sim.tile_nodes()
     sim.close()
     return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "dtype": "f64 (Hermite transforms as double-float pairs on the FP32 pipe)",
+            "dtype": "f64 (Hermite transforms and WENO-5 faces as double-float pairs on the FP32 pipe)",
             "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(nd - n64).max() / np.abs(n64).max()),
             "gpu_launches": 3 * args.steps, "tile_nodes": tile}

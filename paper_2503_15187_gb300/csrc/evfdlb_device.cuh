@@ -548,6 +548,152 @@ __device__ void faces(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the FP64_DF faces: a value is an unevaluated
+// pair hi + lo of floats (about 48 significant bits).  Addition is Knuth's
+// TwoSum with the low parts folded in and one renormalisation (Dekker's
+// FastTwoSum); multiplication is the FMA TwoProduct with the cross terms;
+// the quotient takes the float reciprocal of the divisor's head and two
+// remainder corrections (each adds ~24 bits).  __fadd_rn / __fmul_rn keep
+// the compiler from contracting the error-free transformations.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl dfl_of(double x) {
+    const float2 p = df_split(x);
+    return {p.x, p.y};
+}
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+    const float s = __fadd_rn(a.h, b.h), bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, {-b.h, -b.l}); }
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+// times a float (exact small integers such as 3)
+__device__ __forceinline__ dfl dfl_mulf(dfl a, float b) {
+    const float p = __fmul_rn(a.h, b);
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
+    const float r = __frcp_rn(b.h);
+    const float q1 = __fmul_rn(a.h, r);
+    const dfl r1 = dfl_sub(a, dfl_mulf(b, q1));
+    const float q2 = __fmul_rn(r1.h, r);
+    const dfl r2 = dfl_sub(r1, dfl_mulf(b, q2));
+    const float q3 = __fmul_rn(r2.h, r);
+    const float s = __fadd_rn(q1, q2), bb = __fsub_rn(s, q1);
+    const float e = __fadd_rn(__fsub_rn(q1, __fsub_rn(s, bb)), __fsub_rn(q2, bb));
+    return dfl_add({s, e}, {q3, 0.0f});
+}
+// float -> double by bit surgery (exponent rebiased, significand shifted:
+// exact for normal floats, zero for zero and subnormals, inf / NaN kept),
+// so that joining a pair costs one FP64 add and no conversion instruction
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned long long e64 = (ex == 0u) ? 0ull : (ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u));
+    const unsigned long long man = (ex == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) | man));
+}
+// the constants of the difference-form WENO-5 face as pairs
+__device__ __forceinline__ dfl dfl_const(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// The difference-form WENO-5 run of Weno5Run in double-float arithmetic.
+struct Weno5RunDF {
+    dfl v2, v3, v4, d0, d1, d2, d3, u0, u1, u2;
+    dfl eps4, k133;
+    __device__ __forceinline__ dfl tterm(dfl t) const { return dfl_add(dfl_mul(dfl_mul(k133, t), t), eps4); }
+    // eps4 = 4 eps as a pair (formed once per thread by the caller)
+    __device__ __forceinline__ void start(double w0, double w1, double w2, double w3, double w4, dfl e4) {
+        eps4 = e4;
+        k133 = dfl_const(13.0 / 3.0);
+        const dfl a0 = dfl_of(w0), a1 = dfl_of(w1);
+        v2 = dfl_of(w2);
+        v3 = dfl_of(w3);
+        v4 = dfl_of(w4);
+        d0 = dfl_sub(a1, a0);
+        d1 = dfl_sub(v2, a1);
+        d2 = dfl_sub(v3, v2);
+        d3 = dfl_sub(v4, v3);
+        u0 = tterm(dfl_sub(d1, d0));
+        u1 = tterm(dfl_sub(d2, d1));
+        u2 = tterm(dfl_sub(d3, d2));
+    }
+    __device__ __forceinline__ double face() const {
+        const dfl s0 = dfl_sub(dfl_mulf(d1, 3.0f), d0), s1 = dfl_add(d1, d2), s2 = dfl_sub(d3, dfl_mulf(d2, 3.0f));
+        const dfl e0 = dfl_add(dfl_mul(s0, s0), u0), e1 = dfl_add(dfl_mul(s1, s1), u1), e2 = dfl_add(dfl_mul(s2, s2), u2);
+        const dfl E0 = dfl_mul(e0, e0), E1 = dfl_mul(e1, e1), E2 = dfl_mul(e2, e2);
+        const dfl a0 = dfl_mul(E1, E2), a1 = dfl_mul(E0, E2), a2 = dfl_mul(E0, E1);
+        const dfl c0 = dfl_sub(dfl_mul(dfl_const(5.0 / 60.0), d1), dfl_mul(dfl_const(2.0 / 60.0), d0));
+        const dfl c1 = dfl_add(dfl_mul(dfl_const(0.2), d2), dfl_mul(dfl_const(0.1), d1));
+        const dfl c2 = dfl_sub(dfl_mul(dfl_const(0.2), d2), dfl_mul(dfl_const(0.05), d3));
+        const dfl num = dfl_add(dfl_add(dfl_mul(a0, c0), dfl_mul(a1, c1)), dfl_mul(a2, c2));
+        const dfl den = dfl_add(dfl_add(dfl_mul(dfl_const(0.1), a0), dfl_mul(dfl_const(0.6), a1)),
+                                dfl_mul(dfl_const(0.3), a2));
+        const dfl f = dfl_add(v2, dfl_div(num, den));
+        return f2d_bits(f.h) + f2d_bits(f.l);
+    }
+    __device__ __forceinline__ void shift(double w5) {
+        const dfl v5 = dfl_of(w5);
+        const dfl d4 = dfl_sub(v5, v4);
+        u0 = u1;
+        u1 = u2;
+        u2 = tterm(dfl_sub(d4, d3));
+        d0 = d1;
+        d1 = d2;
+        d2 = d3;
+        d3 = d4;
+        v2 = v3;
+        v3 = v4;
+        v4 = v5;
+    }
+};
+
+// faces() of the FP64_DF kernel: the same runs and walk, the face values in
+// double-float arithmetic on the FP32 pipe, stored as FP64.
+__device__ inline void faces_df(const SlabDesc& sd, const WorkItem& it, const Smem<double>& s, int Z,
+                                const double* __restrict__ tab, int tid, int nth) {
+    const int Q = sd.Q, W = Z + 6, nf = it.nz + 1, rows = 2 * Q;
+    const int nruns = (nf + kRun - 1) / kRun;
+    TableLayout L(Q);
+    const double* xi = tab + sd.tab_off + L.xi;
+    const dfl eps4 = dfl_const(4.0 * sd.weno_eps);
+    for (int e = tid; e < rows * nruns; e += nth) {
+        const int r = e % rows, run = e / rows;
+        const int k = r % Q;
+        const int fa = run * kRun, n = min(kRun, nf - fa), fl = fa + n - 1;
+        const bool pos = xi[k] >= 0.0;
+        const int dir = pos ? 1 : -1, f0 = pos ? fa : fl;
+        const double* hb = s.F + (size_t)r * W + (pos ? fa : fl + 5);
+        double* out = s.Face + (size_t)r * (Z + 1);
+        Weno5RunDF w;
+        w.start(hb[0], hb[dir], hb[2 * dir], hb[3 * dir], hb[4 * dir], eps4);
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            if (q >= n) break;
+            out[f0 + dir * q] = w.face();
+            if (q + 1 < n) w.shift(hb[dir * (q + 5)]);
+        }
+    }
+}
+
 // One raw moment sum of one node from a column h[k * stride] (k < Q).  The
 // conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
 // (heat flux) in R.  The velocity powers come from xp = [xi, xi^2, xi^3]

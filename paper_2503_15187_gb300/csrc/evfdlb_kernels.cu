@@ -97,7 +97,8 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         } else {
             analysis<R>(sd, it, s, Z, tid, nth);
         }
-        faces<R>(sd, it, s, Z, vtab, tid, nth);
+        if constexpr (DF) faces_df(sd, it, s, Z, tables, tid, nth);
+        else faces<R>(sd, it, s, Z, vtab, tid, nth);
     }
     __syncthreads();
     coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
