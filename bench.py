@@ -285,8 +285,8 @@ def fp32_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64)
     n32 = sim.moments(with_totals=False)[0]
     tile = sim.tile_nodes()
     sim.close()
-    return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32 (f64 chi, "
-            "transport, gradients, conserved sums)", "ms_per_step": ms / args.steps,
+    return {"value": NZ * Q * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32 (f64 FM average and chi, "
+            "gradient differences, heat flux, conserved sums)", "ms_per_step": ms / args.steps,
             "max_rel_diff_n_vs_fp64": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
             "gpu_launches": 3 * args.steps, "tile_nodes": tile}
 

@@ -134,6 +134,18 @@ __device__ __forceinline__ float2 df_split(double x) {
     return make_float2(h, l);
 }
 __device__ __forceinline__ double df_join(float s, float e) { return (double)s + (double)e; }
+// double -> float by bit surgery (the head of df_split: the significand cut
+// to 24 bits, within one float ulp), no conversion instruction
+__device__ __forceinline__ float d2f_bits(double x) { return df_split(x).x; }
+// float -> double by bit surgery (exponent rebiased, significand shifted:
+// exact for normal floats, zero for zero and subnormals, inf / NaN kept)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned long long e64 = (ex == 0u) ? 0ull : (ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u));
+    const unsigned long long man = (ex == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) | man));
+}
 
 // (s, e) += a * b for pairs a, b.
 __device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b) {
@@ -255,21 +267,50 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         double dT = (s.T[c - 2] - 8.0 * s.T[c - 1] + 8.0 * s.T[c + 1] - s.T[c + 2]) * inv12;
         double dU = (s.U[c - 2] - 8.0 * s.U[c - 1] + 8.0 * s.U[c + 1] - s.U[c + 2]) * inv12;
         double X = s.X[c], chi = s.Chi[c];
-        double A = dX / X, B = dT / T;
+        double A, B;
         // self-consistent force, Eq. (F1), Simpson taps over |j| <= M
         const R* nn = s.Nr + (t + M);
         R f1r = 0;
         for (int j = -M; j <= M; ++j) f1r = fma(ftap[j + M], nn[j], f1r);
-        double f1 = (double)f1r;
+        double f1;
+        if constexpr (std::is_same<R, float>::value) f1 = f2d_bits(f1r);
+        else f1 = (double)f1r;
         // heat flux from the raw sums: q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
         double q = 0.5 * (S3[i] - 3.0 * u * S2[i] + 3.0 * u * u * S1[i] - u * u * u * S0[i]) + G1[i] - u * G0[i];
         // transport, Eqs. (viscosity), (tau), (prandtl)
-        double bn = sd.b * n, x = bn * chi;
-        double mu = sd.mu0_coef * sqrt(T) * (1.0 / chi + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
-        double tau = mu / (n * T * (1.0 + 0.4 * x));
-        double Pr = (2.0 / 3.0) * (1.0 + 0.6 * x) * (1.0 + 0.8 * x + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * x * x) /
-                    ((1.0 + 0.4 * x) * (1.0 + 1.2 * x + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * x * x));
-        double nu = (sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 / tau : chi / tau;
+        double bn, x, mu, tau, Pr, nu;
+        if constexpr (std::is_same<R, float>::value) {
+            // the FP32 variant: gradient ratios and transport on the FP32 pipe
+            // (chi, the gradients' differences and the heat flux stay FP64);
+            // values cross by bit surgery, not conversion instructions
+            const float fn = d2f_bits(n), fT = d2f_bits(T), fchi = d2f_bits(chi);
+            const float fA = d2f_bits(dX) / d2f_bits(X), fB = d2f_bits(dT) / fT;
+            const float fbn = d2f_bits(sd.b) * fn, fx = fbn * fchi;
+            const float c16 = (float)((4.0 / 25.0) * (1.0 + 12.0 / M_PI)), c9 = (float)((9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)));
+            const float fmu = d2f_bits(sd.mu0_coef) * sqrtf(fT) * (1.0f / fchi + 0.8f * fbn + c16 * fbn * fbn * fchi);
+            const float ftau = fmu / (fn * fT * (1.0f + 0.4f * fx));
+            const float fPr = (2.0f / 3.0f) * (1.0f + 0.6f * fx) * (1.0f + 0.8f * fx + c16 * fx * fx) /
+                              ((1.0f + 0.4f * fx) * (1.0f + 1.2f * fx + c9 * fx * fx));
+            const float fnu = (sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0f / ftau : fchi / ftau;
+            A = f2d_bits(fA);
+            B = f2d_bits(fB);
+            bn = f2d_bits(fbn);
+            x = f2d_bits(fx);
+            mu = f2d_bits(fmu);
+            tau = f2d_bits(ftau);
+            Pr = f2d_bits(fPr);
+            nu = f2d_bits(fnu);
+        } else {
+            A = dX / X;
+            B = dT / T;
+            bn = sd.b * n;
+            x = bn * chi;
+            mu = sd.mu0_coef * sqrt(T) * (1.0 / chi + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
+            tau = mu / (n * T * (1.0 + 0.4 * x));
+            Pr = (2.0 / 3.0) * (1.0 + 0.6 * x) * (1.0 + 0.8 * x + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * x * x) /
+                 ((1.0 + 0.4 * x) * (1.0 + 1.2 * x + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * x * x));
+            nu = (sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 / tau : chi / tau;
+        }
         double* sc = s.Sc;
         sc[SC_N * Z + t] = n;
         sc[SC_U * Z + t] = u;
@@ -281,7 +322,8 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         sc[SC_A * Z + t] = A;
         sc[SC_B * Z + t] = B;
         sc[SC_D * Z + t] = dU;
-        s.Scr[t] = (R)nu;
+        if constexpr (std::is_same<R, float>::value) s.Scr[t] = d2f_bits(nu);
+        else s.Scr[t] = (R)nu;
         s.Scr[Z + t] = f1r;
         if (!(n > 0.0) || !(T > 0.0)) {
             atomicOr(err, (finite(n) && finite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
@@ -337,15 +379,36 @@ __device__ void node_coefficients(const SlabDesc& sd, const WorkItem& it, const 
         double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
         R* cF = s.Cc + t;
         R* cG = s.Cc + 4 * Z + t;
-        cF[0] = (R)(nu * n);
-        cF[Z] = (R)(K * A * T);
-        cF[2 * Z] = (R)(0.6 * K * D * T);
-        cF[3 * Z] = (R)(0.2 * nu * kq + 0.3 * K * B * T * T);
-        cG[0] = (R)(nu * n * T + 0.4 * K * T * D);
-        cG[Z] = (R)(0.4 * nu * kq + K * T * T * (A + 0.6 * B));
-        cG[2 * Z] = (R)(0.6 * K * T * T * D);
-        cG[3 * Z] = (R)(0.2 * nu * kq * T + 0.3 * K * T * T * T * B);
-        const R ru = (R)u, Tm1 = (R)(T - 1.0);
+        if constexpr (std::is_same<R, float>::value) {
+            // the FP32 variant forms the constants on the FP32 pipe
+            const float fn = d2f_bits(n), fT = d2f_bits(T), fnu = d2f_bits(nu), fkq = d2f_bits(kq);
+            const float fK = d2f_bits(K), fA = d2f_bits(A), fB = d2f_bits(B), fD = d2f_bits(D);
+            cF[0] = fnu * fn;
+            cF[Z] = fK * fA * fT;
+            cF[2 * Z] = 0.6f * fK * fD * fT;
+            cF[3 * Z] = 0.2f * fnu * fkq + 0.3f * fK * fB * fT * fT;
+            cG[0] = fnu * fn * fT + 0.4f * fK * fT * fD;
+            cG[Z] = 0.4f * fnu * fkq + fK * fT * fT * (fA + 0.6f * fB);
+            cG[2 * Z] = 0.6f * fK * fT * fT * fD;
+            cG[3 * Z] = 0.2f * fnu * fkq * fT + 0.3f * fK * fT * fT * fT * fB;
+        } else {
+            cF[0] = (R)(nu * n);
+            cF[Z] = (R)(K * A * T);
+            cF[2 * Z] = (R)(0.6 * K * D * T);
+            cF[3 * Z] = (R)(0.2 * nu * kq + 0.3 * K * B * T * T);
+            cG[0] = (R)(nu * n * T + 0.4 * K * T * D);
+            cG[Z] = (R)(0.4 * nu * kq + K * T * T * (A + 0.6 * B));
+            cG[2 * Z] = (R)(0.6 * K * T * T * D);
+            cG[3 * Z] = (R)(0.2 * nu * kq * T + 0.3 * K * T * T * T * B);
+        }
+        R ru, Tm1;
+        if constexpr (std::is_same<R, float>::value) {
+            ru = d2f_bits(u);
+            Tm1 = d2f_bits(T - 1.0);
+        } else {
+            ru = (R)u;
+            Tm1 = (R)(T - 1.0);
+        }
         R m0 = 1, m1 = 0;
         for (int l = 0; l < Q; ++l) {
             s.Mm[l * Z + t] = m0;
@@ -598,16 +661,6 @@ __device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
     const float s = __fadd_rn(q1, q2), bb = __fsub_rn(s, q1);
     const float e = __fadd_rn(__fsub_rn(q1, __fsub_rn(s, bb)), __fsub_rn(q2, bb));
     return dfl_add({s, e}, {q3, 0.0f});
-}
-// float -> double by bit surgery (exponent rebiased, significand shifted:
-// exact for normal floats, zero for zero and subnormals, inf / NaN kept),
-// so that joining a pair costs one FP64 add and no conversion instruction
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned ex = (b >> 23) & 0xffu;
-    const unsigned long long e64 = (ex == 0u) ? 0ull : (ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u));
-    const unsigned long long man = (ex == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
-    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) | man));
 }
 // the constants of the difference-form WENO-5 face as pairs
 __device__ __forceinline__ dfl dfl_const(double x) {

@@ -2,15 +2,18 @@
 
 The FP32 variant stores F, G and does the per-velocity work (WENO faces,
 Hermite analysis and synthesis, force convolution, coefficient recurrences,
-RK combine) in FP32, and keeps FP64 for chi, the transport coefficients, the
-gradients and the per-node sums of the conserved moments.  Its error against
+RK combine) and the transport coefficients and coefficient constants in
+FP32, and keeps FP64 for the Fischer-Methfessel average and chi, the
+gradients' differences, the heat flux and the per-node sums of the
+conserved moments.  Its error against
 the FP64 oracle is therefore set by FP32 rounding, u = 2^-24 = 6.0e-8 per
 operation.  The bars below are derived from that: a right-hand side sums
 O(Q) = 32 terms of the size of the state (Hermite synthesis), so its error is
 bounded by about Q u |F| = 2e-6 of the state; one RK step adds three such
 right-hand sides times dt plus the rounding of the stored state, so 1e-5
-normwise per step (measured values are printed by -s); node fields formed in
-FP64 from FP32 sums are good to ~1e-6.  Over a run the error grows at most
+normwise per step (measured values are printed by -s); node fields formed
+from FP32 sums (and, for the transport, in FP32 arithmetic over a few
+operations) are good to ~1e-6.  Over a run the error grows at most
 linearly in the number of steps on these non-chaotic cases.
 Error measure: ||GPU - oracle||_inf / ||oracle||_inf per distribution.
 """
