@@ -55,7 +55,7 @@ namespace evfdlb {
 // pairs on the FP32 pipe (state tile split into pairs once per stage in a
 // block after the Hermite moments), everything else as in the FP64 kernel.
 template <typename R, bool DF = false>
-__global__ void __launch_bounds__(StageThreads<R>::value, 1)
+__global__ void __launch_bounds__(StageThreads<R>::value, DF ? 3 : 1)
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
