@@ -146,6 +146,20 @@ __device__ __forceinline__ double f2d_bits(float f) {
     const unsigned long long man = (ex == 0u) ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
     return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) | man));
 }
+// a / b in FP64 by Newton-Raphson reciprocal refinement with a final
+// residual correction (Markstein, IBM J. Res. Dev. 34, 1990): a float
+// reciprocal of b (b cut to a float by bit surgery, reciprocal to 2^-23),
+// one Newton step r <- r + r (1 - b r) (2^-46), q = a r and q <- q + r (a - b q)
+// (within about one ulp; not correctly rounded).  Divisors outside the
+// float exponent range take the IEEE quotient.
+__device__ __forceinline__ double div_nr(double a, double b) {
+    const int ex = (int)((__double_as_longlong(b) >> 52) & 0x7ff);
+    if (ex < 1023 - 120 || ex > 1023 + 120) return a / b;
+    double r = f2d_bits(__frcp_rn(d2f_bits(b)));
+    r = fma(r, fma(-b, r, 1.0), r);
+    const double q = a * r;
+    return fma(fma(-b, q, a), r, q);
+}
 
 // (s, e) += a * b for pairs a, b.
 __device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b) {
@@ -555,9 +569,11 @@ struct Weno5Run {
         const R den = fma(R(0.1), a0, fma(R(0.6), a1, R(0.3) * a2));
         R q;
         // FP32: the fast reciprocal-based quotient (2 ulp) is far inside the
-        // FP32 variant's error budget; FP64 keeps the IEEE quotient
+        // FP32 variant's error budget; FP64: the Newton-corrected quotient of
+        // div_nr (about one ulp), cheaper on this part's FP64 pipe than the
+        // IEEE division
         if constexpr (std::is_same<R, float>::value) q = __fdividef(num, den);
-        else q = num / den;
+        else q = div_nr(num, den);
         return v2 + q;
     }
     __device__ __forceinline__ void shift(R w5) {
