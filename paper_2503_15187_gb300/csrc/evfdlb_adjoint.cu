@@ -106,7 +106,7 @@ __device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, doub
     const double c2 = fma(0.2, d2, -0.05 * d3);
     const double num = fma(a0, c0, fma(a1, c1, a2 * c2));
     const double den = fma(0.1, a0, fma(0.6, a1, 0.3 * a2));
-    const double iden = 1.0 / den;
+    const double iden = div_nr(1.0, den);
     const double R = pb * iden;
     const double psi = num * iden;             // Phi - v2
     // adjoints (all times pb)

@@ -197,7 +197,7 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
     for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
         int i = gidx(it.i0 - 2 + t, nx, bc);
-        double n = S0[i], inv_n = 1.0 / n;
+        double n = S0[i], inv_n = div_nr(1.0, n);
         double u = S1[i] * inv_n;
         // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2
         s.U[t] = u;
@@ -246,7 +246,7 @@ __device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const 
         double nb = 0.0;
         for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], nn[j], nb);
         double eta = sd.eta_coef * nb, om = 1.0 - eta;
-        double chi = (2.0 - eta) / (2.0 * om * om * om);
+        double chi = div_nr(2.0 - eta, 2.0 * om * om * om);
         double n = nn[0];
         s.Chi[t] = chi;
         s.X[t] = n * n * chi * s.T[t];
@@ -315,15 +315,16 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
             Pr = f2d_bits(fPr);
             nu = f2d_bits(fnu);
         } else {
-            A = dX / X;
-            B = dT / T;
+            A = div_nr(dX, X);
+            B = div_nr(dT, T);
             bn = sd.b * n;
             x = bn * chi;
-            mu = sd.mu0_coef * sqrt(T) * (1.0 / chi + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
-            tau = mu / (n * T * (1.0 + 0.4 * x));
-            Pr = (2.0 / 3.0) * (1.0 + 0.6 * x) * (1.0 + 0.8 * x + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * x * x) /
-                 ((1.0 + 0.4 * x) * (1.0 + 1.2 * x + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * x * x));
-            nu = (sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 / tau : chi / tau;
+            mu = sd.mu0_coef * sqrt(T) *
+                 (div_nr(1.0, chi) + 0.8 * bn + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * bn * bn * chi);
+            tau = div_nr(mu, n * T * (1.0 + 0.4 * x));
+            Pr = div_nr((2.0 / 3.0) * (1.0 + 0.6 * x) * (1.0 + 0.8 * x + (4.0 / 25.0) * (1.0 + 12.0 / M_PI) * x * x),
+                        (1.0 + 0.4 * x) * (1.0 + 1.2 * x + (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI)) * x * x));
+            nu = div_nr((sd.relax == EVFDLB_RELAX_INV_TAU) ? 1.0 : chi, tau);
         }
         double* sc = s.Sc;
         sc[SC_N * Z + t] = n;
