@@ -21,6 +21,10 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const void* rtaps, const void* src, const void* base, void* out, double* rhs_out,
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err);
+void launch_stage_beside(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                         const double* tables, const double* taps, const double* src, const double* base,
+                         double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
+                         double alpha, double beta, int Z, unsigned* err);
 void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                    const WorkItem* items, const double* tables, const void* rtab, const double* n0,
                    const double* u0, const double* T0, void* state, double* mom, long long NF, long long NN, int Z,
@@ -819,7 +823,8 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     // the sweep of segment sg + 1 has finished with it.  Every kernel computes
     // the same values as in a serial order: the overlap changes no result.
     auto segp = [&](int64_t sg) { return c->seg[sg & 1]; };
-    auto recompute = [&](int64_t sg) -> cudaError_t {
+    // `beside`: the recompute overlaps a reverse sweep on the user stream
+    auto recompute = [&](int64_t sg, bool beside) -> cudaError_t {
         double* base = segp(sg);
         auto sst = [&](size_t j) { return base + j * 2 * NF; };
         auto smo = [&](size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
@@ -827,17 +832,20 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
         cudaError_t e = cudaMemcpyAsync(sst(0), c->ckpts[sg], sizeof(double) * 2 * NF, cudaMemcpyDeviceToDevice, c->aux);
         if (e != cudaSuccess) return e;
         launch_sums_p(EVFDLB_FP64, n, c->aux, c->slabs, c->items, c->tables, c->tables, sst(0), smo(0), NF, NN, c->err);
+        auto stage = [&](const double* src, const double* sbase, double* out, const double* mi, double* mo,
+                         double alpha, double beta) {
+            if (beside)
+                launch_stage_beside(n, c->smem, c->aux, c->slabs, c->items, c->tables, c->taps, src, sbase, out, mi,
+                                    mo, NF, NN, alpha, beta, c->Z, c->err);
+            else
+                launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
+                               c->taps, src, sbase, out, nullptr, mi, mo, NF, NN, alpha, beta, 0, c->Z, c->err);
+        };
         for (int t = 0; t < ns; ++t) {
             size_t b = 3 * (size_t)t;
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sst(b), nullptr, sst(b + 1), nullptr, smo(b), smo(b + 1), NF, NN, 0.0,
-                           1.0, 0, c->Z, c->err);
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sst(b + 1), sst(b), sst(b + 2), nullptr, smo(b + 1), smo(b + 2), NF,
-                           NN, 0.75, 0.25, 0, c->Z, c->err);
-            launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
-                           c->taps, sst(b + 2), sst(b), sst(b + 3), nullptr, smo(b + 2), smo(b + 3), NF,
-                           NN, 1.0 / 3.0, 2.0 / 3.0, 0, c->Z, c->err);
+            stage(sst(b), nullptr, sst(b + 1), smo(b), smo(b + 1), 0.0, 1.0);
+            stage(sst(b + 1), sst(b), sst(b + 2), smo(b + 1), smo(b + 2), 0.75, 0.25);
+            stage(sst(b + 2), sst(b), sst(b + 3), smo(b + 2), smo(b + 3), 1.0 / 3.0, 2.0 / 3.0);
         }
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_rec[sg & 1], c->aux);
@@ -845,11 +853,11 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     };
     TRY_CUDA(cudaEventRecord(c->ev_fork, c->user));      // the checkpoints and lam are ready
     TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-    TRY_CUDA(recompute(nseg - 1));
+    TRY_CUDA(recompute(nseg - 1, false));
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
         if (sg >= 1) {
             if (sg + 1 <= nseg - 1) TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_sweep[(sg + 1) & 1], 0));
-            TRY_CUDA(recompute(sg - 1));
+            TRY_CUDA(recompute(sg - 1, true));
         }
         TRY_CUDA(cudaStreamWaitEvent(c->user, c->ev_rec[sg & 1], 0));
         double* base = segp(sg);

@@ -21,9 +21,14 @@ constexpr int kZMax = 64;          // largest node tile of one CTA
 constexpr int kThreads = 256;      // threads of the per-tile kernels
 // Threads of the RK-stage kernel (warp 0 forms the node work): the FP32
 // variant's per-velocity work is cheap and latency-bound, so it runs 16
-// warps per tile; the FP64 forms are FP64-pipe-bound and run 8.
-template <typename R> struct StageThreads { static constexpr int value = 256; };
-template <> struct StageThreads<float> { static constexpr int value = 512; };
+// warps per tile; the FP64 kernel is FP64-pipe-bound and runs 12 when its
+// grid is one wave (one CTA per SM), else kStageThreadsWaves = 8, so that two
+// CTAs of ~110 registers share an SM; the FP64_DF kernel runs 8 so that
+// three CTAs per SM keep 80 registers.
+template <typename R, bool DF = false> struct StageThreads { static constexpr int value = 384; };
+template <> struct StageThreads<double, true> { static constexpr int value = 256; };
+template <> struct StageThreads<float, false> { static constexpr int value = 512; };
+constexpr int kStageThreadsWaves = 256;
 constexpr int kNumMoments = 6;     // raw moment sums kept per node
 constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
 

@@ -54,8 +54,8 @@ namespace evfdlb {
 // the FP64 `tables`; the Hermite analysis and synthesis run as Dot2 sums of
 // pairs on the FP32 pipe (state tile split into pairs once per stage in a
 // block after the Hermite moments), everything else as in the FP64 kernel.
-template <typename R, bool DF = false>
-__global__ void __launch_bounds__(StageThreads<R>::value, DF ? 3 : 1)
+template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
+__global__ void __launch_bounds__(T, DF ? 3 : 1)
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
@@ -441,7 +441,7 @@ void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* s
                      const double* tables, const double* dftab, const double* taps, const double* src,
                      const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
                      long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<double, true><<<nitems, StageThreads<double>::value, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
+    stage_kernel<double, true><<<nitems, StageThreads<double, true>::value, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
                                                                out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
                                                                mode, Z, err);
 }
@@ -450,6 +450,11 @@ template <typename R>
 static cudaError_t configure_t(size_t smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<R, double>::value) {
+        e = cudaFuncSetAttribute(stage_kernel<double, false, kStageThreadsWaves>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(init_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(iso_reset_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -466,7 +471,8 @@ cudaError_t configure_kernels(size_t smem_bytes) { return configure_t<double>(sm
 // Raises (never lowers) the dynamic shared-memory limit of the FP64 stage and
 // isothermal-reset kernels on the current device to at least smem_bytes.
 cudaError_t ensure_stage_smem(size_t smem_bytes) {
-    const void* fns[2] = {(const void*)stage_kernel<double>, (const void*)iso_reset_kernel<double>};
+    const void* fns[3] = {(const void*)stage_kernel<double>, (const void*)stage_kernel<double, false, kStageThreadsWaves>,
+                          (const void*)iso_reset_kernel<double>};
     for (const void* f : fns) {
         cudaFuncAttributes a;
         cudaError_t e = cudaFuncGetAttributes(&a, f);
@@ -476,6 +482,37 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Multiprocessors of the current device (cached per device).
+static int device_sms() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
+}
+
+// The FP64 stage at 12 warps when the work list is one wave, at 8 warps
+// (two CTAs per SM) when it is several or when `beside` says that other
+// kernels share the SMs.
+static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
+                              const WorkItem* items, const double* tables, const double* rtab, const double* taps,
+                              const double* rtaps, const double* src, const double* base, double* out,
+                              double* rhs_out, const double* mom_in, double* mom_out, long long NF, long long NN,
+                              double alpha, double beta, int mode, int Z, unsigned* err, bool beside = false) {
+    if (!beside && nitems <= device_sms())
+        stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
+            slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
+            mode, Z, err);
+    else
+        stage_kernel<double, false, kStageThreadsWaves><<<nitems, kStageThreadsWaves, smem, st>>>(
+            slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
+            mode, Z, err);
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
@@ -488,9 +525,20 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
             slabs, items, tables, (const float*)rtab, taps, (const float*)rtaps, (const float*)src,
             (const float*)base, (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
     else
-        stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
-            slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps, (const double*)src,
-            (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+        launch_stage_fp64(nitems, smem, st, slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps,
+                          (const double*)src, (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN,
+                          alpha, beta, mode, Z, err);
+}
+
+// FP64 stage running concurrently with kernels on another stream (the
+// adjoint's segment recompute beside the reverse sweep): the 8-warp form,
+// which leaves a third more of each SM's registers to the other kernels.
+void launch_stage_beside(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+                         const double* tables, const double* taps, const double* src, const double* base,
+                         double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
+                         double alpha, double beta, int Z, unsigned* err) {
+    launch_stage_fp64(nitems, smem, st, slabs, items, tables, tables, taps, taps, src, base, out, nullptr, mom_in,
+                      mom_out, NF, NN, alpha, beta, 0, Z, err, true);
 }
 
 // FP64 stage (mode 0 writes out; mode 1 writes the right-hand side to out).
@@ -498,8 +546,8 @@ void launch_stage(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slab
                   const double* tables, const double* taps, const double* src, const double* base,
                   double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
                   double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(slabs, items, tables, tables, taps, taps, src, base, out,
-                                                         out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+    launch_stage_fp64(nitems, smem, st, slabs, items, tables, tables, taps, taps, src, base, out, out, mom_in, mom_out,
+                      NF, NN, alpha, beta, mode, Z, err);
 }
 
 void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
