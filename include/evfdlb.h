@@ -173,8 +173,12 @@ evfdlb_status evfdlb_moments(evfdlb_ctx* ctx, double* n, double* u, double* T,
                              double* q, double* totals, int32_t on_device);
 
 /* Copies the state (F, G; [sum Q nx] each, layout above) out of / into the
- * context.  set_state also clears a latched device error.  For dim = 2 the
- * state is [Q * Q][ny][nx] per distribution, velocity index kx * Q + ky. */
+ * context.  set_state also clears a latched device error; it returns once
+ * host arrays have been read (device arrays: once the copies are queued), and
+ * a state that the kernels reject (a non-finite moment sum) is reported by
+ * the next call that synchronises (for dim = 2, set_state itself, which
+ * synchronises).  For dim = 2 the state is
+ * [Q * Q][ny][nx] per distribution, velocity index kx * Q + ky. */
 evfdlb_status evfdlb_get_state(evfdlb_ctx* ctx, double* F, double* G, int32_t on_device);
 evfdlb_status evfdlb_set_state(evfdlb_ctx* ctx, const double* F, const double* G,
                                int32_t on_device);

@@ -50,7 +50,7 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
                     double* q);
 void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                    const WorkItem* items, const double* taps, const double* mom, long long NN, double* part,
-                   double* out);
+                   double* out, double* n, double* u, double* T, double* q);
 size_t adj_smem_bytes(int Q, int Z, int M);
 size_t adj_moments_smem_bytes(int Z, int m, int M);
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
@@ -109,6 +109,8 @@ struct evfdlb_ctx {
     SlabDesc* slabs = nullptr;
     WorkItem* items = nullptr;
     unsigned* err = nullptr;
+    unsigned* err_h = nullptr;   // pinned host copy of the error word
+    cudaEvent_t ev_in = nullptr; // end of set_state's host-to-device copies
     cudaGraphExec_t g_chunk = nullptr;
     cudaGraphExec_t g_one = nullptr;
     int chunk = 16;
@@ -176,6 +178,8 @@ void free_ctx(evfdlb_ctx* c) {
     cudaFree(c->slabs);
     cudaFree(c->items);
     cudaFree(c->err);
+    if (c->err_h) cudaFreeHost(c->err_h);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
@@ -229,9 +233,11 @@ evfdlb_status capture(evfdlb_ctx* c, int steps, cudaGraphExec_t* out) {
 
 // Reads and clears the device error word (synchronises the user stream).
 evfdlb_status check_device(evfdlb_ctx* c) {
-    unsigned h = 0;
-    TRY_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->user));
+    unsigned hs = 0;
+    unsigned* hp = c->err_h ? c->err_h : &hs;
+    TRY_CUDA(cudaMemcpyAsync(hp, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->user));
     TRY_CUDA(cudaStreamSynchronize(c->user));
+    const unsigned h = *hp;
     if (h) {
         c->poisoned = true;
         TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
@@ -493,6 +499,8 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
     alloc((void**)&c->slabs, sizeof(SlabDesc) * nbatch);
     alloc((void**)&c->items, sizeof(WorkItem) * c->items_cap);
     alloc((void**)&c->err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->err_h, sizeof(unsigned), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (c->ckpt_every > 0) alloc((void**)&c->init_fields, sizeof(double) * 3 * NN);
     if (e == cudaSuccess) e = cudaMemcpy(c->tables, tables.data(), sizeof(double) * tables.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice);
@@ -656,6 +664,7 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
     evfdlb_status s;
     if ((s = copy_in(c, dst, F, bytes, on_device)) != EVFDLB_OK) return s;
     if ((s = copy_in(c, dst + c->NF, G, bytes, on_device)) != EVFDLB_OK) return s;
+    if (!on_device) TRY_CUDA(cudaEventRecord(c->ev_in, c->user));
     if (c->prec == EVFDLB_FP32) {   // round to the state precision
         launch_convert_to_f32(c->user, c->scratch, (float*)c->state[0], 2 * c->NF);
         TRY_CUDA(cudaGetLastError());
@@ -667,9 +676,12 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
     c->steps = 0;
     c->origin_init = false;
     c->poisoned = false;
-    s = check_device(c);
-    c->have_state = (s == EVFDLB_OK);
-    return s;
+    c->have_state = true;
+    // Host arrays are released once their copies have run; the moment sums
+    // stay queued, and a state they reject is reported by the next call that
+    // synchronises.
+    if (!on_device) TRY_CUDA(cudaEventSynchronize(c->ev_in));
+    return EVFDLB_OK;
 }
 
 evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_device) {
@@ -714,7 +726,14 @@ evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, dou
     double* outs[4] = {n, u, T, q};
     double* dptr[4];
     for (int i = 0; i < 4; ++i) dptr[i] = outs[i] ? (on_device ? outs[i] : buf + i * c->NN) : nullptr;
-    launch_moments(c->user, c->mom[0], c->NN, dptr[0], dptr[1], dptr[2], dptr[3]);
+    double* dt = buf + EVFDLB_NFIELDS * c->NN;
+    if (totals) {   // the totals' first pass writes n, u, T, q as well
+        double* part = dt + 4 * c->nbatch;   // 4 per work item (<= 4 NN <= 2 NF)
+        launch_totals(c->nbatch, (int)c->items_h.size(), sizeof(double) * (c->Z + 2 * c->Mmax), c->user, c->slabs,
+                      c->items, c->taps, c->mom[0], c->NN, part, dt, dptr[0], dptr[1], dptr[2], dptr[3]);
+    } else {
+        launch_moments(c->user, c->mom[0], c->NN, dptr[0], dptr[1], dptr[2], dptr[3]);
+    }
     TRY_CUDA(cudaGetLastError());
     if (!on_device)
         for (int i = 0; i < 4; ++i)
@@ -723,11 +742,6 @@ evfdlb_status evfdlb_moments(evfdlb_ctx* c, double* n, double* u, double* T, dou
                 if (s != EVFDLB_OK) return s;
             }
     if (totals) {
-        double* dt = buf + EVFDLB_NFIELDS * c->NN;
-        double* part = dt + 4 * c->nbatch;   // 4 per work item (<= 4 NN <= 2 NF)
-        launch_totals(c->nbatch, (int)c->items_h.size(), sizeof(double) * (c->Z + 2 * c->Mmax), c->user, c->slabs,
-                      c->items, c->taps, c->mom[0], c->NN, part, dt);
-        TRY_CUDA(cudaGetLastError());
         evfdlb_status s = copy_out(c, totals, dt, sizeof(double) * 4 * c->nbatch, 0);
         if (s != EVFDLB_OK) return s;
     }

@@ -277,7 +277,9 @@ iso_reset_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
 }
 
 // Raw moment sums of an arbitrary state (after set_state); same precision rule
-// as the stage kernel.
+// and summation order as the stage kernel's tile_moment_sums.  The tile's
+// 2 Q rows are staged in shared memory with coalesced loads first, so that
+// the per-node sums do not wait on Q serial global loads.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 sums_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
@@ -285,17 +287,24 @@ sums_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ ite
             double* mom, long long NF, long long NN, unsigned* err) {
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
-    const int Q = sd.Q;
+    const int Q = sd.Q, nz = it.nz;
     TableLayout L(Q);
     __shared__ double xp[3 * kQMax];
     __shared__ R xr[2 * kQMax];
+    __shared__ R tile[2 * kQMax * kZMax];   // [d][k][t], row length nz
     velocity_powers<R>(Q, tables + sd.tab_off + L.xi, rtab + sd.tab_off + L.xi, xp, xr, threadIdx.x, blockDim.x);
+    const int rows = 2 * Q;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < rows * nz; e += blockDim.x) {
+        const int r = e / nz, t = e - r * nz;              // r = d Q + k
+        const int d = r >= Q ? 1 : 0, k = r - d * Q;
+        tile[e] = state[d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t];
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < kNumMoments * it.nz; e += blockDim.x) {
-        int t = e % it.nz, which = e / it.nz;
+    for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
+        int t = e % nz, which = e / nz;
         int d = which >= MOM_G0 ? 1 : 0;
-        const R* h = state + d * NF + sd.f_off + it.i0 + t;
-        double acc = moment_sum<R>(which, Q, h, sd.nx, xp, xr);
+        double acc = moment_sum<R>(which, Q, tile + (size_t)d * Q * nz + t, nz, xp, xr);
         if (!finite(acc)) atomicOr(err, ERR_NONFINITE);
         mom[which * NN + sd.node_off + it.i0 + t] = acc;
     }
@@ -316,28 +325,34 @@ fields_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ i
     node_fields<R>(sd, it, s, Z, taps, rtaps, mom, NN, err, fields);
 }
 
+// n, u, T, q of node i from its raw sums (null outputs are skipped).
+__device__ __forceinline__ void node_moments(const double* __restrict__ mom, long long NN, long long i, double* n,
+                                             double* u, double* T, double* q) {
+    double S0 = mom[MOM_S0 * NN + i], S1 = mom[MOM_S1 * NN + i], S2 = mom[MOM_S2 * NN + i];
+    double S3 = mom[MOM_S3 * NN + i], G0 = mom[MOM_G0 * NN + i], G1 = mom[MOM_G1 * NN + i];
+    double uu = S1 / S0;
+    if (n) n[i] = S0;
+    if (u) u[i] = uu;
+    if (T) T[i] = (2.0 / 3.0) * ((0.5 * S2 + G0) / S0 - 0.5 * uu * uu);
+    if (q) q[i] = 0.5 * (S3 - 3.0 * uu * S2 + 3.0 * uu * uu * S1 - uu * uu * uu * S0) + G1 - uu * G0;
+}
+
 // n, u, T, q per node from the raw sums.
 __global__ void moments_kernel(const double* __restrict__ mom, long long NN, double* n, double* u,
                                double* T, double* q) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < NN;
-         i += (long long)gridDim.x * blockDim.x) {
-        double S0 = mom[MOM_S0 * NN + i], S1 = mom[MOM_S1 * NN + i], S2 = mom[MOM_S2 * NN + i];
-        double S3 = mom[MOM_S3 * NN + i], G0 = mom[MOM_G0 * NN + i], G1 = mom[MOM_G1 * NN + i];
-        double uu = S1 / S0;
-        if (n) n[i] = S0;
-        if (u) u[i] = uu;
-        if (T) T[i] = (2.0 / 3.0) * ((0.5 * S2 + G0) / S0 - 0.5 * uu * uu);
-        if (q) q[i] = 0.5 * (S3 - 3.0 * uu * S2 + 3.0 * uu * uu * S1 - uu * uu * uu * S0) + G1 - uu * G0;
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        node_moments(mom, NN, i, n, u, T, q);
 }
 
 // Conserved totals, first pass: per work item (node tile) the sums of S0,
 // S1, S2/2 + G0 and of the mean-field energy density (1/2) n_i sum_j e_j
-// n_{i+j} (energy taps over a staged density halo), fixed-order tree.
+// n_{i+j} (energy taps over a staged density halo), fixed-order tree; the
+// tile's n, u, T, q as well where those outputs are given (non-null).
 __global__ void __launch_bounds__(kThreads)
 totals_part_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
                    const double* __restrict__ taps, const double* __restrict__ mom, long long NN,
-                   double* __restrict__ part) {
+                   double* __restrict__ part, double* n, double* u, double* T, double* q) {
     extern __shared__ double sn[];          // S0 on [i0 - M, i0 + nz + M)
     __shared__ double red[4][kThreads];
     const WorkItem it = items[blockIdx.x];
@@ -363,6 +378,7 @@ totals_part_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (t < nz && sub == 0) {
             const int i = it.i0 + t;
+            node_moments(mom, NN, sd.node_off + i, n, u, T, q);
             a0 += S0[i];
             a1 += S1[i];
             a2 += 0.5 * S2[i] + G0[i];
@@ -622,10 +638,12 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
 
 // Conserved totals: per-tile partial sums (part: 4 per work item), then per
 // slab in work-list order.  smem: (Z + 2 Mmax) doubles.
+// Conserved totals per slab into out [4 nslabs]; n, u, T, q per node on the
+// way (each may be null).
 void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                    const WorkItem* items, const double* taps, const double* mom, long long NN, double* part,
-                   double* out) {
-    totals_part_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, taps, mom, NN, part);
+                   double* out, double* n, double* u, double* T, double* q) {
+    totals_part_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, taps, mom, NN, part, n, u, T, q);
     totals_kernel<<<nslabs, kThreads, 0, st>>>(slabs, items, nitems, part, out);
 }
 

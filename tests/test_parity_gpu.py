@@ -136,6 +136,64 @@ def test_twenty_steps_and_totals(name):
     assert abs(tot[0, 3] - to[3]) < 1e-11 * abs(to[3])
 
 
+def test_moments_with_and_without_totals_agree():
+    """The node moments come from the totals' first pass when totals are asked
+    for and from a kernel of their own otherwise: the same values, and the
+    oracle's."""
+    sim, orc, n0, u0, T0 = make("outflow_q24_slab")
+    F, G = nonequilibrium_state(orc, n0, u0, T0)
+    sim.set_state(F.ravel(), G.ravel())
+    a = sim.moments()
+    b = sim.moments(with_totals=False)
+    for x, y in zip(a[:4], b[:4]):
+        assert rel(x, y) < 1e-15
+    no, uo, To, qo = orc.moments(F, G)
+    assert rel(b[0], no) < 1e-13 and rel(b[2], To) < 1e-12 and rel(b[3], qo) < 1e-9
+
+
+def test_bad_state_is_reported_by_the_next_synchronising_call():
+    """set_state returns once its copies have run; a state whose moment sums
+    are not finite is reported by the next call that synchronises, after which
+    the context refuses to step until a new state is set."""
+    sim, orc, n0, u0, T0 = make("periodic_q16")
+    F, G = nonequilibrium_state(orc, n0, u0, T0)
+    bad = F.copy()
+    bad[3, 5] = np.nan
+    sim.set_state(bad.ravel(), G.ravel())
+    with pytest.raises(ev.EvfdlbError) as e:
+        sim.step(1)
+    assert e.value.code == -4
+    with pytest.raises(ev.EvfdlbError) as e:
+        sim.step(1)
+    assert e.value.code == -7
+    sim.set_state(F.ravel(), G.ravel())            # recovers
+    sim.step(1)
+    Fg, Gg = sim.state_2d()
+    Fo, Go = orc.step(F, G, 1)
+    assert rel(Fg, Fo) < 1e-12 and rel(Gg, Go) < 1e-12
+
+
+def test_set_state_from_page_locked_memory_releases_the_arrays():
+    """From page-locked host arrays the copies are asynchronous; set_state
+    returns only once they have run, so the caller may overwrite its arrays at
+    once."""
+    import torch
+    sim, orc, n0, u0, T0 = make("outflow_q32_dz01")
+    F, G = nonequilibrium_state(orc, n0, u0, T0)
+    Fp = torch.empty(F.size, dtype=torch.float64, pin_memory=True).numpy()
+    Gp = torch.empty(G.size, dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(3):
+        Fp[:] = F.ravel()
+        Gp[:] = G.ravel()
+        sim.set_state(Fp, Gp)
+        Fp[:] = -1.0
+        Gp[:] = np.nan
+        sim.step(1)
+        Fg, Gg = sim.state_2d()
+    Fo, Go = orc.step(F, G, 1)
+    assert rel(Fg, Fo) < 1e-12 and rel(Gg, Go) < 1e-12
+
+
 def test_mass_momentum_conserved_on_gpu():
     sim, orc, n0, u0, T0 = make("periodic_q16")
     sim.init(n0, u0, T0)
