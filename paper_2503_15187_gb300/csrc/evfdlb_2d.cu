@@ -868,15 +868,17 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* 
 // 128-255 the y faces (32 columns x runs 5+4+4+4 of the 17 faces of a
 // column); for a negative velocity the stencil is mirrored and the run walked
 // down.  Then the right-hand side and the Shu-Osher combine
-//   out = alpha base + beta (h + dt R)   (mode 0),   rhs_out = R (mode 1).
-// Q is a compile-time parameter: the plane index splits by constants.
+//   out = alpha base + beta (h + dt R)   (RHS false),   rhs_out = R (RHS true).
+// Q is a compile-time parameter: the plane index splits by constants.  So is
+// the output form: with a run-time switch the FP32 kernel issued the FP64
+// store's conversion (predicated off) for every output of the combine.
 template <typename R>
 constexpr int adv_min_blocks() { return std::is_same<R, float>::value ? 4 : 2; }
 
-template <typename R, int Q>
+template <typename R, int Q, bool RHS>
 __global__ void __launch_bounds__(256, adv_min_blocks<R>())
 k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* base, R* out,
-       const R* __restrict__ RL, double* rhs_out, double alpha, double beta, int mode) {
+       const R* __restrict__ RL, double* rhs_out, double alpha, double beta) {
     constexpr int WX = kAdvX + 6, WY = kAdvY + 6, NH = WX * WY;
     constexpr int NHR = (NH + 255) / 256;                   // halo loads per thread
     constexpr int RPW = kAdvY / 8;                          // output rows per warp
@@ -960,7 +962,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
             rl[rr] = oval[rr] ? rlp[ooff[rr]] : R(0);
-            bs[rr] = (oval[rr] && with_base && mode == 0) ? bsp[ooff[rr]] : R(0);
+            bs[rr] = (oval[rr] && with_base && !RHS) ? bsp[ooff[rr]] : R(0);
         }
         __syncthreads();
         {
@@ -986,7 +988,7 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
             R Rv = rl[rr];
             Rv = fma(-vx * idx, FX[ty * (kAdvX + 1) + lane + 1] - FX[ty * (kAdvX + 1) + lane], Rv);
             Rv = fma(-vy * idx, FY[(ty + 1) * kAdvX + lane] - FY[ty * kAdvX + lane], Rv);
-            if (mode == 1) {
+            if constexpr (RHS) {
                 rp[(plane - p0) * N + ooff[rr]] = (double)Rv;
                 continue;
             }
@@ -1347,19 +1349,27 @@ void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, co
     }
 }
 
-// k2_adv is compiled for each even Q of the 2D model (4 .. 16)
+// k2_adv is compiled for each even Q of the 2D model (4 .. 16) and both
+// output forms
+template <typename R, bool RHS>
+void launch_adv_t(int Q, dim3 g, cudaStream_t st, const Slab2& s, const R* rtab, const R* src, const R* base,
+                  R* out, const R* RL, double* rhs_out, double alpha, double beta) {
+    switch (Q) {
+        case 4: k2_adv<R, 4, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        case 6: k2_adv<R, 6, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        case 8: k2_adv<R, 8, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        case 10: k2_adv<R, 10, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        case 12: k2_adv<R, 12, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        case 14: k2_adv<R, 14, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+        default: k2_adv<R, 16, RHS><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta); break;
+    }
+}
+
 template <typename R>
 void launch_adv(int Q, dim3 g, cudaStream_t st, const Slab2& s, const R* rtab, const R* src, const R* base, R* out,
                 const R* RL, double* rhs_out, double alpha, double beta, int mode) {
-    switch (Q) {
-        case 4: k2_adv<R, 4><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        case 6: k2_adv<R, 6><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        case 8: k2_adv<R, 8><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        case 10: k2_adv<R, 10><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        case 12: k2_adv<R, 12><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        case 14: k2_adv<R, 14><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-        default: k2_adv<R, 16><<<g, 256, 0, st>>>(s, rtab, src, base, out, RL, rhs_out, alpha, beta, mode); break;
-    }
+    if (mode == 1) launch_adv_t<R, true>(Q, g, st, s, rtab, src, base, out, RL, rhs_out, alpha, beta);
+    else launch_adv_t<R, false>(Q, g, st, s, rtab, src, base, out, RL, rhs_out, alpha, beta);
 }
 
 // k2_moments: 128 nodes per CTA pass (grid-stride beyond 8192 CTAs)

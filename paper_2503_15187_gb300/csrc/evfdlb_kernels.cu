@@ -108,6 +108,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     // velocities of a thread share every coefficient loaded.
     const R* xi = rt + L.xi;
     const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
+    const bool rhs_form = (mode == 1), with_base = (alpha != 0.0);
     // velocities per thread: two in FP64/FP32, four in DF (four independent
     // Dot2 chains hide the FP32 latency)
     constexpr int VK = DF ? 4 : 2;
@@ -140,23 +141,34 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
                 for (int q = 0; q < VK; ++q) syn[q] = fma(s.S[min(k0 + q, Q - 1) * Q + l], cl, syn[q]);
             }
         }
-#pragma unroll
-        for (int q = 0; q < VK; ++q) {
-            if (q >= nk) break;
-            const int k = k0 + q;
-            const R sq = syn[q];
+        // R at velocity k of this node (h: the state there)
+        auto rhs_at = [&](int q, int k, R h) {
             const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
-            R h = s.F[(size_t)(d * Q + k) * W + t + 3];
-            R Rv = fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, sq));
-            long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
-            if (mode == 1) {
-                rhs_out[g] = (double)Rv;
-                continue;
+            return fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn[q]));
+        };
+        // the two output forms in separate loops under one uniform branch, so
+        // that the RK form issues no FP64 conversion of the right-hand-side form
+        if (rhs_form) {
+#pragma unroll
+            for (int q = 0; q < VK; ++q) {
+                if (q >= nk) break;
+                const int k = k0 + q;
+                const R h = s.F[(size_t)(d * Q + k) * W + t + 3];
+                rhs_out[d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t] = (double)rhs_at(q, k, h);
             }
-            R o = rbeta * fma(dt, Rv, h);
-            if (alpha != 0.0) o = fma(ralpha, base[g], o);
-            out[g] = o;
-            s.F[(size_t)(d * Q + k) * W + t + 3] = o;
+        } else {
+#pragma unroll
+            for (int q = 0; q < VK; ++q) {
+                if (q >= nk) break;
+                const int k = k0 + q;
+                R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
+                const R h = *hp;
+                const long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
+                R o = rbeta * fma(dt, rhs_at(q, k, h), h);
+                if (with_base) o = fma(ralpha, base[g], o);
+                out[g] = o;
+                *hp = o;
+            }
         }
     }
     if (mode == 1) return;
