@@ -38,6 +38,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "evfdlb_device.cuh"
@@ -512,16 +513,21 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
     return cudaSuccess;
 }
 
-// Multiprocessors of the current device (cached per device).
+// Multiprocessors of the current device (cached per device; contexts on
+// different host threads may launch concurrently).
 static int device_sms() {
-    static int cache[64] = {};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    const bool cached = dev >= 0 && dev < 64;
+    if (cached) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
-    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    if (cached) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 
