@@ -106,3 +106,41 @@ def test_ev2_invalid_params_rejected(L):
         kw = dict(nx=64, dx=0.25, force_model=ev.EV2)
         kw.update(bad)
         assert math.isnan(ev.critical_T(ev.Params(**kw))), bad
+
+
+def _create(L, plist, nbatch=None, with_out=True):
+    """evfdlb_create on a batch of Params; (status, handle or None)."""
+    arr = (ev.CParams * len(plist))(*[p.c() for p in plist]) if plist else None
+    h = ctypes.c_void_p(0x1234)                    # create must clear it on failure
+    rc = L.evfdlb_create(None, len(plist) if nbatch is None else nbatch, arr, None,
+                         ctypes.byref(h) if with_out else None)
+    return rc, h.value
+
+
+def test_create_rejects_invalid_arguments_before_any_device_call(L):
+    """Argument validation of evfdlb_create runs on the host before its first
+    CUDA call: empty or tiny grids, Q outside the supported orders, unknown
+    enums, an empty batch, mixed precisions in one batch and a missing output
+    pointer return E_INVALID_ARG and leave no handle; 2D requests this model
+    does not cover return E_UNSUPPORTED."""
+    INVALID, UNSUPPORTED = -1, -8
+    base = dict(nx=64, dx=0.25)
+    for bad in (dict(nx=0), dict(nx=7), dict(Q=3), dict(Q=33), dict(dx=0.0), dict(bc=5),
+                dict(precision=9), dict(relax_mode=4), dict(force_model=3), dict(weno_eps=0.0),
+                dict(dt=0.0, cfl=0.0), dict(T_iso=-1.0), dict(dim=1, ny=2)):
+        kw = dict(base)
+        kw.update(bad)
+        rc, h = _create(L, [ev.Params(**kw)])
+        assert rc == INVALID and h is None, bad
+    assert _create(L, [ev.Params(**base)], nbatch=0) == (INVALID, None)
+    mixed = [ev.Params(**base), ev.Params(precision=ev.FP32, **base)]
+    assert _create(L, mixed) == (INVALID, None)
+    assert _create(L, [ev.Params(**base)], with_out=False)[0] == INVALID
+    # 2D: more nodes than 32-bit node offsets address, odd Q, outflow ends
+    for bad in (dict(nx=50000, ny=50000), dict(Q=7), dict(bc=ev.BC_OUTFLOW)):
+        kw = dict(dim=2, nx=64, ny=64, dx=0.25, Q=8)
+        kw.update(bad)
+        assert _create(L, [ev.Params(**kw)]) == (INVALID, None), bad
+    two_d = dict(dim=2, nx=64, ny=64, dx=0.25, Q=8)
+    assert _create(L, [ev.Params(**two_d)] * 2)[0] == UNSUPPORTED
+    assert _create(L, [ev.Params(force_model=ev.EV2, **two_d)]) == (UNSUPPORTED, None)
