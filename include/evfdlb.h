@@ -110,7 +110,11 @@ typedef struct {
     int32_t relax_mode;   /* EVFDLB_RELAX_INV_TAU or EVFDLB_RELAX_CHI_OVER_TAU         */
     double  dt;           /* > 0: time step; <= 0: dt = cfl * dx / max|xi_k|           */
     double  cfl;          /* used when dt <= 0; 0 < cfl <= 1                           */
-    int32_t ckpt_every;   /* checkpoint interval of the adjoint (reserved; 0 = none)   */
+    int32_t ckpt_every;   /* > 0: the context keeps the state every ckpt_every steps   */
+                          /* (the checkpoints of evfdlb_adjoint / adjoint_state, which */
+                          /* recompute each segment from them); 0: no checkpoints, and */
+                          /* the trajectory adjoint returns E_STATE.  One value per    */
+                          /* context (that of slab 0)                                   */
     double  weno_eps;     /* WENO-5 smoothness regulariser (> 0), e.g. 1e-6            */
     double  T_iso;        /* 0: thermal (default).  > 0: isothermal mode -- after every */
                           /* step each node's temperature is set back to T_iso, its    */
@@ -211,6 +215,50 @@ int32_t evfdlb_launches_per_step(const evfdlb_ctx* ctx);
  * Synchronises the stream.  Errors: E_INVALID_ARG, E_CUDA. */
 evfdlb_status evfdlb_tune(evfdlb_ctx* ctx, int32_t tile_nodes);
 int32_t evfdlb_tile_nodes(const evfdlb_ctx* ctx);
+
+/* ---- Discrete adjoint (FP64, periodic, thermal, one-dimensional contexts) ----
+ * The reverse mode of the FP64 step above: exact discrete vector-Jacobian
+ * products of the right-hand side L of Eqs. (ev1), (enskog_approx) and of the
+ * Shu-Osher stages (Sec. III), for the gradient of a loss of the final state.
+ * phi_a enters through the Eq. (F1) force, which is linear in it (the kernel
+ * g of Eq. (F1) integrates the Sutherland tail of Eq. (sutherland)), and
+ * through nothing else; the initial fields enter through the projected
+ * Maxwellian pair of evfdlb_init.  The trajectory is the one since the last
+ * evfdlb_init or evfdlb_set_state: it is rebuilt segment by segment from the
+ * checkpoints kept every ckpt_every steps (checkpoint-and-recompute; the
+ * recompute of one segment runs on a second stream of the context beside the
+ * reverse sweep of the next, with identical results).  Work buffers are
+ * allocated on the first adjoint call.  Per-slab outputs (dL_dphi_a, dphi)
+ * are always host memory ([nbatch]); the others follow on_device.
+ * Errors: E_INVALID_ARG (NULL context or cotangent), E_STATE (no state; for
+ * the trajectory calls also a context without checkpoints, ckpt_every = 0,
+ * a poisoned context, or field gradients asked of a trajectory that began
+ * at set_state), E_UNSUPPORTED (dim = 2, FP32, FP64_DF, outflow ends,
+ * isothermal mode, phi_a = 0), E_OOM, E_CUDA, and the latched device errors.
+ *
+ * evfdlb_rhs_vjp: at the current state u, (outF, outG) = J(u)^T (WF, WG) with
+ *   J = dL/du (one right-hand side), and dphi[s] = sum W . dL/dphi_a of slab s
+ *   (may be NULL).  WF, WG, outF, outG: [sum Q nx] each, the state layout. */
+evfdlb_status evfdlb_rhs_vjp(evfdlb_ctx* ctx, const double* WF, const double* WG, int32_t on_device,
+                             double* outF, double* outG, double* dphi);
+
+/* evfdlb_adjoint_state: given the cotangent (barF, barG) = dL/d(F, G) of the
+ * current state, sweeps the trajectory back to its origin and returns (each
+ * output may be NULL) dL/dphi_a per slab, dL/dF0 and dL/dG0 of the origin
+ * state ([sum Q nx] each) and, for a trajectory that began at evfdlb_init,
+ * the gradients with respect to the initial fields dL/dn0, dL/du0, dL/dT0
+ * ([sum nx] each, per node: a uniform T0 has dL/dT = sum_i dL/dT0_i). */
+evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* ctx, const double* barF, const double* barG, int32_t on_device,
+                                   double* dL_dphi_a, double* dL_dF0, double* dL_dG0, double* dL_dn0,
+                                   double* dL_du0, double* dL_dT0);
+
+/* evfdlb_adjoint: the density-profile form of the above for a loss L(n_end)
+ * of the final density n = sum_k F_k (Sec. II.B): given dL/dn_end ([sum nx]),
+ * dL/dF_k = dL/dn for every k and dL/dG = 0; returns dL/dphi_a per slab
+ * (host, [nbatch]) and dL/dT0, dL/dn0 per node ([sum nx], on_device; any
+ * output may be NULL).  The trajectory must begin at evfdlb_init. */
+evfdlb_status evfdlb_adjoint(evfdlb_ctx* ctx, const double* dL_dn_end, int32_t on_device, double* dL_dphi_a,
+                             double* dL_dT0, double* dL_dn0);
 
 /* Time step without any device allocation.  The paper has no counterpart.
  * It serves callers that cannot call cudaMalloc: a plugin whose host

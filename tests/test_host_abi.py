@@ -29,11 +29,38 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(evfdlb_[A-Za-z0-9_]+)\s*\(", src)))
 
 
+def exported_functions():
+    """Names of the evfdlb_* functions the built library exports (the
+    dynamic symbol table as `nm -D --defined-only` lists it)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm is not available")
+    out = subprocess.run([nm, "-D", "--defined-only", ev.LIB_PATH], capture_output=True, text=True, check=True)
+    names = set()
+    for line in out.stdout.splitlines():
+        parts = line.split()
+        if len(parts) == 3 and parts[1] == "T" and parts[2].startswith("evfdlb_"):
+            names.add(parts[2])
+    return sorted(names)
+
+
 def test_exports_every_declared_symbol(L):
     names = declared_functions()
     assert len(names) >= 18
     for n in names:
         assert hasattr(L, n), n
+
+
+def test_declares_every_exported_symbol(L):
+    """The header and the library agree in both directions: every evfdlb_*
+    function the library exports is declared in include/evfdlb.h."""
+    declared = set(declared_functions())
+    exported = exported_functions()
+    assert len(exported) >= 18
+    missing = [n for n in exported if n not in declared]
+    assert not missing, f"exported but not declared in include/evfdlb.h: {missing}"
 
 
 def test_status_strings(L):
