@@ -386,6 +386,63 @@ def test_transport_dilute_limit_and_prandtl_identity():
             assert abs(f["mu"][0] - mu0) < 1e-6 and abs(f["Pr"][0] - 2 / 3) < 1e-6
 
 
+def _uniform_transport(o, n0, T0):
+    nz = o.s.nz
+    F, G = o.equilibrium(np.full(nz, n0), np.zeros(nz), np.full(nz, T0))
+    return o.node_fields(F, G)
+
+
+def test_tau_through_the_conductivity_equality_of_eq_tau():
+    """tau of the oracle (formed from mu, the first equality of Eq. (tau)) is
+    checked against the second equality of Eq. (tau), which ties tau to the
+    thermal conductivity lambda (the companion of Eq. (viscosity), not formed
+    by the oracle) and to the Prandtl number of Eq. (prandtl):
+        lambda = (5/2) (tau P_i / Pr) (1 + 3/5 b rho chi),  P_i = n T,
+    read with the printed tau inside the bracket as the kinetic conductivity
+    factor (the printed form, tau on both sides, is not dimensionally a
+    solution for tau).  chi is re-derived here from the Carnahan-Starling
+    identity n b chi = P_hs/(n T) - 1 of Eqs. (carnstar) and (EOSS), so the
+    check runs on a chi the oracle did not supply.  mu itself is not
+    retyped: a slip in the oracle's mu (any of its three terms) or in its tau
+    moves tau against lambda Pr."""
+    o = mk(nz=16, Q=8, bc=0)
+    b = 2 * math.pi / 3
+    for n0, T0 in [(0.02, 0.9), (0.1, 0.8), (0.3, 0.7), (0.55, 0.6), (0.8, 0.55)]:
+        f = _uniform_transport(o, n0, T0)
+        eta = math.pi * n0 / 6
+        p_hs = n0 * T0 * (1 + eta + eta ** 2 - eta ** 3) / (1 - eta) ** 3
+        chi = (p_hs / (n0 * T0) - 1) / (b * n0)
+        assert abs(f["chi"][0] - chi) < 1e-13 * chi
+        x = b * n0 * chi
+        lam0 = 75 / 64 * math.sqrt(T0 / math.pi)
+        lam = lam0 * (1 / chi + 1.2 * b * n0 + 9 / 25 * (1 + 32 / (9 * math.pi)) * (b * n0) ** 2 * chi)
+        tau_from_lambda = lam * f["Pr"][0] / (2.5 * n0 * T0 * (1 + 0.6 * x))
+        assert abs(f["tau"][0] - tau_from_lambda) < 1e-13 * tau_from_lambda, (n0, T0)
+
+
+def test_viscosity_density_expansion_of_the_enskog_theory():
+    """Low-density expansion of Eq. (viscosity) composed with chi of
+    Eq. (carnstar): with eta = b n / 4 the Carnahan-Starling chi is
+    1 + (5/8) b n + (9/32) (b n)^2 + O((b n)^3), so
+        mu / mu0 = 1 + (4/5 - 5/8) b n + (c2 + 7/64) (b n)^2 + O((b n)^3),
+    the first coefficient 7/40 being Enskog's first-order density correction
+    of the dilute viscosity (it involves the 4/5 and 1/chi terms only), and
+    c2 = (4/25)(1 + 12/pi) the dense-gas coefficient.  The oracle's mu/mu0 at
+    small densities is fitted with a cubic in b n and its coefficients
+    compared: a dropped term, a wrong coefficient or a chi evaluated at the
+    wrong density changes one of them."""
+    o = mk(nz=16, Q=8, bc=0)
+    b = 2 * math.pi / 3
+    T0 = 0.8
+    mu0 = 5 / 16 * math.sqrt(T0 / math.pi)
+    y = np.linspace(1e-4, 4e-3, 12)                # b n
+    r = np.array([_uniform_transport(o, yi / b, T0)["mu"][0] / mu0 for yi in y])
+    c = np.polynomial.polynomial.polyfit(y, r, 4)
+    assert abs(c[0] - 1) < 1e-11
+    assert abs(c[1] - 7 / 40) < 1e-9
+    assert abs(c[2] - (4 / 25 * (1 + 12 / math.pi) + 7 / 64)) < 1e-6
+
+
 def test_critical_temperature_matches_paper():
     """With a = 4 pi/3 (Eq. (F2), gamma = 6) the CS + mean-field EOS gives the
     paper's printed T_c ~ 0.754632 (Sec. III.A) to its printed digits."""
