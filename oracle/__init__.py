@@ -51,15 +51,36 @@ PI = np.pi
 
 def build(force: bool = False) -> str:
     """Compile the C oracle into oracle/_build/liborc.so (gcc, -O2, IEEE FP):
-    the FP64 routines and their complex-step twins from the same source."""
+    the FP64 routines and their complex-step twins from the same source, with
+    OpenMP over the independent node loops where the compiler offers it (the
+    thread count changes no result; ``set_threads``)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_CS, _SRC_2D))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_CS, _SRC_2D, os.path.abspath(__file__)))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_CS, _SRC_2D, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", "-o", tmp, _SRC, _SRC_CS, _SRC_2D, "-lm"],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:      # no OpenMP runtime: serial build
+            subprocess.check_call(base + ["-o", tmp, _SRC, _SRC_CS, _SRC_2D, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int | None = None) -> int:
+    """Threads of the oracle's node loops (n > 0 sets them; None only reads);
+    returns the count in effect (1 for a build without OpenMP).  The default is
+    one thread, or ORACLE_THREADS from the environment."""
+    return int(_load().orc_set_threads(0 if n is None else int(n)))
+
+
+def available_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:                          # pragma: no cover
+        return os.cpu_count() or 1
 
 
 _lib = None
@@ -108,6 +129,9 @@ def _load():
         _lib.orc2_rhs.argtypes = [P2, vp, vp, vp, vp, vp]
         _lib.orc2_step.argtypes = [P2, vp, vp, i]
         _lib.orc2_totals.argtypes = [P2, vp, vp, vp]
+        _lib.orc_set_threads.restype = i
+        _lib.orc_set_threads.argtypes = [i]
+        _lib.orc_set_threads(max(1, int(os.environ.get("ORACLE_THREADS", "1"))))
     return _lib
 
 

@@ -12,7 +12,10 @@
  * computed here from the paper's formulas.
  *
  * Every routine follows the paper's statement in the paper's order, in plain
- * loops; nothing is blocked, fused or reordered for speed.
+ * loops; nothing is blocked, fused or reordered for speed.  Built with
+ * OpenMP, the independent node loops (and velocity rows) are shared among
+ * threads; each node's arithmetic, and so every result bit, is the same for
+ * any thread count.
  *
  * Notation (reduced units of Sec. III: m = k_B = 1):
  *   F(z, xi) = integral of f over the transverse momenta,
@@ -24,6 +27,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Scalar type of everything that depends on the state.  The file is compiled
  * twice: as plain FP64 (real = double, entry points orc_*), and with
@@ -163,6 +169,7 @@ void ORC(moments)(const orc_params *p, const real *F, const real *G,
                   real *n, real *u, real *T, real *q)
 {
     int nz = p->nz, Q = p->Q;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nz; i++) {
         real sn = 0.0, sj = 0.0;
         for (int k = 0; k < Q; k++) {
@@ -408,18 +415,22 @@ void ORC(equilibrium)(const orc_params *p, const real *n, const real *u,
                       const real *T, real *F, real *G)
 {
     int nz = p->nz, Q = p->Q;
-    real *FS = (real *)malloc(Q * sizeof(real));
-    real *GS = (real *)malloc(Q * sizeof(real));
-    real *JF = (real *)malloc(Q * sizeof(real));
-    real *JG = (real *)malloc(Q * sizeof(real));
-    for (int i = 0; i < nz; i++) {
-        ORC(equilibria_node)(p, n[i], u[i], T[i], 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, FS, GS, JF, JG);
-        for (int k = 0; k < Q; k++) {
-            F[k * nz + i] = FS[k];
-            G[k * nz + i] = GS[k];
+#pragma omp parallel
+    {
+        real *FS = (real *)malloc(Q * sizeof(real));
+        real *GS = (real *)malloc(Q * sizeof(real));
+        real *JF = (real *)malloc(Q * sizeof(real));
+        real *JG = (real *)malloc(Q * sizeof(real));
+#pragma omp for schedule(static)
+        for (int i = 0; i < nz; i++) {
+            ORC(equilibria_node)(p, n[i], u[i], T[i], 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, FS, GS, JF, JG);
+            for (int k = 0; k < Q; k++) {
+                F[k * nz + i] = FS[k];
+                G[k * nz + i] = GS[k];
+            }
         }
+        free(FS); free(GS); free(JF); free(JG);
     }
-    free(FS); free(GS); free(JF); free(JG);
 }
 
 /* ------------------------------------------------------------------ */
@@ -523,13 +534,6 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     real *T = (real *)malloc(nz * sizeof(real));
     real *q = (real *)malloc(nz * sizeof(real));
     real *fl = (real *)malloc((size_t)ORC_NFIELDS * nz * sizeof(real));
-    real *row = (real *)malloc(nz * sizeof(real));
-    real *hk = (real *)malloc(Q * sizeof(real));
-    real *dh = (real *)malloc(Q * sizeof(real));
-    real *FS = (real *)malloc(Q * sizeof(real));
-    real *GS = (real *)malloc(Q * sizeof(real));
-    real *JF = (real *)malloc(Q * sizeof(real));
-    real *JG = (real *)malloc(Q * sizeof(real));
 
     /* moments, then node fields */
     ORC(moments)(p, F, G, n, u, T, q);
@@ -538,27 +542,39 @@ void ORC(rhs)(const orc_params *p, const real *F, const real *G,
     const real *A = fl + 11 * nz, *B = fl + 12 * nz, *D = fl + 13 * nz;
     const real *bnchi = fl + 15 * nz;
 
-    /* free streaming term */
+    /* free streaming term (velocity rows are independent) */
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < Q; k++) {
         advect_row(p, p->xi[k], F + (size_t)k * nz, RF + (size_t)k * nz);
         advect_row(p, p->xi[k], G + (size_t)k * nz, RG + (size_t)k * nz);
     }
-    /* force, collision and J1 terms, node by node */
-    for (int i = 0; i < nz; i++) {
-        ORC(equilibria_node)(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
-                             A[i], B[i], D[i], FS, GS, JF, JG);
-        for (int k = 0; k < Q; k++) hk[k] = F[k * nz + i];
-        ORC(dxi)(p, hk, dh);
-        for (int k = 0; k < Q; k++)
-            RF[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - FS[k]) + JF[k];
-        for (int k = 0; k < Q; k++) hk[k] = G[k * nz + i];
-        ORC(dxi)(p, hk, dh);
-        for (int k = 0; k < Q; k++)
-            RG[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - GS[k]) + JG[k];
+    /* force, collision and J1 terms, node by node (nodes are independent;
+     * with OpenMP each thread has its own scratch) */
+#pragma omp parallel
+    {
+        real *hk = (real *)malloc(Q * sizeof(real));
+        real *dh = (real *)malloc(Q * sizeof(real));
+        real *FS = (real *)malloc(Q * sizeof(real));
+        real *GS = (real *)malloc(Q * sizeof(real));
+        real *JF = (real *)malloc(Q * sizeof(real));
+        real *JG = (real *)malloc(Q * sizeof(real));
+#pragma omp for schedule(static)
+        for (int i = 0; i < nz; i++) {
+            ORC(equilibria_node)(p, n[i], u[i], T[i], q[i], Pr[i], bnchi[i],
+                                 A[i], B[i], D[i], FS, GS, JF, JG);
+            for (int k = 0; k < Q; k++) hk[k] = F[k * nz + i];
+            ORC(dxi)(p, hk, dh);
+            for (int k = 0; k < Q; k++)
+                RF[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - FS[k]) + JF[k];
+            for (int k = 0; k < Q; k++) hk[k] = G[k * nz + i];
+            ORC(dxi)(p, hk, dh);
+            for (int k = 0; k < Q; k++)
+                RG[k * nz + i] += -force[i] * dh[k] - rate[i] * (hk[k] - GS[k]) + JG[k];
+        }
+        free(hk); free(dh); free(FS); free(GS); free(JF); free(JG);
     }
     if (fields) memcpy(fields, fl, (size_t)ORC_NFIELDS * nz * sizeof(real));
-    free(n); free(u); free(T); free(q); free(fl); free(row);
-    free(hk); free(dh); free(FS); free(GS); free(JF); free(JG);
+    free(n); free(u); free(T); free(q); free(fl);
 }
 
 /* ------------------------------------------------------------------ */
@@ -612,16 +628,19 @@ void ORC(step)(const orc_params *p, real *F, real *G, int nsteps)
     double dt = p->dt;
     for (int s = 0; s < nsteps; s++) {
         ORC(rhs)(p, F, G, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < N; e++) {
             F1[e] = F[e] + dt * RF[e];
             G1[e] = G[e] + dt * RG[e];
         }
         ORC(rhs)(p, F1, G1, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < N; e++) {
             F2[e] = 0.75 * F[e] + 0.25 * (F1[e] + dt * RF[e]);
             G2[e] = 0.75 * G[e] + 0.25 * (G1[e] + dt * RG[e]);
         }
         ORC(rhs)(p, F2, G2, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < N; e++) {
             F[e] = F[e] / 3.0 + 2.0 / 3.0 * (F2[e] + dt * RF[e]);
             G[e] = G[e] / 3.0 + 2.0 / 3.0 * (G2[e] + dt * RG[e]);
@@ -632,6 +651,26 @@ void ORC(step)(const orc_params *p, real *F, real *G, int nsteps)
 }
 
 #ifndef ORC_COMPLEX
+/* ------------------------------------------------------------------ */
+/* Threads                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Node loops (and the velocity rows of the free-streaming term) run in
+ * parallel when the oracle is built with OpenMP; every node's arithmetic is
+ * the same in any thread, so results do not depend on the thread count.
+ * Sets the thread count (n > 0) and returns the count in effect (1 without
+ * OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Conserved totals                                                    */
 /* ------------------------------------------------------------------ */

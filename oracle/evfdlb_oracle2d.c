@@ -110,9 +110,12 @@ static double line_integral(int s, double a, double z0)
 {
     static double gx[32], gw[32];
     static int ready = 0;
-    if (!ready) {
-        gauss_legendre32(gx, gw);
-        ready = 1;
+#pragma omp critical(orc2_gauss_legendre)
+    {
+        if (!ready) {
+            gauss_legendre32(gx, gw);
+            ready = 1;
+        }
     }
     double phi0 = (z0 > 0.0) ? atan(a / z0) : 0.5 * PI2D;
     double acc = 0.0;
@@ -168,6 +171,7 @@ void orc2_moments(const orc2_params *p, const double *F, const double *G, double
                   double *ux, double *uy, double *T, double *qx, double *qy)
 {
     int N = p->nx * p->ny, Q = p->Q;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; i++) {
         double sn = 0.0, sx = 0.0, sy = 0.0;
         for (int kx = 0; kx < Q; kx++)
@@ -245,6 +249,7 @@ void orc2_node_fields(const orc2_params *p, const double *n, const double *ux, c
             double r2 = (a * a + c * c) * p->dx * p->dx;
             if (r2 < p->sigma * p->sigma) wsum += 2.0 * sqrt(p->sigma * p->sigma - r2);
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             double acc = 0.0;
@@ -267,6 +272,7 @@ void orc2_node_fields(const orc2_params *p, const double *n, const double *ux, c
             if (rx * rx + ry * ry > p->rcut * p->rcut * (1.0 + 1e-12)) continue;
             orc2_force_kernel(p, rx, ry, gt + 2 * ((a + M) * W + (c + M)));
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             double sx = 0.0, sy = 0.0;
@@ -400,22 +406,26 @@ void orc2_equilibrium(const orc2_params *p, const double *n, const double *ux, c
                       const double *T, double *F, double *G)
 {
     int N = p->nx * p->ny, Q = p->Q;
-    double fl[ORC2_NFIELDS];
-    double *FS = (double *)malloc(Q * Q * sizeof(double));
-    double *GS = (double *)malloc(Q * Q * sizeof(double));
-    double *JF = (double *)malloc(Q * Q * sizeof(double));
-    double *JG = (double *)malloc(Q * Q * sizeof(double));
-    for (int i = 0; i < N; i++) {
-        memset(fl, 0, sizeof(fl));
-        fl[0] = n[i]; fl[1] = ux[i]; fl[2] = uy[i]; fl[3] = T[i];
-        fl[7] = 1.0; fl[12] = 1.0;   /* q = 0, Pr = 1: the Shakhov factor is 1 */
-        orc2_equilibria_node(p, fl, FS, GS, JF, JG);
-        for (int k = 0; k < Q * Q; k++) {
-            F[k * N + i] = FS[k];
-            G[k * N + i] = GS[k];
+#pragma omp parallel
+    {
+        double fl[ORC2_NFIELDS];
+        double *FS = (double *)malloc(Q * Q * sizeof(double));
+        double *GS = (double *)malloc(Q * Q * sizeof(double));
+        double *JF = (double *)malloc(Q * Q * sizeof(double));
+        double *JG = (double *)malloc(Q * Q * sizeof(double));
+#pragma omp for schedule(static)
+        for (int i = 0; i < N; i++) {
+            memset(fl, 0, sizeof(fl));
+            fl[0] = n[i]; fl[1] = ux[i]; fl[2] = uy[i]; fl[3] = T[i];
+            fl[7] = 1.0; fl[12] = 1.0;   /* q = 0, Pr = 1: the Shakhov factor is 1 */
+            orc2_equilibria_node(p, fl, FS, GS, JF, JG);
+            for (int k = 0; k < Q * Q; k++) {
+                F[k * N + i] = FS[k];
+                G[k * N + i] = GS[k];
+            }
         }
+        free(FS); free(GS); free(JF); free(JG);
     }
-    free(FS); free(GS); free(JF); free(JG);
 }
 
 /* ------------------------------------------------------------------ */
@@ -506,32 +516,40 @@ void orc2_rhs(const orc2_params *p, const double *F, const double *G, double *RF
     double *fl = (double *)malloc((size_t)ORC2_NFIELDS * N * sizeof(double));
     orc2_moments(p, F, G, mom, mom + N, mom + 2 * N, mom + 3 * N, mom + 4 * N, mom + 5 * N);
     orc2_node_fields(p, mom, mom + N, mom + 2 * N, mom + 3 * N, mom + 4 * N, mom + 5 * N, fl);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int kx = 0; kx < Q; kx++)
         for (int ky = 0; ky < Q; ky++) {
             int k = kx * Q + ky;
             advect_plane(p, p->xi[kx], p->xi[ky], F + (size_t)k * N, RF + (size_t)k * N);
             advect_plane(p, p->xi[kx], p->xi[ky], G + (size_t)k * N, RG + (size_t)k * N);
         }
-    double *FS = (double *)malloc(K * sizeof(double)), *GS = (double *)malloc(K * sizeof(double));
-    double *JF = (double *)malloc(K * sizeof(double)), *JG = (double *)malloc(K * sizeof(double));
-    double *h = (double *)malloc(K * sizeof(double));
-    double *dx_ = (double *)malloc(K * sizeof(double)), *dy_ = (double *)malloc(K * sizeof(double));
-    double node[ORC2_NFIELDS];
-    for (int i = 0; i < N; i++) {
-        for (int f = 0; f < ORC2_NFIELDS; f++) node[f] = fl[(size_t)f * N + i];
-        orc2_equilibria_node(p, node, FS, GS, JF, JG);
-        double Fx = node[8], Fy = node[9], nu = node[13];
-        for (int k = 0; k < K; k++) h[k] = F[(size_t)k * N + i];
-        orc2_dxi(p, h, dx_, dy_);
-        for (int k = 0; k < K; k++)
-            RF[(size_t)k * N + i] += -Fx * dx_[k] - Fy * dy_[k] - nu * (h[k] - FS[k]) + JF[k];
-        for (int k = 0; k < K; k++) h[k] = G[(size_t)k * N + i];
-        orc2_dxi(p, h, dx_, dy_);
-        for (int k = 0; k < K; k++)
-            RG[(size_t)k * N + i] += -Fx * dx_[k] - Fy * dy_[k] - nu * (h[k] - GS[k]) + JG[k];
+    /* node by node (nodes are independent; with OpenMP each thread has its
+     * own scratch) */
+#pragma omp parallel
+    {
+        double *FS = (double *)malloc(K * sizeof(double)), *GS = (double *)malloc(K * sizeof(double));
+        double *JF = (double *)malloc(K * sizeof(double)), *JG = (double *)malloc(K * sizeof(double));
+        double *h = (double *)malloc(K * sizeof(double));
+        double *dx_ = (double *)malloc(K * sizeof(double)), *dy_ = (double *)malloc(K * sizeof(double));
+        double node[ORC2_NFIELDS];
+#pragma omp for schedule(static)
+        for (int i = 0; i < N; i++) {
+            for (int f = 0; f < ORC2_NFIELDS; f++) node[f] = fl[(size_t)f * N + i];
+            orc2_equilibria_node(p, node, FS, GS, JF, JG);
+            double Fx = node[8], Fy = node[9], nu = node[13];
+            for (int k = 0; k < K; k++) h[k] = F[(size_t)k * N + i];
+            orc2_dxi(p, h, dx_, dy_);
+            for (int k = 0; k < K; k++)
+                RF[(size_t)k * N + i] += -Fx * dx_[k] - Fy * dy_[k] - nu * (h[k] - FS[k]) + JF[k];
+            for (int k = 0; k < K; k++) h[k] = G[(size_t)k * N + i];
+            orc2_dxi(p, h, dx_, dy_);
+            for (int k = 0; k < K; k++)
+                RG[(size_t)k * N + i] += -Fx * dx_[k] - Fy * dy_[k] - nu * (h[k] - GS[k]) + JG[k];
+        }
+        free(FS); free(GS); free(JF); free(JG); free(h); free(dx_); free(dy_);
     }
     if (fields) memcpy(fields, fl, (size_t)ORC2_NFIELDS * N * sizeof(double));
-    free(mom); free(fl); free(FS); free(GS); free(JF); free(JG); free(h); free(dx_); free(dy_);
+    free(mom); free(fl);
 }
 
 /* Shu-Osher RK3, in place */
@@ -544,16 +562,19 @@ void orc2_step(const orc2_params *p, double *F, double *G, int nsteps)
     double dt = p->dt;
     for (int s = 0; s < nsteps; s++) {
         orc2_rhs(p, F, G, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < M; e++) {
             F1[e] = F[e] + dt * RF[e];
             G1[e] = G[e] + dt * RG[e];
         }
         orc2_rhs(p, F1, G1, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < M; e++) {
             F2[e] = 0.75 * F[e] + 0.25 * (F1[e] + dt * RF[e]);
             G2[e] = 0.75 * G[e] + 0.25 * (G1[e] + dt * RG[e]);
         }
         orc2_rhs(p, F2, G2, RF, RG, NULL);
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < M; e++) {
             F[e] = F[e] / 3.0 + 2.0 / 3.0 * (F2[e] + dt * RF[e]);
             G[e] = G[e] / 3.0 + 2.0 / 3.0 * (G2[e] + dt * RG[e]);
