@@ -286,10 +286,14 @@ evfdlb_status evfdlb_adjoint(evfdlb_ctx* ctx, const double* dL_dn_end, int32_t o
  * (the error word is cleared at the start of each call; everything else is
  * written before it is read), so calls that overlap on the GPU -- on
  * different streams or host threads of one device -- race: the caller must
- * serialise them.  Work is queued on cuda_stream (a cudaStream_t, NULL = the
- * legacy default stream); the call synchronises that stream once at the end
- * to read the error word.
- * Errors: E_INVALID_ARG, E_UNSUPPORTED, E_NONFINITE, E_NEGATIVE, E_CUDA. */
+ * serialise them (calls from host threads of one process are serialised by
+ * the library; a lock is held for the whole call).  Work is queued on
+ * cuda_stream (a cudaStream_t, NULL = the legacy default stream); every call
+ * copies its small parameter block from static host memory and synchronises
+ * that stream before it returns, to read the error word.
+ * Errors: E_INVALID_ARG, E_UNSUPPORTED, E_NONFINITE, E_NEGATIVE, E_CUDA (also
+ * when a CUDA error is already pending in the calling thread: it is returned,
+ * not cleared, and nothing is queued). */
 #define EVFDLB_STATIC_MAX_NODES 8192
 #define EVFDLB_STATIC_MAX_ELEMENTS 65536
 #define EVFDLB_STATIC_MAX_HALFWIDTH 500

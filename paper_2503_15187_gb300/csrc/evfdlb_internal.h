@@ -77,8 +77,9 @@ struct WorkItem {
 };
 
 // ---- host model code (host_model.cpp) ----
-bool velocity_set(int Q, double* xi, double* w);                 // ascending, sum w = 1
-void build_tables(int Q, const double* xi, const double* w, double* out);  // TableLayout(Q)
+constexpr int kVelocitySetMax = 64;                              // largest order of evfdlb_velocity_set
+bool velocity_set(int Q, double* xi, double* w);                 // ascending, sum w = 1; no heap
+void build_tables(int Q, const double* xi, const double* w, double* out);  // TableLayout(Q); no heap
 bool validate(const evfdlb_params& p, const char** why);
 int tap_halfwidth(double len, double dx);                        // len/dx if integral, else -1
 int force_halfwidth(const evfdlb_params& p);                     // force/energy taps and density halo

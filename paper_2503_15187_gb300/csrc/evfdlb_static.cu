@@ -12,8 +12,11 @@
 // library holds that array (about 3.4 MiB) until the process exits.
 //
 // The state buffer, the only data the caller passes, is advanced in place.
-// Calls share the array, so calls that overlap on the GPU race; the mutex
-// below only orders the host-side set-up.
+// Calls share the array, so calls that overlap on the GPU race.  The mutex
+// below is held for a whole call, through its final stream synchronisation,
+// so calls from different host threads of one process are serialised; calls
+// from different processes, or work the caller queues on other streams
+// against the same state, are not.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -78,45 +81,6 @@ evfdlb_status st_of(cudaError_t e) {
     return e == cudaSuccess ? EVFDLB_OK : (e == cudaErrorMemoryAllocation ? EVFDLB_E_OOM : EVFDLB_E_CUDA);
 }
 
-// Velocity set of order Q <= 32 with fixed-size storage: Sturm-count
-// bisection on the Jacobi matrix of the probabilists' Hermite recurrence,
-// then Newton on psi_Q (psi_Q' = sqrt(Q) psi_{Q-1}); w = 1/(Q psi_{Q-1}^2).
-void psi_fixed(int L, long double x, long double* psi) {
-    psi[0] = 1;
-    if (L >= 1) psi[1] = x;
-    for (int l = 1; l < L; ++l)
-        psi[l + 1] = (x * psi[l] - sqrtl((long double)l) * psi[l - 1]) / sqrtl((long double)(l + 1));
-}
-
-bool velocity_set_fixed(int Q, double* xi, double* w) {
-    if (Q < 1 || Q > kQMax) return false;
-    long double psi[kQMax + 1];
-    long double bound = sqrtl(4.0L * Q + 2.0L) + 1.0L;
-    for (int k = 0; k < Q; ++k) {
-        long double lo = -bound, hi = bound;
-        for (int it = 0; it < 200 && hi - lo > 1e-18L * (1 + fabsl(lo)); ++it) {
-            long double mid = 0.5L * (lo + hi), d = -mid;
-            int count = d < 0;
-            for (int j = 1; j < Q; ++j) {
-                d = -mid - (long double)j / (d == 0 ? 1e-300L : d);
-                count += d < 0;
-            }
-            if (count >= k + 1) hi = mid; else lo = mid;
-        }
-        long double x = 0.5L * (lo + hi);
-        for (int it = 0; it < 3; ++it) {
-            psi_fixed(Q, x, psi);
-            long double dpsi = sqrtl((long double)Q) * psi[Q - 1];
-            if (dpsi == 0) break;
-            x -= psi[Q] / dpsi;
-        }
-        psi_fixed(Q, x, psi);
-        xi[k] = (double)x;
-        w[k] = (double)(1.0L / ((long double)Q * psi[Q - 1] * psi[Q - 1]));
-    }
-    return true;
-}
-
 }  // namespace
 
 extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* state, int64_t nsteps,
@@ -130,6 +94,11 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     std::lock_guard<std::mutex> lock(g_mutex);
+    // an error left pending by earlier, unrelated work of this host thread
+    // is reported as it stands (not cleared) before anything is queued, so
+    // that it is not mistaken for a failure of this call's launches
+    cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return st_of(pending);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EVFDLB_E_CUDA;
     int sms = 1;
@@ -161,7 +130,7 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
 
     // tables, taps, slab descriptor and work list of this call
     double xi[kQMax], w[kQMax];
-    if (!velocity_set_fixed(p->Q, xi, w)) return EVFDLB_E_INVALID_ARG;
+    if (!velocity_set(p->Q, xi, w)) return EVFDLB_E_INVALID_ARG;
     build_tables(p->Q, xi, w, h_tables);
     int ntaps = fill_taps(*p, h_taps, kMaxTaps);
     if (ntaps < 0) return EVFDLB_E_INVALID_ARG;

@@ -45,9 +45,10 @@ int sturm_count(int Q, long double x) {
 // Roots of He_Q (the velocity nodes of the full-range Gauss-Hermite rule) by
 // bisection on the Sturm count, polished by Newton on psi_Q with
 // psi_Q' = sqrt(Q) psi_{Q-1}; weights w = 1 / (Q psi_{Q-1}(x)^2), which sum to 1.
+// Fixed-size storage (no heap), so that the allocation-free step can call it.
 bool velocity_set(int Q, double* xi, double* w) {
-    if (Q < 1 || Q > 64) return false;
-    std::vector<long double> psi(Q + 1);
+    if (Q < 1 || Q > kVelocitySetMax) return false;
+    long double psi[kVelocitySetMax + 1];
     long double bound = sqrtl(4.0L * Q + 2.0L) + 1.0L;
     for (int k = 0; k < Q; ++k) {
         long double lo = -bound, hi = bound;   // k-th smallest: count(x) >= k+1
@@ -57,25 +58,26 @@ bool velocity_set(int Q, double* xi, double* w) {
         }
         long double x = 0.5L * (lo + hi);
         for (int it = 0; it < 3; ++it) {
-            psi_all<long double>(Q, x, psi.data());
+            psi_all<long double>(Q, x, psi);
             long double dpsi = sqrtl((long double)Q) * psi[Q - 1];
             if (dpsi == 0) break;
             x -= psi[Q] / dpsi;
         }
-        psi_all<long double>(Q, x, psi.data());
+        psi_all<long double>(Q, x, psi);
         xi[k] = (double)x;
         w[k] = (double)(1.0L / ((long double)Q * psi[Q - 1] * psi[Q - 1]));
     }
     return true;
 }
 
+// Fixed-size storage (no heap), like velocity_set.
 void build_tables(int Q, const double* xi, const double* w, double* out) {
     TableLayout L(Q);
-    std::vector<long double> psi(Q + 1);
+    long double psi[kVelocitySetMax + 1];
     for (int k = 0; k < Q; ++k) {
         out[L.xi + k] = xi[k];
         out[L.w + k] = w[k];
-        psi_all<long double>(Q, (long double)xi[k], psi.data());
+        psi_all<long double>(Q, (long double)xi[k], psi);
         for (int l = 0; l < Q; ++l) {
             out[L.P + l * Q + k] = (double)psi[l];
             out[L.S + k * Q + l] = (double)((long double)w[k] * psi[l]);

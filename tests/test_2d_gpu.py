@@ -155,3 +155,52 @@ def test_2d_other_disc_shapes(prec, bar, dx, rcut):
     eF, eG = rel(Fg, Fo), rel(Gg, Go)
     print(f"2D dx={dx} r_cut={rcut} prec={prec}: step F {eF:.1e} G {eG:.1e}")
     assert eF < bar and eG < bar
+
+
+# A grid wider than the force disc on both axes (r_cut = 6 at dx = 0.25: 49
+# nodes across), and a multiple of no tile edge: the 16 x 16 field tiles,
+# the 32 x 16 advection tiles and the 8-node collision groups all have
+# interior instances and ragged edges, and every force tap wraps the
+# periodic domain at most once -- the configuration of the 1024 x 1024 run.
+BIG = (72, 61, 16)
+
+
+@pytest.fixture(scope="module")
+def big_case():
+    import oracle as Om
+    nx, ny, Q = BIG
+    xi, _ = Om.gauss_hermite(Q)
+    dx = 0.25
+    dt = 0.5 * dx / (2 * np.abs(xi).max())          # the library's default CFL step
+    orc = Om.Oracle2D(Om.Setup2(nx=nx, ny=ny, Q=Q, dx=dx, dt=dt))
+    n, ux, uy, T = fields(nx, ny, seed=21)
+    F0, G0 = orc.equilibrium(n, ux, uy, T)
+    F, G = orc.step(F0, G0, 1)                       # a non-equilibrium state
+    RF, RG = orc.rhs(F, G)
+    F1, G1 = orc.step(F, G, 1)
+    return dict(dt=dt, F=F, G=G, RF=RF, RG=RG, F1=F1, G1=G1)
+
+
+@pytest.mark.parametrize("prec,bar_step", [(ev.FP64, 1e-12), (ev.FP32, 1e-5)])
+def test_2d_parity_beyond_the_force_disc(big_case, prec, bar_step):
+    """72 x 61 grid, dx 0.25, r_cut 6, 16 x 16 velocities: one right-hand
+    side (FP64, 1e-11) and one RK3 step (FP64 1e-12, FP32 1e-5) against the
+    2D oracle, reaching the interior k2_fields / k2_adv tiles and the full
+    1809-tap force column plan."""
+    nx, ny, Q = BIG
+    p = ev.Params(nx=nx, dx=0.25, Q=Q, dim=2, ny=ny, precision=prec)
+    sim = ev.Sim(p)
+    assert abs(sim.dt() - big_case["dt"]) < 1e-15 * big_case["dt"]
+    sim.set_state(big_case["F"].ravel(), big_case["G"].ravel())
+    if prec == ev.FP64:
+        RF, RG = sim.rhs()
+        eF = rel(RF.reshape(big_case["RF"].shape), big_case["RF"])
+        eG = rel(RG.reshape(big_case["RG"].shape), big_case["RG"])
+        print(f"2D FP64 {nx}x{ny}: rhs F {eF:.1e} G {eG:.1e}")
+        assert eF < 1e-11 and eG < 1e-11
+    sim.step(1)
+    Fg, Gg = sim.state_2d()
+    eF, eG = rel(Fg, big_case["F1"]), rel(Gg, big_case["G1"])
+    print(f"2D prec={prec} {nx}x{ny}: step F {eF:.1e} G {eG:.1e}")
+    assert eF < bar_step and eG < bar_step
+    sim.close()
