@@ -34,9 +34,19 @@ UNIT = "GNVUPS"
 L2_FLUSH_BYTES = 512 << 20
 
 
+def stage_flops_method(Q: int) -> float:
+    """Algorithmic FP64 flops of one stage-kernel launch per node, on the
+    method's own operation count per node-velocity and distribution: one
+    WENO-5 face (about 60 flops with its divisions), the force term's Hermite
+    analysis (2Q), the synthesis of the collision and force terms (2Q) and
+    the collision / RK combine (8); two distributions:
+    2 (68 + 4Q) per node-velocity, 392 at Q = 32."""
+    return Q * 2.0 * (68 + 4 * Q)
+
+
 def stage_flops(Q: int, M: int, m: int) -> float:
-    """Algorithmic FP64 flops of one stage-kernel launch per node (FMA = 2,
-    division = 1), from the operation counts of the method:
+    """Detailed FP64 flop count of one stage-kernel launch per node (FMA = 2,
+    division = 1), from the operation counts of this kernel's arithmetic:
       per node and distribution, per velocity: Hermite analysis 2(Q-1),
       synthesis 2Q, one WENO-5 face 65, advective difference, relaxation and
       RK combine 10, moment sums 6;
@@ -48,8 +58,14 @@ def stage_flops(Q: int, M: int, m: int) -> float:
 
 
 def fp64_peak_gflops(sm_mhz: float, sms: int = 152) -> float:
-    """FP64 FMA rate of GB300: 2 FP64 FMA per clock per SM (4 flops)."""
+    """Nominal FP64 FMA rate of GB300: 2 FP64 FMA per clock per SM (4 flops)."""
     return sms * 4 * sm_mhz * 1e6 / 1e9
+
+
+def fp64_peak_measured(ev, stream):
+    """FP64 FMA throughput measured on this device in this run (the library's
+    probe: independent FMA chains on every SM, best of 5 timed launches)."""
+    return ev.probe_fp64_fma(5, stream=stream)
 
 
 class ClockSampler:
@@ -100,6 +116,8 @@ class ClockSampler:
 
 
 TILE = 0   # --tile: fixed node tile for every leg (0: the autotuner's choice per leg)
+# 2D step: bytes of state the kernels move per node-velocity-step (FP32)
+IMPL_BYTES_2D = 168
 # DRAM bytes (read + write) of one stage_kernel<double> launch (its one-wave
 # 12-warp form) of this workload at the one-wave 27-node tile, from
 # `ncu --set full` of the current kernel (4.51 MB read, 0 written: the outputs
@@ -168,6 +186,21 @@ def run_ours(args, rank, world):
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_total = sum(ms_steps)
 
+    # the stage kernel by itself: each of the three stage launches of a step
+    # bracketed by events on the context's stream (the state is not changed),
+    # L2 flushed before each step as in the timed loop
+    nprof = min(args.steps, 200)
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nprof)]
+    for i in range(nprof):
+        flush.fill_(float(i))
+        for j in range(3):
+            sev[i][j].record(stream)
+            sim.profile_stage(j)
+        sev[i][3].record(stream)
+    torch.cuda.synchronize()
+    stage_ms = [statistics.mean(sev[i][j].elapsed_time(sev[i][j + 1]) for i in range(nprof)) for j in range(3)]
+    peak_meas = fp64_peak_measured(ev, stream)
+
     # end-to-end through the public API with pinned host buffers: per step the
     # state goes host -> device, one step runs, the moments come back (the
     # step is queued with evfdlb_step_async; evfdlb_moments synchronises and
@@ -210,10 +243,12 @@ def run_ours(args, rank, world):
     sd = [ev.lib()]  # keep the library loaded until here
     del sd
     M, m = int(round(6.0 / DZ)), int(round(1.0 / DZ))
-    launch_ms = (ms_total / args.steps) / 3.0      # three stage launches per step, back to back
-    flops = stage_flops(Q, M, m) * NZ
+    launch_ms = statistics.mean(stage_ms)          # measured per stage launch (above)
+    flops = stage_flops_method(Q) * NZ
+    flops_detail = stage_flops(Q, M, m) * NZ
     achieved = flops / (launch_ms * 1e-3) / 1e9
-    peak = fp64_peak_gflops(2070.0)
+    peak = peak_meas
+    peak_nom = fp64_peak_gflops(2070.0)
     hbm_bytes = 128 * NZ * Q                       # 8 array passes x 2 distributions x 8 B per NVU-step
     hbm = hbm_bytes / (ms_total / args.steps * 1e-3) / 1e9
     peaks = {}
@@ -231,8 +266,18 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}", "tile_nodes": sim.tile_nodes()},
         "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": achieved, "peak": peak,
                      "unit": "GFLOP/s", "frac": achieved / peak,
-                     "peak_note": "FP64 FMA: 152 SMs x 2 FMA/clk x 2070 MHz (derived)",
-                     "flops_per_launch": flops, "launch_ms": launch_ms, "traffic": STAGE_TRAFFIC_BYTES,
+                     "peak_note": "FP64 FMA throughput measured in this run (evfdlb_probe_fp64_fma, of measured)",
+                     "peak_nominal": peak_nom, "frac_of_nominal": achieved / peak_nom,
+                     "peak_nominal_note": "152 SMs x 2 FP64 FMA/clk x 2070 MHz",
+                     "flops_per_launch": flops,
+                     "flops_note": "2 (68 + 4Q) per node-velocity (WENO-5 face ~60, analysis 2Q, synthesis 2Q, "
+                                   "collision and RK 8; two distributions)",
+                     "flops_per_launch_detailed": flops_detail,
+                     "frac_detailed": flops_detail / (launch_ms * 1e-3) / 1e9 / peak,
+                     "launch_ms": launch_ms, "stage_ms": stage_ms,
+                     "launch_note": "CUDA events around each stage launch alone (evfdlb_profile_stage), "
+                                    f"mean over {nprof} steps",
+                     "traffic": STAGE_TRAFFIC_BYTES,
                      "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one stage_kernel<double> "
                                      "launch at the 27-node tile (ncu, profiles/stage_kernel_liquid_slab_"
                                      "4096x32_fp64_full.md)"},
@@ -358,7 +403,7 @@ def df_variant(args, ev, p, T, n0, stream, flush, barrier, maxred, world, n64):
             "gpu_launches": 3 * args.steps, "tile_nodes": tile}
 
 
-def adjoint_leg(ev, W, stream, steps=200):
+def adjoint_leg(ev, W, stream, steps=2000):
     """Cost of the discrete adjoint against the forward run on the adjoint
     calibration workload (periodic slab Nz = 1024, dz = 0.25, Q = 24,
     T = 0.7 T_c, mean n = 0.25 with +-1% noise, checkpoint every 100 steps),
@@ -390,7 +435,7 @@ def adjoint_leg(ev, W, stream, steps=200):
             "backward_ms": bwd, "backward_over_forward": bwd / fwd}
 
 
-def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=4):
+def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=100):
     """Batched against per-instance launches on the phase-separation batch:
     256 independent periodic slabs, Nz log-uniform in [128, 8192],
     Q in {16, 24, 32}, T/T_c in [0.6, 0.95], mean n in [0.15, 0.35], +-1%
@@ -461,9 +506,11 @@ def two_d_leg(ev, stream, flush, maxred, world, steps=3, size=1024):
     tensor-product Gauss-Hermite 16 x 16 velocities, FP32 bulk with FP64
     conserved sums, T = 0.75 T_c, mean n = 0.25 with +-1% seeded noise.
     State 2 GiB per copy (larger than L2); timed over `steps` steps with CUDA
-    events.  Algorithmic HBM bytes per node-velocity-step: the four launches
-    of a stage move the state 7 times (moments 1, collision 2, advection 4:
-    source, local RHS, base, output), 2 distributions x 4 B, 3 stages: 168 B."""
+    events.  Algorithmic HBM bytes per node-velocity-step: the Shu-Osher RK3
+    streams 8 array passes per step (stage 1 reads u and writes u1, stages 2
+    and 3 read u and their input and write), 2 distributions x 4 B: 64 B.
+    The implementation's own state traffic per node-velocity-step is
+    reported beside it (IMPL_BYTES_2D)."""
     import numpy as np
     import torch
     nx = ny = size           # --two-d-size: a smaller grid for ncu captures only
@@ -483,19 +530,30 @@ def two_d_leg(ev, stream, flush, maxred, world, steps=3, size=1024):
     sim.step(0)
     ms = maxred(e0.elapsed_time(e1)) / steps
     mass = sim.moments()[4][0][0]
+    launches = sim.launches_per_step()
     sim.close()
     nvu = nx * ny * Q * Q
-    gbs = 168.0 * nvu / (ms * 1e-3) / 1e9
+    gbs = 64.0 * nvu / (ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     return {"workload": f"2D phase separation {nx}x{ny}, dx 0.25, 16x16 velocities, FP32 (FP64 conserved sums)",
-            "value": nvu * world / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "algorithmic_GBps": gbs,
-            "mass": mass, "gpu_launches_per_step": 12}
+            "value": nvu * world / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "algorithmic_GBps": gbs, "algorithmic_bytes_per_nvu_step": 64,
+            "hbm_frac_of_measured": gbs / hbm_peak, "hbm_peak_GBps": hbm_peak,
+            "impl_state_bytes_per_nvu_step": IMPL_BYTES_2D,
+            "impl_state_GBps": IMPL_BYTES_2D * nvu / (ms * 1e-3) / 1e9,
+            "mass": mass, "gpu_launches_per_step": launches}
 
 
-def cpu_baseline(budget_s, T, n0, max_steps=10**9):
-    """Times the FP64 oracle as it stands on one host core on a bounded sample
-    of the same workload (whole slab, as many steps as fit in budget_s)."""
+def _oracle_rate(O, threads, budget_s, T, n0, max_steps=10**9):
+    """(GNVUPS, steps, seconds, threads used) of the FP64 oracle as it stands
+    on the bench slab, whole slab per step, as many steps as fit in budget_s."""
     import numpy as np
-    import oracle as O
+    used = O.set_threads(threads)
     xi, _ = O.gauss_hermite(Q)
     dt = 0.5 * DZ / np.abs(xi).max()
     orc = O.Oracle(O.Setup(nz=NZ, Q=Q, dz=DZ, dt=dt, bc=1))
@@ -507,17 +565,32 @@ def cpu_baseline(budget_s, T, n0, max_steps=10**9):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": NZ * Q * steps / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full time steps of the {NZ}x{Q} slab ({el:.1f} s, single thread)"}
+    return NZ * Q * steps / el / 1e9, steps, el, used
+
+
+def cpu_baseline(budget_s, T, n0):
+    """Times the FP64 oracle as it stands on the host's cores on a bounded
+    sample of the same workload: OpenMP over the nodes on every core this
+    process may use (the primary figure), and on one core (`single_core`)."""
+    import oracle as O
+    cores = O.available_cores()
+    v1, s1, e1, _ = _oracle_rate(O, 1, budget_s, T, n0)
+    vn, sn, en, used = _oracle_rate(O, cores, budget_s, T, n0)
+    O.set_threads(1)
+    return {"value": vn, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{sn} full time steps of the {NZ}x{Q} slab ({en:.1f} s, OpenMP over nodes, {used} threads)",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{s1} full time steps of the {NZ}x{Q} slab ({e1:.1f} s, one thread)"}}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step one full oracle time step
-    (about 0.3 s on one core), timed over at most 100 steps so that the run
-    stays within a minute; the line reports the steps actually timed."""
+    """The oracle as the reference arm, on every host core this process may
+    use (OpenMP over nodes): each step one full oracle time step, at most 100
+    steps timed so that the run stays within a minute or two; the line
+    reports the steps actually timed and the threads used."""
     import numpy as np
     import oracle as O
-    p_T = None
+    used = O.set_threads(O.available_cores())
     xi, _ = O.gauss_hermite(Q)
     dt = 0.5 * DZ / np.abs(xi).max()
     orc = O.Oracle(O.Setup(nz=NZ, Q=Q, dz=DZ, dt=dt, bc=1))
@@ -532,13 +605,13 @@ def run_reference(args):
     F, G = orc.step(F, G, steps)
     el = time.perf_counter() - t0
     v = NZ * Q * steps / el / 1e9
-    del p_T
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "nodes": NZ, "velocities": Q},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{steps} full time steps of the {NZ}x{Q} slab, single thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": f"{steps} full time steps of the {NZ}x{Q} slab, OpenMP over nodes, "
+                                       f"{used} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -548,7 +621,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="seconds of oracle time per CPU-baseline leg (one core, then all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="report the headline FP64 leg only (no FP32 / adjoint / batched / 2D legs), e.g. for ncu")

@@ -300,6 +300,31 @@ evfdlb_status evfdlb_adjoint(evfdlb_ctx* ctx, const double* dL_dn_end, int32_t o
 evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* state, int64_t nsteps,
                                  void* cuda_stream);
 
+/* ---- Measurement and self-test (no counterpart in the paper) ----
+ * evfdlb_probe_fp64_fma: FP64 fused multiply-add throughput of the current
+ *   device in GFLOP/s (2 flops per FMA): independent FMA chains on every SM,
+ *   timed with CUDA events on cuda_stream; best of reps >= 1 timed launches
+ *   after one warm-up.  The FP64 step is bound by this pipe, so this is the
+ *   measured peak of its roofline.  Synchronises the stream.
+ * evfdlb_divide_fp64: q[i] = a[i] / b[i] (n >= 0 DEVICE arrays) as the
+ *   kernels form FP64 quotients on the hot path (a Newton-refined reciprocal
+ *   with a final residual correction, Markstein's scheme: within about one
+ *   ulp, not correctly rounded; divisors outside the float exponent range use
+ *   the IEEE quotient; a quotient that overflows, or an infinite numerator,
+ *   gives NaN where IEEE gives +-inf -- both non-finite, which is what the
+ *   kernels check), and, if q_ieee != NULL, the IEEE quotient beside it.
+ *   Synchronises the stream.
+ * evfdlb_profile_stage: queues stage s (0, 1, 2) of one Shu-Osher step of a
+ *   one-dimensional context on its stream, as evfdlb_step runs it, without
+ *   touching the context's state: stage 2 writes the first intermediate
+ *   buffer instead of the state.  For timing the stage kernel by itself (the
+ *   caller brackets the call with events on the context's stream).  Errors:
+ *   E_INVALID_ARG, E_STATE (no state), E_UNSUPPORTED (dim = 2), E_CUDA. */
+evfdlb_status evfdlb_probe_fp64_fma(int32_t reps, void* cuda_stream, double* gflops);
+evfdlb_status evfdlb_divide_fp64(const double* a, const double* b, double* q, double* q_ieee, int64_t n,
+                                 void* cuda_stream);
+evfdlb_status evfdlb_profile_stage(evfdlb_ctx* ctx, int32_t stage);
+
 /* Releases the context and its device memory (NULL is a no-op). */
 void evfdlb_destroy(evfdlb_ctx* ctx);
 

@@ -113,6 +113,9 @@ def lib():
             "evfdlb_rhs_vjp": (i32, [vp, vp, vp, i32, vp, vp, vp]),
             "evfdlb_adjoint_state": (i32, [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
             "evfdlb_adjoint": (i32, [vp, vp, i32, vp, vp, vp]),
+            "evfdlb_probe_fp64_fma": (i32, [i32, vp, ctypes.POINTER(d)]),
+            "evfdlb_divide_fp64": (i32, [vp, vp, vp, vp, i64, vp]),
+            "evfdlb_profile_stage": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -185,6 +188,34 @@ def step_static(p: Params, state, nsteps: int = 1, stream=None):
            "evfdlb_step_static")
 
 
+def probe_fp64_fma(reps: int = 5, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, GFLOP/s (the peak
+    of the FP64 step's roofline); ``stream``: torch.cuda.Stream or None."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    g = ctypes.c_double()
+    _check(lib().evfdlb_probe_fp64_fma(int(reps), ctypes.c_void_p(s.cuda_stream), ctypes.byref(g)),
+           "evfdlb_probe_fp64_fma")
+    return g.value
+
+
+def divide_fp64(a, b, with_ieee=True, stream=None):
+    """(q, q_ieee): the library's FP64 quotient a / b of two CUDA float64
+    tensors, and the IEEE quotient beside it (None unless with_ieee)."""
+    import torch
+    if a.shape != b.shape:
+        raise ValueError("a and b must have the same shape")
+    (pa, da), (pb, db) = _ptr(a), _ptr(b)
+    if not (da and db):
+        raise ValueError("a and b must be CUDA float64 tensors")
+    q = torch.empty_like(a)
+    qi = torch.empty_like(a) if with_ieee else None
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().evfdlb_divide_fp64(pa, pb, q.data_ptr(), qi.data_ptr() if qi is not None else None,
+                                    a.numel(), ctypes.c_void_p(s.cuda_stream)), "evfdlb_divide_fp64")
+    return q, qi
+
+
 # ---------------------------------------------------------------------------
 # simulation context
 # ---------------------------------------------------------------------------
@@ -238,6 +269,11 @@ class Sim:
 
     def tile_nodes(self):
         return lib().evfdlb_tile_nodes(self.h)
+
+    def profile_stage(self, stage):
+        """Queues stage 0, 1 or 2 of one step (as evfdlb_step runs it) on the
+        context's stream without changing the state, for timing."""
+        _check(lib().evfdlb_profile_stage(self.h, int(stage)), "evfdlb_profile_stage")
 
     def init(self, n0, u0, T0):
         """Projected Maxwellian state of (n0, u0, T0); in 2D u0 holds ux then

@@ -668,6 +668,26 @@ void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, co
     adj_moments_kernel<<<nitems, kThreads, smem2, st>>>(slabs, items, tables, taps, mom, nadj, out, NF, NN, Z);
 }
 
+// Cotangent of the state for a loss of the final density n = sum_k F_k:
+// dL/dF_k = dL/dn at every velocity, dL/dG = 0 (per work item: its nodes).
+__global__ void __launch_bounds__(kThreads)
+adj_seed_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                const double* __restrict__ dn, double* __restrict__ barF, double* __restrict__ barG, long long NF) {
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    for (int e = threadIdx.x; e < sd.Q * it.nz; e += blockDim.x) {
+        const int k = e / it.nz, t = e - k * it.nz;
+        const long long g = sd.f_off + (long long)k * sd.nx + it.i0 + t;
+        barF[g] = dn[sd.node_off + it.i0 + t];
+        barG[g] = 0.0;
+    }
+}
+
+void launch_adj_seed(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items, const double* dn,
+                     double* barF, double* barG, long long NF) {
+    adj_seed_kernel<<<nitems, kThreads, 0, st>>>(slabs, items, dn, barF, barG, NF);
+}
+
 void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                      const double* tables, const double* init_fields, const double* lam, double* dn0, double* du0,
                      double* dT0, long long NF, long long NN) {

@@ -64,6 +64,8 @@ void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const W
                      double* dT0, long long NF, long long NN);
 void launch_adj_phi(int nslabs, cudaStream_t st, const SlabDesc* slabs, const double* phis, const double* phi_a,
                     double* out);
+void launch_adj_seed(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items, const double* dn,
+                     double* barF, double* barG, long long NF);
 // two-dimensional model (evfdlb_2d.cu)
 struct Ctx2;
 evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out);
@@ -184,21 +186,25 @@ void free_ctx(evfdlb_ctx* c) {
     delete c;
 }
 
+// One RK stage kernel of the context's step: out = a base + b (src + dt L(src)).
+void queue_stage(evfdlb_ctx* c, cudaStream_t st, const void* src, const void* base, void* out, const double* mi,
+                 double* mo, double a, double b) {
+    const int n = (int)c->items_h.size();
+    if (c->df)
+        launch_stage_df(n, c->smem_df, st, c->slabs, c->items, c->tables, c->dftables, c->taps, (const double*)src,
+                        (const double*)base, (double*)out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
+    else
+        launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps, src,
+                       base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
+}
+
 // Queues one time step (three stages) on stream st.
 void queue_step(evfdlb_ctx* c, cudaStream_t st) {
     const int n = (int)c->items_h.size();
     void *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
     double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
     auto stage = [&](const void* src, const void* base, void* out, const double* mi, double* mo, double a,
-                     double b) {
-        if (c->df)
-            launch_stage_df(n, c->smem_df, st, c->slabs, c->items, c->tables, c->dftables, c->taps,
-                            (const double*)src, (const double*)base, (double*)out, nullptr, mi, mo, c->NF, c->NN, a,
-                            b, 0, c->Z, c->err);
-        else
-            launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps,
-                           src, base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
-    };
+                     double b) { queue_stage(c, st, src, base, out, mi, mo, a, b); };
     stage(f0, nullptr, f1, m0, m1, 0.0, 1.0);              // u1 = u + dt L(u)
     stage(f1, f0, f2, m1, m2, 0.75, 0.25);                 // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
     stage(f2, f0, f0, m2, m0, 1.0 / 3.0, 2.0 / 3.0);       // u_new = 1/3 u + 2/3 (u2 + dt L(u2)), over u
@@ -780,6 +786,19 @@ evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
     return st;
 }
 
+evfdlb_status evfdlb_profile_stage(evfdlb_ctx* c, int32_t stage) {
+    if (!c || stage < 0 || stage > 2) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
+    if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
+    void *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
+    double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
+    if (stage == 0) queue_stage(c, c->user, f0, nullptr, f1, m0, m1, 0.0, 1.0);
+    else if (stage == 1) queue_stage(c, c->user, f1, f0, f2, m1, m2, 0.75, 0.25);
+    else queue_stage(c, c->user, f2, f0, f1, m2, m1, 1.0 / 3.0, 2.0 / 3.0);   // the state stays untouched
+    TRY_CUDA(cudaGetLastError());
+    return EVFDLB_OK;
+}
+
 evfdlb_status evfdlb_rhs_vjp(evfdlb_ctx* c, const double* WF, const double* WG, int32_t on_device, double* outF,
                              double* outG, double* dphi) {
     if (!c || !WF || !WG || !outF || !outG) return EVFDLB_E_INVALID_ARG;
@@ -917,27 +936,30 @@ evfdlb_status evfdlb_adjoint(evfdlb_ctx* c, const double* dL_dn_end, int32_t on_
     if (!c || !dL_dn_end) return EVFDLB_E_INVALID_ARG;
     if (c->c2) return EVFDLB_E_UNSUPPORTED;
     if (!c->have_state) return EVFDLB_E_STATE;
-    // n = sum_k F_k, so dL/dF_k = dL/dn for every k and dL/dG = 0
-    std::vector<double> hF((size_t)c->NF), hG((size_t)c->NF, 0.0), hn((size_t)c->NN);
-    if (on_device) {
-        TRY_CUDA(cudaMemcpyAsync(hn.data(), dL_dn_end, sizeof(double) * c->NN, cudaMemcpyDeviceToHost, c->user));
-        TRY_CUDA(cudaStreamSynchronize(c->user));
-    } else {
-        std::copy(dL_dn_end, dL_dn_end + c->NN, hn.begin());
+    // n = sum_k F_k, so dL/dF_k = dL/dn for every k and dL/dG = 0: the
+    // cotangent is formed on the device, in the scratch block [2 NF]
+    const double* g = dL_dn_end;
+    if (!on_device) {
+        double* gd = c->scratch + 2 * c->NF;     // [NN] after the cotangent (scratch holds 2 NF + 16 NN)
+        evfdlb_status s = copy_in(c, gd, dL_dn_end, sizeof(double) * c->NN, 0);
+        if (s != EVFDLB_OK) return s;
+        g = gd;
     }
-    for (int s = 0; s < c->nbatch; ++s) {
-        const SlabDesc& d = c->slabs_h[s];
-        for (int k = 0; k < d.Q; ++k)
-            for (int i = 0; i < d.nx; ++i) hF[(size_t)d.f_off + (size_t)k * d.nx + i] = hn[(size_t)d.node_off + i];
-    }
-    if (!on_device)
-        return evfdlb_adjoint_state(c, hF.data(), hG.data(), 0, dL_dphi_a, nullptr, nullptr, dL_dn0, nullptr, dL_dT0);
-    // device outputs: the cotangent goes through the scratch block
-    TRY_CUDA(cudaMemcpyAsync(c->scratch, hF.data(), sizeof(double) * c->NF, cudaMemcpyHostToDevice, c->user));
-    TRY_CUDA(cudaMemcpyAsync(c->scratch + c->NF, hG.data(), sizeof(double) * c->NF, cudaMemcpyHostToDevice, c->user));
+    launch_adj_seed((int)c->items_h.size(), c->user, c->slabs, c->items, g, c->scratch, c->scratch + c->NF, c->NF);
+    TRY_CUDA(cudaGetLastError());
+    // host outputs pass through device homes in the scratch block
+    double* tn = c->scratch + 2 * c->NF + c->NN;
+    double* tT = tn + c->NN;
+    double* on = dL_dn0 ? (on_device ? dL_dn0 : tn) : nullptr;
+    double* oT = dL_dT0 ? (on_device ? dL_dT0 : tT) : nullptr;
+    evfdlb_status s = evfdlb_adjoint_state(c, c->scratch, c->scratch + c->NF, 1, dL_dphi_a, nullptr, nullptr, on,
+                                           nullptr, oT);
+    if (s != EVFDLB_OK || on_device) return s;
+    const size_t nb = sizeof(double) * c->NN;
+    if (dL_dn0 && (s = copy_out(c, dL_dn0, tn, nb, 0)) != EVFDLB_OK) return s;
+    if (dL_dT0 && (s = copy_out(c, dL_dT0, tT, nb, 0)) != EVFDLB_OK) return s;
     TRY_CUDA(cudaStreamSynchronize(c->user));
-    return evfdlb_adjoint_state(c, c->scratch, c->scratch + c->NF, 1, dL_dphi_a, nullptr, nullptr, dL_dn0, nullptr,
-                                dL_dT0);
+    return EVFDLB_OK;
 }
 
 }  // extern "C"

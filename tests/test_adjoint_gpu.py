@@ -229,3 +229,30 @@ def test_adjoint_calibration_full_size_against_central_differences():
     for name, fd, got in checks:
         print(f"calibration {name}: central difference {fd:.9e} adjoint {got:.9e} rel {abs(got - fd) / abs(fd):.2e}")
         assert abs(got - fd) < 1e-6 * abs(fd), name
+
+
+def test_autograd_function_on_a_side_stream_matches_default_stream():
+    """EVRun passes device pointers on torch's current stream: run inside a
+    side stream, it gives bit-identical values and gradients to a run on the
+    default stream (same kernels, same order)."""
+    import torch
+    from paper_2503_15187_gb300.autograd import EVRun
+    nz, Q, dz, steps = 48, 8, 0.25, 9
+    p = ev.Params(nx=nz, dx=dz, Q=Q, ckpt_every=4)
+    n0h = 0.25 * (1 + 0.05 * np.random.default_rng(5).uniform(-1, 1, nz))
+
+    def run():
+        phi = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        T0 = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+        n0 = torch.tensor(n0h, dtype=torch.float64, device="cuda", requires_grad=True)
+        n_end = EVRun.apply(phi, T0, n0, p, steps)
+        (n_end ** 2).sum().backward()
+        torch.cuda.current_stream().synchronize()
+        return n_end.detach().cpu().numpy(), float(phi.grad), float(T0.grad), n0.grad.cpu().numpy()
+
+    ref = run()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        got = run()
+    for a, b in zip(ref, got):
+        assert np.array_equal(np.asarray(a), np.asarray(b))

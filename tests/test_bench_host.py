@@ -46,3 +46,12 @@ def test_clock_summary_reports_median_max_and_active_reasons():
     s = cs.summary()
     assert s["sm_mhz"] == 2065.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_method_flop_count_of_the_bench_slab():
+    """The method's count per node-velocity and stage, 2 (68 + 4Q): 392 at
+    Q = 32 (about 1200 per node-velocity-step over the three stages)."""
+    import bench as b
+    assert b.stage_flops_method(32) == 32 * 392
+    assert b.stage_flops_method(16) == 16 * 2 * (68 + 64)
+    assert abs(3 * b.stage_flops_method(32) / 32 - 1176) < 1e-12
