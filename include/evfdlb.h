@@ -309,7 +309,9 @@ evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* state, int64_t 
  * evfdlb_divide_fp64: q[i] = a[i] / b[i] (n >= 0 DEVICE arrays) as the
  *   kernels form FP64 quotients on the hot path (a Newton-refined reciprocal
  *   with a final residual correction, Markstein's scheme: within about one
- *   ulp, not correctly rounded; divisors outside the float exponent range use
+ *   ulp for numerators of magnitude >= 2^-920, within 2^8 ulp below, where
+ *   the residual leaves the normal range; not correctly rounded; divisors
+ *   outside the float exponent range use
  *   the IEEE quotient; a quotient that overflows, or an infinite numerator,
  *   gives NaN where IEEE gives +-inf -- both non-finite, which is what the
  *   kernels check), and, if q_ieee != NULL, the IEEE quotient beside it.

@@ -150,8 +150,11 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // residual correction (Markstein, IBM J. Res. Dev. 34, 1990): a float
 // reciprocal of b (b cut to a float by bit surgery, reciprocal to 2^-23),
 // one Newton step r <- r + r (1 - b r) (2^-46), q = a r and q <- q + r (a - b q)
-// (within about one ulp; not correctly rounded).  Divisors outside the
-// float exponent range take the IEEE quotient.
+// (within about one ulp for numerators of magnitude >= 2^-920; below that the
+// residual leaves the normal range and the error grows to at most 2^8 ulp;
+// not correctly rounded; an overflowing quotient or an infinite numerator
+// gives NaN, non-finite like the IEEE +-inf).  Divisors outside the float
+// exponent range take the IEEE quotient.
 __device__ __forceinline__ double div_nr(double a, double b) {
     const int ex = (int)((__double_as_longlong(b) >> 52) & 0x7ff);
     if (ex < 1023 - 120 || ex > 1023 + 120) return a / b;
