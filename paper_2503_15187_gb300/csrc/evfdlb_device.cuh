@@ -39,13 +39,17 @@ struct Smem {
     R *P, *S;           // analysis / synthesis tables [Q*Q] each
     R *Nr;              // n halo in R (the force convolution), aliases N for FP64
     R *Scr;             // nu and F1 in R, [2][Z]
-    R *C;               // coefficients [2][Q][Z]
+    R *C;               // coefficients [2][Q][Z] (block of 4 H Z >= 2 Q Z values)
     R *A;               // analysis [2][Q][Z]
     R *F;               // state tile with halo [2][Q][Z+6]
     R *Face;            // WENO face values [2][Q][Z+1]
     R *Cc;              // per-node coefficient constants c0..c3 [2][4][Z]
     R *Ftap;            // staged force taps [2M+1] (padded to an even count)
     R *Mm;              // Hermite moments m_l of N(u, T) per node [Q][Z]
+    R *EO;              // parity-split state tile [2][2][H][Z] (d, E/O), H = (Q+1)/2; it is
+                        // read only before the coefficients are formed, so it shares
+                        // their block; the FP64_DF kernel keeps its float-pair state
+                        // tile there instead
 };
 
 // Length of the R copy of the density halo, rounded up to an even count so
@@ -55,12 +59,18 @@ __host__ __device__ inline size_t nr_len(int Z, int M) { return ((size_t)(Z + 2 
 
 __host__ __device__ inline size_t ftap_len(int M) { return ((size_t)(2 * M + 1) + 1) & ~(size_t)1; }
 
+// Q*Q rounded up to an even count, so that the table blocks stay aligned for
+// two-wide (R2) loads.
+__host__ __device__ inline size_t qq_len(int Q) { return ((size_t)Q * Q + 1) & ~(size_t)1; }
+
 template <typename R>
 __host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
+    // the FP64 block is padded to an even count (16-byte aligned R2 tables)
     size_t nd = (size_t)(Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + (size_t)(2 * M + 1);
-    size_t nr = 2 * (size_t)Q * Q + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
-                4 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) + 2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z +
-                ftap_len(M) + (size_t)Q * Z;
+    nd = (nd + 1) & ~(size_t)1;
+    size_t nr = 2 * qq_len(Q) + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
+                4 * (size_t)((Q + 1) / 2) * Z + 2 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) +
+                2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z + ftap_len(M) + (size_t)Q * Z;
     return nd * sizeof(double) + nr * sizeof(R);
 }
 
@@ -74,18 +84,22 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     s.Chi = s.X + (Z + 4);
     s.Sc = s.Chi + (Z + 4);
     s.Mtap = s.Sc + kNumScalars * Z;
-    R* r = reinterpret_cast<R*>(s.Mtap + (2 * M + 1));
+    // Mtap holds 2m+1 <= 2M+1 taps; the FP64 block ends on an even count
+    // (the dynamic shared memory starts 16-byte aligned)
+    const size_t nd = ((size_t)(s.Mtap - base) + (2 * M + 1) + 1) & ~(size_t)1;
+    R* r = reinterpret_cast<R*>(base + nd);
     s.P = r;
-    s.S = s.P + Q * Q;
+    s.S = s.P + qq_len(Q);
     if constexpr (std::is_same<R, double>::value) {
         s.Nr = s.N;
-        s.Scr = s.S + Q * Q;
+        s.Scr = s.S + qq_len(Q);
     } else {
-        s.Nr = s.S + Q * Q;
+        s.Nr = s.S + qq_len(Q);
         s.Scr = s.Nr + nr_len(Z, M);
     }
     s.C = s.Scr + 2 * Z;
-    s.A = s.C + 2 * Q * Z;
+    s.EO = s.C;
+    s.A = s.C + 4 * ((Q + 1) / 2) * Z;
     s.F = s.A + 2 * Q * Z;
     s.Face = s.F + 2 * Q * (Z + 6);
     s.Cc = s.Face + 2 * Q * (Z + 1);
@@ -182,13 +196,25 @@ __device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b)
 // Phase 0: stage the tables, the density halo, u/T near the tile and the
 // state tile (+-3 nodes for WENO-5) into shared memory.
 // ---------------------------------------------------------------------------
-template <typename R>
+// PARITY: the parity-split tables Pp and Sp go to s.P and s.S in place of
+// the full analysis and synthesis tables.
+template <typename R, bool PARITY = false>
 __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                  const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
     const int Q = sd.Q, M = sd.M, nx = sd.nx, bc = sd.bc;
     TableLayout L(Q);
     const R* tab = rtab + sd.tab_off;
-    for (int t = threadIdx.x; t < 2 * Q * Q; t += blockDim.x) s.P[t] = tab[L.P + t];  // P then S
+    if constexpr (PARITY) {
+        const ParitySplit ps(Q);
+        const int la = ps.analysis_len(), ls = ps.synthesis_len(Q);
+        for (int t = threadIdx.x; t < la; t += blockDim.x) s.P[t] = tab[L.Pp + t];
+        for (int t = threadIdx.x; t < ls; t += blockDim.x) s.S[t] = tab[L.Sp + t];
+    } else {
+        for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
+            s.P[t] = tab[L.P + t];
+            s.S[t] = tab[L.S + t];
+        }
+    }
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
     for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {
         double n = S0[gidx(it.i0 - M + t, nx, bc)];
@@ -222,6 +248,35 @@ __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Sm
         R v = src[d * NF + sd.f_off + (long long)k * nx + i];
         s.F[(d * Q + k) * W + c] = v;
         if (Fd && c >= 3 && c < it.nz + 3) Fd[(size_t)r * Z + c - 3] = df_split((double)v);
+    }
+}
+
+// The state tile (+-3 nodes) and the parity-split interior columns
+// EO[((d * 2 + par) * H + j) * Z + t]: E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j}
+// (the middle node of an odd Q: E = h, O = 0).  Each thread loads a node
+// pair (j, Q-1-j) of one column.
+template <typename R>
+__device__ void load_state_tile_eo(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                   const R* __restrict__ src, long long NF) {
+    const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6, H = (Q + 1) / 2;
+    const int cols = it.nz + 6;
+    for (int e = threadIdx.x; e < 2 * H * cols; e += blockDim.x) {
+        const int c = e % cols, r = e / cols;
+        const int j = r % H, d = r / H, jm = Q - 1 - j;
+        const int i = gidx(it.i0 - 3 + c, nx, bc);
+        const R* row = src + d * NF + sd.f_off + i;
+        const R v = row[(long long)j * nx];
+        s.F[(d * Q + j) * W + c] = v;
+        R vm = R(0);
+        if (jm != j) {
+            vm = row[(long long)jm * nx];
+            s.F[(d * Q + jm) * W + c] = vm;
+        }
+        if (c >= 3 && c < it.nz + 3) {
+            R* eo = s.EO + ((size_t)(2 * d) * H + j) * Z + (c - 3);
+            eo[0] = (jm != j) ? v + vm : v;
+            eo[(size_t)H * Z] = (jm != j) ? v - vm : R(0);
+        }
     }
 }
 
@@ -492,6 +547,35 @@ __device__ void analysis(const SlabDesc& sd, const WorkItem& it, const Smem<R>& 
         }
         s.A[((size_t)d * Q + l0) * Z + t] = a0;
         if (two) s.A[((size_t)d * Q + l0 + 1) * Z + t] = a1;
+    }
+}
+
+// Parity-split analysis: a_l = sum_{j<H} psi_l(xi_j) (E_j or O_j), l <= Q-2,
+// two orders of one parity (l, l+2) per thread sharing each E/O value loaded
+// (Pp holds the two table values side by side: one two-wide load).
+template <typename R>
+__device__ void analysis_eo(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z, int tid, int nth) {
+    using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+    const int Q = sd.Q, nz = it.nz;
+    const ParitySplit ps(Q);
+    const int H = ps.H, G = ps.GE + ps.GO;
+    const R2* Pp = reinterpret_cast<const R2*>(s.P);
+    for (int e = tid; e < 2 * G * nz; e += nth) {
+        const int t = e % nz, r = e / nz;
+        const int g = r % G, d = r / G;
+        const int par = g < ps.GE ? 0 : 1;
+        const int l0 = par ? 4 * (g - ps.GE) + 1 : 4 * g;
+        const R* x = s.EO + ((size_t)(2 * d + par) * H) * Z + t;
+        const R2* pp = Pp + (size_t)g * H;
+        R a0 = 0, a1 = 0;
+        for (int j = 0; j < H; ++j) {
+            const R v = x[j * Z];
+            const R2 p = pp[j];
+            a0 = fma(p.x, v, a0);
+            a1 = fma(p.y, v, a1);
+        }
+        s.A[((size_t)d * Q + l0) * Z + t] = a0;
+        if (l0 + 2 <= Q - 2) s.A[((size_t)d * Q + l0 + 2) * Z + t] = a1;
     }
 }
 

@@ -39,10 +39,33 @@ enum { MOM_S0 = 0, MOM_S1, MOM_S2, MOM_S3, MOM_G0, MOM_G1 };
 // Error bits latched by the kernels.
 enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u };
 
+// Parity split of the Gauss-Hermite transforms.  The nodes are symmetric,
+// xi_{Q-1-j} = -xi_j (w likewise), and psi_l(-x) = (-1)^l psi_l(x), so with
+// E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j} (j < H = (Q+1)/2; for odd Q the
+// middle node has E = h, O = 0) the analysis is
+//   a_l = sum_{j<H} psi_l(xi_j) (l even ? E_j : O_j),
+// and a synthesis sum_l w_k psi_l(xi_k) c_l = E_k + O_k at k < H, E_k - O_k at
+// Q-1-k, with E_k, O_k its even- and odd-order parts: half the products.
+struct ParitySplit {
+    int H;        // nodes with xi <= 0
+    int GE, GO;   // analysis groups of two even / two odd orders (orders <= Q-2)
+    int GS;       // synthesis groups of two node pairs
+    EVF_HD explicit ParitySplit(int Q) {
+        H = (Q + 1) / 2;
+        const int ne = (Q - 2) / 2 + 1, no = (Q - 3) / 2 + 1;   // even / odd orders <= Q-2
+        GE = (ne + 1) / 2;
+        GO = (no + 1) / 2;
+        GS = (H + 1) / 2;
+    }
+    EVF_HD int analysis_len() const { return 2 * (GE + GO) * H; }   // Pp
+    EVF_HD int synthesis_len(int Q) const { return 2 * GS * Q; }    // Sp
+};
+
 // Offsets inside the table block of one velocity order Q (doubles).
 struct TableLayout {
-    int xi, w, P, S, rinv, rr, r1, r2, r3, total;
+    int xi, w, P, S, rinv, rr, r1, r2, r3, Pp, Sp, total;
     EVF_HD explicit TableLayout(int Q) {
+        const ParitySplit ps(Q);
         xi = 0;
         w = xi + Q;
         P = w + Q;          // P[l*Q + j] = psi_l(xi_j)          (analysis)
@@ -52,7 +75,14 @@ struct TableLayout {
         r1 = rr + Q;        // sqrt(l)
         r2 = r1 + Q;        // sqrt(l(l-1))
         r3 = r2 + Q;        // sqrt(l(l-1)(l-2))
-        total = r3 + Q;
+        // parity-split analysis pairs Pp[g][j] = (psi_l(xi_j), psi_{l+2}(xi_j)), j < H,
+        // groups g: even orders l = 4g (g < GE), then odd orders l = 4(g - GE) + 1
+        // (a missing second order is 0)
+        Pp = r3 + Q;
+        // parity-split synthesis pairs Sp[g][l] = (S[k][l], S[k+1][l]), k = 2g < H
+        // (a missing second node pair is 0)
+        Sp = Pp + ps.analysis_len();
+        total = Sp + ps.synthesis_len(Q);
     }
 };
 

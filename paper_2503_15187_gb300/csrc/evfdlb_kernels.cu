@@ -63,15 +63,19 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
              const R* __restrict__ src, const R* base, R* out, double* rhs_out,
              const double* __restrict__ mom_in, double* __restrict__ mom_out,
              long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     Smem<R> s = carve<R>(smem, Q, Z, sd.M);
 
-    float2* Fd = DF ? reinterpret_cast<float2*>(s.Mm + (size_t)Q * Z) : nullptr;
-    load_node_inputs<R>(sd, it, s, Z, rtab, mom_in, NN);
-    load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
+    // FP64 / FP32: parity-split tables and state tile (half the transform
+    // products); FP64_DF: the full tables as float pairs and the state tile
+    // split into float pairs in the EO block
+    float2* Fd = DF ? reinterpret_cast<float2*>(s.EO) : nullptr;
+    load_node_inputs<R, !DF>(sd, it, s, Z, rtab, mom_in, NN);
+    if constexpr (DF) load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
+    else load_state_tile_eo<R>(sd, it, s, Z, src, NF);
     // the slab's force and Fischer-Methfessel taps, read in warp 0's serial
     // tap loops, staged once into shared memory
     for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.Ftap[j] = rtaps[sd.tap_off + j];
@@ -96,7 +100,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         if constexpr (DF) {
             analysis_df(sd, it, s, Fd, reinterpret_cast<const float2*>(s.P), Z, tid, nth);
         } else {
-            analysis<R>(sd, it, s, Z, tid, nth);
+            analysis_eo<R>(sd, it, s, Z, tid, nth);
         }
         if constexpr (DF) faces_df(sd, it, s, Z, tables, tid, nth);
         else faces<R>(sd, it, s, Z, vtab, tid, nth);
@@ -105,21 +109,40 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
     __syncthreads();
 
-    // Phase 5: synthesis, advection, relaxation and the RK stage; the VK
-    // velocities of a thread share every coefficient loaded.
+    // Phase 5: synthesis, advection, relaxation and the RK stage.
     const R* xi = rt + L.xi;
     const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
     const bool rhs_form = (mode == 1), with_base = (alpha != 0.0);
-    // velocities per thread: two in FP64/FP32, four in DF (four independent
-    // Dot2 chains hide the FP32 latency)
-    constexpr int VK = DF ? 4 : 2;
-    const int nkg = (Q + VK - 1) / VK;
-    for (int e = threadIdx.x; e < 2 * nkg * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int k0 = VK * (r % nkg), d = r / nkg;
-        const int nk = min(VK, Q - k0);
-        R syn[VK];
-        if constexpr (DF) {
+    // R at velocity k of node t of distribution d (h: the state there)
+    auto rhs_at = [&](int d, int t, int k, R h, R syn) {
+        const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
+        return fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
+    };
+    // output of velocity k of node t: the RHS form or the RK stage (the two
+    // forms under one uniform branch, so that the RK form issues no FP64
+    // conversion of the right-hand-side form)
+    auto emit = [&](int d, int t, int k, R syn) {
+        R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
+        const R h = *hp;
+        const long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
+        if (rhs_form) {
+            rhs_out[g] = (double)rhs_at(d, t, k, h, syn);
+        } else {
+            R o = rbeta * fma(dt, rhs_at(d, t, k, h, syn), h);
+            if (with_base) o = fma(ralpha, base[g], o);
+            out[g] = o;
+            *hp = o;
+        }
+    };
+    if constexpr (DF) {
+        // four velocities per thread (four independent Dot2 chains hide the
+        // FP32 latency)
+        constexpr int VK = 4;
+        const int nkg = (Q + VK - 1) / VK;
+        for (int e = threadIdx.x; e < 2 * nkg * nz; e += blockDim.x) {
+            int t = e % nz, r = e / nz;
+            int k0 = VK * (r % nkg), d = r / nkg;
+            const int nk = min(VK, Q - k0);
             const float2* Sd = reinterpret_cast<const float2*>(s.S);
             const float2* c = reinterpret_cast<const float2*>(s.C) + (size_t)d * Q * Z + t;
             float a[VK], b[VK];
@@ -131,44 +154,43 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
                 for (int q = 0; q < VK; ++q) dot2_acc(a[q], b[q], Sd[min(k0 + q, Q - 1) * Q + l], cl);
             }
 #pragma unroll
-            for (int q = 0; q < VK; ++q) syn[q] = df_join(a[q], b[q]);
-        } else {
-            const R* c = s.C + (size_t)d * Q * Z + t;
-#pragma unroll
-            for (int q = 0; q < VK; ++q) syn[q] = 0;
-            for (int l = 0; l < Q; ++l) {
-                R cl = c[l * Z];
-#pragma unroll
-                for (int q = 0; q < VK; ++q) syn[q] = fma(s.S[min(k0 + q, Q - 1) * Q + l], cl, syn[q]);
-            }
+            for (int q = 0; q < VK; ++q)
+                if (q < nk) emit(d, t, k0 + q, df_join(a[q], b[q]));
         }
-        // R at velocity k of this node (h: the state there)
-        auto rhs_at = [&](int q, int k, R h) {
-            const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
-            return fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn[q]));
-        };
-        // the two output forms in separate loops under one uniform branch, so
-        // that the RK form issues no FP64 conversion of the right-hand-side form
-        if (rhs_form) {
-#pragma unroll
-            for (int q = 0; q < VK; ++q) {
-                if (q >= nk) break;
-                const int k = k0 + q;
-                const R h = s.F[(size_t)(d * Q + k) * W + t + 3];
-                rhs_out[d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t] = (double)rhs_at(q, k, h);
+    } else {
+        // parity split: two node pairs (k, Q-1-k), (k+1, Q-2-k) per thread,
+        // k = 2g; even orders build E, odd orders O; the synthesis is E + O at
+        // k and E - O at Q-1-k (one product per table value and order)
+        using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+        const ParitySplit ps(Q);
+        const int H = ps.H, GS = ps.GS;
+        const R2* Sp = reinterpret_cast<const R2*>(s.S);
+        for (int e = threadIdx.x; e < 2 * GS * nz; e += blockDim.x) {
+            const int t = e % nz, r = e / nz;
+            const int g = r % GS, d = r / GS, k0 = 2 * g;
+            const R* c = s.C + (size_t)d * Q * Z + t;
+            const R2* sp = Sp + (size_t)g * Q;
+            R e0 = 0, o0 = 0, e1 = 0, o1 = 0;
+            int l = 0;
+            for (; l + 1 < Q; l += 2) {
+                const R c0 = c[l * Z], c1 = c[(l + 1) * Z];
+                const R2 sa = sp[l], sb = sp[l + 1];
+                e0 = fma(sa.x, c0, e0);
+                e1 = fma(sa.y, c0, e1);
+                o0 = fma(sb.x, c1, o0);
+                o1 = fma(sb.y, c1, o1);
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < VK; ++q) {
-                if (q >= nk) break;
-                const int k = k0 + q;
-                R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
-                const R h = *hp;
-                const long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
-                R o = rbeta * fma(dt, rhs_at(q, k, h), h);
-                if (with_base) o = fma(ralpha, base[g], o);
-                out[g] = o;
-                *hp = o;
+            if (l < Q) {                                  // odd Q: the last (even) order
+                const R c0 = c[l * Z];
+                const R2 sa = sp[l];
+                e0 = fma(sa.x, c0, e0);
+                e1 = fma(sa.y, c0, e1);
+            }
+            emit(d, t, k0, e0 + o0);
+            if (Q - 1 - k0 != k0) emit(d, t, Q - 1 - k0, e0 - o0);
+            if (k0 + 1 < H) {
+                emit(d, t, k0 + 1, e1 + o1);
+                if (Q - 2 - k0 != k0 + 1) emit(d, t, Q - 2 - k0, e1 - o1);
             }
         }
     }
@@ -188,7 +210,7 @@ init_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ ite
             const double* __restrict__ tables, const R* __restrict__ rtab, const double* __restrict__ n0,
             const double* __restrict__ u0, const double* __restrict__ T0, R* state,
             double* mom, long long NF, long long NN, int Z, unsigned* err) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
@@ -241,7 +263,7 @@ __global__ void __launch_bounds__(kThreads)
 iso_reset_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
                  const double* __restrict__ tables, const R* __restrict__ rtab, R* state, double* mom, long long NF,
                  long long NN, int Z) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     if (!(sd.T_iso > 0.0)) return;
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(kThreads)
 fields_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
               const R* __restrict__ rtab, const double* __restrict__ taps, const R* __restrict__ rtaps,
               const double* __restrict__ mom, double* fields, long long NN, int Z, unsigned* err) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     Smem<R> s = carve<R>(smem, sd.Q, Z, sd.M);
@@ -457,8 +479,9 @@ size_t stage_smem_bytes_p(int prec, int Q, int Z, int M) {
     return prec == EVFDLB_FP32 ? smem_bytes_t<float>(Q, Z, M) : smem_bytes_t<double>(Q, Z, M);
 }
 
-// The FP64_DF stage adds the split state tile, 2 Q Z pairs.
-size_t stage_smem_bytes_df(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M) + 16 * (size_t)Q * Z; }
+// The FP64_DF stage keeps its split state tile (2 Q Z float pairs) in the EO
+// block (4 H Z >= 2 Q Z doubles).
+size_t stage_smem_bytes_df(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M); }
 
 cudaError_t configure_df(size_t smem_bytes) {
     return cudaFuncSetAttribute(stage_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

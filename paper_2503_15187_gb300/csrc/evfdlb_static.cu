@@ -49,7 +49,7 @@ constexpr long long kMaxElems = EVFDLB_STATIC_MAX_ELEMENTS;  // Q * nx
 constexpr int kMaxNodes = EVFDLB_STATIC_MAX_NODES;           // nx
 constexpr int kMaxHalfWidth = EVFDLB_STATIC_MAX_HALFWIDTH;   // force tap half-width
 constexpr int kMaxTaps = 3 * (2 * kMaxHalfWidth + 1);         // force, FM (m <= M), energy
-constexpr int kTableDoubles = 7 * kQMax + 2 * kQMax * kQMax; // TableLayout(32).total
+constexpr int kTableDoubles = 7 * kQMax + 4 * kQMax * kQMax; // >= TableLayout(Q).total, Q <= 32
 constexpr int kDescDoubles = (sizeof(SlabDesc) + 7) / 8;
 constexpr int kItemDoubles = (sizeof(WorkItem) + 7) / 8;
 

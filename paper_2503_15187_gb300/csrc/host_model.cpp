@@ -67,6 +67,17 @@ bool velocity_set(int Q, double* xi, double* w) {
         xi[k] = (double)x;
         w[k] = (double)(1.0L / ((long double)Q * psi[Q - 1] * psi[Q - 1]));
     }
+    // He_Q has the parity of Q: its roots are symmetric about 0.  Make the
+    // stored set exactly so (xi_{Q-1-k} = -xi_k, w_{Q-1-k} = w_k, a zero node
+    // for odd Q), which the parity-split transforms rely on.
+    for (int k = 0; k < Q / 2; ++k) {
+        const long double a = 0.5L * ((long double)xi[Q - 1 - k] - (long double)xi[k]);
+        const long double b = 0.5L * ((long double)w[Q - 1 - k] + (long double)w[k]);
+        xi[k] = (double)(-a);
+        xi[Q - 1 - k] = (double)a;
+        w[k] = w[Q - 1 - k] = (double)b;
+    }
+    if (Q & 1) xi[Q / 2] = 0.0;
     return true;
 }
 
@@ -83,6 +94,21 @@ void build_tables(int Q, const double* xi, const double* w, double* out) {
             out[L.S + k * Q + l] = (double)((long double)w[k] * psi[l]);
         }
     }
+    // parity-split tables (the nodes are symmetric: see velocity_set)
+    const ParitySplit ps(Q);
+    for (int g = 0; g < ps.GE + ps.GO; ++g) {
+        const int l = (g < ps.GE) ? 4 * g : 4 * (g - ps.GE) + 1;
+        for (int j = 0; j < ps.H; ++j) {
+            out[L.Pp + 2 * (g * ps.H + j)] = (l <= Q - 2) ? out[L.P + l * Q + j] : 0.0;
+            out[L.Pp + 2 * (g * ps.H + j) + 1] = (l + 2 <= Q - 2) ? out[L.P + (l + 2) * Q + j] : 0.0;
+        }
+    }
+    for (int g = 0; g < ps.GS; ++g)
+        for (int l = 0; l < Q; ++l) {
+            const int k = 2 * g;
+            out[L.Sp + 2 * (g * Q + l)] = out[L.S + k * Q + l];
+            out[L.Sp + 2 * (g * Q + l) + 1] = (k + 1 < ps.H) ? out[L.S + (k + 1) * Q + l] : 0.0;
+        }
     for (int l = 0; l < Q; ++l) {
         long double ll = l;
         out[L.rinv + l] = (double)(1.0L / sqrtl(ll + 1));

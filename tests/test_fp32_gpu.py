@@ -36,6 +36,7 @@ CASES = {
     "outflow_q32_slab": (150, 32, 0.1, 1, "slab", None),
     "periodic_q16_noise": (64, 16, 0.25, 0, "noise", 7),
     "outflow_q24_slab_ragged": (97, 24, 0.25, 1, "slab", 13),
+    "periodic_q15_odd": (55, 15, 0.25, 0, "noise", 9),
 }
 
 

@@ -5,7 +5,7 @@ Error measure (per distribution F, G): ||GPU - oracle||_inf / ||oracle||_inf.
 Bars: 1e-12 per step (state), 1e-11 for a single right-hand side (which can
 be small against its terms), 1e-8 on end-of-run moments.  Cases span tiles
 of several sizes with a ragged last tile, both boundary rules, both
-relaxation readings and Q = 8..32.
+relaxation readings and Q = 8..32, odd orders included.
 """
 import numpy as np
 import pytest
@@ -29,6 +29,9 @@ CASES = {
     "outflow_q32_dz01": (150, 32, 0.1, 1, 0, "slab", 27),
     "periodic_q8_chi_over_tau": (50, 8, 0.25, 0, 1, "noise", 64),
     "periodic_q12_short": (16, 12, 0.25, 0, 0, "noise", 5),
+    # odd orders: a zero velocity node, the middle of the parity split
+    "periodic_q9_odd": (40, 9, 0.25, 0, 0, "noise", 6),
+    "outflow_q31_odd": (77, 31, 0.25, 1, 0, "slab", 11),
 }
 
 
