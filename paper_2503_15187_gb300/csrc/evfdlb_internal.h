@@ -19,16 +19,14 @@ namespace evfdlb {
 constexpr int kQMax = 32;          // largest Gauss-Hermite order of a slab
 constexpr int kZMax = 64;          // largest node tile of one CTA
 constexpr int kThreads = 256;      // threads of the per-tile kernels
-// Threads of the RK-stage kernel (warp 0 forms the node work): the FP32
-// variant's per-velocity work is cheap and latency-bound, so it runs 16
-// warps per tile; the FP64 kernel is FP64-pipe-bound and runs 12 when its
-// grid is one wave (one CTA per SM), else kStageThreadsWaves = 8, so that two
-// CTAs of ~110 registers share an SM; the FP64_DF kernel runs 8 so that
-// three CTAs per SM keep 80 registers.
-template <typename R, bool DF = false> struct StageThreads { static constexpr int value = 384; };
-template <> struct StageThreads<double, true> { static constexpr int value = 256; };
+// Threads of the RK-stage kernel (warp 0 forms the node work).  The FP64 pipe
+// of this part accepts one warp instruction per scheduler every 64 cycles
+// whatever the number of active lanes, so the FP64 kernels run 8 warps (two
+// worker warps beside the node warp per scheduler, and two CTAs of at most
+// 128 registers per SM when the work list spans several waves); the FP32
+// variant's per-velocity work is cheap and latency-bound, so it runs 16.
+template <typename R, bool DF = false> struct StageThreads { static constexpr int value = 256; };
 template <> struct StageThreads<float, false> { static constexpr int value = 512; };
-constexpr int kStageThreadsWaves = 256;
 constexpr int kNumMoments = 6;     // raw moment sums kept per node
 constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
 
@@ -49,16 +47,16 @@ enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u };
 struct ParitySplit {
     int H;        // nodes with xi <= 0
     int GE, GO;   // analysis groups of two even / two odd orders (orders <= Q-2)
-    int GS;       // synthesis groups of two node pairs
+    int QE;       // Q rounded up to even: the synthesis row length
     EVF_HD explicit ParitySplit(int Q) {
         H = (Q + 1) / 2;
         const int ne = (Q - 2) / 2 + 1, no = (Q - 3) / 2 + 1;   // even / odd orders <= Q-2
         GE = (ne + 1) / 2;
         GO = (no + 1) / 2;
-        GS = (H + 1) / 2;
+        QE = Q + (Q & 1);
     }
     EVF_HD int analysis_len() const { return 2 * (GE + GO) * H; }   // Pp
-    EVF_HD int synthesis_len(int Q) const { return 2 * GS * Q; }    // Sp
+    EVF_HD int synthesis_len() const { return H * QE; }             // Sp
 };
 
 // Offsets inside the table block of one velocity order Q (doubles).
@@ -79,10 +77,10 @@ struct TableLayout {
         // groups g: even orders l = 4g (g < GE), then odd orders l = 4(g - GE) + 1
         // (a missing second order is 0)
         Pp = r3 + Q;
-        // parity-split synthesis pairs Sp[g][l] = (S[k][l], S[k+1][l]), k = 2g < H
-        // (a missing second node pair is 0)
+        // parity-split synthesis rows Sp[k][l] = S[k][l], k < H, rows padded to
+        // an even length QE with zeros (orders l, l+1 in one two-wide load)
         Sp = Pp + ps.analysis_len();
-        total = Sp + ps.synthesis_len(Q);
+        total = Sp + ps.synthesis_len();
     }
 };
 

@@ -38,7 +38,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <atomic>
 #include <type_traits>
 
 #include "evfdlb_device.cuh"
@@ -56,7 +55,7 @@ namespace evfdlb {
 // pairs on the FP32 pipe (state tile split into pairs once per stage in a
 // block after the Hermite moments), everything else as in the FP64 kernel.
 template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
-__global__ void __launch_bounds__(T, DF ? 3 : 1)
+__global__ void __launch_bounds__(T, DF ? 3 : (std::is_same<R, double>::value ? 2 : 1))
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
@@ -113,23 +112,27 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     const R* xi = rt + L.xi;
     const R dt = (R)sd.dt, inv_dx = (R)sd.inv_dx, ralpha = (R)alpha, rbeta = (R)beta;
     const bool rhs_form = (mode == 1), with_base = (alpha != 0.0);
-    // R at velocity k of node t of distribution d (h: the state there)
-    auto rhs_at = [&](int d, int t, int k, R h, R syn) {
-        const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
-        return fma(-xi[k] * inv_dx, fc[t + 1] - fc[t], fma(-s.Scr[t], h, syn));
-    };
-    // output of velocity k of node t: the RHS form or the RK stage (the two
-    // forms under one uniform branch, so that the RK form issues no FP64
-    // conversion of the right-hand-side form)
-    auto emit = [&](int d, int t, int k, R syn) {
+    // The stage out = alpha base + beta (h + dt R) with
+    // R = -xi_k/dx (f_{t+1/2} - f_{t-1/2}) - nu h + syn is formed as
+    // fma(cx_k, df, fma(cs, syn, fma(ch, h, alpha base))): cs = beta dt,
+    // ch = beta (1 - dt nu) per node, cx_k = -beta dt xi_k / dx.
+    const R cs = rbeta * dt, csx = -cs * inv_dx;
+    // output of velocity k of node t of distribution d; the two output forms
+    // under one uniform branch, so that the RK form issues no FP64
+    // conversion of the right-hand-side form
+    auto emit = [&](int d, int t, int k, R syn, R ch, R cx) {
         R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
         const R h = *hp;
+        const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
+        const R df = fc[t + 1] - fc[t];
         const long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
         if (rhs_form) {
-            rhs_out[g] = (double)rhs_at(d, t, k, h, syn);
+            rhs_out[g] = (double)fma(-xi[k] * inv_dx, df, fma(-s.Scr[t], h, syn));
         } else {
-            R o = rbeta * fma(dt, rhs_at(d, t, k, h, syn), h);
-            if (with_base) o = fma(ralpha, base[g], o);
+            R o = with_base ? ralpha * base[g] : R(0);
+            o = fma(ch, h, o);
+            o = fma(cs, syn, o);
+            o = fma(cx, df, o);
             out[g] = o;
             *hp = o;
         }
@@ -153,45 +156,35 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
 #pragma unroll
                 for (int q = 0; q < VK; ++q) dot2_acc(a[q], b[q], Sd[min(k0 + q, Q - 1) * Q + l], cl);
             }
+            const R ch = fma(-cs, s.Scr[t], rbeta);
 #pragma unroll
             for (int q = 0; q < VK; ++q)
-                if (q < nk) emit(d, t, k0 + q, df_join(a[q], b[q]));
+                if (q < nk) emit(d, t, k0 + q, df_join(a[q], b[q]), ch, csx * xi[k0 + q]);
         }
     } else {
-        // parity split: two node pairs (k, Q-1-k), (k+1, Q-2-k) per thread,
-        // k = 2g; even orders build E, odd orders O; the synthesis is E + O at
-        // k and E - O at Q-1-k (one product per table value and order)
+        // parity split: one node pair (k, Q-1-k) per task; even orders build
+        // E, odd orders O (one two-wide table load per two orders); the
+        // synthesis is E + O at k and E - O at Q-1-k
         using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
         const ParitySplit ps(Q);
-        const int H = ps.H, GS = ps.GS;
+        const int H = ps.H, QE2 = ps.QE / 2;
         const R2* Sp = reinterpret_cast<const R2*>(s.S);
-        for (int e = threadIdx.x; e < 2 * GS * nz; e += blockDim.x) {
+        for (int e = threadIdx.x; e < 2 * H * nz; e += blockDim.x) {
             const int t = e % nz, r = e / nz;
-            const int g = r % GS, d = r / GS, k0 = 2 * g;
+            const int k = r % H, d = r / H;
             const R* c = s.C + (size_t)d * Q * Z + t;
-            const R2* sp = Sp + (size_t)g * Q;
-            R e0 = 0, o0 = 0, e1 = 0, o1 = 0;
+            const R2* sp = Sp + (size_t)k * QE2;
+            R ev = 0, od = 0;
             int l = 0;
             for (; l + 1 < Q; l += 2) {
-                const R c0 = c[l * Z], c1 = c[(l + 1) * Z];
-                const R2 sa = sp[l], sb = sp[l + 1];
-                e0 = fma(sa.x, c0, e0);
-                e1 = fma(sa.y, c0, e1);
-                o0 = fma(sb.x, c1, o0);
-                o1 = fma(sb.y, c1, o1);
+                const R2 sv = sp[l >> 1];
+                ev = fma(sv.x, c[l * Z], ev);
+                od = fma(sv.y, c[(l + 1) * Z], od);
             }
-            if (l < Q) {                                  // odd Q: the last (even) order
-                const R c0 = c[l * Z];
-                const R2 sa = sp[l];
-                e0 = fma(sa.x, c0, e0);
-                e1 = fma(sa.y, c0, e1);
-            }
-            emit(d, t, k0, e0 + o0);
-            if (Q - 1 - k0 != k0) emit(d, t, Q - 1 - k0, e0 - o0);
-            if (k0 + 1 < H) {
-                emit(d, t, k0 + 1, e1 + o1);
-                if (Q - 2 - k0 != k0 + 1) emit(d, t, Q - 2 - k0, e1 - o1);
-            }
+            if (l < Q) ev = fma(sp[l >> 1].x, c[l * Z], ev);   // odd Q: the last (even) order
+            const R ch = fma(-cs, s.Scr[t], rbeta), cx = csx * xi[k];
+            emit(d, t, k, ev + od, ch, cx);
+            if (Q - 1 - k != k) emit(d, t, Q - 1 - k, ev - od, ch, -cx);
         }
     }
     if (mode == 1) return;
@@ -502,11 +495,6 @@ template <typename R>
 static cudaError_t configure_t(size_t smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
-    if constexpr (std::is_same<R, double>::value) {
-        e = cudaFuncSetAttribute(stage_kernel<double, false, kStageThreadsWaves>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
     e = cudaFuncSetAttribute(init_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(iso_reset_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -523,8 +511,7 @@ cudaError_t configure_kernels(size_t smem_bytes) { return configure_t<double>(sm
 // Raises (never lowers) the dynamic shared-memory limit of the FP64 stage and
 // isothermal-reset kernels on the current device to at least smem_bytes.
 cudaError_t ensure_stage_smem(size_t smem_bytes) {
-    const void* fns[3] = {(const void*)stage_kernel<double>, (const void*)stage_kernel<double, false, kStageThreadsWaves>,
-                          (const void*)iso_reset_kernel<double>};
+    const void* fns[2] = {(const void*)stage_kernel<double>, (const void*)iso_reset_kernel<double>};
     for (const void* f : fns) {
         cudaFuncAttributes a;
         cudaError_t e = cudaFuncGetAttributes(&a, f);
@@ -536,40 +523,18 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
     return cudaSuccess;
 }
 
-// Multiprocessors of the current device (cached per device; contexts on
-// different host threads may launch concurrently).
-static int device_sms() {
-    static std::atomic<int> cache[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    const bool cached = dev >= 0 && dev < 64;
-    if (cached) {
-        const int v = cache[dev].load(std::memory_order_relaxed);
-        if (v > 0) return v;
-    }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-    if (cached) cache[dev].store(sms, std::memory_order_relaxed);
-    return sms;
-}
-
-// The FP64 stage at 12 warps when the work list is one wave, at 8 warps
-// (two CTAs per SM) when it is several or when `beside` says that other
-// kernels share the SMs.
+// The FP64 stage (8 warps; see StageThreads).  `beside`: the launch runs
+// concurrently with kernels on another stream (the adjoint's segment
+// recompute beside the reverse sweep); the form is the same.
 static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                               const WorkItem* items, const double* tables, const double* rtab, const double* taps,
                               const double* rtaps, const double* src, const double* base, double* out,
                               double* rhs_out, const double* mom_in, double* mom_out, long long NF, long long NN,
                               double alpha, double beta, int mode, int Z, unsigned* err, bool beside = false) {
-    if (!beside && nitems <= device_sms())
-        stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
-            slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
-            mode, Z, err);
-    else
-        stage_kernel<double, false, kStageThreadsWaves><<<nitems, kStageThreadsWaves, smem, st>>>(
-            slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
-            mode, Z, err);
+    (void)beside;
+    stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
+        slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode,
+        Z, err);
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,

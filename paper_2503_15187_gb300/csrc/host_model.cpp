@@ -103,12 +103,8 @@ void build_tables(int Q, const double* xi, const double* w, double* out) {
             out[L.Pp + 2 * (g * ps.H + j) + 1] = (l + 2 <= Q - 2) ? out[L.P + (l + 2) * Q + j] : 0.0;
         }
     }
-    for (int g = 0; g < ps.GS; ++g)
-        for (int l = 0; l < Q; ++l) {
-            const int k = 2 * g;
-            out[L.Sp + 2 * (g * Q + l)] = out[L.S + k * Q + l];
-            out[L.Sp + 2 * (g * Q + l) + 1] = (k + 1 < ps.H) ? out[L.S + (k + 1) * Q + l] : 0.0;
-        }
+    for (int k = 0; k < ps.H; ++k)
+        for (int l = 0; l < ps.QE; ++l) out[L.Sp + k * ps.QE + l] = (l < Q) ? out[L.S + k * Q + l] : 0.0;
     for (int l = 0; l < Q; ++l) {
         long double ll = l;
         out[L.rinv + l] = (double)(1.0L / sqrtl(ll + 1));
