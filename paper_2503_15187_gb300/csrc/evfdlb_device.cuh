@@ -46,6 +46,8 @@ struct Smem {
     R *Cc;              // per-node coefficient constants c0..c3 [2][4][Z]
     R *Ftap;            // staged force taps [2M+1] (padded to an even count)
     R *Mm;              // Hermite moments m_l of N(u, T) per node [Q][Z]
+    double *Vp;         // velocity powers of the moment sums: xi, xi^2, xi^3 (FP64) [3Q]
+    R *Vr;              //   and xi, xi^3 in R [2Q]
     R *EO;              // parity-split state tile [2][2][H][Z] (d, E/O), H = (Q+1)/2; it is
                         // read only before the coefficients are formed, so it shares
                         // their block; the FP64_DF kernel keeps its float-pair state
@@ -71,7 +73,8 @@ __host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
     size_t nr = 2 * qq_len(Q) + (std::is_same<R, double>::value ? 0 : nr_len(Z, M)) + 2 * (size_t)Z +
                 4 * (size_t)((Q + 1) / 2) * Z + 2 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) +
                 2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z + ftap_len(M) + (size_t)Q * Z;
-    return nd * sizeof(double) + nr * sizeof(R);
+    // + the velocity powers (3Q doubles, 2Q R) and one R of padding before them
+    return (nd + 3 * (size_t)Q) * sizeof(double) + (nr + 2 * (size_t)Q + 1) * sizeof(R);
 }
 
 template <typename R>
@@ -105,6 +108,10 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     s.Cc = s.Face + 2 * Q * (Z + 1);
     s.Ftap = s.Cc + 8 * Z;
     s.Mm = s.Ftap + ftap_len(M);
+    // the velocity powers close the layout: FP64 first (the R block ends on
+    // an even count of doubles' worth: all its segment lengths are even)
+    s.Vp = reinterpret_cast<double*>(s.Mm + (size_t)Q * Z + ((size_t)Q * Z) % 2);
+    s.Vr = reinterpret_cast<R*>(s.Vp + 3 * Q);
     return s;
 }
 
@@ -221,7 +228,9 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     if constexpr (PARITY) {
         const ParitySplit ps(Q);
         const int la = ps.analysis_len(), ls = ps.synthesis_len();
+#pragma unroll 4
         for (int t = threadIdx.x; t < la; t += blockDim.x) s.P[t] = tab[L.Pp + t];
+#pragma unroll 4
         for (int t = threadIdx.x; t < ls; t += blockDim.x) s.S[t] = tab[L.Sp + t];
     } else {
         for (int t = threadIdx.x; t < Q * Q; t += blockDim.x) {
@@ -230,6 +239,7 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
         }
     }
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
+#pragma unroll 2
     for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {
         double n = S0[gidx(it.i0 - M + t, nx, bc)];
         s.N[t] = n;
@@ -274,6 +284,7 @@ __device__ void load_state_tile_eo(const SlabDesc& sd, const WorkItem& it, const
                                    const R* __restrict__ src, long long NF) {
     const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6, H = (Q + 1) / 2;
     const int cols = it.nz + 6;
+#pragma unroll 4
     for (int e = threadIdx.x; e < 2 * H * cols; e += blockDim.x) {
         const int c = e % cols, r = e / cols;
         const int j = r % H, d = r / H, jm = Q - 1 - j;
@@ -292,6 +303,23 @@ __device__ void load_state_tile_eo(const SlabDesc& sd, const WorkItem& it, const
             eo[(size_t)H * Z] = (jm != j) ? v - vm : R(0);
         }
     }
+}
+
+// sum_{|j| <= m} tap[j + m] x[j] in four interleaved partial sums: a quarter
+// of the dependent chain (an FP64 operation waits for the whole warp to pass
+// the FP64 pipe of its scheduler, tens of cycles on this part).
+template <typename R, typename T>
+__device__ __forceinline__ R tap_sum(const T* __restrict__ tap, const R* x, int m) {
+    R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int j = -m;
+    for (; j + 3 <= m; j += 4) {
+        a0 = fma((R)tap[j + m], x[j], a0);
+        a1 = fma((R)tap[j + 1 + m], x[j + 1], a1);
+        a2 = fma((R)tap[j + 2 + m], x[j + 2], a2);
+        a3 = fma((R)tap[j + 3 + m], x[j + 3], a3);
+    }
+    for (; j <= m; ++j) a0 = fma((R)tap[j + m], x[j], a0);
+    return (a0 + a1) + (a2 + a3);
 }
 
 // ---------------------------------------------------------------------------
@@ -315,8 +343,7 @@ __device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const 
         int pos = it.i0 - 2 + t;
         int shift = (sd.bc == EVFDLB_BC_OUTFLOW) ? gidx(pos, sd.nx, sd.bc) - pos : 0;
         const double* nn = s.N + (t - 2 + M + shift);
-        double nb = 0.0;
-        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], nn[j], nb);
+        const double nb = tap_sum<double>(mtap, nn, m);
         double eta = sd.eta_coef * nb, om = 1.0 - eta;
         double chi = div_nr(2.0 - eta, 2.0 * om * om * om);
         double n = nn[0];
@@ -356,8 +383,7 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         double A, B;
         // self-consistent force, Eq. (F1), Simpson taps over |j| <= M
         const R* nn = s.Nr + (t + M);
-        R f1r = 0;
-        for (int j = -M; j <= M; ++j) f1r = fma(ftap[j + M], nn[j], f1r);
+        const R f1r = tap_sum<R>(ftap, nn, M);
         double f1;
         if constexpr (std::is_same<R, float>::value) f1 = f2d_bits(f1r);
         else f1 = (double)f1r;
@@ -877,14 +903,34 @@ __device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long 
     const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
     if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
         which == MOM_G0) {
-        double acc = 0.0;
+        // four partial sums (a quarter of the FP64 dependent chain); a float
+        // state is widened by bit surgery (exact for normal floats; no FP64
+        // conversion instruction)
+        auto wide = [](R v) -> double {
+            if constexpr (std::is_same<R, float>::value) return f2d_bits(v);
+            else return v;
+        };
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = 0;
         if (p == 0) {
-            for (int k = 0; k < Q; ++k) acc += (double)h[k * stride];
+            for (; k + 3 < Q; k += 4) {
+                a0 += wide(h[k * stride]);
+                a1 += wide(h[(k + 1) * stride]);
+                a2 += wide(h[(k + 2) * stride]);
+                a3 += wide(h[(k + 3) * stride]);
+            }
+            for (; k < Q; ++k) a0 += wide(h[k * stride]);
         } else {
             const double* w = xp + (p - 1) * Q;
-            for (int k = 0; k < Q; ++k) acc = fma(w[k], (double)h[k * stride], acc);
+            for (; k + 3 < Q; k += 4) {
+                a0 = fma(w[k], wide(h[k * stride]), a0);
+                a1 = fma(w[k + 1], wide(h[(k + 1) * stride]), a1);
+                a2 = fma(w[k + 2], wide(h[(k + 2) * stride]), a2);
+                a3 = fma(w[k + 3], wide(h[(k + 3) * stride]), a3);
+            }
+            for (; k < Q; ++k) a0 = fma(w[k], wide(h[k * stride]), a0);
         }
-        return acc;
+        return (a0 + a1) + (a2 + a3);
     }
     const R* w = xr + (p == 1 ? 0 : Q);
     R racc = 0;
@@ -907,24 +953,33 @@ __device__ __forceinline__ void velocity_powers(int Q, const double* __restrict_
     }
 }
 
-// Raw moment sums of the tile held in s.F (columns 3 .. nz+2).  Called by
-// all threads once the tile's velocity work is done: the velocity powers
-// are staged in the (then free) table block s.P / s.S (5 Q values).
+// Raw moment sums of the tile held in s.F (columns 3 .. nz+2), from velocity
+// powers staged in shared memory (xp = [xi, xi^2, xi^3] FP64, xr = [xi, xi^3]
+// in R).  Called by all threads once the tile's velocity work is done.
 template <typename R>
-__device__ void tile_moment_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                 const double* __restrict__ xi, const R* __restrict__ rxi,
-                                 double* __restrict__ mom_out, long long NN) {
+__device__ void tile_moment_sums_staged(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                        const double* xp, const R* xr, double* __restrict__ mom_out, long long NN) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
-    double* xp = reinterpret_cast<double*>(s.P);
-    R* xr = reinterpret_cast<R*>(xp + 3 * Q);
-    velocity_powers<R>(Q, xi, rxi, xp, xr, threadIdx.x, blockDim.x);
-    __syncthreads();
     for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
         int t = e % nz, which = e / nz;
         int d = which >= MOM_G0 ? 1 : 0;
         const R* h = s.F + (size_t)d * Q * W + t + 3;
         mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xp, xr);
     }
+}
+
+// The same with the velocity powers formed here first, in the (then free)
+// table block s.P / s.S (5 Q values).
+template <typename R>
+__device__ void tile_moment_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                 const double* __restrict__ xi, const R* __restrict__ rxi,
+                                 double* __restrict__ mom_out, long long NN) {
+    const int Q = sd.Q;
+    double* xp = reinterpret_cast<double*>(s.P);
+    R* xr = reinterpret_cast<R*>(xp + 3 * Q);
+    velocity_powers<R>(Q, xi, rxi, xp, xr, threadIdx.x, blockDim.x);
+    __syncthreads();
+    tile_moment_sums_staged<R>(sd, it, s, Z, xp, xr, mom_out, NN);
 }
 
 }  // namespace evfdlb

@@ -79,8 +79,14 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     // tap loops, staged once into shared memory
     for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.Ftap[j] = rtaps[sd.tap_off + j];
     for (int j = threadIdx.x; j < 2 * sd.m + 1; j += blockDim.x) s.Mtap[j] = taps[sd.tap_off + 2 * sd.M + 1 + j];
+    // velocity powers of the closing moment sums, formed once per CTA
+    {
+        const R* vt = DF ? reinterpret_cast<const R*>(tables) : rtab;
+        const int xo = sd.tab_off + TableLayout(Q).xi;
+        velocity_powers<R>(Q, tables + xo, vt + xo, s.Vp, s.Vr, threadIdx.x, blockDim.x);
+    }
     __syncthreads();
-    // Warp 0 forms the node-level quantities of the tile (node fields,
+    // The node warps form the node-level quantities of the tile (node fields,
     // coefficient constants, Hermite moments of the local Gaussian) while the
     // other warps do the velocity-space work that needs only the state tile
     // (Hermite analysis, WENO-5 faces), so the serial node work overlaps it.
@@ -88,14 +94,22 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     const R* vtab = DF ? reinterpret_cast<const R*>(tables) : rtab;
     const R* rt = vtab + sd.tab_off;
     TableLayout L(Q);
-    if (threadIdx.x < 32) {
-        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32);
-        __syncwarp();
-        node_fields_pass2<R>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32);
-        __syncwarp();
-        node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32);
+    // Node warps: one, or two when pass 1 (nz + 4 nodes) would take a
+    // second round on one warp; the passes are separated by a barrier of the
+    // node warps only (named barrier 1).
+    const int NW = (nz + 4 > 32) ? 2 : 1;
+    auto node_sync = [&]() {
+        if (NW == 1) __syncwarp();
+        else asm volatile("bar.sync 1, 64;" ::: "memory");
+    };
+    if (threadIdx.x < 32 * NW) {
+        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32 * NW);
+        node_sync();
+        node_fields_pass2<R>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32 * NW);
+        node_sync();
+        node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
     } else {
-        const int tid = threadIdx.x - 32, nth = blockDim.x - 32;
+        const int tid = threadIdx.x - 32 * NW, nth = blockDim.x - 32 * NW;
         if constexpr (DF) {
             analysis_df(sd, it, s, Fd, reinterpret_cast<const float2*>(s.P), Z, tid, nth);
         } else {
@@ -191,7 +205,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     __syncthreads();
 
     // Phase 6: raw moment sums of the new stage for the next stage's node fields.
-    tile_moment_sums<R>(sd, it, s, Z, tables + sd.tab_off + L.xi, xi, mom_out, NN);
+    tile_moment_sums_staged<R>(sd, it, s, Z, s.Vp, s.Vr, mom_out, NN);
 }
 
 // Projected Maxwellian pair (F_MB, T F_MB) from node fields, formed in FP64 and
