@@ -247,14 +247,24 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     }
     const double* S1 = mom + MOM_S1 * NN + sd.node_off;
     const double* S2 = mom + MOM_S2 * NN + sd.node_off;
+    const double* S3 = mom + MOM_S3 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
+    const double* G1 = mom + MOM_G1 * NN + sd.node_off;
     for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
         int i = gidx(it.i0 - 2 + t, nx, bc);
-        double n = S0[i], inv_n = div_nr(1.0, n);
-        double u = S1[i] * inv_n;
+        const bool tile = (t >= 2 && t < it.nz + 2);
+        double n = S0[i], s1 = S1[i], s2 = S2[i], g0 = G0[i];
+        double s3 = tile ? S3[i] : 0.0, g1 = tile ? G1[i] : 0.0;
+        double inv_n = div_nr(1.0, n);
+        double u = s1 * inv_n;
         // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2
         s.U[t] = u;
-        s.T[t] = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) * inv_n - 0.5 * u * u);
+        s.T[t] = (2.0 / 3.0) * ((0.5 * s2 + g0) * inv_n - 0.5 * u * u);
+        // heat flux of the tile's nodes, q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0,
+        // formed here (in parallel, off the node warps' serial chain); the node
+        // fields read it from the KQ slot, which they then overwrite with (1 - Pr) q
+        if (tile)
+            s.Sc[SC_KQ * Z + (t - 2)] = 0.5 * (s3 - 3.0 * u * s2 + 3.0 * u * u * s1 - u * u * u * n) + g1 - u * g0;
     }
 }
 
@@ -272,6 +282,56 @@ __device__ void load_state_tile(const SlabDesc& sd, const WorkItem& it, const Sm
         R v = src[d * NF + sd.f_off + (long long)k * nx + i];
         s.F[(d * Q + k) * W + c] = v;
         if (Fd && c >= 3 && c < it.nz + 3) Fd[(size_t)r * Z + c - 3] = df_split((double)v);
+    }
+}
+
+// Asynchronous global-to-shared copy of one element (4 or 8 bytes, cp.async,
+// L1-allocating); completion by cp_async_wait_all.
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* smem_dst, const R* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(R) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The state tile (+-3 nodes) into s.F by asynchronous copies, all of them in
+// flight at once; the caller waits (cp_async_wait_all) and synchronises
+// before reading it.
+template <typename R>
+__device__ void issue_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                 const R* __restrict__ src, long long NF) {
+    const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
+    const int cols = it.nz + 6;
+    for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
+        const int c = e % cols, r = e / cols;
+        const int k = r % Q, d = r / Q;
+        const int i = gidx(it.i0 - 3 + c, nx, bc);
+        cp_async_elem<R>(s.F + (size_t)r * W + c, src + d * NF + sd.f_off + (long long)k * nx + i);
+    }
+    cp_async_commit();
+}
+
+// The parity-split interior columns EO[((d * 2 + par) * H + j) * Z + t] of
+// the state tile in s.F: E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j} (the
+// middle node of an odd Q: E = h, O = 0); threads tid, tid + nth, ...
+template <typename R>
+__device__ void split_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z, int tid, int nth) {
+    const int Q = sd.Q, W = Z + 6, H = (Q + 1) / 2, nz = it.nz;
+    for (int e = tid; e < 2 * H * nz; e += nth) {
+        const int t = e % nz, r = e / nz;
+        const int j = r % H, d = r / H, jm = Q - 1 - j;
+        const R v = s.F[(size_t)(d * Q + j) * W + t + 3];
+        R* eo = s.EO + ((size_t)(2 * d) * H + j) * Z + t;
+        if (jm != j) {
+            const R vm = s.F[(size_t)(d * Q + jm) * W + t + 3];
+            eo[0] = v + vm;
+            eo[(size_t)H * Z] = v - vm;
+        } else {
+            eo[0] = v;
+            eo[(size_t)H * Z] = R(0);
+        }
     }
 }
 
@@ -365,12 +425,7 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
                                   unsigned* err, double* fields_out, int tid, int nth) {
     const int M = sd.M;
     const double inv12 = sd.inv_dx / 12.0;
-    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
-    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
-    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
-    const double* S3 = mom + MOM_S3 * NN + sd.node_off;
-    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    const double* G1 = mom + MOM_G1 * NN + sd.node_off;
+    (void)mom;
     for (int t = tid; t < it.nz; t += nth) {
         const int c = t + 2;                         // index in the +-2 arrays
         const int i = it.i0 + t;
@@ -387,8 +442,8 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         double f1;
         if constexpr (std::is_same<R, float>::value) f1 = f2d_bits(f1r);
         else f1 = (double)f1r;
-        // heat flux from the raw sums: q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
-        double q = 0.5 * (S3[i] - 3.0 * u * S2[i] + 3.0 * u * u * S1[i] - u * u * u * S0[i]) + G1[i] - u * G0[i];
+        // heat flux, formed with the node inputs (load_node_inputs)
+        double q = s.Sc[SC_KQ * Z + t];
         // transport, Eqs. (viscosity), (tau), (prandtl)
         double bn, x, mu, tau, Pr, nu;
         if constexpr (std::is_same<R, float>::value) {
@@ -960,6 +1015,17 @@ template <typename R>
 __device__ void tile_moment_sums_staged(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                         const double* xp, const R* xr, double* __restrict__ mom_out, long long NN) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
+    if (nz <= 32 && blockDim.x >= 32 * kNumMoments) {
+        // one moment kind per warp, lanes on nodes: no divergence between
+        // the plain and the weighted sums inside a warp
+        const int which = threadIdx.x >> 5, t = threadIdx.x & 31;
+        if (which < kNumMoments && t < nz) {
+            const int d = which >= MOM_G0 ? 1 : 0;
+            const R* h = s.F + (size_t)d * Q * W + t + 3;
+            mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xp, xr);
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
         int t = e % nz, which = e / nz;
         int d = which >= MOM_G0 ? 1 : 0;

@@ -71,10 +71,12 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     // FP64 / FP32: parity-split tables and state tile (half the transform
     // products); FP64_DF: the full tables as float pairs and the state tile
     // split into float pairs in the EO block
+    // (FP64 / FP32: the tile by asynchronous copies, issued first, so that
+    // they are in flight with the node inputs' loads and arithmetic)
     float2* Fd = DF ? reinterpret_cast<float2*>(s.EO) : nullptr;
+    if constexpr (!DF) issue_state_tile<R>(sd, it, s, Z, src, NF);
     load_node_inputs<R, !DF>(sd, it, s, Z, rtab, mom_in, NN);
     if constexpr (DF) load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
-    else load_state_tile_eo<R>(sd, it, s, Z, src, NF);
     // the slab's force and Fischer-Methfessel taps, read in warp 0's serial
     // tap loops, staged once into shared memory
     for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.Ftap[j] = rtaps[sd.tap_off + j];
@@ -85,6 +87,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         const int xo = sd.tab_off + TableLayout(Q).xi;
         velocity_powers<R>(Q, tables + xo, vt + xo, s.Vp, s.Vr, threadIdx.x, blockDim.x);
     }
+    if constexpr (!DF) cp_async_wait_all();
     __syncthreads();
     // The node warps form the node-level quantities of the tile (node fields,
     // coefficient constants, Hermite moments of the local Gaussian) while the
@@ -113,6 +116,10 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         if constexpr (DF) {
             analysis_df(sd, it, s, Fd, reinterpret_cast<const float2*>(s.P), Z, tid, nth);
         } else {
+            // the worker warps split the tile into parity parts, then join on
+            // named barrier 2 (the node warps go on meanwhile)
+            split_state_tile<R>(sd, it, s, Z, tid, nth);
+            asm volatile("bar.sync 2, %0;" ::"r"(nth) : "memory");
             analysis_eo<R>(sd, it, s, Z, tid, nth);
         }
         if constexpr (DF) faces_df(sd, it, s, Z, tables, tid, nth);
@@ -134,16 +141,19 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     // output of velocity k of node t of distribution d; the two output forms
     // under one uniform branch, so that the RK form issues no FP64
     // conversion of the right-hand-side form
-    auto emit = [&](int d, int t, int k, R syn, R ch, R cx) {
+    // bv: the base value at (d, k, t), loaded by the caller ahead of its
+    // synthesis loop so that the global load's latency is hidden
+    auto gidx_of = [&](int d, int t, int k) { return d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t; };
+    auto emit = [&](int d, int t, int k, R syn, R ch, R cx, R bv) {
         R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
         const R h = *hp;
         const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
         const R df = fc[t + 1] - fc[t];
-        const long long g = d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t;
+        const long long g = gidx_of(d, t, k);
         if (rhs_form) {
             rhs_out[g] = (double)fma(-xi[k] * inv_dx, df, fma(-s.Scr[t], h, syn));
         } else {
-            R o = with_base ? ralpha * base[g] : R(0);
+            R o = with_base ? ralpha * bv : R(0);
             o = fma(ch, h, o);
             o = fma(cs, syn, o);
             o = fma(cx, df, o);
@@ -173,7 +183,9 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
             const R ch = fma(-cs, s.Scr[t], rbeta);
 #pragma unroll
             for (int q = 0; q < VK; ++q)
-                if (q < nk) emit(d, t, k0 + q, df_join(a[q], b[q]), ch, csx * xi[k0 + q]);
+                if (q < nk)
+                    emit(d, t, k0 + q, df_join(a[q], b[q]), ch, csx * xi[k0 + q],
+                         (with_base && !rhs_form) ? base[gidx_of(d, t, k0 + q)] : R(0));
         }
     } else {
         // parity split: one node pair (k, Q-1-k) per task; even orders build
@@ -188,6 +200,9 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
             const int k = r % H, d = r / H;
             const R* c = s.C + (size_t)d * Q * Z + t;
             const R2* sp = Sp + (size_t)k * QE2;
+            const bool pair = (Q - 1 - k != k), lb = with_base && !rhs_form;
+            const R b0 = lb ? base[gidx_of(d, t, k)] : R(0);
+            const R b1 = (lb && pair) ? base[gidx_of(d, t, Q - 1 - k)] : R(0);
             R ev = 0, od = 0;
             int l = 0;
             for (; l + 1 < Q; l += 2) {
@@ -197,8 +212,8 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
             }
             if (l < Q) ev = fma(sp[l >> 1].x, c[l * Z], ev);   // odd Q: the last (even) order
             const R ch = fma(-cs, s.Scr[t], rbeta), cx = csx * xi[k];
-            emit(d, t, k, ev + od, ch, cx);
-            if (Q - 1 - k != k) emit(d, t, Q - 1 - k, ev - od, ch, -cx);
+            emit(d, t, k, ev + od, ch, cx, b0);
+            if (pair) emit(d, t, Q - 1 - k, ev - od, ch, -cx, b1);
         }
     }
     if (mode == 1) return;
