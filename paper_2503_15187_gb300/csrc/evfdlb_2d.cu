@@ -548,311 +548,247 @@ k2_fields(Slab2 s, const double* __restrict__ mom, const float* __restrict__ prf
 }
 
 // ---------------------------------------------------------------------------
-// k2_coll: per group of kNB nodes, the velocity-space part of the RHS.
-// With m_l = E[psi_l(u + c)] and mu^a_l = E[c^a psi_l(u + c)] (c ~ N(0, T)):
+// k2_coll: per group of kNB consecutive nodes, the local (velocity-space)
+// part of the right-hand side,
+//   RL = -nu h + F_x (D (x) I) h + F_y (I (x) D) h + sum_{a<4} phi^a (x) psi^a.
+// D = S diag-shift(sqrt(l)) P is the derivative of the force term on the
+// Gauss-Hermite set: the synthesis of its coefficient form F sqrt(l) a_{l-1}
+// (S P = I on the set, so the relaxation -nu h needs no transform).  The
+// projected Shakhov equilibrium and J1, sum_ab P_ab n mu^a_l(u_x) mu^b_m(u_y)
+// in coefficient space (the one-axis Gaussian moments
 //   mu^0 = m_l, mu^1 = T sqrt(l) m_{l-1}, mu^2 = T m_l + T^2 sqrt(l(l-1)) m_{l-2},
 //   mu^3 = 3T^2 sqrt(l) m_{l-1} + T^3 sqrt(l(l-1)(l-2)) m_{l-3},
-// the coefficient of psi_l(xi_x) psi_m(xi_y) of F_MB sum_ab P_ab c_x^a c_y^b is
-// n sum_ab P_ab mu^a_l(u_x) mu^b_m(u_y).
+// m_l = E[psi_l(u + c)], c ~ N(0, T)), synthesise to the rank-4 sum of
+// outer products of phi^a = S mu^a(u_x) and psi^a = sum_b P_ab S mu^b(u_y).
+// D anticommutes with the node reflection xi -> -xi, so with
+// E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j} (j < Q/2) a line's D h is
+//   (D h)_k = (DB E)_k + (DA O)_k,   (D h)_{Q-1-k} = (DA O)_k - (DB E)_k,
+// DA_kj = (D_kj - D_{k,Q-1-j})/2, DB_kj = (D_kj + D_{k,Q-1-j})/2: two
+// (Q/2)^2 blocks instead of Q^2 products per line.
 // ---------------------------------------------------------------------------
-// Shared layout of k2_coll: per distribution and node a Q x Q matrix with
-// rows padded to kRow = 20 elements (a multiple of 4, so that rows are
-// 16-byte aligned for four-wide loads, and 80 bytes apart, so that rows 4
-// apart fall 16 banks apart: the eight threads of a quarter warp then read
-// distinct banks in both transform directions), node stride padded by 4 so
-// that the eight nodes of a group fall in different banks for the scalar
-// state loads.
-constexpr int kRow = 20;
-__host__ __device__ constexpr int padded_q(int Q) { return (Q + 3) & ~3; }
-__host__ __device__ constexpr int node_stride(int Q) { return padded_q(Q) * kRow + 4; }
+template <int Q>
+struct Coll2Lay {
+    static constexpr int K = Q * Q, QH = Q / 2;
+    // matrix row and node strides: with XR = 20 the row pairs and column
+    // pairs of a half-warp's tasks fall in distinct banks, and the odd node
+    // stride puts the two matrices of a warp on alternate banks
+    static constexpr int XR = 20, XS = Q * XR + 1, DR = QH + 1;   // DR: padded rows of DA, DB
+    // X [2 kNB][XS] state, RLs [2 kNB][XS] result, mu, my, phi, chi [kNB][4][Q],
+    // psi [2][4][kNB][Q], sc [kNumFld2][kNB], St [Q][Q] (transposed synthesis
+    // table St[l][k] = w_k psi_l(xi_k)), DA, DB [QH][QH], rinv, rr, r1, r2, r3 [Q]
+};
 
 template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
-    size_t X = 2 * (size_t)kNB * node_stride(Q);      // one [2][kNB][Q][kRow] buffer
-    return sizeof(R) * (2 * (size_t)padded_q(Q) * kRow + 3 * (size_t)padded_q(Q) + 2 * X + kNumFld2 * kNB +
-                        (4 * (size_t)padded_q(Q) + 4) * kNB +
-                        2 * 4 * (size_t)(padded_q(Q) + 4) * kNB);
-}
-
-// Four consecutive elements of a 16-byte aligned shared row.
-__device__ __forceinline__ void load4(const float* p, float v[4]) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-__device__ __forceinline__ void load4(const double* p, double v[4]) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
-// Four consecutive elements to a 16-byte aligned shared row.
-__device__ __forceinline__ void store4(float* p, const float v[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void store4(double* p, const double v[4]) {
-    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
-
-// Out[i][j] = sum_k Lt[k][i] In[k][j]  (left contraction, Lt = transposed left matrix)
-// or         sum_k In[i][k] Rt[k][j]  (right contraction, Rt = transposed right matrix)
-// for the matrices of one (distribution, node); each thread forms a 4 x 4
-// block from four-wide row loads: the left form walks k one row of Lt and
-// In at a time, the right form four k at a time (four rows of In, four rows
-// of Rt; the padded rows and columns Q .. Qp-1 are zero).
-template <typename R, bool LEFT, int Q>
-__device__ __forceinline__ void block_acc(const R* __restrict__ M, const R* __restrict__ In, R (&acc)[4][4], int i0,
-                                          int j0) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-    if constexpr (LEFT) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            R m[4], x[4];
-            load4(M + k * kRow + i0, m);       // Lt[k][i0 .. i0+3]
-            load4(In + k * kRow + j0, x);      // In[k][j0 .. j0+3]
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a], x[b], acc[a][b]);
-        }
-    } else {
-        constexpr int Qp = padded_q(Q);
-#pragma unroll
-        for (int k = 0; k < Qp; k += 4) {
-            R m[4][4], x[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) load4(In + (i0 + a) * kRow + k, m[a]);   // In[i0 + a][k .. k+3]
-#pragma unroll
-            for (int q = 0; q < 4; ++q) load4(M + (k + q) * kRow + j0, x[q]);    // Rt[k + q][j0 .. j0+3]
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(m[a][q], x[q][b], acc[a][b]);
-        }
-    }
-}
-
-template <typename R, bool LEFT, int Q>
-__device__ __forceinline__ void block_transform(const R* __restrict__ M, const R* __restrict__ In, R* __restrict__ Out,
-                                                int i0, int j0) {
-    R acc[4][4];
-    block_acc<R, LEFT, Q>(M, In, acc, i0, j0);
-    // one 16-byte store per row: the 32 rows of a warp fill the banks 4 wavefronts deep
-#pragma unroll
-    for (int a = 0; a < 4; ++a) store4(Out + (i0 + a) * kRow + j0, acc[a]);
-}
-
-// One-axis Gaussian moments of the kNB nodes of a collision group (the
-// recurrence of the mu^a_l above): x on lanes 0 .. kNB-1 of warp 0 into mux
-// ([kNB][4][Qp], node stride 4 Qp + 4), y folded with the polynomial
-// coefficients of F and G on lanes 0 .. kNB-1 of warp 1 into Vy
-// ([2][4][kNB] rows of Qp + 4).
-template <typename R, int Q>
-__device__ __forceinline__ void coll_moments(const R* __restrict__ rtab, const TableLayout& L, const R* sc, const R* r1,
-                                             const R* r2, const R* r3, R* mux, R* Vy) {
-    constexpr int Qp = padded_q(Q), MXS = 4 * Qp + 4, VYS = Qp + 4;
-    if (threadIdx.x < 64 && (threadIdx.x & 31) < kNB) {
-        const int t = threadIdx.x & 31, axis = threadIdx.x >> 5;
-        const R u = sc[(axis ? F2_UY : F2_UX) * kNB + t], T = sc[F2_T * kNB + t], Tm1 = T - R(1);
-        R m[4] = {0, 0, 0, 0};   // m_{l}, m_{l-1}, m_{l-2}, m_{l-3}
-        R m0 = 1, m1 = 0;
-        R PF[4][4], PG[4][4];
-        if (axis) {
-            // P_ab as a 4x4 table (zero where a + b > 3)
-            const int ia[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0}, ib[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-            for (int a = 0; a < 4; ++a)
-                for (int b = 0; b < 4; ++b) PF[a][b] = PG[a][b] = 0;
-            for (int j = 0; j < 10; ++j) {
-                PF[ia[j]][ib[j]] = sc[(F2_PF + j) * kNB + t];
-                PG[ia[j]][ib[j]] = sc[(F2_PG + j) * kNB + t];
-            }
-        }
-        for (int l = 0; l < Q; ++l) {
-            m[3] = m[2];
-            m[2] = m[1];
-            m[1] = m[0];
-            m[0] = m0;
-            R mu0 = m[0];
-            R mu1 = T * r1[l] * m[1];
-            R mu2 = T * m[0] + T * T * r2[l] * m[2];
-            R mu3 = R(3) * T * T * r1[l] * m[1] + T * T * T * r3[l] * m[3];
-            if (!axis) {
-                mux[t * MXS + 0 * Qp + l] = mu0;
-                mux[t * MXS + 1 * Qp + l] = mu1;
-                mux[t * MXS + 2 * Qp + l] = mu2;
-                mux[t * MXS + 3 * Qp + l] = mu3;
-            } else {
-                const R mb[4] = {mu0, mu1, mu2, mu3};
-                for (int a = 0; a < 4; ++a) {
-                    R vf = 0, vg = 0;
-                    for (int b = 0; b < 4; ++b) {
-                        vf = fma(PF[a][b], mb[b], vf);
-                        vg = fma(PG[a][b], mb[b], vg);
-                    }
-                    Vy[((0 * 4 + a) * kNB + t) * VYS + l] = vf;
-                    Vy[((1 * 4 + a) * kNB + t) * VYS + l] = vg;
-                }
-            }
-            R mn = fma(u * rtab[L.rinv + l], m0, Tm1 * rtab[L.rr + l] * m1);
-            m1 = m0;
-            m0 = mn;
-        }
-    }
+    const int XS = Q * 20 + 1, QH = Q / 2;
+    return sizeof(R) * ((size_t)4 * kNB * XS + 4 * kNB * 4 * Q + 8 * kNB * Q + kNumFld2 * kNB + Q * Q +
+                        2 * QH * (QH + 1) + 5 * Q);
 }
 
 template <typename R, int Q>
-__global__ void __launch_bounds__(256)
-k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* __restrict__ fld, R* __restrict__ RL) {
+__global__ void __launch_bounds__(256, 2)
+k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ dtab, const R* __restrict__ st,
+        const R* __restrict__ fld, R* __restrict__ RL) {
+    using Lay = Coll2Lay<Q>;
+    constexpr int K = Lay::K, QH = Lay::QH, XR = Lay::XR, XS = Lay::XS, DR = Lay::DR, NT = 256;
+    static_assert(Q <= 20, "rows of XR = 20");
     extern __shared__ __align__(16) double smc[];
-    constexpr int K = Q * Q, NS = node_stride(Q), Qp = padded_q(Q);
+    R* X = reinterpret_cast<R*>(smc);                          // [2 kNB][XS]: h[kx][ky] at kx XR + ky
+    R* RLs = X + 2 * kNB * XS;
+    R* mu = RLs + 2 * kNB * XS;                                 // x-axis moments [kNB][4][Q]
+    R* my = mu + kNB * 4 * Q;                                   // y-axis moments [kNB][4][Q]
+    R* phi = my + kNB * 4 * Q;                                  // S mu [kNB][4][Q]
+    R* chi = phi + kNB * 4 * Q;                                 // S my [kNB][4][Q]
+    R* psi = chi + kNB * 4 * Q;                                 // [2][4][kNB][Q]
+    R* sc = psi + 8 * kNB * Q;                                  // [kNumFld2][kNB]
+    R* St = sc + kNumFld2 * kNB;                                // [Q][Q] transposed synthesis table
+    R* DA = St + K;                                             // [QH][DR]
+    R* DB = DA + QH * DR;
+    R* rinv = DB + QH * DR;
+    R* rr = rinv + Q;
+    R* r1 = rr + Q;
+    R* r2 = r1 + Q;
+    R* r3 = r2 + Q;
     const long long N = s.N, NF = (long long)K * N;
     const long long i0 = (long long)blockIdx.x * kNB;
     const int nb = (int)min((long long)kNB, N - i0);
     TableLayout L(Q);
-    R* Pt = reinterpret_cast<R*>(smc);     // Pt[j][l] = psi_l(xi_j)       (transposed analysis table)
-    R* St = Pt + Qp * kRow;                // St[l][k] = w_k psi_l(xi_k)   (transposed synthesis table)
-    R* r1 = St + Qp * kRow;
-    R* r2 = r1 + Qp;
-    R* r3 = r2 + Qp;
-    R* X0 = r3 + Qp;                       // [2][kNB] matrices, node stride NS (16-byte aligned)
-    R* X1 = X0 + 2 * kNB * NS;
-    R* sc = X1 + 2 * kNB * NS;             // [kNumFld2][kNB]
-    // node strides padded by 4 so that the eight nodes' writes fall in
-    // different banks; rows stay 16-byte aligned for the epilogue's loads
-    constexpr int MXS = 4 * Qp + 4, VYS = Qp + 4;
-    R* mux = sc + kNumFld2 * kNB;          // [kNB][4][Qp], node stride MXS
-    R* Vy = mux + MXS * kNB;               // [2][4][kNB][Qp], node stride VYS
-    auto mat = [&](R* X, int d, int t) { return X + (d * kNB + t) * NS; };
-    for (int e = threadIdx.x; e < Qp * kRow; e += blockDim.x) {
-        int r = e / kRow, c = e % kRow;
-        Pt[e] = (c < Q && r < Q) ? rtab[L.P + c * Q + r] : R(0);
-        St[e] = (c < Q && r < Q) ? rtab[L.S + c * Q + r] : R(0);
+    for (int e = threadIdx.x; e < K; e += NT) St[e] = rtab[L.S + (e % Q) * Q + e / Q];
+    // the group's state as [d][node][kx][ky] by asynchronous copies, all in
+    // flight at once (8 consecutive nodes per plane: 32-byte segments)
+    for (int e = threadIdx.x; e < 2 * K * kNB; e += NT) {
+        const int n = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
+        R* dst = X + (d * kNB + n) * XS + (k / Q) * XR + k % Q;
+        if (n < nb) cp_async_elem<R>(dst, st + d * NF + (long long)k * N + i0 + n);
+        else *dst = R(0);
     }
-    for (int e = threadIdx.x; e < Q; e += blockDim.x) {
+    cp_async_commit();
+    for (int e = threadIdx.x; e < QH * QH; e += NT) {
+        DA[(e / QH) * DR + e % QH] = dtab[e];
+        DB[(e / QH) * DR + e % QH] = dtab[QH * QH + e];
+    }
+    for (int e = threadIdx.x; e < Q; e += NT) {
+        rinv[e] = rtab[L.rinv + e];
+        rr[e] = rtab[L.rr + e];
         r1[e] = rtab[L.r1 + e];
         r2[e] = rtab[L.r2 + e];
         r3[e] = rtab[L.r3 + e];
     }
-    // state of the group as [d][node][kx][ky] (ky contiguous, rows of kRow);
-    // rows and columns Q .. Qp-1 of every matrix, and the padding of the
-    // moment rows, stay zero (nothing outside Q x Q is read when Qp = Q)
-    if constexpr (Qp != Q) {
-        for (int e = threadIdx.x; e < 2 * 2 * kNB * NS; e += blockDim.x) X0[e] = R(0);
-        for (int e = threadIdx.x; e < MXS * kNB + 8 * VYS * kNB; e += blockDim.x) mux[e] = R(0);
-        __syncthreads();
+    for (int e = threadIdx.x; e < kNumFld2 * kNB; e += NT) {
+        const int n = e % kNB, f = e / kNB;
+        sc[e] = (n < nb) ? fld[f * N + i0 + n] : (f == F2_N || f == F2_T ? R(1) : R(0));
     }
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int t = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
-        mat(X0, d, t)[(k / Q) * kRow + k % Q] = (t < nb) ? st[d * NF + (long long)k * N + i0 + t] : R(0);
-    }
-    for (int e = threadIdx.x; e < kNumFld2 * kNB; e += blockDim.x) {
-        int t = e % kNB, f = e / kNB;
-        sc[e] = (t < nb) ? fld[f * N + i0 + t] : (f == F2_N || f == F2_T ? R(1) : R(0));
+    cp_async_wait_all();
+    __syncthreads();
+    // one-axis Gaussian moments mu^a_l, one node and axis per thread
+    if (threadIdx.x < 2 * kNB) {
+        const int n = threadIdx.x % kNB, axis = threadIdx.x / kNB;
+        const R u = sc[(axis ? F2_UY : F2_UX) * kNB + n], T = sc[F2_T * kNB + n], Tm1 = T - R(1);
+        R* out = (axis ? my : mu) + n * 4 * Q;
+        R m1v = 0, m2v = 0, m3v = 0;                            // m_{l-1}, m_{l-2}, m_{l-3}
+        R m0 = 1;                                               // m_l
+        for (int l = 0; l < Q; ++l) {
+            out[l] = m0;
+            out[Q + l] = T * r1[l] * m1v;
+            out[2 * Q + l] = T * m0 + T * T * r2[l] * m2v;
+            out[3 * Q + l] = R(3) * T * T * r1[l] * m1v + T * T * T * r3[l] * m3v;
+            const R mn = fma(u * rinv[l], m0, Tm1 * rr[l] * m1v);
+            m3v = m2v;
+            m2v = m1v;
+            m1v = m0;
+            m0 = mn;
+        }
     }
     __syncthreads();
-    coll_moments<R, Q>(rtab, L, sc, r1, r2, r3, mux, Vy);
-    // the four tensor transforms: one (distribution, node, 4x4 block) per thread
-    const int nblk = (Qp / 4) * (Qp / 4);
-    const int item = threadIdx.x / nblk, blk = threadIdx.x % nblk;   // item = d * kNB + node
-    const bool active = item < 2 * kNB;
-    const int d = item / kNB, t = item % kNB;
-    const int bi = 4 * (blk / (Qp / 4)), bj = 4 * (blk % (Qp / 4));
-    // Two buffers: the state is needed only by the first transform, since
-    // -nu h is synthesised from -nu times its own analysis (the tensor
-    // Gauss-Hermite transform of order Q per axis is invertible).
-    // analysis along xi_x: X1[l][ky] = sum_kx psi_l(xi_kx) X0[kx][ky]
-    if (active) block_transform<R, true, Q>(Pt, mat(X0, d, t), mat(X1, d, t), bi, bj);
+    // one-axis syntheses phi = S mu, chi = S my (consecutive threads on consecutive nodes k of St rows)
+    for (int e = threadIdx.x; e < 8 * kNB * Q; e += NT) {
+        const int k = e % Q, v = e / Q;
+        const R* c = mu + v * Q;                                // mu and my are adjacent: v < 8 kNB
+        R acc = 0;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) acc = fma(St[l * Q + k], c[l], acc);
+        phi[v * Q + k] = acc;                                   // phi then chi
+    }
     __syncthreads();
-    // analysis along xi_y, Z[l][m] = sum_ky X1[l][ky] psi_m(xi_ky), and the
-    // coefficients (relaxation -nu a, equilibria, J1, force terms)
-    //   C[l][m] = sum_a mu^a_l V^a_m + F_x r1_l Z[l-1][m] + F_y r1_m Z[l][m-1] - nu Z[l][m]
-    // into CB.  When an item's blocks lie in one warp (32 % nblk == 0) they
-    // are formed in the transform's epilogue: Z[l-1][.] of a block's top row
-    // and Z[.][m-1] of its left column come from the blocks above and to the
-    // left by warp shuffles.  Otherwise a separate pass over Z.
-    constexpr bool kFuse = (32 % ((Qp / 4) * (Qp / 4)) == 0);
-    R* CB = kFuse ? X0 : X1;
-    R* OB = kFuse ? X1 : X0;
-    if constexpr (kFuse) {
-        R acc[4][4];
-        if (active) block_acc<R, false, Q>(Pt, mat(X1, d, t), acc, bi, bj);
-        R up[4], left[4];
+    // psi^{a,d} = sum_b P^d_ab chi^b (P^d: the equilibrium polynomials' coefficients, times n)
+    for (int e = threadIdx.x; e < 8 * kNB * Q; e += NT) {
+        const int k = e % Q, r = e / Q;
+        const int n = r % kNB, a = (r / kNB) % 4, d = r / (4 * kNB);
+        // the coefficient of c_x^a c_y^b sits at (a+b)(a+b+1)/2 + b in the order
+        // (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (3,0) (2,1) (1,2) (0,3)
+        const int f0 = d ? F2_PG : F2_PF;
+        R acc = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) up[b] = __shfl_up_sync(0xffffffffu, acc[3][b], Qp / 4);
+        for (int b = 0; b < 4; ++b)
+            if (a + b <= 3)
+                acc = fma(sc[(f0 + (a + b) * (a + b + 1) / 2 + b) * kNB + n], chi[(n * 4 + b) * Q + k], acc);
+        psi[r * Q + k] = acc;
+    }
+    __syncthreads();
+    // D along x and y on node-pair blocks and the combination; a task owns
+    // KP pairs of rows (k, Q-1-k) and KP pairs of columns of one (d, node)
+    constexpr int KP = (QH % 2 == 0) ? 2 : 1, NKB = QH / KP;
+    constexpr int TASKS = 2 * kNB * NKB * NKB;
+    for (int task = threadIdx.x; task < TASKS; task += NT) {
+        const int mi = task / (NKB * NKB), kb = (task / NKB) % NKB, mb = task % NKB;
+        const int d = mi / kNB, n = mi % kNB;
+        const R* h = X + mi * XS;
+        int rw[2 * KP], cl[2 * KP];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) left[a] = __shfl_up_sync(0xffffffffu, acc[a][3], 1);
-        if (active) {
-            const R mnu = -sc[F2_NU * kNB + t], fx = sc[F2_FX * kNB + t], fy = sc[F2_FY * kNB + t];
-            R mx[4][4], vv[4][4], rl[4], rm[4];
+        for (int a = 0; a < KP; ++a) {
+            rw[a] = kb * KP + a;
+            rw[KP + a] = Q - 1 - rw[a];
+            cl[a] = mb * KP + a;
+            cl[KP + a] = Q - 1 - cl[a];
+        }
+        R dx[2 * KP][2 * KP], dy[2 * KP][2 * KP];
+        {   // along x: for each column, u = DA O, v = DB E over the row pairs
+            R u[KP][2 * KP], v[KP][2 * KP];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                load4(mux + t * MXS + a * Qp + bi, mx[a]);
-                load4(Vy + ((d * 4 + a) * kNB + t) * VYS + bj, vv[a]);
-            }
-            load4(r1 + bi, rl);
-            load4(r1 + bj, rm);
-            R* C = mat(CB, d, t);
+            for (int a = 0; a < KP; ++a)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                R cr[4];
+                for (int c = 0; c < 2 * KP; ++c) u[a][c] = v[a][c] = R(0);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int l = bi + a, m = bj + b;
-                    R c = 0;
+            for (int j = 0; j < QH; ++j) {
+                R ev[2 * KP], od[2 * KP];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) c = fma(mx[q][a], vv[q][b], c);
-                    if (l >= 1) c = fma(fx * rl[a], a == 0 ? up[b] : acc[a - 1][b], c);
-                    if (m >= 1) c = fma(fy * rm[b], b == 0 ? left[a] : acc[a][b - 1], c);
-                    c = fma(mnu, acc[a][b], c);
-                    cr[b] = (l < Q && m < Q) ? c : R(0);
+                for (int c = 0; c < 2 * KP; ++c) {
+                    const R p = h[j * XR + cl[c]], q = h[(Q - 1 - j) * XR + cl[c]];
+                    ev[c] = p + q;
+                    od[c] = p - q;
                 }
-                store4(C + (bi + a) * kRow + bj, cr);
+#pragma unroll
+                for (int a = 0; a < KP; ++a) {
+                    const R da = DA[rw[a] * DR + j], db = DB[rw[a] * DR + j];
+#pragma unroll
+                    for (int c = 0; c < 2 * KP; ++c) {
+                        u[a][c] = fma(da, od[c], u[a][c]);
+                        v[a][c] = fma(db, ev[c], v[a][c]);
+                    }
+                }
             }
+#pragma unroll
+            for (int a = 0; a < KP; ++a)
+#pragma unroll
+                for (int c = 0; c < 2 * KP; ++c) {
+                    dx[a][c] = v[a][c] + u[a][c];
+                    dx[KP + a][c] = u[a][c] - v[a][c];
+                }
         }
-        __syncthreads();
-    } else {
-        if (active) block_transform<R, false, Q>(Pt, mat(X1, d, t), mat(X0, d, t), bi, bj);
-        __syncthreads();
-        // one y-order mm per thread (lanes on consecutive mm: conflict-free
-        // rows), looping over the x-order l; its y-moment factors are loop-invariant
-        for (int e = threadIdx.x; e < 2 * kNB * Q; e += blockDim.x) {
-            const int mm = e % Q, tt = (e / Q) % kNB, dd = e / (Q * kNB);
-            const R* A = mat(X0, dd, tt);
-            R* C = mat(X1, dd, tt);
-            const R mnu = -sc[F2_NU * kNB + tt];
-            R vy[4];
+        {   // along y: for each row, over the column pairs
+            R u[2 * KP][KP], v[2 * KP][KP];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) vy[a] = Vy[((dd * 4 + a) * kNB + tt) * VYS + mm];
-            const R fx = sc[F2_FX * kNB + tt], fyr = sc[F2_FY * kNB + tt] * r1[mm];
+            for (int r = 0; r < 2 * KP; ++r)
 #pragma unroll
-            for (int l = 0; l < Q; ++l) {
-                R c = 0;
+                for (int a = 0; a < KP; ++a) u[r][a] = v[r][a] = R(0);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) c = fma(mux[tt * MXS + a * Qp + l], vy[a], c);
-                if (l >= 1) c = fma(fx * r1[l], A[(l - 1) * kRow + mm], c);
-                if (mm >= 1) c = fma(fyr, A[l * kRow + mm - 1], c);
-                c = fma(mnu, A[l * kRow + mm], c);
-                C[l * kRow + mm] = c;
+            for (int j = 0; j < QH; ++j) {
+                R ev[2 * KP], od[2 * KP];
+#pragma unroll
+                for (int r = 0; r < 2 * KP; ++r) {
+                    const R p = h[rw[r] * XR + j], q = h[rw[r] * XR + Q - 1 - j];
+                    ev[r] = p + q;
+                    od[r] = p - q;
+                }
+#pragma unroll
+                for (int a = 0; a < KP; ++a) {
+                    const R da = DA[cl[a] * DR + j], db = DB[cl[a] * DR + j];
+#pragma unroll
+                    for (int r = 0; r < 2 * KP; ++r) {
+                        u[r][a] = fma(da, od[r], u[r][a]);
+                        v[r][a] = fma(db, ev[r], v[r][a]);
+                    }
+                }
             }
+#pragma unroll
+            for (int r = 0; r < 2 * KP; ++r)
+#pragma unroll
+                for (int a = 0; a < KP; ++a) {
+                    dy[r][a] = v[r][a] + u[r][a];
+                    dy[r][KP + a] = u[r][a] - v[r][a];
+                }
         }
-        __syncthreads();
+        const R mnu = -sc[F2_NU * kNB + n], fx = sc[F2_FX * kNB + n], fy = sc[F2_FY * kNB + n];
+        R* o = RLs + mi * XS;
+#pragma unroll
+        for (int r = 0; r < 2 * KP; ++r)
+#pragma unroll
+            for (int c = 0; c < 2 * KP; ++c) {
+                R eq = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    eq = fma(phi[(n * 4 + a) * Q + rw[r]], psi[((d * 4 + a) * kNB + n) * Q + cl[c]], eq);
+                R rl = fma(mnu, h[rw[r] * XR + cl[c]], eq);
+                rl = fma(fx, dx[r][c], rl);
+                rl = fma(fy, dy[r][c], rl);
+                o[rw[r] * XR + cl[c]] = rl;
+            }
     }
-    // synthesis along xi_x: OB[kx][m] = sum_l w_kx psi_l(xi_kx) CB[l][m]
-    if (active) block_transform<R, true, Q>(St, mat(CB, d, t), mat(OB, d, t), bi, bj);
     __syncthreads();
-    // synthesis along xi_y: CB[kx][ky] = sum_m OB[kx][m] w_ky psi_m(xi_ky)
-    if (active) block_transform<R, false, Q>(St, mat(OB, d, t), mat(CB, d, t), bi, bj);
-    __syncthreads();
-    // the local right-hand side -nu h + sum S S c (both in CB)
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += blockDim.x) {
-        int tt = e % kNB, k = (e / kNB) % K, dd = e / (kNB * K);
-        if (tt >= nb) continue;
-        const int off = (k / Q) * kRow + k % Q;
-        RL[dd * NF + (long long)k * N + i0 + tt] = mat(CB, dd, tt)[off];
+    // the local right-hand side to global memory, 8 consecutive nodes per plane
+    for (int e = threadIdx.x; e < 2 * K * kNB; e += NT) {
+        const int n = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
+        if (n < nb) RL[d * NF + (long long)k * N + i0 + n] = RLs[(d * kNB + n) * XS + (k / Q) * XR + k % Q];
     }
 }
 
@@ -1263,6 +1199,37 @@ ForcePlan force_plan(const Taps2& t) {
     return fp;
 }
 
+// Parity blocks of the force term's derivative on the velocity set,
+// D_kj = sum_{l=1}^{Q-1} w_k psi_l(xi_k) sqrt(l) psi_{l-1}(xi_j) (D = S shift P,
+// the synthesis of the coefficient form F sqrt(l) a_{l-1}), in long double:
+// DA_kj = (D_kj - D_{k,Q-1-j}) / 2 and DB_kj = (D_kj + D_{k,Q-1-j}) / 2 for
+// k, j < Q/2, as [QH][QH] each (DA then DB).
+std::vector<double> d_blocks(int Q, const double* xi, const double* w) {
+    const int QH = Q / 2;
+    std::vector<long double> ps((size_t)Q * (Q + 1));
+    for (int k = 0; k < Q; ++k) {
+        long double* p = ps.data() + (size_t)k * (Q + 1);
+        const long double x = xi[k];
+        p[0] = 1;
+        p[1] = x;
+        for (int l = 1; l < Q; ++l) p[l + 1] = (x * p[l] - sqrtl((long double)l) * p[l - 1]) / sqrtl((long double)(l + 1));
+    }
+    auto D = [&](int k, int j) {
+        long double acc = 0;
+        for (int l = 1; l < Q; ++l)
+            acc += (long double)w[k] * ps[(size_t)k * (Q + 1) + l] * sqrtl((long double)l) * ps[(size_t)j * (Q + 1) + l - 1];
+        return acc;
+    };
+    std::vector<double> out(2 * (size_t)QH * QH);
+    for (int k = 0; k < QH; ++k)
+        for (int j = 0; j < QH; ++j) {
+            const long double a = D(k, j), b = D(k, Q - 1 - j);
+            out[k * QH + j] = (double)(0.5L * (a - b));
+            out[QH * QH + k * QH + j] = (double)(0.5L * (a + b));
+        }
+    return out;
+}
+
 template <typename R>
 Pow2<R> make_pow2(int Q, const double* xi) {
     Pow2<R> p{};
@@ -1325,6 +1292,7 @@ struct Ctx2 {
     int* fm_off = nullptr;
     void* fm_w = nullptr;        // Fischer-Methfessel weights, precision R
     float* prf = nullptr;        // FP32 build: node primitives [kNumPrf2][N] of the stage input
+    void* dtab = nullptr;        // parity blocks DA, DB of the force derivative (k2_coll), precision R
     Pow2<float> pwf{};
     Pow2<double> pwd{};
     double* scratch = nullptr;   // [2 Q^2 N + 8] doubles
@@ -1336,16 +1304,16 @@ struct Ctx2 {
 namespace {
 // k2_coll is compiled for each even Q of the 2D model (4 .. 16)
 template <typename R>
-void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, const R* rtab, const R* src,
-                 const R* fld, R* RL) {
+void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, const R* rtab, const R* dtab,
+                 const R* src, const R* fld, R* RL) {
     switch (Q) {
-        case 4: k2_coll<R, 4><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        case 6: k2_coll<R, 6><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        case 8: k2_coll<R, 8><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        case 10: k2_coll<R, 10><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        case 12: k2_coll<R, 12><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        case 14: k2_coll<R, 14><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
-        default: k2_coll<R, 16><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 4: k2_coll<R, 4><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 6: k2_coll<R, 6><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 8: k2_coll<R, 8><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 10: k2_coll<R, 10><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 12: k2_coll<R, 12><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 14: k2_coll<R, 14><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        default: k2_coll<R, 16><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
     }
 }
 
@@ -1419,7 +1387,8 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
     k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->prf, (const R*)c->ftw, c->fplan, c->fm_off,
                                                    (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
-    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
+    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)c->dtab, (const R*)src, (const R*)c->fld,
+                   (R*)c->RL);
     dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
     launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
                   alpha, beta, mode);
@@ -1456,6 +1425,7 @@ void destroy_2d(Ctx2* c) {
     cudaFree(c->fm_off);
     cudaFree(c->fm_w);
     cudaFree(c->prf);
+    cudaFree(c->dtab);
     cudaFree(c->scratch);
     cudaFree(c->err);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -1512,6 +1482,9 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     alloc((void**)&c->fm_off, sizeof(int) * t.moff.size());
     alloc(&c->fm_w, c->esize * t.mw.size());
     if (f32) alloc((void**)&c->prf, sizeof(float) * kNumPrf2 * s.N);
+    const std::vector<double> dbl = d_blocks(p.Q, xi.data(), w.data());
+    const std::vector<float> dblf(dbl.begin(), dbl.end());
+    alloc(&c->dtab, c->esize * dbl.size());
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + 8));
     alloc((void**)&c->err, sizeof(unsigned));
     std::vector<float> tabf(tab.begin(), tab.end()), ftwf(fp.w.begin(), fp.w.end()), mwf(t.mw.begin(), t.mw.end());
@@ -1523,6 +1496,9 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
         e = cudaMemcpy(c->rtab, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->fplan, fp.plan.data(), sizeof(int) * fp.plan.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = f32 ? cudaMemcpy(c->dtab, dblf.data(), sizeof(float) * dblf.size(), cudaMemcpyHostToDevice)
+                : cudaMemcpy(c->dtab, dbl.data(), sizeof(double) * dbl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = f32 ? cudaMemcpy(c->ftw, ftwf.data(), sizeof(float) * ftwf.size(), cudaMemcpyHostToDevice)
                 : cudaMemcpy(c->ftw, fp.w.data(), sizeof(double) * fp.w.size(), cudaMemcpyHostToDevice);
