@@ -440,7 +440,9 @@ def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=100):
     256 independent periodic slabs, Nz log-uniform in [128, 8192],
     Q in {16, 24, 32}, T/T_c in [0.6, 0.95], mean n in [0.15, 0.35], +-1%
     noise, dz = 0.25, FP64.  Batched: one context, one launch per RK stage for
-    all slabs, node tile from the autotuner.  Per-instance: one context per
+    all slabs, node tile from the autotuner.  Persistent: the same context
+    and tile with one resident launch per graph of steps, each slab's stages
+    ordered by device-side counters.  Per-instance: one context per
     slab, each with its own (one-wave) tile, launched back to back on the
     same stream.  Both are timed over `steps` steps from the same state.
     Under N ranks each rank advances its longest-processing-time share of the
@@ -472,6 +474,18 @@ def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=100):
     sim.step(0)
     ms_b = maxred(e0.elapsed_time(e1))
     mass = sim.moments()[4][:, 0]
+    state_b = np.concatenate(sim.get_state())
+    # persistent form: one launch per graph of steps, stage dependencies per
+    # slab waited on the device; same tile, same initial state
+    sim.set_persistent(True)
+    sim.init(n0, u0, T0)
+    sim.step(2)
+    e0.record(stream)
+    sim.step_async(steps)
+    e1.record(stream)
+    sim.step(0)
+    ms_q = maxred(e0.elapsed_time(e1))
+    same = bool(np.array_equal(np.concatenate(sim.get_state()), state_b))
     sim.close()
     if world > 1:
         masses = shard.gather_by_slab({i: float(m) for i, m in zip(mine, mass)}, len(all_slabs))
@@ -494,10 +508,18 @@ def batched_leg(ev, W, stream, rank=0, world=1, maxred=lambda x: x, steps=100):
         one.step(0)
         one.close()
     vb, vp = nvu / (ms_b * 1e-3) / 1e9, nvu / (ms_p * 1e-3) / 1e9
+    vq = nvu / (ms_q * 1e-3) / 1e9
     return {"workload": "256 periodic slabs, Nz log-uniform [128, 8192], Q in {16,24,32}, dz 0.25, FP64",
             "sharding": f"LPT over {world} rank(s), {len(mine)} slabs on rank {rank}",
             "nvu_per_step": nvu // steps, "steps": steps, "batched_GNVUPS": vb, "per_instance_GNVUPS": vp,
             "batched_over_per_instance": vb / vp, "tile_nodes": best,
+            "persistent_GNVUPS": vq, "persistent_over_per_stage": vq / vb,
+            "persistent_bit_identical": same,
+            # the time the launch-per-stage form loses at its three grid-wide
+            # stage boundaries per step (tails of the last wave, launch gaps)
+            "stage_boundary_ms_per_step": (ms_b - ms_q) / steps,
+            "ms_per_step": {"per_stage": ms_b / steps, "persistent": ms_q / steps,
+                            "per_instance": ms_p / steps},
             "autotune_ms_per_step": {str(k): round(v, 3) for k, v in tune_ms.items()}}
 
 

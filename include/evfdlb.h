@@ -327,6 +327,32 @@ evfdlb_status evfdlb_divide_fp64(const double* a, const double* b, double* q, do
                                  void* cuda_stream);
 evfdlb_status evfdlb_profile_stage(evfdlb_ctx* ctx, int32_t stage);
 
+/* Persistent form of the step for a batch of slabs (FP64, thermal, dim = 1).
+ * enable = 1: every evfdlb_step / step_async advances all slabs by one
+ * launch per graph of steps: the CTAs stay resident and take work items
+ * (RK stage, slab tile) from a queue in stage order; an item of stage g of
+ * slab s waits, on the device, until every item of stage g-1 of slab s is
+ * complete, so slabs of different lengths move through their stages
+ * independently instead of meeting at a grid-wide launch boundary after
+ * every stage.  Results are bit-identical to the launch-per-stage form.
+ * Every such wait is bounded: after spin_limit polls (each sleeps about
+ * 0.1 us; spin_limit <= 0: 2^23, about a second) the kernel records a timeout
+ * and all its CTAs return; the next synchronising call reports
+ * EVFDLB_E_TIMEOUT and the context refuses to step until init / set_state.
+ * enable = 0: back to one launch per RK stage.  Re-captures the step graphs
+ * and synchronises the stream.
+ * Errors: E_INVALID_ARG, E_UNSUPPORTED (dim = 2, FP32, FP64_DF, isothermal
+ * mode), E_OOM, E_CUDA. */
+evfdlb_status evfdlb_set_persistent(evfdlb_ctx* ctx, int32_t enable, int64_t spin_limit);
+
+/* Testing hook of the persistent form: with open = 0 every dependency wait
+ * also waits for a gate flag that nothing sets, so that each wait runs to
+ * its spin limit and the launch ends with EVFDLB_E_TIMEOUT (the bounded-wait
+ * path, exercised without faulting the GPU); open = 1 (the default)
+ * restores normal operation.  Synchronises the stream.  Errors:
+ * E_INVALID_ARG, E_STATE (the persistent form was never enabled), E_CUDA. */
+evfdlb_status evfdlb_debug_gate(evfdlb_ctx* ctx, int32_t open);
+
 /* Releases the context and its device memory (NULL is a no-op). */
 void evfdlb_destroy(evfdlb_ctx* ctx);
 

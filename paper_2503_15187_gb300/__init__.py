@@ -116,6 +116,8 @@ def lib():
             "evfdlb_probe_fp64_fma": (i32, [i32, vp, ctypes.POINTER(d)]),
             "evfdlb_divide_fp64": (i32, [vp, vp, vp, vp, i64, vp]),
             "evfdlb_profile_stage": (i32, [vp, i32]),
+            "evfdlb_set_persistent": (i32, [vp, i32, i64]),
+            "evfdlb_debug_gate": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -269,6 +271,17 @@ class Sim:
 
     def tile_nodes(self):
         return lib().evfdlb_tile_nodes(self.h)
+
+    def set_persistent(self, enable=True, spin_limit=0):
+        """The persistent form of the step (one launch per graph of steps,
+        per-slab stage dependencies waited on the device with bounded polls),
+        or back to one launch per RK stage."""
+        _check(lib().evfdlb_set_persistent(self.h, int(bool(enable)), int(spin_limit)), "evfdlb_set_persistent")
+
+    def debug_gate(self, open_):
+        """Testing hook: with open_ False every dependency wait of the
+        persistent form waits on a flag nothing sets (bounded-wait path)."""
+        _check(lib().evfdlb_debug_gate(self.h, int(bool(open_))), "evfdlb_debug_gate")
 
     def profile_stage(self, stage):
         """Queues stage 0, 1 or 2 of one step (as evfdlb_step runs it) on the

@@ -44,6 +44,9 @@ void launch_iso_reset_p(int prec, int nitems, size_t smem, cudaStream_t st, cons
 void launch_fields_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                      const WorkItem* items, const void* rtab, const double* taps, const void* rtaps,
                      const double* mom, double* fields, long long NN, int Z, unsigned* err);
+cudaError_t configure_persist(size_t smem_bytes);
+int persist_grid(size_t smem_bytes);
+void launch_persist(int grid, size_t smem, cudaStream_t st, const PersistArgs& a);
 void launch_convert_to_f32(cudaStream_t st, const double* in, float* out, long long n);
 void launch_convert_to_f64(cudaStream_t st, const float* in, double* out, long long n);
 void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
@@ -136,6 +139,13 @@ struct evfdlb_ctx {
     cudaStream_t aux = nullptr;            // the adjoint's recompute stream
     cudaEvent_t ev_fork = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_sweep[2] = {nullptr, nullptr};
     double* adj = nullptr;       // lam, y1, y2, acc [4][2 NF]; nadj [10 NN]; nbo [4 NN]; phis [NN]; phi [2 nbatch]
+    // persistent form of the step (evfdlb_set_persistent)
+    bool persistent = false;
+    long long spin_limit = 0;
+    unsigned* pq = nullptr;      // [0] queue head, [1] gate, [2 ..] completed items per slab
+    int* tiles_d = nullptr;      // work items per slab
+    std::vector<int> tiles_h;
+    int pgrid = 1;               // resident CTAs of the persistent kernel
 };
 
 namespace {
@@ -177,6 +187,8 @@ void free_ctx(evfdlb_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->aux) cudaStreamDestroy(c->aux);
     cudaFree(c->adj);
+    cudaFree(c->pq);
+    cudaFree(c->tiles_d);
     cudaFree(c->slabs);
     cudaFree(c->items);
     cudaFree(c->err);
@@ -196,6 +208,34 @@ void queue_stage(evfdlb_ctx* c, cudaStream_t st, const void* src, const void* ba
     else
         launch_stage_p(c->prec, n, c->smem, st, c->slabs, c->items, c->tables, c->rtables, c->taps, c->rtaps, src,
                        base, out, nullptr, mi, mo, c->NF, c->NN, a, b, 0, c->Z, c->err);
+}
+
+// Queues nsteps steps of every slab as one persistent launch (after zeroing
+// the queue head and the per-slab counters).
+void queue_persist(evfdlb_ctx* c, cudaStream_t st, int nsteps) {
+    cudaMemsetAsync(c->pq, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(c->pq + 2, 0, sizeof(unsigned) * c->nbatch, st);
+    PersistArgs a;
+    a.slabs = c->slabs;
+    a.items = c->items;
+    a.tiles = c->tiles_d;
+    a.tables = c->tables;
+    a.taps = c->taps;
+    for (int i = 0; i < 3; ++i) {
+        a.st[i] = (double*)c->state[i];
+        a.mom[i] = c->mom[i];
+    }
+    a.err = c->err;
+    a.queue = c->pq;
+    a.gate = c->pq + 1;
+    a.done = c->pq + 2;
+    a.NF = c->NF;
+    a.NN = c->NN;
+    a.spin_limit = c->spin_limit;
+    a.nitems = (int)c->items_h.size();
+    a.nstages = 3 * nsteps;
+    a.Z = c->Z;
+    launch_persist(c->pgrid, c->smem, st, a);
 }
 
 // Queues one time step (three stages) on stream st.
@@ -224,12 +264,16 @@ void partition(evfdlb_ctx* c, int Z) {
     c->smem = stage_smem_bytes_p(c->prec, c->Qmax, Z, c->Mmax);
     c->smem_df = stage_smem_bytes_df(c->Qmax, Z, c->Mmax);
     if (c->items_cap == 0) c->items_cap = (size_t)c->NN;
+    c->tiles_h.assign(c->nbatch, 0);
+    for (const WorkItem& w : c->items_h) ++c->tiles_h[w.slab];
 }
 
 evfdlb_status capture(evfdlb_ctx* c, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     TRY_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    for (int s = 0; s < steps; ++s) queue_step(c, c->cap);
+    if (c->persistent) queue_persist(c, c->cap, steps);
+    else
+        for (int s = 0; s < steps; ++s) queue_step(c, c->cap);
     cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaGraphInstantiate(out, g, 0);
@@ -247,6 +291,7 @@ evfdlb_status check_device(evfdlb_ctx* c) {
     if (h) {
         c->poisoned = true;
         TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
+        if (h & ERR_TIMEOUT) return EVFDLB_E_TIMEOUT;
         return (h & ERR_NONFINITE) ? EVFDLB_E_NONFINITE : EVFDLB_E_NEGATIVE;
     }
     return EVFDLB_OK;
@@ -768,7 +813,9 @@ evfdlb_status evfdlb_slab_info(const evfdlb_ctx* c, int32_t s, int32_t* nx, int3
     return EVFDLB_OK;
 }
 
-int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) { return c ? (c->c2 ? 12 : (c->iso ? 4 : 3)) : 0; }
+int32_t evfdlb_launches_per_step(const evfdlb_ctx* c) {
+    return c ? (c->c2 ? 12 : (c->persistent ? 1 : (c->iso ? 4 : 3))) : 0;
+}
 
 int32_t evfdlb_tile_nodes(const evfdlb_ctx* c) { return c ? (c->c2 ? 0 : c->Z) : 0; }
 
@@ -778,6 +825,12 @@ evfdlb_status evfdlb_tune(evfdlb_ctx* c, int32_t tile_nodes) {
     TRY_CUDA(cudaStreamSynchronize(c->user));
     partition(c, tile_nodes);
     TRY_CUDA(cudaMemcpy(c->items, c->items_h.data(), sizeof(WorkItem) * c->items_h.size(), cudaMemcpyHostToDevice));
+    if (c->tiles_d)
+        TRY_CUDA(cudaMemcpy(c->tiles_d, c->tiles_h.data(), sizeof(int) * c->nbatch, cudaMemcpyHostToDevice));
+    if (c->persistent) {
+        TRY_CUDA(configure_persist(c->smem));
+        c->pgrid = persist_grid(c->smem);
+    }
     if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
     if (c->g_one) cudaGraphExecDestroy(c->g_one);
     c->g_chunk = c->g_one = nullptr;
@@ -796,6 +849,44 @@ evfdlb_status evfdlb_profile_stage(evfdlb_ctx* c, int32_t stage) {
     else if (stage == 1) queue_stage(c, c->user, f1, f0, f2, m1, m2, 0.75, 0.25);
     else queue_stage(c, c->user, f2, f0, f1, m2, m1, 1.0 / 3.0, 2.0 / 3.0);   // the state stays untouched
     TRY_CUDA(cudaGetLastError());
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_set_persistent(evfdlb_ctx* c, int32_t enable, int64_t spin_limit) {
+    if (!c || (enable != 0 && enable != 1)) return EVFDLB_E_INVALID_ARG;
+    if (c->c2) return EVFDLB_E_UNSUPPORTED;
+    if (enable && (c->prec != EVFDLB_FP64 || c->df || c->iso)) return EVFDLB_E_UNSUPPORTED;
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    if (enable && !c->pq) {
+        TRY_CUDA(cudaMalloc((void**)&c->pq, sizeof(unsigned) * (2 + (size_t)c->nbatch)));
+        TRY_CUDA(cudaMalloc((void**)&c->tiles_d, sizeof(int) * (size_t)c->nbatch));
+        TRY_CUDA(cudaMemset(c->pq, 0, sizeof(unsigned) * (2 + (size_t)c->nbatch)));
+        const unsigned open = 1u;
+        TRY_CUDA(cudaMemcpy(c->pq + 1, &open, sizeof(unsigned), cudaMemcpyHostToDevice));
+    }
+    if (enable)
+        TRY_CUDA(cudaMemcpy(c->tiles_d, c->tiles_h.data(), sizeof(int) * c->nbatch, cudaMemcpyHostToDevice));
+    c->persistent = (enable == 1);
+    // about a second of polling by default (each poll sleeps ~0.1 us)
+    c->spin_limit = spin_limit > 0 ? spin_limit : (1LL << 23);
+    if (c->persistent) {
+        TRY_CUDA(configure_persist(c->smem));
+        c->pgrid = persist_grid(c->smem);
+    }
+    if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
+    if (c->g_one) cudaGraphExecDestroy(c->g_one);
+    c->g_chunk = c->g_one = nullptr;
+    evfdlb_status st = capture(c, 1, &c->g_one);
+    if (st == EVFDLB_OK) st = capture(c, c->chunk, &c->g_chunk);
+    return st;
+}
+
+evfdlb_status evfdlb_debug_gate(evfdlb_ctx* c, int32_t open) {
+    if (!c || (open != 0 && open != 1)) return EVFDLB_E_INVALID_ARG;
+    if (!c->pq) return EVFDLB_E_STATE;
+    const unsigned v = (unsigned)open;
+    TRY_CUDA(cudaStreamSynchronize(c->user));
+    TRY_CUDA(cudaMemcpy(c->pq + 1, &v, sizeof(unsigned), cudaMemcpyHostToDevice));
     return EVFDLB_OK;
 }
 

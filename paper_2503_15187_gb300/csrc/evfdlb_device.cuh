@@ -119,6 +119,14 @@ enum { SC_N = 0, SC_U, SC_T, SC_NU, SC_FORCE, SC_KQ, SC_K, SC_A, SC_B, SC_D };
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
+// Global load of data that other CTAs of the same launch may have written
+// (CG: cached in L2 only, never a stale L1 line), or an ordinary load.
+template <bool CG, typename T>
+__device__ __forceinline__ T gload(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic for the FP64_DF variant: a value is an unevaluated
 // pair of floats (hi, lo) with x = hi + lo to about 48 significant bits.  Sums of products use the compensated dot product Dot2
@@ -219,7 +227,9 @@ __device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b)
 // ---------------------------------------------------------------------------
 // PARITY: the parity-split tables Pp and Sp go to s.P and s.S in place of
 // the full analysis and synthesis tables.
-template <typename R, bool PARITY = false>
+// CG: the moment sums are read with L2-coherent loads (written earlier in
+// the same launch by other CTAs).
+template <typename R, bool PARITY = false, bool CG = false>
 __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                  const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
     const int Q = sd.Q, M = sd.M, nx = sd.nx, bc = sd.bc;
@@ -241,7 +251,7 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
 #pragma unroll 2
     for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {
-        double n = S0[gidx(it.i0 - M + t, nx, bc)];
+        double n = gload<CG>(S0 + gidx(it.i0 - M + t, nx, bc));
         s.N[t] = n;
         if constexpr (!std::is_same<R, double>::value) s.Nr[t] = (R)n;
     }
@@ -253,8 +263,8 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
         int i = gidx(it.i0 - 2 + t, nx, bc);
         const bool tile = (t >= 2 && t < it.nz + 2);
-        double n = S0[i], s1 = S1[i], s2 = S2[i], g0 = G0[i];
-        double s3 = tile ? S3[i] : 0.0, g1 = tile ? G1[i] : 0.0;
+        double n = gload<CG>(S0 + i), s1 = gload<CG>(S1 + i), s2 = gload<CG>(S2 + i), g0 = gload<CG>(G0 + i);
+        double s3 = tile ? gload<CG>(S3 + i) : 0.0, g1 = tile ? gload<CG>(G1 + i) : 0.0;
         double inv_n = div_nr(1.0, n);
         double u = s1 * inv_n;
         // (3/2) n T = sum (xi-u)^2/2 F + sum G = S2/2 + G0 - n u^2/2
@@ -299,18 +309,23 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // The state tile (+-3 nodes) into s.F by asynchronous copies, all of them in
 // flight at once; the caller waits (cp_async_wait_all) and synchronises
 // before reading it.
-template <typename R>
+// CG: L2-coherent loads instead of the (L1-allocating) copies, for data
+// written earlier in the same launch by other CTAs.
+template <typename R, bool CG = false>
 __device__ void issue_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                  const R* __restrict__ src, long long NF) {
     const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
     const int cols = it.nz + 6;
+#pragma unroll 4
     for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
         const int c = e % cols, r = e / cols;
         const int k = r % Q, d = r / Q;
         const int i = gidx(it.i0 - 3 + c, nx, bc);
-        cp_async_elem<R>(s.F + (size_t)r * W + c, src + d * NF + sd.f_off + (long long)k * nx + i);
+        const R* g = src + d * NF + sd.f_off + (long long)k * nx + i;
+        if constexpr (CG) s.F[(size_t)r * W + c] = __ldcg(g);
+        else cp_async_elem<R>(s.F + (size_t)r * W + c, g);
     }
-    cp_async_commit();
+    if constexpr (!CG) cp_async_commit();
 }
 
 // The parity-split interior columns EO[((d * 2 + par) * H + j) * Z + t] of

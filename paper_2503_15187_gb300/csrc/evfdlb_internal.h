@@ -35,7 +35,7 @@ constexpr int kNumScalars = 10;    // per-node scalars feeding the synthesis
 enum { MOM_S0 = 0, MOM_S1, MOM_S2, MOM_S3, MOM_G0, MOM_G1 };
 
 // Error bits latched by the kernels.
-enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u };
+enum : unsigned { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u, ERR_TIMEOUT = 4u };
 
 // Parity split of the Gauss-Hermite transforms.  The nodes are symmetric,
 // xi_{Q-1-j} = -xi_j (w likewise), and psi_l(-x) = (-1)^l psi_l(x), so with
@@ -102,6 +102,25 @@ struct SlabDesc {
 // One CTA's share of work: nodes [i0, i0 + nz) of slab `slab`.
 struct WorkItem {
     int slab, i0, nz, pad;
+};
+
+// Arguments of the persistent step (by value): nsteps Shu-Osher steps of
+// every slab as 3 nsteps x nitems queued work items.
+struct PersistArgs {
+    const SlabDesc* slabs;
+    const WorkItem* items;   // the work list, one entry per slab tile
+    const int* tiles;        // work items per slab
+    const double* tables;
+    const double* taps;
+    double* st[3];           // u, u1, u2: [2][NF] each
+    double* mom[3];          // their raw moment sums [6][NN]
+    unsigned* err;           // error word (ERR_* bits)
+    unsigned* queue;         // next work item (zeroed before the launch)
+    unsigned* done;          // completed items per slab (zeroed before the launch)
+    const unsigned* gate;    // 1: open; 0: every wait waits on a flag nothing sets
+    long long NF, NN;
+    long long spin_limit;    // polls of a dependency wait before it gives up
+    int nitems, nstages, Z;
 };
 
 // ---- host model code (host_model.cpp) ----

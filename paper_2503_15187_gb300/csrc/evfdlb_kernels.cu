@@ -54,17 +54,17 @@ namespace evfdlb {
 // the FP64 `tables`; the Hermite analysis and synthesis run as Dot2 sums of
 // pairs on the FP32 pipe (state tile split into pairs once per stage in a
 // block after the Hermite moments), everything else as in the FP64 kernel.
-template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
-__global__ void __launch_bounds__(T, DF ? 3 : (std::is_same<R, double>::value ? 2 : 1))
-stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-             const double* __restrict__ tables, const R* __restrict__ rtab,
-             const double* __restrict__ taps, const R* __restrict__ rtaps,
-             const R* __restrict__ src, const R* base, R* out, double* rhs_out,
-             const double* __restrict__ mom_in, double* __restrict__ mom_out,
-             long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    extern __shared__ __align__(16) double smem[];
-    const WorkItem it = items[blockIdx.x];
-    const SlabDesc sd = slabs[it.slab];
+//
+// The body runs one work item (slab tile) with the CTA's threads; CG: the
+// stage input, base and moment sums are read with L2-coherent loads (the
+// persistent form, where other CTAs of the same launch wrote them).
+template <typename R, bool DF, bool CG>
+__device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& it, double* smem,
+                                           const double* __restrict__ tables, const R* __restrict__ rtab,
+                                           const double* __restrict__ taps, const R* __restrict__ rtaps,
+                                           const R* src, const R* base, R* out, double* rhs_out,
+                                           const double* mom_in, double* mom_out, long long NF, long long NN,
+                                           double alpha, double beta, int mode, int Z, unsigned* err) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     Smem<R> s = carve<R>(smem, Q, Z, sd.M);
 
@@ -74,8 +74,8 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
     // (FP64 / FP32: the tile by asynchronous copies, issued first, so that
     // they are in flight with the node inputs' loads and arithmetic)
     float2* Fd = DF ? reinterpret_cast<float2*>(s.EO) : nullptr;
-    if constexpr (!DF) issue_state_tile<R>(sd, it, s, Z, src, NF);
-    load_node_inputs<R, !DF>(sd, it, s, Z, rtab, mom_in, NN);
+    if constexpr (!DF) issue_state_tile<R, CG>(sd, it, s, Z, src, NF);
+    load_node_inputs<R, !DF, CG>(sd, it, s, Z, rtab, mom_in, NN);
     if constexpr (DF) load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
     // the slab's force and Fischer-Methfessel taps, read in warp 0's serial
     // tap loops, staged once into shared memory
@@ -87,7 +87,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
         const int xo = sd.tab_off + TableLayout(Q).xi;
         velocity_powers<R>(Q, tables + xo, vt + xo, s.Vp, s.Vr, threadIdx.x, blockDim.x);
     }
-    if constexpr (!DF) cp_async_wait_all();
+    if constexpr (!DF && !CG) cp_async_wait_all();
     __syncthreads();
     // The node warps form the node-level quantities of the tile (node fields,
     // coefficient constants, Hermite moments of the local Gaussian) while the
@@ -185,7 +185,7 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
             for (int q = 0; q < VK; ++q)
                 if (q < nk)
                     emit(d, t, k0 + q, df_join(a[q], b[q]), ch, csx * xi[k0 + q],
-                         (with_base && !rhs_form) ? base[gidx_of(d, t, k0 + q)] : R(0));
+                         (with_base && !rhs_form) ? gload<CG>(base + gidx_of(d, t, k0 + q)) : R(0));
         }
     } else {
         // parity split: one node pair (k, Q-1-k) per task; even orders build
@@ -201,8 +201,8 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
             const R* c = s.C + (size_t)d * Q * Z + t;
             const R2* sp = Sp + (size_t)k * QE2;
             const bool pair = (Q - 1 - k != k), lb = with_base && !rhs_form;
-            const R b0 = lb ? base[gidx_of(d, t, k)] : R(0);
-            const R b1 = (lb && pair) ? base[gidx_of(d, t, Q - 1 - k)] : R(0);
+            const R b0 = lb ? gload<CG>(base + gidx_of(d, t, k)) : R(0);
+            const R b1 = (lb && pair) ? gload<CG>(base + gidx_of(d, t, Q - 1 - k)) : R(0);
             R ev = 0, od = 0;
             int l = 0;
             for (; l + 1 < Q; l += 2) {
@@ -221,6 +221,106 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
 
     // Phase 6: raw moment sums of the new stage for the next stage's node fields.
     tile_moment_sums_staged<R>(sd, it, s, Z, s.Vp, s.Vr, mom_out, NN);
+}
+
+template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
+__global__ void __launch_bounds__(T, DF ? 3 : (std::is_same<R, double>::value ? 2 : 1))
+stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+             const double* __restrict__ tables, const R* __restrict__ rtab,
+             const double* __restrict__ taps, const R* __restrict__ rtaps,
+             const R* __restrict__ src, const R* base, R* out, double* rhs_out,
+             const double* __restrict__ mom_in, double* __restrict__ mom_out,
+             long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
+    extern __shared__ __align__(16) double smem[];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    stage_body<R, DF, false>(sd, it, smem, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF,
+                             NN, alpha, beta, mode, Z, err);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of the step for a batch of independent slabs (FP64): one
+// launch advances every slab by nsteps Shu-Osher steps.  The CTAs stay
+// resident and pull work items (stage, slab tile) from a queue in stage
+// order; an item of global stage g of slab b starts once every item of stage
+// g-1 of that slab has completed (a per-slab counter of completed items,
+// released after the item's writes and acquired before its reads), so slabs
+// proceed independently and a short slab does not wait at the stage
+// boundaries of a long one.  An item only ever waits for items dequeued
+// before it, by CTAs that are running: the queue cannot deadlock, whatever
+// the number of resident CTAs.  Every wait is bounded: after spin_limit polls
+// the CTA sets ERR_TIMEOUT, and every CTA leaves at its next dequeue; nothing
+// traps.  Data written in the same launch are read with L2-coherent loads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(StageThreads<double>::value, 2) persist_kernel(PersistArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int s_q, s_stop;
+    const int total = a.nstages * a.nitems;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int stop = (ld_acquire_u32(a.err) & ERR_TIMEOUT) ? 1 : 0;
+            const int q = stop ? total : (int)atomicAdd(a.queue, 1u);
+            if (q < total) {
+                const int g = q / a.nitems, b = a.items[q % a.nitems].slab;
+                const unsigned need = (unsigned)g * (unsigned)a.tiles[b];
+                long long polls = 0;
+                while (ld_acquire_u32(a.gate) == 0u || ld_acquire_u32(a.done + b) < need) {
+                    if (++polls > a.spin_limit) {
+                        atomicOr(a.err, ERR_TIMEOUT);
+                        stop = 1;
+                        break;
+                    }
+                    if (ld_acquire_u32(a.err) & ERR_TIMEOUT) {   // another CTA gave up
+                        stop = 1;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            s_q = q;
+            s_stop = stop || q >= total;
+        }
+        __syncthreads();
+        if (s_stop) return;
+        const int q = s_q, g = q / a.nitems, stage = g % 3;
+        const WorkItem it = a.items[q % a.nitems];
+        const SlabDesc sd = a.slabs[it.slab];
+        // stage 0: u1 = u + dt L(u); 1: u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+        // 2: u = 1/3 u + 2/3 (u2 + dt L(u2)), over u
+        const double* src = a.st[stage];
+        const double* base = stage == 0 ? nullptr : a.st[0];
+        double* out = a.st[(stage + 1) % 3];
+        const double alpha = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+        const double beta = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+        stage_body<double, false, true>(sd, it, smem, a.tables, a.tables, a.taps, a.taps, src, base, out, nullptr,
+                                        a.mom[stage], a.mom[(stage + 1) % 3], a.NF, a.NN, alpha, beta, 0, a.Z, a.err);
+        __threadfence();                               // this thread's writes, before the release
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(a.done + it.slab, 1u);
+    }
+}
+
+cudaError_t configure_persist(size_t smem_bytes) {
+    return cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+// Resident CTAs of the persistent kernel on the current device (at least one).
+int persist_grid(size_t smem_bytes) {
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_kernel, StageThreads<double>::value, smem_bytes);
+    return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
+void launch_persist(int grid, size_t smem, cudaStream_t st, const PersistArgs& a) {
+    persist_kernel<<<grid, StageThreads<double>::value, smem, st>>>(a);
 }
 
 // Projected Maxwellian pair (F_MB, T F_MB) from node fields, formed in FP64 and
