@@ -58,7 +58,21 @@ typedef enum {
     EVFDLB_E_UNSUPPORTED = -8  /* valid request this build does not implement    */
 } evfdlb_status;
 
-enum { EVFDLB_BC_PERIODIC = 0, EVFDLB_BC_OUTFLOW = 1 };
+/* Boundary of a slab.  PERIODIC: the slab wraps.  OUTFLOW: ghost nodes copy
+ * the nearest interior node.  HALO: the slab is one rank's part of a larger
+ * z-split domain; its first and last G = evfdlb_halo_width(params) of the nx
+ * nodes are ghost nodes that only the caller's halo exchange writes
+ * (evfdlb_halo_pack / evfdlb_halo_unpack), and each RK stage (evfdlb_stage)
+ * updates the interior nodes alone.  HALO_OUTFLOW_LO / _HI: the same, for the
+ * first / last part of a split OUTFLOW slab: that end has no ghost band and
+ * is the slab's outflow boundary (node 0 / nx-1 is a boundary node). */
+enum {
+    EVFDLB_BC_PERIODIC = 0,
+    EVFDLB_BC_OUTFLOW = 1,
+    EVFDLB_BC_HALO = 2,
+    EVFDLB_BC_HALO_OUTFLOW_LO = 3,
+    EVFDLB_BC_HALO_OUTFLOW_HI = 4
+};
 /* Precision.  FP64: every step in FP64.  FP32: FP32 state and per-velocity
  * work, FP64 chi / transport / gradients / conserved sums.  FP64_DF: FP64
  * state and FP64 arithmetic except the Hermite analysis and synthesis of the
@@ -103,7 +117,7 @@ typedef struct {
     double  gamma;        /* tail exponent (> 3), Eq. (sutherland)                     */
     double  r_cut;        /* EV1: cut of the Eq. (F1) integral (>= sigma + 2dx)        */
     int32_t Q;            /* Gauss-Hermite order, 4 <= Q <= 32                         */
-    int32_t bc;           /* EVFDLB_BC_PERIODIC or EVFDLB_BC_OUTFLOW                   */
+    int32_t bc;           /* EVFDLB_BC_* (above)                                       */
     int32_t precision;    /* EVFDLB_FP64, EVFDLB_FP32 or EVFDLB_FP64_DF (see above);   */
                           /* one precision per context (the ABI stays float64)         */
     int32_t force_model;  /* EVFDLB_EV1 or EVFDLB_EV2 (see above)                      */
@@ -291,7 +305,8 @@ evfdlb_status evfdlb_adjoint(evfdlb_ctx* ctx, const double* dL_dn_end, int32_t o
  * cuda_stream (a cudaStream_t, NULL = the legacy default stream); every call
  * copies its small parameter block from static host memory and synchronises
  * that stream before it returns, to read the error word.
- * Errors: E_INVALID_ARG, E_UNSUPPORTED, E_NONFINITE, E_NEGATIVE, E_CUDA (also
+ * Errors: E_INVALID_ARG, E_UNSUPPORTED (precision other than FP64, or bc =
+ * EVFDLB_BC_HALO), E_NONFINITE, E_NEGATIVE, E_CUDA (also
  * when a CUDA error is already pending in the calling thread: it is returned,
  * not cleared, and nothing is queued). */
 #define EVFDLB_STATIC_MAX_NODES 8192
@@ -352,6 +367,63 @@ evfdlb_status evfdlb_set_persistent(evfdlb_ctx* ctx, int32_t enable, int64_t spi
  * restores normal operation.  Synchronises the stream.  Errors:
  * E_INVALID_ARG, E_STATE (the persistent form was never enabled), E_CUDA. */
 evfdlb_status evfdlb_debug_gate(evfdlb_ctx* ctx, int32_t open);
+
+/* --- z-split slab (domain decomposition across ranks) ---------------------
+ * The method is an explicit stencil in z (Sec. III): one RK stage of a node
+ * reads F and G over +-3 nodes (WENO-5) and the density sums over +-M nodes
+ * (the Eq. (F1) integral; M = r_cut/dx for EV1).  A slab is split along z by
+ * giving each rank a context with bc = EVFDLB_BC_HALO over its part plus G
+ * ghost nodes per side, and by exchanging, before every RK stage, one
+ * message per side with each neighbour:
+ *   init (ghost entries of n0, u0, T0 are ignored; ghosts hold 0)
+ *   repeat: pack -> exchange -> unpack -> evfdlb_stage(s), s = 0, 1, 2
+ * where the message a rank sends to its left neighbour becomes that
+ * neighbour's from_right (and the right-going one its from_left).  A
+ * periodic slab splits into HALO parts on a ring; an outflow slab into
+ * HALO_OUTFLOW_LO (first part), HALO (middle parts) and HALO_OUTFLOW_HI
+ * (last part) on a line.  The interior nodes then evolve bit-identically to
+ * the same nodes of the unsplit slab.  evfdlb_step and evfdlb_rhs return E_UNSUPPORTED for a HALO
+ * context; moments / totals cover its interior nodes for the totals, every
+ * node for the per-node fields. */
+
+/* Ghost nodes per side of a HALO slab with these parameters:
+ * max(3, force half-width), or -1 when the parameters fail validation or
+ * dim != 1.  A split part needs at least G interior nodes besides its ghost
+ * bands (nx >= 3 G for HALO, nx >= 2 G for the outflow ends). */
+int32_t evfdlb_halo_width(const evfdlb_params* params);
+
+/* Length, in doubles, of one halo message of this context:
+ * 6 Q + 6 G (F and G over 3 columns, the six raw moment sums over G columns,
+ * FP64 whatever the state precision); 0 for a context that is not HALO. */
+int64_t evfdlb_halo_len(const evfdlb_ctx* ctx);
+
+/* Runs RK stage `stage` (0, 1, 2 of the Shu-Osher step) of every slab,
+ * queued on the context's stream without synchronising (errors in the
+ * kernels show at the next synchronising call).  Stages must come in order,
+ * starting at 0 after init / set_state; after stage 2 the state is one step
+ * further, exactly as evfdlb_step(ctx, 1) leaves it.  Works for every 1D
+ * context; the only way to advance a HALO context.  Errors: E_INVALID_ARG,
+ * E_STATE (no state, poisoned, or stage out of order), E_UNSUPPORTED (dim 2,
+ * or ckpt_every > 0), E_CUDA. */
+evfdlb_status evfdlb_stage(evfdlb_ctx* ctx, int32_t stage);
+
+/* Writes the two halo messages of the state the next stage reads, with
+ * lo / hi the ghost nodes below / above the interior (G, or 0 at an outflow
+ * end): to_left from the first interior nodes (F, G at nodes lo .. lo+2,
+ * moments at lo .. lo+G-1), to_right from the last ones (F, G at
+ * nx-hi-3 .. nx-hi-1, moments at nx-hi-G .. nx-hi-1).  Both are device
+ * buffers of evfdlb_halo_len(ctx) doubles owned by the caller; the one of an
+ * outflow end is not touched and may be NULL.  Queued on the context's
+ * stream.  Errors: E_INVALID_ARG, E_UNSUPPORTED (not HALO), E_STATE, E_CUDA. */
+evfdlb_status evfdlb_halo_pack(evfdlb_ctx* ctx, double* to_left, double* to_right);
+
+/* Writes the neighbours' messages into the ghost nodes of the state the next
+ * stage reads: from_left (the left neighbour's to_right) into F, G at nodes
+ * lo-3 .. lo-1 and moments at lo-G .. lo-1; from_right (the right
+ * neighbour's to_left) into F, G at nx-hi .. nx-hi+2 and moments at
+ * nx-hi .. nx-hi+G-1.  Device buffers as for pack (NULL at an outflow end);
+ * queued on the context's stream.  Errors as pack. */
+evfdlb_status evfdlb_halo_unpack(evfdlb_ctx* ctx, const double* from_left, const double* from_right);
 
 /* Releases the context and its device memory (NULL is a no-op). */
 void evfdlb_destroy(evfdlb_ctx* ctx);

@@ -22,7 +22,7 @@ EVFDLB_NFIELDS = 16
 FIELD_NAMES = ("n", "u", "T", "q", "nbar", "chi", "force", "mu", "tau", "Pr",
                "nu", "A", "B", "D", "X", "bnchi")
 
-BC_PERIODIC, BC_OUTFLOW = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_HALO, BC_HALO_OUTFLOW_LO, BC_HALO_OUTFLOW_HI = 0, 1, 2, 3, 4
 FP64, FP32, FP64_DF = 0, 1, 2
 EV1, EV2 = 0, 1
 RELAX_INV_TAU, RELAX_CHI_OVER_TAU = 0, 1
@@ -118,6 +118,11 @@ def lib():
             "evfdlb_profile_stage": (i32, [vp, i32]),
             "evfdlb_set_persistent": (i32, [vp, i32, i64]),
             "evfdlb_debug_gate": (i32, [vp, i32]),
+            "evfdlb_halo_width": (i32, [P]),
+            "evfdlb_halo_len": (i64, [vp]),
+            "evfdlb_stage": (i32, [vp, i32]),
+            "evfdlb_halo_pack": (i32, [vp, vp, vp]),
+            "evfdlb_halo_unpack": (i32, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -188,6 +193,15 @@ def step_static(p: Params, state, nsteps: int = 1, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().evfdlb_step_static(ctypes.byref(p.c()), ptr, int(nsteps), ctypes.c_void_p(s.cuda_stream)),
            "evfdlb_step_static")
+
+
+def halo_width(p: Params) -> int:
+    """Ghost nodes per side of a z-split (BC_HALO) slab with parameters p:
+    the widest read of one RK stage about a node (host computation)."""
+    g = lib().evfdlb_halo_width(ctypes.byref(p.c()))
+    if g < 0:
+        raise ValueError("invalid parameters")
+    return g
 
 
 def probe_fp64_fma(reps: int = 5, stream=None) -> float:
@@ -282,6 +296,37 @@ class Sim:
         """Testing hook: with open_ False every dependency wait of the
         persistent form waits on a flag nothing sets (bounded-wait path)."""
         _check(lib().evfdlb_debug_gate(self.h, int(bool(open_))), "evfdlb_debug_gate")
+
+    def stage(self, s):
+        """Queues RK stage s (0, 1, 2 in order) of one step."""
+        _check(lib().evfdlb_stage(self.h, int(s)), "evfdlb_stage")
+
+    def halo_len(self):
+        return int(lib().evfdlb_halo_len(self.h))
+
+    def _halo_ptrs(self, a, b):
+        """Device pointers of two halo messages (None: the side of an outflow
+        end, which the library skips)."""
+        n = self.halo_len()
+        out = []
+        for x in (a, b):
+            if x is None:
+                out.append(None)
+                continue
+            p, dev = _ptr(x)
+            if not dev or x.numel() != n:
+                raise ValueError(f"halo messages are CUDA float64 tensors of {n} values")
+            out.append(p)
+        return out
+
+    def halo_pack(self, to_left, to_right):
+        """Edge columns of the state the next stage reads into two CUDA
+        float64 tensors of halo_len() values (queued on the stream)."""
+        _check(lib().evfdlb_halo_pack(self.h, *self._halo_ptrs(to_left, to_right)), "evfdlb_halo_pack")
+
+    def halo_unpack(self, from_left, from_right):
+        """The neighbours' messages into the ghost nodes (queued on the stream)."""
+        _check(lib().evfdlb_halo_unpack(self.h, *self._halo_ptrs(from_left, from_right)), "evfdlb_halo_unpack")
 
     def profile_stage(self, stage):
         """Queues stage 0, 1 or 2 of one step (as evfdlb_step runs it) on the

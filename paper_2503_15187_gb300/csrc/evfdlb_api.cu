@@ -48,6 +48,11 @@ cudaError_t configure_persist(size_t smem_bytes);
 int persist_grid(size_t smem_bytes);
 void launch_persist(int grid, size_t smem, cudaStream_t st, const PersistArgs& a);
 void launch_convert_to_f32(cudaStream_t st, const double* in, float* out, long long n);
+long long halo_message_len(int Q, int G);
+void launch_halo_pack(int prec, cudaStream_t st, const void* state, const double* mom, long long NF, long long NN,
+                      int nx, int Q, int G, int lo, int hi, double* to_left, double* to_right);
+void launch_halo_unpack(int prec, cudaStream_t st, void* state, double* mom, long long NF, long long NN, int nx, int Q,
+                        int G, int lo, int hi, const double* from_left, const double* from_right);
 void launch_convert_to_f64(cudaStream_t st, const float* in, double* out, long long n);
 void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n, double* u, double* T,
                     double* q);
@@ -125,6 +130,12 @@ struct evfdlb_ctx {
     bool poisoned = false;
     bool iso = false;            // some slab has T_iso > 0 (reset after every step)
     bool df = false;             // FP64_DF: FP64 context whose stages use double-float transforms
+    // z-split slab (EVFDLB_BC_HALO): G ghost nodes per side, and the RK stage
+    // that evfdlb_stage runs next (0 after init / set_state / a whole step)
+    bool halo = false;
+    int halo_G = 0;
+    int halo_lo = 0, halo_hi = 0;   // ghost nodes below / above the interior (0: an outflow end)
+    int rk_next = 0;
     double* dftables = nullptr;  // analysis / synthesis tables as float pairs (FP64_DF)
     size_t smem_df = 0;          // stage shared memory of the FP64_DF kernel
     // adjoint: checkpoints of the trajectory since the last init / set_state
@@ -258,9 +269,11 @@ void queue_step(evfdlb_ctx* c, cudaStream_t st) {
 void partition(evfdlb_ctx* c, int Z) {
     c->Z = Z;
     c->items_h.clear();
-    for (int s = 0; s < c->nbatch; ++s)
-        for (int i0 = 0; i0 < c->params[s].nx; i0 += Z)
-            c->items_h.push_back(WorkItem{s, i0, std::min(Z, c->params[s].nx - i0), 0});
+    for (int s = 0; s < c->nbatch; ++s) {
+        // a HALO slab's work covers its interior nodes alone
+        const int lo = c->halo_lo, hi = c->params[s].nx - c->halo_hi;
+        for (int i0 = lo; i0 < hi; i0 += Z) c->items_h.push_back(WorkItem{s, i0, std::min(Z, hi - i0), 0});
+    }
     c->smem = stage_smem_bytes_p(c->prec, c->Qmax, Z, c->Mmax);
     c->smem_df = stage_smem_bytes_df(c->Qmax, Z, c->Mmax);
     if (c->items_cap == 0) c->items_cap = (size_t)c->NN;
@@ -455,11 +468,16 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         if (ps[s].precision != EVFDLB_FP64 && ps[s].precision != EVFDLB_FP32 && ps[s].precision != EVFDLB_FP64_DF)
             return EVFDLB_E_INVALID_ARG;
         if (ps[s].precision != ps[0].precision) return EVFDLB_E_INVALID_ARG;   // one precision per context
+        if (is_halo_bc(ps[s].bc) && nbatch != 1) return EVFDLB_E_UNSUPPORTED;   // one split slab per context
     }
     evfdlb_ctx* c = new (std::nothrow) evfdlb_ctx();
     if (!c) return EVFDLB_E_OOM;
     c->nbatch = nbatch;
     c->params = ps;
+    c->halo = is_halo_bc(ps[0].bc);
+    c->halo_G = c->halo ? halo_width(ps[0]) : 0;
+    c->halo_lo = (c->halo && ps[0].bc != EVFDLB_BC_HALO_OUTFLOW_LO) ? c->halo_G : 0;
+    c->halo_hi = (c->halo && ps[0].bc != EVFDLB_BC_HALO_OUTFLOW_HI) ? c->halo_G : 0;
     c->user = (cudaStream_t)cuda_stream;
     c->df = (ps[0].precision == EVFDLB_FP64_DF);
     c->prec = c->df ? EVFDLB_FP64 : ps[0].precision;   // FP64_DF is an FP64 context but for its stages
@@ -492,7 +510,9 @@ evfdlb_status evfdlb_create(const evfdlb_params* p, int32_t nbatch, const evfdlb
         memset(&d, 0, sizeof(d));
         d.nx = q.nx;
         d.Q = q.Q;
-        d.bc = q.bc;
+        // a split slab reads with the outflow rule: inside a ghost band the
+        // clamp never acts, and at an outflow end it is that end's boundary
+        d.bc = is_halo_bc(q.bc) ? EVFDLB_BC_OUTFLOW : q.bc;
         d.relax = q.relax_mode;
         d.M = force_halfwidth(q);
         d.m = tap_halfwidth(q.sigma, q.dx);
@@ -624,6 +644,13 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
         dT = buf + 2 * c->NN;
     }
     TRY_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->user));
+    if (c->halo) {   // ghost columns hold zeros until the first exchange
+        const size_t es = (c->prec == EVFDLB_FP32) ? sizeof(float) : sizeof(double);
+        for (int i = 0; i < 3; ++i) {
+            TRY_CUDA(cudaMemsetAsync(c->state[i], 0, es * 2 * c->NF, c->user));
+            TRY_CUDA(cudaMemsetAsync(c->mom[i], 0, sizeof(double) * kNumMoments * c->NN, c->user));
+        }
+    }
     launch_init_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->rtables, dn,
                   du, dT, c->state[0], c->mom[0], c->NF, c->NN, c->Z, c->err);
     TRY_CUDA(cudaGetLastError());
@@ -633,6 +660,7 @@ evfdlb_status evfdlb_init(evfdlb_ctx* c, const double* n0, const double* u0, con
         TRY_CUDA(cudaMemcpyAsync(c->init_fields + 2 * c->NN, dT, bytes, cudaMemcpyDeviceToDevice, c->user));
     }
     c->steps = 0;
+    c->rk_next = 0;
     c->origin_init = true;
     c->poisoned = false;
     evfdlb_status s = check_device(c);
@@ -647,6 +675,8 @@ evfdlb_status evfdlb_step_async(evfdlb_ctx* c, int64_t nsteps) {
         return step_async_2d(c->c2, nsteps);
     }
     if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
+    if (c->halo) return EVFDLB_E_UNSUPPORTED;   // a split slab advances by evfdlb_stage + halo exchange
+    if (c->rk_next != 0) return EVFDLB_E_STATE;   // a step started by evfdlb_stage is unfinished
     while (nsteps > 0) {
         int64_t n = nsteps;
         if (c->ckpt_every > 0) {
@@ -725,6 +755,7 @@ evfdlb_status evfdlb_set_state(evfdlb_ctx* c, const double* F, const double* G, 
                   c->mom[0], c->NF, c->NN, c->err);
     TRY_CUDA(cudaGetLastError());
     c->steps = 0;
+    c->rk_next = 0;
     c->origin_init = false;
     c->poisoned = false;
     c->have_state = true;
@@ -739,6 +770,7 @@ evfdlb_status evfdlb_rhs(evfdlb_ctx* c, double* RF, double* RG, int32_t on_devic
     if (!c || !RF || !RG) return EVFDLB_E_INVALID_ARG;
     if (c->c2) return c->c2_state ? rhs_2d(c->c2, RF, RG, on_device) : EVFDLB_E_STATE;
     if (!c->have_state) return EVFDLB_E_STATE;
+    if (c->halo) return EVFDLB_E_UNSUPPORTED;
     if (c->df)
         launch_stage_df((int)c->items_h.size(), c->smem_df, c->user, c->slabs, c->items, c->tables, c->dftables,
                         c->taps, (const double*)c->state[0], nullptr, nullptr, c->scratch, c->mom[0], nullptr, c->NF,
@@ -855,7 +887,7 @@ evfdlb_status evfdlb_profile_stage(evfdlb_ctx* c, int32_t stage) {
 evfdlb_status evfdlb_set_persistent(evfdlb_ctx* c, int32_t enable, int64_t spin_limit) {
     if (!c || (enable != 0 && enable != 1)) return EVFDLB_E_INVALID_ARG;
     if (c->c2) return EVFDLB_E_UNSUPPORTED;
-    if (enable && (c->prec != EVFDLB_FP64 || c->df || c->iso)) return EVFDLB_E_UNSUPPORTED;
+    if (enable && (c->prec != EVFDLB_FP64 || c->df || c->iso || c->halo)) return EVFDLB_E_UNSUPPORTED;
     TRY_CUDA(cudaStreamSynchronize(c->user));
     if (enable && !c->pq) {
         TRY_CUDA(cudaMalloc((void**)&c->pq, sizeof(unsigned) * (2 + (size_t)c->nbatch)));
@@ -887,6 +919,60 @@ evfdlb_status evfdlb_debug_gate(evfdlb_ctx* c, int32_t open) {
     const unsigned v = (unsigned)open;
     TRY_CUDA(cudaStreamSynchronize(c->user));
     TRY_CUDA(cudaMemcpy(c->pq + 1, &v, sizeof(unsigned), cudaMemcpyHostToDevice));
+    return EVFDLB_OK;
+}
+
+int32_t evfdlb_halo_width(const evfdlb_params* p) {
+    if (!p || p->dim != 1 || !validate(*p, nullptr)) return -1;
+    return halo_width(*p);
+}
+
+int64_t evfdlb_halo_len(const evfdlb_ctx* c) {
+    return (c && c->halo) ? halo_message_len(c->params[0].Q, c->halo_G) : 0;
+}
+
+evfdlb_status evfdlb_stage(evfdlb_ctx* c, int32_t stage) {
+    if (!c || stage < 0 || stage > 2) return EVFDLB_E_INVALID_ARG;
+    if (c->c2 || c->ckpt_every > 0) return EVFDLB_E_UNSUPPORTED;
+    if (!c->have_state || c->poisoned || stage != c->rk_next) return EVFDLB_E_STATE;
+    void *f0 = c->state[0], *f1 = c->state[1], *f2 = c->state[2];
+    double *m0 = c->mom[0], *m1 = c->mom[1], *m2 = c->mom[2];
+    // the three stages of queue_step, one per call
+    if (stage == 0) queue_stage(c, c->user, f0, nullptr, f1, m0, m1, 0.0, 1.0);
+    else if (stage == 1) queue_stage(c, c->user, f1, f0, f2, m1, m2, 0.75, 0.25);
+    else {
+        queue_stage(c, c->user, f2, f0, f0, m2, m0, 1.0 / 3.0, 2.0 / 3.0);
+        if (c->iso)
+            launch_iso_reset_p(c->prec, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables,
+                               c->rtables, f0, m0, c->NF, c->NN, c->Z);
+        ++c->steps;
+    }
+    TRY_CUDA(cudaGetLastError());
+    c->rk_next = (stage + 1) % 3;
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_halo_pack(evfdlb_ctx* c, double* to_left, double* to_right) {
+    if (!c) return EVFDLB_E_INVALID_ARG;
+    if (!c->halo) return EVFDLB_E_UNSUPPORTED;
+    if ((c->halo_lo && !to_left) || (c->halo_hi && !to_right)) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
+    const int b = c->rk_next;   // the buffers the next stage reads
+    launch_halo_pack(c->prec, c->user, c->state[b], c->mom[b], c->NF, c->NN, c->params[0].nx, c->params[0].Q,
+                     c->halo_G, c->halo_lo, c->halo_hi, to_left, to_right);
+    TRY_CUDA(cudaGetLastError());
+    return EVFDLB_OK;
+}
+
+evfdlb_status evfdlb_halo_unpack(evfdlb_ctx* c, const double* from_left, const double* from_right) {
+    if (!c) return EVFDLB_E_INVALID_ARG;
+    if (!c->halo) return EVFDLB_E_UNSUPPORTED;
+    if ((c->halo_lo && !from_left) || (c->halo_hi && !from_right)) return EVFDLB_E_INVALID_ARG;
+    if (!c->have_state || c->poisoned) return EVFDLB_E_STATE;
+    const int b = c->rk_next;
+    launch_halo_unpack(c->prec, c->user, c->state[b], c->mom[b], c->NF, c->NN, c->params[0].nx, c->params[0].Q,
+                       c->halo_G, c->halo_lo, c->halo_hi, from_left, from_right);
+    TRY_CUDA(cudaGetLastError());
     return EVFDLB_OK;
 }
 

@@ -130,6 +130,8 @@ void build_tables(int Q, const double* xi, const double* w, double* out);  // Ta
 bool validate(const evfdlb_params& p, const char** why);
 int tap_halfwidth(double len, double dx);                        // len/dx if integral, else -1
 int force_halfwidth(const evfdlb_params& p);                     // force/energy taps and density halo
+int halo_width(const evfdlb_params& p);                          // ghost nodes per side of a HALO slab
+inline bool is_halo_bc(int bc) { return bc >= EVFDLB_BC_HALO && bc <= EVFDLB_BC_HALO_OUTFLOW_HI; }
 int fill_taps(const evfdlb_params& p, double* out, int cap);     // force, fm, energy; no heap
 void build_taps(const evfdlb_params& p, std::vector<double>& out);  // force, fm, energy
 double ev2_a(const evfdlb_params& p);                            // Eq. (F2) a

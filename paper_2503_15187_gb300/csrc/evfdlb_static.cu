@@ -88,6 +88,7 @@ extern "C" evfdlb_status evfdlb_step_static(const evfdlb_params* p, double* stat
     if (!p || !state || nsteps < 0) return EVFDLB_E_INVALID_ARG;
     if (!validate(*p, nullptr)) return EVFDLB_E_INVALID_ARG;
     if (p->precision != EVFDLB_FP64) return EVFDLB_E_UNSUPPORTED;
+    if (p->bc == EVFDLB_BC_HALO) return EVFDLB_E_UNSUPPORTED;   // needs a halo exchange between stages
     if (p->nx > kMaxNodes || (long long)p->Q * p->nx > kMaxElems) return EVFDLB_E_INVALID_ARG;
     const int M = force_halfwidth(*p);
     if (M > kMaxHalfWidth) return EVFDLB_E_INVALID_ARG;

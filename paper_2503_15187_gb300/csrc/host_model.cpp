@@ -6,6 +6,7 @@
 // Paper: Busuioc & Sofonea, arXiv:2503.15187.  Equations cited by label.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "evfdlb_internal.h"
@@ -132,7 +133,7 @@ bool validate(const evfdlb_params& p, const char** why) {
     else if (!(p.phi_a >= 0)) w = "phi_a must be >= 0";
     else if (!(p.gamma > 3)) w = "gamma must be > 3";
     else if (p.Q < 4 || p.Q > kQMax) w = "Q must be in [4, 32]";
-    else if (p.bc != EVFDLB_BC_PERIODIC && p.bc != EVFDLB_BC_OUTFLOW) w = "bad bc";
+    else if (p.bc < EVFDLB_BC_PERIODIC || p.bc > EVFDLB_BC_HALO_OUTFLOW_HI) w = "bad bc";
     else if (p.relax_mode != EVFDLB_RELAX_INV_TAU && p.relax_mode != EVFDLB_RELAX_CHI_OVER_TAU) w = "bad relax_mode";
     else if (!(p.weno_eps > 0)) w = "weno_eps must be > 0";
     else if (!(p.T_iso >= 0) || !isfinite(p.T_iso)) w = "T_iso must be 0 (thermal) or > 0";
@@ -148,9 +149,18 @@ bool validate(const evfdlb_params& p, const char** why) {
         else if (M < m + 2) w = "r_cut must be >= sigma + 2 dx";
         else if ((M - m) % 2) w = "(r_cut - sigma)/dx must be even (Simpson panels end at +-sigma)";
     }
+    // a HALO slab sends its first and last G interior nodes: it holds >= G of
+    // them besides its ghost bands
+    if (!w && is_halo_bc(p.bc) && p.nx < (p.bc == EVFDLB_BC_HALO ? 3 : 2) * halo_width(p))
+        w = "HALO needs at least halo_width interior nodes";
     if (why) *why = w;
     return w == nullptr;
 }
+
+// Ghost nodes per side of a HALO slab: the widest read of the stage about a
+// node, i.e. the density sums over +-M (force / energy taps) and F, G over
+// +-3 (the WENO-5 stencil of the face fluxes).
+int halo_width(const evfdlb_params& p) { return std::max(3, force_halfwidth(p)); }
 
 namespace {
 double simpson(int j, int M, double dx) {
