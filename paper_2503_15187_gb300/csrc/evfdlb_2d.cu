@@ -56,7 +56,8 @@ enum { M2_S0 = 0, M2_S1X, M2_S1Y, M2_S2XX, M2_S2YY, M2_G0, M2_S2XY, M2_S3X, M2_S
 enum { F2_N = 0, F2_UX, F2_UY, F2_T, F2_NU, F2_FX, F2_FY, F2_PF = 7, F2_PG = 17, kNumFld2 = 27 };
 
 constexpr int kTile2 = 16;     // k2_fields tile edge
-constexpr int kNB = 8;         // nodes per k2_coll CTA
+constexpr int kNB = 16;        // nodes per k2_coll CTA (half a warp: a lane per node and distribution)
+static_assert(kNB == 16, "k2_coll maps the 32 lanes of a warp to 2 distributions x 16 nodes");
 constexpr int kAdvX = 32, kAdvY = 16, kAdvPlanes = 8;
 static_assert(kAdvX == 32 && kAdvY % 8 == 0, "k2_adv maps a warp (256 threads per CTA) to tile rows");
 
@@ -559,52 +560,138 @@ k2_fields(Slab2 s, const double* __restrict__ mom, const float* __restrict__ prf
 //   mu^0 = m_l, mu^1 = T sqrt(l) m_{l-1}, mu^2 = T m_l + T^2 sqrt(l(l-1)) m_{l-2},
 //   mu^3 = 3T^2 sqrt(l) m_{l-1} + T^3 sqrt(l(l-1)(l-2)) m_{l-3},
 // m_l = E[psi_l(u + c)], c ~ N(0, T)), synthesise to the rank-4 sum of
-// outer products of phi^a = S mu^a(u_x) and psi^a = sum_b P_ab S mu^b(u_y).
-// D anticommutes with the node reflection xi -> -xi, so with
-// E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j} (j < Q/2) a line's D h is
+// outer products of phi^a = S mu^a(u_x) and psi^a = sum_b P_ab chi^b,
+// chi^b = S mu^b(u_y); a row r of the sum is sum_b pr_b chi^b with
+// pr_b = sum_a phi^a_r P_ab.
+// The node reflection xi -> -xi maps psi_l to (-1)^l psi_l, so S's rows k and
+// Q-1-k differ in the sign of the odd orders, and D anticommutes with it.
+// With E_j = h_j + h_{Q-1-j}, O_j = h_j - h_{Q-1-j} (j < Q/2) a line's D h is
 //   (D h)_k = (DB E)_k + (DA O)_k,   (D h)_{Q-1-k} = (DA O)_k - (DB E)_k,
 // DA_kj = (D_kj - D_{k,Q-1-j})/2, DB_kj = (D_kj + D_{k,Q-1-j})/2: two
-// (Q/2)^2 blocks instead of Q^2 products per line.
+// (Q/2)^2 blocks instead of Q^2 products per line, and a synthesis is
+// (S c)_k = e_k + o_k, (S c)_{Q-1-k} = e_k - o_k over the even and odd orders.
+//
+// Work layout: a lane owns one (distribution, node) pair -- the 32 lanes of
+// a warp are the 2 x 16 pairs of the group -- and the state sits plane-major
+// in shared memory (16 nodes of a plane contiguous, staged by 16-byte
+// asynchronous copies), so a warp's shared accesses are conflict-free and its
+// global stores are 16 consecutive nodes of one plane per distribution.  A
+// warp takes velocity rows w, w + 8, ... (then columns): a line of Q values
+// is loaded, split into E and O and multiplied by DA and DB, whose entries
+// sit in the constant bank -- uniform across the warp at compile-time
+// indices, they are operands of the multiply-adds, with no load instructions
+// (the syntheses of phi and chi use S from the constant bank the same way).
+//   pass 1 (rows, D along y):  Y = -nu h + F_y (I (x) D) h + sum_b pr_b chi^b
+//   pass 2 (columns, along x): RL = Y + F_x (D (x) I) h, to global memory.
 // ---------------------------------------------------------------------------
+// per even Q of the 2D model (4 .. 16), at coll_coff(Q): DA, DB [(Q/2)^2
+// each], then S [Q][Q] (S[k][l] = w_k psi_l(xi_k))
+__host__ __device__ constexpr int coll_coff(int Q) {
+    int o = 0;
+    for (int q = 4; q < Q; q += 2) o += q * q / 2 + q * q;
+    return o;
+}
+constexpr int kCollConst = coll_coff(18);
+__constant__ float c_coll_f[kCollConst];
+__constant__ double c_coll_d[kCollConst];
+template <typename R>
+__device__ __forceinline__ R ccoll(int i);
+template <>
+__device__ __forceinline__ float ccoll<float>(int i) { return c_coll_f[i]; }
+template <>
+__device__ __forceinline__ double ccoll<double>(int i) { return c_coll_d[i]; }
+
 template <int Q>
 struct Coll2Lay {
     static constexpr int K = Q * Q, QH = Q / 2;
-    // matrix row and node strides: with XR = 20 the row pairs and column
-    // pairs of a half-warp's tasks fall in distinct banks, and the odd node
-    // stride puts the two matrices of a warp on alternate banks
-    static constexpr int XR = 20, XS = Q * XR + 1, DR = QH + 1;   // DR: padded rows of DA, DB
-    // X [2 kNB][XS] state, RLs [2 kNB][XS] result, mu, my, phi, chi [kNB][4][Q],
-    // psi [2][4][kNB][Q], sc [kNumFld2][kNB], St [Q][Q] (transposed synthesis
-    // table St[l][k] = w_k psi_l(xi_k)), DA, DB [QH][QH], rinv, rr, r1, r2, r3 [Q]
+    // Xp, Yp [2][K][kNB] (+16 per distribution: the two halves of a warp on
+    // opposite bank halves); chi4 [kNB][PS] (chi^b at column k: k 4 + b; PS an
+    // odd count of 16-byte units); phi [4][PH] (phi^a_k of node n at k kNB + n;
+    // PH = 8 mod 32: the 4 a of 8 nodes on distinct banks); mu [2][Q][kNB][4]
+    // (axis, order, node, a); sc [kNumFld2][kNB]; rinv, rr, r1, r2, r3 [Q]
+    static constexpr int XD = K * kNB + 16, PS = 4 * (Q + 1), PH = Q * kNB + 8;
 };
 
 template <typename R>
 __host__ __device__ inline size_t coll_smem_bytes(int Q) {
-    const int XS = Q * 20 + 1, QH = Q / 2;
-    return sizeof(R) * ((size_t)4 * kNB * XS + 4 * kNB * 4 * Q + 8 * kNB * Q + kNumFld2 * kNB + Q * Q +
-                        2 * QH * (QH + 1) + 5 * Q);
+    const size_t K = (size_t)Q * Q, XD = K * kNB + 16, PS = 4 * ((size_t)Q + 1), PH = (size_t)Q * kNB + 8;
+    return sizeof(R) * (4 * XD + kNB * PS + 4 * PH + 2 * (size_t)Q * kNB * 4 + kNumFld2 * kNB + 5 * (size_t)Q);
 }
 
+template <typename R>
+__device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = v.x, b = v.y, c = v.z, d = v.w;
+    } else {
+        const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+        a = v0.x, b = v0.y, c = v1.x, d = v1.y;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// D h along one line of Q values hv: out[k] = sum_j D_kj hv[j]
 template <typename R, int Q>
-__global__ void __launch_bounds__(256, 2)
-k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ dtab, const R* __restrict__ st,
-        const R* __restrict__ fld, R* __restrict__ RL) {
+__device__ __forceinline__ void d_line(const R (&hv)[Q], R (&out)[Q]) {
+    constexpr int QH = Q / 2, O0 = coll_coff(Q), O1 = O0 + QH * QH;
+    R E[QH], Od[QH];
+#pragma unroll
+    for (int j = 0; j < QH; ++j) {
+        E[j] = hv[j] + hv[Q - 1 - j];
+        Od[j] = hv[j] - hv[Q - 1 - j];
+    }
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+        R u = R(0), v = R(0);
+#pragma unroll
+        for (int j = 0; j < QH; ++j) {
+            u = fma(ccoll<R>(O0 + k * QH + j), Od[j], u);
+            v = fma(ccoll<R>(O1 + k * QH + j), E[j], v);
+        }
+        out[k] = v + u;
+        out[Q - 1 - k] = u - v;
+    }
+}
+
+// S c for one vector of Q orders: out[k] = sum_l S_kl c[l]
+template <typename R, int Q>
+__device__ __forceinline__ void s_line(const R (&c)[Q], R (&out)[Q]) {
+    constexpr int QH = Q / 2, OS = coll_coff(Q) + 2 * QH * QH;
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+        R e = R(0), o = R(0);
+#pragma unroll
+        for (int l = 0; l < Q; l += 2) {
+            e = fma(ccoll<R>(OS + k * Q + l), c[l], e);
+            o = fma(ccoll<R>(OS + k * Q + l + 1), c[l + 1], o);
+        }
+        out[k] = e + o;
+        out[Q - 1 - k] = e - o;
+    }
+}
+
+// FP32: two CTAs per SM (85 KB of shared memory each at Q = 16); FP64: one
+template <typename R>
+constexpr int coll_min_blocks() { return std::is_same<R, float>::value ? 2 : 1; }
+
+template <typename R, int Q>
+__global__ void __launch_bounds__(256, coll_min_blocks<R>())
+k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ st, const R* __restrict__ fld,
+        R* __restrict__ RL) {
     using Lay = Coll2Lay<Q>;
-    constexpr int K = Lay::K, QH = Lay::QH, XR = Lay::XR, XS = Lay::XS, DR = Lay::DR, NT = 256;
-    static_assert(Q <= 20, "rows of XR = 20");
+    constexpr int K = Lay::K, XD = Lay::XD, PS = Lay::PS, PH = Lay::PH, NT = 256;
     extern __shared__ __align__(16) double smc[];
-    R* X = reinterpret_cast<R*>(smc);                          // [2 kNB][XS]: h[kx][ky] at kx XR + ky
-    R* RLs = X + 2 * kNB * XS;
-    R* mu = RLs + 2 * kNB * XS;                                 // x-axis moments [kNB][4][Q]
-    R* my = mu + kNB * 4 * Q;                                   // y-axis moments [kNB][4][Q]
-    R* phi = my + kNB * 4 * Q;                                  // S mu [kNB][4][Q]
-    R* chi = phi + kNB * 4 * Q;                                 // S my [kNB][4][Q]
-    R* psi = chi + kNB * 4 * Q;                                 // [2][4][kNB][Q]
-    R* sc = psi + 8 * kNB * Q;                                  // [kNumFld2][kNB]
-    R* St = sc + kNumFld2 * kNB;                                // [Q][Q] transposed synthesis table
-    R* DA = St + K;                                             // [QH][DR]
-    R* DB = DA + QH * DR;
-    R* rinv = DB + QH * DR;
+    R* Xp = reinterpret_cast<R*>(smc);                         // [2][K][kNB] (+16 per distribution)
+    R* Yp = Xp + 2 * XD;
+    R* chi4 = Yp + 2 * XD;                                      // [kNB][PS]
+    R* phi = chi4 + kNB * PS;                                   // [4][PH]
+    R* mu = phi + 4 * PH;                                       // [2][Q][kNB][4]
+    R* sc = mu + 2 * Q * kNB * 4;                               // [kNumFld2][kNB]
+    R* rinv = sc + kNumFld2 * kNB;
     R* rr = rinv + Q;
     R* r1 = rr + Q;
     R* r2 = r1 + Q;
@@ -613,20 +700,23 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ dtab, const R
     const long long i0 = (long long)blockIdx.x * kNB;
     const int nb = (int)min((long long)kNB, N - i0);
     TableLayout L(Q);
-    for (int e = threadIdx.x; e < K; e += NT) St[e] = rtab[L.S + (e % Q) * Q + e / Q];
-    // the group's state as [d][node][kx][ky] by asynchronous copies, all in
-    // flight at once (8 consecutive nodes per plane: 32-byte segments)
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += NT) {
-        const int n = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
-        R* dst = X + (d * kNB + n) * XS + (k / Q) * XR + k % Q;
-        if (n < nb) cp_async_elem<R>(dst, st + d * NF + (long long)k * N + i0 + n);
-        else *dst = R(0);
+    // the group's state, plane-major: 16-byte copies when whole aligned
+    // chunks of 4 nodes exist (N a multiple of 4, a full group), else per element
+    constexpr int CH = 16 / (int)sizeof(R);                     // elements per 16-byte chunk
+    if (nb == kNB && (N % CH) == 0) {
+        for (int e = threadIdx.x; e < 2 * K * (kNB / CH); e += NT) {
+            const int c = e % (kNB / CH), k = (e / (kNB / CH)) % K, d = e / ((kNB / CH) * K);
+            cp_async16(Xp + d * XD + k * kNB + c * CH, st + d * NF + (long long)k * N + i0 + c * CH);
+        }
+    } else {
+        for (int e = threadIdx.x; e < 2 * K * kNB; e += NT) {
+            const int n = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
+            R* dst = Xp + d * XD + k * kNB + n;
+            if (n < nb) cp_async_elem<R>(dst, st + d * NF + (long long)k * N + i0 + n);
+            else *dst = R(0);
+        }
     }
     cp_async_commit();
-    for (int e = threadIdx.x; e < QH * QH; e += NT) {
-        DA[(e / QH) * DR + e % QH] = dtab[e];
-        DB[(e / QH) * DR + e % QH] = dtab[QH * QH + e];
-    }
     for (int e = threadIdx.x; e < Q; e += NT) {
         rinv[e] = rtab[L.rinv + e];
         rr[e] = rtab[L.rr + e];
@@ -638,20 +728,20 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ dtab, const R
         const int n = e % kNB, f = e / kNB;
         sc[e] = (n < nb) ? fld[f * N + i0 + n] : (f == F2_N || f == F2_T ? R(1) : R(0));
     }
-    cp_async_wait_all();
     __syncthreads();
     // one-axis Gaussian moments mu^a_l, one node and axis per thread
     if (threadIdx.x < 2 * kNB) {
         const int n = threadIdx.x % kNB, axis = threadIdx.x / kNB;
         const R u = sc[(axis ? F2_UY : F2_UX) * kNB + n], T = sc[F2_T * kNB + n], Tm1 = T - R(1);
-        R* out = (axis ? my : mu) + n * 4 * Q;
+        R* out = mu + (axis * Q * kNB + n) * 4;
         R m1v = 0, m2v = 0, m3v = 0;                            // m_{l-1}, m_{l-2}, m_{l-3}
         R m0 = 1;                                               // m_l
         for (int l = 0; l < Q; ++l) {
-            out[l] = m0;
-            out[Q + l] = T * r1[l] * m1v;
-            out[2 * Q + l] = T * m0 + T * T * r2[l] * m2v;
-            out[3 * Q + l] = R(3) * T * T * r1[l] * m1v + T * T * T * r3[l] * m3v;
+            R* o = out + l * kNB * 4;
+            o[0] = m0;
+            o[1] = T * r1[l] * m1v;
+            o[2] = T * m0 + T * T * r2[l] * m2v;
+            o[3] = R(3) * T * T * r1[l] * m1v + T * T * T * r3[l] * m3v;
             const R mn = fma(u * rinv[l], m0, Tm1 * rr[l] * m1v);
             m3v = m2v;
             m2v = m1v;
@@ -660,135 +750,80 @@ k2_coll(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ dtab, const R
         }
     }
     __syncthreads();
-    // one-axis syntheses phi = S mu, chi = S my (consecutive threads on consecutive nodes k of St rows)
-    for (int e = threadIdx.x; e < 8 * kNB * Q; e += NT) {
-        const int k = e % Q, v = e / Q;
-        const R* c = mu + v * Q;                                // mu and my are adjacent: v < 8 kNB
-        R acc = 0;
+    // one-axis syntheses, one vector (axis, node, a) per thread:
+    // phi^a = S mu^a(u_x) to phi, chi^b = S mu^b(u_y) to chi4
+    if (threadIdx.x < 2 * kNB * 4) {
+        const int a = threadIdx.x % 4, n = (threadIdx.x / 4) % kNB, axis = threadIdx.x / (4 * kNB);
+        R c[Q], out[Q];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) acc = fma(St[l * Q + k], c[l], acc);
-        phi[v * Q + k] = acc;                                   // phi then chi
+        for (int l = 0; l < Q; ++l) c[l] = mu[((axis * Q + l) * kNB + n) * 4 + a];
+        s_line<R, Q>(c, out);
+        if (axis == 0) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) phi[a * PH + k * kNB + n] = out[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) chi4[n * PS + k * 4 + a] = out[k];
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
-    // psi^{a,d} = sum_b P^d_ab chi^b (P^d: the equilibrium polynomials' coefficients, times n)
-    for (int e = threadIdx.x; e < 8 * kNB * Q; e += NT) {
-        const int k = e % Q, r = e / Q;
-        const int n = r % kNB, a = (r / kNB) % 4, d = r / (4 * kNB);
-        // the coefficient of c_x^a c_y^b sits at (a+b)(a+b+1)/2 + b in the order
-        // (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (3,0) (2,1) (1,2) (0,3)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = lane >> 4, n = lane & (kNB - 1);
+    const R* h = Xp + d * XD + n;                               // h[k] at k kNB
+    R* y = Yp + d * XD + n;
+    // pass 1: rows r (fixed kx), D along y
+    {
+        const R mnu = -sc[F2_NU * kNB + n], fy = sc[F2_FY * kNB + n];
+        // P^d_ab (the equilibrium polynomial's coefficient of c_x^a c_y^b,
+        // times n) at (a+b)(a+b+1)/2 + b of the order (0,0) (1,0) (0,1)
+        // (2,0) (1,1) (0,2) (3,0) (2,1) (1,2) (0,3)
+        R P[10];
         const int f0 = d ? F2_PG : F2_PF;
-        R acc = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (a + b <= 3)
-                acc = fma(sc[(f0 + (a + b) * (a + b + 1) / 2 + b) * kNB + n], chi[(n * 4 + b) * Q + k], acc);
-        psi[r * Q + k] = acc;
+        for (int i = 0; i < 10; ++i) P[i] = sc[(f0 + i) * kNB + n];
+        const R* ch = chi4 + n * PS;
+        for (int r = warp; r < Q; r += NT / 32) {
+            R hv[Q], dy[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) hv[j] = h[(r * Q + j) * kNB];
+            d_line<R, Q>(hv, dy);
+            const R p0 = phi[0 * PH + r * kNB + n], p1 = phi[1 * PH + r * kNB + n];
+            const R p2 = phi[2 * PH + r * kNB + n], p3 = phi[3 * PH + r * kNB + n];
+            // pr_b = sum_{a <= 3-b} phi^a_r P_ab
+            const R pr0 = fma(p3, P[6], fma(p2, P[3], fma(p1, P[1], p0 * P[0])));
+            const R pr1 = fma(p2, P[7], fma(p1, P[4], p0 * P[2]));
+            const R pr2 = fma(p1, P[8], p0 * P[5]);
+            const R pr3 = p0 * P[9];
+#pragma unroll
+            for (int c = 0; c < Q; ++c) {
+                R q0, q1, q2, q3;
+                ld4<R>(ch + c * 4, q0, q1, q2, q3);
+                R eq = pr0 * q0;
+                eq = fma(pr1, q1, eq);
+                eq = fma(pr2, q2, eq);
+                eq = fma(pr3, q3, eq);
+                const R v = fma(mnu, hv[c], eq);
+                y[(r * Q + c) * kNB] = fma(fy, dy[c], v);
+            }
+        }
     }
     __syncthreads();
-    // D along x and y on node-pair blocks and the combination; a task owns
-    // KP pairs of rows (k, Q-1-k) and KP pairs of columns of one (d, node)
-    constexpr int KP = (QH % 2 == 0) ? 2 : 1, NKB = QH / KP;
-    constexpr int TASKS = 2 * kNB * NKB * NKB;
-    for (int task = threadIdx.x; task < TASKS; task += NT) {
-        const int mi = task / (NKB * NKB), kb = (task / NKB) % NKB, mb = task % NKB;
-        const int d = mi / kNB, n = mi % kNB;
-        const R* h = X + mi * XS;
-        int rw[2 * KP], cl[2 * KP];
+    // pass 2: columns c (fixed ky), D along x, and the store
+    {
+        const R fx = sc[F2_FX * kNB + n];
+        R* g = RL + d * NF + i0 + n;
+        for (int c = warp; c < Q; c += NT / 32) {
+            R hv[Q], dx[Q];
 #pragma unroll
-        for (int a = 0; a < KP; ++a) {
-            rw[a] = kb * KP + a;
-            rw[KP + a] = Q - 1 - rw[a];
-            cl[a] = mb * KP + a;
-            cl[KP + a] = Q - 1 - cl[a];
-        }
-        R dx[2 * KP][2 * KP], dy[2 * KP][2 * KP];
-        {   // along x: for each column, u = DA O, v = DB E over the row pairs
-            R u[KP][2 * KP], v[KP][2 * KP];
+            for (int j = 0; j < Q; ++j) hv[j] = h[(j * Q + c) * kNB];
+            d_line<R, Q>(hv, dx);
 #pragma unroll
-            for (int a = 0; a < KP; ++a)
-#pragma unroll
-                for (int c = 0; c < 2 * KP; ++c) u[a][c] = v[a][c] = R(0);
-#pragma unroll
-            for (int j = 0; j < QH; ++j) {
-                R ev[2 * KP], od[2 * KP];
-#pragma unroll
-                for (int c = 0; c < 2 * KP; ++c) {
-                    const R p = h[j * XR + cl[c]], q = h[(Q - 1 - j) * XR + cl[c]];
-                    ev[c] = p + q;
-                    od[c] = p - q;
-                }
-#pragma unroll
-                for (int a = 0; a < KP; ++a) {
-                    const R da = DA[rw[a] * DR + j], db = DB[rw[a] * DR + j];
-#pragma unroll
-                    for (int c = 0; c < 2 * KP; ++c) {
-                        u[a][c] = fma(da, od[c], u[a][c]);
-                        v[a][c] = fma(db, ev[c], v[a][c]);
-                    }
-                }
+            for (int r = 0; r < Q; ++r) {
+                const R v = fma(fx, dx[r], y[(r * Q + c) * kNB]);
+                if (n < nb) g[(long long)(r * Q + c) * N] = v;
             }
-#pragma unroll
-            for (int a = 0; a < KP; ++a)
-#pragma unroll
-                for (int c = 0; c < 2 * KP; ++c) {
-                    dx[a][c] = v[a][c] + u[a][c];
-                    dx[KP + a][c] = u[a][c] - v[a][c];
-                }
         }
-        {   // along y: for each row, over the column pairs
-            R u[2 * KP][KP], v[2 * KP][KP];
-#pragma unroll
-            for (int r = 0; r < 2 * KP; ++r)
-#pragma unroll
-                for (int a = 0; a < KP; ++a) u[r][a] = v[r][a] = R(0);
-#pragma unroll
-            for (int j = 0; j < QH; ++j) {
-                R ev[2 * KP], od[2 * KP];
-#pragma unroll
-                for (int r = 0; r < 2 * KP; ++r) {
-                    const R p = h[rw[r] * XR + j], q = h[rw[r] * XR + Q - 1 - j];
-                    ev[r] = p + q;
-                    od[r] = p - q;
-                }
-#pragma unroll
-                for (int a = 0; a < KP; ++a) {
-                    const R da = DA[cl[a] * DR + j], db = DB[cl[a] * DR + j];
-#pragma unroll
-                    for (int r = 0; r < 2 * KP; ++r) {
-                        u[r][a] = fma(da, od[r], u[r][a]);
-                        v[r][a] = fma(db, ev[r], v[r][a]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 2 * KP; ++r)
-#pragma unroll
-                for (int a = 0; a < KP; ++a) {
-                    dy[r][a] = v[r][a] + u[r][a];
-                    dy[r][KP + a] = u[r][a] - v[r][a];
-                }
-        }
-        const R mnu = -sc[F2_NU * kNB + n], fx = sc[F2_FX * kNB + n], fy = sc[F2_FY * kNB + n];
-        R* o = RLs + mi * XS;
-#pragma unroll
-        for (int r = 0; r < 2 * KP; ++r)
-#pragma unroll
-            for (int c = 0; c < 2 * KP; ++c) {
-                R eq = 0;
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    eq = fma(phi[(n * 4 + a) * Q + rw[r]], psi[((d * 4 + a) * kNB + n) * Q + cl[c]], eq);
-                R rl = fma(mnu, h[rw[r] * XR + cl[c]], eq);
-                rl = fma(fx, dx[r][c], rl);
-                rl = fma(fy, dy[r][c], rl);
-                o[rw[r] * XR + cl[c]] = rl;
-            }
-    }
-    __syncthreads();
-    // the local right-hand side to global memory, 8 consecutive nodes per plane
-    for (int e = threadIdx.x; e < 2 * K * kNB; e += NT) {
-        const int n = e % kNB, k = (e / kNB) % K, d = e / (kNB * K);
-        if (n < nb) RL[d * NF + (long long)k * N + i0 + n] = RLs[(d * kNB + n) * XS + (k / Q) * XR + k % Q];
     }
 }
 
@@ -1292,7 +1327,6 @@ struct Ctx2 {
     int* fm_off = nullptr;
     void* fm_w = nullptr;        // Fischer-Methfessel weights, precision R
     float* prf = nullptr;        // FP32 build: node primitives [kNumPrf2][N] of the stage input
-    void* dtab = nullptr;        // parity blocks DA, DB of the force derivative (k2_coll), precision R
     Pow2<float> pwf{};
     Pow2<double> pwd{};
     double* scratch = nullptr;   // [2 Q^2 N + 8] doubles
@@ -1304,16 +1338,16 @@ struct Ctx2 {
 namespace {
 // k2_coll is compiled for each even Q of the 2D model (4 .. 16)
 template <typename R>
-void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, const R* rtab, const R* dtab,
-                 const R* src, const R* fld, R* RL) {
+void launch_coll(int Q, int nc, size_t smem, cudaStream_t st, const Slab2& s, const R* rtab, const R* src,
+                 const R* fld, R* RL) {
     switch (Q) {
-        case 4: k2_coll<R, 4><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        case 6: k2_coll<R, 6><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        case 8: k2_coll<R, 8><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        case 10: k2_coll<R, 10><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        case 12: k2_coll<R, 12><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        case 14: k2_coll<R, 14><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
-        default: k2_coll<R, 16><<<nc, 256, smem, st>>>(s, rtab, dtab, src, fld, RL); break;
+        case 4: k2_coll<R, 4><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 6: k2_coll<R, 6><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 8: k2_coll<R, 8><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 10: k2_coll<R, 10><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 12: k2_coll<R, 12><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        case 14: k2_coll<R, 14><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
+        default: k2_coll<R, 16><<<nc, 256, smem, st>>>(s, rtab, src, fld, RL); break;
     }
 }
 
@@ -1387,8 +1421,7 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
     k2_fields<R><<<gf, 256, c->smem_fields, st>>>(s, c->mom, c->prf, (const R*)c->ftw, c->fplan, c->fm_off,
                                                    (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
-    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)c->dtab, (const R*)src, (const R*)c->fld,
-                   (R*)c->RL);
+    launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
     dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
     launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
                   alpha, beta, mode);
@@ -1425,7 +1458,6 @@ void destroy_2d(Ctx2* c) {
     cudaFree(c->fm_off);
     cudaFree(c->fm_w);
     cudaFree(c->prf);
-    cudaFree(c->dtab);
     cudaFree(c->scratch);
     cudaFree(c->err);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -1482,9 +1514,12 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     alloc((void**)&c->fm_off, sizeof(int) * t.moff.size());
     alloc(&c->fm_w, c->esize * t.mw.size());
     if (f32) alloc((void**)&c->prf, sizeof(float) * kNumPrf2 * s.N);
-    const std::vector<double> dbl = d_blocks(p.Q, xi.data(), w.data());
+    std::vector<double> dbl = d_blocks(p.Q, xi.data(), w.data());
+    {   // k2_coll's constant block: DA, DB, then S[k][l] = w_k psi_l(xi_k)
+        const TableLayout L(p.Q);
+        dbl.insert(dbl.end(), tab.begin() + L.S, tab.begin() + L.S + p.Q * p.Q);
+    }
     const std::vector<float> dblf(dbl.begin(), dbl.end());
-    alloc(&c->dtab, c->esize * dbl.size());
     alloc((void**)&c->scratch, sizeof(double) * (2 * NF + 8));
     alloc((void**)&c->err, sizeof(unsigned));
     std::vector<float> tabf(tab.begin(), tab.end()), ftwf(fp.w.begin(), fp.w.end()), mwf(t.mw.begin(), t.mw.end());
@@ -1496,9 +1531,13 @@ evfdlb_status create_2d(const evfdlb_params& p, void* stream, Ctx2** out) {
     if (e == cudaSuccess && c->prec == EVFDLB_FP32)
         e = cudaMemcpy(c->rtab, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->fplan, fp.plan.data(), sizeof(int) * fp.plan.size(), cudaMemcpyHostToDevice);
+    // the parity blocks and the synthesis matrix of this Q into k2_coll's
+    // constant bank (every context of the same Q writes the same values)
     if (e == cudaSuccess)
-        e = f32 ? cudaMemcpy(c->dtab, dblf.data(), sizeof(float) * dblf.size(), cudaMemcpyHostToDevice)
-                : cudaMemcpy(c->dtab, dbl.data(), sizeof(double) * dbl.size(), cudaMemcpyHostToDevice);
+        e = f32 ? cudaMemcpyToSymbol(c_coll_f, dblf.data(), sizeof(float) * dblf.size(),
+                                     sizeof(float) * coll_coff(p.Q))
+                : cudaMemcpyToSymbol(c_coll_d, dbl.data(), sizeof(double) * dbl.size(),
+                                     sizeof(double) * coll_coff(p.Q));
     if (e == cudaSuccess)
         e = f32 ? cudaMemcpy(c->ftw, ftwf.data(), sizeof(float) * ftwf.size(), cudaMemcpyHostToDevice)
                 : cudaMemcpy(c->ftw, fp.w.data(), sizeof(double) * fp.w.size(), cudaMemcpyHostToDevice);
