@@ -972,6 +972,233 @@ k2_adv(Slab2 s, const R* __restrict__ rtab, const R* __restrict__ src, const R* 
 }
 
 // ---------------------------------------------------------------------------
+// k2_adv2: the FP32 stage form of k2_adv.  The F and G planes of one
+// velocity are carried together as float2 through packed FP32 arithmetic
+// (two lanes per instruction): both distributions share the velocity, hence
+// the upwind direction of every face, so the pair runs one stencil walk.
+// Each packed operation is the IEEE single-precision operation of each lane
+// in the order of k2_adv (k2_adv's scalar code may also fuse a product into
+// a following add, so the two agree to rounding, not bit for bit).  The
+// halo tile, RL and base of velocity k+2 are copied asynchronously into a
+// second shared buffer while velocity k is formed (two velocities in
+// flight per CTA, no register staging), which keeps enough bytes in flight
+// for the kernel to stream.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Weno5Run on float2 pairs (its operations, lane by lane, none fused)
+struct Weno5Run2 {
+    float2 v2, v3, v4, d0, d1, d2, d3, u0, u1, u2, eps4;
+    __device__ __forceinline__ float2 tterm(float2 t) const {
+        return fma2(mul2(f2s(float(13.0 / 3.0)), t), t, eps4);
+    }
+    __device__ __forceinline__ void start(float2 w0, float2 w1, float2 w2, float2 w3, float2 w4, float eps) {
+        eps4 = f2s(4.f * eps);
+        v2 = w2;
+        v3 = w3;
+        v4 = w4;
+        d0 = sub2(w1, w0);
+        d1 = sub2(w2, w1);
+        d2 = sub2(w3, w2);
+        d3 = sub2(w4, w3);
+        u0 = tterm(sub2(d1, d0));
+        u1 = tterm(sub2(d2, d1));
+        u2 = tterm(sub2(d3, d2));
+    }
+    __device__ __forceinline__ float2 face() const {
+        const float2 s0 = fma2(f2s(3.f), d1, neg2(d0)), s1 = add2(d1, d2), s2 = fma2(f2s(-3.f), d2, d3);
+        const float2 e0 = fma2(s0, s0, u0), e1 = fma2(s1, s1, u1), e2 = fma2(s2, s2, u2);
+        const float2 E0 = mul2(e0, e0), E1 = mul2(e1, e1), E2 = mul2(e2, e2);
+        const float2 a0 = mul2(E1, E2), a1 = mul2(E0, E2), a2 = mul2(E0, E1);
+        const float2 c0 = fma2(f2s(float(5.0 / 60.0)), d1, mul2(f2s(float(-2.0 / 60.0)), d0));
+        const float2 p2 = mul2(f2s(0.2f), d2);
+        const float2 c1 = fma2(f2s(0.1f), d1, p2);
+        const float2 c2 = fma2(f2s(-0.05f), d3, p2);
+        const float2 num = fma2(a0, c0, fma2(a1, c1, mul2(a2, c2)));
+        const float2 den = fma2(f2s(0.1f), a0, fma2(f2s(0.6f), a1, mul2(f2s(0.3f), a2)));
+        return add2(v2, make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y)));
+    }
+    __device__ __forceinline__ void shift(float2 w5) {
+        const float2 d4 = sub2(w5, v4);
+        u0 = u1;
+        u1 = u2;
+        u2 = tterm(sub2(d4, d3));
+        d0 = d1;
+        d1 = d2;
+        d2 = d3;
+        d3 = d4;
+        v2 = v3;
+        v3 = v4;
+        v4 = w5;
+    }
+};
+
+// Shared layout of k2_adv2 per buffer (two buffers: velocities k and k+1 in
+// flight): the halo tile of F and G, rows y0-3 .. y0+18 with column
+// x0-3+i at i + 1 (the interior x0 .. x0+31 at columns 4 .. 35, 16-byte
+// aligned, row stride 44: a row's 16 lanes of the x runs on 8 banks apart),
+// then RL and base of the tile's nodes.
+constexpr int kA2Row = 44, kA2Rows = kAdvY + 6;
+constexpr int kA2H = 2 * kA2Rows * kA2Row;                  // halo of F and G
+constexpr int kA2T = 2 * kAdvY * kAdvX;                     // RL (or base) of F and G
+constexpr int kA2Buf = kA2H + 2 * kA2T;
+constexpr size_t kA2Smem = sizeof(float) * 2 * kA2Buf + sizeof(float2) * (kAdvY * (kAdvX + 1) + (kAdvY + 1) * kAdvX) +
+                           sizeof(int) * (kA2Rows + kAdvX + 6);
+
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Queues the asynchronous copies of velocity k (planes at F + k N and
+// F + NF + k N) into buffer `buf`: whole 16-byte chunks for the aligned
+// interior when `fast`, element copies otherwise (wrapped columns, a ragged
+// tile edge, nx not a multiple of 4).
+__device__ __forceinline__ void adv2_issue(float* buf, const float* src, const float* RL, const float* base,
+                                           long long kN, long long NF, const int* rowoff, const int* coloff,
+                                           int x0, int y0, int nx, int ny, bool fast, bool with_base) {
+    float* H = buf;
+    float* Rs = buf + kA2H;
+    float* Bs = Rs + kA2T;
+    const int t = threadIdx.x;
+    if (fast) {
+        // interior chunks: 2 d x kA2Rows rows x 8 chunks; side columns: 2 d x rows x 6
+        for (int e = t; e < 2 * kA2Rows * 8; e += 256) {
+            const int c = e % 8, r = (e / 8) % kA2Rows, d = e / (8 * kA2Rows);
+            cp_async16(H + (d * kA2Rows + r) * kA2Row + 4 + 4 * c, src + d * NF + kN + rowoff[r] + x0 + 4 * c);
+        }
+        for (int e = t; e < 2 * kA2Rows * 6; e += 256) {
+            const int c = e % 6, r = (e / 6) % kA2Rows, d = e / (6 * kA2Rows);
+            const int i = c < 3 ? c : 32 + c;               // halo columns 0..2 and 35..37
+            cp_async_elem<float>(H + (d * kA2Rows + r) * kA2Row + i + 1, src + d * NF + kN + rowoff[r] + coloff[i]);
+        }
+        for (int e = t; e < 2 * kAdvY * 8; e += 256) {
+            const int c = e % 8, r = (e / 8) % kAdvY, d = e / (8 * kAdvY);
+            const long long g = d * NF + kN + (long long)(y0 + r) * nx + x0 + 4 * c;
+            cp_async16(Rs + (d * kAdvY + r) * kAdvX + 4 * c, RL + g);
+            if (with_base) cp_async16(Bs + (d * kAdvY + r) * kAdvX + 4 * c, base + g);
+        }
+    } else {
+        for (int e = t; e < 2 * kA2Rows * (kAdvX + 6); e += 256) {
+            const int i = e % (kAdvX + 6), r = (e / (kAdvX + 6)) % kA2Rows, d = e / ((kAdvX + 6) * kA2Rows);
+            cp_async_elem<float>(H + (d * kA2Rows + r) * kA2Row + i + 1, src + d * NF + kN + rowoff[r] + coloff[i]);
+        }
+        for (int e = t; e < 2 * kAdvY * kAdvX; e += 256) {
+            const int c = e % kAdvX, r = (e / kAdvX) % kAdvY, d = e / (kAdvX * kAdvY);
+            if (x0 + c < nx && y0 + r < ny) {
+                const long long g = d * NF + kN + (long long)(y0 + r) * nx + x0 + c;
+                cp_async_elem<float>(Rs + (d * kAdvY + r) * kAdvX + c, RL + g);
+                if (with_base) cp_async_elem<float>(Bs + (d * kAdvY + r) * kAdvX + c, base + g);
+            }
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256, 4)
+k2_adv2(Slab2 s, const float* __restrict__ rtab, const float* __restrict__ src, const float* base, float* out,
+        const float* __restrict__ RL, double alpha, double beta) {
+    constexpr int K = Q * Q, RPW = kAdvY / 8;
+    static_assert(kAdvX == 32 && kAdvY == 16, "run split: 33 = 5 + 7 x 4 x-faces, 17 = 5 + 3 x 4 y-faces");
+    extern __shared__ __align__(16) double sma[];
+    float* buf0 = reinterpret_cast<float*>(sma);
+    float2* FX = reinterpret_cast<float2*>(buf0 + 2 * kA2Buf);
+    float2* FY = FX + kAdvY * (kAdvX + 1);
+    int* rowoff = reinterpret_cast<int*>(FY + (kAdvY + 1) * kAdvX);
+    int* coloff = rowoff + kA2Rows;
+    const int nx = s.nx, ny = s.ny;
+    const long long N = s.N, NF = (long long)K * N;
+    const int tilesx = (nx + kAdvX - 1) / kAdvX;
+    const int x0 = (blockIdx.x % tilesx) * kAdvX, y0 = (blockIdx.x / tilesx) * kAdvY;
+    TableLayout L(Q);
+    for (int e = threadIdx.x; e < kA2Rows + kAdvX + 6; e += blockDim.x) {
+        if (e < kA2Rows) rowoff[e] = wrapi(y0 - 3 + e, ny) * nx;
+        else coloff[e - kA2Rows] = wrapi(x0 - 3 + (e - kA2Rows), nx);
+    }
+    __syncthreads();
+    const bool fast = (nx % 4 == 0) && (x0 + kAdvX <= nx) && (y0 + kAdvY <= ny);
+    const float eps = (float)s.weno_eps, idx = (float)s.inv_dx, dt = (float)s.dt, ralpha = (float)alpha,
+                rbeta = (float)beta;
+    const bool with_base = (alpha != 0.0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool xrun = threadIdx.x < 128;
+    const int rj = xrun ? (threadIdx.x >> 4) : ((threadIdx.x - 128) >> 5);
+    const int rl = xrun ? (threadIdx.x & 15) : (threadIdx.x & 31);
+    const int fa = rj == 0 ? 0 : 4 * rj + 1, nrun = rj == 0 ? 5 : 4, fl = fa + nrun - 1;
+    const int hst = xrun ? 1 : kA2Row;
+    // x face f of row r: stencil from halo (r + 3, f); y face f of column c: from halo (f, c + 3)
+    const int hrow = xrun ? (rl + 3) * kA2Row + 1 : rl + 3 + 1;
+    float2* frow = xrun ? FX + rl * (kAdvX + 1) : FY + rl;
+    const int fst = xrun ? 1 : kAdvX;
+    const int x = x0 + lane;
+    int ooff[RPW];
+    bool oval[RPW];
+#pragma unroll
+    for (int rr = 0; rr < RPW; ++rr) {
+        const int y = y0 + warp * RPW + rr;
+        oval[rr] = (x < nx && y < ny);
+        ooff[rr] = oval[rr] ? y * nx + x : 0;
+    }
+    const int k0 = blockIdx.y * kAdvPlanes, k1 = min(k0 + kAdvPlanes, K);
+    constexpr int HG = kA2Rows * kA2Row;                    // G's halo after F's
+    adv2_issue(buf0, src, RL, base, (long long)k0 * N, NF, rowoff, coloff, x0, y0, nx, ny, fast, with_base);
+    cp_async_commit();
+    if (k0 + 1 < k1)
+        adv2_issue(buf0 + kA2Buf, src, RL, base, (long long)(k0 + 1) * N, NF, rowoff, coloff, x0, y0, nx, ny, fast,
+                   with_base);
+    cp_async_commit();
+    for (int k = k0; k < k1; ++k) {
+        float* buf = buf0 + ((k - k0) & 1) * kA2Buf;
+        const float* H = buf;
+        const float* Rs = buf + kA2H;
+        const float* Bs = Rs + kA2T;
+        const float vx = rtab[L.xi + k / Q], vy = rtab[L.xi + k % Q];
+        cp_async_wait_1();                                  // velocity k's copies (all but the newest group)
+        __syncthreads();
+        {
+            const bool pos = (xrun ? vx : vy) >= 0.f;       // uniform per warp
+            const int dir = pos ? 1 : -1, f0 = pos ? fa : fl;
+            const float* hb = H + hrow + (pos ? fa : fl + 5) * hst;
+            const int hs = dir * hst;
+            auto at = [&](int o) { return make_float2(hb[o], hb[HG + o]); };
+            Weno5Run2 w;
+            w.start(at(0), at(hs), at(2 * hs), at(3 * hs), at(4 * hs), eps);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (q >= nrun) break;
+                frow[(f0 + dir * q) * fst] = w.face();
+                if (q + 1 < nrun) w.shift(at((q + 5) * hs));
+            }
+        }
+        __syncthreads();
+        const float2 cx = f2s(-vx * idx), cy = f2s(-vy * idx);
+        float* op = out + (long long)k * N;
+#pragma unroll
+        for (int rr = 0; rr < RPW; ++rr) {
+            if (!oval[rr]) continue;
+            const int ty = warp * RPW + rr;
+            float2 Rv = make_float2(Rs[ty * kAdvX + lane], Rs[(kAdvY + ty) * kAdvX + lane]);
+            Rv = fma2(cx, sub2(FX[ty * (kAdvX + 1) + lane + 1], FX[ty * (kAdvX + 1) + lane]), Rv);
+            Rv = fma2(cy, sub2(FY[(ty + 1) * kAdvX + lane], FY[ty * kAdvX + lane]), Rv);
+            const int hc = (ty + 3) * kA2Row + lane + 4;
+            const float2 hv = make_float2(H[hc], H[HG + hc]);
+            float2 o = mul2(f2s(rbeta), fma2(f2s(dt), Rv, hv));
+            if (with_base)
+                o = fma2(f2s(ralpha), make_float2(Bs[ty * kAdvX + lane], Bs[(kAdvY + ty) * kAdvX + lane]), o);
+            op[ooff[rr]] = o.x;
+            op[NF + ooff[rr]] = o.y;
+        }
+        __syncthreads();                                    // this buffer and the faces consumed
+        if (k + 2 < k1)
+            adv2_issue(buf, src, RL, base, (long long)(k + 2) * N, NF, rowoff, coloff, x0, y0, nx, ny, fast,
+                       with_base);
+        cp_async_commit();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Initial state, node moments and totals.
 // ---------------------------------------------------------------------------
 // Projected Maxwellian pair: F_{kx,ky} = n phi_kx(ux) phi_ky(uy) with
@@ -1367,6 +1594,20 @@ void launch_adv_t(int Q, dim3 g, cudaStream_t st, const Slab2& s, const R* rtab,
     }
 }
 
+// the FP32 stage form: F and G of a velocity as float2 pairs
+void launch_adv2(int Q, dim3 g, cudaStream_t st, const Slab2& s, const float* rtab, const float* src,
+                 const float* base, float* out, const float* RL, double alpha, double beta) {
+    switch (Q) {
+        case 4: k2_adv2<4><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        case 6: k2_adv2<6><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        case 8: k2_adv2<8><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        case 10: k2_adv2<10><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        case 12: k2_adv2<12><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        case 14: k2_adv2<14><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+        default: k2_adv2<16><<<g, 256, kA2Smem, st>>>(s, rtab, src, base, out, RL, alpha, beta); break;
+    }
+}
+
 template <typename R>
 void launch_adv(int Q, dim3 g, cudaStream_t st, const Slab2& s, const R* rtab, const R* src, const R* base, R* out,
                 const R* RL, double* rhs_out, double alpha, double beta, int mode) {
@@ -1422,9 +1663,16 @@ void queue_stage_t(Ctx2* c, cudaStream_t st, const void* src, const void* base, 
                                                    (const R*)c->fm_w, (R*)c->fld, c->err);
     int nc = (int)((s.N + kNB - 1) / kNB);
     launch_coll<R>(Q, nc, c->smem_coll, st, s, (const R*)c->rtab, (const R*)src, (const R*)c->fld, (R*)c->RL);
-    dim3 ga(((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY), (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
-    launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL, rhs_out,
-                  alpha, beta, mode);
+    const int tiles = ((s.nx + kAdvX - 1) / kAdvX) * ((s.ny + kAdvY - 1) / kAdvY);
+    if (F32 && mode == 0) {   // the FP32 stage form: one CTA column per group of velocities, F and G paired
+        dim3 ga(tiles, (Q * Q + kAdvPlanes - 1) / kAdvPlanes);
+        launch_adv2(Q, ga, st, s, (const float*)c->rtab, (const float*)src, (const float*)base, (float*)out,
+                    (const float*)c->RL, alpha, beta);
+    } else {
+        dim3 ga(tiles, (2 * Q * Q + kAdvPlanes - 1) / kAdvPlanes);
+        launch_adv<R>(Q, ga, st, s, (const R*)c->rtab, (const R*)src, (const R*)base, (R*)out, (const R*)c->RL,
+                      rhs_out, alpha, beta, mode);
+    }
 }
 
 void queue_stage(Ctx2* c, cudaStream_t st, const void* src, const void* base, void* out, double* rhs_out,
