@@ -260,7 +260,10 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
     const double* S3 = mom + MOM_S3 * NN + sd.node_off;
     const double* G0 = mom + MOM_G0 * NN + sd.node_off;
     const double* G1 = mom + MOM_G1 * NN + sd.node_off;
-    for (int t = threadIdx.x; t < it.nz + 4; t += blockDim.x) {
+    // the node loop on the last threads of the CTA, whose share of the
+    // staging above is smallest, so that it runs beside the tap and table
+    // staging of the first warps
+    for (int t = (int)blockDim.x - 1 - (int)threadIdx.x; t >= 0 && t < it.nz + 4; t += blockDim.x) {
         int i = gidx(it.i0 - 2 + t, nx, bc);
         const bool tile = (t >= 2 && t < it.nz + 2);
         double n = gload<CG>(S0 + i), s1 = gload<CG>(S1 + i), s2 = gload<CG>(S2 + i), g0 = gload<CG>(G0 + i);
@@ -314,16 +317,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename R, bool CG = false>
 __device__ void issue_state_tile(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                  const R* __restrict__ src, long long NF) {
+    static_assert(kZMax + 6 <= 96, "a lane holds at most three tile columns");
     const int Q = sd.Q, nx = sd.nx, bc = sd.bc, W = Z + 6;
     const int cols = it.nz + 6;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < 2 * Q * cols; e += blockDim.x) {
-        const int c = e % cols, r = e / cols;
-        const int k = r % Q, d = r / Q;
-        const int i = gidx(it.i0 - 3 + c, nx, bc);
-        const R* g = src + d * NF + sd.f_off + (long long)k * nx + i;
-        if constexpr (CG) s.F[(size_t)r * W + c] = __ldcg(g);
-        else cp_async_elem<R>(s.F + (size_t)r * W + c, g);
+    // lanes on columns (the node index of a column formed once per lane),
+    // warps on velocity rows
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    int gi[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int c = lane + 32 * q;
+        gi[q] = c < cols ? gidx(it.i0 - 3 + c, nx, bc) : 0;
+    }
+    for (int r = threadIdx.x >> 5; r < 2 * Q; r += nwarps) {
+        const int d = r >= Q ? 1 : 0, k = r - d * Q;
+        const R* g = src + d * NF + sd.f_off + (long long)k * nx;
+        R* row = s.F + (size_t)r * W;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int c = lane + 32 * q;
+            if (c < cols) {
+                if constexpr (CG) row[c] = __ldcg(g + gi[q]);
+                else cp_async_elem<R>(row + c, g + gi[q]);
+            }
+        }
     }
     if constexpr (!CG) cp_async_commit();
 }
@@ -434,7 +451,9 @@ __device__ void node_fields_pass1(const SlabDesc& sd, const WorkItem& it, const 
 // Pass 2: per tile node, the gradients, the Eq. (F1) force (in R), the heat
 // flux, the transport coefficients and the scalars of Sc and Scr.
 // ftap: the slab's force taps [2M+1] (global or staged).
-template <typename R>
+// PREFORCE: the tile's Eq. (F1) force sums are already in s.Scr[Z + t]
+// (formed by other warps, tile_force_sums), else they are summed here.
+template <typename R, bool PREFORCE = false>
 __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                   const R* __restrict__ ftap, const double* __restrict__ mom, long long NN,
                                   unsigned* err, double* fields_out, int tid, int nth) {
@@ -453,7 +472,7 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         double A, B;
         // self-consistent force, Eq. (F1), Simpson taps over |j| <= M
         const R* nn = s.Nr + (t + M);
-        const R f1r = tap_sum<R>(ftap, nn, M);
+        const R f1r = PREFORCE ? s.Scr[Z + t] : tap_sum<R>(ftap, nn, M);
         double f1;
         if constexpr (std::is_same<R, float>::value) f1 = f2d_bits(f1r);
         else f1 = (double)f1r;
@@ -519,6 +538,31 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
             for (int f = 0; f < EVFDLB_NFIELDS; ++f)
                 if (f != 4) fields_out[f * NN + o] = vals[f];
         }
+    }
+}
+
+// The Eq. (F1) force sums of the tile's nodes, f1_t = sum_{|j| <= M}
+// ftap_j n_{t+j}, by half-warps of threads tid, tid + nth, ... (nth a
+// multiple of 32): the 16 lanes of a half-warp split a node's 2M+1 taps and
+// reduce their partial sums by shuffles; the results go to s.Scr[Z + t].
+template <typename R>
+__device__ void tile_force_sums(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                const R* __restrict__ ftap, int tid, int nth) {
+    const int M = sd.M, sub = tid & 15;
+    const unsigned half = 0xffffu << (threadIdx.x & 16);
+    for (int t = tid >> 4; t < it.nz; t += nth >> 4) {
+        const R* nn = s.Nr + t;                      // nn[j + M] = n_{t+j}
+        R a0 = 0, a1 = 0;
+        int j = sub;
+        for (; j + 16 < 2 * M + 1; j += 32) {
+            a0 = fma(ftap[j], nn[j], a0);
+            a1 = fma(ftap[j + 16], nn[j + 16], a1);
+        }
+        if (j < 2 * M + 1) a0 = fma(ftap[j], nn[j], a0);
+        R a = a0 + a1;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(half, a, o);
+        if (sub == 0) s.Scr[Z + t] = a;
     }
 }
 

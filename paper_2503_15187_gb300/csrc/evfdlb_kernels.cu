@@ -105,14 +105,27 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         if (NW == 1) __syncwarp();
         else asm volatile("bar.sync 1, 64;" ::: "memory");
     };
+    // FP32: the Eq. (F1) force sums need only the staged densities, so the
+    // worker warps (whose FP32 work finishes well before the node chain)
+    // form them first, a half-warp per node, and signal on named barrier 3
+    // without waiting; the node warps take them up before pass 2.  FP64
+    // keeps them in the node chain: there the worker warps are the longer
+    // side of the phase and the FP64 pipe the bound.
+    constexpr bool WF = std::is_same<R, float>::value && !DF;
     if (threadIdx.x < 32 * NW) {
         node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32 * NW);
         node_sync();
-        node_fields_pass2<R>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32 * NW);
+        if constexpr (WF) asm volatile("bar.sync 3, %0;" ::"r"((int)blockDim.x) : "memory");
+        node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32 * NW);
         node_sync();
         node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
     } else {
         const int tid = threadIdx.x - 32 * NW, nth = blockDim.x - 32 * NW;
+        if constexpr (WF) {
+            tile_force_sums<R>(sd, it, s, Z, s.Ftap, tid, nth);
+            __threadfence_block();
+            asm volatile("bar.arrive 3, %0;" ::"r"((int)blockDim.x) : "memory");
+        }
         if constexpr (DF) {
             analysis_df(sd, it, s, Fd, reinterpret_cast<const float2*>(s.P), Z, tid, nth);
         } else {
