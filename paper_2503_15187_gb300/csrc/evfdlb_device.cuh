@@ -594,7 +594,31 @@ __device__ void node_fields(const SlabDesc& sd, const WorkItem& it, const Smem<R
 // parallel and adds the force term F1 sqrt(l) a_{l-1}
 // (d/dxi [omega psi_{l-1}] = -sqrt(l) omega psi_l).
 // ---------------------------------------------------------------------------
+// m_0 = 1, m_{l+1} = u m_l / sqrt(l+1) + (T-1) sqrt(l/(l+1)) m_{l-1}, to
+// mm[l stride] (u, T widened or narrowed to R as the node constants are)
 template <typename R>
+__device__ __forceinline__ void hermite_moments(int Q, const TableLayout& L, const R* __restrict__ tab, double u,
+                                                double T, R* mm, int stride) {
+    R ru, Tm1;
+    if constexpr (std::is_same<R, float>::value) {
+        ru = d2f_bits(u);
+        Tm1 = d2f_bits(T - 1.0);
+    } else {
+        ru = (R)u;
+        Tm1 = (R)(T - 1.0);
+    }
+    R m0 = 1, m1 = 0;
+    for (int l = 0; l < Q; ++l) {
+        mm[l * stride] = m0;
+        R mn = fma(ru * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
+        m1 = m0;
+        m0 = mn;
+    }
+}
+
+// MM: also the Hermite moments m_l of the local Gaussian (else another
+// group of warps forms them, node_hermite_moments).
+template <typename R, bool MM = true>
 __device__ void node_coefficients(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                   const R* __restrict__ tab, int tid, int nth) {
     const int Q = sd.Q;
@@ -628,22 +652,19 @@ __device__ void node_coefficients(const SlabDesc& sd, const WorkItem& it, const 
             cG[2 * Z] = (R)(0.6 * K * T * T * D);
             cG[3 * Z] = (R)(0.2 * nu * kq * T + 0.3 * K * T * T * T * B);
         }
-        R ru, Tm1;
-        if constexpr (std::is_same<R, float>::value) {
-            ru = d2f_bits(u);
-            Tm1 = d2f_bits(T - 1.0);
-        } else {
-            ru = (R)u;
-            Tm1 = (R)(T - 1.0);
-        }
-        R m0 = 1, m1 = 0;
-        for (int l = 0; l < Q; ++l) {
-            s.Mm[l * Z + t] = m0;
-            R mn = fma(ru * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
-            m1 = m0;
-            m0 = mn;
-        }
+        if constexpr (MM) hermite_moments<R>(Q, L, tab, u, T, s.Mm + t, Z);
     }
+}
+
+// The Hermite moments m_l = E[psi_l(u + c)], c ~ N(0, T), of the tile's
+// nodes (the recurrence of node_coefficients) from the node inputs u, T of
+// load_node_inputs, by threads tid, tid + nth, ...
+template <typename R>
+__device__ void node_hermite_moments(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                     const R* __restrict__ tab, int tid, int nth) {
+    const int Q = sd.Q;
+    TableLayout L(Q);
+    for (int t = tid; t < it.nz; t += nth) hermite_moments<R>(Q, L, tab, s.U[t + 2], s.T[t + 2], s.Mm + t, Z);
 }
 
 // With DF the coefficients are stored as double-float pairs (float2) in the

@@ -108,9 +108,10 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     // FP32: the Eq. (F1) force sums need only the staged densities, so the
     // worker warps (whose FP32 work finishes well before the node chain)
     // form them first, a half-warp per node, and signal on named barrier 3
-    // without waiting; the node warps take them up before pass 2.  FP64
-    // keeps them in the node chain: there the worker warps are the longer
-    // side of the phase and the FP64 pipe the bound.
+    // without waiting; the node warps take them up before pass 2.  The
+    // workers also form the Hermite moments of the local Gaussian after
+    // their faces.  FP64 keeps both in the node chain: there the worker
+    // warps are the longer side of the phase and the FP64 pipe the bound.
     constexpr bool WF = std::is_same<R, float>::value && !DF;
     if (threadIdx.x < 32 * NW) {
         node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32 * NW);
@@ -118,7 +119,7 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         if constexpr (WF) asm volatile("bar.sync 3, %0;" ::"r"((int)blockDim.x) : "memory");
         node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32 * NW);
         node_sync();
-        node_coefficients<R>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
+        node_coefficients<R, !WF>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
     } else {
         const int tid = threadIdx.x - 32 * NW, nth = blockDim.x - 32 * NW;
         if constexpr (WF) {
@@ -137,6 +138,9 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         }
         if constexpr (DF) faces_df(sd, it, s, Z, tables, tid, nth);
         else faces<R>(sd, it, s, Z, vtab, tid, nth);
+        // FP32: the Hermite moments of the local Gaussian need only u and T
+        // of the node inputs, so the worker warps form them too
+        if constexpr (WF) node_hermite_moments<R>(sd, it, s, Z, rt, tid, nth);
     }
     __syncthreads();
     coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
