@@ -229,10 +229,11 @@ __device__ __forceinline__ void dot2_acc(float& s, float& e, float2 a, float2 b)
 // the full analysis and synthesis tables.
 // CG: the moment sums are read with L2-coherent loads (written earlier in
 // the same launch by other CTAs).
-template <typename R, bool PARITY = false, bool CG = false>
-__device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
-                                 const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
-    const int Q = sd.Q, M = sd.M, nx = sd.nx, bc = sd.bc;
+// The velocity tables of the slab into shared memory: the parity-split
+// analysis pairs and synthesis rows (PARITY), else the full P and S.
+template <typename R, bool PARITY = false>
+__device__ void load_velocity_tables(const SlabDesc& sd, const Smem<R>& s, const R* __restrict__ rtab) {
+    const int Q = sd.Q;
     TableLayout L(Q);
     const R* tab = rtab + sd.tab_off;
     if constexpr (PARITY) {
@@ -248,6 +249,15 @@ __device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const S
             s.S[t] = tab[L.S + t];
         }
     }
+}
+
+// The velocity tables and the node inputs of the tile (TABLES false: the
+// node inputs only, the tables being staged already).
+template <typename R, bool PARITY = false, bool CG = false, bool TABLES = true>
+__device__ void load_node_inputs(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
+                                 const R* __restrict__ rtab, const double* __restrict__ mom, long long NN) {
+    const int M = sd.M, nx = sd.nx, bc = sd.bc;
+    if constexpr (TABLES) load_velocity_tables<R, PARITY>(sd, s, rtab);
     const double* S0 = mom + MOM_S0 * NN + sd.node_off;
 #pragma unroll 2
     for (int t = threadIdx.x; t < it.nz + 2 * M; t += blockDim.x) {

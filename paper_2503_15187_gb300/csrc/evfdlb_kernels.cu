@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "evfdlb_device.cuh"
 
@@ -70,15 +71,14 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
 
     // FP64 / FP32: parity-split tables and state tile (half the transform
     // products); FP64_DF: the full tables as float pairs and the state tile
-    // split into float pairs in the EO block
-    // (FP64 / FP32: the tile by asynchronous copies, issued first, so that
-    // they are in flight with the node inputs' loads and arithmetic)
+    // split into float pairs in the EO block.
+    // The inputs that no stage writes come first (velocity tables, force and
+    // Fischer-Methfessel taps, velocity powers): in a programmatic launch
+    // they are staged while the previous stage still runs, and
+    // griddepcontrol.wait then holds back the reads of its state and moment
+    // sums until that stage has completed (a no-op in a plain launch).
     float2* Fd = DF ? reinterpret_cast<float2*>(s.EO) : nullptr;
-    if constexpr (!DF) issue_state_tile<R, CG>(sd, it, s, Z, src, NF);
-    load_node_inputs<R, !DF, CG>(sd, it, s, Z, rtab, mom_in, NN);
-    if constexpr (DF) load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
-    // the slab's force and Fischer-Methfessel taps, read in warp 0's serial
-    // tap loops, staged once into shared memory
+    load_velocity_tables<R, !DF>(sd, s, rtab);
     for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.Ftap[j] = rtaps[sd.tap_off + j];
     for (int j = threadIdx.x; j < 2 * sd.m + 1; j += blockDim.x) s.Mtap[j] = taps[sd.tap_off + 2 * sd.M + 1 + j];
     // velocity powers of the closing moment sums, formed once per CTA
@@ -87,6 +87,12 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         const int xo = sd.tab_off + TableLayout(Q).xi;
         velocity_powers<R>(Q, tables + xo, vt + xo, s.Vp, s.Vr, threadIdx.x, blockDim.x);
     }
+    if constexpr (!CG) asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the state tile by asynchronous copies, issued first, so that they are
+    // in flight with the node inputs' loads and arithmetic
+    if constexpr (!DF) issue_state_tile<R, CG>(sd, it, s, Z, src, NF);
+    load_node_inputs<R, !DF, CG, false>(sd, it, s, Z, rtab, mom_in, NN);
+    if constexpr (DF) load_state_tile<R>(sd, it, s, Z, src, NF, Fd);
     if constexpr (!DF && !CG) cp_async_wait_all();
     __syncthreads();
     // The node warps form the node-level quantities of the tile (node fields,
@@ -145,6 +151,9 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     __syncthreads();
     coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);
     __syncthreads();
+    // the next stage (a programmatic launch) may now be scheduled beside
+    // this CTA and stage its constant inputs
+    if constexpr (!CG) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // Phase 5: synthesis, advection, relaxation and the RK stage.
     const R* xi = rt + L.xi;
@@ -622,6 +631,27 @@ size_t stage_smem_bytes_p(int prec, int Q, int Z, int M) {
 // block (4 H Z >= 2 Q Z doubles).
 size_t stage_smem_bytes_df(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M); }
 
+// Launches a stage kernel as a programmatic dependent of the kernel before
+// it in the stream: its CTAs may be scheduled once every CTA of that kernel
+// has reached griddepcontrol.launch_dependents (or exited), and stage their
+// constant inputs; griddepcontrol.wait in the kernel holds back everything
+// that reads the previous kernel's results until it has completed.  Launch
+// errors are left for cudaGetLastError, as with <<<>>>.
+template <typename... P, typename... A>
+static void launch_stage_pdl(void (*k)(P...), int grid, int threads, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 cudaError_t configure_df(size_t smem_bytes) {
     return cudaFuncSetAttribute(stage_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);
@@ -632,9 +662,9 @@ void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* s
                      const double* tables, const double* dftab, const double* taps, const double* src,
                      const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
                      long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    stage_kernel<double, true><<<nitems, StageThreads<double, true>::value, smem, st>>>(slabs, items, tables, dftab, taps, taps, src, base,
-                                                               out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta,
-                                                               mode, Z, err);
+    launch_stage_pdl(stage_kernel<double, true>, nitems, StageThreads<double, true>::value, smem, st, slabs, items,
+                     tables, dftab, taps, taps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z,
+                     err);
 }
 
 template <typename R>
@@ -678,9 +708,8 @@ static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const Sl
                               double* rhs_out, const double* mom_in, double* mom_out, long long NF, long long NN,
                               double alpha, double beta, int mode, int Z, unsigned* err, bool beside = false) {
     (void)beside;
-    stage_kernel<double><<<nitems, StageThreads<double>::value, smem, st>>>(
-        slabs, items, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode,
-        Z, err);
+    launch_stage_pdl(stage_kernel<double>, nitems, StageThreads<double>::value, smem, st, slabs, items, tables, rtab,
+                     taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
@@ -689,9 +718,9 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err) {
     if (prec == EVFDLB_FP32)
-        stage_kernel<float><<<nitems, StageThreads<float>::value, smem, st>>>(
-            slabs, items, tables, (const float*)rtab, taps, (const float*)rtaps, (const float*)src,
-            (const float*)base, (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+        launch_stage_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
+                         (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base,
+                         (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
     else
         launch_stage_fp64(nitems, smem, st, slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps,
                           (const double*)src, (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN,
