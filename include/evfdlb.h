@@ -182,7 +182,10 @@ evfdlb_status evfdlb_step_async(evfdlb_ctx* ctx, int64_t nsteps);
  * slab four totals {mass, momentum, energy incl. mean-field energy, mean-field
  * energy} ([4 * nbatch], always host memory).  For dim = 2: u and q are
  * [2][nx * ny] and the totals are {mass, momentum x, momentum y, kinetic +
- * internal energy} (the 2D mean-field energy is not formed).  Mean-field energy:
+ * internal energy}: the second momentum component takes the fourth slot,
+ * and the 2D mean-field energy is not formed (it would need the potential
+ * of the z-integrated plane kernel on the force disc's taps, a second
+ * convolution per call, and a fifth slot).  Mean-field energy:
  * EV1: (dx/2) sum_i n_i sum_j s_j [Phi(j dx) - Phi(r_cut)] n_{i+j} with Phi the
  * even potential whose derivative is the Eq. (F1) kernel and s_j Simpson
  * weights; EV2: (dx/2) sum_i n_i psi_i with psi = -2a n - kappa d2n/dz2 (the
