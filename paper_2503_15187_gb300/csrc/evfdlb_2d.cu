@@ -1052,34 +1052,73 @@ constexpr size_t kA2Smem = sizeof(float) * 2 * kA2Buf + sizeof(float2) * (kAdvY 
 
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// A thread's share of the whole-chunk copies of one velocity, the same for
+// every velocity of the CTA and so formed once: shared offsets, in-plane
+// global offsets (below N < 2^31) and, per copy, whether it reads the G
+// plane; a negative shared offset marks an absent copy.
+struct Adv2Copies {
+    int hs[2], hg[2];   // 16-byte chunks of the halo interior
+    int ss[2], sg[2];   // 4-byte elements of the halo side columns
+    int rs, rg;         // the 16-byte chunk of RL (and base) every thread copies
+    unsigned gmask;     // bit q: hs[q] reads G; bit 2+q: ss[q]; bit 4: the RL chunk
+};
+static_assert(2 * kAdvY * 8 == 256 && 2 * kA2Rows * 8 <= 512 && 2 * kA2Rows * 6 <= 512,
+              "copy shares of a 256-thread CTA");
+
+__device__ __forceinline__ Adv2Copies adv2_plan(const int* rowoff, const int* coloff, int x0, int y0, int nx) {
+    Adv2Copies p;
+    p.gmask = 0u;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = t + 256 * q;
+        p.hs[q] = -1;
+        p.ss[q] = -1;
+        if (e < 2 * kA2Rows * 8) {
+            const int c = e % 8, r = (e / 8) % kA2Rows, d = e / (8 * kA2Rows);
+            p.hs[q] = (d * kA2Rows + r) * kA2Row + 4 + 4 * c;
+            p.hg[q] = rowoff[r] + x0 + 4 * c;
+            if (d) p.gmask |= 1u << q;
+        }
+        if (e < 2 * kA2Rows * 6) {
+            const int c = e % 6, r = (e / 6) % kA2Rows, d = e / (6 * kA2Rows);
+            const int i = c < 3 ? c : 32 + c;               // halo columns 0..2 and 35..37
+            p.ss[q] = (d * kA2Rows + r) * kA2Row + i + 1;
+            p.sg[q] = rowoff[r] + coloff[i];
+            if (d) p.gmask |= 4u << q;
+        }
+    }
+    const int c = t % 8, r = (t / 8) % kAdvY, d = t / (8 * kAdvY);
+    p.rs = (d * kAdvY + r) * kAdvX + 4 * c;
+    p.rg = (y0 + r) * nx + x0 + 4 * c;
+    if (d) p.gmask |= 16u;
+    return p;
+}
+
 // Queues the asynchronous copies of velocity k (planes at F + k N and
-// F + NF + k N) into buffer `buf`: whole 16-byte chunks for the aligned
-// interior when `fast`, element copies otherwise (wrapped columns, a ragged
-// tile edge, nx not a multiple of 4).
+// F + NF + k N) into buffer `buf`: when `fast`, the thread's whole 16-byte
+// chunks of the aligned interior and its side-column elements (plan `cp`);
+// otherwise element copies of everything (wrapped columns, a ragged tile
+// edge, nx not a multiple of 4).
 __device__ __forceinline__ void adv2_issue(float* buf, const float* src, const float* RL, const float* base,
                                            long long kN, long long NF, const int* rowoff, const int* coloff,
-                                           int x0, int y0, int nx, int ny, bool fast, bool with_base) {
+                                           int x0, int y0, int nx, int ny, bool fast, bool with_base,
+                                           const Adv2Copies& cp) {
     float* H = buf;
     float* Rs = buf + kA2H;
     float* Bs = Rs + kA2T;
     const int t = threadIdx.x;
     if (fast) {
-        // interior chunks: 2 d x kA2Rows rows x 8 chunks; side columns: 2 d x rows x 6
-        for (int e = t; e < 2 * kA2Rows * 8; e += 256) {
-            const int c = e % 8, r = (e / 8) % kA2Rows, d = e / (8 * kA2Rows);
-            cp_async16(H + (d * kA2Rows + r) * kA2Row + 4 + 4 * c, src + d * NF + kN + rowoff[r] + x0 + 4 * c);
+        const float* sF = src + kN;
+        const float* sG = sF + NF;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (cp.hs[q] >= 0) cp_async16(H + cp.hs[q], ((cp.gmask >> q) & 1u ? sG : sF) + cp.hg[q]);
+            if (cp.ss[q] >= 0) cp_async_elem<float>(H + cp.ss[q], ((cp.gmask >> (2 + q)) & 1u ? sG : sF) + cp.sg[q]);
         }
-        for (int e = t; e < 2 * kA2Rows * 6; e += 256) {
-            const int c = e % 6, r = (e / 6) % kA2Rows, d = e / (6 * kA2Rows);
-            const int i = c < 3 ? c : 32 + c;               // halo columns 0..2 and 35..37
-            cp_async_elem<float>(H + (d * kA2Rows + r) * kA2Row + i + 1, src + d * NF + kN + rowoff[r] + coloff[i]);
-        }
-        for (int e = t; e < 2 * kAdvY * 8; e += 256) {
-            const int c = e % 8, r = (e / 8) % kAdvY, d = e / (8 * kAdvY);
-            const long long g = d * NF + kN + (long long)(y0 + r) * nx + x0 + 4 * c;
-            cp_async16(Rs + (d * kAdvY + r) * kAdvX + 4 * c, RL + g);
-            if (with_base) cp_async16(Bs + (d * kAdvY + r) * kAdvX + 4 * c, base + g);
-        }
+        const long long g = kN + ((cp.gmask & 16u) ? NF : 0) + cp.rg;
+        cp_async16(Rs + cp.rs, RL + g);
+        if (with_base) cp_async16(Bs + cp.rs, base + g);
     } else {
         for (int e = t; e < 2 * kA2Rows * (kAdvX + 6); e += 256) {
             const int i = e % (kAdvX + 6), r = (e / (kAdvX + 6)) % kA2Rows, d = e / ((kAdvX + 6) * kA2Rows);
@@ -1096,8 +1135,11 @@ __device__ __forceinline__ void adv2_issue(float* buf, const float* src, const f
     }
 }
 
+// three CTAs per SM: with up to 85 registers the constants of the packed
+// arithmetic and the copy plan stay in registers (with the 64 of four CTAs
+// per SM the kernel executed 9 % more instructions and took 10 % longer)
 template <int Q>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
 k2_adv2(Slab2 s, const float* __restrict__ rtab, const float* __restrict__ src, const float* base, float* out,
         const float* __restrict__ RL, double alpha, double beta) {
     constexpr int K = Q * Q, RPW = kAdvY / 8;
@@ -1119,6 +1161,7 @@ k2_adv2(Slab2 s, const float* __restrict__ rtab, const float* __restrict__ src, 
     }
     __syncthreads();
     const bool fast = (nx % 4 == 0) && (x0 + kAdvX <= nx) && (y0 + kAdvY <= ny);
+    const Adv2Copies cplan = adv2_plan(rowoff, coloff, x0, y0, nx);
     const float eps = (float)s.weno_eps, idx = (float)s.inv_dx, dt = (float)s.dt, ralpha = (float)alpha,
                 rbeta = (float)beta;
     const bool with_base = (alpha != 0.0);
@@ -1143,11 +1186,11 @@ k2_adv2(Slab2 s, const float* __restrict__ rtab, const float* __restrict__ src, 
     }
     const int k0 = blockIdx.y * kAdvPlanes, k1 = min(k0 + kAdvPlanes, K);
     constexpr int HG = kA2Rows * kA2Row;                    // G's halo after F's
-    adv2_issue(buf0, src, RL, base, (long long)k0 * N, NF, rowoff, coloff, x0, y0, nx, ny, fast, with_base);
+    adv2_issue(buf0, src, RL, base, (long long)k0 * N, NF, rowoff, coloff, x0, y0, nx, ny, fast, with_base, cplan);
     cp_async_commit();
     if (k0 + 1 < k1)
         adv2_issue(buf0 + kA2Buf, src, RL, base, (long long)(k0 + 1) * N, NF, rowoff, coloff, x0, y0, nx, ny, fast,
-                   with_base);
+                   with_base, cplan);
     cp_async_commit();
     for (int k = k0; k < k1; ++k) {
         float* buf = buf0 + ((k - k0) & 1) * kA2Buf;
@@ -1193,7 +1236,7 @@ k2_adv2(Slab2 s, const float* __restrict__ rtab, const float* __restrict__ src, 
         __syncthreads();                                    // this buffer and the faces consumed
         if (k + 2 < k1)
             adv2_issue(buf, src, RL, base, (long long)(k + 2) * N, NF, rowoff, coloff, x0, y0, nx, ny, fast,
-                       with_base);
+                       with_base, cplan);
         cp_async_commit();
     }
 }
