@@ -1038,49 +1038,82 @@ __device__ inline void faces_df(const SlabDesc& sd, const WorkItem& it, const Sm
     }
 }
 
-// One raw moment sum of one node from a column h[k * stride] (k < Q).  The
-// conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
-// (heat flux) in R.  The velocity powers come from xp = [xi, xi^2, xi^3]
-// (FP64) and xr = [xi, xi^3] (R).
+// One raw moment sum of one node from a column h[k * stride] (k < Q), formed
+// as P parts over k in [p Q / P, (p+1) Q / P) combined in a fixed order, so
+// that the parts may be formed by different warps (tile_moment_sums_staged)
+// with the same result.  The conserved moments (S0, S1, S2 of F and G0) are
+// summed in FP64; S3 and G1 (heat flux) in R within a part.  The velocity
+// powers come from xp = [xi, xi^2, xi^3] (FP64) and xr = [xi, xi^3] (R).
 template <typename R>
-__device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
-                                             const double* __restrict__ xp, const R* __restrict__ xr) {
+__device__ __forceinline__ double moment_part(int which, int Q, int k0, int k1, const R* h, long long stride,
+                                              const double* __restrict__ xp, const R* __restrict__ xr) {
     const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
     if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
         which == MOM_G0) {
-        // four partial sums (a quarter of the FP64 dependent chain); a float
-        // state is widened by bit surgery (exact for normal floats; no FP64
+        // interleaved chains: four over a whole sum (FP64 state, one part),
+        // two over a quarter (FP32 state, four parts); a float state is
+        // widened by bit surgery (exact for normal floats; no FP64
         // conversion instruction)
         auto wide = [](R v) -> double {
             if constexpr (std::is_same<R, float>::value) return f2d_bits(v);
             else return v;
         };
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int k = 0;
-        if (p == 0) {
-            for (; k + 3 < Q; k += 4) {
-                a0 += wide(h[k * stride]);
-                a1 += wide(h[(k + 1) * stride]);
-                a2 += wide(h[(k + 2) * stride]);
-                a3 += wide(h[(k + 3) * stride]);
+        const double* w = xp + (p > 0 ? p - 1 : 0) * Q;
+        auto acc = [&](double a, int k) { return p == 0 ? a + wide(h[k * stride]) : fma(w[k], wide(h[k * stride]), a); };
+        if constexpr (std::is_same<R, float>::value) {
+            double a0 = 0.0, a1 = 0.0;
+            int k = k0;
+            for (; k + 1 < k1; k += 2) {
+                a0 = acc(a0, k);
+                a1 = acc(a1, k + 1);
             }
-            for (; k < Q; ++k) a0 += wide(h[k * stride]);
+            if (k < k1) a0 = acc(a0, k);
+            return a0 + a1;
         } else {
-            const double* w = xp + (p - 1) * Q;
-            for (; k + 3 < Q; k += 4) {
-                a0 = fma(w[k], wide(h[k * stride]), a0);
-                a1 = fma(w[k + 1], wide(h[(k + 1) * stride]), a1);
-                a2 = fma(w[k + 2], wide(h[(k + 2) * stride]), a2);
-                a3 = fma(w[k + 3], wide(h[(k + 3) * stride]), a3);
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int k = k0;
+            for (; k + 3 < k1; k += 4) {
+                a0 = acc(a0, k);
+                a1 = acc(a1, k + 1);
+                a2 = acc(a2, k + 2);
+                a3 = acc(a3, k + 3);
             }
-            for (; k < Q; ++k) a0 = fma(w[k], wide(h[k * stride]), a0);
+            for (; k < k1; ++k) a0 = acc(a0, k);
+            return (a0 + a1) + (a2 + a3);
         }
-        return (a0 + a1) + (a2 + a3);
     }
     const R* w = xr + (p == 1 ? 0 : Q);
     R racc = 0;
-    for (int k = 0; k < Q; ++k) racc = fma(w[k], h[k * stride], racc);
+    for (int k = k0; k < k1; ++k) racc = fma(w[k], h[k * stride], racc);
     return (double)racc;
+}
+
+// Parts of a moment sum.  FP32 state (whose stage leaves only a few warps
+// of FP64 work at its end): 4 where the staging block of
+// tile_moment_sums_staged holds them (kNumMoments x 4 doubles per node),
+// else 2, else 1.  FP64 state: 1 (one sum per warp measured faster there:
+// the FP64 stage keeps all its warps on FP64 work anyway).
+template <typename R>
+__host__ __device__ inline int moment_parts(int Q) {
+    if (std::is_same<R, double>::value) return 1;
+    const int room = (int)sizeof(R) * 4 * Q;   // bytes per node of the 4 Q Z-element block
+    return room >= 8 * kNumMoments * 4 ? 4 : (room >= 8 * kNumMoments * 2 ? 2 : 1);
+}
+
+// The fixed combination of the parts: ((p0 + p1) + (p2 + p3)) for four.
+__device__ __forceinline__ double combine_parts(const double* v, int P) {
+    if (P == 4) return (v[0] + v[1]) + (v[2] + v[3]);
+    if (P == 2) return v[0] + v[1];
+    return v[0];
+}
+
+template <typename R>
+__device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
+                                             const double* __restrict__ xp, const R* __restrict__ xr) {
+    const int P = moment_parts<R>(Q);
+    double v[4];
+    for (int q = 0; q < P; ++q) v[q] = moment_part<R>(which, Q, q * Q / P, (q + 1) * Q / P, h, stride, xp, xr);
+    return combine_parts(v, P);
 }
 
 // Velocity powers of moment_sum from the tables xi (FP64) and rxi (R).
@@ -1106,13 +1139,37 @@ __device__ void tile_moment_sums_staged(const SlabDesc& sd, const WorkItem& it, 
                                         const double* xp, const R* xr, double* __restrict__ mom_out, long long NN) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     if (nz <= 32 && blockDim.x >= 32 * kNumMoments) {
-        // one moment kind per warp, lanes on nodes: no divergence between
-        // the plain and the weighted sums inside a warp
-        const int which = threadIdx.x >> 5, t = threadIdx.x & 31;
-        if (which < kNumMoments && t < nz) {
-            const int d = which >= MOM_G0 ? 1 : 0;
-            const R* h = s.F + (size_t)d * Q * W + t + 3;
-            mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xp, xr);
+        // one (kind, part) per warp task, lanes on nodes: the parts of a sum
+        // run on different warps, spread over the SM's sub-partitions (task i
+        // on warp i mod warps; the FP64 kinds first), and meet in the block
+        // of the coefficients and the analysis, free after the synthesis
+        const int P = moment_parts<R>(Q), nw = blockDim.x >> 5, t = threadIdx.x & 31;
+        if (P == 1) {   // one sum per warp, written directly
+            const int which = threadIdx.x >> 5;
+            if (which < kNumMoments && t < nz) {
+                const int d = which >= MOM_G0 ? 1 : 0;
+                const R* h = s.F + (size_t)d * Q * W + t + 3;
+                mom_out[which * NN + sd.node_off + it.i0 + t] = moment_part<R>(which, Q, 0, Q, h, W, xp, xr);
+            }
+            return;
+        }
+        double* part = reinterpret_cast<double*>(s.C);            // [kind][part][nz]
+        // FP64 kinds first: for R = float, S3 and G1 are the R-precision ones
+        const int order[kNumMoments] = {MOM_S0, MOM_S1, MOM_S2, MOM_G0, MOM_S3, MOM_G1};
+        for (int task = threadIdx.x >> 5; task < kNumMoments * P; task += nw) {
+            const int which = order[task / P], q = task % P;
+            if (t < nz) {
+                const int d = which >= MOM_G0 ? 1 : 0;
+                const R* h = s.F + (size_t)d * Q * W + t + 3;
+                part[(which * P + q) * nz + t] = moment_part<R>(which, Q, q * Q / P, (q + 1) * Q / P, h, W, xp, xr);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
+            const int which = e / nz, tt = e % nz;
+            double v[4];
+            for (int q = 0; q < P; ++q) v[q] = part[(which * P + q) * nz + tt];
+            mom_out[which * NN + sd.node_off + it.i0 + tt] = combine_parts(v, P);
         }
         return;
     }
