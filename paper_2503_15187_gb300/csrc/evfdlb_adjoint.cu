@@ -6,28 +6,36 @@
 // phi_a of Eq. (sutherland) (through the Eq. (F1) force, which is linear in
 // phi_a).
 //
-// One stage of the reverse sweep, given the adjoint ybar of the stage output
-// and the stage input u (recomputed from a checkpoint), forms
+// One stage of the reverse sweep, given the adjoint ybar of the stage output,
+// the stage input u and the node fields of u (both stored by the segment
+// recompute), forms
 //   out     = ca ybar + J(u)^T v + cc acc_in,   v = cb dt ybar,
 //   acc_out = cacc acc_in + cy ybar,
 // where J(u) is the Jacobian of L at u, in two launches:
 //   adj_local_kernel  -- per node tile: the velocity-space part of J^T v
-//                        (transposed Hermite synthesis and analysis, the
-//                        transposed WENO-5 faces, relaxation) and the adjoints
-//                        of the node fields that L reads (n, u, T, q, chi, X,
-//                        the three gradients and the force F1);
+//                        (transposed WENO-5 faces, each face of the slab
+//                        differentiated once by the tile that owns it;
+//                        transposed Hermite synthesis and analysis on the
+//                        parity-split velocity set; relaxation) and the
+//                        adjoints of the node fields that L reads (n, u, T,
+//                        q, chi, X, the three gradients and the force F1);
 //   adj_moments_kernel-- per node tile: transposed fourth-order differences,
 //                        the chain X = n^2 chi T, chi(nbar) of Eq. (carnstar)
 //                        (on the tile and a Fischer-Methfessel halo), the
 //                        transposed Fischer-Methfessel average and Eq. (F1)
 //                        convolution (correlations), the chain from
-//                        (n, u, T, q) to the raw moment sums, and their
-//                        transpose onto F and G.
-// Forward quantities are recomputed from the stage input and its raw moment
-// sums with the same device code as the forward kernels.
+//                        (n, u, T, q) to the raw moment sums, their transpose
+//                        onto F and G, and the face terms that reach the tile
+//                        from faces owned by its neighbours.
+// FP64 is the GB300's scarcest pipe, and a node tile is small, so the work
+// of every phase is spread over all warps of the CTA (lanes on velocities,
+// faces or tap chunks), and the per-node chains that remain (the Hermite
+// moments of N(u, T), the derivatives of the transport maps) run beside the
+// WENO-5 faces, which take most of the pipe.
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "evfdlb.h"
 #include "evfdlb_device.cuh"
 
 namespace evfdlb {
@@ -35,51 +43,58 @@ namespace evfdlb {
 // per-node adjoints written by adj_local_kernel ([kNumNodeAdj][NN])
 enum { AD_N = 0, AD_U, AD_T, AD_Q, AD_CHI, AD_X, AD_DX, AD_DT, AD_DU, AD_F1, kNumNodeAdj };
 
-constexpr int kHaloH = 5;   // state halo of the transposed WENO-5 faces
-constexpr int kHaloV = 3;   // halo of v
+// slots of the node fields ([EVFDLB_NFIELDS][NN], the layout of evfdlb_fields)
+enum { FL_N = 0, FL_U, FL_T, FL_Q, FL_NBAR, FL_CHI, FL_F1, FL_MU, FL_TAU, FL_PR, FL_NU, FL_A, FL_B, FL_DU, FL_X, FL_XX };
 
-struct AdjSmem {
-    Smem<double> f;   // S, N, U, T, X, Chi, Sc, Scr of the forward layout; f.P holds
-                      // the scaled transposed analysis table PT[l][j] = sqrt(l) psi_{l-1}(xi_j)
-    double* H;        // state tile [2][Q][Z + 2 kHaloH]
-    double* V;        // v tile [2][Q][Z + 2 kHaloV]
-    double* Cb;       // cbar_l = sum_k S_kl v_k, [2][Q][Z]
-    double* Ha;       // sum_l PT[l][j] cbar_l, [2][Q][Z]
-    double* Hw;       // transposed WENO-5 part, [2][Q][Z]
-    double* Red;      // per (distribution, node) sums [2][8][Z]
-    // f.Mtap [2M+1] (the 2m+1 Fischer-Methfessel taps) and f.Ftap [2M+1]
-    // (the Eq. (F1) taps) follow Red, staged once per CTA
+// per-node derivatives of the node maps, formed before the adjoints arrive:
+// nu(n, T, chi) [NNU, TNU, CNU], kq = (1 - Pr(x)) q [QKQ = dkq/dq, NKQ, CKQ],
+// K = -b n^2 chi [NK, CK], and 1/X, A/X, 1/T, B/T for the gradient ratios
+enum { J_NNU = 0, J_TNU, J_CNU, J_QKQ, J_NKQ, J_CKQ, J_NK, J_CK, J_IX, J_AIX, J_IT, J_BIT, kNumJac };
+
+constexpr int kZAdj = 32;   // largest node tile of the sweep kernels
+constexpr int kSumChunks = 4;    // lanes per (distribution, node) of the Hermite sums
+constexpr int kTapChunks = 8;    // lanes per node of the tap correlations
+
+// Shared-memory layout of adj_local_kernel (doubles).  NP = (Q + 1)/2 rows of
+// the parity-split synthesis table and columns of the transposed analysis
+// table (node k pairs with Q-1-k; the middle node of an odd Q stands alone).
+// The state tile holds nodes i0-3 .. i0+nz+1 (the stencils of the tile's
+// own faces), v holds i0-1 .. i0+nz-1.  The face gradients G5 are dead once
+// gathered; Ha and the per-node sums Red then reuse their block.
+struct AdjLay {
+    int NP, WH, WV;
+    size_t S, PT, xi, r1, r2, r3, rinv, rr, H, V, Fl, J, Cc, Mm, VE, Cl, Cb, Hw, G5, Ha, Red, total;
+    __host__ __device__ AdjLay(int Q, int Z) {
+        NP = (Q + 1) / 2;
+        WH = Z + 5;
+        WV = Z + 1;
+        size_t o = 0;
+        S = o;    o += (size_t)NP * Q;         // S[k][l], k < NP
+        PT = o;   o += (size_t)Q * NP;         // PT[l][j] = sqrt(l) psi_{l-1}(xi_j), j < NP
+        xi = o;   o += Q;
+        r1 = o;   o += Q;
+        r2 = o;   o += Q;
+        r3 = o;   o += Q;
+        rinv = o; o += Q;
+        rr = o;   o += Q;
+        H = o;    o += 2 * (size_t)Q * WH;     // [2Q][WH]
+        V = o;    o += 2 * (size_t)Q * WV;     // [2Q][WV]
+        Fl = o;   o += (size_t)EVFDLB_NFIELDS * Z;
+        J = o;    o += (size_t)kNumJac * Z;
+        Cc = o;   o += 8 * (size_t)Z;          // c0..c3 per distribution [2][4][Z]
+        Mm = o;   o += (size_t)Q * Z;          // m_l(u, T) [Q][Z]
+        VE = o;   o += 4 * (size_t)NP * Z;     // v_k +- v_{Q-1-k} [2 d][2 parity][NP][Z]
+        Cl = o;   o += 2 * (size_t)Q * Z;      // c_l [2Q][Z]
+        Cb = o;   o += 2 * (size_t)Q * Z;      // cbar_l [2Q][Z]
+        Hw = o;   o += 2 * (size_t)Q * Z;      // transposed WENO-5 part [2Q][Z]
+        G5 = o;   o += 10 * (size_t)Q * Z;     // face gradients [5][2Q][Z]
+        Ha = G5;                               // [2Q][Z]
+        Red = G5 + 2 * (size_t)Q * Z;          // [2][8][Z] (10 Q Z >= 2 Q Z + 16 Z for Q >= 2)
+        total = o;
+    }
 };
 
-__host__ __device__ inline size_t adj_smem_doubles(int Q, int Z, int M) {
-    return 2 * (size_t)Q * Q + (Z + 2 * M) + 4 * (size_t)(Z + 4) + (size_t)kNumScalars * Z + 2 * (size_t)Z +
-           2 * (size_t)Q * (Z + 2 * kHaloH) + 2 * (size_t)Q * (Z + 2 * kHaloV) + 6 * (size_t)Q * Z + 16 * (size_t)Z +
-           2 * (size_t)(2 * M + 1);
-}
-
-__device__ inline AdjSmem adj_carve(double* base, int Q, int Z, int M) {
-    AdjSmem s;
-    s.f.P = base;
-    s.f.S = s.f.P + Q * Q;
-    s.f.N = s.f.S + Q * Q;
-    s.f.Nr = s.f.N;
-    s.f.U = s.f.N + (Z + 2 * M);
-    s.f.T = s.f.U + (Z + 4);
-    s.f.X = s.f.T + (Z + 4);
-    s.f.Chi = s.f.X + (Z + 4);
-    s.f.Sc = s.f.Chi + (Z + 4);
-    s.f.Scr = s.f.Sc + kNumScalars * Z;
-    s.f.C = s.f.A = s.f.F = s.f.Face = nullptr;
-    s.H = s.f.Scr + 2 * Z;
-    s.V = s.H + 2 * Q * (Z + 2 * kHaloH);
-    s.Cb = s.V + 2 * Q * (Z + 2 * kHaloV);
-    s.Ha = s.Cb + 2 * Q * Z;
-    s.Hw = s.Ha + 2 * Q * Z;
-    s.Red = s.Hw + 2 * Q * Z;
-    s.f.Mtap = s.Red + 16 * Z;
-    s.f.Ftap = s.f.Mtap + (2 * M + 1);
-    return s;
-}
+__host__ __device__ inline size_t adj_smem_doubles(int Q, int Z) { return AdjLay(Q, Z).total; }
 
 // Gradient of the WENO-5 face value Phi(v0..v4) (upwind side v0..v2), times
 // pb: g_r = pb dPhi/dv_r.  Phi is taken in the difference form of the forward
@@ -130,166 +145,336 @@ __device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, doub
 
 __global__ void __launch_bounds__(kThreads)
 adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
-                 const double* __restrict__ tables, const double* __restrict__ taps,
-                 const double* __restrict__ src, const double* __restrict__ mom, const double* __restrict__ ybar,
-                 const double* acc_in, double* acc_out, double* out, double* __restrict__ nadj,
-                 double* __restrict__ phis, long long NF, long long NN, double ca, double cb, int use_dt,
-                 double cc, double cacc, double cy, int Z, unsigned* err) {
-    extern __shared__ double smem[];
+                 const double* __restrict__ tables, const double* __restrict__ src, const double* __restrict__ fld,
+                 const double* __restrict__ ybar, const double* acc_in, double* acc_out, double* out,
+                 double* __restrict__ nadj, double* __restrict__ phis, double* __restrict__ gface, long long NF,
+                 long long NN, double ca, double cb, int use_dt, double cc, double cacc, double cy, int Z) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int s_next;                       // next warp-sized group of faces
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int Q = sd.Q, nz = it.nz, nx = sd.nx, bc = sd.bc;
-    const int WH = Z + 2 * kHaloH, WV = Z + 2 * kHaloV;
-    AdjSmem s = adj_carve(smem, Q, Z, sd.M);
+    const AdjLay Ly(Q, Z);
+    const int NP = Ly.NP, WH = Ly.WH, WV = Ly.WV;
+    double *sS = smem + Ly.S, *sPT = smem + Ly.PT, *sxi = smem + Ly.xi, *sr1 = smem + Ly.r1;
+    double *sr2 = smem + Ly.r2, *sr3 = smem + Ly.r3, *srinv = smem + Ly.rinv, *srr = smem + Ly.rr;
+    double *sH = smem + Ly.H, *sV = smem + Ly.V, *sFl = smem + Ly.Fl, *sJ = smem + Ly.J, *sCc = smem + Ly.Cc;
+    double *sMm = smem + Ly.Mm, *sVE = smem + Ly.VE, *sCl = smem + Ly.Cl, *sCb = smem + Ly.Cb;
+    double *sHw = smem + Ly.Hw, *sG5 = smem + Ly.G5, *sHa = smem + Ly.Ha, *sRed = smem + Ly.Red;
     TableLayout L(Q);
     const double* tab = tables + sd.tab_off;
-    const double* xi = tab + L.xi;
-    const double* r1 = tab + L.r1;
-    const double* r2 = tab + L.r2;
-    const double* r3 = tab + L.r3;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const long long row0 = sd.f_off + it.i0;     // + d NF + k nx: velocity k, distribution d, node i0
 
-    // phase 0: tables and node inputs, the state tile (+-5) and v (+-3)
-    load_node_inputs<double>(sd, it, s.f, Z, tables, mom, NN);
-    for (int e = threadIdx.x; e < 2 * Q * (nz + 2 * kHaloH); e += blockDim.x) {
-        int c = e % (nz + 2 * kHaloH), r = e / (nz + 2 * kHaloH);
-        int k = r % Q, d = r / Q;
-        s.H[r * WH + c] = src[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloH + c, nx, bc)];
+    // Step 0: tables, the state tile (i0-3 .. i0+nz+1), v = cb dt ybar
+    // (i0-1 .. i0+nz-1) and the node fields of the tile.
+    if (tid == 0) s_next = 0;
+    for (int e = tid; e < NP * Q; e += nth) sS[e] = tab[L.S + e];
+    for (int e = tid; e < Q * NP; e += nth) {
+        const int l = e / NP, j = e - l * NP;
+        sPT[e] = (l == 0) ? 0.0 : tab[L.r1 + l] * tab[L.P + (l - 1) * Q + j];
+    }
+    for (int e = tid; e < Q; e += nth) {
+        sxi[e] = tab[L.xi + e];
+        sr1[e] = tab[L.r1 + e];
+        sr2[e] = tab[L.r2 + e];
+        sr3[e] = tab[L.r3 + e];
+        srinv[e] = tab[L.rinv + e];
+        srr[e] = tab[L.rr + e];
+    }
+    for (int e = tid; e < 2 * Q * (nz + 5); e += nth) {
+        const int c = e % (nz + 5), r = e / (nz + 5);
+        const int k = r % Q, d = r / Q;
+        sH[r * WH + c] = src[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - 3 + c, nx, bc)];
     }
     const double vscale = cb * (use_dt ? sd.dt : 1.0);
-    for (int e = threadIdx.x; e < 2 * Q * (nz + 2 * kHaloV); e += blockDim.x) {
-        int c = e % (nz + 2 * kHaloV), r = e / (nz + 2 * kHaloV);
-        int k = r % Q, d = r / Q;
-        s.V[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - kHaloV + c, nx, bc)];
+    for (int e = tid; e < 2 * Q * (nz + 1); e += nth) {
+        const int c = e % (nz + 1), r = e / (nz + 1);
+        const int k = r % Q, d = r / Q;
+        sV[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - 1 + c, nx, bc)];
     }
-    for (int j = threadIdx.x; j < 2 * sd.M + 1; j += blockDim.x) s.f.Ftap[j] = taps[sd.tap_off + j];
-    for (int j = threadIdx.x; j < 2 * sd.m + 1; j += blockDim.x) s.f.Mtap[j] = taps[sd.tap_off + 2 * sd.M + 1 + j];
-    __syncthreads();
-    // Warp 0 recomputes the node fields while warps 1-7 run phases 1 and 1b,
-    // which need only v and the tables (named barrier 1 joins warps 1-7).
-    const bool node_warp = threadIdx.x < 32;
-    const int tid7 = threadIdx.x - 32, nth7 = blockDim.x - 32;
-    if (node_warp) {
-        node_fields_pass1<double>(sd, it, s.f, s.f.Mtap, NN, nullptr, threadIdx.x, 32);
-        __syncwarp();
-        node_fields_pass2<double>(sd, it, s.f, Z, s.f.Ftap, mom, NN, err, nullptr, threadIdx.x, 32);
-    } else {
-        // the analysis table is replaced by PT[l][j] = sqrt(l) psi_{l-1}(xi_j) (l >= 1),
-        // so that sum_l PT[l][j] cbar_l is the transposed analysis of the force term
-        for (int e = tid7; e < Q * Q; e += nth7) {
-            int l = e / Q, j = e % Q;
-            s.f.P[e] = (l == 0) ? 0.0 : r1[l] * tab[L.P + (l - 1) * Q + j];
-        }
-
-        // phase 1: transposed synthesis cbar_l = sum_k S_kl v_k
-        for (int e = tid7; e < 2 * Q * nz; e += nth7) {
-            int t = e % nz, r = e / nz;
-            int l = r % Q, d = r / Q;
-            const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
-            double acc = 0.0;
-            for (int k = 0; k < Q; ++k) acc = fma(s.f.S[k * Q + l], v[k * WV], acc);
-            s.Cb[((size_t)d * Q + l) * Z + t] = acc;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(nth7) : "memory");
-        // phase 1b: Ha_j = sum_l sqrt(l) psi_{l-1}(xi_j) cbar_l, the transposed analysis
-        // of the force term c_l += F1 sqrt(l) a_{l-1} (times F1 in phase 4); with
-        // a_{l-1} = sum_j psi_{l-1}(xi_j) h_j it also gives F1b = sum_j h_j Ha_j.
-        for (int e = tid7; e < 2 * Q * nz; e += nth7) {
-            int t = e % nz, r = e / nz;
-            int j = r % Q, d = r / Q;
-            const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-            double acc = 0.0;
-            for (int l = 1; l < Q; ++l) acc = fma(s.f.P[l * Q + j], cbar[l * Z], acc);
-            s.Ha[(size_t)r * Z + t] = acc;
-        }
+    for (int e = tid; e < EVFDLB_NFIELDS * nz; e += nth) {
+        const int f = e / nz, t = e - f * nz;
+        sFl[f * Z + t] = fld[f * NN + sd.node_off + it.i0 + t];
     }
     __syncthreads();
 
-    // Warp 0 runs phases 2 and 3a (per node) while warps 1-7 run phase 3b.
-    if (node_warp) {
-
-        // phase 2: per (distribution, node): adjoints of the coefficient
-        // constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!) m_{l-r}), of u and T
-        // through m_l (dm_l/du = sqrt(l) m_{l-1}, dm_l/dT = sqrt(l(l-1)) m_{l-2}/2,
-        // so dc_l/du = sqrt(l) c_{l-1}, dc_l/dT = sqrt(l(l-1)) c_{l-2}/2), of F1
-        // (c_l += F1 sqrt(l) a_{l-1}) and of nu (the -nu h term).
-        for (int e = threadIdx.x; e < 2 * nz; e += 32) {
-            int t = e % nz, d = e / nz;
-            const double* sc = s.f.Sc;
-            double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
-            double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
-            double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-            double c0, c1, c2, c3;
-            if (d == 0) {
-                c0 = nu * n;
-                c1 = K * A * T;
-                c2 = 0.6 * K * D * T;
-                c3 = 0.2 * nu * kq + 0.3 * K * B * T * T;
-            } else {
-                c0 = nu * n * T + 0.4 * K * T * D;
-                c1 = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
-                c2 = 0.6 * K * T * T * D;
-                c3 = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
-            }
-            const double* cbar = s.Cb + (size_t)d * Q * Z + t;
-            double m0 = 1.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, Tm1 = T - 1.0;
-            double cm1 = 0.0, cm2 = 0.0;      // c_{l-1}, c_{l-2}
-            double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, fb = 0;
-            for (int l = 0; l < Q; ++l) {
-                double cl = cbar[l * Z];
-                double w1 = r1[l] * m1, w2 = r2[l] * m2, w3 = r3[l] * m3;
-                b0 = fma(cl, m0, b0);
-                b1 = fma(cl, w1, b1);
-                b2 = fma(cl, w2, b2);
-                b3 = fma(cl, w3, b3);
-                ub = fma(cl * r1[l], cm1, ub);
-                Tb = fma(cl * 0.5 * r2[l], cm2, Tb);
-                double c = c0 * m0 + c1 * w1 + c2 * w2 + c3 * w3;
-                cm2 = cm1;
-                cm1 = c;
-                double mn = fma(u * tab[L.rinv + l], m0, Tm1 * tab[L.rr + l] * m1);
-                m3 = m2;
-                m2 = m1;
+    // Step 1.  Warps 0-2 form the per-node quantities first; then every warp
+    // takes warp-sized groups of the tile's own faces from a shared counter.
+    //  warp 0: Hermite moments m_l of N(u, T) (m_{l+1} = u m_l / sqrt(l+1)
+    //          + (T-1) sqrt(l/(l+1)) m_{l-1});
+    //  warp 1: derivatives of the node maps (nu, kq, K, gradient ratios);
+    //  warp 2: coefficient constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!)
+    //          m_{l-r}, Eqs. (enskog_approx) and (J1)) and the parity parts
+    //          of v at the tile nodes.
+    auto F = [&](int f, int t) { return sFl[f * Z + t]; };
+    if (warp == 0) {
+        for (int t = lane; t < nz; t += 32) {
+            const double u = F(FL_U, t), Tm1 = F(FL_T, t) - 1.0;
+            double m0 = 1.0, m1 = 0.0;
+            sMm[t] = 1.0;
+            for (int l = 0; l + 1 < Q; ++l) {
+                const double mn = fma(u * srinv[l], m0, Tm1 * srr[l] * m1);
                 m1 = m0;
                 m0 = mn;
+                sMm[(l + 1) * Z + t] = mn;
             }
-            double nb = 0.0;
-            const double* h = s.H + (size_t)d * Q * WH + t + kHaloH;
-            const double* v = s.V + (size_t)d * Q * WV + t + kHaloV;
-            const double* ha = s.Ha + (size_t)d * Q * Z + t;
-            for (int k = 0; k < Q; ++k) {
-                nb = fma(-h[k * WH], v[k * WV], nb);
-                fb = fma(h[k * WH], ha[k * Z], fb);
+        }
+    } else if (warp == 1) {
+        const double b = sd.b;
+        const double k1 = (4.0 / 25.0) * (1.0 + 12.0 / M_PI), k2 = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI));
+        for (int t = lane; t < nz; t += 32) {
+            const double n = F(FL_N, t), T = F(FL_T, t), chi = F(FL_CHI, t), nu = F(FL_NU, t);
+            const double q = F(FL_Q, t), Pr = F(FL_PR, t), x = F(FL_XX, t), X = F(FL_X, t);
+            const double bn = b * n;
+            const double ichi = div_nr(1.0, chi), in = div_nr(1.0, n), iT = div_nr(1.0, T);
+            // nu = 1/tau or chi/tau, tau = mu / (n T (1 + 2x/5)), mu = mu0 sqrt(T) g(n, chi),
+            // g = 1/chi + 4/5 b n + k1 b^2 n^2 chi (Eqs. (viscosity), (tau)); both forms give
+            // dnu = -nu dln(tau) (+ nu/chi dchi for chi/tau)
+            const double den = 1.0 + 0.4 * x;
+            const double ig = div_nr(1.0, ichi + 0.8 * bn + k1 * bn * bn * chi), iden = div_nr(1.0, den);
+            double* J = sJ + t;
+            J[J_NNU * Z] = nu * (in - (0.8 * b + 2.0 * k1 * b * bn * chi) * ig + 0.4 * b * chi * iden);
+            J[J_TNU * Z] = 0.5 * nu * iT;
+            double cnu = nu * ((ichi * ichi - k1 * bn * bn) * ig + 0.4 * bn * iden);
+            if (sd.relax != EVFDLB_RELAX_INV_TAU) cnu += nu * ichi;
+            J[J_CNU * Z] = cnu;
+            // kq = (1 - Pr(x)) q, Pr of Eq. (prandtl), x = b n chi
+            const double N1 = 1.0 + 0.6 * x, N2 = 1.0 + 0.8 * x + k1 * x * x, D2 = 1.0 + 1.2 * x + k2 * x * x;
+            const double dPr = Pr * (0.6 * div_nr(1.0, N1) + (0.8 + 2.0 * k1 * x) * div_nr(1.0, N2) - 0.4 * iden -
+                                     (1.2 + 2.0 * k2 * x) * div_nr(1.0, D2));
+            J[J_QKQ * Z] = 1.0 - Pr;
+            J[J_NKQ * Z] = -q * dPr * b * chi;
+            J[J_CKQ * Z] = -q * dPr * bn;
+            // K = -b n^2 chi
+            J[J_NK * Z] = -2.0 * x;
+            J[J_CK * Z] = -bn * n;
+            // A = dX/X, B = dT/T
+            const double iX = div_nr(1.0, X);
+            J[J_IX * Z] = iX;
+            J[J_AIX * Z] = F(FL_A, t) * iX;
+            J[J_IT * Z] = iT;
+            J[J_BIT * Z] = F(FL_B, t) * iT;
+        }
+    } else if (warp == 2) {
+        for (int e = lane; e < 2 * nz; e += 32) {
+            const int t = e % nz, d = e / nz;
+            const double n = F(FL_N, t), T = F(FL_T, t), nu = F(FL_NU, t);
+            const double kq = (1.0 - F(FL_PR, t)) * F(FL_Q, t), K = -F(FL_XX, t) * n;
+            const double A = F(FL_A, t), B = F(FL_B, t), D = F(FL_DU, t);
+            double* c = sCc + d * 4 * Z + t;
+            if (d == 0) {
+                c[0] = nu * n;
+                c[Z] = K * A * T;
+                c[2 * Z] = 0.6 * K * D * T;
+                c[3 * Z] = 0.2 * nu * kq + 0.3 * K * B * T * T;
+            } else {
+                c[0] = nu * n * T + 0.4 * K * T * D;
+                c[Z] = 0.4 * nu * kq + K * T * T * (A + 0.6 * B);
+                c[2 * Z] = 0.6 * K * T * T * D;
+                c[3 * Z] = 0.2 * nu * kq * T + 0.3 * K * T * T * T * B;
             }
-            double* red = s.Red + (size_t)d * 8 * Z + t;
-            red[0] = b0;
-            red[Z] = b1;
-            red[2 * Z] = b2;
-            red[3 * Z] = b3;
-            red[4 * Z] = ub;
-            red[5 * Z] = Tb;
-            red[6 * Z] = fb;
-            red[7 * Z] = nb;
+        }
+        for (int e = lane; e < 2 * NP * nz; e += 32) {
+            const int t = e % nz, r = e / nz;
+            const int k = r % NP, d = r / NP;
+            const double* v = sV + (size_t)d * Q * WV + t + 1;
+            const double a = v[k * WV];
+            const bool pair = (Q - 1 - k != k);
+            const double bm = pair ? v[(Q - 1 - k) * WV] : 0.0;
+            sVE[((d * 2 + 0) * NP + k) * Z + t] = pair ? a + bm : a;
+            sVE[((d * 2 + 1) * NP + k) * Z + t] = pair ? a - bm : 0.0;
+        }
+    }
+    // The tile's own faces: face p (tile-relative, between nodes p-1 and p)
+    // of row r = d Q + k.  For xi > 0 its WENO-5 stencil is nodes p-3 .. p+1
+    // (v0 .. v4), for xi < 0 nodes p+2 .. p-2; its adjoint is
+    // pb = xi/dz (v_p - v_{p-1}).  G5[s][r][p] = pb dPhi/dv_s.  A face whose
+    // stencil leaves the tile also goes to gface (global, by face), where the
+    // neighbouring tiles' adj_moments_kernel collects its terms.
+    {
+        const int nface = 2 * Q * nz, ngroup = (nface + 31) / 32;
+        const double rdz = sd.inv_dx, eps = sd.weno_eps;
+        for (;;) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&s_next, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= ngroup) break;
+            const int e = g * 32 + lane;
+            if (e < nface) {
+                const int p = e % nz, r = e / nz;
+                const int k = r % Q, d = r / Q;
+                const double x = sxi[k];
+                double gg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                const double* h = sH + (size_t)r * WH + p;      // h[c] = node p - 3 + c
+                const double* v = sV + (size_t)r * WV + p;      // v[0] = node p - 1, v[1] = node p
+                if (x > 0.0) {
+                    weno5_grad(h[0], h[1], h[2], h[3], h[4], eps, x * rdz * (v[1] - v[0]), gg);
+                } else if (x < 0.0) {
+                    weno5_grad(h[5], h[4], h[3], h[2], h[1], eps, x * rdz * (v[1] - v[0]), gg);
+                }
+#pragma unroll
+                for (int s = 0; s < 5; ++s) sG5[((size_t)s * 2 * Q + r) * Z + p] = gg[s];
+                const bool edge = (x > 0.0) ? (p < 3 || p + 1 >= nz) : (x < 0.0 && (p < 2 || p + 2 >= nz));
+                if (edge) {
+                    double* gf = gface + d * NF + row0 + (long long)k * nx + p;
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) gf[s * 2 * NF] = gg[s];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // Step 2, per (distribution d, order or velocity l, node t):
+    //  cbar_l = sum_k S_kl v_k on the parity parts (even l: v_k + v_{Q-1-k},
+    //           odd l: v_k - v_{Q-1-k});
+    //  c_l    = c0 m_l + c1 sqrt(l) m_{l-1} + c2 sqrt(l(l-1)) m_{l-2} + c3 sqrt(l(l-1)(l-2)) m_{l-3};
+    //  Hw_l   = the tile's own faces' terms at node t of row (d, l).
+    for (int e = tid; e < 2 * Q * nz; e += nth) {
+        const int t = e % nz, r = e / nz;
+        const int l = r % Q, d = r / Q;
+        const double* ve = sVE + ((d * 2 + (l & 1)) * NP) * Z + t;
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 1 < NP; k += 2) {
+            a0 = fma(sS[k * Q + l], ve[k * Z], a0);
+            a1 = fma(sS[(k + 1) * Q + l], ve[(k + 1) * Z], a1);
+        }
+        if (k < NP) a0 = fma(sS[k * Q + l], ve[k * Z], a0);
+        sCb[(size_t)r * Z + t] = a0 + a1;
+        const double* c = sCc + d * 4 * Z + t;
+        const double* m = sMm + t;
+        double cl = c[0] * m[l * Z];
+        if (l >= 1) cl = fma(c[Z] * sr1[l], m[(l - 1) * Z], cl);
+        if (l >= 2) cl = fma(c[2 * Z] * sr2[l], m[(l - 2) * Z], cl);
+        if (l >= 3) cl = fma(c[3 * Z] * sr3[l], m[(l - 3) * Z], cl);
+        sCl[(size_t)r * Z + t] = cl;
+        const double x = sxi[l];
+        double hw = 0.0;
+        if (x != 0.0) {
+            // xi > 0: faces p = t-1 .. t+3, node t is v_{t-p+3}; xi < 0: p = t-2 .. t+2, v_{p+2-t}
+            const int plo = (x > 0.0) ? t - 1 : t - 2;
+            for (int p = max(plo, 0); p <= min(plo + 4, nz - 1); ++p) {
+                const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
+                hw += sG5[((size_t)s * 2 * Q + r) * Z + p];
+            }
+        }
+        sHw[(size_t)r * Z + t] = hw;
+    }
+    __syncthreads();
+
+    // Step 3.  (a) Per (d, node t, chunk of orders): the sums over l of
+    //   b_r = sum cbar_l sqrt(l!/(l-r)!) m_{l-r}  (r = 0..3: adjoints of c0..c3),
+    //   ub  = sum cbar_l sqrt(l) c_{l-1}          (dc_l/du = sqrt(l) c_{l-1}),
+    //   Tb  = sum cbar_l sqrt(l(l-1)) c_{l-2} / 2 (dc_l/dT),
+    //   nub = -sum_k h_k v_k                      (the -nu h term),
+    // kSumChunks lanes per (d, t), joined by shuffles.  (b) Per (d, j < NP, t):
+    // Ha_j = sum_l sqrt(l) psi_{l-1}(xi_j) cbar_l, the transposed analysis of
+    // the force term c_l += F1 sqrt(l) a_{l-1}, on the parity parts (odd l
+    // symmetric, even l antisymmetric about j <-> Q-1-j).
+    {
+        const int nsum = kSumChunks * 2 * nz, nsum_p = (nsum + 31) & ~31;
+        const int LQ = (Q + kSumChunks - 1) / kSumChunks;
+        for (int base = warp * 32; base < nsum_p + 2 * NP * nz; base += nth) {
+            if (base < nsum_p) {
+                const int e = base + lane;
+                const bool act = e < nsum;
+                const int ch = e % kSumChunks, dt = e / kSumChunks;
+                const int t = act ? dt % nz : 0, d = act ? dt / nz : 0;
+                const double* cbr = sCb + (size_t)d * Q * Z + t;
+                const double* clr = sCl + (size_t)d * Q * Z + t;
+                const double* m = sMm + t;
+                const double* h = sH + (size_t)d * Q * WH + t + 3;
+                const double* v = sV + (size_t)d * Q * WV + t + 1;
+                double b0 = 0, b1 = 0, b2 = 0, b3 = 0, ub = 0, Tb = 0, nb = 0;
+                const int l0 = act ? ch * LQ : Q, l1 = min(Q, l0 + LQ);
+                for (int l = l0; l < l1; ++l) {
+                    const double cbl = cbr[l * Z];
+                    b0 = fma(cbl, m[l * Z], b0);
+                    nb = fma(-h[l * WH], v[l * WV], nb);
+                    if (l >= 1) {
+                        const double p1 = cbl * sr1[l];
+                        b1 = fma(p1, m[(l - 1) * Z], b1);
+                        ub = fma(p1, clr[(l - 1) * Z], ub);
+                    }
+                    if (l >= 2) {
+                        const double p2 = cbl * sr2[l];
+                        b2 = fma(p2, m[(l - 2) * Z], b2);
+                        Tb = fma(p2, clr[(l - 2) * Z], Tb);
+                    }
+                    if (l >= 3) b3 = fma(cbl * sr3[l], m[(l - 3) * Z], b3);
+                }
+                double acc[7] = {b0, b1, b2, b3, ub, Tb, nb};
+#pragma unroll
+                for (int s = 0; s < 7; ++s) {
+                    acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], 1);
+                    acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], 2);
+                }
+                if (act && ch == 0) {
+                    double* red = sRed + (size_t)d * 8 * Z + t;
+                    red[0] = acc[0];
+                    red[Z] = acc[1];
+                    red[2 * Z] = acc[2];
+                    red[3 * Z] = acc[3];
+                    red[4 * Z] = acc[4];
+                    red[5 * Z] = 0.5 * acc[5];
+                    red[7 * Z] = acc[6];
+                }
+            } else {
+                const int e = base - nsum_p + lane;
+                if (e < 2 * NP * nz) {
+                    const int t = e % nz, r = e / nz;
+                    const int j = r % NP, d = r / NP;
+                    const double* cbr = sCb + (size_t)d * Q * Z + t;
+                    double eo = 0.0, ee = 0.0;      // odd l (symmetric), even l (antisymmetric)
+                    int l = 1;
+                    for (; l + 1 < Q; l += 2) {
+                        eo = fma(sPT[l * NP + j], cbr[l * Z], eo);
+                        ee = fma(sPT[(l + 1) * NP + j], cbr[(l + 1) * Z], ee);
+                    }
+                    if (l < Q) eo = fma(sPT[l * NP + j], cbr[l * Z], eo);
+                    double* ha = sHa + (size_t)d * Q * Z + t;
+                    ha[j * Z] = eo + ee;
+                    if (Q - 1 - j != j) ha[(Q - 1 - j) * Z] = eo - ee;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // Step 4.  Warp 0: the force adjoint sum F1b_d = sum_k h_k Ha_k, then per
+    // node the chain through the coefficient constants, the node maps and the
+    // gradient ratios, written as the node adjoints.  Warps 1-7: the
+    // distribution-local adjoint and the RK-stage combination.
+    if (warp == 0) {
+        for (int e = lane; e < 2 * nz; e += 32) {
+            const int t = e % nz, d = e / nz;
+            const double* h = sH + (size_t)d * Q * WH + t + 3;
+            const double* ha = sHa + (size_t)d * Q * Z + t;
+            double f0 = 0.0, f1 = 0.0;
+            int k = 0;
+            for (; k + 1 < Q; k += 2) {
+                f0 = fma(h[k * WH], ha[k * Z], f0);
+                f1 = fma(h[(k + 1) * WH], ha[(k + 1) * Z], f1);
+            }
+            if (k < Q) f0 = fma(h[k * WH], ha[k * Z], f0);
+            sRed[(size_t)d * 8 * Z + 6 * Z + t] = f0 + f1;
         }
         __syncwarp();
-
-        // phase 3a: per node, the chain through the coefficient constants, the
-        // transport coefficients of Eqs. (viscosity), (tau), (prandtl), and the
-        // gradients A = dX/X, B = dT/T, D = du.
-        for (int t = threadIdx.x; t < nz; t += 32) {
-            const double* sc = s.f.Sc;
-            double n = sc[SC_N * Z + t], u = sc[SC_U * Z + t], T = sc[SC_T * Z + t];
-            double nu = sc[SC_NU * Z + t], kq = sc[SC_KQ * Z + t], K = sc[SC_K * Z + t];
-            double A = sc[SC_A * Z + t], B = sc[SC_B * Z + t], D = sc[SC_D * Z + t];
-            double F1 = sc[SC_FORCE * Z + t];
-            const double* rF = s.Red + t;
-            const double* rG = s.Red + 8 * Z + t;
-            double cF0 = rF[0], cF1 = rF[Z], cF2 = rF[2 * Z], cF3 = rF[3 * Z];
-            double cG0 = rG[0], cG1 = rG[Z], cG2 = rG[2 * Z], cG3 = rG[3 * Z];
+        for (int t = lane; t < nz; t += 32) {
+            const double n = F(FL_N, t), T = F(FL_T, t), nu = F(FL_NU, t);
+            const double kq = (1.0 - F(FL_PR, t)) * F(FL_Q, t), K = -F(FL_XX, t) * n;
+            const double A = F(FL_A, t), B = F(FL_B, t), D = F(FL_DU, t), F1 = F(FL_F1, t);
+            const double* rF = sRed + t;
+            const double* rG = sRed + 8 * Z + t;
+            const double cF0 = rF[0], cF1 = rF[Z], cF2 = rF[2 * Z], cF3 = rF[3 * Z];
+            const double cG0 = rG[0], cG1 = rG[Z], cG2 = rG[2 * Z], cG3 = rG[3 * Z];
             double ub = rF[4 * Z] + rG[4 * Z];
             double Tb = rF[5 * Z] + rG[5 * Z];
-            double F1b = rF[6 * Z] + rG[6 * Z];
+            const double F1b = rF[6 * Z] + rG[6 * Z];
             double nub = rF[7 * Z] + rG[7 * Z];
-            double nb = 0, Kb = 0, kqb = 0, Ab = 0, Bb = 0, Db = 0, chib = 0, xb = 0, qb = 0;
+            double nb = 0, Kb = 0, kqb = 0, Ab = 0, Bb = 0, Db = 0;
             // F: c0 = nu n, c1 = K A T, c2 = 3/5 K D T, c3 = nu kq/5 + 3/10 K B T^2
             nub += cF0 * n;
             nb += cF0 * nu;
@@ -325,136 +510,39 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
             Tb += cG3 * (0.2 * nu * kq + 0.9 * K * T * T * B);
             Kb += 0.3 * cG3 * T * T * T * B;
             Bb += 0.3 * cG3 * K * T * T * T;
-            // transport (recomputed as in node_fields)
-            double chi = s.f.Chi[t + 2], X = s.f.X[t + 2];
-            double bn = sd.b * n, x = bn * chi;
-            const double k1 = (4.0 / 25.0) * (1.0 + 12.0 / M_PI), k2 = (9.0 / 25.0) * (1.0 + 32.0 / (9.0 * M_PI));
-            double sqT = sqrt(T);
-            double gmu = 1.0 / chi + 0.8 * bn + k1 * bn * bn * chi;
-            double mu = sd.mu0_coef * sqT * gmu;
-            double den = 1.0 + 0.4 * x;
-            double tau = mu / (n * T * den);
-            double N1 = 1.0 + 0.6 * x, N2 = 1.0 + 0.8 * x + k1 * x * x, D1 = den, D2 = 1.0 + 1.2 * x + k2 * x * x;
-            double Pr = (2.0 / 3.0) * N1 * N2 / (D1 * D2);
-            // q from the raw sums (as node_fields forms it)
-            long long o = sd.node_off + it.i0 + t;
-            double S0 = mom[MOM_S0 * NN + o], S1 = mom[MOM_S1 * NN + o], S2 = mom[MOM_S2 * NN + o];
-            double S3 = mom[MOM_S3 * NN + o], G0 = mom[MOM_G0 * NN + o], G1 = mom[MOM_G1 * NN + o];
-            double q = 0.5 * (S3 - 3.0 * u * S2 + 3.0 * u * u * S1 - u * u * u * S0) + G1 - u * G0;
-            // K = -b n^2 chi
-            nb += -2.0 * x * Kb;
-            chib += -bn * n * Kb;
-            // kq = (1 - Pr) q
-            qb += kqb * (1.0 - Pr);
-            double Prb = -kqb * q;
-            // nu = 1/tau or chi/tau
-            double taub;
-            if (sd.relax == EVFDLB_RELAX_INV_TAU) {
-                taub = -nub / (tau * tau);
-            } else {
-                chib += nub / tau;
-                taub = -nub * chi / (tau * tau);
-            }
-            // tau = mu / (n T (1 + 2x/5))
-            double mub = taub / (n * T * den);
-            nb += -taub * tau / n;
-            Tb += -taub * tau / T;
-            xb += -taub * tau * 0.4 / den;
-            // Pr(x)
-            xb += Prb * Pr * (0.6 / N1 + (0.8 + 2.0 * k1 * x) / N2 - 0.4 / D1 - (1.2 + 2.0 * k2 * x) / D2);
-            // mu = mu0 sqrt(T) (1/chi + 4/5 b n + k1 b^2 n^2 chi)
-            Tb += mub * mu / (2.0 * T);
-            nb += mub * sd.mu0_coef * sqT * (0.8 * sd.b + 2.0 * k1 * sd.b * bn * chi);
-            chib += mub * sd.mu0_coef * sqT * (-1.0 / (chi * chi) + k1 * bn * bn);
-            // x = b n chi
-            nb += xb * sd.b * chi;
-            chib += xb * bn;
-            // gradients
-            double dXb = Ab / X;
-            double Xb = -Ab * A / X;
-            double dTb = Bb / T;
-            Tb += -Bb * B / T;
-            double* na = nadj + sd.node_off + it.i0 + t;
+            // the node maps nu(n, T, chi), kq(q, n, chi), K(n, chi) and the ratios A, B
+            const double* J = sJ + t;
+            nb += nub * J[J_NNU * Z] + kqb * J[J_NKQ * Z] + Kb * J[J_NK * Z];
+            Tb += nub * J[J_TNU * Z] - Bb * J[J_BIT * Z];
+            const double chib = nub * J[J_CNU * Z] + kqb * J[J_CKQ * Z] + Kb * J[J_CK * Z];
+            const long long o = sd.node_off + it.i0 + t;
+            double* na = nadj + o;
             na[AD_N * NN] = nb;
             na[AD_U * NN] = ub;
             na[AD_T * NN] = Tb;
-            na[AD_Q * NN] = qb;
+            na[AD_Q * NN] = kqb * J[J_QKQ * Z];
             na[AD_CHI * NN] = chib;
-            na[AD_X * NN] = Xb;
-            na[AD_DX * NN] = dXb;
-            na[AD_DT * NN] = dTb;
+            na[AD_X * NN] = -Ab * J[J_AIX * Z];
+            na[AD_DX * NN] = Ab * J[J_IX * Z];
+            na[AD_DT * NN] = Bb * J[J_IT * Z];
             na[AD_DU * NN] = Db;
             na[AD_F1 * NN] = F1b;
             phis[o] += F1b * F1;
         }
-
-        // phase 3b: transposed WENO-5 faces.  A velocity row is cut into chunks of
-        // up to 28 tile nodes; a chunk's cn + 4 faces occupy a segment of cn + 4
-        // consecutive lanes (one face per lane), and a warp carries as many
-        // segments (rows) as fit in 32 lanes.  Each lane forms the five
-        // derivatives of its face value times the face adjoint, ordered so that
-        // the node at segment lane L' collects g'[s] from segment lane L' + s,
-        // s = 0..4 (the five faces that read it).
     } else {
-        const int warp = threadIdx.x / 32 - 1, lane = threadIdx.x % 32, nwarps = blockDim.x / 32 - 1;
-        const double rdz = sd.inv_dx, eps = sd.weno_eps;
-        const int nchunk = (nz + 27) / 28;
-        const int cmax = min(28, nz), seg = cmax + 4;
-        const int per_warp = 32 / seg;                 // segments per warp
-        const int nseg = 2 * Q * nchunk;               // (row, chunk) pairs
-        const int sub = lane / seg, sl = lane % seg;
-        for (int base = warp * per_warp; base < nseg; base += nwarps * per_warp) {
-            const int sid = base + sub;
-            const bool active = (sub < per_warp) && (sid < nseg);
-            double g[5] = {0, 0, 0, 0, 0};
-            int row = 0, c0 = 0, cn = 0;
-            double x = 0.0;
-            if (active) {
-                row = sid / nchunk;
-                c0 = (sid % nchunk) * 28;
-                cn = min(28, nz - c0);
-                x = xi[row % Q];
-                const double* h = s.H + (size_t)row * WH + kHaloH;   // h[i], i tile-relative
-                const double* v = s.V + (size_t)row * WV + kHaloV;
-                if (x != 0.0 && sl < cn + 4) {
-                    double gg[5];
-                    if (x > 0.0) {
-                        int f = c0 - 1 + sl;                     // face between nodes f-1 and f
-                        double pb = x * rdz * (v[f] - v[f - 1]);
-                        weno5_grad(h[f - 3], h[f - 2], h[f - 1], h[f], h[f + 1], eps, pb, gg);
-                        g[0] = gg[4]; g[1] = gg[3]; g[2] = gg[2]; g[3] = gg[1]; g[4] = gg[0];
-                    } else {
-                        int f = c0 - 2 + sl;
-                        double pb = x * rdz * (v[f] - v[f - 1]);
-                        weno5_grad(h[f + 2], h[f + 1], h[f], h[f - 1], h[f - 2], eps, pb, gg);
-                        g[0] = gg[0]; g[1] = gg[1]; g[2] = gg[2]; g[3] = gg[3]; g[4] = gg[4];
-                    }
-                }
-            }
-            const int src = min(lane, 27);               // keeps src + 4 <= 31
-            double acc = __shfl_sync(0xffffffffu, g[0], src);
-            acc += __shfl_sync(0xffffffffu, g[1], src + 1);
-            acc += __shfl_sync(0xffffffffu, g[2], src + 2);
-            acc += __shfl_sync(0xffffffffu, g[3], src + 3);
-            acc += __shfl_sync(0xffffffffu, g[4], src + 4);
-            if (active && sl < cn) s.Hw[(size_t)row * Z + c0 + sl] = (x != 0.0) ? acc : 0.0;
+        for (int e = tid - 32; e < 2 * Q * nz; e += nth - 32) {
+            const int t = e % nz, r = e / nz;
+            const int j = r % Q, d = r / Q;
+            const double F1 = F(FL_F1, t), nu = F(FL_NU, t);
+            const double vv = sV[(size_t)r * WV + t + 1];
+            const double val = fma(F1, sHa[(size_t)r * Z + t], fma(-nu, vv, sHw[(size_t)r * Z + t]));
+            const long long g = d * NF + row0 + (long long)j * nx + t;
+            const double yb = ybar[g];
+            double o = fma(ca, yb, val);
+            if (cc != 0.0) o = fma(cc, acc_in[g], o);
+            if (acc_out) acc_out[g] = (cacc != 0.0 ? cacc * acc_in[g] : 0.0) + cy * yb;
+            out[g] = o;
         }
-    }
-    __syncthreads();
-
-    // phase 4: the distribution-local adjoint and the RK-stage combination
-    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int j = r % Q, d = r / Q;
-        double F1 = s.f.Sc[SC_FORCE * Z + t], nu = s.f.Sc[SC_NU * Z + t];
-        double vv = s.V[(size_t)r * WV + t + kHaloV];
-        double val = fma(F1, s.Ha[(size_t)r * Z + t], fma(-nu, vv, s.Hw[(size_t)r * Z + t]));
-        long long g = d * NF + sd.f_off + (long long)j * nx + it.i0 + t;
-        double yb = ybar[g];
-        double o = fma(ca, yb, val);
-        if (cc != 0.0) o = fma(cc, acc_in[g], o);
-        if (acc_out) acc_out[g] = (cacc != 0.0 ? cacc * acc_in[g] : 0.0) + cy * yb;
-        out[g] = o;
     }
 }
 
@@ -463,105 +551,124 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
 // the tile and its Fischer-Methfessel halo, the transposed Fischer-Methfessel
 // average and Eq. (F1) convolution (correlations with the same taps), the
 // chain (n, u, T, q) <- raw sums, and
-// out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b.
-__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m, int M) {
-    return 5 * (size_t)(Z + 2 * m) + (size_t)kNumMoments * Z + (size_t)(Z + 4 * m) + (size_t)(Z + 2 * M) +
-           (size_t)(Z + 2 * m + 4) + 2 * (size_t)(Z + 4) + (size_t)(2 * M + 1) + (size_t)(2 * m + 1);
-}
+// out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b,
+// plus the terms of the faces outside the tile whose stencils reach it.
+struct AdjMomLay {
+    size_t Xb, Nb, n, T, chi, F1, DX, DU, DT, sb, part, ftap, mtap, total;
+    __host__ __device__ AdjMomLay(int Z, int m, int M) {
+        const size_t HW = Z + 2 * m;
+        size_t o = 0;
+        Xb = o;   o += HW;                      // X adjoint on [i0 - m, i0 + nz + m)
+        Nb = o;   o += HW;                      // nbar adjoint (source of the FM correlation)
+        n = o;    o += HW;                      // n, T, chi on the same nodes
+        T = o;    o += HW;
+        chi = o;  o += HW;
+        F1 = o;   o += (size_t)Z + 2 * M;       // force adjoint on [i0 - M, i0 + nz + M)
+        DX = o;   o += (size_t)Z + 2 * m + 4;   // X-gradient adjoint on [i0 - m - 2, i0 + nz + m + 2)
+        DU = o;   o += (size_t)Z + 4;           // u- and T-gradient adjoints on [i0 - 2, i0 + nz + 2)
+        DT = o;   o += (size_t)Z + 4;
+        sb = o;   o += (size_t)kNumMoments * Z; // raw-sum adjoints of the tile
+        part = o; o += (size_t)kTapChunks * Z;  // partial tap sums
+        ftap = o; o += 2 * (size_t)M + 1;       // Eq. (F1) taps
+        mtap = o; o += 2 * (size_t)m + 1;       // Fischer-Methfessel taps
+        total = o;
+    }
+};
+
+__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m, int M) { return AdjMomLay(Z, m, M).total; }
 
 __global__ void __launch_bounds__(kThreads)
 adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
                    const double* __restrict__ tables, const double* __restrict__ taps,
-                   const double* __restrict__ mom, const double* __restrict__ nadj, double* out, long long NF,
-                   long long NN, int Z) {
-    extern __shared__ double sm[];
+                   const double* __restrict__ mom, const double* __restrict__ fld, const double* __restrict__ nadj,
+                   const double* __restrict__ gface, double* out, long long NF, long long NN, int Z) {
+    extern __shared__ __align__(16) double sm[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int nx = sd.nx, bc = sd.bc, M = sd.M, m = sd.m, Q = sd.Q, nz = it.nz;
-    const int HW = Z + 2 * m;
-    double* sXb = sm;              // X adjoint on [i0 - m, i0 + nz + m)
-    double* sNb = sXb + HW;        // nbar adjoint (source of the FM correlation)
-    double* sn = sNb + HW;         // n, T, chi on the same nodes
-    double* sT = sn + HW;
-    double* schi = sT + HW;
-    double* sb = schi + HW;        // [kNumMoments][Z] raw-sum adjoints of the tile
-    // inputs read by the tap loops, staged once (all threads, coalesced):
-    double* sS0 = sb + kNumMoments * Z;    // S0 on [i0 - 2m, i0 + nz + 2m)
-    double* sF1 = sS0 + (Z + 4 * m);       // force adjoint on [i0 - M, i0 + nz + M)
-    double* sDX = sF1 + (Z + 2 * M);       // X-gradient adjoint on [i0 - m - 2, i0 + nz + m + 2)
-    double* sDU = sDX + (Z + 2 * m + 4);   // u- and T-gradient adjoints on [i0 - 2, i0 + nz + 2)
-    double* sDT = sDU + (Z + 4);
-    double* ftap = sDT + (Z + 4);          // Eq. (F1) taps [2M+1] and FM taps [2m+1]
-    double* mtap = ftap + (2 * M + 1);
+    const AdjMomLay Ly(Z, m, M);
+    double *sXb = sm + Ly.Xb, *sNb = sm + Ly.Nb, *sn = sm + Ly.n, *sT = sm + Ly.T, *schi = sm + Ly.chi;
+    double *sF1 = sm + Ly.F1, *sDX = sm + Ly.DX, *sDU = sm + Ly.DU, *sDT = sm + Ly.DT, *sb = sm + Ly.sb;
+    double *spart = sm + Ly.part, *ftap = sm + Ly.ftap, *mtap = sm + Ly.mtap;
+    const int tid = threadIdx.x, nth = blockDim.x;
     const double inv12 = sd.inv_dx / 12.0;
-    const double* S0 = mom + MOM_S0 * NN + sd.node_off;
-    const double* S1 = mom + MOM_S1 * NN + sd.node_off;
-    const double* S2 = mom + MOM_S2 * NN + sd.node_off;
-    const double* G0 = mom + MOM_G0 * NN + sd.node_off;
-    const double* gF1 = nadj + AD_F1 * NN + sd.node_off;
-    const double* gDX = nadj + AD_DX * NN + sd.node_off;
-    const double* gDU = nadj + AD_DU * NN + sd.node_off;
-    const double* gDT = nadj + AD_DT * NN + sd.node_off;
-    for (int c = threadIdx.x; c < nz + 4 * m; c += blockDim.x) sS0[c] = S0[gidx(it.i0 - 2 * m + c, nx, bc)];
-    for (int c = threadIdx.x; c < nz + 2 * M; c += blockDim.x) sF1[c] = gF1[gidx(it.i0 - M + c, nx, bc)];
-    for (int c = threadIdx.x; c < nz + 2 * m + 4; c += blockDim.x) sDX[c] = gDX[gidx(it.i0 - m - 2 + c, nx, bc)];
-    for (int c = threadIdx.x; c < nz + 4; c += blockDim.x) {
+    const long long no = sd.node_off;
+    const double* gF1 = nadj + AD_F1 * NN + no;
+    const double* gDX = nadj + AD_DX * NN + no;
+    const double* gDU = nadj + AD_DU * NN + no;
+    const double* gDT = nadj + AD_DT * NN + no;
+    for (int j = tid; j < 2 * M + 1; j += nth) ftap[j] = taps[sd.tap_off + j];
+    for (int j = tid; j < 2 * m + 1; j += nth) mtap[j] = taps[sd.tap_off + 2 * M + 1 + j];
+    for (int c = tid; c < nz + 2 * M; c += nth) sF1[c] = gF1[gidx(it.i0 - M + c, nx, bc)];
+    for (int c = tid; c < nz + 2 * m + 4; c += nth) sDX[c] = gDX[gidx(it.i0 - m - 2 + c, nx, bc)];
+    for (int c = tid; c < nz + 4; c += nth) {
         const int i = gidx(it.i0 - 2 + c, nx, bc);
         sDU[c] = gDU[i];
         sDT[c] = gDT[i];
     }
-    for (int j = threadIdx.x; j < 2 * M + 1; j += blockDim.x) ftap[j] = taps[sd.tap_off + j];
-    for (int j = threadIdx.x; j < 2 * m + 1; j += blockDim.x) mtap[j] = taps[sd.tap_off + 2 * M + 1 + j];
     __syncthreads();
     // transposed fourth-order difference at staged position p (value at p)
     auto d4t = [&](const double* g, int p) { return (g[p + 2] - 8.0 * g[p + 1] + 8.0 * g[p - 1] - g[p - 2]) * inv12; };
-    for (int c = threadIdx.x; c < nz + 2 * m; c += blockDim.x) {
-        const int i = gidx(it.i0 - m + c, nx, bc);
-        double n = S0[i], u = S1[i] / n;
-        double T = (2.0 / 3.0) * ((0.5 * S2[i] + G0[i]) / n - 0.5 * u * u);
-        double nbF = 0.0;
-        const double* s0c = sS0 + c + m;               // S0 at node i0 - m + c
-        for (int j = -m; j <= m; ++j) nbF = fma(mtap[j + m], s0c[j], nbF);
-        double eta = sd.eta_coef * nbF, om = 1.0 - eta;
-        double chi = (2.0 - eta) / (2.0 * om * om * om);
-        long long o = sd.node_off + i;
-        double Xb = nadj[AD_X * NN + o] + d4t(sDX, c + 2);
-        double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
-        double dchi = (5.0 - 2.0 * eta) / (2.0 * om * om * om * om);
+    // the chain to chi on the tile and its Fischer-Methfessel halo
+    for (int c = tid; c < nz + 2 * m; c += nth) {
+        const long long o = no + gidx(it.i0 - m + c, nx, bc);
+        const double n = fld[FL_N * NN + o], T = fld[FL_T * NN + o], chi = fld[FL_CHI * NN + o];
+        const double eta = sd.eta_coef * fld[FL_NBAR * NN + o], om = 1.0 - eta, om2 = om * om;
+        const double Xb = nadj[AD_X * NN + o] + d4t(sDX, c + 2);
+        const double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
+        // dchi/deta = (5 - 2 eta) / (2 (1 - eta)^4)
         sXb[c] = Xb;
-        sNb[c] = chib * dchi * sd.eta_coef;
+        sNb[c] = chib * div_nr(5.0 - 2.0 * eta, 2.0 * om2 * om2) * sd.eta_coef;
         sn[c] = n;
         sT[c] = T;
         schi[c] = chi;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) {
-        const int i = it.i0 + t, c = t + m;
-        long long o = sd.node_off + i;
-        double n = sn[c], T = sT[c], chi = schi[c], Xb = sXb[c];
+    // the two correlations, sum_j mtap_j Nb_{i-j} + sum_j ftap_j F1b_{i-j},
+    // as one list of 2m+1 + 2M+1 terms cut into kTapChunks chunks per node
+    {
+        const int LT = 2 * m + 1 + 2 * M + 1, LC = (LT + kTapChunks - 1) / kTapChunks;
+        for (int e = tid; e < kTapChunks * nz; e += nth) {
+            const int ch = e % kTapChunks, t = e / kTapChunks;
+            double a = 0.0;
+            for (int j = ch * LC; j < min(LT, (ch + 1) * LC); ++j) {
+                if (j < 2 * m + 1) a = fma(mtap[j], sNb[t + 2 * m - j], a);
+                else {
+                    const int jj = j - (2 * m + 1);
+                    a = fma(ftap[jj], sF1[t + 2 * M - jj], a);
+                }
+            }
+            spart[ch * Z + t] = a;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < nz; t += nth) {
+        const int c = t + m;
+        const long long o = no + it.i0 + t;
+        const double n = sn[c], T = sT[c], chi = schi[c], Xb = sXb[c];
         double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
-        for (int j = -m; j <= m; ++j) nb = fma(mtap[j + m], sNb[c - j], nb);
-        const double* f1c = sF1 + t + M;               // force adjoint at node i
-        for (int j = -M; j <= M; ++j) nb = fma(ftap[j + M], f1c[-j], nb);
+        for (int ch = 0; ch < kTapChunks; ++ch) nb += spart[ch * Z + t];
         double ub = nadj[AD_U * NN + o] + d4t(sDU, t + 2);
         double Tb = nadj[AD_T * NN + o] + d4t(sDT, t + 2) + Xb * n * n * chi;
-        double qb = nadj[AD_Q * NN + o];
-        double S0v = S0[i], S1v = S1[i], S2v = S2[i], G0v = G0[i];
-        double u = S1v / n;
-        double E = (0.5 * S2v + G0v) / n;
+        const double qb = nadj[AD_Q * NN + o];
+        const double S0v = mom[MOM_S0 * NN + o], S1v = mom[MOM_S1 * NN + o];
+        const double S2v = mom[MOM_S2 * NN + o], G0v = mom[MOM_G0 * NN + o];
+        const double in = div_nr(1.0, n);
+        const double u = fld[FL_U * NN + o];
+        const double E = (0.5 * S2v + G0v) * in;
         // q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
         double S3b = 0.5 * qb, S2b = -1.5 * u * qb, S1b = 1.5 * u * u * qb, S0b = -0.5 * u * u * u * qb;
         double G1b = qb, G0b = -u * qb;
         ub += qb * (-1.5 * S2v + 3.0 * u * S1v - 1.5 * u * u * S0v - G0v);
         // T = (2/3)(E - u^2/2), E = (S2/2 + G0)/n
-        double Eb = (2.0 / 3.0) * Tb;
+        const double Eb = (2.0 / 3.0) * Tb;
         ub += -(2.0 / 3.0) * u * Tb;
-        S2b += Eb / (2.0 * n);
-        G0b += Eb / n;
-        nb += -Eb * E / n;
+        S2b += 0.5 * Eb * in;
+        G0b += Eb * in;
+        nb += -Eb * E * in;
         // u = S1/n
-        S1b += ub / n;
-        nb += -ub * u / n;
+        S1b += ub * in;
+        nb += -ub * u * in;
         S0b += nb;
         sb[MOM_S0 * Z + t] = S0b;
         sb[MOM_S1 * Z + t] = S1b;
@@ -573,12 +680,25 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     __syncthreads();
     TableLayout L(Q);
     const double* xi = tables + sd.tab_off + L.xi;
-    for (int e = threadIdx.x; e < 2 * Q * nz; e += blockDim.x) {
-        int t = e % nz, r = e / nz;
-        int k = r % Q, d = r / Q;
-        double x = xi[k];
+    for (int e = tid; e < 2 * Q * nz; e += nth) {
+        const int t = e % nz, r = e / nz;
+        const int k = r % Q, d = r / Q;
+        const double x = xi[k];
         double add = (d == 0) ? sb[MOM_S0 * Z + t] + x * (sb[MOM_S1 * Z + t] + x * (sb[MOM_S2 * Z + t] + x * sb[MOM_S3 * Z + t]))
                               : sb[MOM_G0 * Z + t] + x * sb[MOM_G1 * Z + t];
+        // faces outside the tile whose stencils hold node t (see adj_local_kernel):
+        // xi > 0: faces p = t-1 .. t+3, node t is v_{t-p+3}; xi < 0: p = t-2 .. t+2, v_{p+2-t}
+        if (x != 0.0) {
+            const int plo = (x > 0.0) ? t - 1 : t - 2;
+            if (plo < 0 || plo + 4 >= nz) {
+                const double* gf = gface + d * NF + sd.f_off + (long long)k * nx;
+                for (int p = plo; p <= plo + 4; ++p) {
+                    if (p >= 0 && p < nz) continue;
+                    const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
+                    add += gf[s * 2 * NF + gidx(it.i0 + p, nx, bc)];
+                }
+            }
+        }
         out[d * NF + sd.f_off + (long long)k * nx + it.i0 + t] += add;
     }
 }
@@ -646,7 +766,9 @@ adj_phi_kernel(const SlabDesc* __restrict__ slabs, const double* __restrict__ ph
 // ---------------------------------------------------------------------------
 // Host-side launch helpers.
 // ---------------------------------------------------------------------------
-size_t adj_smem_bytes(int Q, int Z, int M) { return adj_smem_doubles(Q, Z, M) * sizeof(double); }
+int adj_tile_max() { return kZAdj; }
+
+size_t adj_smem_bytes(int Q, int Z) { return adj_smem_doubles(Q, Z) * sizeof(double); }
 
 size_t adj_moments_smem_bytes(int Z, int m, int M) { return adj_moments_smem_doubles(Z, m, M) * sizeof(double); }
 
@@ -656,16 +778,19 @@ cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes) {
     return cudaFuncSetAttribute(adj_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2_bytes);
 }
 
-// One stage of the reverse sweep (see the file comment); nadj [10][NN] is a
-// work array, phis [NN] accumulates F1b * F1.
+// One stage of the reverse sweep (see the file comment) over the work items
+// of the sweep's node tile Z <= kZAdj.  fld: node fields of src
+// [EVFDLB_NFIELDS][NN]; nadj [10][NN] and gface [5][2 NF] are work arrays;
+// phis [NN] accumulates F1b * F1.
 void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
                       const WorkItem* items, const double* tables, const double* taps, const double* src,
-                      const double* mom, const double* ybar, const double* acc_in, double* acc_out, double* out,
-                      double* nadj, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
-                      double cc, double cacc, double cy, int Z, unsigned* err) {
-    adj_local_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, taps, src, mom, ybar, acc_in, acc_out,
-                                                     out, nadj, phis, NF, NN, ca, cb, use_dt, cc, cacc, cy, Z, err);
-    adj_moments_kernel<<<nitems, kThreads, smem2, st>>>(slabs, items, tables, taps, mom, nadj, out, NF, NN, Z);
+                      const double* fld, const double* mom, const double* ybar, const double* acc_in, double* acc_out,
+                      double* out, double* nadj, double* phis, double* gface, long long NF, long long NN, double ca,
+                      double cb, int use_dt, double cc, double cacc, double cy, int Z) {
+    adj_local_kernel<<<nitems, kThreads, smem, st>>>(slabs, items, tables, src, fld, ybar, acc_in, acc_out, out, nadj,
+                                                     phis, gface, NF, NN, ca, cb, use_dt, cc, cacc, cy, Z);
+    adj_moments_kernel<<<nitems, kThreads, smem2, st>>>(slabs, items, tables, taps, mom, fld, nadj, gface, out, NF,
+                                                        NN, Z);
 }
 
 // Cotangent of the state for a loss of the final density n = sum_k F_k:

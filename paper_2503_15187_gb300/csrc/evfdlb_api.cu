@@ -21,10 +21,10 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const void* rtaps, const void* src, const void* base, void* out, double* rhs_out,
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err);
-void launch_stage_beside(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+void launch_stage_fields(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                          const double* tables, const double* taps, const double* src, const double* base,
-                         double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
-                         double alpha, double beta, int Z, unsigned* err);
+                         double* out, const double* mom_in, double* mom_out, double* fields_out, long long NF,
+                         long long NN, double alpha, double beta, int Z, unsigned* err);
 void launch_init_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                    const WorkItem* items, const double* tables, const void* rtab, const double* n0,
                    const double* u0, const double* T0, void* state, double* mom, long long NF, long long NN, int Z,
@@ -59,14 +59,15 @@ void launch_moments(cudaStream_t st, const double* mom, long long NN, double* n,
 void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                    const WorkItem* items, const double* taps, const double* mom, long long NN, double* part,
                    double* out, double* n, double* u, double* T, double* q);
-size_t adj_smem_bytes(int Q, int Z, int M);
+int adj_tile_max();
+size_t adj_smem_bytes(int Q, int Z);
 size_t adj_moments_smem_bytes(int Z, int m, int M);
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
 void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
                       const WorkItem* items, const double* tables, const double* taps, const double* src,
-                      const double* mom, const double* ybar, const double* acc_in, double* acc_out, double* out,
-                      double* nadj, double* phis, long long NF, long long NN, double ca, double cb, int use_dt,
-                      double cc, double cacc, double cy, int Z, unsigned* err);
+                      const double* fld, const double* mom, const double* ybar, const double* acc_in, double* acc_out,
+                      double* out, double* nadj, double* phis, double* gface, long long NF, long long NN, double ca,
+                      double cb, int use_dt, double cc, double cacc, double cy, int Z);
 void launch_adj_init(int nitems, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                      const double* tables, const double* init_fields, const double* lam, double* dn0, double* du0,
                      double* dT0, long long NF, long long NN);
@@ -145,11 +146,16 @@ struct evfdlb_ctx {
     double* init_fields = nullptr;           // [3][NN]: n0, u0, T0
     std::vector<double*> ckpts;              // state at steps 0, K, 2K, ...
     double* seg[2] = {nullptr, nullptr};   // recomputed segments (two: the recompute of one overlaps
-                                           // the reverse sweep of the other); each (3K+1) states [2 NF]
-                                           // then (3K+1) moment sets [6 NN]
+                                           // the reverse sweep of the other); each (3K+1) states [2 NF],
+                                           // then (3K+1) moment sets [6 NN], then (3K+1) node-field
+                                           // sets [EVFDLB_NFIELDS NN] (of the stage inputs)
     cudaStream_t aux = nullptr;            // the adjoint's recompute stream
     cudaEvent_t ev_fork = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_sweep[2] = {nullptr, nullptr};
-    double* adj = nullptr;       // lam, y1, y2, acc [4][2 NF]; nadj [10 NN]; nbo [4 NN]; phis [NN]; phi [2 nbatch]
+    double* adj = nullptr;       // see AdjBuf
+    // the sweep's work items (node tile aZ <= the sweep kernels' largest tile)
+    WorkItem* aitems = nullptr;
+    std::vector<WorkItem> aitems_h;
+    int aZ = 0;
     // persistent form of the step (evfdlb_set_persistent)
     bool persistent = false;
     long long spin_limit = 0;
@@ -198,6 +204,7 @@ void free_ctx(evfdlb_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->aux) cudaStreamDestroy(c->aux);
     cudaFree(c->adj);
+    cudaFree(c->aitems);
     cudaFree(c->pq);
     cudaFree(c->tiles_d);
     cudaFree(c->slabs);
@@ -322,23 +329,67 @@ evfdlb_status copy_out(evfdlb_ctx* c, double* dst, const double* src, size_t byt
     return EVFDLB_OK;
 }
 
+// Slots of the adjoint's work buffer c->adj (doubles).
+struct AdjBuf {
+    double *lam, *y1, *y2, *acc;   // [2 NF] each
+    double* gface;                 // face gradients of the tiles' edge faces [5][2 NF]
+    double* nadj;                  // node adjoints [10][NN]
+    double* fld;                   // node fields of the state (evfdlb_rhs_vjp) [EVFDLB_NFIELDS][NN]
+    double* phis;                  // per-node phi_a terms [NN]
+    double* phi;                   // phi_a per slab [nbatch]
+    double* dphi;                  // dL/dphi_a per slab [nbatch]
+    size_t total;
+    AdjBuf(double* base, long long NF, long long NN, int nbatch) {
+        double* p = base;
+        auto take = [&](size_t n) { double* q = p; p += n; return q; };
+        lam = take(2 * NF);
+        y1 = take(2 * NF);
+        y2 = take(2 * NF);
+        acc = take(2 * NF);
+        gface = take(10 * (size_t)NF);
+        nadj = take(10 * (size_t)NN);
+        fld = take((size_t)EVFDLB_NFIELDS * NN);
+        phis = take(NN);
+        phi = take(nbatch);
+        dphi = take(nbatch);
+        total = (size_t)(p - base);
+    }
+};
+
+AdjBuf adj_buf(const evfdlb_ctx* c) { return AdjBuf(c->adj, c->NF, c->NN, c->nbatch); }
+
 // Work buffers of the adjoint, allocated on first use.
 evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
     if (!c->adj) {
-        size_t n = 4 * 2 * (size_t)c->NF + (10 + 4 + 1) * (size_t)c->NN + 2 * (size_t)c->nbatch;
-        TRY_CUDA(cudaMalloc((void**)&c->adj, sizeof(double) * n));
+        TRY_CUDA(cudaMalloc((void**)&c->adj, sizeof(double) * AdjBuf(nullptr, c->NF, c->NN, c->nbatch).total));
         std::vector<double> phi(c->nbatch);
         for (int s = 0; s < c->nbatch; ++s) phi[s] = c->params[s].phi_a;
-        double* dphi = c->adj + 4 * 2 * c->NF + 15 * c->NN;
-        TRY_CUDA(cudaMemcpy(dphi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
-        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, kZMax, c->Mmax), adj_moments_smem_bytes(kZMax, c->mmax, c->Mmax)));
+        TRY_CUDA(cudaMemcpy(adj_buf(c).phi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
+        TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, adj_tile_max()),
+                                   adj_moments_smem_bytes(adj_tile_max(), c->mmax, c->Mmax)));
+        TRY_CUDA(cudaMalloc((void**)&c->aitems, sizeof(WorkItem) * (size_t)c->NN));
+    }
+    // the sweep's work items: the step's node tile, capped at the sweep
+    // kernels' largest tile (rebuilt when the step's tile changes; the
+    // previous sweep may still read the list)
+    const int aZ = std::min(c->Z, adj_tile_max());
+    if (aZ != c->aZ) {
+        TRY_CUDA(cudaStreamSynchronize(c->user));
+        c->aitems_h.clear();
+        for (int s = 0; s < c->nbatch; ++s)
+            for (int i0 = 0; i0 < c->params[s].nx; i0 += aZ)
+                c->aitems_h.push_back(WorkItem{s, i0, std::min(aZ, c->params[s].nx - i0), 0});
+        TRY_CUDA(cudaMemcpy(c->aitems, c->aitems_h.data(), sizeof(WorkItem) * c->aitems_h.size(),
+                            cudaMemcpyHostToDevice));
+        c->aZ = aZ;
     }
     if (!c->seg[1] && c->ckpt_every > 0) {
         size_t nst = 3 * (size_t)c->ckpt_every + 1;
         for (int i = 0; i < 2; ++i)
             if (!c->seg[i])
                 TRY_CUDA(cudaMalloc((void**)&c->seg[i],
-                                    sizeof(double) * nst * (2 * (size_t)c->NF + kNumMoments * (size_t)c->NN)));
+                                    sizeof(double) * nst *
+                                        (2 * (size_t)c->NF + (kNumMoments + EVFDLB_NFIELDS) * (size_t)c->NN)));
     }
     if (!c->aux) {
         TRY_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
@@ -361,15 +412,16 @@ evfdlb_status adjoint_supported(evfdlb_ctx* c) {
     return EVFDLB_OK;
 }
 
-// One stage of the reverse sweep on the context's stream.
-void adj_stage(evfdlb_ctx* c, const double* src, const double* mom, const double* ybar, const double* acc_in,
-               double* acc_out, double* out, double ca, double cb, int use_dt, double cc, double cacc, double cy) {
-    double* nadj = c->adj + 4 * 2 * c->NF;
-    double* phis = nadj + 14 * c->NN;
-    launch_adj_stage((int)c->items_h.size(), adj_smem_bytes(c->Qmax, c->Z, c->Mmax),
-                     adj_moments_smem_bytes(c->Z, c->mmax, c->Mmax), c->user, c->slabs, c->items, c->tables, c->taps, src,
-                     mom, ybar, acc_in, acc_out, out, nadj, phis, c->NF, c->NN, ca, cb, use_dt, cc, cacc, cy, c->Z,
-                     c->err);
+// One stage of the reverse sweep on the context's stream; fld: the node
+// fields of src.
+void adj_stage(evfdlb_ctx* c, const double* src, const double* fld, const double* mom, const double* ybar,
+               const double* acc_in, double* acc_out, double* out, double ca, double cb, int use_dt, double cc,
+               double cacc, double cy) {
+    const AdjBuf a = adj_buf(c);
+    launch_adj_stage((int)c->aitems_h.size(), adj_smem_bytes(c->Qmax, c->aZ),
+                     adj_moments_smem_bytes(c->aZ, c->mmax, c->Mmax), c->user, c->slabs, c->aitems, c->tables,
+                     c->taps, src, fld, mom, ybar, acc_in, acc_out, out, a.nadj, a.phis, a.gface, c->NF, c->NN, ca, cb,
+                     use_dt, cc, cacc, cy, c->aZ);
 }
 
 }  // namespace
@@ -985,19 +1037,21 @@ evfdlb_status evfdlb_rhs_vjp(evfdlb_ctx* c, const double* WF, const double* WG, 
     if (st != EVFDLB_OK) return st;
     if ((st = ensure_adjoint_buffers(c)) != EVFDLB_OK) return st;
     size_t bytes = sizeof(double) * c->NF;
-    double* w = c->adj + 2 * c->NF;        // y1 slot
-    double* o = c->adj;                    // lam slot
-    double* phis = c->adj + 4 * 2 * c->NF + 14 * c->NN;
-    double* dph = phis + c->NN + c->nbatch;
+    const AdjBuf a = adj_buf(c);
+    double* w = a.y1;
+    double* o = a.lam;
     if ((st = copy_in(c, w, WF, bytes, on_device)) != EVFDLB_OK) return st;
     if ((st = copy_in(c, w + c->NF, WG, bytes, on_device)) != EVFDLB_OK) return st;
-    TRY_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * c->NN, c->user));
-    adj_stage(c, (const double*)c->state[0], c->mom[0], w, nullptr, nullptr, o, 0.0, 1.0, 0, 0.0, 0.0, 0.0);
-    launch_adj_phi(c->nbatch, c->user, c->slabs, phis, phis + c->NN, dph);
+    TRY_CUDA(cudaMemsetAsync(a.phis, 0, sizeof(double) * c->NN, c->user));
+    // the node fields of the state, then one transposed right-hand side
+    launch_fields_p(EVFDLB_FP64, (int)c->items_h.size(), c->smem, c->user, c->slabs, c->items, c->tables, c->taps,
+                    c->taps, c->mom[0], a.fld, c->NN, c->Z, c->err);
+    adj_stage(c, (const double*)c->state[0], a.fld, c->mom[0], w, nullptr, nullptr, o, 0.0, 1.0, 0, 0.0, 0.0, 0.0);
+    launch_adj_phi(c->nbatch, c->user, c->slabs, a.phis, a.phi, a.dphi);
     TRY_CUDA(cudaGetLastError());
     if ((st = copy_out(c, outF, o, bytes, on_device)) != EVFDLB_OK) return st;
     if ((st = copy_out(c, outG, o + c->NF, bytes, on_device)) != EVFDLB_OK) return st;
-    if (dphi) TRY_CUDA(cudaMemcpyAsync(dphi, dph, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
+    if (dphi) TRY_CUDA(cudaMemcpyAsync(dphi, a.dphi, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
     return check_device(c);
 }
 
@@ -1013,13 +1067,8 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     if ((st = ensure_adjoint_buffers(c)) != EVFDLB_OK) return st;
     const long long NF = c->NF, NN = c->NN;
     const size_t sbytes = sizeof(double) * NF;
-    double* lam = c->adj;
-    double* y1 = lam + 2 * NF;
-    double* y2 = y1 + 2 * NF;
-    double* acc = y2 + 2 * NF;
-    double* phis = c->adj + 4 * 2 * NF + 14 * NN;
-    double* phi_dev = phis + NN;
-    double* dph = phi_dev + c->nbatch;
+    const AdjBuf a = adj_buf(c);
+    double *lam = a.lam, *y1 = a.y1, *y2 = a.y2, *acc = a.acc, *phis = a.phis;
     if ((st = copy_in(c, lam, barF, sbytes, on_device)) != EVFDLB_OK) return st;
     if ((st = copy_in(c, lam + NF, barG, sbytes, on_device)) != EVFDLB_OK) return st;
     TRY_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * NN, c->user));
@@ -1033,29 +1082,31 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     // the sweep of segment sg + 1 has finished with it.  Every kernel computes
     // the same values as in a serial order: the overlap changes no result.
     auto segp = [&](int64_t sg) { return c->seg[sg & 1]; };
-    // `beside`: the recompute overlaps a reverse sweep on the user stream
-    auto recompute = [&](int64_t sg, bool beside) -> cudaError_t {
+    // slot j of a segment buffer: state, raw moment sums, node fields
+    auto sst_of = [&](double* base, size_t j) { return base + j * 2 * NF; };
+    auto smo_of = [&](double* base, size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
+    auto sfl_of = [&](double* base, size_t j) {
+        return base + nst * (2 * NF + kNumMoments * NN) + j * EVFDLB_NFIELDS * NN;
+    };
+    // the recompute of a segment from its checkpoint; every stage also
+    // stores the node fields of its input for the sweep
+    auto recompute = [&](int64_t sg) -> cudaError_t {
         double* base = segp(sg);
-        auto sst = [&](size_t j) { return base + j * 2 * NF; };
-        auto smo = [&](size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
+        auto sst = [&](size_t j) { return sst_of(base, j); };
+        auto smo = [&](size_t j) { return smo_of(base, j); };
         const int ns = (int)std::min<int64_t>(K, c->steps - sg * K);
         cudaError_t e = cudaMemcpyAsync(sst(0), c->ckpts[sg], sizeof(double) * 2 * NF, cudaMemcpyDeviceToDevice, c->aux);
         if (e != cudaSuccess) return e;
         launch_sums_p(EVFDLB_FP64, n, c->aux, c->slabs, c->items, c->tables, c->tables, sst(0), smo(0), NF, NN, c->err);
-        auto stage = [&](const double* src, const double* sbase, double* out, const double* mi, double* mo,
-                         double alpha, double beta) {
-            if (beside)
-                launch_stage_beside(n, c->smem, c->aux, c->slabs, c->items, c->tables, c->taps, src, sbase, out, mi,
-                                    mo, NF, NN, alpha, beta, c->Z, c->err);
-            else
-                launch_stage_p(EVFDLB_FP64, n, c->smem, c->aux, c->slabs, c->items, c->tables, c->tables, c->taps,
-                               c->taps, src, sbase, out, nullptr, mi, mo, NF, NN, alpha, beta, 0, c->Z, c->err);
+        auto stage = [&](size_t j, const double* sbase, double alpha, double beta) {
+            launch_stage_fields(n, c->smem, c->aux, c->slabs, c->items, c->tables, c->taps, sst(j), sbase, sst(j + 1),
+                                smo(j), smo(j + 1), sfl_of(base, j), NF, NN, alpha, beta, c->Z, c->err);
         };
         for (int t = 0; t < ns; ++t) {
             size_t b = 3 * (size_t)t;
-            stage(sst(b), nullptr, sst(b + 1), smo(b), smo(b + 1), 0.0, 1.0);
-            stage(sst(b + 1), sst(b), sst(b + 2), smo(b + 1), smo(b + 2), 0.75, 0.25);
-            stage(sst(b + 2), sst(b), sst(b + 3), smo(b + 2), smo(b + 3), 1.0 / 3.0, 2.0 / 3.0);
+            stage(b, nullptr, 0.0, 1.0);
+            stage(b + 1, sst(b), 0.75, 0.25);
+            stage(b + 2, sst(b), 1.0 / 3.0, 2.0 / 3.0);
         }
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_rec[sg & 1], c->aux);
@@ -1063,16 +1114,17 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
     };
     TRY_CUDA(cudaEventRecord(c->ev_fork, c->user));      // the checkpoints and lam are ready
     TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-    TRY_CUDA(recompute(nseg - 1, false));
+    TRY_CUDA(recompute(nseg - 1));
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
         if (sg >= 1) {
             if (sg + 1 <= nseg - 1) TRY_CUDA(cudaStreamWaitEvent(c->aux, c->ev_sweep[(sg + 1) & 1], 0));
-            TRY_CUDA(recompute(sg - 1, true));
+            TRY_CUDA(recompute(sg - 1));
         }
         TRY_CUDA(cudaStreamWaitEvent(c->user, c->ev_rec[sg & 1], 0));
         double* base = segp(sg);
-        auto sstate = [&](size_t j) { return base + j * 2 * NF; };
-        auto smom = [&](size_t j) { return base + nst * 2 * NF + j * kNumMoments * NN; };
+        auto sstate = [&](size_t j) { return sst_of(base, j); };
+        auto smom = [&](size_t j) { return smo_of(base, j); };
+        auto sfld = [&](size_t j) { return sfl_of(base, j); };
         const int ns = (int)std::min<int64_t>(K, c->steps - sg * K);
         // reverse sweep of the segment (Shu-Osher stages in reverse order):
         //   y2  = 2/3 lam + J(u2)^T (2/3 dt lam),   acc = 1/3 lam
@@ -1080,10 +1132,10 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
         //   lam = y1 + J(u)^T (dt y1) + acc
         for (int t = ns - 1; t >= 0; --t) {
             size_t b = 3 * (size_t)t;
-            adj_stage(c, sstate(b + 2), smom(b + 2), lam, nullptr, acc, y2, 2.0 / 3.0, 2.0 / 3.0, 1, 0.0, 0.0,
-                      1.0 / 3.0);
-            adj_stage(c, sstate(b + 1), smom(b + 1), y2, acc, acc, y1, 0.25, 0.25, 1, 0.0, 1.0, 0.75);
-            adj_stage(c, sstate(b), smom(b), y1, acc, nullptr, lam, 1.0, 1.0, 1, 1.0, 0.0, 0.0);
+            adj_stage(c, sstate(b + 2), sfld(b + 2), smom(b + 2), lam, nullptr, acc, y2, 2.0 / 3.0, 2.0 / 3.0, 1,
+                      0.0, 0.0, 1.0 / 3.0);
+            adj_stage(c, sstate(b + 1), sfld(b + 1), smom(b + 1), y2, acc, acc, y1, 0.25, 0.25, 1, 0.0, 1.0, 0.75);
+            adj_stage(c, sstate(b), sfld(b), smom(b), y1, acc, nullptr, lam, 1.0, 1.0, 1, 1.0, 0.0, 0.0);
         }
         TRY_CUDA(cudaGetLastError());
         TRY_CUDA(cudaEventRecord(c->ev_sweep[sg & 1], c->user));
@@ -1101,9 +1153,9 @@ evfdlb_status evfdlb_adjoint_state(evfdlb_ctx* c, const double* barF, const doub
         if (dL_dT0 && (s2 = copy_out(c, dL_dT0, f + 2 * NN, nb, on_device)) != EVFDLB_OK) return s2;
     }
     if (dL_dphi_a) {
-        launch_adj_phi(c->nbatch, c->user, c->slabs, phis, phi_dev, dph);
+        launch_adj_phi(c->nbatch, c->user, c->slabs, phis, a.phi, a.dphi);
         TRY_CUDA(cudaGetLastError());
-        TRY_CUDA(cudaMemcpyAsync(dL_dphi_a, dph, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
+        TRY_CUDA(cudaMemcpyAsync(dL_dphi_a, a.dphi, sizeof(double) * c->nbatch, cudaMemcpyDeviceToHost, c->user));
     }
     return check_device(c);
 }

@@ -12,10 +12,33 @@
 #include <math.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "evfdlb_internal.h"
 
 namespace evfdlb {
+
+// Launches a kernel as a programmatic dependent of the kernel before it in
+// the stream: its CTAs may be scheduled once every CTA of that kernel has
+// reached griddepcontrol.launch_dependents (or exited), and stage what no
+// kernel writes; griddepcontrol.wait in the kernel holds back everything
+// that reads the previous kernel's results until it has completed.  Only
+// for launches whose stream predecessor is a kernel (not an event wait).
+// Launch errors are left for cudaGetLastError, as with <<<>>>.
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), int grid, int threads, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 __device__ __forceinline__ int gidx(int i, int nx, int bc) {
     if (bc == EVFDLB_BC_PERIODIC) {

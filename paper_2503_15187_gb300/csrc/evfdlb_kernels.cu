@@ -64,8 +64,9 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
                                            const double* __restrict__ tables, const R* __restrict__ rtab,
                                            const double* __restrict__ taps, const R* __restrict__ rtaps,
                                            const R* src, const R* base, R* out, double* rhs_out,
-                                           const double* mom_in, double* mom_out, long long NF, long long NN,
-                                           double alpha, double beta, int mode, int Z, unsigned* err) {
+                                           const double* mom_in, double* mom_out, double* fields_out,
+                                           long long NF, long long NN, double alpha, double beta, int mode, int Z,
+                                           unsigned* err) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     Smem<R> s = carve<R>(smem, Q, Z, sd.M);
 
@@ -120,10 +121,10 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     // warps are the longer side of the phase and the FP64 pipe the bound.
     constexpr bool WF = std::is_same<R, float>::value && !DF;
     if (threadIdx.x < 32 * NW) {
-        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, nullptr, threadIdx.x, 32 * NW);
+        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, fields_out, threadIdx.x, 32 * NW);
         node_sync();
         if constexpr (WF) asm volatile("bar.sync 3, %0;" ::"r"((int)blockDim.x) : "memory");
-        node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, nullptr, threadIdx.x, 32 * NW);
+        node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, fields_out, threadIdx.x, 32 * NW);
         node_sync();
         node_coefficients<R, !WF>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
     } else {
@@ -255,13 +256,13 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
              const R* __restrict__ src, const R* base, R* out, double* rhs_out,
-             const double* __restrict__ mom_in, double* __restrict__ mom_out,
+             const double* __restrict__ mom_in, double* __restrict__ mom_out, double* __restrict__ fields_out,
              long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
     extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
-    stage_body<R, DF, false>(sd, it, smem, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF,
-                             NN, alpha, beta, mode, Z, err);
+    stage_body<R, DF, false>(sd, it, smem, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out,
+                             fields_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,7 +326,8 @@ __global__ void __launch_bounds__(StageThreads<double>::value, 2) persist_kernel
         const double alpha = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
         const double beta = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
         stage_body<double, false, true>(sd, it, smem, a.tables, a.tables, a.taps, a.taps, src, base, out, nullptr,
-                                        a.mom[stage], a.mom[(stage + 1) % 3], a.NF, a.NN, alpha, beta, 0, a.Z, a.err);
+                                        a.mom[stage], a.mom[(stage + 1) % 3], nullptr, a.NF, a.NN, alpha, beta, 0,
+                                        a.Z, a.err);
         __threadfence();                               // this thread's writes, before the release
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(a.done + it.slab, 1u);
@@ -631,27 +633,6 @@ size_t stage_smem_bytes_p(int prec, int Q, int Z, int M) {
 // block (4 H Z >= 2 Q Z doubles).
 size_t stage_smem_bytes_df(int Q, int Z, int M) { return smem_bytes_t<double>(Q, Z, M); }
 
-// Launches a stage kernel as a programmatic dependent of the kernel before
-// it in the stream: its CTAs may be scheduled once every CTA of that kernel
-// has reached griddepcontrol.launch_dependents (or exited), and stage their
-// constant inputs; griddepcontrol.wait in the kernel holds back everything
-// that reads the previous kernel's results until it has completed.  Launch
-// errors are left for cudaGetLastError, as with <<<>>>.
-template <typename... P, typename... A>
-static void launch_stage_pdl(void (*k)(P...), int grid, int threads, size_t smem, cudaStream_t st, A&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
-}
-
 cudaError_t configure_df(size_t smem_bytes) {
     return cudaFuncSetAttribute(stage_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);
@@ -662,9 +643,9 @@ void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* s
                      const double* tables, const double* dftab, const double* taps, const double* src,
                      const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
                      long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
-    launch_stage_pdl(stage_kernel<double, true>, nitems, StageThreads<double, true>::value, smem, st, slabs, items,
-                     tables, dftab, taps, taps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z,
-                     err);
+    launch_pdl(stage_kernel<double, true>, nitems, StageThreads<double, true>::value, smem, st, slabs, items, tables,
+               dftab, taps, taps, src, base, out, rhs_out, mom_in, mom_out, nullptr, NF, NN, alpha, beta, mode, Z,
+               err);
 }
 
 template <typename R>
@@ -699,17 +680,16 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
     return cudaSuccess;
 }
 
-// The FP64 stage (8 warps; see StageThreads).  `beside`: the launch runs
-// concurrently with kernels on another stream (the adjoint's segment
-// recompute beside the reverse sweep); the form is the same.
+// The FP64 stage (8 warps; see StageThreads); fields_out (or null): the
+// node fields of the stage input, [EVFDLB_NFIELDS][NN].
 static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                               const WorkItem* items, const double* tables, const double* rtab, const double* taps,
                               const double* rtaps, const double* src, const double* base, double* out,
                               double* rhs_out, const double* mom_in, double* mom_out, long long NF, long long NN,
-                              double alpha, double beta, int mode, int Z, unsigned* err, bool beside = false) {
-    (void)beside;
-    launch_stage_pdl(stage_kernel<double>, nitems, StageThreads<double>::value, smem, st, slabs, items, tables, rtab,
-                     taps, rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+                              double alpha, double beta, int mode, int Z, unsigned* err,
+                              double* fields_out = nullptr) {
+    launch_pdl(stage_kernel<double>, nitems, StageThreads<double>::value, smem, st, slabs, items, tables, rtab, taps,
+               rtaps, src, base, out, rhs_out, mom_in, mom_out, fields_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
@@ -718,25 +698,24 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err) {
     if (prec == EVFDLB_FP32)
-        launch_stage_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
-                         (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base,
-                         (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+        launch_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
+                   (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base, (float*)out,
+                   rhs_out, mom_in, mom_out, nullptr, NF, NN, alpha, beta, mode, Z, err);
     else
         launch_stage_fp64(nitems, smem, st, slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps,
                           (const double*)src, (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN,
                           alpha, beta, mode, Z, err);
 }
 
-// FP64 stage running concurrently with kernels on another stream (the
-// adjoint's segment recompute beside the reverse sweep): the 8-warp form,
-// which leaves the other kernels about half again as many of each SM's
-// registers (37 K against 24 K beside one stage CTA).
-void launch_stage_beside(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
+// FP64 stage that also stores the node fields of its input state (the
+// adjoint's segment recompute: the reverse sweep reads them instead of
+// forming them again).
+void launch_stage_fields(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs, const WorkItem* items,
                          const double* tables, const double* taps, const double* src, const double* base,
-                         double* out, const double* mom_in, double* mom_out, long long NF, long long NN,
-                         double alpha, double beta, int Z, unsigned* err) {
+                         double* out, const double* mom_in, double* mom_out, double* fields_out, long long NF,
+                         long long NN, double alpha, double beta, int Z, unsigned* err) {
     launch_stage_fp64(nitems, smem, st, slabs, items, tables, tables, taps, taps, src, base, out, nullptr, mom_in,
-                      mom_out, NF, NN, alpha, beta, 0, Z, err, true);
+                      mom_out, NF, NN, alpha, beta, 0, Z, err, fields_out);
 }
 
 // FP64 stage (mode 0 writes out; mode 1 writes the right-hand side to out).
