@@ -59,7 +59,8 @@ constexpr int kTapChunks = 8;    // lanes per node of the tap correlations
 // the parity-split synthesis table and columns of the transposed analysis
 // table (node k pairs with Q-1-k; the middle node of an odd Q stands alone).
 // The state tile holds nodes i0-3 .. i0+nz+1 (the stencils of the tile's
-// own faces), v holds i0-1 .. i0+nz-1.  The face gradients G5 are dead once
+// own faces), the ybar tile i0-1 .. i0+nz-1 (v = cb dt ybar is formed where
+// it is used).  The face gradients G5 are dead once
 // gathered; Ha and the per-node sums Red then reuse their block.
 struct AdjLay {
     int NP, WH, WV;
@@ -78,7 +79,7 @@ struct AdjLay {
         rinv = o; o += Q;
         rr = o;   o += Q;
         H = o;    o += 2 * (size_t)Q * WH;     // [2Q][WH]
-        V = o;    o += 2 * (size_t)Q * WV;     // [2Q][WV]
+        V = o;    o += 2 * (size_t)Q * WV;     // ybar [2Q][WV]
         Fl = o;   o += (size_t)EVFDLB_NFIELDS * Z;
         J = o;    o += (size_t)kNumJac * Z;
         Cc = o;   o += 8 * (size_t)Z;          // c0..c3 per distribution [2][4][Z]
@@ -166,8 +167,8 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const long long row0 = sd.f_off + it.i0;     // + d NF + k nx: velocity k, distribution d, node i0
 
-    // Step 0: tables, the state tile (i0-3 .. i0+nz+1), v = cb dt ybar
-    // (i0-1 .. i0+nz-1) and the node fields of the tile.
+    // Step 0: tables, the state tile (i0-3 .. i0+nz+1), ybar (i0-1 ..
+    // i0+nz-1) and the node fields of the tile, all loads in one phase.
     if (tid == 0) s_next = 0;
     for (int e = tid; e < NP * Q; e += nth) sS[e] = tab[L.S + e];
     for (int e = tid; e < Q * NP; e += nth) {
@@ -191,7 +192,7 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     for (int e = tid; e < 2 * Q * (nz + 1); e += nth) {
         const int c = e % (nz + 1), r = e / (nz + 1);
         const int k = r % Q, d = r / Q;
-        sV[r * WV + c] = vscale * ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - 1 + c, nx, bc)];
+        sV[r * WV + c] = ybar[d * NF + sd.f_off + (long long)k * nx + gidx(it.i0 - 1 + c, nx, bc)];
     }
     for (int e = tid; e < EVFDLB_NFIELDS * nz; e += nth) {
         const int f = e / nz, t = e - f * nz;
@@ -206,7 +207,7 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
     //  warp 1: derivatives of the node maps (nu, kq, K, gradient ratios);
     //  warp 2: coefficient constants c0..c3 (c_l = sum_r c_r sqrt(l!/(l-r)!)
     //          m_{l-r}, Eqs. (enskog_approx) and (J1)) and the parity parts
-    //          of v at the tile nodes.
+    //          of v = cb dt ybar at the tile nodes.
     auto F = [&](int f, int t) { return sFl[f * Z + t]; };
     if (warp == 0) {
         for (int t = lane; t < nz; t += 32) {
@@ -282,19 +283,19 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
             const double a = v[k * WV];
             const bool pair = (Q - 1 - k != k);
             const double bm = pair ? v[(Q - 1 - k) * WV] : 0.0;
-            sVE[((d * 2 + 0) * NP + k) * Z + t] = pair ? a + bm : a;
-            sVE[((d * 2 + 1) * NP + k) * Z + t] = pair ? a - bm : 0.0;
+            sVE[((d * 2 + 0) * NP + k) * Z + t] = vscale * (pair ? a + bm : a);
+            sVE[((d * 2 + 1) * NP + k) * Z + t] = pair ? vscale * (a - bm) : 0.0;
         }
     }
     // The tile's own faces: face p (tile-relative, between nodes p-1 and p)
     // of row r = d Q + k.  For xi > 0 its WENO-5 stencil is nodes p-3 .. p+1
     // (v0 .. v4), for xi < 0 nodes p+2 .. p-2; its adjoint is
-    // pb = xi/dz (v_p - v_{p-1}).  G5[s][r][p] = pb dPhi/dv_s.  A face whose
+    // pb = xi/dz (v_p - v_{p-1}), v = cb dt ybar.  G5[s][r][p] = pb dPhi/dv_s.  A face whose
     // stencil leaves the tile also goes to gface (global, by face), where the
     // neighbouring tiles' adj_moments_kernel collects its terms.
     {
         const int nface = 2 * Q * nz, ngroup = (nface + 31) / 32;
-        const double rdz = sd.inv_dx, eps = sd.weno_eps;
+        const double rdz = sd.inv_dx * vscale, eps = sd.weno_eps;
         for (;;) {
             int g = 0;
             if (lane == 0) g = atomicAdd(&s_next, 1);
@@ -307,7 +308,7 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
                 const double x = sxi[k];
                 double gg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
                 const double* h = sH + (size_t)r * WH + p;      // h[c] = node p - 3 + c
-                const double* v = sV + (size_t)r * WV + p;      // v[0] = node p - 1, v[1] = node p
+                const double* v = sV + (size_t)r * WV + p;      // ybar at nodes p - 1, p
                 if (x > 0.0) {
                     weno5_grad(h[0], h[1], h[2], h[3], h[4], eps, x * rdz * (v[1] - v[0]), gg);
                 } else if (x < 0.0) {
@@ -419,7 +420,7 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
                     red[3 * Z] = acc[3];
                     red[4 * Z] = acc[4];
                     red[5 * Z] = 0.5 * acc[5];
-                    red[7 * Z] = acc[6];
+                    red[7 * Z] = vscale * acc[6];
                 }
             } else {
                 const int e = base - nsum_p + lane;
@@ -534,10 +535,9 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
             const int t = e % nz, r = e / nz;
             const int j = r % Q, d = r / Q;
             const double F1 = F(FL_F1, t), nu = F(FL_NU, t);
-            const double vv = sV[(size_t)r * WV + t + 1];
-            const double val = fma(F1, sHa[(size_t)r * Z + t], fma(-nu, vv, sHw[(size_t)r * Z + t]));
+            const double yb = sV[(size_t)r * WV + t + 1];
+            const double val = fma(F1, sHa[(size_t)r * Z + t], fma(-nu, vscale * yb, sHw[(size_t)r * Z + t]));
             const long long g = d * NF + row0 + (long long)j * nx + t;
-            const double yb = ybar[g];
             double o = fma(ca, yb, val);
             if (cc != 0.0) o = fma(cc, acc_in[g], o);
             if (acc_out) acc_out[g] = (cacc != 0.0 ? cacc * acc_in[g] : 0.0) + cy * yb;
@@ -553,29 +553,39 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
 // chain (n, u, T, q) <- raw sums, and
 // out_{F,k} += S0b + xi S1b + xi^2 S2b + xi^3 S3b, out_{G,k} += G0b + xi G1b,
 // plus the terms of the faces outside the tile whose stencils reach it.
+// Every global input is staged in one phase, so that their latencies overlap.
 struct AdjMomLay {
-    size_t Xb, Nb, n, T, chi, F1, DX, DU, DT, sb, part, ftap, mtap, total;
-    __host__ __device__ AdjMomLay(int Z, int m, int M) {
+    size_t Xb, Nb, n, T, chi, nbar, xa, ca, F1, DX, DU, DT, na, mm, u, sb, part, out, ftap, mtap, total;
+    __host__ __device__ AdjMomLay(int Q, int Z, int m, int M) {
         const size_t HW = Z + 2 * m;
         size_t o = 0;
         Xb = o;   o += HW;                      // X adjoint on [i0 - m, i0 + nz + m)
         Nb = o;   o += HW;                      // nbar adjoint (source of the FM correlation)
-        n = o;    o += HW;                      // n, T, chi on the same nodes
+        n = o;    o += HW;                      // n, T, chi, nbar on the same nodes
         T = o;    o += HW;
         chi = o;  o += HW;
+        nbar = o; o += HW;
+        xa = o;   o += HW;                      // node adjoints of X and chi there
+        ca = o;   o += HW;
         F1 = o;   o += (size_t)Z + 2 * M;       // force adjoint on [i0 - M, i0 + nz + M)
         DX = o;   o += (size_t)Z + 2 * m + 4;   // X-gradient adjoint on [i0 - m - 2, i0 + nz + m + 2)
         DU = o;   o += (size_t)Z + 4;           // u- and T-gradient adjoints on [i0 - 2, i0 + nz + 2)
         DT = o;   o += (size_t)Z + 4;
+        na = o;   o += 4 * (size_t)Z;           // node adjoints of n, u, T, q on the tile
+        mm = o;   o += 3 * (size_t)Z;           // S1, S2, G0 on the tile
+        u = o;    o += (size_t)Z;               // u on the tile
         sb = o;   o += (size_t)kNumMoments * Z; // raw-sum adjoints of the tile
         part = o; o += (size_t)kTapChunks * Z;  // partial tap sums
+        out = o;  o += 2 * (size_t)Q * Z;       // out of the tile plus the outside faces' terms
         ftap = o; o += 2 * (size_t)M + 1;       // Eq. (F1) taps
         mtap = o; o += 2 * (size_t)m + 1;       // Fischer-Methfessel taps
         total = o;
     }
 };
 
-__host__ __device__ inline size_t adj_moments_smem_doubles(int Z, int m, int M) { return AdjMomLay(Z, m, M).total; }
+__host__ __device__ inline size_t adj_moments_smem_doubles(int Q, int Z, int m, int M) {
+    return AdjMomLay(Q, Z, m, M).total;
+}
 
 __global__ void __launch_bounds__(kThreads)
 adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
@@ -586,13 +596,17 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     const int nx = sd.nx, bc = sd.bc, M = sd.M, m = sd.m, Q = sd.Q, nz = it.nz;
-    const AdjMomLay Ly(Z, m, M);
+    const AdjMomLay Ly(Q, Z, m, M);
     double *sXb = sm + Ly.Xb, *sNb = sm + Ly.Nb, *sn = sm + Ly.n, *sT = sm + Ly.T, *schi = sm + Ly.chi;
-    double *sF1 = sm + Ly.F1, *sDX = sm + Ly.DX, *sDU = sm + Ly.DU, *sDT = sm + Ly.DT, *sb = sm + Ly.sb;
-    double *spart = sm + Ly.part, *ftap = sm + Ly.ftap, *mtap = sm + Ly.mtap;
+    double *snbar = sm + Ly.nbar, *sxa = sm + Ly.xa, *sca = sm + Ly.ca;
+    double *sF1 = sm + Ly.F1, *sDX = sm + Ly.DX, *sDU = sm + Ly.DU, *sDT = sm + Ly.DT, *sna = sm + Ly.na;
+    double *smm = sm + Ly.mm, *su = sm + Ly.u, *sb = sm + Ly.sb, *spart = sm + Ly.part, *sout = sm + Ly.out;
+    double *ftap = sm + Ly.ftap, *mtap = sm + Ly.mtap;
     const int tid = threadIdx.x, nth = blockDim.x;
     const double inv12 = sd.inv_dx / 12.0;
     const long long no = sd.node_off;
+    TableLayout L(Q);
+    const double* xi = tables + sd.tab_off + L.xi;
     const double* gF1 = nadj + AD_F1 * NN + no;
     const double* gDX = nadj + AD_DX * NN + no;
     const double* gDU = nadj + AD_DU * NN + no;
@@ -606,22 +620,59 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         sDU[c] = gDU[i];
         sDT[c] = gDT[i];
     }
+    for (int c = tid; c < nz + 2 * m; c += nth) {
+        const long long o = no + gidx(it.i0 - m + c, nx, bc);
+        sn[c] = fld[FL_N * NN + o];
+        sT[c] = fld[FL_T * NN + o];
+        schi[c] = fld[FL_CHI * NN + o];
+        snbar[c] = fld[FL_NBAR * NN + o];
+        sxa[c] = nadj[AD_X * NN + o];
+        sca[c] = nadj[AD_CHI * NN + o];
+    }
+    for (int t = tid; t < nz; t += nth) {
+        const long long o = no + it.i0 + t;
+        sna[t] = nadj[AD_N * NN + o];
+        sna[Z + t] = nadj[AD_U * NN + o];
+        sna[2 * Z + t] = nadj[AD_T * NN + o];
+        sna[3 * Z + t] = nadj[AD_Q * NN + o];
+        smm[t] = mom[MOM_S1 * NN + o];
+        smm[Z + t] = mom[MOM_S2 * NN + o];
+        smm[2 * Z + t] = mom[MOM_G0 * NN + o];
+        su[t] = fld[FL_U * NN + o];
+    }
+    // out of the tile, plus the terms of the faces outside the tile whose
+    // stencils hold node t (see adj_local_kernel): xi > 0: faces p = t-1 ..
+    // t+3, node t is v_{t-p+3}; xi < 0: p = t-2 .. t+2, v_{p+2-t}
+    for (int e = tid; e < 2 * Q * nz; e += nth) {
+        const int t = e % nz, r = e / nz;
+        const int k = r % Q, d = r / Q;
+        const long long row = d * NF + sd.f_off + (long long)k * nx;
+        double v = out[row + it.i0 + t];
+        const double x = xi[k];
+        if (x != 0.0) {
+            const int plo = (x > 0.0) ? t - 1 : t - 2;
+            if (plo < 0 || plo + 4 >= nz) {
+                for (int p = plo; p <= plo + 4; ++p) {
+                    if (p >= 0 && p < nz) continue;
+                    const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
+                    v += gface[s * 2 * NF + row + gidx(it.i0 + p, nx, bc)];
+                }
+            }
+        }
+        sout[(size_t)r * Z + t] = v;
+    }
     __syncthreads();
     // transposed fourth-order difference at staged position p (value at p)
     auto d4t = [&](const double* g, int p) { return (g[p + 2] - 8.0 * g[p + 1] + 8.0 * g[p - 1] - g[p - 2]) * inv12; };
     // the chain to chi on the tile and its Fischer-Methfessel halo
     for (int c = tid; c < nz + 2 * m; c += nth) {
-        const long long o = no + gidx(it.i0 - m + c, nx, bc);
-        const double n = fld[FL_N * NN + o], T = fld[FL_T * NN + o], chi = fld[FL_CHI * NN + o];
-        const double eta = sd.eta_coef * fld[FL_NBAR * NN + o], om = 1.0 - eta, om2 = om * om;
-        const double Xb = nadj[AD_X * NN + o] + d4t(sDX, c + 2);
-        const double chib = nadj[AD_CHI * NN + o] + Xb * n * n * T;
+        const double n = sn[c], T = sT[c];
+        const double eta = sd.eta_coef * snbar[c], om = 1.0 - eta, om2 = om * om;
+        const double Xb = sxa[c] + d4t(sDX, c + 2);
+        const double chib = sca[c] + Xb * n * n * T;
         // dchi/deta = (5 - 2 eta) / (2 (1 - eta)^4)
         sXb[c] = Xb;
         sNb[c] = chib * div_nr(5.0 - 2.0 * eta, 2.0 * om2 * om2) * sd.eta_coef;
-        sn[c] = n;
-        sT[c] = T;
-        schi[c] = chi;
     }
     __syncthreads();
     // the two correlations, sum_j mtap_j Nb_{i-j} + sum_j ftap_j F1b_{i-j},
@@ -644,17 +695,15 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
     __syncthreads();
     for (int t = tid; t < nz; t += nth) {
         const int c = t + m;
-        const long long o = no + it.i0 + t;
         const double n = sn[c], T = sT[c], chi = schi[c], Xb = sXb[c];
-        double nb = nadj[AD_N * NN + o] + Xb * 2.0 * n * chi * T;
+        double nb = sna[t] + Xb * 2.0 * n * chi * T;
         for (int ch = 0; ch < kTapChunks; ++ch) nb += spart[ch * Z + t];
-        double ub = nadj[AD_U * NN + o] + d4t(sDU, t + 2);
-        double Tb = nadj[AD_T * NN + o] + d4t(sDT, t + 2) + Xb * n * n * chi;
-        const double qb = nadj[AD_Q * NN + o];
-        const double S0v = mom[MOM_S0 * NN + o], S1v = mom[MOM_S1 * NN + o];
-        const double S2v = mom[MOM_S2 * NN + o], G0v = mom[MOM_G0 * NN + o];
+        double ub = sna[Z + t] + d4t(sDU, t + 2);
+        double Tb = sna[2 * Z + t] + d4t(sDT, t + 2) + Xb * n * n * chi;
+        const double qb = sna[3 * Z + t];
+        const double S0v = n, S1v = smm[t], S2v = smm[Z + t], G0v = smm[2 * Z + t];
         const double in = div_nr(1.0, n);
-        const double u = fld[FL_U * NN + o];
+        const double u = su[t];
         const double E = (0.5 * S2v + G0v) * in;
         // q = (S3 - 3u S2 + 3u^2 S1 - u^3 S0)/2 + G1 - u G0
         double S3b = 0.5 * qb, S2b = -1.5 * u * qb, S1b = 1.5 * u * u * qb, S0b = -0.5 * u * u * u * qb;
@@ -678,28 +727,13 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         sb[MOM_G1 * Z + t] = G1b;
     }
     __syncthreads();
-    TableLayout L(Q);
-    const double* xi = tables + sd.tab_off + L.xi;
     for (int e = tid; e < 2 * Q * nz; e += nth) {
         const int t = e % nz, r = e / nz;
         const int k = r % Q, d = r / Q;
         const double x = xi[k];
-        double add = (d == 0) ? sb[MOM_S0 * Z + t] + x * (sb[MOM_S1 * Z + t] + x * (sb[MOM_S2 * Z + t] + x * sb[MOM_S3 * Z + t]))
-                              : sb[MOM_G0 * Z + t] + x * sb[MOM_G1 * Z + t];
-        // faces outside the tile whose stencils hold node t (see adj_local_kernel):
-        // xi > 0: faces p = t-1 .. t+3, node t is v_{t-p+3}; xi < 0: p = t-2 .. t+2, v_{p+2-t}
-        if (x != 0.0) {
-            const int plo = (x > 0.0) ? t - 1 : t - 2;
-            if (plo < 0 || plo + 4 >= nz) {
-                const double* gf = gface + d * NF + sd.f_off + (long long)k * nx;
-                for (int p = plo; p <= plo + 4; ++p) {
-                    if (p >= 0 && p < nz) continue;
-                    const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
-                    add += gf[s * 2 * NF + gidx(it.i0 + p, nx, bc)];
-                }
-            }
-        }
-        out[d * NF + sd.f_off + (long long)k * nx + it.i0 + t] += add;
+        const double add = (d == 0) ? sb[MOM_S0 * Z + t] + x * (sb[MOM_S1 * Z + t] + x * (sb[MOM_S2 * Z + t] + x * sb[MOM_S3 * Z + t]))
+                                    : sb[MOM_G0 * Z + t] + x * sb[MOM_G1 * Z + t];
+        out[d * NF + sd.f_off + (long long)k * nx + it.i0 + t] = sout[(size_t)r * Z + t] + add;
     }
 }
 
@@ -770,7 +804,7 @@ int adj_tile_max() { return kZAdj; }
 
 size_t adj_smem_bytes(int Q, int Z) { return adj_smem_doubles(Q, Z) * sizeof(double); }
 
-size_t adj_moments_smem_bytes(int Z, int m, int M) { return adj_moments_smem_doubles(Z, m, M) * sizeof(double); }
+size_t adj_moments_smem_bytes(int Q, int Z, int m, int M) { return adj_moments_smem_doubles(Q, Z, m, M) * sizeof(double); }
 
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes) {
     cudaError_t e = cudaFuncSetAttribute(adj_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

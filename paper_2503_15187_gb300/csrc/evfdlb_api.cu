@@ -61,7 +61,7 @@ void launch_totals(int nslabs, int nitems, size_t smem, cudaStream_t st, const S
                    double* out, double* n, double* u, double* T, double* q);
 int adj_tile_max();
 size_t adj_smem_bytes(int Q, int Z);
-size_t adj_moments_smem_bytes(int Z, int m, int M);
+size_t adj_moments_smem_bytes(int Q, int Z, int m, int M);
 cudaError_t configure_adjoint(size_t smem_bytes, size_t smem2_bytes);
 void launch_adj_stage(int nitems, size_t smem, size_t smem2, cudaStream_t st, const SlabDesc* slabs,
                       const WorkItem* items, const double* tables, const double* taps, const double* src,
@@ -366,7 +366,7 @@ evfdlb_status ensure_adjoint_buffers(evfdlb_ctx* c) {
         for (int s = 0; s < c->nbatch; ++s) phi[s] = c->params[s].phi_a;
         TRY_CUDA(cudaMemcpy(adj_buf(c).phi, phi.data(), sizeof(double) * c->nbatch, cudaMemcpyHostToDevice));
         TRY_CUDA(configure_adjoint(adj_smem_bytes(c->Qmax, adj_tile_max()),
-                                   adj_moments_smem_bytes(adj_tile_max(), c->mmax, c->Mmax)));
+                                   adj_moments_smem_bytes(c->Qmax, adj_tile_max(), c->mmax, c->Mmax)));
         TRY_CUDA(cudaMalloc((void**)&c->aitems, sizeof(WorkItem) * (size_t)c->NN));
     }
     // the sweep's work items: the step's node tile, capped at the sweep
@@ -419,7 +419,7 @@ void adj_stage(evfdlb_ctx* c, const double* src, const double* fld, const double
                double cacc, double cy) {
     const AdjBuf a = adj_buf(c);
     launch_adj_stage((int)c->aitems_h.size(), adj_smem_bytes(c->Qmax, c->aZ),
-                     adj_moments_smem_bytes(c->aZ, c->mmax, c->Mmax), c->user, c->slabs, c->aitems, c->tables,
+                     adj_moments_smem_bytes(c->Qmax, c->aZ, c->mmax, c->Mmax), c->user, c->slabs, c->aitems, c->tables,
                      c->taps, src, fld, mom, ybar, acc_in, acc_out, out, a.nadj, a.phis, a.gface, c->NF, c->NN, ca, cb,
                      use_dt, cc, cacc, cy, c->aZ);
 }
