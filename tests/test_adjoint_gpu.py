@@ -69,8 +69,14 @@ def test_rhs_transpose_jacobian_elementwise():
         assert abs(dphi[0] - ref_phi) < 1e-12 * np.abs(w).sum() * np.abs(np.concatenate([pF.ravel(), pG.ravel()])).max()
 
 
+# (nz, Q, dz, relax, tile): ragged last tiles (64 = 9 x 7 + 1), tiles of
+# one to three nodes (every WENO-5 stencil leaves its tile on both sides),
+# the sweep's tile cap (tile 64 -> 32), one tile for the whole periodic slab
+# (stencils wrap onto the same tile), odd Q (a zero velocity, whose row has
+# no faces, and the middle node of the parity split)
 @pytest.mark.parametrize("case", [(64, 16, 0.25, 0, 7), (97, 24, 0.25, 0, 13), (50, 8, 0.25, 1, 64),
-                                  (150, 32, 0.1, 0, 27)])
+                                  (150, 32, 0.1, 0, 27), (40, 9, 0.25, 0, 2), (33, 15, 0.25, 1, 3),
+                                  (36, 11, 0.25, 0, 1), (20, 12, 0.25, 0, 64), (29, 7, 0.25, 0, 29)])
 def test_rhs_dot_product_identity(case):
     nz, Q, dz, relax, tile = case
     sim, orc = make(nz, Q, dz, relax=relax, tile=tile)
@@ -90,7 +96,7 @@ def test_rhs_dot_product_identity(case):
         assert abs(lhs - rhs) < 1e-11 * scale
 
 
-@pytest.mark.parametrize("case", [(32, 12, 0.25, 20, 6, 5), (40, 16, 0.25, 9, 9, 64)])
+@pytest.mark.parametrize("case", [(32, 12, 0.25, 20, 6, 5), (40, 16, 0.25, 9, 9, 64), (26, 9, 0.25, 8, 3, 2)])
 def test_trajectory_gradient_against_oracle_tangent(case):
     """Loss L = sum_z (n_end - n_target)^2 after `steps` steps from the
     projected (n0, u0 = 0, T0), checkpoints every `ckpt` steps."""
@@ -132,6 +138,36 @@ def test_trajectory_gradient_against_oracle_tangent(case):
     got = (g["dF0"].reshape(Q, nz) * vF).sum() + (g["dG0"].reshape(Q, nz) * vG).sum()
     print(f"{case} F0 direction: oracle {ref:.10e} gpu {got:.10e}")
     assert abs(got - ref) < 1e-9 * abs(ref)
+
+
+def test_rhs_vjp_of_a_batch_equals_its_slabs_alone():
+    """Slabs of different length and Q in one context give, slab by slab,
+    the same transposed right-hand side (bit for bit) as each slab in a
+    context of its own with the same node tile."""
+    cases = [(40, 9, 0.25), (33, 16, 0.25), (27, 12, 0.25)]
+    tile = 5
+    rng = np.random.default_rng(11)
+    singles, states, ws = [], [], []
+    for nz, Q, dz in cases:
+        sim, orc = make(nz, Q, dz, tile=tile)
+        F, G = nonequilibrium(orc, seed=nz)
+        w = rng.uniform(-1, 1, 2 * Q * nz)
+        sim.set_state(F.ravel(), G.ravel())
+        singles.append(sim.rhs_vjp(w[:Q * nz], w[Q * nz:]))
+        states.append((F.ravel(), G.ravel()))
+        ws.append(w)
+    batch = ev.Sim([ev.Params(nx=nz, dx=dz, Q=Q) for nz, Q, dz in cases])
+    batch.tune(tile)
+    batch.set_state(np.concatenate([f for f, _ in states]), np.concatenate([g for _, g in states]))
+    oF, oG, dphi = batch.rhs_vjp(np.concatenate([w[:len(w) // 2] for w in ws]),
+                                 np.concatenate([w[len(w) // 2:] for w in ws]))
+    off = 0
+    for i, (nz, Q, dz) in enumerate(cases):
+        sF, sG, sphi = singles[i]
+        assert np.array_equal(oF[off:off + Q * nz], sF), i
+        assert np.array_equal(oG[off:off + Q * nz], sG), i
+        assert dphi[i] == sphi[0], i
+        off += Q * nz
 
 
 def test_adjoint_requires_tracking_and_periodic():
