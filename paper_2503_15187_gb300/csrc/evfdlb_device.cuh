@@ -75,6 +75,8 @@ struct Smem {
                         // read only before the coefficients are formed, so it shares
                         // their block; the FP64_DF kernel keeps its float-pair state
                         // tile there instead
+    double *Mp64;       // FP32 state only: group terms of the FP64 moment sums [4][G][Z]
+    R *Mp32;            //   and of the R ones [2][G][Z] (see pair_terms_f32)
 };
 
 // Length of the R copy of the density halo, rounded up to an even count so
@@ -83,6 +85,9 @@ struct Smem {
 __host__ __device__ inline size_t nr_len(int Z, int M) { return ((size_t)(Z + 2 * M) + 1) & ~(size_t)1; }
 
 __host__ __device__ inline size_t ftap_len(int M) { return ((size_t)(2 * M + 1) + 1) & ~(size_t)1; }
+
+// Groups of two velocity pairs in the FP32 moment sums (see moment_sum).
+__host__ __device__ inline int pair_groups(int Q) { return ((Q + 1) / 2 + 1) / 2; }
 
 // Q*Q rounded up to an even count, so that the table blocks stay aligned for
 // two-wide (R2) loads.
@@ -97,7 +102,10 @@ __host__ __device__ inline size_t smem_bytes_t(int Q, int Z, int M) {
                 4 * (size_t)((Q + 1) / 2) * Z + 2 * (size_t)Q * Z + 2 * (size_t)Q * (Z + 6) +
                 2 * (size_t)Q * (Z + 1) + 8 * (size_t)Z + ftap_len(M) + (size_t)Q * Z;
     // + the velocity powers (3Q doubles, 2Q R) and one R of padding before them
-    return (nd + 3 * (size_t)Q) * sizeof(double) + (nr + 2 * (size_t)Q + 1) * sizeof(R);
+    size_t bytes = (nd + 3 * (size_t)Q) * sizeof(double) + (nr + 2 * (size_t)Q + 1) * sizeof(R);
+    // + the pair terms of the moment sums (FP32 state)
+    if (std::is_same<R, float>::value) bytes += (size_t)pair_groups(Q) * Z * (4 * sizeof(double) + 2 * sizeof(R));
+    return bytes;
 }
 
 template <typename R>
@@ -135,6 +143,9 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
     // an even count of doubles' worth: all its segment lengths are even)
     s.Vp = reinterpret_cast<double*>(s.Mm + (size_t)Q * Z + ((size_t)Q * Z) % 2);
     s.Vr = reinterpret_cast<R*>(s.Vp + 3 * Q);
+    // Vr ends 8-byte aligned (2Q R values after an aligned block)
+    s.Mp64 = reinterpret_cast<double*>(s.Vr + 2 * Q);
+    s.Mp32 = reinterpret_cast<R*>(s.Mp64 + 4 * (size_t)pair_groups(Q) * Z);
     return s;
 }
 
@@ -1061,82 +1072,130 @@ __device__ inline void faces_df(const SlabDesc& sd, const WorkItem& it, const Sm
     }
 }
 
-// One raw moment sum of one node from a column h[k * stride] (k < Q), formed
-// as P parts over k in [p Q / P, (p+1) Q / P) combined in a fixed order, so
-// that the parts may be formed by different warps (tile_moment_sums_staged)
-// with the same result.  The conserved moments (S0, S1, S2 of F and G0) are
-// summed in FP64; S3 and G1 (heat flux) in R within a part.  The velocity
-// powers come from xp = [xi, xi^2, xi^3] (FP64) and xr = [xi, xi^3] (R).
-template <typename R>
-__device__ __forceinline__ double moment_part(int which, int Q, int k0, int k1, const R* h, long long stride,
-                                              const double* __restrict__ xp, const R* __restrict__ xr) {
-    const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
-    if (std::is_same<R, double>::value || which == MOM_S0 || which == MOM_S1 || which == MOM_S2 ||
-        which == MOM_G0) {
-        // interleaved chains: four over a whole sum (FP64 state, one part),
-        // two over a quarter (FP32 state, four parts); a float state is
-        // widened by bit surgery (exact for normal floats; no FP64
-        // conversion instruction)
-        auto wide = [](R v) -> double {
-            if constexpr (std::is_same<R, float>::value) return f2d_bits(v);
-            else return v;
-        };
-        const double* w = xp + (p > 0 ? p - 1 : 0) * Q;
-        auto acc = [&](double a, int k) { return p == 0 ? a + wide(h[k * stride]) : fma(w[k], wide(h[k * stride]), a); };
-        if constexpr (std::is_same<R, float>::value) {
-            double a0 = 0.0, a1 = 0.0;
-            int k = k0;
-            for (; k + 1 < k1; k += 2) {
-                a0 = acc(a0, k);
-                a1 = acc(a1, k + 1);
-            }
-            if (k < k1) a0 = acc(a0, k);
-            return a0 + a1;
-        } else {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int k = k0;
-            for (; k + 3 < k1; k += 4) {
-                a0 = acc(a0, k);
-                a1 = acc(a1, k + 1);
-                a2 = acc(a2, k + 2);
-                a3 = acc(a3, k + 3);
-            }
-            for (; k < k1; ++k) a0 = acc(a0, k);
-            return (a0 + a1) + (a2 + a3);
-        }
+// Raw moment sums of one node from a column h[k * stride] (k < Q).  The
+// conserved moments (S0, S1, S2 of F and G0) are summed in FP64; S3 and G1
+// (heat flux) in R.  The velocity powers come from xp = [xi, xi^2, xi^3]
+// (FP64) and xr = [xi, xi^3] (R).
+//
+// FP64 state: four interleaved chains over k, joined as ((a0 + a1) + (a2 + a3)).
+//
+// FP32 state: the pair form.  Velocity j < H = (Q+1)/2 and its mirror Q-1-j
+// (xi_{Q-1-j} = -xi_j) give one term per pair, with a = h_j, b = h_{Q-1-j}
+// (b = 0 for the middle velocity of an odd Q):
+//   S0, G0: a + b;   S1: xi_j (a - b);   S2: xi_j^2 (a + b);
+//   S3: xi_j^3 (a - b);   G1: xi_j (a - b),
+// the FP64 terms from floats widened exactly by bit surgery.  The pairs 2g
+// and 2g+1 form group g < G = (H+1)/2 (term(2g) + term(2g+1); a last lone
+// pair alone), and the G group terms are summed in four chains over g mod
+// 4, joined as ((c0 + c1) + (c2 + c3)).  Every operation is an explicitly
+// rounded one, so the stage kernel, which forms the group terms where it
+// writes the new state (pair_terms_f32) and sums them afterwards
+// (sum_pair_terms), gets the same bits as a sum formed here in one pass.
+__device__ __forceinline__ bool moment_is_f64(int which) {
+    return which == MOM_S0 || which == MOM_S1 || which == MOM_S2 || which == MOM_G0;
+}
+
+__device__ __forceinline__ double pair_term_f64(int which, int j, int Q, double a, double b,
+                                                const double* __restrict__ xp) {
+    if (which == MOM_S0 || which == MOM_G0) return __dadd_rn(a, b);
+    if (which == MOM_S1) return __dmul_rn(xp[j], __dsub_rn(a, b));
+    return __dmul_rn(xp[Q + j], __dadd_rn(a, b));                    // S2
+}
+
+__device__ __forceinline__ float pair_term_f32(int which, int j, int Q, float a, float b,
+                                               const float* __restrict__ xr) {
+    return __fmul_rn(which == MOM_S3 ? xr[Q + j] : xr[j], __fsub_rn(a, b));   // S3, G1
+}
+
+template <typename T>
+__device__ __forceinline__ T add_rn(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) return __fadd_rn(a, b);
+    else return __dadd_rn(a, b);
+}
+
+// Sum of the n terms term(j) in four chains over j mod 4.
+template <typename T, typename F>
+__device__ __forceinline__ T sum_chains4(int n, F term) {
+    T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    int j = 0;
+    for (; j + 3 < n; j += 4) {
+        c0 = add_rn(c0, term(j));
+        c1 = add_rn(c1, term(j + 1));
+        c2 = add_rn(c2, term(j + 2));
+        c3 = add_rn(c3, term(j + 3));
     }
-    const R* w = xr + (p == 1 ? 0 : Q);
-    R racc = 0;
-    for (int k = k0; k < k1; ++k) racc = fma(w[k], h[k * stride], racc);
-    return (double)racc;
+    if (j < n) c0 = add_rn(c0, term(j));
+    if (j + 1 < n) c1 = add_rn(c1, term(j + 1));
+    if (j + 2 < n) c2 = add_rn(c2, term(j + 2));
+    return add_rn(add_rn(c0, c1), add_rn(c2, c3));
 }
 
-// Parts of a moment sum.  FP32 state (whose stage leaves only a few warps
-// of FP64 work at its end): 4 where the staging block of
-// tile_moment_sums_staged holds them (kNumMoments x 4 doubles per node),
-// else 2, else 1.  FP64 state: 1 (one sum per warp measured faster there:
-// the FP64 stage keeps all its warps on FP64 work anyway).
-template <typename R>
-__host__ __device__ inline int moment_parts(int Q) {
-    if (std::is_same<R, double>::value) return 1;
-    const int room = (int)sizeof(R) * 4 * Q;   // bytes per node of the 4 Q Z-element block
-    return room >= 8 * kNumMoments * 4 ? 4 : (room >= 8 * kNumMoments * 2 ? 2 : 1);
-}
-
-// The fixed combination of the parts: ((p0 + p1) + (p2 + p3)) for four.
-__device__ __forceinline__ double combine_parts(const double* v, int P) {
-    if (P == 4) return (v[0] + v[1]) + (v[2] + v[3]);
-    if (P == 2) return v[0] + v[1];
-    return v[0];
+// Sum of n stored terms v[j * stride], in the order of sum_chains4.
+template <typename T>
+__device__ __forceinline__ T sum_pair_terms(const T* v, int n, long long stride) {
+    return sum_chains4<T>(n, [&](int j) { return v[j * stride]; });
 }
 
 template <typename R>
 __device__ __forceinline__ double moment_sum(int which, int Q, const R* h, long long stride,
                                              const double* __restrict__ xp, const R* __restrict__ xr) {
-    const int P = moment_parts<R>(Q);
-    double v[4];
-    for (int q = 0; q < P; ++q) v[q] = moment_part<R>(which, Q, q * Q / P, (q + 1) * Q / P, h, stride, xp, xr);
-    return combine_parts(v, P);
+    const int p = (which >= MOM_G0) ? which - MOM_G0 : which;   // power of xi
+    if constexpr (std::is_same<R, double>::value) {
+        const double* w = xp + (p > 0 ? p - 1 : 0) * Q;
+        auto acc = [&](double a, int k) { return p == 0 ? a + h[k * stride] : fma(w[k], h[k * stride], a); };
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = 0;
+        for (; k + 3 < Q; k += 4) {
+            a0 = acc(a0, k);
+            a1 = acc(a1, k + 1);
+            a2 = acc(a2, k + 2);
+            a3 = acc(a3, k + 3);
+        }
+        for (; k < Q; ++k) a0 = acc(a0, k);
+        return (a0 + a1) + (a2 + a3);
+    } else {
+        const int H = (Q + 1) / 2, G = (H + 1) / 2;
+        auto ha = [&](int j) { return h[j * stride]; };
+        auto hb = [&](int j) { return (Q - 1 - j != j) ? h[(Q - 1 - j) * stride] : 0.f; };
+        if (moment_is_f64(which)) {
+            auto term = [&](int j) { return pair_term_f64(which, j, Q, f2d_bits(ha(j)), f2d_bits(hb(j)), xp); };
+            return sum_chains4<double>(
+                G, [&](int g) { return 2 * g + 1 < H ? __dadd_rn(term(2 * g), term(2 * g + 1)) : term(2 * g); });
+        }
+        auto term = [&](int j) { return pair_term_f32(which, j, Q, ha(j), hb(j), xr); };
+        return (double)sum_chains4<float>(
+            G, [&](int g) { return 2 * g + 1 < H ? __fadd_rn(term(2 * g), term(2 * g + 1)) : term(2 * g); });
+    }
+}
+
+// The group terms of the four FP64 and two R moment sums for group g of
+// one node t and distribution d: pairs j0 = 2g and j1 = 2g+1 (two: j1 < H),
+// from the new state's values a0, b0 (velocity j0 and its mirror) and a1, b1;
+// b is 0 for a middle velocity.  Into t64[slot][g * Z + t] (S0, S1, S2, G0)
+// and t32[slot][g * Z + t] (S3, G1), slot blocks of G Z values.
+__device__ __forceinline__ void pair_terms_f32(int d, int g, bool two, int t, int Q, int Z, float a0, float b0,
+                                               float a1, float b1, const double* __restrict__ xp,
+                                               const float* __restrict__ xr, double* t64, float* t32) {
+    const int j0 = 2 * g, j1 = 2 * g + 1;
+    const size_t o = (size_t)g * Z + t, blk = (size_t)pair_groups(Q) * Z;
+    const double wa0 = f2d_bits(a0), wb0 = f2d_bits(b0), wa1 = f2d_bits(a1), wb1 = f2d_bits(b1);
+    auto t8 = [&](int which) {
+        const double x = pair_term_f64(which, j0, Q, wa0, wb0, xp);
+        return two ? __dadd_rn(x, pair_term_f64(which, j1, Q, wa1, wb1, xp)) : x;
+    };
+    auto t4 = [&](int which) {
+        const float x = pair_term_f32(which, j0, Q, a0, b0, xr);
+        return two ? __fadd_rn(x, pair_term_f32(which, j1, Q, a1, b1, xr)) : x;
+    };
+    if (d == 0) {
+        t64[o] = t8(MOM_S0);
+        t64[blk + o] = t8(MOM_S1);
+        t64[2 * blk + o] = t8(MOM_S2);
+        t32[o] = t4(MOM_S3);
+    } else {
+        t64[3 * blk + o] = t8(MOM_G0);
+        t32[blk + o] = t4(MOM_G1);
+    }
 }
 
 // Velocity powers of moment_sum from the tables xi (FP64) and rxi (R).
@@ -1156,43 +1215,18 @@ __device__ __forceinline__ void velocity_powers(int Q, const double* __restrict_
 
 // Raw moment sums of the tile held in s.F (columns 3 .. nz+2), from velocity
 // powers staged in shared memory (xp = [xi, xi^2, xi^3] FP64, xr = [xi, xi^3]
-// in R).  Called by all threads once the tile's velocity work is done.
+// in R).  Called by all threads once the tile's velocity work is done: one
+// sum per warp, lanes on nodes, where the tile allows.
 template <typename R>
 __device__ void tile_moment_sums_staged(const SlabDesc& sd, const WorkItem& it, const Smem<R>& s, int Z,
                                         const double* xp, const R* xr, double* __restrict__ mom_out, long long NN) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     if (nz <= 32 && blockDim.x >= 32 * kNumMoments) {
-        // one (kind, part) per warp task, lanes on nodes: the parts of a sum
-        // run on different warps, spread over the SM's sub-partitions (task i
-        // on warp i mod warps; the FP64 kinds first), and meet in the block
-        // of the coefficients and the analysis, free after the synthesis
-        const int P = moment_parts<R>(Q), nw = blockDim.x >> 5, t = threadIdx.x & 31;
-        if (P == 1) {   // one sum per warp, written directly
-            const int which = threadIdx.x >> 5;
-            if (which < kNumMoments && t < nz) {
-                const int d = which >= MOM_G0 ? 1 : 0;
-                const R* h = s.F + (size_t)d * Q * W + t + 3;
-                mom_out[which * NN + sd.node_off + it.i0 + t] = moment_part<R>(which, Q, 0, Q, h, W, xp, xr);
-            }
-            return;
-        }
-        double* part = reinterpret_cast<double*>(s.C);            // [kind][part][nz]
-        // FP64 kinds first: for R = float, S3 and G1 are the R-precision ones
-        const int order[kNumMoments] = {MOM_S0, MOM_S1, MOM_S2, MOM_G0, MOM_S3, MOM_G1};
-        for (int task = threadIdx.x >> 5; task < kNumMoments * P; task += nw) {
-            const int which = order[task / P], q = task % P;
-            if (t < nz) {
-                const int d = which >= MOM_G0 ? 1 : 0;
-                const R* h = s.F + (size_t)d * Q * W + t + 3;
-                part[(which * P + q) * nz + t] = moment_part<R>(which, Q, q * Q / P, (q + 1) * Q / P, h, W, xp, xr);
-            }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
-            const int which = e / nz, tt = e % nz;
-            double v[4];
-            for (int q = 0; q < P; ++q) v[q] = part[(which * P + q) * nz + tt];
-            mom_out[which * NN + sd.node_off + it.i0 + tt] = combine_parts(v, P);
+        const int which = threadIdx.x >> 5, t = threadIdx.x & 31;
+        if (which < kNumMoments && t < nz) {
+            const int d = which >= MOM_G0 ? 1 : 0;
+            const R* h = s.F + (size_t)d * Q * W + t + 3;
+            mom_out[which * NN + sd.node_off + it.i0 + t] = moment_sum<R>(which, Q, h, W, xp, xr);
         }
         return;
     }

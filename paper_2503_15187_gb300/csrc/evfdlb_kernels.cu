@@ -58,8 +58,10 @@ namespace evfdlb {
 //
 // The body runs one work item (slab tile) with the CTA's threads; CG: the
 // stage input, base and moment sums are read with L2-coherent loads (the
-// persistent form, where other CTAs of the same launch wrote them).
-template <typename R, bool DF, bool CG>
+// persistent form, where other CTAs of the same launch wrote them); FO: the
+// node fields of the stage input are also written to fields_out (a
+// compile-time choice, so that the other forms carry none of its registers).
+template <typename R, bool DF, bool CG, bool FO = false>
 __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& it, double* smem,
                                            const double* __restrict__ tables, const R* __restrict__ rtab,
                                            const double* __restrict__ taps, const R* __restrict__ rtaps,
@@ -69,6 +71,7 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
                                            unsigned* err) {
     const int Q = sd.Q, W = Z + 6, nz = it.nz;
     Smem<R> s = carve<R>(smem, Q, Z, sd.M);
+    double* const fo = FO ? fields_out : nullptr;
 
     // FP64 / FP32: parity-split tables and state tile (half the transform
     // products); FP64_DF: the full tables as float pairs and the state tile
@@ -121,10 +124,10 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     // warps are the longer side of the phase and the FP64 pipe the bound.
     constexpr bool WF = std::is_same<R, float>::value && !DF;
     if (threadIdx.x < 32 * NW) {
-        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, fields_out, threadIdx.x, 32 * NW);
+        node_fields_pass1<R>(sd, it, s, s.Mtap, NN, fo, threadIdx.x, 32 * NW);
         node_sync();
         if constexpr (WF) asm volatile("bar.sync 3, %0;" ::"r"((int)blockDim.x) : "memory");
-        node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, fields_out, threadIdx.x, 32 * NW);
+        node_fields_pass2<R, WF>(sd, it, s, Z, s.Ftap, mom_in, NN, err, fo, threadIdx.x, 32 * NW);
         node_sync();
         node_coefficients<R, !WF>(sd, it, s, Z, rt, threadIdx.x, 32 * NW);
     } else {
@@ -171,7 +174,11 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     // bv: the base value at (d, k, t), loaded by the caller ahead of its
     // synthesis loop so that the global load's latency is hidden
     auto gidx_of = [&](int d, int t, int k) { return d * NF + sd.f_off + (long long)k * sd.nx + it.i0 + t; };
-    auto emit = [&](int d, int t, int k, R syn, R ch, R cx, R bv) {
+    // The FP32 state's moment sums take their pair terms from the values
+    // written here (PT); the other forms sum the new tile after the
+    // synthesis, so emit stores it back into s.F.
+    constexpr bool PT = std::is_same<R, float>::value && !DF;
+    auto emit = [&](int d, int t, int k, R syn, R ch, R cx, R bv) -> R {
         R* hp = s.F + (size_t)(d * Q + k) * W + t + 3;
         const R h = *hp;
         const R* fc = s.Face + (size_t)(d * Q + k) * (Z + 1);
@@ -179,14 +186,15 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         const long long g = gidx_of(d, t, k);
         if (rhs_form) {
             rhs_out[g] = (double)fma(-xi[k] * inv_dx, df, fma(-s.Scr[t], h, syn));
-        } else {
-            R o = with_base ? ralpha * bv : R(0);
-            o = fma(ch, h, o);
-            o = fma(cs, syn, o);
-            o = fma(cx, df, o);
-            out[g] = o;
-            *hp = o;
+            return R(0);
         }
+        R o = with_base ? ralpha * bv : R(0);
+        o = fma(ch, h, o);
+        o = fma(cs, syn, o);
+        o = fma(cx, df, o);
+        out[g] = o;
+        if constexpr (!PT) *hp = o;
+        return o;
     };
     if constexpr (DF) {
         // four velocities per thread (four independent Dot2 chains hide the
@@ -213,6 +221,55 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
                 if (q < nk)
                     emit(d, t, k0 + q, df_join(a[q], b[q]), ch, csx * xi[k0 + q],
                          (with_base && !rhs_form) ? gload<CG>(base + gidx_of(d, t, k0 + q)) : R(0));
+        }
+    } else if constexpr (PT) {
+        // FP32, parity split: the velocity pairs (k, Q-1-k) of group g
+        // (k = 2g, 2g+1) for one node per task, so that each coefficient
+        // load serves both pairs (four independent chains); even orders
+        // build E, odd orders O, the synthesis is E + O at k and E - O at
+        // Q-1-k.  The task also forms the group's terms of the moment sums.
+        const ParitySplit ps(Q);
+        const int H = ps.H, QE2 = ps.QE / 2, G = pair_groups(Q);
+        const float2* Sp = reinterpret_cast<const float2*>(s.S);
+        const bool lb = with_base && !rhs_form;
+        for (int e = threadIdx.x; e < 2 * G * nz; e += blockDim.x) {
+            const int t = e % nz, r = e / nz;
+            const int g = r % G, d = r / G;
+            const int k0 = 2 * g;
+            const bool two = k0 + 1 < H;
+            const int k1 = two ? k0 + 1 : k0;
+            const bool pair0 = (Q - 1 - k0 != k0), pair1 = two && (Q - 1 - k1 != k1);
+            const R b00 = lb ? gload<CG>(base + gidx_of(d, t, k0)) : R(0);
+            const R b01 = (lb && pair0) ? gload<CG>(base + gidx_of(d, t, Q - 1 - k0)) : R(0);
+            const R b10 = (lb && two) ? gload<CG>(base + gidx_of(d, t, k1)) : R(0);
+            const R b11 = (lb && pair1) ? gload<CG>(base + gidx_of(d, t, Q - 1 - k1)) : R(0);
+            const R* c = s.C + (size_t)d * Q * Z + t;
+            const float2* sp0 = Sp + (size_t)k0 * QE2;
+            const float2* sp1 = Sp + (size_t)k1 * QE2;
+            R e0 = 0, o0 = 0, e1 = 0, o1 = 0;
+            int l = 0;
+            for (; l + 1 < Q; l += 2) {
+                const R c0 = c[l * Z], c1 = c[(l + 1) * Z];
+                const float2 u = sp0[l >> 1], w = sp1[l >> 1];
+                e0 = fma(u.x, c0, e0);
+                o0 = fma(u.y, c1, o0);
+                e1 = fma(w.x, c0, e1);
+                o1 = fma(w.y, c1, o1);
+            }
+            if (l < Q) {   // odd Q: the last (even) order
+                const R c0 = c[l * Z];
+                e0 = fma(sp0[l >> 1].x, c0, e0);
+                e1 = fma(sp1[l >> 1].x, c0, e1);
+            }
+            const R ch = fma(-cs, s.Scr[t], rbeta), cx0 = csx * xi[k0], cx1 = csx * xi[k1];
+            const R a0 = emit(d, t, k0, e0 + o0, ch, cx0, b00);
+            const R m0 = pair0 ? emit(d, t, Q - 1 - k0, e0 - o0, ch, -cx0, b01) : R(0);
+            R a1 = 0, m1 = 0;
+            if (two) {
+                a1 = emit(d, t, k1, e1 + o1, ch, cx1, b10);
+                m1 = pair1 ? emit(d, t, Q - 1 - k1, e1 - o1, ch, -cx1, b11) : R(0);
+            }
+            if (!rhs_form) pair_terms_f32(d, g, two, t, Q, Z, a0, m0, a1, m1, s.Vp, s.Vr, s.Mp64, s.Mp32);
         }
     } else {
         // parity split: one node pair (k, Q-1-k) per task; even orders build
@@ -247,7 +304,22 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     __syncthreads();
 
     // Phase 6: raw moment sums of the new stage for the next stage's node fields.
-    tile_moment_sums_staged<R>(sd, it, s, Z, s.Vp, s.Vr, mom_out, NN);
+    if constexpr (PT) {
+        // the group terms formed with the synthesis, summed per (moment, node)
+        const int G = pair_groups(Q);
+        const size_t blk = (size_t)G * Z;
+        for (int e = threadIdx.x; e < kNumMoments * nz; e += blockDim.x) {
+            const int which = e / nz, t = e - which * nz;
+            double v;
+            if (which == MOM_S3 || which == MOM_G1)
+                v = (double)sum_pair_terms<float>(s.Mp32 + (which == MOM_S3 ? 0 : blk) + t, G, Z);
+            else
+                v = sum_pair_terms<double>(s.Mp64 + (which == MOM_G0 ? 3 : which) * blk + t, G, Z);
+            mom_out[which * NN + sd.node_off + it.i0 + t] = v;
+        }
+    } else {
+        tile_moment_sums_staged<R>(sd, it, s, Z, s.Vp, s.Vr, mom_out, NN);
+    }
 }
 
 template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
@@ -256,13 +328,29 @@ stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ it
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
              const R* __restrict__ src, const R* base, R* out, double* rhs_out,
-             const double* __restrict__ mom_in, double* __restrict__ mom_out, double* __restrict__ fields_out,
+             const double* __restrict__ mom_in, double* __restrict__ mom_out,
              long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
     extern __shared__ __align__(16) double smem[];
     const WorkItem it = items[blockIdx.x];
     const SlabDesc sd = slabs[it.slab];
     stage_body<R, DF, false>(sd, it, smem, tables, rtab, taps, rtaps, src, base, out, rhs_out, mom_in, mom_out,
-                             fields_out, NF, NN, alpha, beta, mode, Z, err);
+                             nullptr, NF, NN, alpha, beta, mode, Z, err);
+}
+
+// The FP64 stage that also writes the node fields of its input state,
+// [EVFDLB_NFIELDS][NN] (the adjoint's segment recompute; the reverse sweep
+// reads them instead of forming them again).
+__global__ void __launch_bounds__(StageThreads<double>::value, 2)
+stage_fields_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
+                    const double* __restrict__ tables, const double* __restrict__ taps,
+                    const double* __restrict__ src, const double* base, double* out,
+                    const double* __restrict__ mom_in, double* __restrict__ mom_out, double* __restrict__ fields_out,
+                    long long NF, long long NN, double alpha, double beta, int Z, unsigned* err) {
+    extern __shared__ __align__(16) double smem[];
+    const WorkItem it = items[blockIdx.x];
+    const SlabDesc sd = slabs[it.slab];
+    stage_body<double, false, false, true>(sd, it, smem, tables, tables, taps, taps, src, base, out, nullptr, mom_in,
+                                           mom_out, fields_out, NF, NN, alpha, beta, 0, Z, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,8 +732,7 @@ void launch_stage_df(int nitems, size_t smem, cudaStream_t st, const SlabDesc* s
                      const double* base, double* out, double* rhs_out, const double* mom_in, double* mom_out,
                      long long NF, long long NN, double alpha, double beta, int mode, int Z, unsigned* err) {
     launch_pdl(stage_kernel<double, true>, nitems, StageThreads<double, true>::value, smem, st, slabs, items, tables,
-               dftab, taps, taps, src, base, out, rhs_out, mom_in, mom_out, nullptr, NF, NN, alpha, beta, mode, Z,
-               err);
+               dftab, taps, taps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
 template <typename R>
@@ -656,6 +743,10 @@ static cudaError_t configure_t(size_t smem_bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(iso_reset_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
+    if (std::is_same<R, double>::value) {
+        e = cudaFuncSetAttribute(stage_fields_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(fields_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
@@ -680,16 +771,14 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
     return cudaSuccess;
 }
 
-// The FP64 stage (8 warps; see StageThreads); fields_out (or null): the
-// node fields of the stage input, [EVFDLB_NFIELDS][NN].
+// The FP64 stage (8 warps; see StageThreads).
 static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                               const WorkItem* items, const double* tables, const double* rtab, const double* taps,
                               const double* rtaps, const double* src, const double* base, double* out,
                               double* rhs_out, const double* mom_in, double* mom_out, long long NF, long long NN,
-                              double alpha, double beta, int mode, int Z, unsigned* err,
-                              double* fields_out = nullptr) {
+                              double alpha, double beta, int mode, int Z, unsigned* err) {
     launch_pdl(stage_kernel<double>, nitems, StageThreads<double>::value, smem, st, slabs, items, tables, rtab, taps,
-               rtaps, src, base, out, rhs_out, mom_in, mom_out, fields_out, NF, NN, alpha, beta, mode, Z, err);
+               rtaps, src, base, out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
 }
 
 void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
@@ -700,7 +789,7 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
     if (prec == EVFDLB_FP32)
         launch_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
                    (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base, (float*)out,
-                   rhs_out, mom_in, mom_out, nullptr, NF, NN, alpha, beta, mode, Z, err);
+                   rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
     else
         launch_stage_fp64(nitems, smem, st, slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps,
                           (const double*)src, (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN,
@@ -714,8 +803,8 @@ void launch_stage_fields(int nitems, size_t smem, cudaStream_t st, const SlabDes
                          const double* tables, const double* taps, const double* src, const double* base,
                          double* out, const double* mom_in, double* mom_out, double* fields_out, long long NF,
                          long long NN, double alpha, double beta, int Z, unsigned* err) {
-    launch_stage_fp64(nitems, smem, st, slabs, items, tables, tables, taps, taps, src, base, out, nullptr, mom_in,
-                      mom_out, NF, NN, alpha, beta, 0, Z, err, fields_out);
+    launch_pdl(stage_fields_kernel, nitems, StageThreads<double>::value, smem, st, slabs, items, tables, taps, src, base,
+               out, mom_in, mom_out, fields_out, NF, NN, alpha, beta, Z, err);
 }
 
 // FP64 stage (mode 0 writes out; mode 1 writes the right-hand side to out).
