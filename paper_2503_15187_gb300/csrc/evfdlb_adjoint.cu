@@ -100,21 +100,25 @@ __host__ __device__ inline size_t adj_smem_doubles(int Q, int Z) { return AdjLay
 // Gradient of the WENO-5 face value Phi(v0..v4) (upwind side v0..v2), times
 // pb: g_r = pb dPhi/dv_r.  Phi is taken in the difference form of the forward
 // faces: with d_i = v_{i+1} - v_i, t_0 = d1 - d0, t_1 = d2 - d1, t_2 = d3 - d2,
-// s_0 = 3 d1 - d0, s_1 = d1 + d2, s_2 = d3 - 3 d2,
-//   e_r = s_r^2 + 13/3 t_r^2 + 4 eps   (= 4 (eps + beta_r)),
+// s_0 = 3 d1 - d0, s_1 = d1 + d2, s_2 = d3 - 3 d2, k_r = 13/3 t_r,
+//   e_r = s_r^2 + k_r t_r + 4 eps   (= 4 (eps + beta_r)),
 //   a_0 = e_1^2 e_2^2, a_1 = e_0^2 e_2^2, a_2 = e_0^2 e_1^2,
 //   c_0 = (5 d1 - 2 d0)/60, c_1 = (d1 + 2 d2)/10, c_2 = (4 d2 - d3)/20,
 //   Phi = v2 + (sum a_r c_r) / (0.1 a_0 + 0.6 a_1 + 0.3 a_2),
-// differentiated in reverse order (one division per face).
+// differentiated in reverse order (one division per face).  With
+// P_r = 4 e_r dL/dE_r (E_r = e_r^2) the adjoints of s_r and k_r t_r's
+// argument are s_r P_r and k_r P_r, so the d-adjoints take the combinations
+// s_r +- k_r and 3 s_r + k_r directly.
 __device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, double v3, double v4, double eps,
                                            double pb, double g[5]) {
     const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3;
     const double t0 = d1 - d0, t1 = d2 - d1, t2 = d3 - d2;
     const double s0 = fma(3.0, d1, -d0), s1 = d1 + d2, s2 = fma(-3.0, d2, d3);
     const double e4 = 4.0 * eps, k133 = 13.0 / 3.0;
-    const double e0 = fma(s0, s0, fma(k133 * t0, t0, e4));
-    const double e1 = fma(s1, s1, fma(k133 * t1, t1, e4));
-    const double e2 = fma(s2, s2, fma(k133 * t2, t2, e4));
+    const double k0 = k133 * t0, k1 = k133 * t1, k2 = k133 * t2;
+    const double e0 = fma(s0, s0, fma(k0, t0, e4));
+    const double e1 = fma(s1, s1, fma(k1, t1, e4));
+    const double e2 = fma(s2, s2, fma(k2, t2, e4));
     const double E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
     const double a0 = E1 * E2, a1 = E0 * E2, a2 = E0 * E1;
     const double c0 = fma(5.0 / 60.0, d1, (-2.0 / 60.0) * d0);
@@ -125,18 +129,15 @@ __device__ __forceinline__ void weno5_grad(double v0, double v1, double v2, doub
     const double iden = div_nr(1.0, den);
     const double R = pb * iden;
     const double psi = num * iden;             // Phi - v2
-    // adjoints (all times pb)
+    const double R4 = 4.0 * R;
+    // adjoints (all times pb): of c_r, of a_r (times 4), of E_r (times 4)
     const double gc0 = a0 * R, gc1 = a1 * R, gc2 = a2 * R;
-    const double gA0 = R * fma(-0.1, psi, c0), gA1 = R * fma(-0.6, psi, c1), gA2 = R * fma(-0.3, psi, c2);
-    const double gE0 = fma(gA1, E2, gA2 * E1), gE1 = fma(gA0, E2, gA2 * E0), gE2 = fma(gA0, E1, gA1 * E0);
-    const double ge0 = 2.0 * e0 * gE0, ge1 = 2.0 * e1 * gE1, ge2 = 2.0 * e2 * gE2;
-    const double gs0 = 2.0 * s0 * ge0, gs1 = 2.0 * s1 * ge1, gs2 = 2.0 * s2 * ge2;
-    const double k263 = 26.0 / 3.0;
-    const double gt0 = k263 * t0 * ge0, gt1 = k263 * t1 * ge1, gt2 = k263 * t2 * ge2;
-    const double gd0 = -gs0 - gt0 + (-2.0 / 60.0) * gc0;
-    const double gd1 = fma(3.0, gs0, gs1) + gt0 - gt1 + fma(5.0 / 60.0, gc0, 0.1 * gc1);
-    const double gd2 = fma(-3.0, gs2, gs1) + gt1 - gt2 + fma(0.2, gc1, 0.2 * gc2);
-    const double gd3 = gs2 + gt2 - 0.05 * gc2;
+    const double gA0 = R4 * fma(-0.1, psi, c0), gA1 = R4 * fma(-0.6, psi, c1), gA2 = R4 * fma(-0.3, psi, c2);
+    const double P0 = e0 * fma(gA1, E2, gA2 * E1), P1 = e1 * fma(gA0, E2, gA2 * E0), P2 = e2 * fma(gA0, E1, gA1 * E0);
+    const double gd0 = fma(-P0, s0 + k0, (-2.0 / 60.0) * gc0);
+    const double gd1 = fma(P0, fma(3.0, s0, k0), fma(P1, s1 - k1, fma(5.0 / 60.0, gc0, 0.1 * gc1)));
+    const double gd2 = fma(P1, s1 + k1, fma(-P2, fma(3.0, s2, k2), 0.2 * (gc1 + gc2)));
+    const double gd3 = fma(P2, s2 + k2, -0.05 * gc2);
     g[0] = -gd0;
     g[1] = gd0 - gd1;
     g[2] = pb + gd1 - gd2;
