@@ -118,10 +118,10 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     // FP32: the Eq. (F1) force sums need only the staged densities, so the
     // worker warps (whose FP32 work finishes well before the node chain)
     // form them first, a half-warp per node, and signal on named barrier 3
-    // without waiting; the node warps take them up before pass 2.  The
-    // workers also form the Hermite moments of the local Gaussian after
-    // their faces.  FP64 keeps both in the node chain: there the worker
-    // warps are the longer side of the phase and the FP64 pipe the bound.
+    // without waiting; the node warps take them up before pass 2.  The last
+    // worker warp forms the Hermite moments of the local Gaussian meanwhile.
+    // FP64 keeps both in the node chain: there the worker warps are the
+    // longer side of the phase and the FP64 pipe the bound.
     constexpr bool WF = std::is_same<R, float>::value && !DF;
     if (threadIdx.x < 32 * NW) {
         node_fields_pass1<R>(sd, it, s, s.Mtap, NN, fo, threadIdx.x, 32 * NW);
@@ -133,6 +133,12 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
     } else {
         const int tid = threadIdx.x - 32 * NW, nth = blockDim.x - 32 * NW;
         if constexpr (WF) {
+            // the Hermite moments of the local Gaussian (a serial recurrence
+            // per node) need only u and T of the node inputs: the last worker
+            // warp, whose share of the force sums (a half-warp per node from
+            // the first worker) is empty on tiles of up to nth/16 - 2 nodes,
+            // forms them first, beside the other workers' force sums
+            if (tid >= nth - 32) node_hermite_moments<R>(sd, it, s, Z, rt, tid - (nth - 32), 32);
             tile_force_sums<R>(sd, it, s, Z, s.Ftap, tid, nth);
             __threadfence_block();
             asm volatile("bar.arrive 3, %0;" ::"r"((int)blockDim.x) : "memory");
@@ -148,9 +154,6 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
         }
         if constexpr (DF) faces_df(sd, it, s, Z, tables, tid, nth);
         else faces<R>(sd, it, s, Z, vtab, tid, nth);
-        // FP32: the Hermite moments of the local Gaussian need only u and T
-        // of the node inputs, so the worker warps form them too
-        if constexpr (WF) node_hermite_moments<R>(sd, it, s, Z, rt, tid, nth);
     }
     __syncthreads();
     coefficients<R, DF>(sd, it, s, Z, rt, threadIdx.x, blockDim.x);

@@ -118,6 +118,40 @@ def test_fp32_hundred_steps_moments():
     assert en < 1e-4 and eT < 1e-4                 # 100 x the per-step bar
 
 
+@pytest.mark.parametrize("name", ["outflow_q32_slab", "periodic_q15_odd"])
+@pytest.mark.parametrize("after", ["stage", "set_state"])
+def test_fp32_conserved_sums_are_fp64_sums_of_the_state(name, after):
+    """The per-node sums of the conserved moments of an FP32 state are FP64
+    sums of its stored float values: n = sum_k F_k, n u = sum_k xi_k F_k,
+    n (3/2 T + u^2/2) = sum_k (xi_k^2 F_k / 2 + G_k), to FP64 rounding of a
+    Q-term sum (Q 2^-53 of the sum of magnitudes), where FP32 accumulation
+    would err by ~1e-7.  Formed by the stage kernel (the pair terms of its
+    synthesis) and, after set_state, by the sums kernel."""
+    sim, orc, n0, u0, T0 = make(name)
+    if after == "stage":
+        sim.init(n0, u0, T0)
+        sim.step(3)
+    else:
+        F, G = orc.equilibrium(n0, u0, T0)
+        F, G = orc.step(F, G, 2)
+        sim.set_state(F.ravel(), G.ravel())
+    F, G = sim.state_2d()                          # the stored floats, widened exactly
+    assert np.array_equal(F, F.astype(np.float32).astype(np.float64))
+    xi, _ = ev.velocity_set(F.shape[0])
+    n, u, T, _, _ = sim.moments()
+    Q = F.shape[0]
+    bound = 4 * Q * 2.0 ** -53
+    S0 = F.sum(axis=0)
+    S1 = (xi[:, None] * F).sum(axis=0)
+    E = (0.5 * xi[:, None] ** 2 * F + G).sum(axis=0)
+    mag1 = (np.abs(xi)[:, None] * F).sum(axis=0)
+    e0 = np.abs(n - S0).max() / S0.max()
+    e1 = (np.abs(n * u - S1) / mag1).max()
+    e2 = (np.abs(n * (1.5 * T + 0.5 * u * u) - E) / E).max()
+    print(f"{name} after {after}: mass {e0:.1e} momentum {e1:.1e} energy {e2:.1e} (bound {bound:.1e})")
+    assert e0 < bound and e1 < 4 * bound and e2 < 4 * bound
+
+
 def test_fp32_mass_conserved_to_fp32_rounding():
     sim, orc, n0, u0, T0 = make("periodic_q16_noise")
     sim.init(n0, u0, T0)
