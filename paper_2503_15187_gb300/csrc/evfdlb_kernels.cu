@@ -275,33 +275,63 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
             if (!rhs_form) pair_terms_f32(d, g, two, t, Q, Z, a0, m0, a1, m1, s.Vp, s.Vr, s.Mp64, s.Mp32);
         }
     } else {
-        // parity split: one node pair (k, Q-1-k) per task; even orders build
-        // E, odd orders O (one two-wide table load per two orders); the
+        // parity split: one velocity pair (k, Q-1-k) per task; even orders
+        // build E, odd orders O (one two-wide table load per two orders); the
         // synthesis is E + O at k and E - O at Q-1-k
         using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
         const ParitySplit ps(Q);
         const int H = ps.H, QE2 = ps.QE / 2;
         const R2* Sp = reinterpret_cast<const R2*>(s.S);
-        for (int e = threadIdx.x; e < 2 * H * nz; e += blockDim.x) {
-            const int t = e % nz, r = e / nz;
-            const int k = r % H, d = r / H;
-            const R* c = s.C + (size_t)d * Q * Z + t;
-            const R2* sp = Sp + (size_t)k * QE2;
-            const bool pair = (Q - 1 - k != k), lb = with_base && !rhs_form;
-            const R b0 = lb ? gload<CG>(base + gidx_of(d, t, k)) : R(0);
-            const R b1 = (lb && pair) ? gload<CG>(base + gidx_of(d, t, Q - 1 - k)) : R(0);
-            R ev = 0, od = 0;
-            int l = 0;
-            for (; l + 1 < Q; l += 2) {
-                const R2 sv = sp[l >> 1];
-                ev = fma(sv.x, c[l * Z], ev);
-                od = fma(sv.y, c[(l + 1) * Z], od);
+        // NODES nodes per task, t0 and t1 = t0 + ceil(nz/2) for two (four
+        // independent chains per thread, each table load serving both
+        // nodes); two where that saves a round of tasks or still fills
+        // every thread, else one (small tiles: more warps in the phase)
+        const bool lb = with_base && !rhs_form;
+        auto synth = [&](auto nodes) {
+            constexpr int NODES = decltype(nodes)::value;
+            const int nzh = (nz + NODES - 1) / NODES;
+            for (int e = threadIdx.x; e < 2 * H * nzh; e += blockDim.x) {
+                const int t0 = e % nzh, r = e / nzh;
+                const int t1 = t0 + nzh;
+                const bool two = NODES == 2 && t1 < nz;
+                const int k = r % H, d = r / H;
+                const R* c = s.C + (size_t)d * Q * Z + t0;
+                const R2* sp = Sp + (size_t)k * QE2;
+                const bool pair = (Q - 1 - k != k);
+                const R b0 = lb ? gload<CG>(base + gidx_of(d, t0, k)) : R(0);
+                const R b1 = (lb && pair) ? gload<CG>(base + gidx_of(d, t0, Q - 1 - k)) : R(0);
+                const R b2 = (lb && two) ? gload<CG>(base + gidx_of(d, t1, k)) : R(0);
+                const R b3 = (lb && pair && two) ? gload<CG>(base + gidx_of(d, t1, Q - 1 - k)) : R(0);
+                R ev = 0, od = 0, ev1 = 0, od1 = 0;
+                const int dt1 = two ? nzh : 0;      // a lone last node repeats t0 (results unused)
+                int l = 0;
+                for (; l + 1 < Q; l += 2) {
+                    const R2 sv = sp[l >> 1];
+                    ev = fma(sv.x, c[l * Z], ev);
+                    od = fma(sv.y, c[(l + 1) * Z], od);
+                    if constexpr (NODES == 2) {
+                        ev1 = fma(sv.x, c[l * Z + dt1], ev1);
+                        od1 = fma(sv.y, c[(l + 1) * Z + dt1], od1);
+                    }
+                }
+                if (l < Q) {   // odd Q: the last (even) order
+                    ev = fma(sp[l >> 1].x, c[l * Z], ev);
+                    if constexpr (NODES == 2) ev1 = fma(sp[l >> 1].x, c[l * Z + dt1], ev1);
+                }
+                const R cx = csx * xi[k];
+                const R ch0 = fma(-cs, s.Scr[t0], rbeta);
+                emit(d, t0, k, ev + od, ch0, cx, b0);
+                if (pair) emit(d, t0, Q - 1 - k, ev - od, ch0, -cx, b1);
+                if (two) {
+                    const R ch1 = fma(-cs, s.Scr[t1], rbeta);
+                    emit(d, t1, k, ev1 + od1, ch1, cx, b2);
+                    if (pair) emit(d, t1, Q - 1 - k, ev1 - od1, ch1, -cx, b3);
+                }
             }
-            if (l < Q) ev = fma(sp[l >> 1].x, c[l * Z], ev);   // odd Q: the last (even) order
-            const R ch = fma(-cs, s.Scr[t], rbeta), cx = csx * xi[k];
-            emit(d, t, k, ev + od, ch, cx, b0);
-            if (pair) emit(d, t, Q - 1 - k, ev - od, ch, -cx, b1);
-        }
+        };
+        const int nth = blockDim.x, T1 = 2 * H * nz, T2 = 2 * H * ((nz + 1) / 2);
+        if ((T2 + nth - 1) / nth < (T1 + nth - 1) / nth || T2 >= nth) synth(std::integral_constant<int, 2>{});
+        else synth(std::integral_constant<int, 1>{});
     }
     if (mode == 1) return;
     __syncthreads();
