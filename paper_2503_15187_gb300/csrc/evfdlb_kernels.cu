@@ -356,7 +356,7 @@ __device__ __forceinline__ void stage_body(const SlabDesc& sd, const WorkItem& i
 }
 
 template <typename R, bool DF = false, int T = StageThreads<R, DF>::value>
-__global__ void __launch_bounds__(T, DF ? 3 : (std::is_same<R, double>::value ? 2 : 1))
+__global__ void __launch_bounds__(T, DF ? 3 : ((std::is_same<R, double>::value || T <= 256) ? 2 : 1))
 stage_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict__ items,
              const double* __restrict__ tables, const R* __restrict__ rtab,
              const double* __restrict__ taps, const R* __restrict__ rtaps,
@@ -772,6 +772,11 @@ template <typename R>
 static cudaError_t configure_t(size_t smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
+    if (std::is_same<R, float>::value) {
+        e = cudaFuncSetAttribute(stage_kernel<float, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(init_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(iso_reset_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -804,6 +809,20 @@ cudaError_t ensure_stage_smem(size_t smem_bytes) {
     return cudaSuccess;
 }
 
+// SMs of the current device (cached per device).
+static int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
 // The FP64 stage (8 warps; see StageThreads).
 static void launch_stage_fp64(int nitems, size_t smem, cudaStream_t st, const SlabDesc* slabs,
                               const WorkItem* items, const double* tables, const double* rtab, const double* taps,
@@ -819,11 +838,19 @@ void launch_stage_p(int prec, int nitems, size_t smem, cudaStream_t st, const Sl
                     const void* rtaps, const void* src, const void* base, void* out, double* rhs_out,
                     const double* mom_in, double* mom_out, long long NF, long long NN, double alpha, double beta,
                     int mode, int Z, unsigned* err) {
-    if (prec == EVFDLB_FP32)
-        launch_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
-                   (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base, (float*)out,
-                   rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
-    else
+    if (prec == EVFDLB_FP32) {
+        // the 16-warp form (one CTA per SM) where the work list fits one wave
+        // on the SMs, else the 8-warp form (two CTAs per SM), which finishes
+        // up to twice as many tiles in a wave
+        if (nitems <= sm_count())
+            launch_pdl(stage_kernel<float>, nitems, StageThreads<float>::value, smem, st, slabs, items, tables,
+                       (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base,
+                       (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+        else
+            launch_pdl(stage_kernel<float, false, 256>, nitems, 256, smem, st, slabs, items, tables,
+                       (const float*)rtab, taps, (const float*)rtaps, (const float*)src, (const float*)base,
+                       (float*)out, rhs_out, mom_in, mom_out, NF, NN, alpha, beta, mode, Z, err);
+    } else
         launch_stage_fp64(nitems, smem, st, slabs, items, tables, (const double*)rtab, taps, (const double*)rtaps,
                           (const double*)src, (const double*)base, (double*)out, rhs_out, mom_in, mom_out, NF, NN,
                           alpha, beta, mode, Z, err);
