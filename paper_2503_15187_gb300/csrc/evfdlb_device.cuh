@@ -151,7 +151,16 @@ __device__ inline Smem<R> carve(double* base, int Q, int Z, int M) {
 
 enum { SC_N = 0, SC_U, SC_T, SC_NU, SC_FORCE, SC_KQ, SC_K, SC_A, SC_B, SC_D };
 
-__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+// IEEE tests by the bit pattern: integer operations, not the FP64 pipe
+// (whose compares sit on the node chain's critical path).
+__device__ __forceinline__ bool finite(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+// x > 0: false for +-0, negatives and NaN, true for +inf
+__device__ __forceinline__ bool positive(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
 
 // Global load of data that other CTAs of the same launch may have written
 // (CG: cached in L2 only, never a stale L1 line), or an ordinary load.
@@ -571,7 +580,7 @@ __device__ void node_fields_pass2(const SlabDesc& sd, const WorkItem& it, const 
         if constexpr (std::is_same<R, float>::value) s.Scr[t] = d2f_bits(nu);
         else s.Scr[t] = (R)nu;
         s.Scr[Z + t] = f1r;
-        if (!(n > 0.0) || !(T > 0.0)) {
+        if (!positive(n) || !positive(T)) {
             atomicOr(err, (finite(n) && finite(T)) ? ERR_NEGATIVE : ERR_NONFINITE);
         } else if (!finite(f1) || !finite(nu) || !finite(q) || !finite(A) || !finite(B)) {
             atomicOr(err, ERR_NONFINITE);
