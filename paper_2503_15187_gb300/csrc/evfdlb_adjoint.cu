@@ -52,6 +52,13 @@ enum { FL_N = 0, FL_U, FL_T, FL_Q, FL_NBAR, FL_CHI, FL_F1, FL_MU, FL_TAU, FL_PR,
 enum { J_NNU = 0, J_TNU, J_CNU, J_QKQ, J_NKQ, J_CKQ, J_NK, J_CK, J_IX, J_AIX, J_IT, J_BIT, kNumJac };
 
 constexpr int kZAdj = 32;   // largest node tile of the sweep kernels
+
+// Sign of a velocity by its bit pattern (+1, -1, 0 for +-0): integer
+// operations, not compares on the FP64 pipe.
+__device__ __forceinline__ int xsign(double x) {
+    const long long b = __double_as_longlong(x);
+    return (b << 1) == 0 ? 0 : (b < 0 ? -1 : 1);
+}
 constexpr int kSumChunks = 4;    // lanes per (distribution, node) of the Hermite sums
 constexpr int kTapChunks = 8;    // lanes per node of the tap correlations
 
@@ -307,17 +314,18 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
                 const int p = e % nz, r = e / nz;
                 const int k = r % Q, d = r / Q;
                 const double x = sxi[k];
+                const int sg = xsign(x);
                 double gg[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
                 const double* h = sH + (size_t)r * WH + p;      // h[c] = node p - 3 + c
                 const double* v = sV + (size_t)r * WV + p;      // ybar at nodes p - 1, p
-                if (x > 0.0) {
+                if (sg > 0) {
                     weno5_grad(h[0], h[1], h[2], h[3], h[4], eps, x * rdz * (v[1] - v[0]), gg);
-                } else if (x < 0.0) {
+                } else if (sg < 0) {
                     weno5_grad(h[5], h[4], h[3], h[2], h[1], eps, x * rdz * (v[1] - v[0]), gg);
                 }
 #pragma unroll
                 for (int s = 0; s < 5; ++s) sG5[((size_t)s * 2 * Q + r) * Z + p] = gg[s];
-                const bool edge = (x > 0.0) ? (p < 3 || p + 1 >= nz) : (x < 0.0 && (p < 2 || p + 2 >= nz));
+                const bool edge = (sg > 0) ? (p < 3 || p + 1 >= nz) : (sg < 0 && (p < 2 || p + 2 >= nz));
                 if (edge) {
                     double* gf = gface + d * NF + row0 + (long long)k * nx + p;
 #pragma unroll
@@ -352,13 +360,13 @@ adj_local_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restrict_
         if (l >= 2) cl = fma(c[2 * Z] * sr2[l], m[(l - 2) * Z], cl);
         if (l >= 3) cl = fma(c[3 * Z] * sr3[l], m[(l - 3) * Z], cl);
         sCl[(size_t)r * Z + t] = cl;
-        const double x = sxi[l];
+        const int sg = xsign(sxi[l]);
         double hw = 0.0;
-        if (x != 0.0) {
+        if (sg != 0) {
             // xi > 0: faces p = t-1 .. t+3, node t is v_{t-p+3}; xi < 0: p = t-2 .. t+2, v_{p+2-t}
-            const int plo = (x > 0.0) ? t - 1 : t - 2;
+            const int plo = (sg > 0) ? t - 1 : t - 2;
             for (int p = max(plo, 0); p <= min(plo + 4, nz - 1); ++p) {
-                const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
+                const int s = (sg > 0) ? t - p + 3 : p + 2 - t;
                 hw += sG5[((size_t)s * 2 * Q + r) * Z + p];
             }
         }
@@ -649,13 +657,13 @@ adj_moments_kernel(const SlabDesc* __restrict__ slabs, const WorkItem* __restric
         const int k = r % Q, d = r / Q;
         const long long row = d * NF + sd.f_off + (long long)k * nx;
         double v = out[row + it.i0 + t];
-        const double x = xi[k];
-        if (x != 0.0) {
-            const int plo = (x > 0.0) ? t - 1 : t - 2;
+        const int sg = xsign(xi[k]);
+        if (sg != 0) {
+            const int plo = (sg > 0) ? t - 1 : t - 2;
             if (plo < 0 || plo + 4 >= nz) {
                 for (int p = plo; p <= plo + 4; ++p) {
                     if (p >= 0 && p < nz) continue;
-                    const int s = (x > 0.0) ? t - p + 3 : p + 2 - t;
+                    const int s = (sg > 0) ? t - p + 3 : p + 2 - t;
                     v += gface[s * 2 * NF + row + gidx(it.i0 + p, nx, bc)];
                 }
             }
